@@ -1,0 +1,157 @@
+"""Pins of the FP64 forward-backward oracle (App. A, B, F of arXiv 2207.11336)."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import fb
+from oracle import nufft as nu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "appF_parameters.txt")
+
+
+def _small_problem(n=8, K=16, M=300, seed=11):
+    rng = np.random.default_rng(seed)
+    omega = rng.uniform(-0.8 * np.pi, 0.8 * np.pi, (M, 2))
+    return nu.Operator(n, K, omega), rng
+
+
+def _dense_normal(op):
+    n = op.n
+    A = np.empty((n * n, n * n))
+    for i in range(n * n):
+        e = np.zeros(n * n)
+        e[i] = 1.0
+        A[:, i] = op.normal(e.reshape(n, n)).ravel()
+    return A
+
+
+def test_gradient_matches_finite_differences():
+    op, rng = _small_problem()
+    x = rng.random((op.n, op.n))
+    y = op.forward(rng.random((op.n, op.n))) + 0.01 * synth.complex_normal(op.M, rng)
+    g = fb.gradient(op, x, y)
+    h = 1e-5
+    for _ in range(6):
+        i, j = rng.integers(0, op.n, 2)
+        e = np.zeros_like(x)
+        e[i, j] = h
+        fd = (fb.data_fidelity(op, x + e, y) - fb.data_fidelity(op, x - e, y)) / (2 * h)
+        assert g[i, j] == pytest.approx(fd, rel=1e-7, abs=1e-9 * abs(g).max())
+
+
+def test_normal_operator_is_symmetric_psd():
+    op, _ = _small_problem()
+    A = _dense_normal(op)
+    assert np.allclose(A, A.T, atol=1e-9 * abs(A).max())
+    assert np.linalg.eigvalsh(0.5 * (A + A.T)).min() > -1e-9 * abs(A).max()
+
+
+def test_power_iteration_equals_dense_spectral_norm():
+    op, rng = _small_problem()
+    A = _dense_normal(op)
+    lam = np.linalg.eigvalsh(0.5 * (A + A.T)).max()
+    L, v, it = fb.power_iteration(op, rng.standard_normal((op.n, op.n)), 5000, 1e-14)
+    assert L == pytest.approx(lam, rel=1e-10)
+
+
+def test_psf_peak_equals_M_and_bounds_L():
+    # unit weights: (Re{Phi^H Phi} delta)(0) = sum_m |1|^2 = M up to NUFFT error
+    op, rng = _small_problem(n=16, K=32, M=400)
+    beta = fb.psf_peak(op)
+    assert beta == pytest.approx(op.M, rel=1e-5)
+    L, _, _ = fb.power_iteration(op, rng.standard_normal((16, 16)), 3000, 1e-12)
+    assert L >= beta * (1 - 1e-9)
+
+
+def test_appF_printed_parameter_arithmetic():
+    rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
+    for band, noise_mjy, peak_jy, dr_printed in rows[:2]:
+        dr = fb.dynamic_range(float(peak_jy), float(noise_mjy) * 1e-3)
+        # printed with two significant figures ("5x10^5" for 4.93e5)
+        assert dr == pytest.approx(float(dr_printed), rel=0.02), band
+    _, dr_train, sigma = rows[2]
+    assert fb.sigma_from_dynamic_range(float(dr_train)) == pytest.approx(float(sigma), rel=1e-12)
+    # Eq. sigma and its inverse agree
+    tau, L = 0.3, 7.0e4
+    a = fb.alpha_for_denoiser(tau, L, 2.5e-6)
+    assert fb.sigma_heuristic(tau, a, L) == pytest.approx(2.5e-6, rel=1e-12)
+    assert fb.soft_threshold_from_noise(tau, L) == pytest.approx(tau / np.sqrt(2 * L))
+
+
+def test_haar_is_orthonormal():
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal((8, 12))
+    c = fb.haar_analysis(x)
+    assert np.allclose(fb.haar_synthesis(*c), x, atol=1e-15)
+    assert sum(np.sum(ci ** 2) for ci in c) == pytest.approx(np.sum(x ** 2), rel=1e-14)
+    # explicit 4x4 analysis matrix is orthogonal
+    B = np.array([fb.np.concatenate([ci.ravel() for ci in fb.haar_analysis(e.reshape(2, 2))])
+                  for e in np.eye(4)])
+    assert np.allclose(B @ B.T, np.eye(4), atol=1e-15)
+
+
+@pytest.mark.parametrize("c,t", [(1.0, 0.5), (0.2, 0.5), (0.25, 0.5), (3.0, 0.0), (-1.0, 0.3)])
+def test_haar_denoise_constant_block_closed_form(c, t):
+    z = np.full((2, 2), c)
+    expect = max(0.0, c - t / 2) if 2 * c > t else 0.0
+    if c < 0:
+        expect = 0.0
+    assert np.allclose(fb.haar_denoise(z, t), expect, atol=1e-15)
+
+
+def test_haar_denoise_t0_is_positivity():
+    z = np.random.default_rng(4).standard_normal((6, 6))
+    assert np.allclose(fb.haar_denoise(z, 0.0), np.maximum(z, 0.0), atol=1e-15)
+
+
+def test_haar_soft_threshold_is_prox():
+    # u* = Psi S_t Psi^T z minimises t||Psi^T u||_1 + 1/2||z - u||^2 (App. A prox)
+    rng = np.random.default_rng(5)
+    z = rng.standard_normal((4, 4))
+    t = 0.4
+    u = fb.haar_denoise(z, t, positivity=False)
+
+    def obj(v):
+        return t * sum(np.abs(ci).sum() for ci in fb.haar_analysis(v)) + 0.5 * np.sum((z - v) ** 2)
+    base = obj(u)
+    for _ in range(300):
+        assert obj(u + 1e-3 * rng.standard_normal(u.shape)) >= base - 1e-12
+
+
+@pytest.mark.parametrize("mode", ["positivity", "haar"])
+def test_fb_objective_monotone_with_exact_prox(mode):
+    # Exact prox + gamma < 2/L => F(x^{k+1}) <= F(x^k) (sufficient decrease of FB).
+    op, rng = _small_problem(n=16, K=32, M=600)
+    x_true = np.maximum(rng.standard_normal((16, 16)), 0)
+    y = op.forward(x_true) + 0.05 * synth.complex_normal(op.M, rng)
+    L, _, _ = fb.power_iteration(op, rng.standard_normal((16, 16)), 3000, 1e-12)
+    gamma = fb.step_size(L)
+    t = 0.0 if mode == "positivity" else 0.05 * np.sqrt(op.M)
+    lam = t / gamma
+    if mode == "positivity":
+        den = lambda z: np.maximum(z, 0.0)           # noqa: E731
+        reg = lambda v: 0.0                          # noqa: E731
+    else:
+        den = lambda z: fb.haar_denoise(z, t, positivity=False)   # noqa: E731
+        reg = lambda v: lam * sum(np.abs(c).sum() for c in fb.haar_analysis(v))  # noqa: E731
+    x = np.zeros((16, 16))
+    F = [fb.data_fidelity(op, x, y) + reg(x)]
+    for _ in range(40):
+        x = den(fb.gradient_step(op, x, y, gamma))
+        F.append(fb.data_fidelity(op, x, y) + reg(x))
+    assert all(b <= a * (1 + 1e-12) + 1e-12 for a, b in zip(F, F[1:]))
+    assert F[-1] < F[0]
+
+
+def test_pnp_fb_fixed_point_and_history():
+    op, rng = _small_problem(n=16, K=32, M=600)
+    x_true = np.maximum(rng.standard_normal((16, 16)), 0)
+    y = op.forward(x_true)
+    L, _, _ = fb.power_iteration(op, rng.standard_normal((16, 16)), 3000, 1e-12)
+    gamma = fb.step_size(L)
+    den = lambda z: np.maximum(z, 0.0)   # noqa: E731
+    x, h = fb.pnp_fb(op, y, gamma, den, 3000, tol=1e-12, x_true=x_true)
+    assert np.allclose(den(fb.gradient_step(op, x, y, gamma)), x, atol=1e-8 * abs(x).max())
+    assert len(h["rel_change"]) == len(h["f"]) == len(h["snr"])
