@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""PnP-FB imaging throughput on one GB300 (iterations per second).
+
+Workload (default): 4096^2 float32 image, 8192^2 complex64 grid, M = 2e7
+synthetic MeerKAT-like visibilities in 64 radial data blocks, w folded into G
+with J in {7, 9, 12, 16} by |w| quartile (complex64 weights, int32 columns),
+40 dB input SNR, plain Haar-threshold denoiser (gamma = 1.98/L,
+t = tau / sqrt(2L)).  A step is one full PnP-FB iteration (forward FFT with
+padding and grid correction, fused de-gridding + residual + gridding pass,
+adjoint FFT with the fused gradient step, Haar prox, positivity and FP64
+norms), replayed as a captured CUDA graph.
+
+``--gpus N`` under torchrun runs N independent replicas (the path does not
+shard across GPUs here); ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PnP-FB iter/s (4096² img, 2e7 vis), learned vs plain at equal SNR (dB)"
+UNIT = "iter/s"
+WORKLOADS = {
+    "C3": dict(name="C3", desc="4096^2 image, 8192^2 grid, M=2e7 vis in 64 radial blocks, "
+                               "w-folded G J{7,9,12,16} c64+int32, Haar prox"),
+    "C1": dict(name="C1", desc="2048^2 image, 4096^2 grid, M=2e7 vis, w-folded G J{7,9,12,16} "
+                               "c64+int32, Haar prox"),
+    "C0": dict(name="C0", desc="256^2 image, 512^2 grid, M=2e5 vis, KB J=7, Haar prox"),
+}
+BLOCKS = {"C3": 64, "C1": 1, "C0": 1}
+CPU_SAMPLE_ROWS = 4000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="C3")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = threading.Thread(target=self._run, daemon=True)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([s.strip() for s in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 5 + i and s[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def src_hash(*names):
+    h = hashlib.sha256()
+    for nm in names:
+        with open(os.path.join(ROOT, "paper_2207_11336_gb300", "csrc", nm), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_file: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(f"{kernel_file}:{workload}")
+    if not e or e.get("src_sha") != src_hash(kernel_file):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def oracle_sample(prob, rows, x, y_rows, gamma, t):
+    """Time one oracle PnP-FB iteration on a row sample of G; returns (s/iter estimate, parts)."""
+    from oracle import fb as ofb
+    from oracle import nufft as onu
+    n, K, M = prob["n"], prob["K"], prob["M"]
+    gs = onu.GridSpec(n, K)
+    G = onu.degridding_matrix(gs, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"], rows)
+    GH = G.conj().T.tocsr()
+    t0 = time.perf_counter()
+    Xh = onu.dft2(onu.zero_pad(gs, x)).ravel()
+    t1 = time.perf_counter()
+    reps = 5
+    for _ in range(reps):
+        r = G @ Xh - y_rows
+        grid = GH @ r
+    t2 = time.perf_counter()
+    z = x - gamma * onu.zero_pad_adjoint(gs, onu.dft2_adjoint(grid.reshape(K, K))).real
+    ofb.haar_denoise(z, t)
+    t3 = time.perf_counter()
+    g_full = (t2 - t1) / reps * (M / rows.size)
+    est = (t1 - t0) + g_full + (t3 - t2)
+    return est, dict(fft_and_pad_s=(t1 - t0) + (t3 - t2), g_pass_scaled_s=g_full,
+                     g_sample_s=(t2 - t1) / reps)
+
+
+def cpu_sample_inputs(prob, x_dev_np, y_np):
+    rng = np.random.default_rng(1234)
+    rows = np.sort(rng.choice(prob["M"], CPU_SAMPLE_ROWS, replace=False))
+    return rows, y_np[rows]
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    wl = WORKLOADS[args.workload]
+    prob = synth.make_problem(wl["name"])
+    from oracle import nufft as onu
+    n, K, M = prob["n"], prob["K"], prob["M"]
+    x = np.zeros((n, n))
+    # the oracle's y on the sampled rows (noise-free sky model + scaled noise)
+    rows, _ = cpu_sample_inputs(prob, None, np.zeros(M, complex))
+    gs = onu.GridSpec(n, K)
+    Xt = onu.dft2(onu.zero_pad(gs, prob["x_true"])).ravel()
+    G = onu.degridding_matrix(gs, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"], rows)
+    y_rows = G @ Xt + 1e-3 * prob["noise"][rows]
+    gamma, t = 1.0 / M, 1e-6
+    times = []
+    for i in range(args.warmup + args.steps):
+        est, _ = oracle_sample(prob, rows, x, y_rows, gamma, t)
+        if i >= args.warmup:
+            times.append(est)
+    total = sum(times)
+    val = len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wl["desc"],
+                                            "l2": "inputs larger than L2 (G 31.8 GB)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"per step: one FP64 oracle iteration with the full-size "
+                                       f"FFT pair and G restricted to {CPU_SAMPLE_ROWS} seeded "
+                                       f"rows, G time scaled by M/{CPU_SAMPLE_ROWS}"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2207_11336_gb300 as pnp
+    import synth
+
+    wl = WORKLOADS[args.workload]
+    prob = synth.make_problem(wl["name"])
+    n, K, M = prob["n"], prob["K"], prob["M"]
+    stream = torch.cuda.current_stream()
+    plan = pnp.Plan(n, K, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"],
+                    block=prob["block"], nblocks=BLOCKS[wl["name"]], stream=stream)
+    info = plan.info
+    x_true = torch.from_numpy(prob["x_true"].astype(np.float32)).cuda()
+    y0 = plan.phi_forward(x_true)
+    norm_y0 = float(torch.linalg.vector_norm(y0.to(torch.complex128)).item())
+    tau = synth.noise_std_for_isnr(norm_y0, M, prob["isnr_db"])
+    noise = torch.from_numpy(prob["noise"].astype(np.complex64)).cuda()
+    y = (y0 + tau * noise).contiguous()
+    v0 = torch.from_numpy(synth.rng_for("power").standard_normal((n, n)).astype(np.float32)).cuda()
+    L, _ = plan.op_norm(v0, 1000, 1e-6)
+    gamma = 1.98 / L
+    t = tau / np.sqrt(2 * L)
+    den = pnp.HaarDenoiser(t, stream=stream)
+    x = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # warm-up (also primes kernel attributes; graph capture happens inside each run)
+    plan.fb_run(den, y, x0=x, gamma=gamma, L=L, max_iter=max(args.warmup, 3), check_every=2,
+                use_graph=True, inplace=True)
+    torch.cuda.synchronize()
+    barrier()
+    k0 = pnp.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = args.steps + (args.steps & 1)  # the graph replays iteration pairs
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        _, st = plan.fb_run(den, y, x0=x, gamma=gamma, L=L, max_iter=steps, check_every=steps,
+                            use_graph=True, inplace=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    launches = pnp.kernel_launches() - k0
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = ws * steps / (ms / 1e3)
+
+    # kernel timing: eager replay of the same steps with CUDA events around each stage
+    plan.set_timing(True)
+    kt = min(steps, 10)
+    plan.fb_run(den, y, x0=x, gamma=gamma, L=L, max_iter=kt, check_every=kt, use_graph=False,
+                inplace=True)
+    tim = plan.read_timing()
+    plan.set_timing(False)
+    g_ms, g_cnt = tim["gridding"]
+    g_ms_launch = g_ms / max(g_cnt, 1)
+    wbytes = 8
+    alg_bytes = info["nnz"] * (wbytes + 4) + M * 16 + 2 * K * K * 8
+    hbm, peak_kind = measured_peaks()
+    achieved = alg_bytes / (g_ms_launch * 1e-3) / 1e9
+
+    # end to end through the public API with host buffers
+    y_host = y.cpu().pin_memory()
+    y_dev = torch.empty_like(y)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, args.e2e_steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start = time.perf_counter()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        y_dev.copy_(y_host, non_blocking=True)
+        plan.fb_run(den, y_dev, x0=x, gamma=gamma, L=L, max_iter=1, check_every=1,
+                    use_graph=False, inplace=True)   # ends with the D2H read of the FP64 norms
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t_start)
+    e2e_val = ws * e2e_steps / e2e_s
+
+    out = None
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
+               "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "impl": "gpu",
+               "config": {"workload": wl["desc"], "parallelism": f"replicas{ws}",
+                          "l2": "inputs larger than L2 (G %.1f GB)" % (info["nnz"] * 12 / 1e9),
+                          "nnz": info["nnz"], "denoiser": "haar", "graph": True},
+               "clocks": clk.summary(),
+               "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": M * 8,
+                       "d2h_bytes_per_step": 16},
+               "gpu_launches": launches,
+               "roofline": {"bound": "hbm", "kernel": "gpass<G_FUSED> (degrid+residual+grid)",
+                            "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
+                            "frac": achieved / hbm, "traffic": profiled_traffic("gridding.cu", wl["name"]),
+                            "alg_bytes_per_launch": alg_bytes, "ms_per_launch": g_ms_launch,
+                            "stage_ms_per_iter": {k: v[0] / max(v[1], 1) for k, v in tim.items()}},
+               "fb": {"L": L, "gamma": gamma, "t": t, "tau": tau, "rel_change": st.rel_change}}
+        if ws == 1 and not args.no_cpu_baseline:
+            rows, y_rows = cpu_sample_inputs(prob, None, y.cpu().numpy().astype(np.complex128))
+            xs = x.cpu().numpy().astype(np.float64)
+            est, parts = oracle_sample(prob, rows, xs, y_rows, gamma, t)
+            out["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                   "sample": f"one FP64 oracle iteration: full-size FFT pair, G "
+                                             f"restricted to {CPU_SAMPLE_ROWS} seeded rows (time "
+                                             f"scaled by M/{CPU_SAMPLE_ROWS}); numpy FFT and scipy "
+                                             f"CSR are single-threaded",
+                                   "parts_s": parts, "host_cores": os.cpu_count()}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,214 @@
+/*
+ * pnp.h - C ABI of the GB300 (sm_103a) plug-and-play forward-backward (PnP-FB)
+ * radio-interferometric imaging library (arXiv 2207.11336, Dabbech et al. 2022).
+ *
+ * The library implements the measurement model of Eq. 1,
+ *     y = Phi x + n,   Phi = G F Z,
+ * the data-fidelity gradient of App. A,
+ *     grad f(x) = Re{Phi^H (Phi x - y)},   L = ||Re{Phi^H Phi}||_S,
+ * and the forward-backward iteration of Eq. fb with a plug-in denoiser D:
+ *     x^{k+1} = D(x^k - gamma grad f(x^k)).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Image x: n x n float32, row-major x[a*n + b], Jy/pixel.  Pixel (a, b) sits
+ *    at the centred offset p = (a - n/2, b - n/2); p = (0, 0) is the phase centre.
+ *  - Visibilities y: M complex64 (interleaved re, im) in the caller's row order.
+ *    Row m has angular frequencies (omega_0, omega_1) in rad/pixel (omega_0 pairs
+ *    with image axis 0) and w in wavelengths.
+ *  - Z: zero-padding on a K x K grid plus division by the Kaiser-Bessel (KB)
+ *    kernel's continuous Fourier transform c(p0) c(p1).  F: unnormalised 2-D
+ *    DFT.  G: sparse rows; row m holds the J_m x J_m taps nearest
+ *    kappa = omega K / (2 pi) of the KB kernel (J = 7 by default) convolved
+ *    with the row's w-kernel (App. E), stored as complex64 (or bfloat16
+ *    complex) weights with int32 column indices and int64 row offsets.
+ *  - Device pointers ("dev") are CUDA global-memory addresses owned by the
+ *    caller; the library never frees them.  Host pointers ("host") are read
+ *    during the call only.
+ *  - Every call that takes a plan or denoiser is asynchronous on that handle's
+ *    stream unless it says otherwise; results are ready after a stream
+ *    synchronisation.
+ *  - Return value: PNP_OK (0) or a negative PNP_ERR_* code; pnp_last_error()
+ *    gives a message for the calling thread.
+ */
+#ifndef PNP_H
+#define PNP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  PNP_OK = 0,
+  PNP_ERR_INVALID_ARG = -1, /* a size, pointer or option is out of range      */
+  PNP_ERR_OOM = -2,         /* device or host allocation failed               */
+  PNP_ERR_CUDA = -3,        /* a CUDA runtime call failed                     */
+  PNP_ERR_DIVERGED = -4,    /* NaN/Inf or growing iterate in pnp_fb_run       */
+  PNP_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up             */
+  PNP_ERR_UNSUPPORTED = -6  /* valid request outside what this build supports */
+};
+
+/* Storage type of G's weights. */
+enum { PNP_W_C64 = 0, PNP_W_BF16C = 1 };
+
+/* Denoiser kinds. */
+enum { PNP_DEN_HAAR = 0, PNP_DEN_CNN = 1 };
+
+typedef struct pnp_plan pnp_plan;
+typedef struct pnp_den pnp_den;
+
+/* Parameters of pnp_fb_run (Eq. fb; App. B, F). */
+typedef struct pnp_params {
+  double gamma;      /* step size; <= 0 selects 1.98 / L (App. B)                */
+  double L;          /* Lipschitz constant; <= 0 runs op_norm first (App. A)    */
+  int max_iter;      /* number of FB iterations (>= 0)                           */
+  double tol;        /* stop when ||x+ - x|| / ||x+|| < tol (tested only if > 0) */
+  int check_every;   /* host reads the FP64 norms every this many iterations    */
+  int use_graph;     /* 1: replay iterations as one captured CUDA graph          */
+  double diverge_factor; /* > 0: fail with PNP_ERR_DIVERGED if ||x+|| grows past
+                            this factor times its smallest checked value        */
+} pnp_params;
+
+/* Outputs of pnp_fb_run. */
+typedef struct pnp_stats {
+  int iters;          /* iterations executed                                     */
+  double L;           /* Lipschitz constant used                                 */
+  double gamma;       /* step size used                                          */
+  double rel_change;  /* ||x^k - x^{k-1}|| / ||x^k|| at the last check (FP64)    */
+  double x_norm;      /* ||x^k|| at the last check (FP64)                        */
+} pnp_stats;
+
+/* Read-only facts about a plan. */
+typedef struct pnp_plan_info {
+  int n, K, J, weight_dtype, tile, nblocks;
+  int64_t M, nnz, n_units;
+  double beta;          /* KB shape parameter                                  */
+  double dl;            /* pixel size [rad] used for the w-term (0: none)      */
+  int64_t device_bytes; /* device memory held by the plan                      */
+} pnp_plan_info;
+
+/* ------------------------------------------------------------------ plans */
+
+/* Build the measurement operator Phi = G F Z of Eq. 1 (w-terms folded into G
+ * as in App. E) on the current CUDA device.
+ *  n             image side (even, 8 <= n <= K/2)
+ *  K             grid side (power of two, 64 <= K <= 16384)
+ *  M             number of visibilities (>= 0; 0 gives an empty operator)
+ *  uvw_host      host, M x 3 float64 row-major: omega_0, omega_1 [rad/px] in
+ *                [-pi, pi), w [wavelengths]
+ *  dl            pixel size [rad] for the w-term; 0 disables w (KB rows only)
+ *  J_per_row_host host, M int8 supports J_m in [J, 16], or NULL for J_m = J
+ *  J             KB kernel support (odd or even, 2 <= J <= 16)
+ *  weight_dtype  PNP_W_C64 or PNP_W_BF16C
+ *  block_host    host, M int32 data-block ids in [0, nblocks) (App. E data
+ *                clustering), or NULL for one block
+ *  nblocks       number of data blocks (>= 1)
+ *  stream        cudaStream_t for every later call on this plan (NULL: legacy)
+ * Rows are reordered internally by grid tile and block; every call takes and
+ * returns visibilities in the caller's order.  Errors: INVALID_ARG, OOM, CUDA. */
+int pnp_plan_create(pnp_plan** plan, int n, int K, int64_t M, const double* uvw_host,
+                    double dl, const int8_t* J_per_row_host, int J, int weight_dtype,
+                    const int32_t* block_host, int nblocks, void* stream);
+
+void pnp_plan_destroy(pnp_plan* plan);
+
+int pnp_plan_get_info(const pnp_plan* plan, pnp_plan_info* info);
+
+/* Set the rows per work unit of the gridding kernels (autotuner hook; 0 keeps
+ * the current choice).  Rebuilds the work list only; G is unchanged. */
+int pnp_plan_set_unit_nnz(pnp_plan* plan, int64_t unit_nnz);
+
+/* Device-side status flags of the plan's kernels (synchronous read).  Bit 0:
+ * a gridding tap fell outside its tile's staged shared-memory region and was
+ * skipped (an internal consistency check; never set by a correct plan). */
+int pnp_plan_device_status(pnp_plan* plan, int* flags_host);
+
+/* Per-stage CUDA-event timing (profiling aid).  While enabled, every
+ * forward FFT, gridding pass and adjoint FFT issued eagerly on the plan's stream
+ * is bracketed by a pair of CUDA events; launches inside CUDA-graph capture are
+ * not timed.  pnp_plan_read_timing synchronises the stream and returns, per
+ * stage (0 forward FFT pair, 1 gridding pass, 2 adjoint FFT pair), the summed
+ * milliseconds and the number of timed launches, then clears the record. */
+int pnp_plan_set_timing(pnp_plan* plan, int enable);
+int pnp_plan_read_timing(pnp_plan* plan, double* ms_host /*[3]*/, int64_t* count_host /*[3]*/);
+
+/* Copy rows of G to the host for inspection (synchronous).
+ *  rows_host      host, nrows row indices in the caller's order
+ *  offsets_host   host, nrows+1 int64: written with exclusive prefix sums of J_m^2
+ *  weights_host   host, offsets_host[nrows] complex64 (interleaved)
+ *  cols_host      host, offsets_host[nrows] int32 column indices in the
+ *                 canonical grid layout (k0 mod K) * K + (k1 mod K)
+ * Pass weights_host = cols_host = NULL to query offsets only. */
+int pnp_plan_export_rows(const pnp_plan* plan, const int64_t* rows_host, int64_t nrows,
+                         int64_t* offsets_host, float* weights_host, int32_t* cols_host);
+
+/* ------------------------------------------------------ operator (Eq. 1) */
+
+/* y = Phi x = G F Z x (Eq. 1).  x: dev n*n float32.  y: dev M complex64. */
+int phi_forward(pnp_plan* plan, const float* x, float* y);
+
+/* x = Re{Phi^H y} = Re{Z^H F^H G^H y} (App. A).  y: dev M complex64.  x: dev n*n. */
+int phi_adjoint(pnp_plan* plan, const float* y, float* x);
+
+/* x_out = x - gamma Re{Phi^H (Phi x - y)}: the forward (gradient) step of
+ * Eq. fb with the gradient of App. A; one pass over G computes the residual
+ * and its gridding.  x, x_out: dev n*n (may not alias).  y: dev M complex64. */
+int grad_step(pnp_plan* plan, const float* x, const float* y, double gamma, float* x_out);
+
+/* L = ||Re{Phi^H Phi}||_S by power iteration (App. A), FP64 norms.
+ *  v0       dev n*n float32 start vector, or NULL for all ones
+ *  max_it   iteration cap (>= 1); tol: stop when |L_k - L_{k-1}| <= tol L_k
+ *  L_out    host, receives L (synchronous)
+ *  iters_out host, receives the iteration count (may be NULL) */
+int op_norm(pnp_plan* plan, const float* v0, int max_it, double tol, double* L_out,
+            int* iters_out);
+
+/* ------------------------------------------------------------- denoisers */
+
+/* Plain denoiser: one-level orthonormal 2-D Haar on 2x2 blocks, soft-threshold
+ * of all four subbands at t, synthesis, then positivity (App. B with the
+ * threshold gamma*lambda = tau / sqrt(2L) of Eq. lambda).  t >= 0. */
+int pnp_den_create_haar(pnp_den** den, double t, void* stream);
+
+/* Learned denoiser (App. C): residual CNN, 8 layers 3x3, 1->64->...->64->1,
+ * ReLU between layers, D(z) = max(0, z - N(z)), applied on facets with a halo
+ * (App. D).
+ *  weights_host  host float32, the 8 layers' (W, b) concatenated: layer l
+ *                stores W[co][ci][3][3] then b[co]; shapes 64x1, 6 x 64x64, 1x64
+ *  facet_rows_host / facet_cols_host  host int32 facet core sizes along each
+ *                axis (sum n), or NULL for the whole image as one facet
+ *  nfr, nfc      number of facet sizes given per axis
+ *  halo          facet overlap in pixels (>= 8 makes faceting exact)
+ *  n             image side the denoiser will be applied to */
+int pnp_den_create_cnn(pnp_den** den, const float* weights_host,
+                       const int32_t* facet_rows_host, int nfr,
+                       const int32_t* facet_cols_host, int nfc, int halo, int n, void* stream);
+
+void pnp_den_destroy(pnp_den* den);
+
+/* x_out = D(x_in) for an n x n image (dev float32; may not alias). */
+int denoise(pnp_den* den, const float* x_in, float* x_out, int n);
+
+/* ------------------------------------------------------------ PnP-FB loop */
+
+/* Run Eq. fb: x^{k+1} = D(x^k - gamma Re{Phi^H (Phi x^k - y)}), starting from
+ * x_inout (dev n*n float32, overwritten with the result).  y: dev M complex64.
+ * params may leave gamma and L at 0 to derive them (App. B).  stats (host)
+ * may be NULL.  Returns PNP_ERR_DIVERGED if the iterate becomes non-finite or
+ * grows past params->diverge_factor. */
+int pnp_fb_run(pnp_plan* plan, pnp_den* den, const float* y, const pnp_params* params,
+               float* x_inout, pnp_stats* stats);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char* pnp_last_error(void);
+
+/* Number of this library's kernels launched by the calling process so far. */
+int64_t pnp_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PNP_H */

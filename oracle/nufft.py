@@ -264,3 +264,12 @@ def nudft(omega, x, w=None, dl: float = 0.0, paraxial: bool = True) -> np.ndarra
         W = np.exp(-2j * np.pi * w[m] * nm1)
         out[m] = np.sum(np.outer(E0[m], E1[m]) * W * x)
     return out
+
+
+def nudft_adjoint(omega, y, n: int) -> np.ndarray:
+    """Direct adjoint of ``nudft`` without w: x_p = sum_m exp(+i omega_m . p) y_m (complex n x n)."""
+    omega = np.asarray(omega, dtype=np.float64)
+    p = pixel_offsets(n).astype(np.float64)
+    E0 = np.exp(1j * omega[:, 0:1] * p[None, :])
+    E1 = np.exp(1j * omega[:, 1:2] * p[None, :])
+    return np.einsum("ma,m,mb->ab", E0, y, E1)

@@ -1,0 +1,337 @@
+"""GB300 (sm_103a) plug-and-play forward-backward radio-interferometric imaging.
+
+Thin Python binding over the C ABI of ``libpnp.so`` (declared in
+``include/pnp.h``).  Every step of the imaging path runs in the library's CUDA
+kernels; this module only marshals arguments.  PyTorch provides device memory
+and streams.  Importing works without a GPU; constructing a plan needs the
+built library and a CUDA device and fails loudly otherwise.
+
+Reference: Dabbech et al. 2022, arXiv 2207.11336 (Eq. 1: y = Phi x + n,
+Phi = G F Z; App. A: forward-backward; App. B/C: denoisers).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpnp.so")
+
+PNP_W_C64, PNP_W_BF16C = 0, 1
+PNP_DEN_HAAR, PNP_DEN_CNN = 0, 1
+ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "DIVERGED", -5: "TIMEOUT", -6: "UNSUPPORTED"}
+
+EXPORTED = [
+    "pnp_plan_create", "pnp_plan_destroy", "pnp_plan_get_info", "pnp_plan_set_unit_nnz",
+    "pnp_plan_export_rows", "phi_forward", "phi_adjoint", "grad_step", "op_norm",
+    "pnp_den_create_haar", "pnp_den_create_cnn", "pnp_den_destroy", "denoise", "pnp_fb_run",
+    "pnp_last_error", "pnp_kernel_launch_count", "pnp_plan_set_timing", "pnp_plan_read_timing",
+    "pnp_plan_device_status",
+]
+
+
+class PnPError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"PNP_ERR_{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Params(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("L", C.c_double), ("max_iter", C.c_int), ("tol", C.c_double),
+                ("check_every", C.c_int), ("use_graph", C.c_int), ("diverge_factor", C.c_double)]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("L", C.c_double), ("gamma", C.c_double),
+                ("rel_change", C.c_double), ("x_norm", C.c_double)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("n", C.c_int), ("K", C.c_int), ("J", C.c_int), ("weight_dtype", C.c_int),
+                ("tile", C.c_int), ("nblocks", C.c_int), ("M", C.c_int64), ("nnz", C.c_int64),
+                ("n_units", C.c_int64), ("beta", C.c_double), ("dl", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
+_lib = None
+
+
+def lib(path: str = LIB_PATH) -> C.CDLL:
+    """Load libpnp.so (built by ``paper_2207_11336_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with `python -m paper_2207_11336_gb300.build`")
+    L = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    L.pnp_plan_create.argtypes = [C.POINTER(vp), i32, i32, i64, vp, dbl, vp, i32, i32, vp, i32, vp]
+    L.pnp_plan_destroy.argtypes = [vp]
+    L.pnp_plan_destroy.restype = None
+    L.pnp_plan_get_info.argtypes = [vp, C.POINTER(_Info)]
+    L.pnp_plan_set_unit_nnz.argtypes = [vp, i64]
+    L.pnp_plan_export_rows.argtypes = [vp, vp, i64, vp, vp, vp]
+    L.phi_forward.argtypes = [vp, vp, vp]
+    L.phi_adjoint.argtypes = [vp, vp, vp]
+    L.grad_step.argtypes = [vp, vp, vp, dbl, vp]
+    L.op_norm.argtypes = [vp, vp, i32, dbl, C.POINTER(dbl), C.POINTER(i32)]
+    L.pnp_den_create_haar.argtypes = [C.POINTER(vp), dbl, vp]
+    L.pnp_den_create_cnn.argtypes = [C.POINTER(vp), vp, vp, i32, vp, i32, i32, i32, vp]
+    L.pnp_den_destroy.argtypes = [vp]
+    L.pnp_den_destroy.restype = None
+    L.denoise.argtypes = [vp, vp, vp, i32]
+    L.pnp_fb_run.argtypes = [vp, vp, vp, C.POINTER(_Params), vp, C.POINTER(_Stats)]
+    L.pnp_plan_set_timing.argtypes = [vp, i32]
+    L.pnp_plan_device_status.argtypes = [vp, C.POINTER(i32)]
+    L.pnp_plan_read_timing.argtypes = [vp, vp, vp]
+    L.pnp_last_error.restype = C.c_char_p
+    L.pnp_kernel_launch_count.restype = i64
+    for name in ("pnp_plan_create", "pnp_plan_get_info", "pnp_plan_set_unit_nnz", "pnp_plan_export_rows",
+                 "phi_forward", "phi_adjoint", "grad_step", "op_norm", "pnp_den_create_haar",
+                 "pnp_den_create_cnn", "denoise", "pnp_fb_run", "pnp_plan_set_timing",
+                 "pnp_plan_read_timing", "pnp_plan_device_status"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise PnPError(rc, lib().pnp_last_error().decode())
+
+
+def kernel_launches() -> int:
+    """Number of this library's kernels launched in this process."""
+    return int(lib().pnp_kernel_launch_count())
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+def _cuda_f32(t, shape, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA float32 tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+def _cuda_c64(t, m, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.complex64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA complex64 tensor")
+    if t.numel() != m:
+        raise ValueError(f"{name} has {t.numel()} entries, expected {m}")
+    return t
+
+
+def _stream_handle(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class FBStats:
+    iters: int
+    L: float
+    gamma: float
+    rel_change: float
+    x_norm: float
+
+
+class Plan:
+    """Measurement operator Phi = G F Z (Eq. 1) with w-terms folded into G (App. E).
+
+    ``omega``: (M, 2) float64 rad/pixel (column 0 pairs with image axis 0);
+    ``w``: (M,) wavelengths; ``dl``: pixel size [rad] for the w-term (0: none);
+    ``J_per_row``: (M,) int8 supports in [J, 16] or None.
+    """
+
+    def __init__(self, n, K, omega, w=None, dl=0.0, J_per_row=None, J=7, weight_dtype="c64",
+                 block=None, nblocks=1, stream=None):
+        import torch
+        L = lib()
+        omega = np.asarray(omega, dtype=np.float64)
+        M = omega.shape[0]
+        uvw = np.zeros((M, 3), dtype=np.float64)
+        uvw[:, :2] = omega
+        if w is not None:
+            uvw[:, 2] = np.asarray(w, dtype=np.float64)
+        uvw = np.ascontiguousarray(uvw)
+        jr = None if J_per_row is None else np.ascontiguousarray(J_per_row, dtype=np.int8)
+        blk = None if block is None else np.ascontiguousarray(block, dtype=np.int32)
+        self.stream = torch.cuda.current_stream() if stream is None else stream
+        self._h = C.c_void_p()
+        wd = PNP_W_BF16C if weight_dtype in ("bf16", PNP_W_BF16C) else PNP_W_C64
+        _check(L.pnp_plan_create(C.byref(self._h), int(n), int(K), int(M), uvw.ctypes.data, float(dl),
+                                 None if jr is None else jr.ctypes.data, int(J), wd,
+                                 None if blk is None else blk.ctypes.data, int(nblocks),
+                                 _stream_handle(self.stream)))
+        self.n, self.K, self.M = int(n), int(K), int(M)
+
+    # ------------------------------------------------------------------ info
+    @property
+    def info(self) -> dict:
+        inf = _Info()
+        _check(lib().pnp_plan_get_info(self._h, C.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in _Info._fields_}
+
+    def set_unit_nnz(self, unit_nnz: int):
+        _check(lib().pnp_plan_set_unit_nnz(self._h, int(unit_nnz)))
+
+    def device_status(self) -> int:
+        """Device status flags (0 when every kernel check passed)."""
+        f = C.c_int()
+        _check(lib().pnp_plan_device_status(self._h, C.byref(f)))
+        return f.value
+
+    def set_timing(self, enable: bool):
+        """Bracket each eager FFT / gridding stage with CUDA events."""
+        _check(lib().pnp_plan_set_timing(self._h, 1 if enable else 0))
+
+    def read_timing(self):
+        """{stage: (total ms, launches)} for 'fft_forward', 'gridding', 'fft_adjoint'; clears the record."""
+        ms = np.zeros(3, dtype=np.float64)
+        cnt = np.zeros(3, dtype=np.int64)
+        _check(lib().pnp_plan_read_timing(self._h, ms.ctypes.data, cnt.ctypes.data))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(("fft_forward", "gridding", "fft_adjoint"))}
+
+    def export_rows(self, rows):
+        """(offsets, weights complex64, canonical columns k0*K + k1) of the given rows of G."""
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        off = np.zeros(rows.size + 1, dtype=np.int64)
+        _check(lib().pnp_plan_export_rows(self._h, rows.ctypes.data, rows.size, off.ctypes.data, None, None))
+        wts = np.zeros(int(off[-1]), dtype=np.complex64)
+        cols = np.zeros(int(off[-1]), dtype=np.int32)
+        _check(lib().pnp_plan_export_rows(self._h, rows.ctypes.data, rows.size, off.ctypes.data,
+                                          wts.ctypes.data, cols.ctypes.data))
+        return off, wts, cols
+
+    # ------------------------------------------------------------------ operator
+    def phi_forward(self, x, out=None):
+        """y = Phi x (Eq. 1)."""
+        import torch
+        _cuda_f32(x, (self.n, self.n), "x")
+        y = torch.empty(self.M, dtype=torch.complex64, device=x.device) if out is None else out
+        _cuda_c64(y, self.M, "y")
+        _check(lib().phi_forward(self._h, _ptr(x), _ptr(y)))
+        return y
+
+    def phi_adjoint(self, y, out=None):
+        """x = Re{Phi^H y} (App. A)."""
+        import torch
+        _cuda_c64(y, self.M, "y")
+        x = torch.empty((self.n, self.n), dtype=torch.float32, device=y.device) if out is None else out
+        _cuda_f32(x, (self.n, self.n), "out")
+        _check(lib().phi_adjoint(self._h, _ptr(y), _ptr(x)))
+        return x
+
+    def grad_step(self, x, y, gamma, out=None):
+        """x - gamma Re{Phi^H (Phi x - y)} (forward step of Eq. fb)."""
+        import torch
+        _cuda_f32(x, (self.n, self.n), "x")
+        _cuda_c64(y, self.M, "y")
+        o = torch.empty_like(x) if out is None else out
+        _cuda_f32(o, (self.n, self.n), "out")
+        _check(lib().grad_step(self._h, _ptr(x), _ptr(y), float(gamma), _ptr(o)))
+        return o
+
+    def op_norm(self, v0=None, max_it=1000, tol=1e-7):
+        """(L, iterations): ||Re{Phi^H Phi}||_S by power iteration (App. A)."""
+        if v0 is not None:
+            _cuda_f32(v0, (self.n, self.n), "v0")
+        Lv = C.c_double()
+        it = C.c_int()
+        _check(lib().op_norm(self._h, None if v0 is None else _ptr(v0), int(max_it), float(tol),
+                             C.byref(Lv), C.byref(it)))
+        return Lv.value, it.value
+
+    def fb_run(self, den, y, x0=None, gamma=0.0, L=0.0, max_iter=200, tol=0.0, check_every=10,
+               use_graph=True, diverge_factor=0.0, inplace=False):
+        """Run Eq. fb with denoiser ``den`` from x0 (zeros if None); returns (x, FBStats).
+
+        With ``inplace`` the iterate is updated in x0 itself."""
+        import torch
+        _cuda_c64(y, self.M, "y")
+        if x0 is None:
+            x = torch.zeros((self.n, self.n), dtype=torch.float32, device=y.device)
+        else:
+            x = x0 if inplace else x0.clone()
+        _cuda_f32(x, (self.n, self.n), "x0")
+        prm = _Params(float(gamma), float(L), int(max_iter), float(tol), int(check_every),
+                      1 if use_graph else 0, float(diverge_factor))
+        st = _Stats()
+        _check(lib().pnp_fb_run(self._h, den._h, _ptr(y), C.byref(prm), _ptr(x), C.byref(st)))
+        return x, FBStats(st.iters, st.L, st.gamma, st.rel_change, st.x_norm)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().pnp_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Denoiser:
+    _h = None
+
+    def denoise(self, x, out=None):
+        """x_out = D(x)."""
+        import torch
+        n = x.shape[0]
+        _cuda_f32(x, (n, n), "x")
+        o = torch.empty_like(x) if out is None else out
+        _check(lib().denoise(self._h, _ptr(x), _ptr(o), int(n)))
+        return o
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().pnp_den_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HaarDenoiser(_Denoiser):
+    """Haar soft-threshold at t + positivity (App. B; t = tau / sqrt(2L), Eq. lambda)."""
+
+    def __init__(self, t: float, stream=None):
+        lib()
+        self._h = C.c_void_p()
+        _check(lib().pnp_den_create_haar(C.byref(self._h), float(t), _stream_handle(stream)))
+        self.t = float(t)
+
+
+def pack_cnn_weights(params) -> np.ndarray:
+    """Flatten [(W (co, ci, 3, 3), b (co,)), ...] into the float32 layout of pnp_den_create_cnn."""
+    return np.ascontiguousarray(np.concatenate([np.concatenate([np.ravel(W), np.ravel(b)])
+                                                for W, b in params]).astype(np.float32))
+
+
+class CnnDenoiser(_Denoiser):
+    """Residual CNN denoiser D(z) = max(0, z - N(z)) (App. C), faceted with a halo (App. D)."""
+
+    def __init__(self, params, n: int, facet_rows=None, facet_cols=None, halo: int = 32, stream=None):
+        lib()
+        wts = pack_cnn_weights(params)
+        fr = None if facet_rows is None else np.ascontiguousarray(facet_rows, dtype=np.int32)
+        fc = None if facet_cols is None else np.ascontiguousarray(facet_cols, dtype=np.int32)
+        self._h = C.c_void_p()
+        _check(lib().pnp_den_create_cnn(C.byref(self._h), wts.ctypes.data,
+                                        None if fr is None else fr.ctypes.data, 0 if fr is None else fr.size,
+                                        None if fc is None else fc.ctypes.data, 0 if fc is None else fc.size,
+                                        int(halo), int(n), _stream_handle(stream)))

@@ -1,0 +1,146 @@
+// Shared internals of the PnP-FB library: plan/denoiser structs, error
+// plumbing and small device helpers.  Everything here is sm_103a-only.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <vector>
+
+#include "../../include/pnp.h"
+
+namespace pnp {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+extern std::atomic<int64_t> g_launches;
+
+#define PNP_CUDA(call)                                                           \
+  do {                                                                           \
+    cudaError_t e_ = (call);                                                     \
+    if (e_ != cudaSuccess) {                                                     \
+      cudaGetLastError(); /* clear a non-sticky error so later checks are clean */ \
+      return ::pnp::fail(PNP_ERR_CUDA, std::string(#call) + ": " +              \
+                                           cudaGetErrorString(e_));             \
+    }                                                                            \
+  } while (0)
+
+#define PNP_CHECK_LAUNCH()                                                       \
+  do {                                                                           \
+    ::pnp::g_launches.fetch_add(1, std::memory_order_relaxed);                   \
+    cudaError_t e_ = cudaGetLastError();                                         \
+    if (e_ != cudaSuccess)                                                       \
+      return ::pnp::fail(PNP_ERR_CUDA, std::string("kernel launch: ") +         \
+                                           cudaGetErrorString(e_));             \
+  } while (0)
+
+// ------------------------------------------------------------------ complex
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+// ------------------------------------------------------------------ work units
+// A work unit of the gridding kernels: consecutive rows (in tile-sorted order)
+// whose first tap lies in one grid tile.
+struct Unit {
+  long long row_begin;
+  int nrows;
+  int tile;
+};
+
+// Q2 epilogue modes of the last inverse-FFT pass (see fft.cu).
+enum EpiMode { EPI_ADJ = 0, EPI_GRAD = 1, EPI_HAAR = 2, EPI_Z = 3, EPI_NORMAL = 4 };
+
+// Gridding pass modes (see gridding.cu).
+enum GMode { G_DEGRID = 0, G_GRID = 1, G_FUSED = 2 };
+
+}  // namespace pnp
+
+// ------------------------------------------------------------------ plan
+struct pnp_plan {
+  int n = 0, K = 0, logK = 0, J = 7, Jmax = 7, wdtype = PNP_W_C64, nblocks = 1;
+  int tile = 48;       // gridding tile side T (cells)
+  int ntc = 0;         // tiles per grid side, ceil(K / tile)
+  int slots = 8;       // register slots per lane per row (32*slots >= Jmax^2)
+  int rpw = 2;         // rows per warp in flight
+  int64_t M = 0, nnz = 0, unit_nnz = 1 << 15;
+  double beta = 0, dl = 0;
+  cudaStream_t stream = nullptr;   // caller's stream: every launch goes here
+  cudaStream_t cstream = nullptr;  // private non-blocking stream for graph capture/replay
+  cudaEvent_t ev_join[2] = {nullptr, nullptr};
+  int device = 0, num_sms = 0;
+  int primed = 0;  // bit k: an eager FB iteration with denoiser kind k has configured every kernel
+
+  // device buffers
+  float* d_cinv = nullptr;     // n: 1 / c(a - n/2)
+  float2* d_tw = nullptr;      // K: exp(-2 pi i j / K)
+  float2* d_gridA = nullptr;   // K*K: F Z x   (layout [k1][k0])
+  float2* d_gridB = nullptr;   // K*K: G^H r   (layout [k1][k0]); kept zero between uses
+  float2* d_tmp = nullptr;     // K*n: half-transformed intermediate
+  void* d_w = nullptr;         // nnz weights (float2 or bf16x2)
+  int32_t* d_cols = nullptr;   // nnz internal column indices k1*K + k0
+  int64_t* d_rowptr = nullptr; // M+1 (sorted order)
+  int32_t* d_perm = nullptr;   // sorted row -> caller row
+  float2* d_ysorted = nullptr; // M scratch: y in sorted order
+  pnp::Unit* d_units = nullptr;
+  int64_t n_units = 0;
+  double* d_acc = nullptr;     // FP64 accumulators [8]
+  int* d_status = nullptr;     // device status flags [4] (bit 0: gridding index out of range)
+  float* d_img[3] = {nullptr, nullptr, nullptr};  // n*n work images
+  int64_t device_bytes = 0;
+
+  // optional per-stage event timing: (stage, start, stop)
+  bool timing = false;
+  struct TimedEvent { int stage; cudaEvent_t a, b; };
+  std::vector<TimedEvent> timed;
+
+  // host mirrors used by export and work-list rebuilds
+  std::vector<int64_t> h_rowptr;   // M+1
+  std::vector<int32_t> h_perm;     // sorted -> caller
+  std::vector<int32_t> h_inv;      // caller -> sorted
+  std::vector<int32_t> h_key;      // sorted: tile * nblocks + block
+};
+
+struct pnp_den {
+  int kind = PNP_DEN_HAAR;
+  double t = 0;
+  cudaStream_t stream = nullptr;
+  void* impl = nullptr;   // CNN state (cnn.cu)
+};
+
+namespace pnp {
+// pnp_api.cu: bracket one stage with events when timing is enabled
+int stage_begin(pnp_plan* p, int stage, cudaEvent_t* a);
+int stage_end(pnp_plan* p, int stage, cudaEvent_t a);
+// fft.cu
+int fft_forward(pnp_plan* p, const float* x);                       // x -> d_gridA
+int fft_adjoint(pnp_plan* p, int mode, const float* x, float* out,  // d_gridB -> out
+                float gamma, float t);
+// gridding.cu
+int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out);
+int permute_y(pnp_plan* p, const float2* y_user);  // d_ysorted = y_user[perm]
+// plan_build.cu
+int build_units(pnp_plan* p);
+// update.cu
+int haar_denoise_dev(cudaStream_t s, const float* z, float* out, int n, float t, double* acc,
+                     const float* x_prev);
+int scale_image(cudaStream_t s, const float* in, float* out, int64_t count, const double* acc,
+                int acc_index);
+int zero_acc(cudaStream_t s, double* acc, int count);
+// cnn.cu
+int cnn_create(pnp_den* d, const float* weights_host, const int32_t* fr, int nfr,
+               const int32_t* fc, int nfc, int halo, int n);
+void cnn_destroy(pnp_den* d);
+int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc,
+                const float* x_prev);
+}  // namespace pnp

@@ -1,0 +1,492 @@
+// Oversampled 2-D DFT F (Eq. 1) fused with zero-padding and grid correction Z,
+// and its adjoint F^H fused with Z^H, the real part, the gradient step and the
+// plain Haar denoiser (App. A, B).
+//
+// Layouts.  Image x[a][b] (n x n, float32).  The K x K grid is stored with the
+// axis-1 frequency k1 slow and the axis-0 frequency k0 fast: grid[k1*K + k0].
+// The forward transform runs in two kernels, each a batch of contiguous
+// length-K FFTs in shared memory:
+//   P1  rows a of the image: place x[a][b] / (c_a c_b) at (b - n/2) mod K,
+//       FFT along axis 1, write the result transposed into T[k1][a] (K x n);
+//   P2  rows k1 of T: place T[k1][a] at (a - n/2) mod K, FFT along axis 0,
+//       write grid[k1][k0].
+// Only n of the K input positions are non-zero in each pass (the zero-padding
+// of Z), so both passes read n values per row.  The adjoint runs the mirror:
+//   Q1  rows k1 of the gridded data: inverse FFT along axis 0, keep the n
+//       image rows, write U[a][k1] (n x K); re-zeroes the grid it consumed;
+//   Q2  rows a of U: inverse FFT along axis 1, keep the n image columns,
+//       divide by c_a c_b, take the real part, and apply the epilogue
+//       (adjoint only / gradient step / gradient step + Haar + positivity /
+//       power-iteration norm), two image rows per CTA so the 2 x 2 Haar
+//       blocks are local.
+//
+// Each length-K FFT is a Stockham autosort: radix-16 passes done in registers
+// (16 complex values per thread, K/16 threads per row) with the data exchanged
+// through padded shared memory between passes, then one radix-2/4/8 pass in
+// registers when log2 K is not a multiple of 4.  Twiddles come from a table
+// exp(-2 pi i j / K) computed on the host in double precision.
+#include "common.cuh"
+
+namespace pnp {
+namespace {
+
+constexpr int PAD_SHIFT = 4;
+__device__ __forceinline__ int PADI(int i) { return i + (i >> PAD_SHIFT); }
+
+// cos and sin of 2 pi m / 16
+__device__ __forceinline__ float2 w16(int m, int dir) {
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, r2 = 0.70710678118654752f;
+  float c, s;
+  switch (m & 15) {
+    case 0: c = 1.f; s = 0.f; break;
+    case 1: c = c1; s = s1; break;
+    case 2: c = r2; s = r2; break;
+    case 3: c = s1; s = c1; break;
+    case 4: c = 0.f; s = 1.f; break;
+    case 5: c = -s1; s = c1; break;
+    case 6: c = -r2; s = r2; break;
+    case 7: c = -c1; s = s1; break;
+    case 8: c = -1.f; s = 0.f; break;
+    case 9: c = -c1; s = -s1; break;
+    case 10: c = -r2; s = -r2; break;
+    case 11: c = -s1; s = -c1; break;
+    case 12: c = 0.f; s = -1.f; break;
+    case 13: c = s1; s = -c1; break;
+    case 14: c = r2; s = -r2; break;
+    default: c = c1; s = -s1; break;
+  }
+  // exp(dir * 2 pi i m / 16), dir = -1 forward, +1 inverse
+  return make_float2(c, dir < 0 ? -s : s);
+}
+
+// multiply by exp(dir * i pi / 2)
+template <int DIR>
+__device__ __forceinline__ float2 rotq(float2 a) {
+  return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <int DIR>
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  float2 s02 = cadd(x0, x2), d02 = csub(x0, x2);
+  float2 s13 = cadd(x1, x3), d13 = rotq<DIR>(csub(x1, x3));
+  x0 = cadd(s02, s13);
+  x2 = csub(s02, s13);
+  x1 = cadd(d02, d13);
+  x3 = csub(d02, d13);
+}
+
+// 8-point DFT on u[0..7] (natural order in and out): n = n1 + 4 n2, k = 2 k1 + k2.
+template <int DIR>
+__device__ __forceinline__ void dft8(float2* u) {
+  float2 A[4][2];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    A[n1][0] = u[n1];
+    A[n1][1] = u[n1 + 4];
+    dft2<DIR>(A[n1][0], A[n1][1]);
+    if (n1) A[n1][1] = cmul(A[n1][1], w16(2 * n1, DIR));
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 2; ++k2) {
+    float2 b0 = A[0][k2], b1 = A[1][k2], b2 = A[2][k2], b3 = A[3][k2];
+    dft4<DIR>(b0, b1, b2, b3);
+    u[k2] = b0;
+    u[2 + k2] = b1;
+    u[4 + k2] = b2;
+    u[6 + k2] = b3;
+  }
+}
+
+// 16-point DFT on v[0..15]: n = n1 + 4 n2, k = 4 k1 + k2.
+template <int DIR>
+__device__ __forceinline__ void dft16(float2* v) {
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) dft4<DIR>(v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]);
+  // now v[n1 + 4 k2] = A[n1][k2]
+#pragma unroll
+  for (int n1 = 1; n1 < 4; ++n1)
+#pragma unroll
+    for (int k2 = 1; k2 < 4; ++k2) v[n1 + 4 * k2] = cmul(v[n1 + 4 * k2], w16(n1 * k2, DIR));
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) dft4<DIR>(v[4 * k2], v[4 * k2 + 1], v[4 * k2 + 2], v[4 * k2 + 3]);
+  // v[k1 + 4 k2] = X[4 k1 + k2]
+  float2 t[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) t[i] = v[(i >> 2) + 4 * (i & 3)];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = t[i];
+}
+
+template <int DIR>
+__device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int idx) {
+  float2 w = __ldg(&tw[idx]);
+  if (DIR > 0) w.y = -w.y;
+  return w;
+}
+
+// Length-K FFT of one row.  On entry v[i] holds element j + i*K/16 of the
+// row; on exit v[i] holds output element j + i*K/16 (natural order).
+// s is this row's padded shared-memory buffer (K + K/16 float2).
+template <int LOGK, int DIR>
+__device__ __forceinline__ void fft_row(float2 (&v)[16], float2* s, int j,
+                                        const float2* __restrict__ tw) {
+  constexpr int K = 1 << LOGK;
+  constexpr int Q = LOGK / 4;
+  constexpr int REM = LOGK % 4;
+  constexpr int K16 = K / 16;
+#pragma unroll
+  for (int p = 0; p < Q; ++p) {
+    const int Ns = 1 << (4 * p);
+    const int k = j & (Ns - 1);
+    if (p > 0) {
+      const int step = K >> (4 * p + 4);
+#pragma unroll
+      for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twiddle<DIR>(tw, r * k * step));
+    }
+    dft16<DIR>(v);
+    if (!(p == Q - 1 && REM == 0)) {
+      const int idxD = ((j >> (4 * p)) << (4 * p + 4)) + k;
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 16; ++r) s[PADI(idxD + r * Ns)] = v[r];
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = s[PADI(j + r * K16)];
+    }
+  }
+  if constexpr (REM > 0) {
+    constexpr int RS = 1 << REM;
+    constexpr int G = 16 / RS;
+#pragma unroll
+    for (int t = 0; t < G; ++t) {
+      const int jj = j + t * K16;
+      float2 u[RS];
+#pragma unroll
+      for (int r = 0; r < RS; ++r) {
+        u[r] = v[t + r * G];
+        if (r) u[r] = cmul(u[r], twiddle<DIR>(tw, r * jj));
+      }
+      if constexpr (RS == 2) dft2<DIR>(u[0], u[1]);
+      if constexpr (RS == 4) dft4<DIR>(u[0], u[1], u[2], u[3]);
+      if constexpr (RS == 8) dft8<DIR>(u);
+#pragma unroll
+      for (int r = 0; r < RS; ++r) v[t + r * G] = u[r];
+    }
+  }
+}
+
+// image column / row index held at padded position e, or -1 when e is padding
+__device__ __forceinline__ int unpad_index(int e, int n, int K) {
+  const int h = n >> 1;
+  return e < h ? e + h : (e >= K - h ? e - (K - h) : -1);
+}
+__device__ __forceinline__ int pad_position(int a, int n, int K) {
+  const int h = n >> 1;
+  return a < h ? a + K - h : a - h;
+}
+
+struct FftArgs {
+  int n;
+  const float* x;          // P1 input image / Q2 current iterate
+  const float* cinv;       // 1 / c(p)
+  const float2* tw;
+  float2* tmp;             // T (K x n) or U (n x K)
+  float2* grid;            // P2 output / Q1 input (re-zeroed)
+  float* out;              // Q2 output image
+  double* acc;             // Q1 zeroes acc[0..3]; Q2 accumulates
+  float gamma, t;
+  int epi;
+};
+
+// ---------------------------------------------------------------- P1
+template <int LOGK, int R>
+__global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_p1(FftArgs A) {
+  constexpr int K = 1 << LOGK, T = K / 16, SROW = K + K / 16 + 1;
+  extern __shared__ float2 smem[];
+  const int rr = threadIdx.x / T, j = threadIdx.x % T;
+  const int n = A.n;
+  const int a = blockIdx.x * R + rr;
+  const bool live = a < n;  // the last CTA may hold fewer than R image rows
+  float2* s = smem + rr * SROW;
+  const float ca = live ? A.cinv[a] : 0.f;
+  float2 v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int b = unpad_index(j + i * T, n, K);
+    v[i] = (live && b >= 0) ? make_float2(A.x[(size_t)a * n + b] * ca * A.cinv[b], 0.f)
+                            : make_float2(0.f, 0.f);
+  }
+  fft_row<LOGK, -1>(v, s, j, A.tw);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 16; ++i) s[PADI(j + i * T)] = v[i];
+  __syncthreads();
+  const int a0 = blockIdx.x * R;
+  for (int idx = threadIdx.x; idx < R * K; idx += R * T) {
+    const int r = idx % R, k1 = idx / R;
+    if (a0 + r < n) A.tmp[(size_t)k1 * n + a0 + r] = smem[r * SROW + PADI(k1)];
+  }
+}
+
+// ---------------------------------------------------------------- P2
+template <int LOGK, int R>
+__global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_p2(FftArgs A) {
+  constexpr int K = 1 << LOGK, T = K / 16, SROW = K + K / 16 + 1;
+  extern __shared__ float2 smem[];
+  const int rr = threadIdx.x / T, j = threadIdx.x % T;
+  const int n = A.n;
+  const int k1 = blockIdx.x * R + rr;
+  float2* s = smem + rr * SROW;
+  const float2* row = A.tmp + (size_t)k1 * n;
+  float2 v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int a = unpad_index(j + i * T, n, K);
+    v[i] = a >= 0 ? row[a] : make_float2(0.f, 0.f);
+  }
+  fft_row<LOGK, -1>(v, s, j, A.tw);
+  float2* g = A.grid + (size_t)k1 * K;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) g[j + i * T] = v[i];
+}
+
+// ---------------------------------------------------------------- Q1
+template <int LOGK, int R>
+__global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_q1(FftArgs A) {
+  constexpr int K = 1 << LOGK, T = K / 16, SROW = K + K / 16 + 1;
+  extern __shared__ float2 smem[];
+  const int rr = threadIdx.x / T, j = threadIdx.x % T;
+  const int n = A.n;
+  const int k1 = blockIdx.x * R + rr;
+  if (blockIdx.x == 0 && threadIdx.x < 4 && A.acc) A.acc[threadIdx.x] = 0.0;
+  float2* s = smem + rr * SROW;
+  float2* g = A.grid + (size_t)k1 * K;
+  float2 v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = g[j + i * T];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) g[j + i * T] = make_float2(0.f, 0.f);
+  fft_row<LOGK, +1>(v, s, j, A.tw);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 16; ++i) s[PADI(j + i * T)] = v[i];
+  __syncthreads();
+  const int k10 = blockIdx.x * R;
+  for (int idx = threadIdx.x; idx < R * n; idx += R * T) {
+    const int r = idx % R, a = idx / R;
+    A.tmp[(size_t)a * K + k10 + r] = smem[r * SROW + PADI(pad_position(a, n, K))];
+  }
+}
+
+__device__ __forceinline__ float soft(float c, float t) {
+  const float m = fabsf(c) - t;
+  return m > 0.f ? copysignf(m, c) : 0.f;
+}
+
+__device__ __forceinline__ void block_reduce_add(double v0, double v1, double* acc, double* red) {
+  // red holds 2 doubles per thread; blocks narrower than a warp use the shared-memory path only
+  __syncthreads();
+  red[2 * threadIdx.x] = v0;
+  red[2 * threadIdx.x + 1] = v1;
+  __syncthreads();
+  for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[2 * threadIdx.x] += red[2 * (threadIdx.x + s)];
+      red[2 * threadIdx.x + 1] += red[2 * (threadIdx.x + s) + 1];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&acc[0], red[0]);
+    atomicAdd(&acc[1], red[1]);
+  }
+}
+
+// ---------------------------------------------------------------- Q2
+// Two image rows per CTA, processed one after the other through one FFT buffer.
+template <int LOGK>
+__global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(FftArgs A) {
+  constexpr int K = 1 << LOGK, T = K / 16, SROW = K + K / 16 + 1;
+  extern __shared__ float2 smem[];
+  float* gs = reinterpret_cast<float*>(smem + SROW);  // 2 x n gradient values
+  const int j = threadIdx.x;
+  const int n = A.n;
+  const int a0 = 2 * blockIdx.x;
+#pragma unroll 1
+  for (int q = 0; q < 2; ++q) {
+    const int a = a0 + q;
+    const float2* row = A.tmp + (size_t)a * K;
+    float2 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = row[j + i * T];
+    fft_row<LOGK, +1>(v, smem, j, A.tw);
+    const float ca = A.cinv[a];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int b = unpad_index(j + i * T, n, K);
+      if (b >= 0) gs[q * n + b] = v[i].x * ca * A.cinv[b];
+    }
+  }
+  __syncthreads();
+  double s0 = 0.0, s1 = 0.0;
+  const float gamma = A.gamma;
+  const size_t base = (size_t)a0 * n;
+  if (A.epi == EPI_ADJ || A.epi == EPI_NORMAL) {
+    for (int i = j; i < 2 * n; i += T) {
+      const float g = gs[i];
+      A.out[base + i] = g;
+      s0 += (double)g * g;
+    }
+  } else if (A.epi == EPI_GRAD) {
+    for (int i = j; i < 2 * n; i += T) A.out[base + i] = A.x[base + i] - gamma * gs[i];
+  } else {  // EPI_HAAR: z = x - gamma g on 2x2 blocks, Haar soft-threshold, positivity
+    const float t = A.t;
+    for (int bb = j; bb < n / 2; bb += T) {
+      const int b = 2 * bb;
+      const float x00 = A.x[base + b], x01 = A.x[base + b + 1];
+      const float x10 = A.x[base + n + b], x11 = A.x[base + n + b + 1];
+      const float z00 = x00 - gamma * gs[b], z01 = x01 - gamma * gs[b + 1];
+      const float z10 = x10 - gamma * gs[n + b], z11 = x11 - gamma * gs[n + b + 1];
+      const float ha = soft(0.5f * (z00 + z01 + z10 + z11), t);
+      const float hh = soft(0.5f * (z00 - z01 + z10 - z11), t);
+      const float hv = soft(0.5f * (z00 + z01 - z10 - z11), t);
+      const float hd = soft(0.5f * (z00 - z01 - z10 + z11), t);
+      const float o00 = fmaxf(0.f, 0.5f * (ha + hh + hv + hd));
+      const float o01 = fmaxf(0.f, 0.5f * (ha - hh + hv - hd));
+      const float o10 = fmaxf(0.f, 0.5f * (ha + hh - hv - hd));
+      const float o11 = fmaxf(0.f, 0.5f * (ha - hh - hv + hd));
+      A.out[base + b] = o00;
+      A.out[base + b + 1] = o01;
+      A.out[base + n + b] = o10;
+      A.out[base + n + b + 1] = o11;
+      const double d00 = (double)o00 - x00, d01 = (double)o01 - x01;
+      const double d10 = (double)o10 - x10, d11 = (double)o11 - x11;
+      s0 += d00 * d00 + d01 * d01 + d10 * d10 + d11 * d11;
+      s1 += (double)o00 * o00 + (double)o01 * o01 + (double)o10 * o10 + (double)o11 * o11;
+      // fmaxf(0, NaN) is 0, so positivity would hide a non-finite gradient: poison the norms
+      if (!(isfinite(z00) && isfinite(z01) && isfinite(z10) && isfinite(z11))) s1 = __longlong_as_double(0x7ff8000000000000LL);
+    }
+  }
+  if (A.acc && (A.epi == EPI_HAAR || A.epi == EPI_NORMAL))
+    block_reduce_add(s0, s1, A.acc, reinterpret_cast<double*>(smem));
+}
+
+// ---------------------------------------------------------------- launchers
+constexpr int SMEM_BUDGET = 140 * 1024;
+
+template <int LOGK>
+constexpr int rows_per_cta() {
+  constexpr int K = 1 << LOGK, T = K / 16;
+  int r = 16;
+  while (r > 1 && (r * T > 1024 || r * (K + K / 16) * 8 > SMEM_BUDGET)) r >>= 1;
+  return r;
+}
+
+template <int LOGK>
+int launch_forward(pnp_plan* p, const FftArgs& A) {
+  constexpr int K = 1 << LOGK, T = K / 16, R = rows_per_cta<LOGK>(), SROW = K + K / 16 + 1;
+  const int smem = R * SROW * 8;
+  static bool attr = false;
+  if (!attr) {
+    PNP_CUDA(cudaFuncSetAttribute(fft_p1<LOGK, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PNP_CUDA(cudaFuncSetAttribute(fft_p2<LOGK, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  fft_p1<LOGK, R><<<(p->n + R - 1) / R, R * T, smem, p->stream>>>(A);
+  PNP_CHECK_LAUNCH();
+  fft_p2<LOGK, R><<<K / R, R * T, smem, p->stream>>>(A);
+  PNP_CHECK_LAUNCH();
+  return PNP_OK;
+}
+
+template <int LOGK>
+int launch_adjoint(pnp_plan* p, const FftArgs& A) {
+  constexpr int K = 1 << LOGK, T = K / 16, R = rows_per_cta<LOGK>(), SROW = K + K / 16 + 1;
+  const int smem1 = R * SROW * 8;
+  const int smem2 = SROW * 8 + 2 * p->n * 4;
+  static int attr2 = 0;
+  static bool attr1 = false;
+  if (!attr1) {
+    PNP_CUDA(cudaFuncSetAttribute(fft_q1<LOGK, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
+    attr1 = true;
+  }
+  if (smem2 > attr2) {
+    PNP_CUDA(cudaFuncSetAttribute(fft_q2<LOGK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+    attr2 = smem2;
+  }
+  fft_q1<LOGK, R><<<K / R, R * T, smem1, p->stream>>>(A);
+  PNP_CHECK_LAUNCH();
+  fft_q2<LOGK><<<p->n / 2, T, smem2, p->stream>>>(A);
+  PNP_CHECK_LAUNCH();
+  return PNP_OK;
+}
+
+}  // namespace
+
+int fft_forward(pnp_plan* p, const float* x) {
+  FftArgs A{};
+  A.n = p->n;
+  A.x = x;
+  A.cinv = p->d_cinv;
+  A.tw = p->d_tw;
+  A.tmp = p->d_tmp;
+  A.grid = p->d_gridA;
+  cudaEvent_t ev;
+  if (int rc = stage_begin(p, 0, &ev)) return rc;
+  int rc = PNP_OK;
+  switch (p->logK) {
+    case 6: rc = launch_forward<6>(p, A); break;
+    case 7: rc = launch_forward<7>(p, A); break;
+    case 8: rc = launch_forward<8>(p, A); break;
+    case 9: rc = launch_forward<9>(p, A); break;
+    case 10: rc = launch_forward<10>(p, A); break;
+    case 11: rc = launch_forward<11>(p, A); break;
+    case 12: rc = launch_forward<12>(p, A); break;
+    case 13: rc = launch_forward<13>(p, A); break;
+    case 14: rc = launch_forward<14>(p, A); break;
+    default: rc = fail(PNP_ERR_UNSUPPORTED, "grid side K must be 2^6..2^14");
+  }
+  if (rc) return rc;
+  return stage_end(p, 0, ev);
+}
+
+int fft_adjoint(pnp_plan* p, int mode, const float* x, float* out, float gamma, float t) {
+  FftArgs A{};
+  A.n = p->n;
+  A.x = x;
+  A.cinv = p->d_cinv;
+  A.tw = p->d_tw;
+  A.tmp = p->d_tmp;
+  A.grid = p->d_gridB;
+  A.out = out;
+  A.acc = p->d_acc;
+  A.gamma = gamma;
+  A.t = t;
+  A.epi = mode;
+  cudaEvent_t ev;
+  if (int rc = stage_begin(p, 2, &ev)) return rc;
+  int rc = PNP_OK;
+  switch (p->logK) {
+    case 6: rc = launch_adjoint<6>(p, A); break;
+    case 7: rc = launch_adjoint<7>(p, A); break;
+    case 8: rc = launch_adjoint<8>(p, A); break;
+    case 9: rc = launch_adjoint<9>(p, A); break;
+    case 10: rc = launch_adjoint<10>(p, A); break;
+    case 11: rc = launch_adjoint<11>(p, A); break;
+    case 12: rc = launch_adjoint<12>(p, A); break;
+    case 13: rc = launch_adjoint<13>(p, A); break;
+    case 14: rc = launch_adjoint<14>(p, A); break;
+    default: rc = fail(PNP_ERR_UNSUPPORTED, "grid side K must be 2^6..2^14");
+  }
+  if (rc) return rc;
+  return stage_end(p, 2, ev);
+}
+
+}  // namespace pnp

@@ -1,0 +1,449 @@
+// C ABI entry points (include/pnp.h): plan lifetime, the operator calls of
+// Eq. 1 and App. A, power iteration, denoisers and the PnP-FB loop of Eq. fb.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace pnp {
+
+static thread_local std::string t_err;
+std::atomic<int64_t> g_launches{0};
+
+void set_error(const std::string& msg) { t_err = msg; }
+int fail(int code, const std::string& msg) {
+  t_err = msg;
+  return code;
+}
+
+int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t* block);
+int export_rows_impl(const pnp_plan* p, const int64_t* rows, int64_t nrows, int64_t* offsets,
+                     float* weights, int32_t* cols);
+int norm2_dev(cudaStream_t s, const float* v, int64_t count, double* acc);
+int fill_image(cudaStream_t s, float* out, int64_t count, float v);
+
+int stage_begin(pnp_plan* p, int stage, cudaEvent_t* a) {
+  *a = nullptr;
+  if (!p->timing) return PNP_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  PNP_CUDA(cudaStreamIsCapturing(p->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return PNP_OK;
+  PNP_CUDA(cudaEventCreate(a));
+  PNP_CUDA(cudaEventRecord(*a, p->stream));
+  (void)stage;
+  return PNP_OK;
+}
+
+int stage_end(pnp_plan* p, int stage, cudaEvent_t a) {
+  if (!a) return PNP_OK;
+  cudaEvent_t b;
+  PNP_CUDA(cudaEventCreate(&b));
+  PNP_CUDA(cudaEventRecord(b, p->stream));
+  p->timed.push_back({stage, a, b});
+  return PNP_OK;
+}
+
+namespace {
+
+void clear_timing(pnp_plan* p) {
+  for (auto& t : p->timed) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  p->timed.clear();
+}
+
+void free_plan(pnp_plan* p) {
+  if (!p) return;
+  clear_timing(p);
+  cudaFree(p->d_cinv);
+  cudaFree(p->d_tw);
+  cudaFree(p->d_gridA);
+  cudaFree(p->d_gridB);
+  cudaFree(p->d_tmp);
+  cudaFree(p->d_w);
+  cudaFree(p->d_cols);
+  cudaFree(p->d_rowptr);
+  cudaFree(p->d_perm);
+  cudaFree(p->d_ysorted);
+  cudaFree(p->d_units);
+  cudaFree(p->d_acc);
+  cudaFree(p->d_status);
+  if (p->cstream) cudaStreamDestroy(p->cstream);
+  for (auto& e : p->ev_join)
+    if (e) cudaEventDestroy(e);
+  for (float* im : p->d_img) cudaFree(im);
+  delete p;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int read_acc(pnp_plan* p, double* h, int count) {
+  PNP_CUDA(cudaMemcpyAsync(h, p->d_acc, count * sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  PNP_CUDA(cudaStreamSynchronize(p->stream));
+  return PNP_OK;
+}
+
+// One FB iteration x_next = D(x_cur - gamma grad f(x_cur)); FP64 norms land in acc[0..1].
+int fb_iteration(pnp_plan* p, pnp_den* d, const float* cur, float* nxt, double gamma) {
+  if (int rc = fft_forward(p, cur)) return rc;
+  if (int rc = gridding_pass(p, G_FUSED, reinterpret_cast<const float2*>(p->d_ysorted), nullptr)) return rc;
+  if (d->kind == PNP_DEN_HAAR) return fft_adjoint(p, EPI_HAAR, cur, nxt, (float)gamma, (float)d->t);
+  if (int rc = fft_adjoint(p, EPI_GRAD, cur, p->d_img[1], (float)gamma, 0.f)) return rc;
+  return cnn_denoise(d, p->stream, p->d_img[1], nxt, p->n, p->d_acc, cur);
+}
+
+// Captures two FB iterations (x -> work -> x) once and replays them on the
+// plan's private stream, joined to the caller's stream with events.
+struct GraphRunner {
+  pnp_plan* p;
+  pnp_den* d;
+  float** buf;
+  double gamma;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;
+  GraphRunner(pnp_plan* p_, pnp_den* d_, float** b, double g) : p(p_), d(d_), buf(b), gamma(g) {}
+  ~GraphRunner() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+  int capture() {
+    cudaGraph_t g = nullptr;
+    const int64_t before = g_launches.load();
+    PNP_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = fb_iteration(p, d, buf[0], buf[1], gamma);
+    if (!rc) rc = fb_iteration(p, d, buf[1], buf[0], gamma);
+    cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+    kernels = g_launches.load() - before;
+    g_launches.fetch_sub(kernels);
+    if (!rc && e != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(PNP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    if (!rc) {
+      e = cudaGraphInstantiate(&exec, g, 0);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        exec = nullptr;
+        rc = fail(PNP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
+    }
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  int run_pairs(int pairs) {
+    cudaStream_t user = p->stream;
+    PNP_CUDA(cudaEventRecord(p->ev_join[0], user));
+    PNP_CUDA(cudaStreamWaitEvent(p->cstream, p->ev_join[0], 0));
+    p->stream = p->cstream;
+    int rc = exec ? PNP_OK : capture();
+    for (int i = 0; i < pairs && rc == PNP_OK; ++i) {
+      cudaError_t e = cudaGraphLaunch(exec, p->stream);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(PNP_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+      } else {
+        g_launches.fetch_add(kernels);
+      }
+    }
+    p->stream = user;
+    if (cudaEventRecord(p->ev_join[1], p->cstream) != cudaSuccess ||
+        cudaStreamWaitEvent(user, p->ev_join[1], 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (rc == PNP_OK) rc = fail(PNP_ERR_CUDA, "stream join failed");
+    }
+    return rc;
+  }
+};
+
+}  // namespace
+}  // namespace pnp
+
+using namespace pnp;
+
+extern "C" {
+
+const char* pnp_last_error(void) { return t_err.c_str(); }
+
+int64_t pnp_kernel_launch_count(void) { return g_launches.load(); }
+
+int pnp_plan_create(pnp_plan** plan, int n, int K, int64_t M, const double* uvw_host, double dl,
+                    const int8_t* J_per_row_host, int J, int weight_dtype, const int32_t* block_host,
+                    int nblocks, void* stream) {
+  if (!plan) return fail(PNP_ERR_INVALID_ARG, "plan pointer is NULL");
+  *plan = nullptr;
+  if (n < 8 || (n & 1)) return fail(PNP_ERR_INVALID_ARG, "n must be even and >= 8");
+  if (!is_pow2(K) || K < 64 || K > 16384) return fail(PNP_ERR_INVALID_ARG, "K must be a power of two in [64, 16384]");
+  if (n > K / 2) return fail(PNP_ERR_INVALID_ARG, "n must be <= K/2 (at least 2x oversampling)");
+  if (J < 2 || J > 14) return fail(PNP_ERR_INVALID_ARG, "J must lie in [2, 14]");
+  if (M < 0 || M > INT32_MAX) return fail(PNP_ERR_INVALID_ARG, "M must lie in [0, 2^31)");
+  if (M > 0 && !uvw_host) return fail(PNP_ERR_INVALID_ARG, "uvw is NULL");
+  if (weight_dtype != PNP_W_C64 && weight_dtype != PNP_W_BF16C) return fail(PNP_ERR_INVALID_ARG, "bad weight_dtype");
+  if (nblocks < 1) return fail(PNP_ERR_INVALID_ARG, "nblocks must be >= 1");
+  if (!(dl >= 0.0) || !std::isfinite(dl)) return fail(PNP_ERR_INVALID_ARG, "dl must be finite and >= 0");
+  pnp_plan* p = new pnp_plan();
+  p->n = n;
+  p->K = K;
+  p->logK = 0;
+  while ((1 << p->logK) < K) ++p->logK;
+  p->M = M;
+  p->J = J;
+  p->dl = dl;
+  p->wdtype = weight_dtype;
+  p->nblocks = nblocks;
+  p->stream = reinterpret_cast<cudaStream_t>(stream);
+  p->tile = K >= 128 ? 48 : 16;
+  if (cudaGetDevice(&p->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return fail(PNP_ERR_CUDA, "no CUDA device available");
+  }
+  if (cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->ev_join[1], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(p);
+    return fail(PNP_ERR_CUDA, "stream/event creation failed");
+  }
+  int rc = plan_build(p, uvw_host, J_per_row_host, block_host);
+  if (rc != PNP_OK) {
+    std::string keep = t_err;
+    free_plan(p);
+    t_err = keep;
+    return rc;
+  }
+  *plan = p;
+  return PNP_OK;
+}
+
+void pnp_plan_destroy(pnp_plan* plan) {
+  if (plan) cudaStreamSynchronize(plan->stream);
+  free_plan(plan);
+}
+
+int pnp_plan_get_info(const pnp_plan* p, pnp_plan_info* info) {
+  if (!p || !info) return fail(PNP_ERR_INVALID_ARG, "NULL argument");
+  info->n = p->n;
+  info->K = p->K;
+  info->J = p->J;
+  info->weight_dtype = p->wdtype;
+  info->tile = p->tile;
+  info->nblocks = p->nblocks;
+  info->M = p->M;
+  info->nnz = p->nnz;
+  info->n_units = p->n_units;
+  info->beta = p->beta;
+  info->dl = p->dl;
+  info->device_bytes = p->device_bytes;
+  return PNP_OK;
+}
+
+int pnp_plan_set_unit_nnz(pnp_plan* p, int64_t unit_nnz) {
+  if (!p || unit_nnz < 0) return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  if (unit_nnz == 0) return PNP_OK;
+  PNP_CUDA(cudaStreamSynchronize(p->stream));
+  p->unit_nnz = unit_nnz;
+  return build_units(p);
+}
+
+int pnp_plan_device_status(pnp_plan* p, int* flags) {
+  if (!p || !flags) return fail(PNP_ERR_INVALID_ARG, "NULL argument");
+  PNP_CUDA(cudaMemcpyAsync(flags, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  PNP_CUDA(cudaStreamSynchronize(p->stream));
+  return PNP_OK;
+}
+
+int pnp_plan_set_timing(pnp_plan* p, int enable) {
+  if (!p) return fail(PNP_ERR_INVALID_ARG, "NULL plan");
+  p->timing = enable != 0;
+  return PNP_OK;
+}
+
+int pnp_plan_read_timing(pnp_plan* p, double* ms, int64_t* count) {
+  if (!p || !ms || !count) return fail(PNP_ERR_INVALID_ARG, "NULL argument");
+  PNP_CUDA(cudaStreamSynchronize(p->stream));
+  for (int i = 0; i < 3; ++i) {
+    ms[i] = 0;
+    count[i] = 0;
+  }
+  for (auto& t : p->timed) {
+    float e = 0;
+    PNP_CUDA(cudaEventElapsedTime(&e, t.a, t.b));
+    if (t.stage >= 0 && t.stage < 3) {
+      ms[t.stage] += e;
+      count[t.stage] += 1;
+    }
+  }
+  clear_timing(p);
+  return PNP_OK;
+}
+
+int pnp_plan_export_rows(const pnp_plan* p, const int64_t* rows, int64_t nrows, int64_t* offsets,
+                         float* weights, int32_t* cols) {
+  if (!p || (nrows > 0 && (!rows || !offsets)) || nrows < 0) return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  if (nrows == 0) {
+    if (offsets) offsets[0] = 0;
+    return PNP_OK;
+  }
+  return export_rows_impl(p, rows, nrows, offsets, weights, cols);
+}
+
+int phi_forward(pnp_plan* p, const float* x, float* y) {
+  if (!p || !x || (p->M > 0 && !y)) return fail(PNP_ERR_INVALID_ARG, "NULL argument");
+  if (int rc = fft_forward(p, x)) return rc;
+  return gridding_pass(p, G_DEGRID, nullptr, reinterpret_cast<float2*>(y));
+}
+
+int phi_adjoint(pnp_plan* p, const float* y, float* x) {
+  if (!p || !x || (p->M > 0 && !y)) return fail(PNP_ERR_INVALID_ARG, "NULL argument");
+  if (int rc = permute_y(p, reinterpret_cast<const float2*>(y))) return rc;
+  if (int rc = gridding_pass(p, G_GRID, reinterpret_cast<const float2*>(y), nullptr)) return rc;
+  return fft_adjoint(p, EPI_ADJ, nullptr, x, 0.f, 0.f);
+}
+
+int grad_step(pnp_plan* p, const float* x, const float* y, double gamma, float* x_out) {
+  if (!p || !x || !x_out || (p->M > 0 && !y)) return fail(PNP_ERR_INVALID_ARG, "NULL argument");
+  if (x == x_out) return fail(PNP_ERR_INVALID_ARG, "x and x_out must not alias");
+  if (!std::isfinite(gamma)) return fail(PNP_ERR_INVALID_ARG, "gamma must be finite");
+  if (int rc = permute_y(p, reinterpret_cast<const float2*>(y))) return rc;
+  if (int rc = fft_forward(p, x)) return rc;
+  if (int rc = gridding_pass(p, G_FUSED, reinterpret_cast<const float2*>(y), nullptr)) return rc;
+  return fft_adjoint(p, EPI_GRAD, x, x_out, (float)gamma, 0.f);
+}
+
+int op_norm(pnp_plan* p, const float* v0, int max_it, double tol, double* L_out, int* iters_out) {
+  if (!p || !L_out || max_it < 1 || !(tol >= 0)) return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  const int64_t N = (int64_t)p->n * p->n;
+  float* v = p->d_img[0];
+  float* g = p->d_img[2];
+  if (v0) PNP_CUDA(cudaMemcpyAsync(v, v0, N * sizeof(float), cudaMemcpyDeviceToDevice, p->stream));
+  else if (int rc = fill_image(p->stream, v, N, 1.f)) return rc;
+  if (int rc = zero_acc(p->stream, p->d_acc, 4)) return rc;
+  if (int rc = norm2_dev(p->stream, v, N, p->d_acc)) return rc;
+  if (int rc = scale_image(p->stream, v, v, N, p->d_acc, 0)) return rc;
+  double L = 0.0, h[2];
+  int it = 0;
+  for (it = 1; it <= max_it; ++it) {
+    if (int rc = fft_forward(p, v)) return rc;
+    if (int rc = gridding_pass(p, G_FUSED, nullptr, nullptr)) return rc;
+    if (int rc = fft_adjoint(p, EPI_NORMAL, nullptr, g, 0.f, 0.f)) return rc;
+    if (int rc = scale_image(p->stream, g, v, N, p->d_acc, 0)) return rc;
+    if (int rc = read_acc(p, h, 1)) return rc;
+    const double Ln = std::sqrt(h[0]);
+    if (!std::isfinite(Ln)) return fail(PNP_ERR_DIVERGED, "power iteration produced a non-finite norm");
+    const bool done = it > 1 && std::fabs(Ln - L) <= tol * Ln;
+    L = Ln;
+    if (done) break;
+  }
+  *L_out = L;
+  if (iters_out) *iters_out = it > max_it ? max_it : it;
+  return PNP_OK;
+}
+
+int pnp_den_create_haar(pnp_den** den, double t, void* stream) {
+  if (!den || !(t >= 0) || !std::isfinite(t)) return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  pnp_den* d = new pnp_den();
+  d->kind = PNP_DEN_HAAR;
+  d->t = t;
+  d->stream = reinterpret_cast<cudaStream_t>(stream);
+  *den = d;
+  return PNP_OK;
+}
+
+int pnp_den_create_cnn(pnp_den** den, const float* weights_host, const int32_t* facet_rows_host, int nfr,
+                       const int32_t* facet_cols_host, int nfc, int halo, int n, void* stream) {
+  if (!den || !weights_host || n < 1 || halo < 0) return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  *den = nullptr;
+  pnp_den* d = new pnp_den();
+  d->kind = PNP_DEN_CNN;
+  d->stream = reinterpret_cast<cudaStream_t>(stream);
+  int rc = cnn_create(d, weights_host, facet_rows_host, nfr, facet_cols_host, nfc, halo, n);
+  if (rc != PNP_OK) {
+    std::string keep = t_err;
+    cnn_destroy(d);
+    delete d;
+    t_err = keep;
+    return rc;
+  }
+  *den = d;
+  return PNP_OK;
+}
+
+void pnp_den_destroy(pnp_den* den) {
+  if (!den) return;
+  cudaStreamSynchronize(den->stream);
+  if (den->kind == PNP_DEN_CNN) cnn_destroy(den);
+  delete den;
+}
+
+int denoise(pnp_den* d, const float* x_in, float* x_out, int n) {
+  if (!d || !x_in || !x_out || n < 2 || (n & 1)) return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  if (x_in == x_out) return fail(PNP_ERR_INVALID_ARG, "x_in and x_out must not alias");
+  if (d->kind == PNP_DEN_HAAR) return haar_denoise_dev(d->stream, x_in, x_out, n, (float)d->t, nullptr, nullptr);
+  return cnn_denoise(d, d->stream, x_in, x_out, n, nullptr, nullptr);
+}
+
+int pnp_fb_run(pnp_plan* p, pnp_den* d, const float* y, const pnp_params* prm, float* x, pnp_stats* st) {
+  if (!p || !d || !prm || !x || (p->M > 0 && !y)) return fail(PNP_ERR_INVALID_ARG, "NULL argument");
+  if (prm->max_iter < 0) return fail(PNP_ERR_INVALID_ARG, "max_iter must be >= 0");
+  double L = prm->L;
+  if (!(L > 0)) {
+    if (int rc = op_norm(p, nullptr, 500, 1e-6, &L, nullptr)) return rc;
+  }
+  const double gamma = prm->gamma > 0 ? prm->gamma : 1.98 / L;
+  const int check = prm->check_every > 0 ? prm->check_every : 10;
+  const bool graph = prm->use_graph != 0;
+  const int bit = 1 << d->kind;
+  if (int rc = permute_y(p, reinterpret_cast<const float2*>(y))) return rc;
+  float* buf[2] = {x, p->d_img[0]};
+  int c = 0, k = 0, rc = PNP_OK;
+  double h[2] = {0, 0}, rel = 0, xn = 0, xn_min = -1;
+  GraphRunner gr(p, d, buf, gamma);
+  while (k < prm->max_iter && rc == PNP_OK) {
+    const int chunk = std::min(check, prm->max_iter - k);
+    for (int done = 0; done < chunk && rc == PNP_OK;) {
+      const int left = chunk - done;
+      if (graph && c == 0 && left >= 2 && (p->primed & bit)) {
+        rc = gr.run_pairs(left / 2);
+        done += 2 * (left / 2);
+      } else {
+        rc = fb_iteration(p, d, buf[c], buf[1 - c], gamma);
+        if (rc == PNP_OK) p->primed |= bit;
+        c = 1 - c;
+        ++done;
+      }
+    }
+    if (rc) break;
+    k += chunk;
+    if ((rc = read_acc(p, h, 2))) break;
+    xn = std::sqrt(h[1]);
+    rel = xn > 0 ? std::sqrt(h[0]) / xn : 0.0;
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) {
+      rc = fail(PNP_ERR_DIVERGED, "iterate became non-finite at iteration " + std::to_string(k));
+      break;
+    }
+    if (prm->diverge_factor > 0 && xn_min > 0 && xn > prm->diverge_factor * xn_min) {
+      rc = fail(PNP_ERR_DIVERGED, "iterate norm grew past the divergence factor at iteration " + std::to_string(k));
+      break;
+    }
+    if (xn > 0 && (xn_min < 0 || xn < xn_min)) xn_min = xn;
+    if (prm->tol > 0 && rel < prm->tol) break;
+  }
+  if (c == 1) {
+    cudaError_t e = cudaMemcpyAsync(x, buf[1], (size_t)p->n * p->n * sizeof(float), cudaMemcpyDeviceToDevice, p->stream);
+    if (e != cudaSuccess && rc == PNP_OK) {
+      cudaGetLastError();
+      rc = fail(PNP_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
+  if (st) {
+    st->iters = k;
+    st->L = L;
+    st->gamma = gamma;
+    st->rel_change = rel;
+    st->x_norm = xn;
+  }
+  return rc;
+}
+
+}  // extern "C"

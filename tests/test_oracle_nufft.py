@@ -170,3 +170,14 @@ def test_w_rows_truncation_error_decreases_with_support():
         errs.append(np.linalg.norm(y - yd) / np.linalg.norm(yd))
     assert all(e1 > e2 for e1, e2 in zip(errs, errs[1:]))
     assert errs[-1] < 1e-2
+
+
+def test_nudft_adjoint_identity():
+    n = 12
+    rng = _rng(8)
+    omega = rng.uniform(-np.pi, np.pi, (70, 2))
+    x = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    r = rng.standard_normal(70) + 1j * rng.standard_normal(70)
+    lhs = np.vdot(r, nu.nudft(omega, x))
+    rhs = np.vdot(nu.nudft_adjoint(omega, r, n), x)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
