@@ -202,6 +202,25 @@ int denoise(pnp_den* den, const float* x_in, float* x_out, int n);
 int pnp_fb_run(pnp_plan* plan, pnp_den* den, const float* y, const pnp_params* params,
                float* x_inout, pnp_stats* stats);
 
+/* Allocation-free plain denoiser with stopping-test norms.  The paper has no
+ * counterpart: this call exists for callers that cannot allocate device memory
+ * (code running under a fixed, pre-reserved memory budget or a caller-owned
+ * pool, or a host runtime that forbids allocation after start-up).  It applies
+ * the same Haar soft-threshold + positivity as the Haar denoiser to z (dev
+ * n*n float32) and writes x_out (dev n*n), and writes into norms (dev, 2
+ * doubles) the FP64 sums ||x_out - x_prev||^2 (0 when x_prev is NULL) and
+ * ||x_out||^2, summed in a fixed order.  It calls no cudaMalloc/cudaFree and
+ * no allocating library routine: its scratch (two doubles per pair of image
+ * rows) is a static device array of 128 KiB that every GPU loading the library
+ * holds until exit.  Limit: n even, 2 <= n <= 16384; larger n is rejected with
+ * PNP_ERR_INVALID_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the array: calls that
+ * overlap on the GPU race and must be serialised by the caller.  Asynchronous
+ * on stream (NULL: legacy default stream). */
+int pnp_haar_denoise_noalloc(const float* z, const float* x_prev, float* x_out, int n, double t,
+                             double* norms, void* stream);
+
 /* Thread-local message of the last failing call ("" if none). */
 const char* pnp_last_error(void);
 

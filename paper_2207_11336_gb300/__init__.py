@@ -29,7 +29,7 @@ EXPORTED = [
     "pnp_plan_export_rows", "phi_forward", "phi_adjoint", "grad_step", "op_norm",
     "pnp_den_create_haar", "pnp_den_create_cnn", "pnp_den_destroy", "denoise", "pnp_fb_run",
     "pnp_last_error", "pnp_kernel_launch_count", "pnp_plan_set_timing", "pnp_plan_read_timing",
-    "pnp_plan_device_status",
+    "pnp_plan_device_status", "pnp_haar_denoise_noalloc",
 ]
 
 
@@ -86,13 +86,14 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_fb_run.argtypes = [vp, vp, vp, C.POINTER(_Params), vp, C.POINTER(_Stats)]
     L.pnp_plan_set_timing.argtypes = [vp, i32]
     L.pnp_plan_device_status.argtypes = [vp, C.POINTER(i32)]
+    L.pnp_haar_denoise_noalloc.argtypes = [vp, vp, vp, i32, dbl, vp, vp]
     L.pnp_plan_read_timing.argtypes = [vp, vp, vp]
     L.pnp_last_error.restype = C.c_char_p
     L.pnp_kernel_launch_count.restype = i64
     for name in ("pnp_plan_create", "pnp_plan_get_info", "pnp_plan_set_unit_nnz", "pnp_plan_export_rows",
                  "phi_forward", "phi_adjoint", "grad_step", "op_norm", "pnp_den_create_haar",
                  "pnp_den_create_cnn", "denoise", "pnp_fb_run", "pnp_plan_set_timing",
-                 "pnp_plan_read_timing", "pnp_plan_device_status"):
+                 "pnp_plan_read_timing", "pnp_plan_device_status", "pnp_haar_denoise_noalloc"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -335,3 +336,23 @@ class CnnDenoiser(_Denoiser):
                                         None if fr is None else fr.ctypes.data, 0 if fr is None else fr.size,
                                         None if fc is None else fc.ctypes.data, 0 if fc is None else fc.size,
                                         int(halo), int(n), _stream_handle(stream)))
+
+
+def haar_denoise_noalloc(z, t: float, x_prev=None, out=None, norms=None, stream=None):
+    """Haar denoiser + FP64 norms through the allocation-free entry point.
+
+    For callers that cannot let the library allocate: every buffer is passed
+    in (``out`` n x n float32 and ``norms`` 2 float64 on the device are
+    created here only when omitted).  Returns (out, norms) with
+    norms = (||out - x_prev||^2, ||out||^2).
+    """
+    import torch
+    n = z.shape[0]
+    _cuda_f32(z, (n, n), "z")
+    if x_prev is not None:
+        _cuda_f32(x_prev, (n, n), "x_prev")
+    o = torch.empty_like(z) if out is None else out
+    nr = torch.empty(2, dtype=torch.float64, device=z.device) if norms is None else norms
+    _check(lib().pnp_haar_denoise_noalloc(_ptr(z), None if x_prev is None else _ptr(x_prev), _ptr(o),
+                                          int(n), float(t), _ptr(nr), _stream_handle(stream)))
+    return o, nr
