@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="C3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--kernel-case", choices=["gridding"], default=None,
+                    help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
     return ap.parse_args()
 
 
@@ -281,7 +283,7 @@ def run_gpu(args):
     g_ms, g_cnt = tim["gridding"]
     g_ms_launch = g_ms / max(g_cnt, 1)
     wbytes = 8
-    alg_bytes = info["nnz"] * (wbytes + 4) + M * 16 + 2 * K * K * 8
+    alg_bytes = info["nnz"] * (wbytes + 4) + M * 8 + 2 * K * K * 8
     hbm, peak_kind = measured_peaks()
     achieved = alg_bytes / (g_ms_launch * 1e-3) / 1e9
 
@@ -337,8 +339,37 @@ def run_gpu(args):
     return 0
 
 
+def run_kernel_case(args):
+    """Small case of the fused gridding pass for ncu: 1024^2 image, 2048^2 grid, M = 2e6
+    (same row density per grid cell and J mix as the benchmark workload, G = 3.2 GB)."""
+    import torch
+    import paper_2207_11336_gb300 as pnp
+    import synth
+    n, K, M = 1024, 2048, 2_000_000
+    prob = synth.make_problem("C1", M=M, n=n, K=K)
+    plan = pnp.Plan(n, K, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"])
+    x = torch.from_numpy(prob["x_true"].astype(np.float32)).cuda()
+    y = torch.from_numpy(prob["noise"].astype(np.complex64)).cuda()
+    out = torch.empty_like(x)
+    for _ in range(max(args.warmup, 1)):
+        plan.grad_step(x, y, 1e-6, out)
+    plan.set_timing(True)
+    for _ in range(max(args.steps, 1)):
+        plan.grad_step(x, y, 1e-6, out)
+    t = plan.read_timing()
+    info = plan.info
+    ms = t["gridding"][0] / max(t["gridding"][1], 1)
+    alg = info["nnz"] * 12 + M * 8 + 2 * K * K * 8
+    print(json.dumps({"case": "gridding 1024^2/2048^2 M=2e6", "nnz": info["nnz"], "units": info["n_units"],
+                      "gridding_ms": ms, "alg_bytes": alg, "GBps": alg / ms / 1e6,
+                      "stage_ms": {k: v[0] / max(v[1], 1) for k, v in t.items()}}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.kernel_case:
+        return run_kernel_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -50,11 +50,30 @@ __host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 }
 
 // ------------------------------------------------------------------ work units
-// A work unit of the gridding kernels: consecutive rows (in tile-sorted order)
-// whose first tap lies in one grid tile.
-struct Unit {
+// Gridding work list.  A chunk is a run of consecutive rows (tile-sorted order)
+// with at most CHUNK_TAPS taps and CHUNK_ROWS rows: the unit of one TMA bulk
+// transfer.  A unit is a run of consecutive chunks whose rows all have their
+// first tap in one grid tile (and one data block).
+constexpr int CHUNK_TAPS = 4096;
+constexpr int CHUNK_ROWS = 128;
+constexpr int NSTAGE = 3;          // shared-memory pipeline depth of the gridding pass
+constexpr int GPASS_CONSUMERS = 24; // consumer warps per gridding CTA (plus one producer warp)
+constexpr int GPASS_THREADS = 32 * (GPASS_CONSUMERS + 1);
+constexpr int TAP_PAD = 16;        // weights/columns are allocated nnz + TAP_PAD long
+constexpr int ROW_PAD = 4;         // row offsets M + 1 + ROW_PAD, sorted y M + ROW_PAD
+
+struct Chunk {
   long long row_begin;
+  long long tap_begin;
   int nrows;
+  int ntaps;
+  int nn;   // taps per row (J^2, the same for every row of the chunk)
+  int pad;
+};
+
+struct Unit {
+  long long chunk_begin;
+  int nchunks;
   int tile;
 };
 
@@ -73,7 +92,7 @@ struct pnp_plan {
   int ntc = 0;         // tiles per grid side, ceil(K / tile)
   int slots = 8;       // register slots per lane per row (32*slots >= Jmax^2)
   int rpw = 2;         // rows per warp in flight
-  int64_t M = 0, nnz = 0, unit_nnz = 1 << 15;
+  int64_t M = 0, nnz = 0, unit_nnz = 1 << 17;
   double beta = 0, dl = 0;
   cudaStream_t stream = nullptr;   // caller's stream: every launch goes here
   cudaStream_t cstream = nullptr;  // private non-blocking stream for graph capture/replay
@@ -94,6 +113,8 @@ struct pnp_plan {
   float2* d_ysorted = nullptr; // M scratch: y in sorted order
   pnp::Unit* d_units = nullptr;
   int64_t n_units = 0;
+  pnp::Chunk* d_chunks = nullptr;
+  int64_t n_chunks = 0;
   double* d_acc = nullptr;     // FP64 accumulators [8]
   int* d_status = nullptr;     // device status flags [4] (bit 0: gridding index out of range)
   float* d_img[3] = {nullptr, nullptr, nullptr};  // n*n work images

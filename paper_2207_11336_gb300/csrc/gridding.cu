@@ -2,28 +2,36 @@
 // into one pass over G that forms the residual r = G X - y and grids it.
 //
 // G is CSR with rows sorted by the grid tile holding their first tap (and by
-// data block within a tile).  A work unit is a run of consecutive rows of one
-// tile.  For each unit a CTA
+// data block within a tile).  The host cuts the sorted rows into row-aligned
+// chunks of at most CHUNK_TAPS taps and groups consecutive chunks of one tile
+// into work units.  Each persistent CTA walks its units (round robin) and
+// streams their chunks through a ring of NSTAGE shared-memory stages with TMA
+// bulk copies (cp.async.bulk, completion counted on one mbarrier per stage):
+// the chunk's complex weights, int32 columns, int64 row offsets and (for the
+// gridding modes) its visibilities.  One thread issues the copies NSTAGE-1
+// chunks ahead -- across unit boundaries -- so HBM latency is hidden by copies
+// in flight rather than by resident warps.  Per unit the CTA
 //   1. stages the tile plus a (Jmax-1)-cell halo of the input grid X in shared
 //      memory (coalesced along k0, wrapped mod K);
-//   2. runs warp-per-row SpMV: the row's taps are read lane-strided (coalesced
-//      8-byte weights and 4-byte column indices, streamed past L1/L2), gathered
-//      from shared memory and reduced with warp shuffles; RPW rows are in
-//      flight per warp so enough loads are outstanding to cover HBM latency;
-//   3. scatters conj(G_mk) r_m of every tap into a shared-memory copy of the
-//      same tile+halo region (shared-memory float atomics);
-//   4. adds the non-zero cells of that region to the output grid with
-//      vector float2 global atomics.
+//   2. runs warp-per-row SpMV over each chunk from shared memory: lane-strided
+//      taps, gathers from the staged grid, warp-shuffle reduction;
+//   3. scatters conj(G_mk) r_m into a shared-memory copy of the same region
+//      (shared-memory float atomics);
+//   4. adds the non-zero cells of that region to the output grid with vector
+//      float2 global atomics.
 // Grid layout: grid[k1*K + k0]; column index of a tap = k1*K + k0.
 #include "common.cuh"
 
 namespace pnp {
 namespace {
 
+constexpr uint32_t WAIT_LIMIT = 1u << 26;  // bounded mbarrier waits (seconds, not forever)
+
 struct GArgs {
   int K, logK, T, S, ntc;
   const Unit* units;
   long long n_units;
+  const Chunk* chunks;
   const int64_t* rowptr;
   const void* w;
   const int32_t* cols;
@@ -32,122 +40,336 @@ struct GArgs {
   float2* y_out;        // caller order (G_DEGRID)
   const float2* gridA;  // input grid (G_DEGRID, G_FUSED)
   float2* gridB;        // output grid (G_GRID, G_FUSED)
-  int* status;          // bit 0 set when a tap falls outside the staged region (tap skipped)
+  int* status;          // bit 0: tap outside the staged region (skipped); bit 1: pipeline wait timed out
+};
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, P;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false when the limit was reached
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <typename WT>
+struct WBytes;
+template <>
+struct WBytes<float2> {
+  static constexpr int value = 8;
+};
+template <>
+struct WBytes<__nv_bfloat162> {
+  static constexpr int value = 4;
 };
 
 template <typename WT>
-__device__ __forceinline__ float2 load_w(const void* w, int64_t i);
-template <>
-__device__ __forceinline__ float2 load_w<float2>(const void* w, int64_t i) {
-  return __ldcs(reinterpret_cast<const float2*>(w) + i);
-}
-template <>
-__device__ __forceinline__ float2 load_w<__nv_bfloat162>(const void* w, int64_t i) {
-  const unsigned int u = __ldcs(reinterpret_cast<const unsigned int*>(w) + i);
-  __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&u);
-  return __bfloat1622float2(b);
+__device__ __forceinline__ float2 w_at(const unsigned char* base, int i) {
+  if constexpr (WBytes<WT>::value == 8) {
+    return reinterpret_cast<const float2*>(base)[i];
+  } else {
+    return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(base)[i]);
+  }
 }
 
-template <int MODE, typename WT, int SLOTS, int RPW>
-__global__ void __launch_bounds__(256) gpass(GArgs A) {
-  extern __shared__ float2 sm[];
-  const int S = A.S, SS = S * S, K = A.K, logK = A.logK, Km = K - 1;
-  float2* sx = sm;                                     // staged input region
-  float2* sy = (MODE == G_FUSED) ? sm + SS : sm;       // accumulated output region
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Shared-memory stage: [weights | columns | visibilities], each 128-B aligned.  Every
+// row of a chunk has the same support J (rows are sorted by J within a tile), so
+// row q of a chunk starts at tap q J^2 and the row offsets need not be read.
+template <typename WT>
+struct StageLayout {
+  static constexpr int al(int b) { return (b + 127) & ~127; }
+  static constexpr int W_BYTES = (CHUNK_TAPS + 8) * WBytes<WT>::value;
+  static constexpr int C_BYTES = (CHUNK_TAPS + 8) * 4;
+  static constexpr int Y_BYTES = (CHUNK_ROWS + 4) * 8;
+  static constexpr int W_OFF = 0;
+  static constexpr int C_OFF = al(W_BYTES);
+  static constexpr int Y_OFF = C_OFF + al(C_BYTES);
+  static constexpr int SIZE = Y_OFF + al(Y_BYTES);
+};
 
+// Position in a CTA's stream of chunks: unit u (global index) and chunk c within it.
+struct StreamPos {
+  long long u;
+  int c;
+};
+
+__device__ __forceinline__ bool advance(StreamPos& s, const GArgs& A) {
+  if (++s.c < A.units[s.u].nchunks) return true;
+  s.c = 0;
+  s.u += gridDim.x;
+  return s.u < A.n_units;
+}
+
+template <int MODE, typename WT>
+__device__ __forceinline__ void issue_chunk(const GArgs& A, const Chunk& ch, unsigned char* stage,
+                                            uint64_t* bar) {
+  using L = StageLayout<WT>;
+  constexpr int WB = WBytes<WT>::value;
+  // 16-byte aligned copy windows around the chunk (the arrays are padded at the end)
+  const long long tb0 = ch.tap_begin & ~3LL, te = (ch.tap_begin + ch.ntaps + 3) & ~3LL;
+  const long long rb0 = ch.row_begin & ~1LL, ye = (ch.row_begin + ch.nrows + 1) & ~1LL;
+  const uint32_t wbytes = (uint32_t)((te - tb0) * WB), cbytes = (uint32_t)((te - tb0) * 4);
+  const uint32_t ybytes = (uint32_t)((ye - rb0) * 8);
+  const bool need_y = MODE != G_DEGRID && A.y_in != nullptr;
+  mbar_expect_tx(bar, wbytes + cbytes + (need_y ? ybytes : 0));
+  bulk_g2s(stage + L::W_OFF, reinterpret_cast<const unsigned char*>(A.w) + tb0 * WB, wbytes, bar);
+  bulk_g2s(stage + L::C_OFF, A.cols + tb0, cbytes, bar);
+  if (need_y) bulk_g2s(stage + L::Y_OFF, A.y_in + rb0, ybytes, bar);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// barrier among the consumer warps only (the producer warp never joins it)
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(GPASS_CONSUMERS * 32) : "memory");
+}
+
+struct RowCtx {
+  float2* sx;     // staged input region (complex)
+  float* sy_re;   // accumulated output region, real plane
+  float* sy_im;   // accumulated output region, imaginary plane
+  int S, r0, c0, logK, Km, lane;
+};
+
+// Rows q0, q0 + NCW, ... of one J-uniform chunk, SL register slots of 32 taps per lane.
+// Lanes without a tap (and taps that fail the region check) point at their own dummy
+// cell SS + lane of the staged regions with weight 0, so the slot loops are branch-free.
+template <int MODE, typename WT, int SL>
+__device__ __forceinline__ void process_chunk(const GArgs& A, const Chunk& ch, const unsigned char* stage,
+                                              int q0, const RowCtx& C) {
+  using L = StageLayout<WT>;
+  const unsigned char* sw = stage + L::W_OFF;
+  const int32_t* sc = reinterpret_cast<const int32_t*>(stage + L::C_OFF);
+  const float2* syv = reinterpret_cast<const float2*>(stage + L::Y_OFF);
+  const int toff = (int)(ch.tap_begin & 3LL);
+  const int roff = (int)(ch.row_begin & 1LL);
+  const int nn = ch.nn;
+  const int lane = C.lane, S = C.S, logK = C.logK, Km = C.Km;
+  const int dummy = S * S + lane;
+  for (int q = q0; q < ch.nrows; q += GPASS_CONSUMERS) {
+    const int beg = toff + q * nn;
+    float2 wv[SL];
+    int idx[SL];
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+      const int t = lane + 32 * s;
+      const bool live = t < nn;
+      const int tt = live ? beg + t : beg;
+      const float2 w = w_at<WT>(sw, tt);
+      const int col = sc[tt];
+      const unsigned lr = (unsigned)(((col >> logK) - C.r0) & Km);
+      const unsigned lc = (unsigned)((col - C.c0) & Km);
+      const bool in = lr < (unsigned)S && lc < (unsigned)S;
+      if (live && !in) atomicOr(A.status, 1);
+      const bool use = live && in;
+      idx[s] = use ? (int)(lr * S + lc) : dummy;
+      wv[s] = use ? w : make_float2(0.f, 0.f);
+    }
+    float2 r = make_float2(0.f, 0.f);
+    if (MODE != G_GRID) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int s = 0; s < SL; ++s) {
+        const float2 xv = C.sx[idx[s]];
+        acc.x = fmaf(wv[s].x, xv.x, fmaf(-wv[s].y, xv.y, acc.x));
+        acc.y = fmaf(wv[s].x, xv.y, fmaf(wv[s].y, xv.x, acc.y));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (MODE == G_DEGRID) {
+        if (lane == 0) A.y_out[A.perm[ch.row_begin + q]] = acc;
+        continue;
+      }
+      r = acc;
+      if (A.y_in) r = csub(r, syv[roff + q]);
+    } else {
+      r = syv[roff + q];
+    }
+#pragma unroll
+    for (int s = 0; s < SL; ++s) {
+      if (lane + 32 * s < nn) {  // a predicated pair of atomics, no divergent branch
+        const float2 c = cmulc(wv[s], r);
+        atomicAdd(&C.sy_re[idx[s]], c.x);
+        atomicAdd(&C.sy_im[idx[s]], c.y);
+      }
+    }
+  }
+}
+
+
+// Warp-specialised CTA: warps 0..GPASS_CONSUMERS-1 consume chunks, the last
+// warp produces them.  full[s] completes when stage s has landed (TMA
+// transaction count); empty[s] completes when every consumer warp has released
+// stage s.  Consumer warps only meet at unit boundaries (tile restage/flush).
+template <int MODE, typename WT>
+__global__ void __launch_bounds__(GPASS_THREADS) gpass(GArgs A) {
+  using L = StageLayout<WT>;
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint64_t full[NSTAGE], empty[NSTAGE];
+  __shared__ volatile int s_abort;
+  const int S = A.S, SS = S * S, logK = A.logK, Km = A.K - 1;
+  const int region_bytes = (((SS + 32) * 8 + 127) & ~127);  // + one dummy cell per lane
+  // input region: interleaved complex; output region: separate real and imaginary planes
+  // (consecutive cells in consecutive banks, so the scatter atomics do not conflict)
+  float2* sx = reinterpret_cast<float2*>(sm);
+  float* sy_re = reinterpret_cast<float*>(MODE == G_FUSED ? sm + region_bytes : sm);
+  float* sy_im = sy_re + (SS + 32);
+  unsigned char* stages = sm + (MODE == G_FUSED ? 2 : 1) * region_bytes;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NCW = GPASS_CONSUMERS;
+  constexpr int CT = NCW * 32;
+
+  if (blockIdx.x >= A.n_units) return;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCW);
+    }
+    fence_barrier_init();
+    s_abort = 0;
+  }
+  __syncthreads();  // the only CTA-wide barrier: roles split below
+
+  if (warp == NCW) {
+    // ---------------- producer warp (lane 0 issues every copy)
+    if (lane != 0) return;
+    StreamPos pos{(long long)blockIdx.x, 0};
+    int st = 0;
+    uint32_t ph = 0;       // parity of the current use of stage st
+    long long j = 0;
+    bool more = true;
+    while (more) {
+      if (j >= NSTAGE && !mbar_wait(&empty[st], ph ^ 1u)) {
+        s_abort = 1;
+        break;
+      }
+      if (s_abort) break;
+      fence_proxy_async();
+      const Unit U = A.units[pos.u];
+      issue_chunk<MODE, WT>(A, A.chunks[U.chunk_begin + pos.c], stages + st * L::SIZE, &full[st]);
+      ++j;
+      if (++st == NSTAGE) {
+        st = 0;
+        ph ^= 1u;
+      }
+      more = advance(pos, A);
+    }
+    // every issued copy must land before the CTA's shared memory can be released
+    for (int d = 0; d < NSTAGE && d < j; ++d) {
+      if (--st < 0) {
+        st = NSTAGE - 1;
+        ph ^= 1u;
+      }
+      mbar_wait(&full[st], ph);
+    }
+    return;
+  }
+
+  // ---------------- consumer warps
+  const int ctid = threadIdx.x;  // 0..CT-1
+  int st = 0;
+  uint32_t ph = 0;
+  int rb = 0;  // rows of the stream before the current chunk, modulo NCW
   for (long long u = blockIdx.x; u < A.n_units; u += gridDim.x) {
     const Unit U = A.units[u];
     const int tr = U.tile / A.ntc, tc = U.tile - tr * A.ntc;
     const int r0 = tr * A.T, c0 = tc * A.T;
-    if (MODE != G_GRID) {
-      for (int c = threadIdx.x; c < SS; c += blockDim.x) {
+    if (MODE != G_GRID)
+      for (int c = ctid; c < SS; c += CT) {
         const int i = c / S, jj = c - i * S;
         sx[c] = A.gridA[((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km)];
       }
-    }
+    if (ctid < 32 && MODE != G_GRID) sx[SS + ctid] = make_float2(0.f, 0.f);
     if (MODE != G_DEGRID)
-      for (int c = threadIdx.x; c < SS; c += blockDim.x) sy[c] = make_float2(0.f, 0.f);
-    __syncthreads();
+      for (int c = ctid; c < SS; c += CT) {
+        sy_re[c] = 0.f;
+        sy_im[c] = 0.f;
+      }
+    consumers_sync();
+    const RowCtx C{sx, sy_re, sy_im, S, r0, c0, logK, Km, lane};
 
-    for (int q0 = warp * RPW; q0 < U.nrows; q0 += nw * RPW) {
-      float2 wv[RPW][SLOTS];
-      int idx[RPW][SLOTS];
-      long long m[RPW];
-#pragma unroll
-      for (int q = 0; q < RPW; ++q) {
-        const bool valid = q0 + q < U.nrows;
-        m[q] = U.row_begin + q0 + q;
-        const int64_t beg = valid ? A.rowptr[m[q]] : 0;
-        const int cnt = valid ? (int)(A.rowptr[m[q] + 1] - beg) : 0;
-#pragma unroll
-        for (int s = 0; s < SLOTS; ++s) {
-          const int t = lane + 32 * s;
-          if (t < cnt) {
-            wv[q][s] = load_w<WT>(A.w, beg + t);
-            const int col = __ldcs(A.cols + beg + t);
-            const int lr = ((col >> logK) - r0) & Km;
-            const int lc = ((col & Km) - c0) & Km;
-            if (lr < S && lc < S) {
-              idx[q][s] = lr * S + lc;
-            } else {
-              atomicOr(A.status, 1);
-              idx[q][s] = -1;
-            }
-          } else {
-            wv[q][s] = make_float2(0.f, 0.f);
-            idx[q][s] = -1;
-          }
+    for (int ci = 0; ci < U.nchunks; ++ci) {
+      bool ok = false;
+      if (!s_abort) {
+        ok = mbar_wait(&full[st], ph);
+        if (!ok) s_abort = 1;
+      }
+      const Chunk ch = A.chunks[U.chunk_begin + ci];
+      // a warp works on the stage only when all of its lanes saw the copy land
+      if (__all_sync(0xffffffffu, ok)) {
+        const unsigned char* stage = stages + st * L::SIZE;
+        // rows are dealt to warps round robin over the whole stream, so no warp idles per chunk
+        const int q0 = warp >= rb ? warp - rb : warp - rb + NCW;
+        if (ch.nn * ch.nrows != ch.ntaps || (ch.tap_begin & 3LL) + ch.ntaps > CHUNK_TAPS + 8) {
+          if (lane == 0) atomicOr(A.status, 4);  // inconsistent work list: skip the chunk
+        } else if (ch.nn <= 64) {
+          process_chunk<MODE, WT, 2>(A, ch, stage, q0, C);
+        } else if (ch.nn <= 96) {
+          process_chunk<MODE, WT, 3>(A, ch, stage, q0, C);
+        } else if (ch.nn <= 160) {
+          process_chunk<MODE, WT, 5>(A, ch, stage, q0, C);
+        } else {
+          process_chunk<MODE, WT, 8>(A, ch, stage, q0, C);
         }
       }
-#pragma unroll
-      for (int q = 0; q < RPW; ++q) {
-        if (q0 + q >= U.nrows) break;
-        float2 r = make_float2(0.f, 0.f);
-        if (MODE != G_GRID) {
-          float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int s = 0; s < SLOTS; ++s)
-            if (idx[q][s] >= 0) {
-              const float2 xv = sx[idx[q][s]];
-              acc.x = fmaf(wv[q][s].x, xv.x, fmaf(-wv[q][s].y, xv.y, acc.x));
-              acc.y = fmaf(wv[q][s].x, xv.y, fmaf(wv[q][s].y, xv.x, acc.y));
-            }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-          }
-          if (MODE == G_DEGRID) {
-            if (lane == 0) A.y_out[A.perm[m[q]]] = acc;
-            continue;
-          }
-          r = acc;
-          if (A.y_in) r = csub(r, A.y_in[m[q]]);
-        } else {
-          r = A.y_in[m[q]];
-        }
-#pragma unroll
-        for (int s = 0; s < SLOTS; ++s)
-          if (idx[q][s] >= 0) {
-            const float2 c = cmulc(wv[q][s], r);
-            atomicAdd(&sy[idx[q][s]].x, c.x);
-            atomicAdd(&sy[idx[q][s]].y, c.y);
-          }
+      rb = (rb + ch.nrows) % NCW;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);  // this warp is done with the stage
+      if (++st == NSTAGE) {
+        st = 0;
+        ph ^= 1u;
       }
     }
-    __syncthreads();
-    if (MODE != G_DEGRID) {
-      for (int c = threadIdx.x; c < SS; c += blockDim.x) {
-        const float2 v = sy[c];
+    consumers_sync();  // all scatters of this unit are in sy
+    if (MODE != G_DEGRID && !s_abort) {
+      for (int c = ctid; c < SS; c += CT) {
+        const float2 v = make_float2(sy_re[c], sy_im[c]);
         if (v.x != 0.f || v.y != 0.f) {
           const int i = c / S, jj = c - i * S;
           atomicAdd(&A.gridB[((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km)], v);
         }
       }
-      __syncthreads();
     }
+    consumers_sync();  // the region may be restaged for the next unit
   }
+  if (s_abort && ctid == 0) atomicOr(A.status, 2);
 }
 
 __global__ void permute_kernel(const float2* __restrict__ y, const int32_t* __restrict__ perm,
@@ -157,46 +379,30 @@ __global__ void permute_kernel(const float2* __restrict__ y, const int32_t* __re
     out[i] = y[perm[i]];
 }
 
-template <int MODE, typename WT, int SLOTS, int RPW>
+template <int MODE, typename WT>
 int launch_gpass(pnp_plan* p, const GArgs& A) {
-  const int smem = (MODE == G_FUSED ? 2 : 1) * A.S * A.S * (int)sizeof(float2);
+  const int region_bytes = (((A.S * A.S + 32) * 8 + 127) & ~127);
+  const int smem = (MODE == G_FUSED ? 2 : 1) * region_bytes + NSTAGE * StageLayout<WT>::SIZE;
   static int attr = 0;
+  static int per_sm = 0;
   if (smem > attr) {
-    PNP_CUDA(cudaFuncSetAttribute(gpass<MODE, WT, SLOTS, RPW>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PNP_CUDA(cudaFuncSetAttribute(gpass<MODE, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr = smem;
+    PNP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gpass<MODE, WT>, GPASS_THREADS, smem));
   }
-  int per_sm = 0;
-  PNP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gpass<MODE, WT, SLOTS, RPW>, 256, smem));
   if (per_sm < 1) return fail(PNP_ERR_UNSUPPORTED, "gridding tile does not fit in shared memory");
   long long grid = (long long)per_sm * p->num_sms;
   if (grid > A.n_units) grid = A.n_units;
   if (grid < 1) return PNP_OK;
-  gpass<MODE, WT, SLOTS, RPW><<<(unsigned)grid, 256, smem, p->stream>>>(A);
+  gpass<MODE, WT><<<(unsigned)grid, GPASS_THREADS, smem, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
 
-template <int MODE, typename WT>
-int dispatch_slots(pnp_plan* p, const GArgs& A) {
-  const int rpw = p->rpw;
-  switch (p->slots) {
-    case 2:
-      return rpw == 1 ? launch_gpass<MODE, WT, 2, 1>(p, A)
-           : rpw == 4 ? launch_gpass<MODE, WT, 2, 4>(p, A) : launch_gpass<MODE, WT, 2, 2>(p, A);
-    case 4:
-      return rpw == 1 ? launch_gpass<MODE, WT, 4, 1>(p, A)
-           : rpw == 4 ? launch_gpass<MODE, WT, 4, 4>(p, A) : launch_gpass<MODE, WT, 4, 2>(p, A);
-    default:
-      return rpw == 1 ? launch_gpass<MODE, WT, 8, 1>(p, A)
-           : rpw == 4 ? launch_gpass<MODE, WT, 8, 4>(p, A) : launch_gpass<MODE, WT, 8, 2>(p, A);
-  }
-}
-
 template <int MODE>
 int dispatch_wt(pnp_plan* p, const GArgs& A) {
-  return p->wdtype == PNP_W_BF16C ? dispatch_slots<MODE, __nv_bfloat162>(p, A)
-                                  : dispatch_slots<MODE, float2>(p, A);
+  return p->wdtype == PNP_W_BF16C ? launch_gpass<MODE, __nv_bfloat162>(p, A)
+                                  : launch_gpass<MODE, float2>(p, A);
 }
 
 }  // namespace
@@ -224,6 +430,7 @@ int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out) {
   A.ntc = p->ntc;
   A.units = p->d_units;
   A.n_units = p->n_units;
+  A.chunks = p->d_chunks;
   A.rowptr = p->d_rowptr;
   A.w = p->d_w;
   A.cols = p->d_cols;

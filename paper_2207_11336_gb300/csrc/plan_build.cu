@@ -183,31 +183,58 @@ int dev_alloc(pnp_plan* p, T** ptr, size_t count) {
 
 int build_units(pnp_plan* p) {
   std::vector<Unit> units;
+  std::vector<Chunk> chunks;
   const int64_t M = p->M;
+  auto nnz_of = [&](int64_t i) { return p->h_rowptr[i + 1] - p->h_rowptr[i]; };
   int64_t i = 0;
   while (i < M) {
     const int32_t key = p->h_key[i];
-    int64_t j = i, acc = 0;
-    while (j < M && p->h_key[j] == key && (acc == 0 || acc + (p->h_rowptr[j + 1] - p->h_rowptr[j]) <= p->unit_nnz)) {
-      acc += p->h_rowptr[j + 1] - p->h_rowptr[j];
-      ++j;
-    }
     Unit u;
-    u.row_begin = i;
-    u.nrows = (int)(j - i);
+    u.chunk_begin = (long long)chunks.size();
     u.tile = key / p->nblocks;
+    int64_t unit_taps = 0;
+    while (i < M && p->h_key[i] == key && (unit_taps == 0 || unit_taps + nnz_of(i) <= p->unit_nnz)) {
+      Chunk ch;
+      ch.row_begin = i;
+      ch.tap_begin = p->h_rowptr[i];
+      int nr = 0;
+      int64_t nt = 0;
+      const int64_t row_nnz = nnz_of(i);  // every row of a chunk has the same support
+      while (i < M && p->h_key[i] == key && nnz_of(i) == row_nnz && nr < CHUNK_ROWS &&
+             nt + nnz_of(i) <= CHUNK_TAPS && (unit_taps + nt == 0 || unit_taps + nt + nnz_of(i) <= p->unit_nnz)) {
+        nt += nnz_of(i);
+        ++nr;
+        ++i;
+      }
+      if (nr == 0) return fail(PNP_ERR_INVALID_ARG, "internal: a row does not fit one gridding chunk");
+      ch.nrows = nr;
+      ch.ntaps = (int)nt;
+      ch.nn = (int)row_nnz;
+      ch.pad = 0;
+      chunks.push_back(ch);
+      unit_taps += nt;
+    }
+    u.nchunks = (int)((long long)chunks.size() - u.chunk_begin);
     units.push_back(u);
-    i = j;
   }
   if (p->d_units) {
     cudaFree(p->d_units);
     p->device_bytes -= p->n_units * (int64_t)sizeof(Unit);
     p->d_units = nullptr;
   }
+  if (p->d_chunks) {
+    cudaFree(p->d_chunks);
+    p->device_bytes -= p->n_chunks * (int64_t)sizeof(Chunk);
+    p->d_chunks = nullptr;
+  }
   p->n_units = (int64_t)units.size();
+  p->n_chunks = (int64_t)chunks.size();
   if (int rc = dev_alloc(p, &p->d_units, units.size())) return rc;
-  if (!units.empty())
+  if (int rc = dev_alloc(p, &p->d_chunks, chunks.size())) return rc;
+  if (!units.empty()) {
     PNP_CUDA(cudaMemcpy(p->d_units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice));
+    PNP_CUDA(cudaMemcpy(p->d_chunks, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
+  }
   return PNP_OK;
 }
 
@@ -257,18 +284,28 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
   p->Jmax = Jmax;
   p->slots = Jmax * Jmax <= 64 ? 2 : (Jmax * Jmax <= 128 ? 4 : 8);
 
-  // stable counting sort by key
+  // stable LSD counting sort: first by support J, then by (tile, block) key, so that rows of
+  // one tile come out grouped by J (each gridding chunk then holds rows of a single J)
+  std::vector<int32_t> by_j(M);
+  {
+    std::vector<int64_t> cj(18, 0);
+    for (int64_t m = 0; m < M; ++m) cj[geom[m].J + 1]++;
+    for (int j = 0; j < 17; ++j) cj[j + 1] += cj[j];
+    for (int64_t m = 0; m < M; ++m) by_j[cj[geom[m].J]++] = (int32_t)m;
+  }
   const int64_t nkeys = (int64_t)ntc * ntc * p->nblocks;
   std::vector<int64_t> cnt(nkeys + 1, 0);
   for (int64_t m = 0; m < M; ++m) cnt[key[m] + 1]++;
   for (int64_t k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
   p->h_perm.assign(M, 0);
   p->h_inv.assign(M, 0);
-  for (int64_t m = 0; m < M; ++m) {
+  for (int64_t i = 0; i < M; ++i) {
+    const int32_t m = by_j[i];
     const int64_t pos = cnt[key[m]]++;
-    p->h_perm[pos] = (int32_t)m;
+    p->h_perm[pos] = m;
     p->h_inv[m] = (int32_t)pos;
   }
+  std::vector<int32_t>().swap(by_j);
   std::vector<RowGeom> sgeom(M);
   p->h_key.assign(M, 0);
   p->h_rowptr.assign(M + 1, 0);
@@ -329,18 +366,21 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
   const size_t wbytes = p->wdtype == PNP_W_BF16C ? 4 : 8;
   {
     void* w = nullptr;
-    cudaError_t e = cudaMalloc(&w, std::max<size_t>(1, p->nnz * wbytes));
+    cudaError_t e = cudaMalloc(&w, (p->nnz + TAP_PAD) * wbytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(PNP_ERR_OOM, "cudaMalloc of G weights (" + std::to_string(p->nnz * wbytes) + " bytes) failed");
     }
     p->d_w = w;
-    p->device_bytes += (int64_t)(p->nnz * wbytes);
+    p->device_bytes += (int64_t)((p->nnz + TAP_PAD) * wbytes);
+    PNP_CUDA(cudaMemset(w, 0, (p->nnz + TAP_PAD) * wbytes));
   }
-  if (int rc = dev_alloc(p, &p->d_cols, (size_t)p->nnz)) return rc;
-  if (int rc = dev_alloc(p, &p->d_rowptr, (size_t)M + 1)) return rc;
+  if (int rc = dev_alloc(p, &p->d_cols, (size_t)p->nnz + TAP_PAD)) return rc;
+  if (int rc = dev_alloc(p, &p->d_rowptr, (size_t)M + 1 + ROW_PAD)) return rc;
   if (int rc = dev_alloc(p, &p->d_perm, (size_t)M)) return rc;
-  if (int rc = dev_alloc(p, &p->d_ysorted, (size_t)M)) return rc;
+  if (int rc = dev_alloc(p, &p->d_ysorted, (size_t)M + ROW_PAD)) return rc;
+  PNP_CUDA(cudaMemset(p->d_cols, 0, ((size_t)p->nnz + TAP_PAD) * sizeof(int32_t)));
+  PNP_CUDA(cudaMemset(p->d_ysorted, 0, ((size_t)M + ROW_PAD) * sizeof(float2)));
   if (int rc = dev_alloc(p, &p->d_acc, 8)) return rc;
   if (int rc = dev_alloc(p, &p->d_status, 4)) return rc;
   for (int i = 0; i < 3; ++i)
@@ -350,7 +390,11 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
   PNP_CUDA(cudaMemset(p->d_gridB, 0, KK * sizeof(float2)));
   PNP_CUDA(cudaMemset(p->d_acc, 0, 8 * sizeof(double)));
   PNP_CUDA(cudaMemset(p->d_status, 0, 4 * sizeof(int)));
-  PNP_CUDA(cudaMemcpy(p->d_rowptr, p->h_rowptr.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  {
+    std::vector<int64_t> rp(p->h_rowptr);
+    rp.resize(M + 1 + ROW_PAD, p->nnz);  // padding entries repeat nnz
+    PNP_CUDA(cudaMemcpy(p->d_rowptr, rp.data(), rp.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  }
   if (M) PNP_CUDA(cudaMemcpy(p->d_perm, p->h_perm.data(), M * sizeof(int32_t), cudaMemcpyHostToDevice));
 
   // build G rows on the GPU

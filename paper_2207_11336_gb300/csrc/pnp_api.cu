@@ -67,6 +67,7 @@ void free_plan(pnp_plan* p) {
   cudaFree(p->d_perm);
   cudaFree(p->d_ysorted);
   cudaFree(p->d_units);
+  cudaFree(p->d_chunks);
   cudaFree(p->d_acc);
   cudaFree(p->d_status);
   if (p->cstream) cudaStreamDestroy(p->cstream);
@@ -191,7 +192,7 @@ int pnp_plan_create(pnp_plan** plan, int n, int K, int64_t M, const double* uvw_
   p->wdtype = weight_dtype;
   p->nblocks = nblocks;
   p->stream = reinterpret_cast<cudaStream_t>(stream);
-  p->tile = K >= 128 ? 48 : 16;
+  p->tile = K >= 128 ? 32 : 16;
   if (cudaGetDevice(&p->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
     cudaGetLastError();
