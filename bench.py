@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="C3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--kernel-case", choices=["gridding"], default=None,
+    ap.add_argument("--kernel-case", choices=["gridding", "cnn"], default=None,
                     help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
     return ap.parse_args()
 
@@ -366,8 +366,45 @@ def run_kernel_case(args):
     return 0
 
 
+def cnn_case(args):
+    """The faceted CNN denoiser on the 4096^2 workload: 16 uneven facets, 32 px halo."""
+    import torch
+    import paper_2207_11336_gb300 as pnp
+    import synth
+    prob = synth.make_problem("C3", M=16, with_sky=True)
+    n = prob["n"]
+    params = synth.cnn_init(synth.rng_for("train"), 64, 8, 0.1)
+    den = pnp.CnnDenoiser(params, n, facet_rows=prob["facet_rows"], facet_cols=prob["facet_cols"], halo=32)
+    z = torch.from_numpy(prob["x_true"].astype(np.float32)).cuda()
+    out = torch.empty_like(z)
+    for _ in range(max(args.warmup, 1)):
+        den.denoise(z, out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(max(args.steps, 1)):
+        den.denoise(z, out)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+    h = 32
+    edges_r = np.concatenate([[0], np.cumsum(prob["facet_rows"])])
+    edges_c = np.concatenate([[0], np.cumsum(prob["facet_cols"])])
+    px = 0
+    for a0, a1 in zip(edges_r[:-1], edges_r[1:]):
+        for b0, b1 in zip(edges_c[:-1], edges_c[1:]):
+            px += (min(n, a1 + h) - max(0, a0 - h)) * (min(n, b1 + h) - max(0, b0 - h))
+    flop = px * (2 * 9 * 64 + 6 * 2 * 9 * 64 * 64 + 2 * 9 * 64)
+    print(json.dumps({"case": "cnn 4096^2, 16 facets, halo 32", "ms": ms, "pixels_with_halo": int(px),
+                      "TFLOP_per_call": flop / 1e12, "TFLOPs": flop / ms / 1e9,
+                      "status": den.device_status()}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.kernel_case == "cnn":
+        return cnn_case(args)
     if args.kernel_case:
         return run_kernel_case(args)
     if args.impl == "reference":

@@ -189,6 +189,11 @@ int pnp_den_create_cnn(pnp_den** den, const float* weights_host,
 
 void pnp_den_destroy(pnp_den* den);
 
+/* Device status flags of a denoiser's kernels (synchronous; 0 for the Haar
+ * denoiser).  Bit 1: a bounded pipeline wait in the tensor-core convolution
+ * gave up (the output of that call is invalid). */
+int pnp_den_device_status(pnp_den* den, int* flags_host);
+
 /* x_out = D(x_in) for an n x n image (dev float32; may not alias). */
 int denoise(pnp_den* den, const float* x_in, float* x_out, int n);
 

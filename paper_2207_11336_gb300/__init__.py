@@ -29,7 +29,7 @@ EXPORTED = [
     "pnp_plan_export_rows", "phi_forward", "phi_adjoint", "grad_step", "op_norm",
     "pnp_den_create_haar", "pnp_den_create_cnn", "pnp_den_destroy", "denoise", "pnp_fb_run",
     "pnp_last_error", "pnp_kernel_launch_count", "pnp_plan_set_timing", "pnp_plan_read_timing",
-    "pnp_plan_device_status", "pnp_haar_denoise_noalloc",
+    "pnp_plan_device_status", "pnp_haar_denoise_noalloc", "pnp_den_device_status",
 ]
 
 
@@ -87,13 +87,15 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_plan_set_timing.argtypes = [vp, i32]
     L.pnp_plan_device_status.argtypes = [vp, C.POINTER(i32)]
     L.pnp_haar_denoise_noalloc.argtypes = [vp, vp, vp, i32, dbl, vp, vp]
+    L.pnp_den_device_status.argtypes = [vp, C.POINTER(i32)]
     L.pnp_plan_read_timing.argtypes = [vp, vp, vp]
     L.pnp_last_error.restype = C.c_char_p
     L.pnp_kernel_launch_count.restype = i64
     for name in ("pnp_plan_create", "pnp_plan_get_info", "pnp_plan_set_unit_nnz", "pnp_plan_export_rows",
                  "phi_forward", "phi_adjoint", "grad_step", "op_norm", "pnp_den_create_haar",
                  "pnp_den_create_cnn", "denoise", "pnp_fb_run", "pnp_plan_set_timing",
-                 "pnp_plan_read_timing", "pnp_plan_device_status", "pnp_haar_denoise_noalloc"):
+                 "pnp_plan_read_timing", "pnp_plan_device_status", "pnp_haar_denoise_noalloc",
+                 "pnp_den_device_status"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -294,6 +296,12 @@ class _Denoiser:
         o = torch.empty_like(x) if out is None else out
         _check(lib().denoise(self._h, _ptr(x), _ptr(o), int(n)))
         return o
+
+    def device_status(self) -> int:
+        """Device status flags of this denoiser's kernels (0 when every check passed)."""
+        f = C.c_int()
+        _check(lib().pnp_den_device_status(self._h, C.byref(f)))
+        return f.value
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -1,12 +1,632 @@
-// Learned residual CNN denoiser (App. C) -- not built yet in this revision.
+// Learned residual CNN denoiser (App. C) applied on facets with a halo (App. D).
+//
+// Network: 8 layers of 3x3 'same' convolutions, 1 -> 64 -> ... -> 64 -> 1,
+// bias on every layer, ReLU after all but the last; D(z) = max(0, z - N(z)).
+// Weights and hidden activations are BF16, accumulation FP32; the input z, the
+// last layer's output and the residual stay FP32.
+//
+// Facets.  Each facet core is extended by the halo (clipped at the image
+// border) and denoised on its own with zero padding at its edges; the cores are
+// stitched back.  All facets live in one activation "canvas" [F][Hc][Wc][64]
+// (NHWC, BF16); cells outside a facet are kept at zero so they act as padding.
+//
+// Kernels per application:
+//   cnn_first   z (FP32 image) -> canvas: layer 1 (1 -> 64) on CUDA cores;
+//   conv64_tc   canvas -> canvas: one 64 -> 64 layer as an implicit GEMM on the
+//               5th-generation tensor cores (tcgen05.mma, FP32 accumulators in
+//               tensor memory), one 128-pixel row segment per tile;
+//   cnn_last    canvas -> image: layer 8 (64 -> 1) on CUDA cores, fused with
+//               D(z) = max(0, z - N(z)) on the facet cores and the FP64 norms.
+//
+// conv64_tc layout.  A tile is 128 output pixels (x0 .. x0+127 of row y of one
+// facet).  Its inputs -- rows y-1..y+1, pixels x0-1 .. x0+128, 64 channels --
+// are staged in shared memory channel-block-major: [dy][kb][pixel][8 ch], so
+// for every (kb) the 130 pixels are 16 bytes apart.  That is the canonical
+// no-swizzle K-major operand layout (core matrix = 8 pixels x 8 channels,
+// 128 contiguous bytes), and tap (dy, dx) of the 3x3 stencil is the same
+// matrix with its start address moved by dx pixels (16 B).  The 9 taps x 4
+// K-steps (16 channels each) accumulate M=128 x N=64 into tensor memory.
+// Weights of all taps sit in shared memory as [tap][kb][co][8 ci] (K-major B).
+// Warp roles: warps 0-3 drain tensor memory (bias, ReLU, BF16, store),
+// warp 4 allocates tensor memory and issues the MMAs (one elected lane),
+// warps 5-8 stage input tiles with cp.async.  Two input buffers and two
+// accumulators are pipelined with mbarriers; every wait is bounded.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "common.cuh"
 
 namespace pnp {
-int cnn_create(pnp_den*, const float*, const int32_t*, int, const int32_t*, int, int, int) {
-  return fail(PNP_ERR_UNSUPPORTED, "CNN denoiser not available in this build");
+namespace {
+
+constexpr int CH = 64;
+constexpr int TILE_PX = 128;
+constexpr int STAGE_PX = TILE_PX + 2;                   // x0-1 .. x0+128
+constexpr int KB_BYTES = STAGE_PX * 16;                 // one 8-channel block of a staged row (2080)
+constexpr int ROW_BYTES = 8 * KB_BYTES;                 // 8 channel blocks (16640)
+constexpr int A_BYTES = 3 * ROW_BYTES;                  // 3 staged rows (49920)
+constexpr int B_TAP_BYTES = CH * CH * 2;                // 8192
+constexpr int B_BYTES = 9 * B_TAP_BYTES;                // 73728
+constexpr int CONV_THREADS = 9 * 32;
+constexpr int LOADER_THREADS = 128;
+constexpr uint32_t CNN_WAIT_LIMIT = 1u << 26;
+
+struct CnnState {
+  int n = 0, F = 0, Hc = 0, Wc = 0, halo = 0;
+  std::vector<int> fr0, fr1, fc0, fc1;   // facet cores [r0, r1) x [c0, c1)
+  std::vector<int> R0, C0, Hf, Wf;       // extended facets
+  int4* d_facets = nullptr;              // per facet: (R0, C0, Hf, Wf)
+  int4* d_cores = nullptr;               // per facet: (r0, r1, c0, c1)
+  int4* d_tiles = nullptr;               // per tile: (f, y, x0, Wf)
+  int n_tiles = 0;
+  __nv_bfloat16* d_canvas[2] = {nullptr, nullptr};
+  float* d_w1 = nullptr;                 // [64][9]  (BF16-rounded values)
+  float* d_b = nullptr;                  // [8][64] biases (layer 8 uses entry 0)
+  __nv_bfloat16* d_wmid = nullptr;       // 6 x [9][8][64][8] packed for the tensor cores
+  float* d_w8 = nullptr;                 // [9][64] (BF16-rounded values)
+  int* d_status = nullptr;
+  float b8 = 0.f;                        // last layer's bias (host copy)
+};
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t c) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(c) : "memory");
 }
-void cnn_destroy(pnp_den*) {}
-int cnn_denoise(pnp_den*, cudaStream_t, const float*, float*, int, double*, const float*) {
-  return fail(PNP_ERR_UNSUPPORTED, "CNN denoiser not available in this build");
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
+  for (uint32_t it = 0; it < CNN_WAIT_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(dst)), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem desc] * B[smem desc]^T, BF16 inputs, FP32 accumulate
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrive on an mbarrier once all previously issued MMAs of this thread completed
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: no swizzle, K-major canonical layout.
+//   lbo: byte distance between core matrices adjacent along K
+//   sbo: byte distance between 8-row groups along M (or N)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for this architecture
+  return d;                // base offset 0, relative LBO mode, no swizzle
+}
+
+// Instruction descriptor, kind::f16: FP32 D, BF16 A and B, both K-major, M = 128, N = 64.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CH >> 3) << 17) |
+                           ((uint32_t)(TILE_PX >> 4) << 24);
+
+struct ConvArgs {
+  const __nv_bfloat16* in;
+  __nv_bfloat16* out;
+  const __nv_bfloat16* w;  // packed [9][8][64][8]
+  const float* bias;       // [64]
+  const int4* tiles;
+  int n_tiles, Hc, Wc;
+  int* status;
+};
+
+__global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* sa[2] = {sm, sm + A_BYTES};
+  unsigned char* sb = sm + 2 * A_BYTES;
+  __shared__ uint64_t a_full[2], a_empty[2], t_full[2], t_empty[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ float s_bias[CH];
+  __shared__ volatile int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // weights (already in the operand layout) and biases into shared memory
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(A.w);
+    uint4* dst = reinterpret_cast<uint4*>(sb);
+    for (int i = threadIdx.x; i < B_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x < CH) s_bias[threadIdx.x] = A.bias[threadIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) {
+      bar_init(&a_full[b], LOADER_THREADS);
+      bar_init(&a_empty[b], 1);
+      bar_init(&t_full[b], 1);
+      bar_init(&t_empty[b], 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == 4) {
+    tmem_alloc(&s_tmem, 128);  // two 128 x 64 FP32 accumulators
+    tmem_relinquish();
+  }
+  fence_async_smem();  // the weights written above are read by the tensor cores (async proxy)
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const int stride = gridDim.x;
+
+  if (warp >= 5) {
+    // ---------------- loaders: rows y-1..y+1, pixels x0-1..x0+128 -> [dy][kb][px][8]
+    const int t = threadIdx.x - 5 * 32;
+    int i = 0;
+    for (int tile = blockIdx.x; tile < A.n_tiles; tile += stride, ++i) {
+      const int b = i & 1;
+      if (i >= 2 && !bar_wait(&a_empty[b], ((i >> 1) - 1) & 1)) s_abort = 1;
+      if (s_abort) break;
+      const int4 T = A.tiles[tile];
+      const size_t fbase = (size_t)T.x * A.Hc;
+      for (int c = t; c < 3 * STAGE_PX * 8; c += LOADER_THREADS) {
+        const int kb = c & 7, px = (c >> 3) % STAGE_PX, dy = (c >> 3) / STAGE_PX;
+        const int yy = T.y - 1 + dy, xx = T.z - 1 + px;
+        const bool ok = yy >= 0 && yy < A.Hc && xx >= 0 && xx < A.Wc;
+        const __nv_bfloat16* src =
+            A.in + (((fbase + (ok ? yy : 0)) * A.Wc + (ok ? xx : 0)) * CH + kb * 8);
+        cp_async16(sa[b] + dy * ROW_BYTES + kb * KB_BYTES + px * 16, src, ok);
+      }
+      cp_async_wait_all();
+      fence_async_smem();
+      bar_arrive(&a_full[b]);
+    }
+  } else if (warp == 4) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int i = 0, last = -1;
+      for (int tile = blockIdx.x; tile < A.n_tiles; tile += stride, ++i) {
+        const int b = i & 1, d = i & 1;
+        if (!bar_wait(&a_full[b], (i >> 1) & 1)) s_abort = 1;
+        if (i >= 2 && !bar_wait(&t_empty[d], ((i >> 1) - 1) & 1)) s_abort = 1;
+        if (s_abort) break;
+        tc_fence_after();
+        const uint32_t abase = su32(sa[b]), bbase = su32(sb);
+        const uint32_t dt = tmem + (uint32_t)(d * CH);
+        int first = 1;
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = smem_desc(abase + dy * ROW_BYTES + 2 * kk * KB_BYTES + dx * 16, KB_BYTES, 128);
+            const uint64_t bd = smem_desc(bbase + tap * B_TAP_BYTES + 2 * kk * 1024, 1024, 128);
+            mma_bf16(dt, ad, bd, IDESC, first ? 0u : 1u);
+            first = 0;
+          }
+        }
+        mma_commit(&a_empty[b]);  // input buffer b may be refilled once these MMAs are done
+        mma_commit(&t_full[d]);   // accumulator d is ready for the epilogue
+        last = i;
+      }
+      // the tensor memory is freed below only after the last MMAs have completed
+      if (last >= 0) bar_wait(&t_full[last & 1], (last >> 1) & 1);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: tensor memory -> bias + ReLU -> BF16 -> canvas
+    const int m = threadIdx.x;  // TMEM lane = output pixel of the tile
+    int i = 0;
+    for (int tile = blockIdx.x; tile < A.n_tiles; tile += stride, ++i) {
+      const int d = i & 1;
+      const bool ok = !s_abort && bar_wait(&t_full[d], (i >> 1) & 1);
+      if (!ok) s_abort = 1;
+      if (!__all_sync(0xffffffffu, ok)) break;
+      tc_fence_after();
+      uint32_t r0[32], r1[32];
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * CH);
+      tmem_ld32(ta, r0);
+      tmem_ld32(ta + 32, r1);
+      tmem_wait_ld();
+      tc_fence_before();
+      bar_arrive(&t_empty[d]);
+      const int4 T = A.tiles[tile];
+      const int x = T.z + m;
+      if (x < A.Wc) {
+        const bool live = x < T.w;  // outside the facet the canvas stays zero
+        uint4 pk[8];
+        uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+#pragma unroll
+        for (int c = 0; c < 32; c += 2) {
+          const float v0 = live ? fmaxf(0.f, __uint_as_float(r0[c]) + s_bias[c]) : 0.f;
+          const float v1 = live ? fmaxf(0.f, __uint_as_float(r0[c + 1]) + s_bias[c + 1]) : 0.f;
+          __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+          pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+        }
+#pragma unroll
+        for (int c = 0; c < 32; c += 2) {
+          const float v0 = live ? fmaxf(0.f, __uint_as_float(r1[c]) + s_bias[32 + c]) : 0.f;
+          const float v1 = live ? fmaxf(0.f, __uint_as_float(r1[c + 1]) + s_bias[32 + c + 1]) : 0.f;
+          __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+          pw[16 + c / 2] = *reinterpret_cast<uint32_t*>(&h);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(A.out + (((size_t)T.x * A.Hc + T.y) * A.Wc + x) * CH);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dst[q] = pk[q];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 4) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 128);
+  }
+  if (threadIdx.x == 0 && s_abort) atomicOr(A.status, 2);
+}
+
+// ------------------------------------------------------------ layer 1 (1 -> 64)
+struct FirstArgs {
+  const float* z;
+  int n;
+  const int4* facets;
+  int F, Hc, Wc;
+  const float* w1;  // [64][9]
+  const float* b1;  // [64]
+  __nv_bfloat16* out;
+};
+
+__global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
+  __shared__ float sw[CH * 9], sbias[CH];
+  for (int i = threadIdx.x; i < CH * 9; i += blockDim.x) sw[i] = A.w1[i];
+  if (threadIdx.x < CH) sbias[threadIdx.x] = A.b1[threadIdx.x];
+  __syncthreads();
+  const int64_t total = (int64_t)A.F * A.Hc * A.Wc;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(p % A.Wc);
+    const int y = (int)((p / A.Wc) % A.Hc);
+    const int f = (int)(p / ((int64_t)A.Wc * A.Hc));
+    const int4 fc = A.facets[f];  // R0, C0, Hf, Wf
+    uint4 pk[8];
+    uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+    if (y < fc.z && x < fc.w) {
+      float zin[9];
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+        zin[t] = (yy >= 0 && yy < fc.z && xx >= 0 && xx < fc.w) ? A.z[(size_t)(fc.x + yy) * A.n + fc.y + xx] : 0.f;
+      }
+#pragma unroll 4
+      for (int c = 0; c < CH; c += 2) {
+        float a0 = sbias[c], a1 = sbias[c + 1];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+          a0 = fmaf(sw[c * 9 + t], zin[t], a0);
+          a1 = fmaf(sw[(c + 1) * 9 + t], zin[t], a1);
+        }
+        __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(a0, 0.f), fmaxf(a1, 0.f));
+        pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) pw[q] = 0u;
+    }
+    uint4* dst = reinterpret_cast<uint4*>(A.out + p * CH);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) dst[q] = pk[q];
+  }
+}
+
+// ------------------------------------------------------------ layer 8 (64 -> 1) + residual
+struct LastArgs {
+  const __nv_bfloat16* in;
+  const float* z;
+  const float* x_prev;
+  float* out;
+  int n;
+  const int4* facets;
+  const int4* cores;
+  int F, Hc, Wc;
+  const float* w8;  // [9][64]
+  float b8;
+  double* acc;
+};
+
+__global__ void __launch_bounds__(256) cnn_last(LastArgs A) {
+  __shared__ float sw[9 * CH];
+  __shared__ double red[2 * 256];
+  for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = A.w8[i];
+  __syncthreads();
+  double s0 = 0.0, s1 = 0.0;
+  // every image pixel belongs to exactly one facet core
+  const int64_t total = (int64_t)A.n * A.n;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
+    const int iy = (int)(p / A.n), ix = (int)(p % A.n);
+    int f = 0;
+    for (; f < A.F - 1; ++f) {
+      const int4 c = A.cores[f];
+      if (iy >= c.x && iy < c.y && ix >= c.z && ix < c.w) break;
+    }
+    const int4 fc = A.facets[f];
+    const int y = iy - fc.x, x = ix - fc.y;
+    float nz = A.b8;
+    for (int t = 0; t < 9; ++t) {
+      const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+      if (yy < 0 || yy >= fc.z || xx < 0 || xx >= fc.w) continue;
+      const uint4* src = reinterpret_cast<const uint4*>(A.in + (((size_t)f * A.Hc + yy) * A.Wc + xx) * CH);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint4 v = src[q];
+        const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[e]));
+          nz = fmaf(sw[t * CH + q * 8 + 2 * e], h.x, nz);
+          nz = fmaf(sw[t * CH + q * 8 + 2 * e + 1], h.y, nz);
+        }
+      }
+    }
+    const float zv = A.z[p];
+    const float o = fmaxf(0.f, zv - nz);
+    A.out[p] = o;
+    s1 += (double)o * o;
+    if (!isfinite(zv)) s1 = __longlong_as_double(0x7ff8000000000000LL);
+    if (A.x_prev) {
+      const double dd = (double)o - A.x_prev[p];
+      s0 += dd * dd;
+    }
+  }
+  if (A.acc) {
+    red[2 * threadIdx.x] = s0;
+    red[2 * threadIdx.x + 1] = s1;
+    __syncthreads();
+    for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+      if (threadIdx.x < s) {
+        red[2 * threadIdx.x] += red[2 * (threadIdx.x + s)];
+        red[2 * threadIdx.x + 1] += red[2 * (threadIdx.x + s) + 1];
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      atomicAdd(&A.acc[0], red[0]);
+      atomicAdd(&A.acc[1], red[1]);
+    }
+  }
+}
+
+// ------------------------------------------------------------ host helpers
+uint16_t to_bf16_bits(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  const uint32_t r = u + 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(r >> 16);
+}
+float bf16_round(float f) {
+  const uint32_t u = (uint32_t)to_bf16_bits(f) << 16;
+  float o;
+  std::memcpy(&o, &u, 4);
+  return o;
+}
+
+int sms_of_device() {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+}  // namespace
+
+int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int32_t* fc, int nfc, int halo,
+               int n) {
+  CnnState* S = new CnnState();
+  d->impl = S;
+  S->n = n;
+  S->halo = halo;
+  std::vector<int> rows = fr && nfr > 0 ? std::vector<int>(fr, fr + nfr) : std::vector<int>{n};
+  std::vector<int> cols = fc && nfc > 0 ? std::vector<int>(fc, fc + nfc) : std::vector<int>{n};
+  int sr = 0, sc = 0;
+  for (int v : rows) {
+    if (v <= 0) return fail(PNP_ERR_INVALID_ARG, "facet sizes must be positive");
+    sr += v;
+  }
+  for (int v : cols) {
+    if (v <= 0) return fail(PNP_ERR_INVALID_ARG, "facet sizes must be positive");
+    sc += v;
+  }
+  if (sr != n || sc != n) return fail(PNP_ERR_INVALID_ARG, "facet sizes must sum to n along each axis");
+  int r = 0;
+  for (int a : rows) {
+    int c = 0;
+    for (int b : cols) {
+      S->fr0.push_back(r);
+      S->fr1.push_back(r + a);
+      S->fc0.push_back(c);
+      S->fc1.push_back(c + b);
+      const int R0 = std::max(0, r - halo), R1 = std::min(n, r + a + halo);
+      const int C0 = std::max(0, c - halo), C1 = std::min(n, c + b + halo);
+      S->R0.push_back(R0);
+      S->C0.push_back(C0);
+      S->Hf.push_back(R1 - R0);
+      S->Wf.push_back(C1 - C0);
+      c += b;
+    }
+    r += a;
+  }
+  S->F = (int)S->R0.size();
+  S->Hc = *std::max_element(S->Hf.begin(), S->Hf.end());
+  const int wmax = *std::max_element(S->Wf.begin(), S->Wf.end());
+  S->Wc = (wmax + TILE_PX - 1) / TILE_PX * TILE_PX;
+
+  std::vector<int4> facets(S->F), cores(S->F), tiles;
+  for (int f = 0; f < S->F; ++f) {
+    facets[f] = make_int4(S->R0[f], S->C0[f], S->Hf[f], S->Wf[f]);
+    cores[f] = make_int4(S->fr0[f], S->fr1[f], S->fc0[f], S->fc1[f]);
+    for (int y = 0; y < S->Hf[f]; ++y)
+      for (int x0 = 0; x0 < S->Wf[f]; x0 += TILE_PX) tiles.push_back(make_int4(f, y, x0, S->Wf[f]));
+  }
+  S->n_tiles = (int)tiles.size();
+
+  // weights: layer shapes 64x1, 6 x 64x64, 1x64, each W[co][ci][3][3] then b[co]
+  std::vector<float> w1(CH * 9), w8(9 * CH), bias(8 * CH, 0.f);
+  std::vector<uint16_t> wmid((size_t)6 * 9 * CH * CH);
+  size_t off = 0;
+  for (int co = 0; co < CH; ++co)
+    for (int t = 0; t < 9; ++t) w1[co * 9 + t] = bf16_round(W[off + co * 9 + t]);
+  off += CH * 9;
+  for (int co = 0; co < CH; ++co) bias[co] = W[off + co];
+  off += CH;
+  for (int l = 0; l < 6; ++l) {
+    for (int co = 0; co < CH; ++co)
+      for (int ci = 0; ci < CH; ++ci)
+        for (int t = 0; t < 9; ++t) {
+          const size_t dst = (size_t)l * 9 * CH * CH + (size_t)t * CH * CH + (size_t)(ci / 8) * CH * 8 +
+                             (size_t)co * 8 + (ci % 8);
+          wmid[dst] = to_bf16_bits(W[off + ((size_t)co * CH + ci) * 9 + t]);
+        }
+    off += (size_t)CH * CH * 9;
+    for (int co = 0; co < CH; ++co) bias[(l + 1) * CH + co] = W[off + co];
+    off += CH;
+  }
+  for (int ci = 0; ci < CH; ++ci)
+    for (int t = 0; t < 9; ++t) w8[t * CH + ci] = bf16_round(W[off + ci * 9 + t]);
+  off += CH * 9;
+  bias[7 * CH] = W[off];
+  S->b8 = W[off];
+
+  const size_t canvas = (size_t)S->F * S->Hc * S->Wc * CH;
+  auto al = [&](void** p, size_t bytes) -> int {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(PNP_ERR_OOM, "CNN buffer allocation failed (" + std::to_string(bytes) + " bytes)");
+    }
+    return PNP_OK;
+  };
+  for (int i = 0; i < 2; ++i) {
+    if (int rc = al((void**)&S->d_canvas[i], canvas * 2)) return rc;
+    PNP_CUDA(cudaMemset(S->d_canvas[i], 0, canvas * 2));
+  }
+  if (int rc = al((void**)&S->d_facets, S->F * sizeof(int4))) return rc;
+  if (int rc = al((void**)&S->d_cores, S->F * sizeof(int4))) return rc;
+  if (int rc = al((void**)&S->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(int4))) return rc;
+  if (int rc = al((void**)&S->d_w1, w1.size() * 4)) return rc;
+  if (int rc = al((void**)&S->d_w8, w8.size() * 4)) return rc;
+  if (int rc = al((void**)&S->d_b, bias.size() * 4)) return rc;
+  if (int rc = al((void**)&S->d_wmid, wmid.size() * 2)) return rc;
+  if (int rc = al((void**)&S->d_status, 4 * sizeof(int))) return rc;
+  PNP_CUDA(cudaMemcpy(S->d_facets, facets.data(), S->F * sizeof(int4), cudaMemcpyHostToDevice));
+  PNP_CUDA(cudaMemcpy(S->d_cores, cores.data(), S->F * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!tiles.empty())
+    PNP_CUDA(cudaMemcpy(S->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  PNP_CUDA(cudaMemcpy(S->d_w1, w1.data(), w1.size() * 4, cudaMemcpyHostToDevice));
+  PNP_CUDA(cudaMemcpy(S->d_w8, w8.data(), w8.size() * 4, cudaMemcpyHostToDevice));
+  PNP_CUDA(cudaMemcpy(S->d_b, bias.data(), bias.size() * 4, cudaMemcpyHostToDevice));
+  PNP_CUDA(cudaMemcpy(S->d_wmid, wmid.data(), wmid.size() * 2, cudaMemcpyHostToDevice));
+  PNP_CUDA(cudaMemset(S->d_status, 0, 4 * sizeof(int)));
+  return PNP_OK;
+}
+
+void cnn_destroy(pnp_den* d) {
+  CnnState* S = static_cast<CnnState*>(d->impl);
+  if (!S) return;
+  for (auto p : S->d_canvas) cudaFree(p);
+  cudaFree(S->d_facets);
+  cudaFree(S->d_cores);
+  cudaFree(S->d_tiles);
+  cudaFree(S->d_w1);
+  cudaFree(S->d_w8);
+  cudaFree(S->d_b);
+  cudaFree(S->d_wmid);
+  cudaFree(S->d_status);
+  delete S;
+  d->impl = nullptr;
+}
+
+int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc, const float* x_prev) {
+  CnnState* S = static_cast<CnnState*>(d->impl);
+  if (!S) return fail(PNP_ERR_INVALID_ARG, "CNN denoiser not initialised");
+  if (n != S->n) return fail(PNP_ERR_INVALID_ARG, "image side differs from the one the CNN denoiser was built for");
+  const int sms = sms_of_device();
+  {
+    FirstArgs F{z, n, S->d_facets, S->F, S->Hc, S->Wc, S->d_w1, S->d_b, S->d_canvas[0]};
+    const int64_t total = (int64_t)S->F * S->Hc * S->Wc;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8L * sms);
+    cnn_first<<<blocks, 256, 0, s>>>(F);
+    PNP_CHECK_LAUNCH();
+  }
+  static bool attr = false;
+  const int smem = 2 * A_BYTES + B_BYTES;
+  if (!attr) {
+    PNP_CUDA(cudaFuncSetAttribute(conv64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  int cur = 0;
+  for (int l = 0; l < 6; ++l) {
+    ConvArgs C{S->d_canvas[cur], S->d_canvas[1 - cur], S->d_wmid + (size_t)l * 9 * CH * CH,
+               S->d_b + (l + 1) * CH, S->d_tiles, S->n_tiles, S->Hc, S->Wc, S->d_status};
+    const int grid = std::max(1, std::min(S->n_tiles, sms));
+    conv64_tc<<<grid, CONV_THREADS, smem, s>>>(C);
+    PNP_CHECK_LAUNCH();
+    cur = 1 - cur;
+  }
+  {
+    LastArgs L{S->d_canvas[cur], z, x_prev, out, n, S->d_facets, S->d_cores, S->F, S->Hc, S->Wc, S->d_w8, S->b8, acc};
+    const int blocks = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 8L * sms);
+    cnn_last<<<blocks, 256, 0, s>>>(L);
+    PNP_CHECK_LAUNCH();
+  }
+  return PNP_OK;
+}
+
+int cnn_status(pnp_den* d, int* flags) {
+  CnnState* S = static_cast<CnnState*>(d->impl);
+  if (!S) return fail(PNP_ERR_INVALID_ARG, "CNN denoiser not initialised");
+  PNP_CUDA(cudaMemcpy(flags, S->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  return PNP_OK;
+}
+
 }  // namespace pnp

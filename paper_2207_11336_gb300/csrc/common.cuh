@@ -162,6 +162,7 @@ int zero_acc(cudaStream_t s, double* acc, int count);
 int cnn_create(pnp_den* d, const float* weights_host, const int32_t* fr, int nfr,
                const int32_t* fc, int nfc, int halo, int n);
 void cnn_destroy(pnp_den* d);
+int cnn_status(pnp_den* d, int* flags);
 int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc,
                 const float* x_prev);
 }  // namespace pnp

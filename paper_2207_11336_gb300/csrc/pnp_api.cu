@@ -377,6 +377,14 @@ void pnp_den_destroy(pnp_den* den) {
   delete den;
 }
 
+int pnp_den_device_status(pnp_den* d, int* flags) {
+  if (!d || !flags) return fail(PNP_ERR_INVALID_ARG, "NULL argument");
+  *flags = 0;
+  if (d->kind != PNP_DEN_CNN) return PNP_OK;
+  PNP_CUDA(cudaStreamSynchronize(d->stream));
+  return cnn_status(d, flags);
+}
+
 int denoise(pnp_den* d, const float* x_in, float* x_out, int n) {
   if (!d || !x_in || !x_out || n < 2 || (n & 1)) return fail(PNP_ERR_INVALID_ARG, "bad argument");
   if (x_in == x_out) return fail(PNP_ERR_INVALID_ARG, "x_in and x_out must not alias");

@@ -1,0 +1,92 @@
+"""GPU parity of the learned residual CNN denoiser (App. C, faceting App. D) vs the FP64 oracle.
+
+The oracle runs with the same BF16 rounding points as the GPU (weights of every
+layer and hidden activations), accumulating in FP64; the GPU accumulates in
+FP32 on the tensor cores.  The accumulations differ in rounding, so a small
+fraction of hidden activations round to the neighbouring BF16 value; through
+seven rounded layers this stays below one BF16 unit roundoff, 2^-8, relative
+(L2) on N(z) and on D(z).
+"""
+import numpy as np
+import pytest
+
+BF16_U = 2.0 ** -8
+
+import synth
+from oracle import cnn as ocnn
+
+from gpu_common import pnp, rel_l2, require_gpu, to_dev_f32, to_host, torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _params(seed=0, scale=1.0):
+    return synth.cnn_init(np.random.default_rng(seed), channels=64, depth=8, last_scale=scale)
+
+
+def _sky(n, seed):
+    return synth.training_image(n, np.random.default_rng(seed)) + 0.01 * np.random.default_rng(seed + 1).standard_normal((n, n))
+
+
+@pytest.mark.parametrize("n", [64, 150])
+def test_cnn_whole_image_parity(n):
+    params = _params(1)
+    z = _sky(n, 2)
+    den = pnp.CnnDenoiser(params, n, halo=0)
+    out = to_host(den.denoise(to_dev_f32(z)))
+    assert den.device_status() == 0
+    zf = z.astype(np.float32).astype(np.float64)
+    nz_ref = ocnn.network(params, zf, bf16=True)
+    # compare the network output N(z) where the positivity did not clip
+    ref = np.maximum(zf - nz_ref, 0)
+    assert rel_l2(out, ref) <= BF16_U
+    live = ref > 1e-3
+    assert rel_l2((zf - out)[live], nz_ref[live]) <= BF16_U
+
+
+def test_cnn_faceted_parity_uneven_facets():
+    n = 200
+    params = _params(3)
+    z = _sky(n, 4)
+    fr, fc = [60, 75, 65], [90, 110]
+    den = pnp.CnnDenoiser(params, n, facet_rows=fr, facet_cols=fc, halo=32)
+    out = to_host(den.denoise(to_dev_f32(z)))
+    zf = z.astype(np.float32).astype(np.float64)
+    ref = ocnn.denoise_faceted(params, zf, fr, fc, 32, bf16=True)
+    assert rel_l2(out, ref) <= BF16_U
+    # faceting with a halo covering the receptive field reproduces the whole-image result
+    whole = to_host(pnp.CnnDenoiser(params, n, halo=0).denoise(to_dev_f32(z)))
+    assert rel_l2(out, whole) <= 1e-3
+
+
+def test_cnn_small_halo_differs():
+    n = 128
+    params = _params(5)
+    z = _sky(n, 6)
+    a = to_host(pnp.CnnDenoiser(params, n, facet_rows=[64, 64], facet_cols=[64, 64], halo=2).denoise(to_dev_f32(z)))
+    b = to_host(pnp.CnnDenoiser(params, n, halo=0).denoise(to_dev_f32(z)))
+    assert rel_l2(a, b) > 1e-4
+
+
+def test_pnp_fb_with_cnn_matches_oracle():
+    from oracle import fb as ofb
+    from oracle import nufft as onu
+    n, K, M = 64, 128, 20000
+    prob = synth.make_problem("C0", M=M, n=n, K=K)
+    ora = onu.Operator(n, K, prob["omega"])
+    y = ora.forward(prob["x_true"]) + 0.5 * prob["noise"]
+    L, _, _ = ofb.power_iteration(ora, synth.rng_for("power").standard_normal((n, n)), 500, 1e-10)
+    params = _params(7, scale=0.05)
+    iters = 4
+    x_ref, _ = ofb.pnp_fb(ora, y, ofb.step_size(L), lambda z: ocnn.denoise(params, z, bf16=True), iters)
+    plan = pnp.Plan(n, K, prob["omega"])
+    den = pnp.CnnDenoiser(params, n, facet_rows=[32, 32], facet_cols=[32, 32], halo=16)
+    yd = torch.from_numpy(y.astype(np.complex64)).cuda()
+    x, st = plan.fb_run(den, yd, L=L, max_iter=iters, check_every=2)
+    assert st.iters == iters
+    assert rel_l2(to_host(x), x_ref) <= 5e-3
