@@ -197,6 +197,37 @@ int pnp_den_device_status(pnp_den* den, int* flags_host);
 /* x_out = D(x_in) for an n x n image (dev float32; may not alias). */
 int denoise(pnp_den* den, const float* x_in, float* x_out, int n);
 
+/* ------------------------------------------------------- CNN training */
+
+/* Trainer of the residual CNN denoiser (App. C): minimises the l1 loss
+ * mean |D(u + sigma n) - u|, D(z) = z - N(z), with Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8); the firm non-expansiveness term of Eq. training_loss is not
+ * included.  Weights are FP32 master copies rounded to BF16 for every
+ * convolution; activations and back-propagated gradients are BF16.
+ *  weights_host  FP32 parameters in the layout of pnp_den_create_cnn
+ *                (pnp_cnn_num_params() values)
+ *  batch, size   images per step and their side (size >= 8)
+ *  lr            Adam step size */
+typedef struct pnp_cnn_trainer pnp_cnn_trainer;
+int pnp_cnn_trainer_create(pnp_cnn_trainer** trainer, const float* weights_host, int batch, int size,
+                           double lr, void* stream);
+void pnp_cnn_trainer_destroy(pnp_cnn_trainer* trainer);
+
+/* One step: z = u + sigma n, forward, loss, backward; with update != 0 also an
+ * Adam update (which clears the gradients).
+ *  u, noise   dev, batch x size x size float32: clean images and N(0,1) draws
+ *  loss_host  host, receives the mean l1 loss (synchronous), or NULL */
+int pnp_cnn_train_step(pnp_cnn_trainer* trainer, const float* u, const float* noise, double sigma, int update,
+                       double* loss_host);
+
+/* Copy the FP32 weights and/or accumulated gradients to the host (synchronous;
+ * NULL skips one); clear_grads != 0 zeroes the gradients afterwards.  Returns
+ * PNP_ERR_TIMEOUT if a bounded device wait gave up during training. */
+int pnp_cnn_trainer_read(pnp_cnn_trainer* trainer, float* weights_host, float* grads_host, int clear_grads);
+
+/* Number of FP32 parameters of the CNN (weights and biases of the 8 layers). */
+int64_t pnp_cnn_num_params(void);
+
 /* ------------------------------------------------------------ PnP-FB loop */
 
 /* Run Eq. fb: x^{k+1} = D(x^k - gamma Re{Phi^H (Phi x^k - y)}), starting from

@@ -102,23 +102,37 @@ def denoise(params, z, bf16: bool = False, positivity: bool = True) -> np.ndarra
     return np.maximum(d, 0.0) if positivity else d
 
 
-def l1_loss_and_grads(params, u, noise, sigma: float):
-    """Loss mean|z - N(z) - u|, z = u + sigma n, and its gradients w.r.t. every (W, b)."""
+def l1_loss_and_grads(params, u, noise, sigma: float, bf16: bool = False, with_abs: bool = False):
+    """Loss mean|z - N(z) - u|, z = u + sigma n, and its gradients w.r.t. every (W, b).
+
+    With ``bf16=True`` the forward pass is the BF16 one of ``network`` and the
+    back-propagated pre-activation gradients of the hidden layers are rounded to
+    BF16 after the ReLU mask (weights BF16 too); sums stay FP64.
+    With ``with_abs=True`` also returns, per layer, the same sums taken over the
+    absolute values of their terms (the scale of a floating-point error bound).
+    """
     z = u + sigma * noise
-    nz, acts = network(params, z, keep=True)
+    nz, acts = network(params, z, bf16=bf16, keep=True)
     resid = z - nz - u
     count = resid.size
     loss = float(np.abs(resid).sum() / count)
     g = -np.sign(resid) / count                    # dL/dN(z)
     grads = [None] * len(params)
+    abs_grads = [None] * len(params)
     for i in range(len(params) - 1, -1, -1):
         Wt, _ = params[i]
         if i < len(params) - 1:
             g = g * (acts[i + 1] > 0)              # ReLU
-        dx, dW, db = conv_backward(acts[i], Wt, g)
+            if bf16:
+                g = to_bf16(g)
+        Wq = to_bf16(Wt) if bf16 else Wt
+        dx, dW, db = conv_backward(acts[i], Wq, g)
         grads[i] = (dW, db)
+        if with_abs:
+            _, aW, ab = conv_backward(np.abs(acts[i]), np.abs(Wq), np.abs(g))
+            abs_grads[i] = (aW, ab)
         g = dx
-    return loss, grads
+    return (loss, grads, abs_grads) if with_abs else (loss, grads)
 
 
 def adam_step(params, grads, state, lr: float = 1e-4, b1: float = 0.9, b2: float = 0.999,

@@ -30,6 +30,8 @@ EXPORTED = [
     "pnp_den_create_haar", "pnp_den_create_cnn", "pnp_den_destroy", "denoise", "pnp_fb_run",
     "pnp_last_error", "pnp_kernel_launch_count", "pnp_plan_set_timing", "pnp_plan_read_timing",
     "pnp_plan_device_status", "pnp_haar_denoise_noalloc", "pnp_den_device_status",
+    "pnp_cnn_trainer_create", "pnp_cnn_trainer_destroy", "pnp_cnn_train_step", "pnp_cnn_trainer_read",
+    "pnp_cnn_num_params",
 ]
 
 
@@ -88,6 +90,12 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_plan_device_status.argtypes = [vp, C.POINTER(i32)]
     L.pnp_haar_denoise_noalloc.argtypes = [vp, vp, vp, i32, dbl, vp, vp]
     L.pnp_den_device_status.argtypes = [vp, C.POINTER(i32)]
+    L.pnp_cnn_trainer_create.argtypes = [C.POINTER(vp), vp, i32, i32, dbl, vp]
+    L.pnp_cnn_trainer_destroy.argtypes = [vp]
+    L.pnp_cnn_trainer_destroy.restype = None
+    L.pnp_cnn_train_step.argtypes = [vp, vp, vp, dbl, i32, C.POINTER(dbl)]
+    L.pnp_cnn_trainer_read.argtypes = [vp, vp, vp, i32]
+    L.pnp_cnn_num_params.restype = i64
     L.pnp_plan_read_timing.argtypes = [vp, vp, vp]
     L.pnp_last_error.restype = C.c_char_p
     L.pnp_kernel_launch_count.restype = i64
@@ -95,7 +103,8 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
                  "phi_forward", "phi_adjoint", "grad_step", "op_norm", "pnp_den_create_haar",
                  "pnp_den_create_cnn", "denoise", "pnp_fb_run", "pnp_plan_set_timing",
                  "pnp_plan_read_timing", "pnp_plan_device_status", "pnp_haar_denoise_noalloc",
-                 "pnp_den_device_status"):
+                 "pnp_den_device_status", "pnp_cnn_trainer_create", "pnp_cnn_train_step",
+                 "pnp_cnn_trainer_read"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -329,6 +338,63 @@ def pack_cnn_weights(params) -> np.ndarray:
     """Flatten [(W (co, ci, 3, 3), b (co,)), ...] into the float32 layout of pnp_den_create_cnn."""
     return np.ascontiguousarray(np.concatenate([np.concatenate([np.ravel(W), np.ravel(b)])
                                                 for W, b in params]).astype(np.float32))
+
+
+def unpack_cnn_weights(flat, channels=64, depth=8):
+    """Inverse of ``pack_cnn_weights``: flat float array -> [(W, b), ...] (float64)."""
+    flat = np.asarray(flat, dtype=np.float64)
+    shapes = [(channels, 1)] + [(channels, channels)] * (depth - 2) + [(1, channels)]
+    out, off = [], 0
+    for co, ci in shapes:
+        W = flat[off:off + co * ci * 9].reshape(co, ci, 3, 3)
+        off += co * ci * 9
+        out.append((W.copy(), flat[off:off + co].copy()))
+        off += co
+    return out
+
+
+class CnnTrainer:
+    """Adam training of the residual CNN on batches of size x size images (App. C)."""
+
+    def __init__(self, params, batch: int, size: int, lr: float = 1e-4, stream=None):
+        lib()
+        self.batch, self.size = int(batch), int(size)
+        self._h = C.c_void_p()
+        w = pack_cnn_weights(params)
+        if w.size != lib().pnp_cnn_num_params():
+            raise ValueError("parameters do not match the 8-layer 64-channel network")
+        _check(lib().pnp_cnn_trainer_create(C.byref(self._h), w.ctypes.data, self.batch, self.size,
+                                            float(lr), _stream_handle(stream)))
+
+    def step(self, u, noise, sigma: float, update: bool = True, want_loss: bool = False):
+        """One training step on device batches u, noise (batch x size x size float32)."""
+        shape = (self.batch, self.size, self.size)
+        _cuda_f32(u, shape, "u")
+        _cuda_f32(noise, shape, "noise")
+        loss = C.c_double(0.0)
+        _check(lib().pnp_cnn_train_step(self._h, _ptr(u), _ptr(noise), float(sigma), 1 if update else 0,
+                                        C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def read(self, weights=True, grads=False, clear_grads=False):
+        """(params or None, flat gradients or None) from the device."""
+        n = int(lib().pnp_cnn_num_params())
+        w = np.zeros(n, dtype=np.float32) if weights else None
+        g = np.zeros(n, dtype=np.float32) if grads else None
+        _check(lib().pnp_cnn_trainer_read(self._h, None if w is None else w.ctypes.data,
+                                          None if g is None else g.ctypes.data, 1 if clear_grads else 0))
+        return (unpack_cnn_weights(w) if w is not None else None), g
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().pnp_cnn_trainer_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class CnnDenoiser(_Denoiser):

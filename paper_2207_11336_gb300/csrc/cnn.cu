@@ -18,14 +18,15 @@
 //   cnn_last    canvas -> image: layer 8 (64 -> 1) on CUDA cores, fused with
 //               D(z) = max(0, z - N(z)) on the facet cores and the FP64 norms.
 //
-// conv64_tc layout.  A tile is 128 output pixels (x0 .. x0+127 of row y of one
-// facet).  Its inputs -- rows y-1..y+1, pixels x0-1 .. x0+128, 64 channels --
-// are staged in shared memory channel-block-major: [dy][kb][pixel][8 ch], so
+// conv64_tc layout.  A tile is 2 x 128 output pixels (x0 .. x0+127 of rows y,
+// y+1 of one facet).  Its inputs -- rows y-1..y+2, pixels x0-1 .. x0+128, 64
+// channels -- are staged in shared memory channel-block-major: [row][kb][pixel][8 ch], so
 // for every (kb) the 130 pixels are 16 bytes apart.  That is the canonical
 // no-swizzle K-major operand layout (core matrix = 8 pixels x 8 channels,
 // 128 contiguous bytes), and tap (dy, dx) of the 3x3 stencil is the same
-// matrix with its start address moved by dx pixels (16 B).  The 9 taps x 4
-// K-steps (16 channels each) accumulate M=128 x N=64 into tensor memory.
+// matrix with its start address moved by dx pixels (16 B).  Per output row the
+// 9 taps x 4 K-steps (16 channels each) accumulate M=128 x N=64 into tensor
+// memory; the two output rows share the staged rows.
 // Weights of all taps sit in shared memory as [tap][kb][co][8 ci] (K-major B).
 // Warp roles: warps 0-3 drain tensor memory (bias, ReLU, BF16, store),
 // warp 4 allocates tensor memory and issues the MMAs (one elected lane),
@@ -46,7 +47,10 @@ constexpr int TILE_PX = 128;
 constexpr int STAGE_PX = TILE_PX + 2;                   // x0-1 .. x0+128
 constexpr int KB_BYTES = STAGE_PX * 16;                 // one 8-channel block of a staged row (2080)
 constexpr int ROW_BYTES = 8 * KB_BYTES;                 // 8 channel blocks (16640)
-constexpr int A_BYTES = 3 * ROW_BYTES;                  // 3 staged rows (49920)
+constexpr int OUT_ROWS = 2;                             // output rows per tile
+constexpr int STAGE_ROWS = OUT_ROWS + 2;                // staged input rows per tile
+constexpr int A_BYTES = STAGE_ROWS * ROW_BYTES;         // 66560
+constexpr int TMEM_COLS = 2 * OUT_ROWS * CH;            // two tiles in flight x OUT_ROWS accumulators
 constexpr int B_TAP_BYTES = CH * CH * 2;                // 8192
 constexpr int B_BYTES = 9 * B_TAP_BYTES;                // 73728
 constexpr int CONV_THREADS = 9 * 32;
@@ -59,7 +63,7 @@ struct CnnState {
   std::vector<int> R0, C0, Hf, Wf;       // extended facets
   int4* d_facets = nullptr;              // per facet: (R0, C0, Hf, Wf)
   int4* d_cores = nullptr;               // per facet: (r0, r1, c0, c1)
-  int4* d_tiles = nullptr;               // per tile: (f, y, x0, Wf)
+  int4* d_tiles = nullptr;               // per tile: (f, y0, x0, Hf << 16 | Wf)
   int n_tiles = 0;
   __nv_bfloat16* d_canvas[2] = {nullptr, nullptr};
   float* d_w1 = nullptr;                 // [64][9]  (BF16-rounded values)
@@ -159,10 +163,12 @@ struct ConvArgs {
   const __nv_bfloat16* in;
   __nv_bfloat16* out;
   const __nv_bfloat16* w;  // packed [9][8][64][8]
-  const float* bias;       // [64]
+  const float* bias;       // [64] (forward mode)
   const int4* tiles;
   int n_tiles, Hc, Wc;
   int* status;
+  int mode;                    // 0: forward, out = ReLU(acc + bias); 1: backward data, out = acc * [mask > 0]
+  const __nv_bfloat16* mask;   // backward data: activations whose ReLU mask gates the output (same canvas layout)
 };
 
 __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
@@ -180,7 +186,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
     const uint4* src = reinterpret_cast<const uint4*>(A.w);
     uint4* dst = reinterpret_cast<uint4*>(sb);
     for (int i = threadIdx.x; i < B_BYTES / 16; i += blockDim.x) dst[i] = src[i];
-    if (threadIdx.x < CH) s_bias[threadIdx.x] = A.bias[threadIdx.x];
+    if (threadIdx.x < CH) s_bias[threadIdx.x] = A.bias ? A.bias[threadIdx.x] : 0.f;  // no bias in backward mode
   }
   if (threadIdx.x == 0) {
     for (int b = 0; b < 2; ++b) {
@@ -193,7 +199,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
     s_abort = 0;
   }
   if (warp == 4) {
-    tmem_alloc(&s_tmem, 128);  // two 128 x 64 FP32 accumulators
+    tmem_alloc(&s_tmem, TMEM_COLS);  // 2 tiles in flight x OUT_ROWS accumulators of 128 x 64 FP32
     tmem_relinquish();
   }
   fence_async_smem();  // the weights written above are read by the tensor cores (async proxy)
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
       if (s_abort) break;
       const int4 T = A.tiles[tile];
       const size_t fbase = (size_t)T.x * A.Hc;
-      for (int c = t; c < 3 * STAGE_PX * 8; c += LOADER_THREADS) {
+      for (int c = t; c < STAGE_ROWS * STAGE_PX * 8; c += LOADER_THREADS) {
         const int kb = c & 7, px = (c >> 3) % STAGE_PX, dy = (c >> 3) / STAGE_PX;
         const int yy = T.y - 1 + dy, xx = T.z - 1 + px;
         const bool ok = yy >= 0 && yy < A.Hc && xx >= 0 && xx < A.Wc;
@@ -236,17 +242,21 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
         if (s_abort) break;
         tc_fence_after();
         const uint32_t abase = su32(sa[b]), bbase = su32(sb);
-        const uint32_t dt = tmem + (uint32_t)(d * CH);
-        int first = 1;
 #pragma unroll 1
-        for (int tap = 0; tap < 9; ++tap) {
-          const int dy = tap / 3, dx = tap % 3;
+        for (int r = 0; r < OUT_ROWS; ++r) {
+          const uint32_t dt = tmem + (uint32_t)((d * OUT_ROWS + r) * CH);
+          int first = 1;
+#pragma unroll 1
+          for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const uint64_t ad = smem_desc(abase + dy * ROW_BYTES + 2 * kk * KB_BYTES + dx * 16, KB_BYTES, 128);
-            const uint64_t bd = smem_desc(bbase + tap * B_TAP_BYTES + 2 * kk * 1024, 1024, 128);
-            mma_bf16(dt, ad, bd, IDESC, first ? 0u : 1u);
-            first = 0;
+            for (int kk = 0; kk < 4; ++kk) {
+              const uint64_t ad =
+                  smem_desc(abase + (r + dy) * ROW_BYTES + 2 * kk * KB_BYTES + dx * 16, KB_BYTES, 128);
+              const uint64_t bd = smem_desc(bbase + tap * B_TAP_BYTES + 2 * kk * 1024, 1024, 128);
+              mma_bf16(dt, ad, bd, IDESC, first ? 0u : 1u);
+              first = 0;
+            }
           }
         }
         mma_commit(&a_empty[b]);  // input buffer b may be refilled once these MMAs are done
@@ -267,34 +277,56 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
       if (!ok) s_abort = 1;
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
-      uint32_t r0[32], r1[32];
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(d * CH);
-      tmem_ld32(ta, r0);
-      tmem_ld32(ta + 32, r1);
-      tmem_wait_ld();
-      tc_fence_before();
-      bar_arrive(&t_empty[d]);
       const int4 T = A.tiles[tile];
-      const int x = T.z + m;
-      if (x < A.Wc) {
-        const bool live = x < T.w;  // outside the facet the canvas stays zero
+      for (int orow = 0; orow < OUT_ROWS; ++orow) {
+        uint32_t r0[32], r1[32];
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((d * OUT_ROWS + orow) * CH);
+        tmem_ld32(ta, r0);
+        tmem_ld32(ta + 32, r1);
+        tmem_wait_ld();
+        if (orow == OUT_ROWS - 1) {
+          tc_fence_before();
+          bar_arrive(&t_empty[d]);  // both accumulators of this tile are in registers now
+        }
+        const int y = T.y + orow;
+        const int x = T.z + m;
+        if (y >= A.Hc || x >= A.Wc) continue;
+        const bool live = x < (T.w & 0xFFFF) && y < (T.w >> 16);  // outside the facet the canvas stays zero
+        const size_t pix = ((size_t)T.x * A.Hc + y) * A.Wc + x;
         uint4 pk[8];
         uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+        if (A.mode == 0) {
 #pragma unroll
-        for (int c = 0; c < 32; c += 2) {
-          const float v0 = live ? fmaxf(0.f, __uint_as_float(r0[c]) + s_bias[c]) : 0.f;
-          const float v1 = live ? fmaxf(0.f, __uint_as_float(r0[c + 1]) + s_bias[c + 1]) : 0.f;
-          __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-          pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
-        }
+          for (int c = 0; c < 32; c += 2) {
+            const float v0 = live ? fmaxf(0.f, __uint_as_float(r0[c]) + s_bias[c]) : 0.f;
+            const float v1 = live ? fmaxf(0.f, __uint_as_float(r0[c + 1]) + s_bias[c + 1]) : 0.f;
+            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+          }
 #pragma unroll
-        for (int c = 0; c < 32; c += 2) {
-          const float v0 = live ? fmaxf(0.f, __uint_as_float(r1[c]) + s_bias[32 + c]) : 0.f;
-          const float v1 = live ? fmaxf(0.f, __uint_as_float(r1[c + 1]) + s_bias[32 + c + 1]) : 0.f;
-          __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-          pw[16 + c / 2] = *reinterpret_cast<uint32_t*>(&h);
+          for (int c = 0; c < 32; c += 2) {
+            const float v0 = live ? fmaxf(0.f, __uint_as_float(r1[c]) + s_bias[32 + c]) : 0.f;
+            const float v1 = live ? fmaxf(0.f, __uint_as_float(r1[c + 1]) + s_bias[32 + c + 1]) : 0.f;
+            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            pw[16 + c / 2] = *reinterpret_cast<uint32_t*>(&h);
+          }
+        } else {
+          uint4 mk[8];
+          const uint4* msrc = reinterpret_cast<const uint4*>(A.mask + pix * CH);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) mk[q] = msrc[q];
+          const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(mk);
+#pragma unroll
+          for (int c = 0; c < 64; c += 2) {
+            const float a0 = __uint_as_float(c < 32 ? r0[c] : r1[c - 32]);
+            const float a1 = __uint_as_float(c + 1 < 32 ? r0[c + 1] : r1[c + 1 - 32]);
+            const float v0 = (live && __bfloat162float(mh[c]) > 0.f) ? a0 : 0.f;
+            const float v1 = (live && __bfloat162float(mh[c + 1]) > 0.f) ? a1 : 0.f;
+            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+          }
         }
-        uint4* dst = reinterpret_cast<uint4*>(A.out + (((size_t)T.x * A.Hc + T.y) * A.Wc + x) * CH);
+        uint4* dst = reinterpret_cast<uint4*>(A.out + pix * CH);
 #pragma unroll
         for (int q = 0; q < 8; ++q) dst[q] = pk[q];
       }
@@ -304,7 +336,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
   __syncthreads();
   if (warp == 4) {
     tc_fence_after();
-    tmem_dealloc(tmem, 128);
+    tmem_dealloc(tmem, TMEM_COLS);
   }
   if (threadIdx.x == 0 && s_abort) atomicOr(A.status, 2);
 }
@@ -313,6 +345,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
 struct FirstArgs {
   const float* z;
   int n;
+  int64_t zplane;  // elements between the z planes of consecutive facets (0: one shared image)
   const int4* facets;
   int F, Hc, Wc;
   const float* w1;  // [64][9]
@@ -331,14 +364,17 @@ __global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
     const int y = (int)((p / A.Wc) % A.Hc);
     const int f = (int)(p / ((int64_t)A.Wc * A.Hc));
     const int4 fc = A.facets[f];  // R0, C0, Hf, Wf
+    if (y >= fc.z || x >= fc.w) continue;  // outside the facet: the canvas keeps its zeros
     uint4 pk[8];
     uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
-    if (y < fc.z && x < fc.w) {
+    {
       float zin[9];
 #pragma unroll
       for (int t = 0; t < 9; ++t) {
         const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-        zin[t] = (yy >= 0 && yy < fc.z && xx >= 0 && xx < fc.w) ? A.z[(size_t)(fc.x + yy) * A.n + fc.y + xx] : 0.f;
+        zin[t] = (yy >= 0 && yy < fc.z && xx >= 0 && xx < fc.w)
+                     ? A.z[f * A.zplane + (size_t)(fc.x + yy) * A.n + fc.y + xx]
+                     : 0.f;
       }
 #pragma unroll 4
       for (int c = 0; c < CH; c += 2) {
@@ -351,9 +387,6 @@ __global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
         __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(a0, 0.f), fmaxf(a1, 0.f));
         pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
       }
-    } else {
-#pragma unroll
-      for (int q = 0; q < 32; ++q) pw[q] = 0u;
     }
     uint4* dst = reinterpret_cast<uint4*>(A.out + p * CH);
 #pragma unroll
@@ -382,15 +415,14 @@ __global__ void __launch_bounds__(256) cnn_last(LastArgs A) {
   for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = A.w8[i];
   __syncthreads();
   double s0 = 0.0, s1 = 0.0;
-  // every image pixel belongs to exactly one facet core
-  const int64_t total = (int64_t)A.n * A.n;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
-    const int iy = (int)(p / A.n), ix = (int)(p % A.n);
-    int f = 0;
-    for (; f < A.F - 1; ++f) {
-      const int4 c = A.cores[f];
-      if (iy >= c.x && iy < c.y && ix >= c.z && ix < c.w) break;
-    }
+  // blockIdx.y = facet; the blocks of a facet cover its core pixels
+  const int f = blockIdx.y;
+  const int4 core = A.cores[f];  // r0, r1, c0, c1
+  const int cw = core.w - core.z;
+  const int64_t ncore = (int64_t)(core.y - core.x) * cw;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ncore; k += (int64_t)gridDim.x * blockDim.x) {
+    const int iy = core.x + (int)(k / cw), ix = core.z + (int)(k % cw);
+    const int64_t p = (int64_t)iy * A.n + ix;
     const int4 fc = A.facets[f];
     const int y = iy - fc.x, x = ix - fc.y;
     float nz = A.b8;
@@ -506,8 +538,9 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   for (int f = 0; f < S->F; ++f) {
     facets[f] = make_int4(S->R0[f], S->C0[f], S->Hf[f], S->Wf[f]);
     cores[f] = make_int4(S->fr0[f], S->fr1[f], S->fc0[f], S->fc1[f]);
-    for (int y = 0; y < S->Hf[f]; ++y)
-      for (int x0 = 0; x0 < S->Wf[f]; x0 += TILE_PX) tiles.push_back(make_int4(f, y, x0, S->Wf[f]));
+    for (int y = 0; y < S->Hf[f]; y += OUT_ROWS)
+      for (int x0 = 0; x0 < S->Wf[f]; x0 += TILE_PX)
+        tiles.push_back(make_int4(f, y, x0, (S->Hf[f] << 16) | S->Wf[f]));
   }
   S->n_tiles = (int)tiles.size();
 
@@ -592,7 +625,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
   if (n != S->n) return fail(PNP_ERR_INVALID_ARG, "image side differs from the one the CNN denoiser was built for");
   const int sms = sms_of_device();
   {
-    FirstArgs F{z, n, S->d_facets, S->F, S->Hc, S->Wc, S->d_w1, S->d_b, S->d_canvas[0]};
+    FirstArgs F{z, n, 0, S->d_facets, S->F, S->Hc, S->Wc, S->d_w1, S->d_b, S->d_canvas[0]};
     const int64_t total = (int64_t)S->F * S->Hc * S->Wc;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8L * sms);
     cnn_first<<<blocks, 256, 0, s>>>(F);
@@ -604,10 +637,10 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
     PNP_CUDA(cudaFuncSetAttribute(conv64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr = true;
   }
-  int cur = 0;
+  int cur = 0;  // (tiles hold OUT_ROWS output rows each)
   for (int l = 0; l < 6; ++l) {
     ConvArgs C{S->d_canvas[cur], S->d_canvas[1 - cur], S->d_wmid + (size_t)l * 9 * CH * CH,
-               S->d_b + (l + 1) * CH, S->d_tiles, S->n_tiles, S->Hc, S->Wc, S->d_status};
+               S->d_b + (l + 1) * CH, S->d_tiles, S->n_tiles, S->Hc, S->Wc, S->d_status, 0, nullptr};
     const int grid = std::max(1, std::min(S->n_tiles, sms));
     conv64_tc<<<grid, CONV_THREADS, smem, s>>>(C);
     PNP_CHECK_LAUNCH();
@@ -615,10 +648,39 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
   }
   {
     LastArgs L{S->d_canvas[cur], z, x_prev, out, n, S->d_facets, S->d_cores, S->F, S->Hc, S->Wc, S->d_w8, S->b8, acc};
-    const int blocks = (int)std::min<int64_t>(((int64_t)n * n + 255) / 256, 8L * sms);
-    cnn_last<<<blocks, 256, 0, s>>>(L);
+    int64_t maxcore = 1;
+    for (int f = 0; f < S->F; ++f)
+      maxcore = std::max<int64_t>(maxcore, (int64_t)(S->fr1[f] - S->fr0[f]) * (S->fc1[f] - S->fc0[f]));
+    const int bx = (int)std::max<int64_t>(1, std::min<int64_t>((maxcore + 255) / 256, (8L * sms + S->F - 1) / S->F));
+    cnn_last<<<dim3(bx, S->F), 256, 0, s>>>(L);
     PNP_CHECK_LAUNCH();
   }
+  return PNP_OK;
+}
+
+int conv64_launch(cudaStream_t s, const __nv_bfloat16* in, __nv_bfloat16* out, const __nv_bfloat16* w_packed,
+                  const float* bias, const int4* tiles, int n_tiles, int Hc, int Wc, int mode,
+                  const __nv_bfloat16* mask, int* status) {
+  static bool attr = false;
+  const int smem = 2 * A_BYTES + B_BYTES;
+  if (!attr) {
+    PNP_CUDA(cudaFuncSetAttribute(conv64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  ConvArgs C{in, out, w_packed, bias, tiles, n_tiles, Hc, Wc, status, mode, mask};
+  const int grid = std::max(1, std::min(n_tiles, sms_of_device()));
+  conv64_tc<<<grid, CONV_THREADS, smem, s>>>(C);
+  PNP_CHECK_LAUNCH();
+  return PNP_OK;
+}
+
+int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, const int4* facets, int F, int Hc,
+                     int Wc, const float* w1, const float* b1, __nv_bfloat16* out) {
+  FirstArgs A{z, n, zplane, facets, F, Hc, Wc, w1, b1, out};
+  const int64_t total = (int64_t)F * Hc * Wc;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8L * sms_of_device());
+  cnn_first<<<blocks, 256, 0, s>>>(A);
+  PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
 

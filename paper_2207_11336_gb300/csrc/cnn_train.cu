@@ -1,0 +1,444 @@
+// Training of the residual CNN denoiser (App. C): l1 loss
+//   E || D(u + sigma n) - u ||_1,  D(z) = z - N(z)   (Eq. training_loss, without
+// the firm non-expansiveness term), Adam updates, hand-written forward and
+// backward kernels.  The Gaussian draws n are inputs.
+//
+// Precision: weights are kept in FP32 (master copy) and rounded to BF16 for
+// every convolution, as in inference; hidden activations and the back-propagated
+// pre-activation gradients are BF16 in memory; the loss gradient, weight
+// gradients and Adam moments are FP32.
+//
+// Per step:
+//   forward   z = u + sigma n; layer 1 (CUDA cores) -> act1; layers 2..7 on the
+//             tensor cores (conv64 forward mode) -> act2..act7; layer 8 and the
+//             l1 loss and its gradient g = dL/dN (CUDA cores);
+//   backward  dpre7 = (W8^T g) * [act7 > 0];  for k = 6..1: dW_{k+1} from
+//             (dpre_{k+1}, act_k) and dpre_k = conv(dpre_{k+1}, flipped W_{k+1}^T)
+//             * [act_k > 0] on the tensor cores (conv64 backward-data mode);
+//             dW1 from (dpre_1, z); bias gradients are pixel sums of dpre;
+//   update    Adam on the FP32 master weights, then re-pack the BF16 operands.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pnp {
+namespace {
+
+constexpr int CH = 64;
+constexpr int NW1 = CH * 9, NB1 = CH, NWM = CH * CH * 9, NBM = CH, NW8 = CH * 9;
+constexpr int64_t OFF_W1 = 0, OFF_B1 = NW1;
+constexpr int64_t OFF_MID = NW1 + NB1;  // 6 x (W, b)
+constexpr int64_t MID_STRIDE = NWM + NBM;
+constexpr int64_t OFF_W8 = OFF_MID + 6 * MID_STRIDE, OFF_B8 = OFF_W8 + NW8;
+constexpr int64_t NPARAM = OFF_B8 + 1;
+constexpr int WG_CHUNK = 2048;  // pixels per weight-gradient block
+
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// master FP32 weights -> BF16-rounded first/last layers, biases, packed middle-layer operands
+__global__ void prep_weights(const float* __restrict__ w, float* __restrict__ w1r, float* __restrict__ w8r,
+                             float* __restrict__ bias, __nv_bfloat16* __restrict__ wf,
+                             __nv_bfloat16* __restrict__ wb) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < 6 * (int64_t)NWM) {
+    const int l = (int)(i / NWM), r = (int)(i % NWM);
+    const int co = r / (CH * 9), ci = (r / 9) % CH, t = r % 9;
+    const __nv_bfloat16 v = __float2bfloat16_rn(w[OFF_MID + l * MID_STRIDE + r]);
+    // forward operand B[t][ci/8][co][ci%8] = W[co][ci][t]
+    wf[(size_t)l * NWM + (size_t)t * CH * CH + (size_t)(ci / 8) * CH * 8 + co * 8 + ci % 8] = v;
+    // backward-data operand B'[8-t][co/8][ci][co%8] = W[co][ci][t]
+    wb[(size_t)l * NWM + (size_t)(8 - t) * CH * CH + (size_t)(co / 8) * CH * 8 + ci * 8 + co % 8] = v;
+  }
+  if (i < NW1) w1r[i] = bf16r(w[OFF_W1 + i]);
+  if (i < NW8) {
+    const int ci = (int)(i / 9), t = (int)(i % 9);
+    w8r[t * CH + ci] = bf16r(w[OFF_W8 + i]);
+  }
+  if (i < 8 * CH) {
+    const int l = (int)(i / CH), c = (int)(i % CH);
+    float b = 0.f;
+    if (l == 0) b = w[OFF_B1 + c];
+    else if (l < 7) b = w[OFF_MID + (l - 1) * MID_STRIDE + NWM + c];
+    else if (c == 0) b = w[OFF_B8];
+    bias[i] = b;
+  }
+}
+
+__global__ void make_z(const float* __restrict__ u, const float* __restrict__ nz, float sigma, float* __restrict__ z,
+                       int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] = u[i] + sigma * nz[i];
+}
+
+struct Dims {
+  int B, s, Hc, Wc;
+};
+
+__device__ __forceinline__ size_t cpix(const Dims& d, int b, int y, int x) {
+  return ((size_t)b * d.Hc + y) * d.Wc + x;
+}
+
+// layer 8 forward, l1 loss and g = dL/dN = -sign(z - N - u) / count
+__global__ void __launch_bounds__(256) last_fwd_loss(Dims d, const __nv_bfloat16* __restrict__ act7,
+                                                     const float* __restrict__ w8r, const float* __restrict__ bias,
+                                                     const float* __restrict__ z, const float* __restrict__ u,
+                                                     float* __restrict__ g, double* loss) {
+  __shared__ float sw[9 * CH];
+  __shared__ double red[256];
+  for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = w8r[i];
+  __syncthreads();
+  const int64_t total = (int64_t)d.B * d.s * d.s;
+  const float inv = 1.f / (float)total;
+  double s = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(p / ((int64_t)d.s * d.s)), y = (int)((p / d.s) % d.s), x = (int)(p % d.s);
+    float nz = bias[7 * CH];
+    for (int t = 0; t < 9; ++t) {
+      const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+      if (yy < 0 || yy >= d.s || xx < 0 || xx >= d.s) continue;
+      const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(act7 + cpix(d, b, yy, xx) * CH);
+#pragma unroll 8
+      for (int c = 0; c < CH / 2; ++c) {
+        const float2 v = __bfloat1622float2(a[c]);
+        nz = fmaf(sw[t * CH + 2 * c], v.x, fmaf(sw[t * CH + 2 * c + 1], v.y, nz));
+      }
+    }
+    const float r = z[p] - nz - u[p];
+    s += fabs((double)r);
+    g[p] = r > 0.f ? -inv : (r < 0.f ? inv : 0.f);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x >> 1; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(loss, red[0] * (double)inv);
+}
+
+// dpre7[q][ci] = [act7[q][ci] > 0] * sum_t W8[ci][t] g[q - off_t]
+__global__ void __launch_bounds__(256) last_bwd(Dims d, const __nv_bfloat16* __restrict__ act7,
+                                                const float* __restrict__ w8r, const float* __restrict__ g,
+                                                __nv_bfloat16* __restrict__ dpre) {
+  __shared__ float sw[9 * CH];
+  for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = w8r[i];
+  __syncthreads();
+  const int64_t total = (int64_t)d.B * d.s * d.s;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(p / ((int64_t)d.s * d.s)), y = (int)((p / d.s) % d.s), x = (int)(p % d.s);
+    float gt[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int yy = y - (t / 3 - 1), xx = x - (t % 3 - 1);
+      gt[t] = (yy >= 0 && yy < d.s && xx >= 0 && xx < d.s) ? g[((int64_t)b * d.s + yy) * d.s + xx] : 0.f;
+    }
+    const size_t base = cpix(d, b, y, x) * CH;
+    const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(act7 + base);
+    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(dpre + base);
+#pragma unroll 4
+    for (int c = 0; c < CH / 2; ++c) {
+      float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        v0 = fmaf(sw[t * CH + 2 * c], gt[t], v0);
+        v1 = fmaf(sw[t * CH + 2 * c + 1], gt[t], v1);
+      }
+      const float2 av = __bfloat1622float2(a[c]);
+      o[c] = __floats2bfloat162_rn(av.x > 0.f ? v0 : 0.f, av.y > 0.f ? v1 : 0.f);
+    }
+  }
+}
+
+// Gradients of a one-channel layer: thread (t, c) accumulates sum_p s1[p] * s2(p + off_t)[c]
+// where one side is a one-channel FP32 image and the other a 64-channel canvas.
+//   mode 0 (layer 8): dW8[c][t] += sum_p g[p] act7[p + off_t][c];   db8 += sum_p g[p]
+//   mode 1 (layer 1): dW1[c][t] += sum_p dpre1[p][c] z[p + off_t];    db1[c] += sum_p dpre1[p][c]
+__global__ void __launch_bounds__(576) wgrad_onechannel(Dims d, int mode, const float* __restrict__ img,
+                                                        const __nv_bfloat16* __restrict__ cv, float* __restrict__ dW,
+                                                        float* __restrict__ db) {
+  const int t = threadIdx.x / CH, c = threadIdx.x % CH;
+  const int64_t total = (int64_t)d.B * d.s * d.s;
+  const int64_t p0 = (int64_t)blockIdx.x * WG_CHUNK, p1 = min(total, p0 + WG_CHUNK);
+  const int dy = t / 3 - 1, dx = t % 3 - 1;
+  float acc = 0.f, bacc = 0.f;
+  for (int64_t p = p0; p < p1; ++p) {
+    const int b = (int)(p / ((int64_t)d.s * d.s)), y = (int)((p / d.s) % d.s), x = (int)(p % d.s);
+    const int yy = y + dy, xx = x + dx;
+    const bool in = yy >= 0 && yy < d.s && xx >= 0 && xx < d.s;
+    if (mode == 0) {
+      const float gv = img[p];
+      if (in) acc = fmaf(gv, __bfloat162float(cv[cpix(d, b, yy, xx) * CH + c]), acc);
+      bacc += gv;
+    } else {
+      const float dv = __bfloat162float(cv[cpix(d, b, y, x) * CH + c]);
+      if (in) acc = fmaf(dv, img[((int64_t)b * d.s + yy) * d.s + xx], acc);
+      bacc += dv;
+    }
+  }
+  if (mode == 0) {
+    atomicAdd(&dW[c * 9 + t], acc);
+    if (threadIdx.x == 0) atomicAdd(&db[0], bacc);
+  } else {
+    atomicAdd(&dW[c * 9 + t], acc);
+    if (t == 4) atomicAdd(&db[c], bacc);
+  }
+}
+
+// dW[co][ci][t] += sum_p dpre[p][co] act[p + off_t][ci]; db[co] += sum_p dpre[p][co] (t == 4 blocks)
+// block: one tap, WG_CHUNK pixels; thread owns a 4 (co) x 4 (ci) tile of the 64 x 64 gradient.
+__global__ void __launch_bounds__(256) wgrad64(Dims d, const __nv_bfloat16* __restrict__ dpre,
+                                               const __nv_bfloat16* __restrict__ act, float* __restrict__ dW,
+                                               float* __restrict__ db) {
+  constexpr int PB = 32;  // pixels staged per round
+  __shared__ float sd[PB][CH], sa[PB][CH];
+  const int t = blockIdx.y, dy = t / 3 - 1, dx = t % 3 - 1;
+  const int co0 = (threadIdx.x / 16) * 4, ci0 = (threadIdx.x % 16) * 4;
+  const int64_t total = (int64_t)d.B * d.s * d.s;
+  const int64_t p0 = (int64_t)blockIdx.x * WG_CHUNK, p1 = min(total, p0 + WG_CHUNK);
+  float acc[4][4] = {};
+  float bsum = 0.f;
+  for (int64_t pb = p0; pb < p1; pb += PB) {
+    // stage PB pixels: dpre at p, act at p + off_t (zero outside the image)
+    for (int e = threadIdx.x; e < PB * CH / 2; e += blockDim.x) {
+      const int q = e / (CH / 2), c2 = e % (CH / 2);
+      const int64_t p = pb + q;
+      float2 dv = make_float2(0.f, 0.f), av = make_float2(0.f, 0.f);
+      if (p < p1) {
+        const int b = (int)(p / ((int64_t)d.s * d.s)), y = (int)((p / d.s) % d.s), x = (int)(p % d.s);
+        dv = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(dpre + cpix(d, b, y, x) * CH)[c2]);
+        const int yy = y + dy, xx = x + dx;
+        if (yy >= 0 && yy < d.s && xx >= 0 && xx < d.s)
+          av = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(act + cpix(d, b, yy, xx) * CH)[c2]);
+      }
+      sd[q][2 * c2] = dv.x;
+      sd[q][2 * c2 + 1] = dv.y;
+      sa[q][2 * c2] = av.x;
+      sa[q][2 * c2 + 1] = av.y;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int q = 0; q < PB; ++q) {
+      const float4 dv = *reinterpret_cast<const float4*>(&sd[q][co0]);
+      const float4 av = *reinterpret_cast<const float4*>(&sa[q][ci0]);
+      const float dd[4] = {dv.x, dv.y, dv.z, dv.w}, aa[4] = {av.x, av.y, av.z, av.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(dd[i], aa[j], acc[i][j]);
+    }
+    if (t == 4 && threadIdx.x < CH)
+      for (int q = 0; q < PB; ++q) bsum += sd[q][threadIdx.x];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) atomicAdd(&dW[((size_t)(co0 + i) * CH + (ci0 + j)) * 9 + t], acc[i][j]);
+  if (t == 4 && threadIdx.x < CH) atomicAdd(&db[threadIdx.x], bsum);
+}
+
+// Adam (Kingma & Ba 2015) on the master weights; the gradient is cleared for the next step.
+__global__ void adam_step(float* __restrict__ w, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                          int64_t count, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    g[i] = 0.f;
+  }
+}
+
+__global__ void zero_f(float* p, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = 0.f;
+}
+
+int nblocks(int64_t count, int threads = 256) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return (int)std::max<int64_t>(1, std::min<int64_t>((count + threads - 1) / threads, 8L * sms));
+}
+
+}  // namespace
+}  // namespace pnp
+
+struct pnp_cnn_trainer {
+  pnp::Dims d{};
+  cudaStream_t stream = nullptr;
+  int n_tiles = 0, t = 0;
+  double lr = 1e-4, b1 = 0.9, b2 = 0.999, eps = 1e-8;
+  float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  float *w1r = nullptr, *w8r = nullptr, *bias = nullptr;
+  __nv_bfloat16 *wf = nullptr, *wb = nullptr;
+  __nv_bfloat16* act[8] = {};
+  __nv_bfloat16* dp[2] = {};
+  float *z = nullptr, *gout = nullptr;
+  int4 *facets = nullptr, *tiles = nullptr;
+  double* loss = nullptr;
+  int* status = nullptr;
+};
+
+using namespace pnp;
+
+namespace {
+void trainer_free(pnp_cnn_trainer* T) {
+  if (!T) return;
+  for (void* p : {(void*)T->w, (void*)T->g, (void*)T->m, (void*)T->v, (void*)T->w1r, (void*)T->w8r, (void*)T->bias,
+                  (void*)T->wf, (void*)T->wb, (void*)T->z, (void*)T->gout, (void*)T->facets, (void*)T->tiles,
+                  (void*)T->loss, (void*)T->status})
+    cudaFree(p);
+  for (auto p : T->act) cudaFree(p);
+  for (auto p : T->dp) cudaFree(p);
+  delete T;
+}
+
+int prep(pnp_cnn_trainer* T) {
+  prep_weights<<<nblocks(6 * (int64_t)NWM), 256, 0, T->stream>>>(T->w, T->w1r, T->w8r, T->bias, T->wf, T->wb);
+  PNP_CHECK_LAUNCH();
+  return PNP_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int pnp_cnn_trainer_create(pnp_cnn_trainer** out, const float* weights_host, int batch, int size, double lr,
+                           void* stream) {
+  if (!out || !weights_host || batch < 1 || size < 8 || !(lr > 0)) return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  *out = nullptr;
+  pnp_cnn_trainer* T = new pnp_cnn_trainer();
+  T->stream = reinterpret_cast<cudaStream_t>(stream);
+  T->lr = lr;
+  T->d = Dims{batch, size, size, (size + 127) / 128 * 128};
+  const size_t canvas = (size_t)batch * T->d.Hc * T->d.Wc * CH;
+  const int64_t npx = (int64_t)batch * size * size;
+  auto al = [&](void** p, size_t bytes) -> bool {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  };
+  bool ok = al((void**)&T->w, NPARAM * 4) && al((void**)&T->g, NPARAM * 4) && al((void**)&T->m, NPARAM * 4) &&
+            al((void**)&T->v, NPARAM * 4) && al((void**)&T->w1r, NW1 * 4) && al((void**)&T->w8r, NW8 * 4) &&
+            al((void**)&T->bias, 8 * CH * 4) && al((void**)&T->wf, 6 * (size_t)NWM * 2) &&
+            al((void**)&T->wb, 6 * (size_t)NWM * 2) && al((void**)&T->z, npx * 4) && al((void**)&T->gout, npx * 4) &&
+            al((void**)&T->facets, batch * sizeof(int4)) && al((void**)&T->loss, sizeof(double)) &&
+            al((void**)&T->status, 4 * sizeof(int));
+  for (int i = 1; ok && i <= 7; ++i) ok = al((void**)&T->act[i], canvas * 2);
+  for (int i = 0; ok && i < 2; ++i) ok = al((void**)&T->dp[i], canvas * 2);
+  std::vector<int4> facets(batch), tiles;
+  for (int b = 0; b < batch; ++b) {
+    facets[b] = make_int4(0, 0, size, size);
+    for (int y = 0; y < size; y += 2)  // the convolution tiles hold two output rows
+      for (int x0 = 0; x0 < size; x0 += 128) tiles.push_back(make_int4(b, y, x0, (size << 16) | size));
+  }
+  T->n_tiles = (int)tiles.size();
+  ok = ok && al((void**)&T->tiles, tiles.size() * sizeof(int4));
+  if (!ok) {
+    trainer_free(T);
+    return fail(PNP_ERR_OOM, "trainer allocation failed");
+  }
+  cudaError_t e = cudaMemcpy(T->w, weights_host, NPARAM * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(T->g, 0, NPARAM * 4);
+  if (e == cudaSuccess) e = cudaMemset(T->m, 0, NPARAM * 4);
+  if (e == cudaSuccess) e = cudaMemset(T->v, 0, NPARAM * 4);
+  if (e == cudaSuccess) e = cudaMemset(T->status, 0, 4 * sizeof(int));
+  for (int i = 1; e == cudaSuccess && i <= 7; ++i) e = cudaMemset(T->act[i], 0, canvas * 2);
+  for (int i = 0; e == cudaSuccess && i < 2; ++i) e = cudaMemset(T->dp[i], 0, canvas * 2);
+  if (e == cudaSuccess) e = cudaMemcpy(T->facets, facets.data(), batch * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(T->tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    trainer_free(T);
+    return fail(PNP_ERR_CUDA, std::string("trainer set-up: ") + cudaGetErrorString(e));
+  }
+  if (int rc = prep(T)) {
+    trainer_free(T);
+    return rc;
+  }
+  *out = T;
+  return PNP_OK;
+}
+
+void pnp_cnn_trainer_destroy(pnp_cnn_trainer* T) {
+  if (T) cudaStreamSynchronize(T->stream);
+  trainer_free(T);
+}
+
+int pnp_cnn_train_step(pnp_cnn_trainer* T, const float* u, const float* noise, double sigma, int update,
+                       double* loss_host) {
+  if (!T || !u || !noise || !(sigma >= 0)) return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  const Dims d = T->d;
+  const int64_t npx = (int64_t)d.B * d.s * d.s;
+  cudaStream_t s = T->stream;
+  // ---------------- forward
+  make_z<<<nblocks(npx), 256, 0, s>>>(u, noise, (float)sigma, T->z, npx);
+  PNP_CHECK_LAUNCH();
+  if (int rc = cnn_first_launch(s, T->z, d.s, (int64_t)d.s * d.s, T->facets, d.B, d.Hc, d.Wc, T->w1r, T->bias,
+                                T->act[1]))
+    return rc;
+  for (int k = 1; k <= 6; ++k)
+    if (int rc = conv64_launch(s, T->act[k], T->act[k + 1], T->wf + (size_t)(k - 1) * NWM, T->bias + k * CH,
+                               T->tiles, T->n_tiles, d.Hc, d.Wc, 0, nullptr, T->status))
+      return rc;
+  PNP_CUDA(cudaMemsetAsync(T->loss, 0, sizeof(double), s));
+  last_fwd_loss<<<nblocks(npx), 256, 0, s>>>(d, T->act[7], T->w8r, T->bias, T->z, u, T->gout, T->loss);
+  PNP_CHECK_LAUNCH();
+  // ---------------- backward
+  last_bwd<<<nblocks(npx), 256, 0, s>>>(d, T->act[7], T->w8r, T->gout, T->dp[0]);
+  PNP_CHECK_LAUNCH();
+  const int wgb = (int)((npx + WG_CHUNK - 1) / WG_CHUNK);
+  wgrad_onechannel<<<wgb, 576, 0, s>>>(d, 0, T->gout, T->act[7], T->g + OFF_W8, T->g + OFF_B8);
+  PNP_CHECK_LAUNCH();
+  int cur = 0;
+  for (int k = 6; k >= 1; --k) {
+    float* gW = T->g + OFF_MID + (k - 1) * MID_STRIDE;
+    wgrad64<<<dim3(wgb, 9), 256, 0, s>>>(d, T->dp[cur], T->act[k], gW, gW + NWM);
+    PNP_CHECK_LAUNCH();
+    if (int rc = conv64_launch(s, T->dp[cur], T->dp[1 - cur], T->wb + (size_t)(k - 1) * NWM, nullptr, T->tiles,
+                               T->n_tiles, d.Hc, d.Wc, 1, T->act[k], T->status))
+      return rc;
+    cur = 1 - cur;
+  }
+  wgrad_onechannel<<<wgb, 576, 0, s>>>(d, 1, T->z, T->dp[cur], T->g + OFF_W1, T->g + OFF_B1);
+  PNP_CHECK_LAUNCH();
+  // ---------------- update
+  if (update) {
+    T->t += 1;
+    const float c1 = (float)(1.0 - std::pow(T->b1, T->t)), c2 = (float)(1.0 - std::pow(T->b2, T->t));
+    adam_step<<<nblocks(NPARAM), 256, 0, s>>>(T->w, T->g, T->m, T->v, NPARAM, (float)T->lr, (float)T->b1,
+                                              (float)T->b2, (float)T->eps, c1, c2);
+    PNP_CHECK_LAUNCH();
+    if (int rc = prep(T)) return rc;
+  }
+  if (loss_host) {
+    PNP_CUDA(cudaMemcpyAsync(loss_host, T->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PNP_CUDA(cudaStreamSynchronize(s));
+  }
+  return PNP_OK;
+}
+
+int pnp_cnn_trainer_read(pnp_cnn_trainer* T, float* weights_host, float* grads_host, int clear_grads) {
+  if (!T) return fail(PNP_ERR_INVALID_ARG, "NULL trainer");
+  PNP_CUDA(cudaStreamSynchronize(T->stream));
+  if (weights_host) PNP_CUDA(cudaMemcpy(weights_host, T->w, NPARAM * 4, cudaMemcpyDeviceToHost));
+  if (grads_host) PNP_CUDA(cudaMemcpy(grads_host, T->g, NPARAM * 4, cudaMemcpyDeviceToHost));
+  if (clear_grads) {
+    zero_f<<<nblocks(NPARAM), 256, 0, T->stream>>>(T->g, NPARAM);
+    PNP_CHECK_LAUNCH();
+  }
+  int st = 0;
+  PNP_CUDA(cudaMemcpy(&st, T->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) return fail(PNP_ERR_TIMEOUT, "a bounded wait in the tensor-core convolution gave up");
+  return PNP_OK;
+}
+
+int64_t pnp_cnn_num_params(void) { return NPARAM; }
+
+}  // extern "C"

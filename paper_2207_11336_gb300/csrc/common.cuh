@@ -163,6 +163,12 @@ int cnn_create(pnp_den* d, const float* weights_host, const int32_t* fr, int nfr
                const int32_t* fc, int nfc, int halo, int n);
 void cnn_destroy(pnp_den* d);
 int cnn_status(pnp_den* d, int* flags);
+// shared with the CNN trainer (cnn_train.cu)
+int conv64_launch(cudaStream_t s, const __nv_bfloat16* in, __nv_bfloat16* out, const __nv_bfloat16* w_packed,
+                  const float* bias, const int4* tiles, int n_tiles, int Hc, int Wc, int mode,
+                  const __nv_bfloat16* mask, int* status);
+int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, const int4* facets, int F, int Hc,
+                     int Wc, const float* w1, const float* b1, __nv_bfloat16* out);
 int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc,
                 const float* x_prev);
 }  // namespace pnp
