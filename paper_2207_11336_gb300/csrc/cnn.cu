@@ -28,14 +28,20 @@
 // 9 taps x 4 K-steps (16 channels each) accumulate M=128 x N=64 into tensor
 // memory; the two output rows share the staged rows.
 // Weights of all taps sit in shared memory as [tap][kb][co][8 ci] (K-major B).
-// Warp roles: warps 0-3 drain tensor memory (bias, ReLU, BF16, store),
-// warp 4 allocates tensor memory and issues the MMAs (one elected lane),
-// warps 5-8 stage input tiles with cp.async.  Two input buffers and two
+// The staged tile is one TMA transfer: the canvas is described to the TMA unit
+// as a 5-D tensor (8 channels, x, channel block, y, facet), whose box
+// (8, 130, 8, 4, 1) lands in shared memory in exactly that operand layout, with
+// zeros outside the canvas.  Warp roles: warps 0-3 drain tensor memory (bias,
+// ReLU, BF16, store), warp 4 allocates tensor memory and issues the MMAs (one
+// lane), warp 5 issues the TMA loads (one lane).  Two input buffers and two
 // accumulators are pipelined with mbarriers; every wait is bounded.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "common.cuh"
 
@@ -53,8 +59,7 @@ constexpr int A_BYTES = STAGE_ROWS * ROW_BYTES;         // 66560
 constexpr int TMEM_COLS = 2 * OUT_ROWS * CH;            // two tiles in flight x OUT_ROWS accumulators
 constexpr int B_TAP_BYTES = CH * CH * 2;                // 8192
 constexpr int B_BYTES = 9 * B_TAP_BYTES;                // 73728
-constexpr int CONV_THREADS = 9 * 32;
-constexpr int LOADER_THREADS = 128;
+constexpr int CONV_THREADS = 6 * 32;  // 4 epilogue warps, 1 MMA warp, 1 TMA warp
 constexpr uint32_t CNN_WAIT_LIMIT = 1u << 26;
 
 struct CnnState {
@@ -72,6 +77,7 @@ struct CnnState {
   float* d_w8 = nullptr;                 // [9][64] (BF16-rounded values)
   int* d_status = nullptr;
   float b8 = 0.f;                        // last layer's bias (host copy)
+  CUtensorMap map[2];                    // TMA descriptors of the two canvases
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -102,7 +108,24 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool vali
                : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// arrive on the mbarrier once all cp.async copies issued so far by this thread have landed
+__device__ __forceinline__ void cp_async_arrive(uint64_t* b) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(b)) : "memory");
+}
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+// 5-D tiled TMA load into shared memory, completion counted on an mbarrier
+__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(
+          su32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(su32(bar))
+      : "memory");
+}
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(dst)), "r"(ncols)
@@ -171,7 +194,7 @@ struct ConvArgs {
   const __nv_bfloat16* mask;   // backward data: activations whose ReLU mask gates the output (same canvas layout)
 };
 
-__global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
+__global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(1024) unsigned char sm[];
   unsigned char* sa[2] = {sm, sm + A_BYTES};
   unsigned char* sb = sm + 2 * A_BYTES;
@@ -190,7 +213,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
   }
   if (threadIdx.x == 0) {
     for (int b = 0; b < 2; ++b) {
-      bar_init(&a_full[b], LOADER_THREADS);
+      bar_init(&a_full[b], 1);
       bar_init(&a_empty[b], 1);
       bar_init(&t_full[b], 1);
       bar_init(&t_empty[b], 128);
@@ -209,28 +232,22 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
   const uint32_t tmem = s_tmem;
   const int stride = gridDim.x;
 
-  if (warp >= 5) {
-    // ---------------- loaders: rows y-1..y+1, pixels x0-1..x0+128 -> [dy][kb][px][8]
-    const int t = threadIdx.x - 5 * 32;
-    int i = 0;
-    for (int tile = blockIdx.x; tile < A.n_tiles; tile += stride, ++i) {
-      const int b = i & 1;
-      if (i >= 2 && !bar_wait(&a_empty[b], ((i >> 1) - 1) & 1)) s_abort = 1;
-      if (s_abort) break;
-      const int4 T = A.tiles[tile];
-      const size_t fbase = (size_t)T.x * A.Hc;
-      for (int c = t; c < STAGE_ROWS * STAGE_PX * 8; c += LOADER_THREADS) {
-        const int kb = c & 7, px = (c >> 3) % STAGE_PX, dy = (c >> 3) / STAGE_PX;
-        const int yy = T.y - 1 + dy, xx = T.z - 1 + px;
-        const bool ok = yy >= 0 && yy < A.Hc && xx >= 0 && xx < A.Wc;
-        const __nv_bfloat16* src =
-            A.in + (((fbase + (ok ? yy : 0)) * A.Wc + (ok ? xx : 0)) * CH + kb * 8);
-        cp_async16(sa[b] + dy * ROW_BYTES + kb * KB_BYTES + px * 16, src, ok);
+  if (warp == 5) {
+    // ---------------- TMA producer: rows y0-1..y0+2, pixels x0-1..x0+128 of the tile's facet
+    if (lane == 0) {
+      int i = 0;
+      for (int tile = blockIdx.x; tile < A.n_tiles; tile += stride, ++i) {
+        const int b = i & 1;
+        if (i >= 2 && !bar_wait(&a_empty[b], ((i >> 1) - 1) & 1)) s_abort = 1;
+        if (s_abort) break;
+        const int4 T = A.tiles[tile];
+        bar_expect_tx(&a_full[b], A_BYTES);
+        tma_load_5d(sa[b], &tmap, 0, T.z - 1, 0, T.y - 1, T.x, &a_full[b]);
       }
-      cp_async_wait_all();
-      fence_async_smem();
-      bar_arrive(&a_full[b]);
+      // every issued load must land before the CTA ends (bounded)
+      for (int k = (i >= 2 ? i - 2 : 0); k < i; ++k) bar_wait(&a_full[k & 1], (k >> 1) & 1);
     }
+    __syncwarp();
   } else if (warp == 4) {
     // ---------------- MMA issuer
     if (lane == 0) {
@@ -240,22 +257,22 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A) {
         if (!bar_wait(&a_full[b], (i >> 1) & 1)) s_abort = 1;
         if (i >= 2 && !bar_wait(&t_empty[d], ((i >> 1) - 1) & 1)) s_abort = 1;
         if (s_abort) break;
+        fence_async_smem();  // the tile was written by cp.async (generic proxy); the MMAs read it (async proxy)
         tc_fence_after();
-        const uint32_t abase = su32(sa[b]), bbase = su32(sb);
-#pragma unroll 1
+        // descriptors differ only in their start address (16-B units in the low bits), so each
+        // MMA adds a compile-time offset to a base descriptor (addresses stay below 2^18 B)
+        const uint64_t adesc0 = smem_desc(su32(sa[b]), KB_BYTES, 128);
+        const uint64_t bdesc0 = smem_desc(su32(sb), 1024, 128);
+#pragma unroll
         for (int r = 0; r < OUT_ROWS; ++r) {
           const uint32_t dt = tmem + (uint32_t)((d * OUT_ROWS + r) * CH);
-          int first = 1;
-#pragma unroll 1
+#pragma unroll
           for (int tap = 0; tap < 9; ++tap) {
-            const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t ad =
-                  smem_desc(abase + (r + dy) * ROW_BYTES + 2 * kk * KB_BYTES + dx * 16, KB_BYTES, 128);
-              const uint64_t bd = smem_desc(bbase + tap * B_TAP_BYTES + 2 * kk * 1024, 1024, 128);
-              mma_bf16(dt, ad, bd, IDESC, first ? 0u : 1u);
-              first = 0;
+              const uint32_t aoff = (uint32_t)((r + tap / 3) * ROW_BYTES + 2 * kk * KB_BYTES + (tap % 3) * 16);
+              const uint32_t boff = (uint32_t)(tap * B_TAP_BYTES + 2 * kk * 1024);
+              mma_bf16(dt, adesc0 + (aoff >> 4), bdesc0 + (boff >> 4), IDESC, (tap | kk) ? 1u : 0u);
             }
           }
         }
@@ -354,43 +371,31 @@ struct FirstArgs {
 };
 
 __global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
-  __shared__ float sw[CH * 9], sbias[CH];
-  for (int i = threadIdx.x; i < CH * 9; i += blockDim.x) sw[i] = A.w1[i];
-  if (threadIdx.x < CH) sbias[threadIdx.x] = A.b1[threadIdx.x];
-  __syncthreads();
-  const int64_t total = (int64_t)A.F * A.Hc * A.Wc;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(p % A.Wc);
-    const int y = (int)((p / A.Wc) % A.Hc);
-    const int f = (int)(p / ((int64_t)A.Wc * A.Hc));
-    const int4 fc = A.facets[f];  // R0, C0, Hf, Wf
-    if (y >= fc.z || x >= fc.w) continue;  // outside the facet: the canvas keeps its zeros
-    uint4 pk[8];
-    uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
-    {
-      float zin[9];
+  // grid (x chunks of 64, row y, facet f); warp w handles pixels x0 + w, x0 + w + 8, ...;
+  // lane l produces channels 2l and 2l + 1 (coalesced 128-B stores)
+  const int f = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * 64;
+  const int4 fc = A.facets[f];  // R0, C0, Hf, Wf
+  if (y >= fc.z || x0 >= fc.w) return;  // outside the facet: the canvas keeps its zeros
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  float w0[9], w1[9];
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-        zin[t] = (yy >= 0 && yy < fc.z && xx >= 0 && xx < fc.w)
-                     ? A.z[f * A.zplane + (size_t)(fc.x + yy) * A.n + fc.y + xx]
-                     : 0.f;
-      }
-#pragma unroll 4
-      for (int c = 0; c < CH; c += 2) {
-        float a0 = sbias[c], a1 = sbias[c + 1];
+  for (int t = 0; t < 9; ++t) {
+    w0[t] = A.w1[(2 * lane) * 9 + t];
+    w1[t] = A.w1[(2 * lane + 1) * 9 + t];
+  }
+  const float b0 = A.b1[2 * lane], b1 = A.b1[2 * lane + 1];
+  const float* zf = A.z + (size_t)f * A.zplane;
+  for (int x = x0 + wid; x < min(x0 + 64, fc.w); x += 8) {
+    float a0 = b0, a1 = b1;
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-          a0 = fmaf(sw[c * 9 + t], zin[t], a0);
-          a1 = fmaf(sw[(c + 1) * 9 + t], zin[t], a1);
-        }
-        __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(a0, 0.f), fmaxf(a1, 0.f));
-        pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
-      }
+    for (int t = 0; t < 9; ++t) {
+      const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+      const float zt = (yy >= 0 && yy < fc.z && xx >= 0 && xx < fc.w) ? zf[(size_t)(fc.x + yy) * A.n + fc.y + xx] : 0.f;
+      a0 = fmaf(w0[t], zt, a0);
+      a1 = fmaf(w1[t], zt, a1);
     }
-    uint4* dst = reinterpret_cast<uint4*>(A.out + p * CH);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) dst[q] = pk[q];
+    const size_t p = ((size_t)f * A.Hc + y) * A.Wc + x;
+    reinterpret_cast<__nv_bfloat162*>(A.out + p * CH)[lane] = __floats2bfloat162_rn(fmaxf(a0, 0.f), fmaxf(a1, 0.f));
   }
 }
 
@@ -410,62 +415,64 @@ struct LastArgs {
 };
 
 __global__ void __launch_bounds__(256) cnn_last(LastArgs A) {
-  __shared__ float sw[9 * CH];
-  __shared__ double red[2 * 256];
-  for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = A.w8[i];
-  __syncthreads();
-  double s0 = 0.0, s1 = 0.0;
-  // blockIdx.y = facet; the blocks of a facet cover its core pixels
+  // grid (core row, facet); warp w handles core columns c0 + w, c0 + w + 8, ...;
+  // lane l holds channels 2l, 2l + 1 of the 64-channel activations
+  __shared__ double red[2 * 8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int f = blockIdx.y;
   const int4 core = A.cores[f];  // r0, r1, c0, c1
-  const int cw = core.w - core.z;
-  const int64_t ncore = (int64_t)(core.y - core.x) * cw;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ncore; k += (int64_t)gridDim.x * blockDim.x) {
-    const int iy = core.x + (int)(k / cw), ix = core.z + (int)(k % cw);
-    const int64_t p = (int64_t)iy * A.n + ix;
-    const int4 fc = A.facets[f];
-    const int y = iy - fc.x, x = ix - fc.y;
-    float nz = A.b8;
+  const int4 fc = A.facets[f];   // R0, C0, Hf, Wf
+  const int iy = core.x + blockIdx.x;
+  double s0 = 0.0, s1 = 0.0;
+  if (iy < core.y) {
+    float w0[9], w1[9];
+#pragma unroll
     for (int t = 0; t < 9; ++t) {
-      const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-      if (yy < 0 || yy >= fc.z || xx < 0 || xx >= fc.w) continue;
-      const uint4* src = reinterpret_cast<const uint4*>(A.in + (((size_t)f * A.Hc + yy) * A.Wc + xx) * CH);
+      w0[t] = A.w8[t * CH + 2 * lane];
+      w1[t] = A.w8[t * CH + 2 * lane + 1];
+    }
+    const int y = iy - fc.x;
+    for (int ix = core.z + wid; ix < core.w; ix += 8) {
+      const int x = ix - fc.y;
+      float part = 0.f;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const uint4 v = src[q];
-        const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+      for (int t = 0; t < 9; ++t) {
+        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+        if (yy < 0 || yy >= fc.z || xx < 0 || xx >= fc.w) continue;
+        const float2 v = __bfloat1622float2(
+            reinterpret_cast<const __nv_bfloat162*>(A.in + (((size_t)f * A.Hc + yy) * A.Wc + xx) * CH)[lane]);
+        part = fmaf(w0[t], v.x, fmaf(w1[t], v.y, part));
+      }
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float2 h = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[e]));
-          nz = fmaf(sw[t * CH + q * 8 + 2 * e], h.x, nz);
-          nz = fmaf(sw[t * CH + q * 8 + 2 * e + 1], h.y, nz);
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == 0) {
+        const size_t p = (size_t)iy * A.n + ix;
+        const float zv = A.z[p];
+        const float o = fmaxf(0.f, zv - (A.b8 + part));
+        A.out[p] = o;
+        s1 += (double)o * o;
+        if (!isfinite(zv)) s1 = __longlong_as_double(0x7ff8000000000000LL);
+        if (A.x_prev) {
+          const double dd = (double)o - A.x_prev[p];
+          s0 += dd * dd;
         }
       }
     }
-    const float zv = A.z[p];
-    const float o = fmaxf(0.f, zv - nz);
-    A.out[p] = o;
-    s1 += (double)o * o;
-    if (!isfinite(zv)) s1 = __longlong_as_double(0x7ff8000000000000LL);
-    if (A.x_prev) {
-      const double dd = (double)o - A.x_prev[p];
-      s0 += dd * dd;
-    }
   }
   if (A.acc) {
-    red[2 * threadIdx.x] = s0;
-    red[2 * threadIdx.x + 1] = s1;
-    __syncthreads();
-    for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
-      if (threadIdx.x < s) {
-        red[2 * threadIdx.x] += red[2 * (threadIdx.x + s)];
-        red[2 * threadIdx.x + 1] += red[2 * (threadIdx.x + s) + 1];
-      }
-      __syncthreads();
+    if (lane == 0) {
+      red[2 * wid] = s0;
+      red[2 * wid + 1] = s1;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      atomicAdd(&A.acc[0], red[0]);
-      atomicAdd(&A.acc[1], red[1]);
+      double t0 = 0.0, t1 = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        t0 += red[2 * w];
+        t1 += red[2 * w + 1];
+      }
+      atomicAdd(&A.acc[0], t0);
+      atomicAdd(&A.acc[1], t1);
     }
   }
 }
@@ -482,6 +489,28 @@ float bf16_round(float f) {
   float o;
   std::memcpy(&o, &u, 4);
   return o;
+}
+
+// The canvas [F][Hc][Wc][64] (BF16) as the 5-D tensor (8 ch, x, kb, y, f) whose (8, 130, 8, 4, 1)
+// box is the staged tile of conv64_tc in its shared-memory operand layout.
+int make_canvas_map(CUtensorMap* map, const __nv_bfloat16* canvas, int F, int Hc, int Wc) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    PNP_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn) return fail(PNP_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
+    enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[5] = {8, (cuuint64_t)Wc, 8, (cuuint64_t)Hc, (cuuint64_t)F};
+  const cuuint64_t strides[4] = {(cuuint64_t)CH * 2, 16, (cuuint64_t)Wc * CH * 2, (cuuint64_t)Hc * Wc * CH * 2};
+  const cuuint32_t box[5] = {8, (cuuint32_t)STAGE_PX, 8, (cuuint32_t)STAGE_ROWS, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(canvas), dims, strides,
+                         box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(PNP_ERR_UNSUPPORTED, "tensor map encoding failed (" + std::to_string((int)r) + ")");
+  return PNP_OK;
 }
 
 int sms_of_device() {
@@ -600,6 +629,8 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   PNP_CUDA(cudaMemcpy(S->d_b, bias.data(), bias.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_wmid, wmid.data(), wmid.size() * 2, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemset(S->d_status, 0, 4 * sizeof(int)));
+  for (int i = 0; i < 2; ++i)
+    if (int rc = make_canvas_map(&S->map[i], S->d_canvas[i], S->F, S->Hc, S->Wc)) return rc;
   return PNP_OK;
 }
 
@@ -626,9 +657,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
   const int sms = sms_of_device();
   {
     FirstArgs F{z, n, 0, S->d_facets, S->F, S->Hc, S->Wc, S->d_w1, S->d_b, S->d_canvas[0]};
-    const int64_t total = (int64_t)S->F * S->Hc * S->Wc;
-    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8L * sms);
-    cnn_first<<<blocks, 256, 0, s>>>(F);
+    cnn_first<<<dim3((S->Wc + 63) / 64, S->Hc, S->F), 256, 0, s>>>(F);
     PNP_CHECK_LAUNCH();
   }
   static bool attr = false;
@@ -642,25 +671,23 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
     ConvArgs C{S->d_canvas[cur], S->d_canvas[1 - cur], S->d_wmid + (size_t)l * 9 * CH * CH,
                S->d_b + (l + 1) * CH, S->d_tiles, S->n_tiles, S->Hc, S->Wc, S->d_status, 0, nullptr};
     const int grid = std::max(1, std::min(S->n_tiles, sms));
-    conv64_tc<<<grid, CONV_THREADS, smem, s>>>(C);
+    conv64_tc<<<grid, CONV_THREADS, smem, s>>>(C, S->map[cur]);
     PNP_CHECK_LAUNCH();
     cur = 1 - cur;
   }
   {
     LastArgs L{S->d_canvas[cur], z, x_prev, out, n, S->d_facets, S->d_cores, S->F, S->Hc, S->Wc, S->d_w8, S->b8, acc};
-    int64_t maxcore = 1;
-    for (int f = 0; f < S->F; ++f)
-      maxcore = std::max<int64_t>(maxcore, (int64_t)(S->fr1[f] - S->fr0[f]) * (S->fc1[f] - S->fc0[f]));
-    const int bx = (int)std::max<int64_t>(1, std::min<int64_t>((maxcore + 255) / 256, (8L * sms + S->F - 1) / S->F));
-    cnn_last<<<dim3(bx, S->F), 256, 0, s>>>(L);
+    int maxrows = 1;
+    for (int f = 0; f < S->F; ++f) maxrows = std::max(maxrows, S->fr1[f] - S->fr0[f]);
+    cnn_last<<<dim3(maxrows, S->F), 256, 0, s>>>(L);
     PNP_CHECK_LAUNCH();
   }
   return PNP_OK;
 }
 
-int conv64_launch(cudaStream_t s, const __nv_bfloat16* in, __nv_bfloat16* out, const __nv_bfloat16* w_packed,
-                  const float* bias, const int4* tiles, int n_tiles, int Hc, int Wc, int mode,
-                  const __nv_bfloat16* mask, int* status) {
+int conv64_launch(cudaStream_t s, const void* in_map, const __nv_bfloat16* in, __nv_bfloat16* out,
+                  const __nv_bfloat16* w_packed, const float* bias, const int4* tiles, int n_tiles, int Hc, int Wc,
+                  int mode, const __nv_bfloat16* mask, int* status) {
   static bool attr = false;
   const int smem = 2 * A_BYTES + B_BYTES;
   if (!attr) {
@@ -669,7 +696,7 @@ int conv64_launch(cudaStream_t s, const __nv_bfloat16* in, __nv_bfloat16* out, c
   }
   ConvArgs C{in, out, w_packed, bias, tiles, n_tiles, Hc, Wc, status, mode, mask};
   const int grid = std::max(1, std::min(n_tiles, sms_of_device()));
-  conv64_tc<<<grid, CONV_THREADS, smem, s>>>(C);
+  conv64_tc<<<grid, CONV_THREADS, smem, s>>>(C, *static_cast<const CUtensorMap*>(in_map));
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
@@ -677,11 +704,13 @@ int conv64_launch(cudaStream_t s, const __nv_bfloat16* in, __nv_bfloat16* out, c
 int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, const int4* facets, int F, int Hc,
                      int Wc, const float* w1, const float* b1, __nv_bfloat16* out) {
   FirstArgs A{z, n, zplane, facets, F, Hc, Wc, w1, b1, out};
-  const int64_t total = (int64_t)F * Hc * Wc;
-  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 8L * sms_of_device());
-  cnn_first<<<blocks, 256, 0, s>>>(A);
+  cnn_first<<<dim3((Wc + 63) / 64, Hc, F), 256, 0, s>>>(A);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
+}
+
+int canvas_map_create(void* map_out, const __nv_bfloat16* canvas, int F, int Hc, int Wc) {
+  return make_canvas_map(static_cast<CUtensorMap*>(map_out), canvas, F, Hc, Wc);
 }
 
 int cnn_status(pnp_den* d, int* flags) {

@@ -282,6 +282,8 @@ struct pnp_cnn_trainer {
   int4 *facets = nullptr, *tiles = nullptr;
   double* loss = nullptr;
   int* status = nullptr;
+  alignas(64) unsigned char map_act[8][128];  // TMA descriptors of act[1..7]
+  alignas(64) unsigned char map_dp[2][128];   // and of the two gradient canvases
 };
 
 using namespace pnp;
@@ -358,6 +360,16 @@ int pnp_cnn_trainer_create(pnp_cnn_trainer** out, const float* weights_host, int
     trainer_free(T);
     return fail(PNP_ERR_CUDA, std::string("trainer set-up: ") + cudaGetErrorString(e));
   }
+  for (int i = 1; i <= 7; ++i)
+    if (int rc = canvas_map_create(T->map_act[i], T->act[i], batch, T->d.Hc, T->d.Wc)) {
+      trainer_free(T);
+      return rc;
+    }
+  for (int i = 0; i < 2; ++i)
+    if (int rc = canvas_map_create(T->map_dp[i], T->dp[i], batch, T->d.Hc, T->d.Wc)) {
+      trainer_free(T);
+      return rc;
+    }
   if (int rc = prep(T)) {
     trainer_free(T);
     return rc;
@@ -384,8 +396,8 @@ int pnp_cnn_train_step(pnp_cnn_trainer* T, const float* u, const float* noise, d
                                 T->act[1]))
     return rc;
   for (int k = 1; k <= 6; ++k)
-    if (int rc = conv64_launch(s, T->act[k], T->act[k + 1], T->wf + (size_t)(k - 1) * NWM, T->bias + k * CH,
-                               T->tiles, T->n_tiles, d.Hc, d.Wc, 0, nullptr, T->status))
+    if (int rc = conv64_launch(s, T->map_act[k], T->act[k], T->act[k + 1], T->wf + (size_t)(k - 1) * NWM,
+                               T->bias + k * CH, T->tiles, T->n_tiles, d.Hc, d.Wc, 0, nullptr, T->status))
       return rc;
   PNP_CUDA(cudaMemsetAsync(T->loss, 0, sizeof(double), s));
   last_fwd_loss<<<nblocks(npx), 256, 0, s>>>(d, T->act[7], T->w8r, T->bias, T->z, u, T->gout, T->loss);
@@ -401,8 +413,8 @@ int pnp_cnn_train_step(pnp_cnn_trainer* T, const float* u, const float* noise, d
     float* gW = T->g + OFF_MID + (k - 1) * MID_STRIDE;
     wgrad64<<<dim3(wgb, 9), 256, 0, s>>>(d, T->dp[cur], T->act[k], gW, gW + NWM);
     PNP_CHECK_LAUNCH();
-    if (int rc = conv64_launch(s, T->dp[cur], T->dp[1 - cur], T->wb + (size_t)(k - 1) * NWM, nullptr, T->tiles,
-                               T->n_tiles, d.Hc, d.Wc, 1, T->act[k], T->status))
+    if (int rc = conv64_launch(s, T->map_dp[cur], T->dp[cur], T->dp[1 - cur], T->wb + (size_t)(k - 1) * NWM,
+                               nullptr, T->tiles, T->n_tiles, d.Hc, d.Wc, 1, T->act[k], T->status))
       return rc;
     cur = 1 - cur;
   }

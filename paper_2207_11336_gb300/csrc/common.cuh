@@ -164,9 +164,11 @@ int cnn_create(pnp_den* d, const float* weights_host, const int32_t* fr, int nfr
 void cnn_destroy(pnp_den* d);
 int cnn_status(pnp_den* d, int* flags);
 // shared with the CNN trainer (cnn_train.cu)
-int conv64_launch(cudaStream_t s, const __nv_bfloat16* in, __nv_bfloat16* out, const __nv_bfloat16* w_packed,
-                  const float* bias, const int4* tiles, int n_tiles, int Hc, int Wc, int mode,
-                  const __nv_bfloat16* mask, int* status);
+int conv64_launch(cudaStream_t s, const void* in_map, const __nv_bfloat16* in, __nv_bfloat16* out,
+                  const __nv_bfloat16* w_packed, const float* bias, const int4* tiles, int n_tiles, int Hc, int Wc,
+                  int mode, const __nv_bfloat16* mask, int* status);
+// TMA descriptor (a 128-byte CUtensorMap written to map_out) of an activation canvas [F][Hc][Wc][64]
+int canvas_map_create(void* map_out, const __nv_bfloat16* canvas, int F, int Hc, int Wc);
 int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, const int4* facets, int F, int Hc,
                      int Wc, const float* w1, const float* b1, __nv_bfloat16* out);
 int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc,
