@@ -7,15 +7,19 @@
 //
 // Facets.  Each facet core is extended by the halo (clipped at the image
 // border) and denoised on its own with zero padding at its edges; the cores are
-// stitched back.  All facets live in one activation "canvas" [F][Hc][Wc][64]
-// (NHWC, BF16); cells outside a facet are kept at zero so they act as padding.
+// stitched back.  All facets live in one BF16 activation "canvas" stored in
+// planes of 8 channels, [F][Hc][8][Wc][8] (canvas_index), so that one row of an
+// 8-channel block is contiguous: the TMA reads whole sectors and the epilogue
+// stores whole 512-byte runs per warp.  Cells outside a facet are kept at zero
+// so they act as padding.
 //
 // Kernels per application:
 //   cnn_first   z (FP32 image) -> canvas: layer 1 (1 -> 64) on CUDA cores;
 //   conv64_tc   canvas -> canvas: one 64 -> 64 layer as an implicit GEMM on the
 //               5th-generation tensor cores (tcgen05.mma, FP32 accumulators in
 //               tensor memory), one 128-pixel row segment per tile;
-//   cnn_last    canvas -> image: layer 8 (64 -> 1) on CUDA cores, fused with
+//   cnn_last    canvas -> image: layer 8 (64 -> 1) on CUDA cores from the same
+//               TMA-staged tile as the convolution, fused with
 //               D(z) = max(0, z - N(z)) on the facet cores and the FP64 norms.
 //
 // conv64_tc layout.  A tile is 2 x 128 output pixels (x0 .. x0+127 of rows y,
@@ -309,7 +313,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
         const int x = T.z + m;
         if (y >= A.Hc || x >= A.Wc) continue;
         const bool live = x < (T.w & 0xFFFF) && y < (T.w >> 16);  // outside the facet the canvas stays zero
-        const size_t pix = ((size_t)T.x * A.Hc + y) * A.Wc + x;
+        const size_t pix = canvas_index(T.x, y, x, 0, A.Hc, A.Wc);  // channel block q at pix + q * plane
+        const size_t plane = (size_t)A.Wc * 8;
         uint4 pk[8];
         uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
         if (A.mode == 0) {
@@ -329,9 +334,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
           }
         } else {
           uint4 mk[8];
-          const uint4* msrc = reinterpret_cast<const uint4*>(A.mask + pix * CH);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) mk[q] = msrc[q];
+          for (int q = 0; q < 8; ++q) mk[q] = *reinterpret_cast<const uint4*>(A.mask + pix + q * plane);
           const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(mk);
 #pragma unroll
           for (int c = 0; c < 64; c += 2) {
@@ -343,9 +347,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
             pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
           }
         }
-        uint4* dst = reinterpret_cast<uint4*>(A.out + pix * CH);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) dst[q] = pk[q];
+        for (int q = 0; q < 8; ++q) *reinterpret_cast<uint4*>(A.out + pix + q * plane) = pk[q];
       }
     }
   }
@@ -370,104 +373,167 @@ struct FirstArgs {
   __nv_bfloat16* out;
 };
 
-__global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
-  // grid (x chunks of 64, row y, facet f); warp w handles pixels x0 + w, x0 + w + 8, ...;
-  // lane l produces channels 2l and 2l + 1 (coalesced 128-B stores)
-  const int f = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * 64;
+constexpr int SEG_STRIDE = 9;  // uint4 per pixel in shared memory (8 channel blocks + 16 B of padding)
+
+__global__ void __launch_bounds__(128) cnn_first(FirstArgs A) {
+  // grid (x segments of 128, row y, facet f): thread m computes the 64 channels of pixel x0 + m;
+  // the block then writes each 8-channel plane of the segment as one contiguous 2-KB run
+  __shared__ __align__(16) uint4 seg[TILE_PX * SEG_STRIDE];
+  __shared__ __align__(16) float sw[CH * 9];  // [c / 4][tap][c % 4]: one float4 per (4 channels, tap)
+  __shared__ __align__(16) float sb[CH];
+  const int f = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * TILE_PX;
   const int4 fc = A.facets[f];  // R0, C0, Hf, Wf
   if (y >= fc.z || x0 >= fc.w) return;  // outside the facet: the canvas keeps its zeros
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  float w0[9], w1[9];
-#pragma unroll
-  for (int t = 0; t < 9; ++t) {
-    w0[t] = A.w1[(2 * lane) * 9 + t];
-    w1[t] = A.w1[(2 * lane + 1) * 9 + t];
+  for (int i = threadIdx.x; i < CH * 9; i += blockDim.x) {
+    const int ch = i / 9, t = i % 9;
+    sw[((ch >> 2) * 9 + t) * 4 + (ch & 3)] = A.w1[i];
   }
-  const float b0 = A.b1[2 * lane], b1 = A.b1[2 * lane + 1];
-  const float* zf = A.z + (size_t)f * A.zplane;
-  for (int x = x0 + wid; x < min(x0 + 64, fc.w); x += 8) {
-    float a0 = b0, a1 = b1;
+  if (threadIdx.x < CH) sb[threadIdx.x] = A.b1[threadIdx.x];
+  __syncthreads();
+  const float4* sw4 = reinterpret_cast<const float4*>(sw);
+  const float4* sb4 = reinterpret_cast<const float4*>(sb);
+  const int x = x0 + threadIdx.x;
+  uint4 pk[8];
+  if (x < fc.w) {
+    const float* zf = A.z + (size_t)f * A.zplane;
+    float zin[9];
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
       const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-      const float zt = (yy >= 0 && yy < fc.z && xx >= 0 && xx < fc.w) ? zf[(size_t)(fc.x + yy) * A.n + fc.y + xx] : 0.f;
-      a0 = fmaf(w0[t], zt, a0);
-      a1 = fmaf(w1[t], zt, a1);
+      zin[t] = (yy >= 0 && yy < fc.z && xx >= 0 && xx < fc.w) ? zf[(size_t)(fc.x + yy) * A.n + fc.y + xx] : 0.f;
     }
-    const size_t p = ((size_t)f * A.Hc + y) * A.Wc + x;
-    reinterpret_cast<__nv_bfloat162*>(A.out + p * CH)[lane] = __floats2bfloat162_rn(fmaxf(a0, 0.f), fmaxf(a1, 0.f));
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      uint32_t wv[4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int g = 2 * q + h;
+        float4 a = sb4[g];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+          const float4 w = sw4[g * 9 + t];
+          a.x = fmaf(w.x, zin[t], a.x);
+          a.y = fmaf(w.y, zin[t], a.y);
+          a.z = fmaf(w.z, zin[t], a.z);
+          a.w = fmaf(w.w, zin[t], a.w);
+        }
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(fmaxf(a.z, 0.f), fmaxf(a.w, 0.f));
+        wv[2 * h] = *reinterpret_cast<uint32_t*>(&h0);
+        wv[2 * h + 1] = *reinterpret_cast<uint32_t*>(&h1);
+      }
+      pk[q] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pk[q] = make_uint4(0u, 0u, 0u, 0u);
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) seg[threadIdx.x * SEG_STRIDE + q] = pk[q];
+  __syncthreads();
+  const size_t base = canvas_index(f, y, x0, 0, A.Hc, A.Wc), plane = (size_t)A.Wc * 8;
+  for (int i = threadIdx.x; i < TILE_PX * 8; i += blockDim.x) {
+    const int q = i / TILE_PX, px = i % TILE_PX;
+    *reinterpret_cast<uint4*>(A.out + base + q * plane + px * 8) = seg[px * SEG_STRIDE + q];
   }
 }
 
 // ------------------------------------------------------------ layer 8 (64 -> 1) + residual
 struct LastArgs {
-  const __nv_bfloat16* in;
   const float* z;
   const float* x_prev;
   float* out;
   int n;
   const int4* facets;
   const int4* cores;
-  int F, Hc, Wc;
-  const float* w8;  // [9][64]
+  const float* w8;  // [9][64] (BF16-rounded values)
   float b8;
   double* acc;
+  int* status;
 };
 
-__global__ void __launch_bounds__(256) cnn_last(LastArgs A) {
-  // grid (core row, facet); warp w handles core columns c0 + w, c0 + w + 8, ...;
-  // lane l holds channels 2l, 2l + 1 of the 64-channel activations
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
+
+__global__ void __launch_bounds__(256) cnn_last(LastArgs A, const __grid_constant__ CUtensorMap tmap) {
+  // grid (core column segments of 128, core row pairs, facet): one TMA load stages facet rows
+  // y0-1 .. y0+2, pixels x0-1 .. x0+128 of the layer-7 activations (zero outside the canvas), in
+  // the convolution's shared-memory layout; thread (r, m) then computes N(z) for core pixel
+  // (y0 + r, x0 + m) and writes max(0, z - N(z)) with its FP64 stopping-test terms
+  extern __shared__ __align__(1024) unsigned char st[];  // [STAGE_ROWS][8][STAGE_PX][8] BF16
+  __shared__ __align__(16) float sw[9 * CH];
+  __shared__ uint64_t full;
   __shared__ double red[2 * 8];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int f = blockIdx.y;
+  const int f = blockIdx.z;
   const int4 core = A.cores[f];  // r0, r1, c0, c1
   const int4 fc = A.facets[f];   // R0, C0, Hf, Wf
-  const int iy = core.x + blockIdx.x;
-  double s0 = 0.0, s1 = 0.0;
-  if (iy < core.y) {
-    float w0[9], w1[9];
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      w0[t] = A.w8[t * CH + 2 * lane];
-      w1[t] = A.w8[t * CH + 2 * lane + 1];
+  const int iy0 = core.x + blockIdx.y * OUT_ROWS, ix0 = core.z + blockIdx.x * TILE_PX;
+  if (iy0 >= core.y || ix0 >= core.w) return;
+  const int y0 = iy0 - fc.x, x0 = ix0 - fc.y;  // facet (= canvas) coordinates
+  if (threadIdx.x == 0) {
+    bar_init(&full, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bar_expect_tx(&full, A_BYTES);
+    tma_load_5d(st, &tmap, 0, x0 - 1, 0, y0 - 1, f, &full);
+  }
+  for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = A.w8[i];
+  __syncthreads();
+  if (!bar_wait(&full, 0)) {
+    if (threadIdx.x == 0) {
+      atomicOr(A.status, 4);
+      bar_wait(&full, 0);  // the copy must land before the block's shared memory is released
     }
-    const int y = iy - fc.x;
-    for (int ix = core.z + wid; ix < core.w; ix += 8) {
-      const int x = ix - fc.y;
-      float part = 0.f;
+    return;
+  }
+  const int r = threadIdx.x / TILE_PX, m = threadIdx.x % TILE_PX;
+  const int iy = iy0 + r, ix = ix0 + m;
+  double s0 = 0.0, s1 = 0.0;
+  if (iy < core.y && ix < core.w) {
+    const float4* sw4 = reinterpret_cast<const float4*>(sw);
+    float nz = A.b8;
+#pragma unroll 1
+    for (int t = 0; t < 9; ++t) {
+      const unsigned char* src = st + (r + t / 3) * ROW_BYTES + (m + t % 3) * 16;
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-        if (yy < 0 || yy >= fc.z || xx < 0 || xx >= fc.w) continue;
-        const float2 v = __bfloat1622float2(
-            reinterpret_cast<const __nv_bfloat162*>(A.in + (((size_t)f * A.Hc + yy) * A.Wc + xx) * CH)[lane]);
-        part = fmaf(w0[t], v.x, fmaf(w1[t], v.y, part));
+      for (int cb = 0; cb < 8; ++cb) {
+        const uint4 v = *reinterpret_cast<const uint4*>(src + cb * KB_BYTES);
+        const float4 wa = sw4[(t * CH + cb * 8) / 4], wb = sw4[(t * CH + cb * 8) / 4 + 1];
+        nz = fmaf(wa.x, bf16_lo(v.x), nz);
+        nz = fmaf(wa.y, bf16_hi(v.x), nz);
+        nz = fmaf(wa.z, bf16_lo(v.y), nz);
+        nz = fmaf(wa.w, bf16_hi(v.y), nz);
+        nz = fmaf(wb.x, bf16_lo(v.z), nz);
+        nz = fmaf(wb.y, bf16_hi(v.z), nz);
+        nz = fmaf(wb.z, bf16_lo(v.w), nz);
+        nz = fmaf(wb.w, bf16_hi(v.w), nz);
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      if (lane == 0) {
-        const size_t p = (size_t)iy * A.n + ix;
-        const float zv = A.z[p];
-        const float o = fmaxf(0.f, zv - (A.b8 + part));
-        A.out[p] = o;
-        s1 += (double)o * o;
-        if (!isfinite(zv)) s1 = __longlong_as_double(0x7ff8000000000000LL);
-        if (A.x_prev) {
-          const double dd = (double)o - A.x_prev[p];
-          s0 += dd * dd;
-        }
-      }
+    }
+    const size_t p = (size_t)iy * A.n + ix;
+    const float zv = A.z[p];
+    const float o = fmaxf(0.f, zv - nz);
+    A.out[p] = o;
+    s1 = (double)o * o;
+    if (!isfinite(zv)) s1 = __longlong_as_double(0x7ff8000000000000LL);
+    if (A.x_prev) {
+      const double dd = (double)o - A.x_prev[p];
+      s0 = dd * dd;
     }
   }
   if (A.acc) {
-    if (lane == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
       red[2 * wid] = s0;
       red[2 * wid + 1] = s1;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       double t0 = 0.0, t1 = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      for (int w = 0; w < 8; ++w) {
         t0 += red[2 * w];
         t1 += red[2 * w + 1];
       }
@@ -503,7 +569,7 @@ int make_canvas_map(CUtensorMap* map, const __nv_bfloat16* canvas, int F, int Hc
     enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   const cuuint64_t dims[5] = {8, (cuuint64_t)Wc, 8, (cuuint64_t)Hc, (cuuint64_t)F};
-  const cuuint64_t strides[4] = {(cuuint64_t)CH * 2, 16, (cuuint64_t)Wc * CH * 2, (cuuint64_t)Hc * Wc * CH * 2};
+  const cuuint64_t strides[4] = {16, (cuuint64_t)Wc * 16, (cuuint64_t)Wc * CH * 2, (cuuint64_t)Hc * Wc * CH * 2};
   const cuuint32_t box[5] = {8, (cuuint32_t)STAGE_PX, 8, (cuuint32_t)STAGE_ROWS, 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(canvas), dims, strides,
@@ -657,7 +723,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
   const int sms = sms_of_device();
   {
     FirstArgs F{z, n, 0, S->d_facets, S->F, S->Hc, S->Wc, S->d_w1, S->d_b, S->d_canvas[0]};
-    cnn_first<<<dim3((S->Wc + 63) / 64, S->Hc, S->F), 256, 0, s>>>(F);
+    cnn_first<<<dim3(S->Wc / TILE_PX, S->Hc, S->F), TILE_PX, 0, s>>>(F);
     PNP_CHECK_LAUNCH();
   }
   static bool attr = false;
@@ -676,10 +742,19 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
     cur = 1 - cur;
   }
   {
-    LastArgs L{S->d_canvas[cur], z, x_prev, out, n, S->d_facets, S->d_cores, S->F, S->Hc, S->Wc, S->d_w8, S->b8, acc};
-    int maxrows = 1;
-    for (int f = 0; f < S->F; ++f) maxrows = std::max(maxrows, S->fr1[f] - S->fr0[f]);
-    cnn_last<<<dim3(maxrows, S->F), 256, 0, s>>>(L);
+    LastArgs L{z, x_prev, out, n, S->d_facets, S->d_cores, S->d_w8, S->b8, acc, S->d_status};
+    int maxrows = 1, maxcols = 1;
+    for (int f = 0; f < S->F; ++f) {
+      maxrows = std::max(maxrows, S->fr1[f] - S->fr0[f]);
+      maxcols = std::max(maxcols, S->fc1[f] - S->fc0[f]);
+    }
+    static bool lattr = false;
+    if (!lattr) {
+      PNP_CUDA(cudaFuncSetAttribute(cnn_last, cudaFuncAttributeMaxDynamicSharedMemorySize, A_BYTES));
+      lattr = true;
+    }
+    const dim3 lgrid((maxcols + TILE_PX - 1) / TILE_PX, (maxrows + OUT_ROWS - 1) / OUT_ROWS, S->F);
+    cnn_last<<<lgrid, OUT_ROWS * TILE_PX, A_BYTES, s>>>(L, S->map[cur]);
     PNP_CHECK_LAUNCH();
   }
   return PNP_OK;
@@ -704,7 +779,7 @@ int conv64_launch(cudaStream_t s, const void* in_map, const __nv_bfloat16* in, _
 int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, const int4* facets, int F, int Hc,
                      int Wc, const float* w1, const float* b1, __nv_bfloat16* out) {
   FirstArgs A{z, n, zplane, facets, F, Hc, Wc, w1, b1, out};
-  cnn_first<<<dim3((Wc + 63) / 64, Hc, F), 256, 0, s>>>(A);
+  cnn_first<<<dim3(Wc / TILE_PX, Hc, F), TILE_PX, 0, s>>>(A);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }

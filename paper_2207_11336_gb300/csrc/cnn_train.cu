@@ -76,8 +76,8 @@ struct Dims {
   int B, s, Hc, Wc;
 };
 
-__device__ __forceinline__ size_t cpix(const Dims& d, int b, int y, int x) {
-  return ((size_t)b * d.Hc + y) * d.Wc + x;
+__device__ __forceinline__ size_t cidx(const Dims& d, int b, int y, int x, int c) {
+  return canvas_index(b, y, x, c, d.Hc, d.Wc);
 }
 
 // layer 8 forward, l1 loss and g = dL/dN = -sign(z - N - u) / count
@@ -98,11 +98,15 @@ __global__ void __launch_bounds__(256) last_fwd_loss(Dims d, const __nv_bfloat16
     for (int t = 0; t < 9; ++t) {
       const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
       if (yy < 0 || yy >= d.s || xx < 0 || xx >= d.s) continue;
-      const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(act7 + cpix(d, b, yy, xx) * CH);
-#pragma unroll 8
-      for (int c = 0; c < CH / 2; ++c) {
-        const float2 v = __bfloat1622float2(a[c]);
-        nz = fmaf(sw[t * CH + 2 * c], v.x, fmaf(sw[t * CH + 2 * c + 1], v.y, nz));
+#pragma unroll
+      for (int cb = 0; cb < 8; ++cb) {
+        const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(act7 + cidx(d, b, yy, xx, 8 * cb));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = 4 * cb + k;
+          const float2 v = __bfloat1622float2(a[k]);
+          nz = fmaf(sw[t * CH + 2 * c], v.x, fmaf(sw[t * CH + 2 * c + 1], v.y, nz));
+        }
       }
     }
     const float r = z[p] - nz - u[p];
@@ -134,19 +138,18 @@ __global__ void __launch_bounds__(256) last_bwd(Dims d, const __nv_bfloat16* __r
       const int yy = y - (t / 3 - 1), xx = x - (t % 3 - 1);
       gt[t] = (yy >= 0 && yy < d.s && xx >= 0 && xx < d.s) ? g[((int64_t)b * d.s + yy) * d.s + xx] : 0.f;
     }
-    const size_t base = cpix(d, b, y, x) * CH;
-    const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(act7 + base);
-    __nv_bfloat162* o = reinterpret_cast<__nv_bfloat162*>(dpre + base);
 #pragma unroll 4
     for (int c = 0; c < CH / 2; ++c) {
+      const size_t at = cidx(d, b, y, x, 2 * c);
       float v0 = 0.f, v1 = 0.f;
 #pragma unroll
       for (int t = 0; t < 9; ++t) {
         v0 = fmaf(sw[t * CH + 2 * c], gt[t], v0);
         v1 = fmaf(sw[t * CH + 2 * c + 1], gt[t], v1);
       }
-      const float2 av = __bfloat1622float2(a[c]);
-      o[c] = __floats2bfloat162_rn(av.x > 0.f ? v0 : 0.f, av.y > 0.f ? v1 : 0.f);
+      const float2 av = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(act7 + at));
+      *reinterpret_cast<__nv_bfloat162*>(dpre + at) =
+          __floats2bfloat162_rn(av.x > 0.f ? v0 : 0.f, av.y > 0.f ? v1 : 0.f);
     }
   }
 }
@@ -169,10 +172,10 @@ __global__ void __launch_bounds__(576) wgrad_onechannel(Dims d, int mode, const 
     const bool in = yy >= 0 && yy < d.s && xx >= 0 && xx < d.s;
     if (mode == 0) {
       const float gv = img[p];
-      if (in) acc = fmaf(gv, __bfloat162float(cv[cpix(d, b, yy, xx) * CH + c]), acc);
+      if (in) acc = fmaf(gv, __bfloat162float(cv[cidx(d, b, yy, xx, c)]), acc);
       bacc += gv;
     } else {
-      const float dv = __bfloat162float(cv[cpix(d, b, y, x) * CH + c]);
+      const float dv = __bfloat162float(cv[cidx(d, b, y, x, c)]);
       if (in) acc = fmaf(dv, img[((int64_t)b * d.s + yy) * d.s + xx], acc);
       bacc += dv;
     }
@@ -207,10 +210,10 @@ __global__ void __launch_bounds__(256) wgrad64(Dims d, const __nv_bfloat16* __re
       float2 dv = make_float2(0.f, 0.f), av = make_float2(0.f, 0.f);
       if (p < p1) {
         const int b = (int)(p / ((int64_t)d.s * d.s)), y = (int)((p / d.s) % d.s), x = (int)(p % d.s);
-        dv = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(dpre + cpix(d, b, y, x) * CH)[c2]);
+        dv = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(dpre + cidx(d, b, y, x, 2 * c2)));
         const int yy = y + dy, xx = x + dx;
         if (yy >= 0 && yy < d.s && xx >= 0 && xx < d.s)
-          av = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(act + cpix(d, b, yy, xx) * CH)[c2]);
+          av = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(act + cidx(d, b, yy, xx, 2 * c2)));
       }
       sd[q][2 * c2] = dv.x;
       sd[q][2 * c2 + 1] = dv.y;

@@ -167,7 +167,13 @@ int cnn_status(pnp_den* d, int* flags);
 int conv64_launch(cudaStream_t s, const void* in_map, const __nv_bfloat16* in, __nv_bfloat16* out,
                   const __nv_bfloat16* w_packed, const float* bias, const int4* tiles, int n_tiles, int Hc, int Wc,
                   int mode, const __nv_bfloat16* mask, int* status);
-// TMA descriptor (a 128-byte CUtensorMap written to map_out) of an activation canvas [F][Hc][Wc][64]
+// Activation canvases of the CNN hold BF16 values in planes of 8 channels:
+// [F][Hc][64 / 8][Wc][8], so that a row of one 8-channel block is contiguous (full-sector
+// TMA reads, coalesced epilogue stores); element (f, y, x, c) sits at canvas_index(...).
+__host__ __device__ __forceinline__ size_t canvas_index(int f, int y, int x, int c, int Hc, int Wc) {
+  return ((((size_t)f * Hc + y) * 8 + (c >> 3)) * Wc + x) * 8 + (c & 7);
+}
+// TMA descriptor (a 128-byte CUtensorMap written to map_out) of an activation canvas
 int canvas_map_create(void* map_out, const __nv_bfloat16* canvas, int F, int Hc, int Wc);
 int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, const int4* facets, int F, int Hc,
                      int Wc, const float* w1, const float* b1, __nv_bfloat16* out);
