@@ -35,9 +35,11 @@
 // The staged tile is one TMA transfer: the canvas is described to the TMA unit
 // as a 5-D tensor (8 channels, x, channel block, y, facet), whose box
 // (8, 130, 8, 4, 1) lands in shared memory in exactly that operand layout, with
-// zeros outside the canvas.  Warp roles: warps 0-3 drain tensor memory (bias,
-// ReLU, BF16, store), warp 4 allocates tensor memory and issues the MMAs (one
-// lane), warp 5 issues the TMA loads (one lane).  Two input buffers and two
+// zeros outside the canvas.  Warp roles: warps 0-15 drain tensor memory (bias,
+// ReLU, BF16, store; warp w takes the TMEM lane quarter w % 4, output row w / 8
+// and channel half (w / 4) % 2, so four warps per scheduler hide each other's
+// latency), warp 16 allocates tensor memory and issues the MMAs (one lane),
+// warp 17 issues the TMA loads (one lane).  Two input buffers and two
 // accumulators are pipelined with mbarriers; every wait is bounded.
 #include <algorithm>
 #include <cmath>
@@ -63,7 +65,9 @@ constexpr int A_BYTES = STAGE_ROWS * ROW_BYTES;         // 66560
 constexpr int TMEM_COLS = 2 * OUT_ROWS * CH;            // two tiles in flight x OUT_ROWS accumulators
 constexpr int B_TAP_BYTES = CH * CH * 2;                // 8192
 constexpr int B_BYTES = 9 * B_TAP_BYTES;                // 73728
-constexpr int CONV_THREADS = 6 * 32;  // 4 epilogue warps, 1 MMA warp, 1 TMA warp
+constexpr int EPI_WARPS = 16;                           // 4 lane quarters x OUT_ROWS x 2 channel halves
+constexpr int MMA_WARP = EPI_WARPS, TMA_WARP = EPI_WARPS + 1;
+constexpr int CONV_THREADS = (EPI_WARPS + 2) * 32;
 constexpr uint32_t CNN_WAIT_LIMIT = 1u << 26;
 
 struct CnnState {
@@ -220,12 +224,12 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
       bar_init(&a_full[b], 1);
       bar_init(&a_empty[b], 1);
       bar_init(&t_full[b], 1);
-      bar_init(&t_empty[b], 128);
+      bar_init(&t_empty[b], EPI_WARPS * 32);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
-  if (warp == 4) {
+  if (warp == MMA_WARP) {
     tmem_alloc(&s_tmem, TMEM_COLS);  // 2 tiles in flight x OUT_ROWS accumulators of 128 x 64 FP32
     tmem_relinquish();
   }
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
   const uint32_t tmem = s_tmem;
   const int stride = gridDim.x;
 
-  if (warp == 5) {
+  if (warp == TMA_WARP) {
     // ---------------- TMA producer: rows y0-1..y0+2, pixels x0-1..x0+128 of the tile's facet
     if (lane == 0) {
       int i = 0;
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
       for (int k = (i >= 2 ? i - 2 : 0); k < i; ++k) bar_wait(&a_full[k & 1], (k >> 1) & 1);
     }
     __syncwarp();
-  } else if (warp == 4) {
+  } else if (warp == MMA_WARP) {
     // ---------------- MMA issuer
     if (lane == 0) {
       int i = 0, last = -1;
@@ -289,8 +293,11 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue: tensor memory -> bias + ReLU -> BF16 -> canvas
-    const int m = threadIdx.x;  // TMEM lane = output pixel of the tile
+    // ---------------- epilogue: tensor memory -> bias + ReLU -> BF16 -> canvas.  Warp w reads
+    // TMEM lanes 32 (w % 4) .. + 31 (the lanes a warp may access), i.e. pixels 32 (w % 4) + lane,
+    // of output row (w / 8), channels 32 ((w / 4) % 2) .. + 31.
+    const int lq = warp & 3, orow = warp >> 3, half = (warp >> 2) & 1;
+    const int m = lq * 32 + lane;
     int i = 0;
     for (int tile = blockIdx.x; tile < A.n_tiles; tile += stride, ++i) {
       const int d = i & 1;
@@ -299,62 +306,47 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
       if (!__all_sync(0xffffffffu, ok)) break;
       tc_fence_after();
       const int4 T = A.tiles[tile];
-      for (int orow = 0; orow < OUT_ROWS; ++orow) {
-        uint32_t r0[32], r1[32];
-        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((d * OUT_ROWS + orow) * CH);
-        tmem_ld32(ta, r0);
-        tmem_ld32(ta + 32, r1);
-        tmem_wait_ld();
-        if (orow == OUT_ROWS - 1) {
-          tc_fence_before();
-          bar_arrive(&t_empty[d]);  // both accumulators of this tile are in registers now
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)((d * OUT_ROWS + orow) * CH + half * 32), r);
+      tmem_wait_ld();
+      tc_fence_before();
+      bar_arrive(&t_empty[d]);  // this thread's share of accumulator d is in registers
+      const int y = T.y + orow;
+      const int x = T.z + m;
+      if (y >= A.Hc || x >= A.Wc) continue;
+      const bool live = x < (T.w & 0xFFFF) && y < (T.w >> 16);  // outside the facet the canvas stays zero
+      const size_t pix = canvas_index(T.x, y, x, 32 * half, A.Hc, A.Wc);  // block q at pix + q * plane
+      const size_t plane = (size_t)A.Wc * 8;
+      uint4 pk[4];
+      uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+      if (A.mode == 0) {
+#pragma unroll
+        for (int c = 0; c < 32; c += 2) {
+          const float v0 = live ? fmaxf(0.f, __uint_as_float(r[c]) + s_bias[32 * half + c]) : 0.f;
+          const float v1 = live ? fmaxf(0.f, __uint_as_float(r[c + 1]) + s_bias[32 * half + c + 1]) : 0.f;
+          __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+          pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
         }
-        const int y = T.y + orow;
-        const int x = T.z + m;
-        if (y >= A.Hc || x >= A.Wc) continue;
-        const bool live = x < (T.w & 0xFFFF) && y < (T.w >> 16);  // outside the facet the canvas stays zero
-        const size_t pix = canvas_index(T.x, y, x, 0, A.Hc, A.Wc);  // channel block q at pix + q * plane
-        const size_t plane = (size_t)A.Wc * 8;
-        uint4 pk[8];
-        uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
-        if (A.mode == 0) {
+      } else {
+        uint4 mk[4];
 #pragma unroll
-          for (int c = 0; c < 32; c += 2) {
-            const float v0 = live ? fmaxf(0.f, __uint_as_float(r0[c]) + s_bias[c]) : 0.f;
-            const float v1 = live ? fmaxf(0.f, __uint_as_float(r0[c + 1]) + s_bias[c + 1]) : 0.f;
-            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-            pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
-          }
+        for (int q = 0; q < 4; ++q) mk[q] = *reinterpret_cast<const uint4*>(A.mask + pix + q * plane);
+        const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(mk);
 #pragma unroll
-          for (int c = 0; c < 32; c += 2) {
-            const float v0 = live ? fmaxf(0.f, __uint_as_float(r1[c]) + s_bias[32 + c]) : 0.f;
-            const float v1 = live ? fmaxf(0.f, __uint_as_float(r1[c + 1]) + s_bias[32 + c + 1]) : 0.f;
-            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-            pw[16 + c / 2] = *reinterpret_cast<uint32_t*>(&h);
-          }
-        } else {
-          uint4 mk[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) mk[q] = *reinterpret_cast<const uint4*>(A.mask + pix + q * plane);
-          const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(mk);
-#pragma unroll
-          for (int c = 0; c < 64; c += 2) {
-            const float a0 = __uint_as_float(c < 32 ? r0[c] : r1[c - 32]);
-            const float a1 = __uint_as_float(c + 1 < 32 ? r0[c + 1] : r1[c + 1 - 32]);
-            const float v0 = (live && __bfloat162float(mh[c]) > 0.f) ? a0 : 0.f;
-            const float v1 = (live && __bfloat162float(mh[c + 1]) > 0.f) ? a1 : 0.f;
-            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-            pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
-          }
+        for (int c = 0; c < 32; c += 2) {
+          const float v0 = (live && __bfloat162float(mh[c]) > 0.f) ? __uint_as_float(r[c]) : 0.f;
+          const float v1 = (live && __bfloat162float(mh[c + 1]) > 0.f) ? __uint_as_float(r[c + 1]) : 0.f;
+          __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+          pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
         }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) *reinterpret_cast<uint4*>(A.out + pix + q * plane) = pk[q];
       }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(A.out + pix + q * plane) = pk[q];
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 4) {
+  if (warp == MMA_WARP) {
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
   }
