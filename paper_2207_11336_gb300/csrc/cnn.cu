@@ -55,19 +55,21 @@ namespace pnp {
 namespace {
 
 constexpr int CH = 64;
-constexpr int TILE_PX = 128;
+constexpr int TILE_PX = 128;                            // output pixels per row segment (the MMA's M)
 constexpr int STAGE_PX = TILE_PX + 2;                   // x0-1 .. x0+128
 constexpr int KB_BYTES = STAGE_PX * 16;                 // one 8-channel block of a staged row (2080)
-constexpr int ROW_BYTES = 8 * KB_BYTES;                 // 8 channel blocks (16640)
-constexpr int OUT_ROWS = 2;                             // output rows per tile
-constexpr int STAGE_ROWS = OUT_ROWS + 2;                // staged input rows per tile
-constexpr int A_BYTES = STAGE_ROWS * ROW_BYTES;         // 66560
-constexpr int TMEM_COLS = 2 * OUT_ROWS * CH;            // two tiles in flight x OUT_ROWS accumulators
-constexpr int B_TAP_BYTES = CH * CH * 2;                // 8192
-constexpr int B_BYTES = 9 * B_TAP_BYTES;                // 73728
-constexpr int EPI_WARPS = 16;                           // 4 lane quarters x OUT_ROWS x 2 channel halves
+constexpr int ROW_BYTES = 8 * KB_BYTES;                 // one staged input row, 8 channel blocks (16640)
+constexpr int IN_SLOTS = 8;                             // ring of staged input rows
+constexpr int ACC_SLOTS = 8;                            // ring of output-row accumulators in tensor memory
+constexpr int TMEM_COLS = ACC_SLOTS * CH;               // 512: all of the SM's tensor memory
+constexpr int B_GROUP_BYTES = 3 * CH * 16;              // one (dx, kb) group: [dy=2 | dy=1 | dy=0] x 64 co x 8 ci
+constexpr int B_BYTES = 3 * 8 * B_GROUP_BYTES;          // 73728
+constexpr int CONV_SMEM = IN_SLOTS * ROW_BYTES + B_BYTES;  // 206848
+constexpr int EPI_WARPS = 16;                           // 2 row parities x 2 channel halves x 4 lane quarters
 constexpr int MMA_WARP = EPI_WARPS, TMA_WARP = EPI_WARPS + 1;
 constexpr int CONV_THREADS = (EPI_WARPS + 2) * 32;
+constexpr int LAST_ROWS = 2;                            // cnn_last: output rows per block
+constexpr int LAST_BYTES = (LAST_ROWS + 2) * ROW_BYTES; // its staged rows (66560)
 constexpr uint32_t CNN_WAIT_LIMIT = 1u << 26;
 
 struct CnnState {
@@ -76,8 +78,8 @@ struct CnnState {
   std::vector<int> R0, C0, Hf, Wf;       // extended facets
   int4* d_facets = nullptr;              // per facet: (R0, C0, Hf, Wf)
   int4* d_cores = nullptr;               // per facet: (r0, r1, c0, c1)
-  int4* d_tiles = nullptr;               // per tile: (f, y0, x0, Hf << 16 | Wf)
-  int n_tiles = 0;
+  int4* d_strips = nullptr;              // conv64_tc work list (conv_strips)
+  int n_strips = 0;
   __nv_bfloat16* d_canvas[2] = {nullptr, nullptr};
   float* d_w1 = nullptr;                 // [64][9]  (BF16-rounded values)
   float* d_b = nullptr;                  // [8][64] biases (layer 8 uses entry 0)
@@ -85,7 +87,8 @@ struct CnnState {
   float* d_w8 = nullptr;                 // [9][64] (BF16-rounded values)
   int* d_status = nullptr;
   float b8 = 0.f;                        // last layer's bias (host copy)
-  CUtensorMap map[2];                    // TMA descriptors of the two canvases
+  CUtensorMap map[2];                    // TMA descriptors of the two canvases, one-row boxes (conv64_tc)
+  CUtensorMap map_last[2];               // the same canvases, (LAST_ROWS + 2)-row boxes (cnn_last)
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -186,27 +189,57 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;                // base offset 0, relative LBO mode, no swizzle
 }
 
-// Instruction descriptor, kind::f16: FP32 D, BF16 A and B, both K-major, M = 128, N = 64.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CH >> 3) << 17) |
-                           ((uint32_t)(TILE_PX >> 4) << 24);
+// Instruction descriptor, kind::f16: FP32 D, BF16 A and B, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TILE_PX >> 4) << 24);
+}
+
+// One MMA target of an input row: consecutive accumulator slots (TMEM column), the weight rows
+// (B descriptor start offset, 16-byte units) and the instruction descriptor (N = 64 x rows).
+struct Piece {
+  uint32_t tcol, boff, idesc;
+};
+
+// K steps 1..11 of an input row (dx = dk / 4, K step kk = dk % 4), with compile-time offsets
+// added to the row's A descriptor and the pieces' B descriptors.
+template <int NP>
+__device__ __forceinline__ void mma_steps(uint32_t tmem, uint64_t arow, uint64_t bbase, const Piece (&pc)[2]) {
+#pragma unroll
+  for (int dk = 1; dk < 12; ++dk) {
+    const int dx = dk >> 2, kk = dk & 3;
+    const uint64_t ad = arow + (uint64_t)((2 * kk * KB_BYTES + dx * 16) >> 4);
+    const uint64_t bo = (uint64_t)(((dx * 8 + 2 * kk) * B_GROUP_BYTES) >> 4);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) mma_bf16(tmem + pc[i].tcol, ad, bbase + bo + pc[i].boff, pc[i].idesc, 1u);
+  }
+}
+
+// Pieces for output rows a..b of input row s (ring index of row 0 = g0): one, or two where the
+// accumulator ring wraps.
+__device__ __forceinline__ int make_pieces(int a, int b, int s, uint32_t g0, Piece (&pc)[2]) {
+  const uint32_t k = (g0 + a) % ACC_SLOTS;
+  const int n = b - a + 1, cnt = min(n, (int)(ACC_SLOTS - k));
+  pc[0] = Piece{k * CH, (uint32_t)((2 - (s - a)) * (CH * 16 >> 4)), idesc_n(cnt * CH)};
+  if (cnt == n) return 1;
+  pc[1] = Piece{0u, (uint32_t)((2 - (s - a - cnt)) * (CH * 16 >> 4)), idesc_n((n - cnt) * CH)};
+  return 2;
+}
 
 struct ConvArgs {
-  const __nv_bfloat16* in;
   __nv_bfloat16* out;
-  const __nv_bfloat16* w;  // packed [9][8][64][8]
+  const __nv_bfloat16* w;  // B operand, conv_wpack_index layout
   const float* bias;       // [64] (forward mode)
-  const int4* tiles;
-  int n_tiles, Hc, Wc;
+  const int4* strips;      // conv_strips
+  int n_strips, Hc, Wc;
   int* status;
   int mode;                    // 0: forward, out = ReLU(acc + bias); 1: backward data, out = acc * [mask > 0]
   const __nv_bfloat16* mask;   // backward data: activations whose ReLU mask gates the output (same canvas layout)
 };
 
 __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const __grid_constant__ CUtensorMap tmap) {
-  extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char* sa[2] = {sm, sm + A_BYTES};
-  unsigned char* sb = sm + 2 * A_BYTES;
-  __shared__ uint64_t a_full[2], a_empty[2], t_full[2], t_empty[2];
+  extern __shared__ __align__(1024) unsigned char sm[];  // [IN_SLOTS][ROW_BYTES] input ring, then B
+  unsigned char* sb = sm + IN_SLOTS * ROW_BYTES;
+  __shared__ uint64_t in_full[IN_SLOTS], in_empty[IN_SLOTS], t_full[ACC_SLOTS], t_empty[ACC_SLOTS];
   __shared__ uint32_t s_tmem;
   __shared__ float s_bias[CH];
   __shared__ volatile int s_abort;
@@ -220,17 +253,19 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
     if (threadIdx.x < CH) s_bias[threadIdx.x] = A.bias ? A.bias[threadIdx.x] : 0.f;  // no bias in backward mode
   }
   if (threadIdx.x == 0) {
-    for (int b = 0; b < 2; ++b) {
-      bar_init(&a_full[b], 1);
-      bar_init(&a_empty[b], 1);
-      bar_init(&t_full[b], 1);
-      bar_init(&t_empty[b], EPI_WARPS * 32);
+    for (int i = 0; i < IN_SLOTS; ++i) {
+      bar_init(&in_full[i], 1);
+      bar_init(&in_empty[i], 1);
+    }
+    for (int k = 0; k < ACC_SLOTS; ++k) {
+      bar_init(&t_full[k], 1);
+      bar_init(&t_empty[k], EPI_WARPS / 2 * 32);  // the warps of one row parity drain a row
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
   if (warp == MMA_WARP) {
-    tmem_alloc(&s_tmem, TMEM_COLS);  // 2 tiles in flight x OUT_ROWS accumulators of 128 x 64 FP32
+    tmem_alloc(&s_tmem, TMEM_COLS);  // ACC_SLOTS accumulators of 128 pixels x 64 channels, FP32
     tmem_relinquish();
   }
   fence_async_smem();  // the weights written above are read by the tensor cores (async proxy)
@@ -241,107 +276,134 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
   const int stride = gridDim.x;
 
   if (warp == TMA_WARP) {
-    // ---------------- TMA producer: rows y0-1..y0+2, pixels x0-1..x0+128 of the tile's facet
+    // ---------------- TMA producer: input rows ya-1 .. ya+R of each strip, pixels x0-1 .. x0+128
     if (lane == 0) {
-      int i = 0;
-      for (int tile = blockIdx.x; tile < A.n_tiles; tile += stride, ++i) {
-        const int b = i & 1;
-        if (i >= 2 && !bar_wait(&a_empty[b], ((i >> 1) - 1) & 1)) s_abort = 1;
-        if (s_abort) break;
-        const int4 T = A.tiles[tile];
-        bar_expect_tx(&a_full[b], A_BYTES);
-        tma_load_5d(sa[b], &tmap, 0, T.z - 1, 0, T.y - 1, T.x, &a_full[b]);
+      uint32_t L = 0;  // rows loaded so far (ring position)
+      for (int strip = blockIdx.x; strip < A.n_strips && !s_abort; strip += stride) {
+        const int4 S = A.strips[strip];
+        const int ya = S.z >> 16, R = S.z & 0xFFFF;
+        for (int s = 0; s < R + 2; ++s, ++L) {
+          const uint32_t slot = L % IN_SLOTS;
+          if (L >= IN_SLOTS && !bar_wait(&in_empty[slot], ((L / IN_SLOTS) - 1) & 1)) s_abort = 1;
+          if (s_abort) break;
+          bar_expect_tx(&in_full[slot], ROW_BYTES);
+          tma_load_5d(sm + slot * ROW_BYTES, &tmap, 0, S.y - 1, 0, ya - 1 + s, S.x, &in_full[slot]);
+        }
       }
       // every issued load must land before the CTA ends (bounded)
-      for (int k = (i >= 2 ? i - 2 : 0); k < i; ++k) bar_wait(&a_full[k & 1], (k >> 1) & 1);
+      for (uint32_t k = (L > IN_SLOTS ? L - IN_SLOTS : 0); k < L; ++k)
+        bar_wait(&in_full[k % IN_SLOTS], (k / IN_SLOTS) & 1);
     }
     __syncwarp();
   } else if (warp == MMA_WARP) {
-    // ---------------- MMA issuer
+    // ---------------- MMA issuer.  Input row s of a strip (staged row s = facet row ya-1+s) feeds
+    // output rows s-2, s-1, s with taps dy = 2, 1, 0.  With the weights of one (dx, kb) stored as
+    // [dy=2 | dy=1 | dy=0], the output rows r_lo..r_hi take the contiguous weight rows from block
+    // 2-(s-r_lo) on, and their accumulators are consecutive ring slots: one MMA of N = 64 x rows
+    // (split where the ring wraps) per (dx, K step).  A fresh output row (r = s) starts with
+    // accumulate = 0 in its own MMA on the first K step.
     if (lane == 0) {
-      int i = 0, last = -1;
-      for (int tile = blockIdx.x; tile < A.n_tiles; tile += stride, ++i) {
-        const int b = i & 1, d = i & 1;
-        if (!bar_wait(&a_full[b], (i >> 1) & 1)) s_abort = 1;
-        if (i >= 2 && !bar_wait(&t_empty[d], ((i >> 1) - 1) & 1)) s_abort = 1;
-        if (s_abort) break;
-        fence_async_smem();  // the tile was written by cp.async (generic proxy); the MMAs read it (async proxy)
-        tc_fence_after();
-        // descriptors differ only in their start address (16-B units in the low bits), so each
-        // MMA adds a compile-time offset to a base descriptor (addresses stay below 2^18 B)
-        const uint64_t adesc0 = smem_desc(su32(sa[b]), KB_BYTES, 128);
-        const uint64_t bdesc0 = smem_desc(su32(sb), 1024, 128);
-#pragma unroll
-        for (int r = 0; r < OUT_ROWS; ++r) {
-          const uint32_t dt = tmem + (uint32_t)((d * OUT_ROWS + r) * CH);
-#pragma unroll
-          for (int tap = 0; tap < 9; ++tap) {
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint32_t aoff = (uint32_t)((r + tap / 3) * ROW_BYTES + 2 * kk * KB_BYTES + (tap % 3) * 16);
-              const uint32_t boff = (uint32_t)(tap * B_TAP_BYTES + 2 * kk * 1024);
-              mma_bf16(dt, adesc0 + (aoff >> 4), bdesc0 + (boff >> 4), IDESC, (tap | kk) ? 1u : 0u);
-            }
+      const uint64_t adesc0 = smem_desc(su32(sm), KB_BYTES, 128);
+      const uint64_t bdesc0 = smem_desc(su32(sb), B_GROUP_BYTES, 128);
+      uint32_t L = 0, g0 = 0;  // input rows consumed; ring index of the strip's first output row
+      for (int strip = blockIdx.x; strip < A.n_strips && !s_abort; strip += stride) {
+        const int4 S = A.strips[strip];
+        const int R = S.z & 0xFFFF;
+        for (int s = 0; s < R + 2; ++s, ++L) {
+          const uint32_t slot = L % IN_SLOTS;
+          if (!bar_wait(&in_full[slot], (L / IN_SLOTS) & 1)) s_abort = 1;
+          const bool fresh = s < R;
+          if (fresh) {
+            const uint32_t g = g0 + s;
+            if (g >= ACC_SLOTS && !bar_wait(&t_empty[g % ACC_SLOTS], ((g / ACC_SLOTS) - 1) & 1)) s_abort = 1;
           }
+          if (s_abort) break;
+          tc_fence_after();
+          const int r_lo = max(0, s - 2), r_hi = min(R - 1, s);
+          const uint64_t arow = adesc0 + (uint64_t)((slot * ROW_BYTES) >> 4);
+          Piece pc[2];
+          const int np = make_pieces(r_lo, r_hi, s, g0, pc);
+          // first K step (dx = 0, kk = 0): a fresh row starts its accumulator (accumulate = 0)
+          if (fresh) {
+            if (r_hi > r_lo) {
+              Piece p0[2];
+              const int n0 = make_pieces(r_lo, r_hi - 1, s, g0, p0);
+              for (int i = 0; i < n0; ++i) mma_bf16(tmem + p0[i].tcol, arow, bdesc0 + p0[i].boff, p0[i].idesc, 1u);
+            }
+            mma_bf16(tmem + ((g0 + r_hi) % ACC_SLOTS) * CH, arow, bdesc0 + 2 * (CH * 16 >> 4), idesc_n(CH), 0u);
+          } else {
+            for (int i = 0; i < np; ++i) mma_bf16(tmem + pc[i].tcol, arow, bdesc0 + pc[i].boff, pc[i].idesc, 1u);
+          }
+          if (np == 1)
+            mma_steps<1>(tmem, arow, bdesc0, pc);
+          else
+            mma_steps<2>(tmem, arow, bdesc0, pc);
+          mma_commit(&in_empty[slot]);                                 // the input slot may be refilled
+          if (s >= 2) mma_commit(&t_full[(g0 + s - 2) % ACC_SLOTS]);   // output row s-2 is complete
         }
-        mma_commit(&a_empty[b]);  // input buffer b may be refilled once these MMAs are done
-        mma_commit(&t_full[d]);   // accumulator d is ready for the epilogue
-        last = i;
+        g0 += R;
       }
       // the tensor memory is freed below only after the last MMAs have completed
-      if (last >= 0) bar_wait(&t_full[last & 1], (last >> 1) & 1);
+      if (L > 0) bar_wait(&in_empty[(L - 1) % IN_SLOTS], ((L - 1) / IN_SLOTS) & 1);
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue: tensor memory -> bias + ReLU -> BF16 -> canvas.  Warp w reads
-    // TMEM lanes 32 (w % 4) .. + 31 (the lanes a warp may access), i.e. pixels 32 (w % 4) + lane,
-    // of output row (w / 8), channels 32 ((w / 4) % 2) .. + 31.
-    const int lq = warp & 3, orow = warp >> 3, half = (warp >> 2) & 1;
+    // ---------------- epilogue: tensor memory -> bias + ReLU -> BF16 -> canvas.  Warp w drains the
+    // output rows of parity w / 8; it reads TMEM lanes 32 (w % 4) .. + 31 (the lanes a warp may
+    // access), i.e. pixels 32 (w % 4) + lane, channels 32 ((w / 4) % 2) .. + 31.
+    const int lq = warp & 3, par = warp >> 3, half = (warp >> 2) & 1;
     const int m = lq * 32 + lane;
-    int i = 0;
-    for (int tile = blockIdx.x; tile < A.n_tiles; tile += stride, ++i) {
-      const int d = i & 1;
-      const bool ok = !s_abort && bar_wait(&t_full[d], (i >> 1) & 1);
-      if (!ok) s_abort = 1;
-      if (!__all_sync(0xffffffffu, ok)) break;
-      tc_fence_after();
-      const int4 T = A.tiles[tile];
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)((d * OUT_ROWS + orow) * CH + half * 32), r);
-      tmem_wait_ld();
-      tc_fence_before();
-      bar_arrive(&t_empty[d]);  // this thread's share of accumulator d is in registers
-      const int y = T.y + orow;
-      const int x = T.z + m;
-      if (y >= A.Hc || x >= A.Wc) continue;
-      const bool live = x < (T.w & 0xFFFF) && y < (T.w >> 16);  // outside the facet the canvas stays zero
-      const size_t pix = canvas_index(T.x, y, x, 32 * half, A.Hc, A.Wc);  // block q at pix + q * plane
-      const size_t plane = (size_t)A.Wc * 8;
-      uint4 pk[4];
-      uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
-      if (A.mode == 0) {
-#pragma unroll
-        for (int c = 0; c < 32; c += 2) {
-          const float v0 = live ? fmaxf(0.f, __uint_as_float(r[c]) + s_bias[32 * half + c]) : 0.f;
-          const float v1 = live ? fmaxf(0.f, __uint_as_float(r[c + 1]) + s_bias[32 * half + c + 1]) : 0.f;
-          __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-          pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+    const size_t plane = (size_t)A.Wc * 8;
+    uint32_t g0 = 0;
+    bool stop = false;
+    for (int strip = blockIdx.x; strip < A.n_strips && !stop; strip += stride) {
+      const int4 S = A.strips[strip];
+      const int ya = S.z >> 16, R = S.z & 0xFFFF, Hf = S.w >> 16, Wf = S.w & 0xFFFF;
+      for (int r = (int)((g0 + par) & 1); r < R; r += 2) {  // rows whose ring index has parity par
+        const uint32_t g = g0 + r, k = g % ACC_SLOTS;
+        const bool ok = !s_abort && bar_wait(&t_full[k], (g / ACC_SLOTS) & 1);
+        if (!ok) s_abort = 1;
+        if (!__all_sync(0xffffffffu, ok)) {
+          stop = true;
+          break;
         }
-      } else {
-        uint4 mk[4];
+        tc_fence_after();
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(k * CH + half * 32), v);
+        tmem_wait_ld();
+        tc_fence_before();
+        bar_arrive(&t_empty[k]);  // this thread's share of the row is in registers
+        const int y = ya + r, x = S.y + m;
+        if (y >= A.Hc || x >= A.Wc) continue;
+        const bool live = x < Wf && y < Hf;  // outside the facet the canvas stays zero
+        const size_t pix = canvas_index(S.x, y, x, 32 * half, A.Hc, A.Wc);  // block q at pix + q * plane
+        uint4 pk[4];
+        uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+        if (A.mode == 0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) mk[q] = *reinterpret_cast<const uint4*>(A.mask + pix + q * plane);
-        const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(mk);
+          for (int c = 0; c < 32; c += 2) {
+            const float v0 = live ? fmaxf(0.f, __uint_as_float(v[c]) + s_bias[32 * half + c]) : 0.f;
+            const float v1 = live ? fmaxf(0.f, __uint_as_float(v[c + 1]) + s_bias[32 * half + c + 1]) : 0.f;
+            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+          }
+        } else {
+          uint4 mk[4];
 #pragma unroll
-        for (int c = 0; c < 32; c += 2) {
-          const float v0 = (live && __bfloat162float(mh[c]) > 0.f) ? __uint_as_float(r[c]) : 0.f;
-          const float v1 = (live && __bfloat162float(mh[c + 1]) > 0.f) ? __uint_as_float(r[c + 1]) : 0.f;
-          __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-          pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+          for (int q = 0; q < 4; ++q) mk[q] = *reinterpret_cast<const uint4*>(A.mask + pix + q * plane);
+          const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(mk);
+#pragma unroll
+          for (int c = 0; c < 32; c += 2) {
+            const float v0 = (live && __bfloat162float(mh[c]) > 0.f) ? __uint_as_float(v[c]) : 0.f;
+            const float v1 = (live && __bfloat162float(mh[c + 1]) > 0.f) ? __uint_as_float(v[c + 1]) : 0.f;
+            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+            pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+          }
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(A.out + pix + q * plane) = pk[q];
       }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(A.out + pix + q * plane) = pk[q];
+      g0 += R;
     }
   }
   tc_fence_before();
@@ -452,20 +514,20 @@ __global__ void __launch_bounds__(256) cnn_last(LastArgs A, const __grid_constan
   // y0-1 .. y0+2, pixels x0-1 .. x0+128 of the layer-7 activations (zero outside the canvas), in
   // the convolution's shared-memory layout; thread (r, m) then computes N(z) for core pixel
   // (y0 + r, x0 + m) and writes max(0, z - N(z)) with its FP64 stopping-test terms
-  extern __shared__ __align__(1024) unsigned char st[];  // [STAGE_ROWS][8][STAGE_PX][8] BF16
+  extern __shared__ __align__(1024) unsigned char st[];  // [LAST_ROWS + 2][8][STAGE_PX][8] BF16
   __shared__ __align__(16) float sw[9 * CH];
   __shared__ uint64_t full;
   __shared__ double red[2 * 8];
   const int f = blockIdx.z;
   const int4 core = A.cores[f];  // r0, r1, c0, c1
   const int4 fc = A.facets[f];   // R0, C0, Hf, Wf
-  const int iy0 = core.x + blockIdx.y * OUT_ROWS, ix0 = core.z + blockIdx.x * TILE_PX;
+  const int iy0 = core.x + blockIdx.y * LAST_ROWS, ix0 = core.z + blockIdx.x * TILE_PX;
   if (iy0 >= core.y || ix0 >= core.w) return;
   const int y0 = iy0 - fc.x, x0 = ix0 - fc.y;  // facet (= canvas) coordinates
   if (threadIdx.x == 0) {
     bar_init(&full, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    bar_expect_tx(&full, A_BYTES);
+    bar_expect_tx(&full, LAST_BYTES);
     tma_load_5d(st, &tmap, 0, x0 - 1, 0, y0 - 1, f, &full);
   }
   for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = A.w8[i];
@@ -549,9 +611,9 @@ float bf16_round(float f) {
   return o;
 }
 
-// The canvas [F][Hc][Wc][64] (BF16) as the 5-D tensor (8 ch, x, kb, y, f) whose (8, 130, 8, 4, 1)
-// box is the staged tile of conv64_tc in its shared-memory operand layout.
-int make_canvas_map(CUtensorMap* map, const __nv_bfloat16* canvas, int F, int Hc, int Wc) {
+// A canvas as the 5-D tensor (8 ch, x, kb, y, f); the box (8, 130, 8, rows, 1) lands in shared
+// memory as [row][kb][130 pixels][8 ch], the K-major operand layout of conv64_tc.
+int make_canvas_map(CUtensorMap* map, const __nv_bfloat16* canvas, int F, int Hc, int Wc, int rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   if (!enc) {
     void* fn = nullptr;
@@ -562,7 +624,7 @@ int make_canvas_map(CUtensorMap* map, const __nv_bfloat16* canvas, int F, int Hc
   }
   const cuuint64_t dims[5] = {8, (cuuint64_t)Wc, 8, (cuuint64_t)Hc, (cuuint64_t)F};
   const cuuint64_t strides[4] = {16, (cuuint64_t)Wc * 16, (cuuint64_t)Wc * CH * 2, (cuuint64_t)Hc * Wc * CH * 2};
-  const cuuint32_t box[5] = {8, (cuuint32_t)STAGE_PX, 8, (cuuint32_t)STAGE_ROWS, 1};
+  const cuuint32_t box[5] = {8, (cuuint32_t)STAGE_PX, 8, (cuuint32_t)rows, 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(canvas), dims, strides,
                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -621,15 +683,13 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   const int wmax = *std::max_element(S->Wf.begin(), S->Wf.end());
   S->Wc = (wmax + TILE_PX - 1) / TILE_PX * TILE_PX;
 
-  std::vector<int4> facets(S->F), cores(S->F), tiles;
+  std::vector<int4> facets(S->F), cores(S->F);
   for (int f = 0; f < S->F; ++f) {
     facets[f] = make_int4(S->R0[f], S->C0[f], S->Hf[f], S->Wf[f]);
     cores[f] = make_int4(S->fr0[f], S->fr1[f], S->fc0[f], S->fc1[f]);
-    for (int y = 0; y < S->Hf[f]; y += OUT_ROWS)
-      for (int x0 = 0; x0 < S->Wf[f]; x0 += TILE_PX)
-        tiles.push_back(make_int4(f, y, x0, (S->Hf[f] << 16) | S->Wf[f]));
   }
-  S->n_tiles = (int)tiles.size();
+  const std::vector<int4> strips = conv_strips(S->F, S->Hf.data(), S->Wf.data());
+  S->n_strips = (int)strips.size();
 
   // weights: layer shapes 64x1, 6 x 64x64, 1x64, each W[co][ci][3][3] then b[co]
   std::vector<float> w1(CH * 9), w8(9 * CH), bias(8 * CH, 0.f);
@@ -644,9 +704,8 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
     for (int co = 0; co < CH; ++co)
       for (int ci = 0; ci < CH; ++ci)
         for (int t = 0; t < 9; ++t) {
-          const size_t dst = (size_t)l * 9 * CH * CH + (size_t)t * CH * CH + (size_t)(ci / 8) * CH * 8 +
-                             (size_t)co * 8 + (ci % 8);
-          wmid[dst] = to_bf16_bits(W[off + ((size_t)co * CH + ci) * 9 + t]);
+          wmid[(size_t)l * 9 * CH * CH + conv_wpack_index(t / 3, t % 3, ci, co)] =
+              to_bf16_bits(W[off + ((size_t)co * CH + ci) * 9 + t]);
         }
     off += (size_t)CH * CH * 9;
     for (int co = 0; co < CH; ++co) bias[(l + 1) * CH + co] = W[off + co];
@@ -672,7 +731,7 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   }
   if (int rc = al((void**)&S->d_facets, S->F * sizeof(int4))) return rc;
   if (int rc = al((void**)&S->d_cores, S->F * sizeof(int4))) return rc;
-  if (int rc = al((void**)&S->d_tiles, std::max<size_t>(1, tiles.size()) * sizeof(int4))) return rc;
+  if (int rc = al((void**)&S->d_strips, std::max<size_t>(1, strips.size()) * sizeof(int4))) return rc;
   if (int rc = al((void**)&S->d_w1, w1.size() * 4)) return rc;
   if (int rc = al((void**)&S->d_w8, w8.size() * 4)) return rc;
   if (int rc = al((void**)&S->d_b, bias.size() * 4)) return rc;
@@ -680,15 +739,17 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   if (int rc = al((void**)&S->d_status, 4 * sizeof(int))) return rc;
   PNP_CUDA(cudaMemcpy(S->d_facets, facets.data(), S->F * sizeof(int4), cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_cores, cores.data(), S->F * sizeof(int4), cudaMemcpyHostToDevice));
-  if (!tiles.empty())
-    PNP_CUDA(cudaMemcpy(S->d_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!strips.empty())
+    PNP_CUDA(cudaMemcpy(S->d_strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_w1, w1.data(), w1.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_w8, w8.data(), w8.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_b, bias.data(), bias.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_wmid, wmid.data(), wmid.size() * 2, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemset(S->d_status, 0, 4 * sizeof(int)));
-  for (int i = 0; i < 2; ++i)
-    if (int rc = make_canvas_map(&S->map[i], S->d_canvas[i], S->F, S->Hc, S->Wc)) return rc;
+  for (int i = 0; i < 2; ++i) {
+    if (int rc = make_canvas_map(&S->map[i], S->d_canvas[i], S->F, S->Hc, S->Wc, 1)) return rc;
+    if (int rc = make_canvas_map(&S->map_last[i], S->d_canvas[i], S->F, S->Hc, S->Wc, LAST_ROWS + 2)) return rc;
+  }
   return PNP_OK;
 }
 
@@ -698,7 +759,7 @@ void cnn_destroy(pnp_den* d) {
   for (auto p : S->d_canvas) cudaFree(p);
   cudaFree(S->d_facets);
   cudaFree(S->d_cores);
-  cudaFree(S->d_tiles);
+  cudaFree(S->d_strips);
   cudaFree(S->d_w1);
   cudaFree(S->d_w8);
   cudaFree(S->d_b);
@@ -719,17 +780,16 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
     PNP_CHECK_LAUNCH();
   }
   static bool attr = false;
-  const int smem = 2 * A_BYTES + B_BYTES;
   if (!attr) {
-    PNP_CUDA(cudaFuncSetAttribute(conv64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PNP_CUDA(cudaFuncSetAttribute(conv64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM));
     attr = true;
   }
-  int cur = 0;  // (tiles hold OUT_ROWS output rows each)
+  int cur = 0;
   for (int l = 0; l < 6; ++l) {
-    ConvArgs C{S->d_canvas[cur], S->d_canvas[1 - cur], S->d_wmid + (size_t)l * 9 * CH * CH,
-               S->d_b + (l + 1) * CH, S->d_tiles, S->n_tiles, S->Hc, S->Wc, S->d_status, 0, nullptr};
-    const int grid = std::max(1, std::min(S->n_tiles, sms));
-    conv64_tc<<<grid, CONV_THREADS, smem, s>>>(C, S->map[cur]);
+    ConvArgs C{S->d_canvas[1 - cur], S->d_wmid + (size_t)l * 9 * CH * CH, S->d_b + (l + 1) * CH, S->d_strips,
+               S->n_strips, S->Hc, S->Wc, S->d_status, 0, nullptr};
+    const int grid = std::max(1, std::min(S->n_strips, sms));
+    conv64_tc<<<grid, CONV_THREADS, CONV_SMEM, s>>>(C, S->map[cur]);
     PNP_CHECK_LAUNCH();
     cur = 1 - cur;
   }
@@ -742,30 +802,42 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
     }
     static bool lattr = false;
     if (!lattr) {
-      PNP_CUDA(cudaFuncSetAttribute(cnn_last, cudaFuncAttributeMaxDynamicSharedMemorySize, A_BYTES));
+      PNP_CUDA(cudaFuncSetAttribute(cnn_last, cudaFuncAttributeMaxDynamicSharedMemorySize, LAST_BYTES));
       lattr = true;
     }
-    const dim3 lgrid((maxcols + TILE_PX - 1) / TILE_PX, (maxrows + OUT_ROWS - 1) / OUT_ROWS, S->F);
-    cnn_last<<<lgrid, OUT_ROWS * TILE_PX, A_BYTES, s>>>(L, S->map[cur]);
+    const dim3 lgrid((maxcols + TILE_PX - 1) / TILE_PX, (maxrows + LAST_ROWS - 1) / LAST_ROWS, S->F);
+    cnn_last<<<lgrid, LAST_ROWS * TILE_PX, LAST_BYTES, s>>>(L, S->map_last[cur]);
     PNP_CHECK_LAUNCH();
   }
   return PNP_OK;
 }
 
-int conv64_launch(cudaStream_t s, const void* in_map, const __nv_bfloat16* in, __nv_bfloat16* out,
-                  const __nv_bfloat16* w_packed, const float* bias, const int4* tiles, int n_tiles, int Hc, int Wc,
-                  int mode, const __nv_bfloat16* mask, int* status) {
+int conv64_launch(cudaStream_t s, const void* in_map, __nv_bfloat16* out, const __nv_bfloat16* w_packed,
+                  const float* bias, const int4* strips, int n_strips, int Hc, int Wc, int mode,
+                  const __nv_bfloat16* mask, int* status) {
   static bool attr = false;
-  const int smem = 2 * A_BYTES + B_BYTES;
   if (!attr) {
-    PNP_CUDA(cudaFuncSetAttribute(conv64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PNP_CUDA(cudaFuncSetAttribute(conv64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM));
     attr = true;
   }
-  ConvArgs C{in, out, w_packed, bias, tiles, n_tiles, Hc, Wc, status, mode, mask};
-  const int grid = std::max(1, std::min(n_tiles, sms_of_device()));
-  conv64_tc<<<grid, CONV_THREADS, smem, s>>>(C, *static_cast<const CUtensorMap*>(in_map));
+  ConvArgs C{out, w_packed, bias, strips, n_strips, Hc, Wc, status, mode, mask};
+  const int grid = std::max(1, std::min(n_strips, sms_of_device()));
+  conv64_tc<<<grid, CONV_THREADS, CONV_SMEM, s>>>(C, *static_cast<const CUtensorMap*>(in_map));
   PNP_CHECK_LAUNCH();
   return PNP_OK;
+}
+
+std::vector<int4> conv_strips(int F, const int* Hf, const int* Wf) {
+  std::vector<int4> out;
+  for (int f = 0; f < F; ++f) {
+    const int k = std::max(1, (Hf[f] + STRIP_ROWS - 1) / STRIP_ROWS);  // strips per column segment
+    for (int x0 = 0; x0 < Wf[f]; x0 += TILE_PX)
+      for (int i = 0; i < k; ++i) {
+        const int ya = (int)((int64_t)Hf[f] * i / k), yb = (int)((int64_t)Hf[f] * (i + 1) / k);
+        if (yb > ya) out.push_back(make_int4(f, x0, (ya << 16) | (yb - ya), (Hf[f] << 16) | Wf[f]));
+      }
+  }
+  return out;
 }
 
 int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, const int4* facets, int F, int Hc,
@@ -777,7 +849,7 @@ int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, cons
 }
 
 int canvas_map_create(void* map_out, const __nv_bfloat16* canvas, int F, int Hc, int Wc) {
-  return make_canvas_map(static_cast<CUtensorMap*>(map_out), canvas, F, Hc, Wc);
+  return make_canvas_map(static_cast<CUtensorMap*>(map_out), canvas, F, Hc, Wc, 1);
 }
 
 int cnn_status(pnp_den* d, int* flags) {

@@ -46,10 +46,10 @@ __global__ void prep_weights(const float* __restrict__ w, float* __restrict__ w1
     const int l = (int)(i / NWM), r = (int)(i % NWM);
     const int co = r / (CH * 9), ci = (r / 9) % CH, t = r % 9;
     const __nv_bfloat16 v = __float2bfloat16_rn(w[OFF_MID + l * MID_STRIDE + r]);
-    // forward operand B[t][ci/8][co][ci%8] = W[co][ci][t]
-    wf[(size_t)l * NWM + (size_t)t * CH * CH + (size_t)(ci / 8) * CH * 8 + co * 8 + ci % 8] = v;
-    // backward-data operand B'[8-t][co/8][ci][co%8] = W[co][ci][t]
-    wb[(size_t)l * NWM + (size_t)(8 - t) * CH * CH + (size_t)(co / 8) * CH * 8 + ci * 8 + co % 8] = v;
+    // forward operand: tap (dy, dx), input ci, output co
+    wf[(size_t)l * NWM + conv_wpack_index(t / 3, t % 3, ci, co)] = v;
+    // backward-data operand: the flipped tap (2 - dy, 2 - dx) with input and output channels swapped
+    wb[(size_t)l * NWM + conv_wpack_index(2 - t / 3, 2 - t % 3, co, ci)] = v;
   }
   if (i < NW1) w1r[i] = bf16r(w[OFF_W1 + i]);
   if (i < NW8) {
@@ -274,7 +274,7 @@ int nblocks(int64_t count, int threads = 256) {
 struct pnp_cnn_trainer {
   pnp::Dims d{};
   cudaStream_t stream = nullptr;
-  int n_tiles = 0, t = 0;
+  int n_strips = 0, t = 0;
   double lr = 1e-4, b1 = 0.9, b2 = 0.999, eps = 1e-8;
   float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
   float *w1r = nullptr, *w8r = nullptr, *bias = nullptr;
@@ -282,7 +282,7 @@ struct pnp_cnn_trainer {
   __nv_bfloat16* act[8] = {};
   __nv_bfloat16* dp[2] = {};
   float *z = nullptr, *gout = nullptr;
-  int4 *facets = nullptr, *tiles = nullptr;
+  int4 *facets = nullptr, *strips = nullptr;
   double* loss = nullptr;
   int* status = nullptr;
   alignas(64) unsigned char map_act[8][128];  // TMA descriptors of act[1..7]
@@ -295,7 +295,7 @@ namespace {
 void trainer_free(pnp_cnn_trainer* T) {
   if (!T) return;
   for (void* p : {(void*)T->w, (void*)T->g, (void*)T->m, (void*)T->v, (void*)T->w1r, (void*)T->w8r, (void*)T->bias,
-                  (void*)T->wf, (void*)T->wb, (void*)T->z, (void*)T->gout, (void*)T->facets, (void*)T->tiles,
+                  (void*)T->wf, (void*)T->wb, (void*)T->z, (void*)T->gout, (void*)T->facets, (void*)T->strips,
                   (void*)T->loss, (void*)T->status})
     cudaFree(p);
   for (auto p : T->act) cudaFree(p);
@@ -337,14 +337,11 @@ int pnp_cnn_trainer_create(pnp_cnn_trainer** out, const float* weights_host, int
             al((void**)&T->status, 4 * sizeof(int));
   for (int i = 1; ok && i <= 7; ++i) ok = al((void**)&T->act[i], canvas * 2);
   for (int i = 0; ok && i < 2; ++i) ok = al((void**)&T->dp[i], canvas * 2);
-  std::vector<int4> facets(batch), tiles;
-  for (int b = 0; b < batch; ++b) {
-    facets[b] = make_int4(0, 0, size, size);
-    for (int y = 0; y < size; y += 2)  // the convolution tiles hold two output rows
-      for (int x0 = 0; x0 < size; x0 += 128) tiles.push_back(make_int4(b, y, x0, (size << 16) | size));
-  }
-  T->n_tiles = (int)tiles.size();
-  ok = ok && al((void**)&T->tiles, tiles.size() * sizeof(int4));
+  std::vector<int4> facets(batch, make_int4(0, 0, size, size));
+  const std::vector<int> sides(batch, size);
+  const std::vector<int4> strips = conv_strips(batch, sides.data(), sides.data());
+  T->n_strips = (int)strips.size();
+  ok = ok && al((void**)&T->strips, strips.size() * sizeof(int4));
   if (!ok) {
     trainer_free(T);
     return fail(PNP_ERR_OOM, "trainer allocation failed");
@@ -357,7 +354,8 @@ int pnp_cnn_trainer_create(pnp_cnn_trainer** out, const float* weights_host, int
   for (int i = 1; e == cudaSuccess && i <= 7; ++i) e = cudaMemset(T->act[i], 0, canvas * 2);
   for (int i = 0; e == cudaSuccess && i < 2; ++i) e = cudaMemset(T->dp[i], 0, canvas * 2);
   if (e == cudaSuccess) e = cudaMemcpy(T->facets, facets.data(), batch * sizeof(int4), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(T->tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(T->strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaGetLastError();
     trainer_free(T);
@@ -399,8 +397,8 @@ int pnp_cnn_train_step(pnp_cnn_trainer* T, const float* u, const float* noise, d
                                 T->act[1]))
     return rc;
   for (int k = 1; k <= 6; ++k)
-    if (int rc = conv64_launch(s, T->map_act[k], T->act[k], T->act[k + 1], T->wf + (size_t)(k - 1) * NWM,
-                               T->bias + k * CH, T->tiles, T->n_tiles, d.Hc, d.Wc, 0, nullptr, T->status))
+    if (int rc = conv64_launch(s, T->map_act[k], T->act[k + 1], T->wf + (size_t)(k - 1) * NWM, T->bias + k * CH,
+                               T->strips, T->n_strips, d.Hc, d.Wc, 0, nullptr, T->status))
       return rc;
   PNP_CUDA(cudaMemsetAsync(T->loss, 0, sizeof(double), s));
   last_fwd_loss<<<nblocks(npx), 256, 0, s>>>(d, T->act[7], T->w8r, T->bias, T->z, u, T->gout, T->loss);
@@ -416,8 +414,8 @@ int pnp_cnn_train_step(pnp_cnn_trainer* T, const float* u, const float* noise, d
     float* gW = T->g + OFF_MID + (k - 1) * MID_STRIDE;
     wgrad64<<<dim3(wgb, 9), 256, 0, s>>>(d, T->dp[cur], T->act[k], gW, gW + NWM);
     PNP_CHECK_LAUNCH();
-    if (int rc = conv64_launch(s, T->map_dp[cur], T->dp[cur], T->dp[1 - cur], T->wb + (size_t)(k - 1) * NWM,
-                               nullptr, T->tiles, T->n_tiles, d.Hc, d.Wc, 1, T->act[k], T->status))
+    if (int rc = conv64_launch(s, T->map_dp[cur], T->dp[1 - cur], T->wb + (size_t)(k - 1) * NWM, nullptr,
+                               T->strips, T->n_strips, d.Hc, d.Wc, 1, T->act[k], T->status))
       return rc;
     cur = 1 - cur;
   }

@@ -164,9 +164,20 @@ int cnn_create(pnp_den* d, const float* weights_host, const int32_t* fr, int nfr
 void cnn_destroy(pnp_den* d);
 int cnn_status(pnp_den* d, int* flags);
 // shared with the CNN trainer (cnn_train.cu)
-int conv64_launch(cudaStream_t s, const void* in_map, const __nv_bfloat16* in, __nv_bfloat16* out,
-                  const __nv_bfloat16* w_packed, const float* bias, const int4* tiles, int n_tiles, int Hc, int Wc,
-                  int mode, const __nv_bfloat16* mask, int* status);
+// B operand of the 64 -> 64 convolution: weight W[co][ci][dy][dx] at
+// [dx][ci / 8][2 - dy][co][ci % 8], so that for one (dx, 8-channel block) the three dy taps are
+// consecutive 64-row blocks in descending dy (one MMA serves up to three output rows).
+__host__ __device__ __forceinline__ size_t conv_wpack_index(int dy, int dx, int ci, int co) {
+  return ((((size_t)dx * 8 + (ci >> 3)) * 3 + (2 - dy)) * 64 + co) * 8 + (ci & 7);
+}
+constexpr int STRIP_ROWS = 32;  // target output rows per convolution work unit
+// Work list of conv64_tc: per facet, 128-column segments split into strips of about STRIP_ROWS
+// output rows; each entry is (facet, x0, ya << 16 | rows, Hf << 16 | Wf).
+std::vector<int4> conv_strips(int F, const int* Hf, const int* Wf);
+// the convolution reads its input through the TMA descriptor in_map (canvas_map_create)
+int conv64_launch(cudaStream_t s, const void* in_map, __nv_bfloat16* out, const __nv_bfloat16* w_packed,
+                  const float* bias, const int4* strips, int n_strips, int Hc, int Wc, int mode,
+                  const __nv_bfloat16* mask, int* status);
 // Activation canvases of the CNN hold BF16 values in planes of 8 channels:
 // [F][Hc][64 / 8][Wc][8], so that a row of one 8-channel block is contiguous (full-sector
 // TMA reads, coalesced epilogue stores); element (f, y, x, c) sits at canvas_index(...).
