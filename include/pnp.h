@@ -225,6 +225,10 @@ int pnp_cnn_train_step(pnp_cnn_trainer* trainer, const float* u, const float* no
  * PNP_ERR_TIMEOUT if a bounded device wait gave up during training. */
 int pnp_cnn_trainer_read(pnp_cnn_trainer* trainer, float* weights_host, float* grads_host, int clear_grads);
 
+/* Set the Adam step size used by later pnp_cnn_train_step calls (lr > 0); the
+ * moment estimates and the step count are kept. */
+int pnp_cnn_trainer_set_lr(pnp_cnn_trainer* trainer, double lr);
+
 /* Number of FP32 parameters of the CNN (weights and biases of the 8 layers). */
 int64_t pnp_cnn_num_params(void);
 

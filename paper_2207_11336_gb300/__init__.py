@@ -31,7 +31,7 @@ EXPORTED = [
     "pnp_last_error", "pnp_kernel_launch_count", "pnp_plan_set_timing", "pnp_plan_read_timing",
     "pnp_plan_device_status", "pnp_haar_denoise_noalloc", "pnp_den_device_status",
     "pnp_cnn_trainer_create", "pnp_cnn_trainer_destroy", "pnp_cnn_train_step", "pnp_cnn_trainer_read",
-    "pnp_cnn_num_params",
+    "pnp_cnn_num_params", "pnp_cnn_trainer_set_lr",
 ]
 
 
@@ -96,6 +96,7 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_cnn_train_step.argtypes = [vp, vp, vp, dbl, i32, C.POINTER(dbl)]
     L.pnp_cnn_trainer_read.argtypes = [vp, vp, vp, i32]
     L.pnp_cnn_num_params.restype = i64
+    L.pnp_cnn_trainer_set_lr.argtypes = [vp, dbl]
     L.pnp_plan_read_timing.argtypes = [vp, vp, vp]
     L.pnp_last_error.restype = C.c_char_p
     L.pnp_kernel_launch_count.restype = i64
@@ -104,7 +105,7 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
                  "pnp_den_create_cnn", "denoise", "pnp_fb_run", "pnp_plan_set_timing",
                  "pnp_plan_read_timing", "pnp_plan_device_status", "pnp_haar_denoise_noalloc",
                  "pnp_den_device_status", "pnp_cnn_trainer_create", "pnp_cnn_train_step",
-                 "pnp_cnn_trainer_read"):
+                 "pnp_cnn_trainer_read", "pnp_cnn_trainer_set_lr"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -375,6 +376,10 @@ class CnnTrainer:
         _check(lib().pnp_cnn_train_step(self._h, _ptr(u), _ptr(noise), float(sigma), 1 if update else 0,
                                         C.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
+
+    def set_lr(self, lr: float):
+        """Adam step size for the following steps (moments are kept)."""
+        _check(lib().pnp_cnn_trainer_set_lr(self._h, float(lr)))
 
     def read(self, weights=True, grads=False, clear_grads=False):
         """(params or None, flat gradients or None) from the device."""

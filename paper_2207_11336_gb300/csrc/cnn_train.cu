@@ -452,6 +452,12 @@ int pnp_cnn_trainer_read(pnp_cnn_trainer* T, float* weights_host, float* grads_h
   return PNP_OK;
 }
 
+int pnp_cnn_trainer_set_lr(pnp_cnn_trainer* T, double lr) {
+  if (!T || !(lr > 0)) return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  T->lr = lr;
+  return PNP_OK;
+}
+
 int64_t pnp_cnn_num_params(void) { return NPARAM; }
 
 }  // extern "C"

@@ -1,0 +1,168 @@
+"""Train the residual CNN denoiser of the learned loop on the GPU (App. C).
+
+The training noise level follows the heuristic sigma = tau / (alpha sqrt(2L))
+(Eq. sigma) of the imaging problem the denoiser is meant for: the workload's
+operator and noisy data are built on the GPU and L, beta and alpha come from
+``heuristics.imaging_parameters``.  The training images are seeded synthetic
+peak-normalised skies (points and Gaussian blobs with log-uniform intensities
+down to 1e-5, ``synth.training_image``), standing in for the paper's training
+database, with random dihedral transforms.  Each step draws z = u + sigma n with
+n from ``torch.randn`` (passed in as an input) and takes one Adam step on the
+l1 loss through the library's own forward and backward kernels
+(``CnnTrainer``); the step size follows a cosine decay.
+
+    python -m paper_2207_11336_gb300.train_denoiser --workload C3 \\
+        --out paper_2207_11336_gb300/weights/dncnn_C3.npz
+"""
+from __future__ import annotations
+
+import argparse
+import multiprocessing as mp
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def _pool_chunk(args):
+    size, count, seed = args
+    import synth
+    rng = np.random.default_rng(seed)
+    return np.stack([synth.training_image(size, rng) for _ in range(count)]).astype(np.float32)
+
+
+def image_pool(count: int, size: int, seed: int = 0, workers: int | None = None) -> np.ndarray:
+    """count seeded training images (float32, count x size x size), built in a spawn pool."""
+    chunk = 250
+    seeds = np.random.SeedSequence([seed, 0x7A11]).spawn((count + chunk - 1) // chunk)
+    jobs = [(size, min(chunk, count - i * chunk), s) for i, s in enumerate(seeds)]
+    workers = workers or max(1, min(len(jobs), (os.cpu_count() or 2)))
+    with mp.get_context("spawn").Pool(workers) as pool:
+        parts = pool.map(_pool_chunk, jobs)
+    return np.concatenate(parts)
+
+
+def noisy_problem(name: str, stream=None):
+    """(problem dict, plan, x_true, y, tau) for a benchmark workload: y = Phi x_true + tau n."""
+    import torch
+    import synth
+    import paper_2207_11336_gb300 as pnp
+    prob = synth.make_problem(name)
+    nblocks = int(prob["block"].max()) + 1
+    plan = pnp.Plan(prob["n"], prob["K"], prob["omega"], prob["w"], prob["dl"], prob["J_per_row"],
+                    block=prob["block"], nblocks=nblocks, stream=stream)
+    x_true = torch.from_numpy(prob["x_true"].astype(np.float32)).cuda()
+    y0 = plan.phi_forward(x_true)
+    norm_y0 = float(torch.linalg.vector_norm(y0.to(torch.complex128)).item())
+    tau = synth.noise_std_for_isnr(norm_y0, prob["M"], prob["isnr_db"])
+    y = (y0 + tau * torch.from_numpy(prob["noise"].astype(np.complex64)).cuda()).contiguous()
+    return prob, plan, x_true, y, tau
+
+
+def train(pool, sigma: float, steps: int, batch: int = 16, lr: float = 5e-4, lr_min: float = 1e-5,
+          seed: int = 0, params=None, log_every: int = 200, log=print):
+    """Adam on the l1 loss over random dihedral transforms of pool images; returns (params, history)."""
+    import torch
+    import synth
+    import paper_2207_11336_gb300 as pnp
+    N, s, _ = pool.shape
+    if params is None:
+        params = synth.cnn_init(synth.rng_for("train"), 64, 8, last_scale=0.01)
+    tr = pnp.CnnTrainer(params, batch, s, lr=lr)
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    hist = []
+    t0 = time.perf_counter()
+    run = 0.0
+    for it in range(steps):
+        cur = lr_min + 0.5 * (lr - lr_min) * (1.0 + np.cos(np.pi * it / max(steps - 1, 1)))
+        tr.set_lr(cur)
+        idx = torch.randint(0, N, (batch,), device="cuda", generator=gen)
+        u = pool[idx]
+        k = int(torch.randint(0, 8, (1,), generator=gen, device="cuda").item())
+        if k & 4:
+            u = u.transpose(1, 2)
+        u = torch.rot90(u, k & 3, dims=(1, 2)).contiguous()
+        noise = torch.randn((batch, s, s), device="cuda", generator=gen)
+        want = (it + 1) % log_every == 0 or it == steps - 1
+        loss = tr.step(u, noise, sigma, update=True, want_loss=want)
+        if want:
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            hist.append((it + 1, loss, el))
+            log(f"step {it + 1:6d}  loss {loss:.4e}  lr {cur:.2e}  {el:7.1f} s")
+    out, _ = tr.read()
+    tr.close()
+    return out, hist
+
+
+def save(path: str, params, meta: dict):
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    arrs = {}
+    for i, (W, b) in enumerate(params):
+        arrs[f"W{i}"] = np.asarray(W, dtype=np.float32)
+        arrs[f"b{i}"] = np.asarray(b, dtype=np.float32)
+    for k, v in meta.items():
+        arrs[f"meta_{k}"] = np.asarray(v)
+    np.savez_compressed(path, **arrs)
+
+
+def load(path: str):
+    """(params as float64 (W, b) pairs, metadata dict) from ``save``'s file."""
+    d = np.load(path)
+    depth = sum(1 for k in d.files if k.startswith("W"))
+    params = [(d[f"W{i}"].astype(np.float64), d[f"b{i}"].astype(np.float64)) for i in range(depth)]
+    meta = {k[5:]: d[k].item() if d[k].ndim == 0 else d[k] for k in d.files if k.startswith("meta_")}
+    return params, meta
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--workload", default="C3", help="imaging problem whose heuristic sets sigma")
+    ap.add_argument("--sigma", type=float, default=None, help="override the heuristic noise level")
+    ap.add_argument("--images", type=int, default=20000)
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--lr", type=float, default=5e-4)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                                                  "dncnn_C3.npz"))
+    a = ap.parse_args(argv)
+    t0 = time.perf_counter()
+    pool_np = image_pool(a.images, a.size, a.seed)   # before any CUDA call (spawned workers)
+    print(f"pool: {pool_np.shape} in {time.perf_counter() - t0:.1f} s", flush=True)
+    import torch
+    meta = dict(workload=a.workload, images=a.images, size=a.size, batch=a.batch, steps=a.steps, lr=a.lr,
+                seed=a.seed)
+    if a.sigma is None:
+        from paper_2207_11336_gb300 import heuristics
+        import synth
+        prob, plan, _, y, tau = noisy_problem(a.workload)
+        v0 = torch.from_numpy(synth.rng_for("power").standard_normal((prob["n"],) * 2).astype(np.float32)).cuda()
+        hp = heuristics.imaging_parameters(plan, y, tau, v0)
+        plan.close()
+        del plan, y
+        torch.cuda.empty_cache()
+        sigma = hp["sigma"]
+        meta.update({f"heuristic_{k}": v for k, v in hp.items()})
+        print("heuristics:", {k: float(v) for k, v in hp.items()}, flush=True)
+    else:
+        sigma = a.sigma
+    meta["sigma"] = sigma
+    pool = torch.from_numpy(pool_np).cuda()
+    params, hist = train(pool, sigma, a.steps, a.batch, a.lr, seed=a.seed,
+                         log=lambda s: print(s, flush=True))
+    meta["loss_history"] = np.array([h[1] for h in hist])
+    meta["train_seconds"] = hist[-1][2] if hist else 0.0
+    save(a.out, params, meta)
+    print("saved", a.out, flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
