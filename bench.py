@@ -1,14 +1,18 @@
 #!/usr/bin/env python
-"""PnP-FB imaging throughput on one GB300 (iterations per second).
+"""PnP-FB imaging throughput on one GB300 (iterations per second), learned vs plain.
 
 Workload (default): 4096^2 float32 image, 8192^2 complex64 grid, M = 2e7
 synthetic MeerKAT-like visibilities in 64 radial data blocks, w folded into G
 with J in {7, 9, 12, 16} by |w| quartile (complex64 weights, int32 columns),
-40 dB input SNR, plain Haar-threshold denoiser (gamma = 1.98/L,
-t = tau / sqrt(2L)).  A step is one full PnP-FB iteration (forward FFT with
-padding and grid correction, fused de-gridding + residual + gridding pass,
-adjoint FFT with the fused gradient step, Haar prox, positivity and FP64
-norms), replayed as a captured CUDA graph.
+40 dB input SNR.  A step is one full PnP-FB iteration (forward FFT with padding
+and grid correction, fused de-gridding + residual + gridding pass, adjoint FFT
+with the fused gradient step, denoiser, positivity and FP64 norms), replayed as
+a captured CUDA graph.  The timed loop is the learned one: the problem divided
+by the dirty-image peak bound alpha, the faceted residual CNN (4x4 uneven facets,
+32 px halo, BF16 tensor-core convolutions) trained by the library's kernels at
+the heuristic noise level.  The plain loop (one-level Haar soft threshold
+tau/sqrt(2L) + positivity) is timed beside it, and its SNR after 200
+iterations is the target of the learned loop's time-to-SNR.
 
 ``--gpus N`` under torchrun runs N independent replicas (the path does not
 shard across GPUs here); ``--impl reference`` times the FP64 CPU oracle on a
@@ -55,6 +59,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--kernel-case", choices=["gridding", "cnn"], default=None,
                     help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
+    ap.add_argument("--cnn-side", type=int, default=4096,
+                    help="image side of the cnn kernel case (4x4 facets scaled with it, 32 px halo)")
     return ap.parse_args()
 
 
@@ -64,6 +70,19 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def replica_aggregate(ms: float, steps: int, dist, ws: int, device: str = "cpu"):
+    """(max over ranks of the timed milliseconds, whole-job iterations per second).
+
+    Replicas run the same loop independently (the path is not sharded), so the
+    job's throughput is ws * steps over the slowest rank's time."""
+    if dist is not None and ws > 1:
+        import torch
+        tt = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    return ms, ws * steps / (ms / 1e3)
 
 
 def measured_peaks():
@@ -119,6 +138,30 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(self.samples)}
+
+
+def measured_bf16_peak():
+    """Dense BF16 TFLOP/s for a kernel timed alone (burst), from the measured peaks file."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), "measured (burst)"
+    return 1900.0, "fallback"
+
+
+CNN_FLOP_PER_PX = 2 * 9 * 64 + 6 * 2 * 9 * 64 * 64 + 2 * 9 * 64   # 1->64, 6 x 64->64, 64->1 (3x3)
+
+
+def _facet_pixels(n, facet_rows, facet_cols, halo):
+    """Pixels the faceted denoiser processes: every facet extended by the halo, clipped at the border."""
+    er = np.concatenate([[0], np.cumsum(facet_rows)])
+    ec = np.concatenate([[0], np.cumsum(facet_cols)])
+    px = 0
+    for a0, a1 in zip(er[:-1], er[1:]):
+        for b0, b1 in zip(ec[:-1], ec[1:]):
+            px += (min(n, a1 + halo) - max(0, a0 - halo)) * (min(n, b1 + halo) - max(0, b0 - halo))
+    return int(px)
 
 
 def src_hash(*names):
@@ -214,6 +257,48 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+WEIGHTS = os.path.join(ROOT, "paper_2207_11336_gb300", "weights", "dncnn_C3.npz")
+SNR_ITERS = 200          # the plain loop's SNR after this many iterations is the target
+SNR_CHUNK = 10           # the learned loop's SNR is checked every SNR_CHUNK iterations
+SNR_MAX_ITERS = 600
+
+
+def _snr_db(x_true, x):
+    import torch
+    xt = x_true.double()
+    return float(20.0 * torch.log10(torch.linalg.vector_norm(xt) / torch.linalg.vector_norm(xt - x.double())))
+
+
+def _timed_loop(plan, den, y, x, gamma, L, steps, stream, clocks=None):
+    """ms for ``steps`` graph-replayed iterations (x updated in place), kernel launches inside."""
+    import torch
+    import paper_2207_11336_gb300 as pnp
+    k0 = pnp.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    plan.fb_run(den, y, x0=x, gamma=gamma, L=L, max_iter=steps, check_every=steps, use_graph=True,
+                inplace=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1), pnp.kernel_launches() - k0
+
+
+def _run_to_snr(plan, den, y, x, gamma, L, x_true, scale, target, max_iters):
+    """Iterations (multiples of SNR_CHUNK) until SNR(scale * x) >= target; (iters or None, SNR trace)."""
+    trace = []
+    it = 0
+    while it < max_iters:
+        plan.fb_run(den, y, x0=x, gamma=gamma, L=L, max_iter=SNR_CHUNK, check_every=SNR_CHUNK,
+                    use_graph=True, inplace=True)
+        it += SNR_CHUNK
+        snr = _snr_db(x_true, scale * x)
+        trace.append((it, snr))
+        if target is not None and snr >= target:
+            return it, trace
+    return None, trace
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_env()
@@ -223,6 +308,8 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2207_11336_gb300 as pnp
+    from paper_2207_11336_gb300 import heuristics
+    from paper_2207_11336_gb300.train_denoiser import load as load_weights
     import synth
 
     wl = WORKLOADS[args.workload]
@@ -239,57 +326,94 @@ def run_gpu(args):
     noise = torch.from_numpy(prob["noise"].astype(np.complex64)).cuda()
     y = (y0 + tau * noise).contiguous()
     v0 = torch.from_numpy(synth.rng_for("power").standard_normal((n, n)).astype(np.float32)).cuda()
-    L, _ = plan.op_norm(v0, 1000, 1e-6)
-    gamma = 1.98 / L
-    t = tau / np.sqrt(2 * L)
-    den = pnp.HaarDenoiser(t, stream=stream)
-    x = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    hp = heuristics.imaging_parameters(plan, y, tau, v0)
+    L, gamma, t = hp["L"], hp["gamma"], hp["noise_level"]
+    haar = pnp.HaarDenoiser(t, stream=stream)
+
+    learned = os.path.exists(WEIGHTS) and "facet_rows" in prob
+    if learned:
+        params, wmeta = load_weights(WEIGHTS)
+        cnn = pnp.CnnDenoiser(params, n, facet_rows=prob["facet_rows"], facet_cols=prob["facet_cols"],
+                              halo=prob["halo"], stream=stream)
+        # App. C: the problem is divided by alpha so the denoiser sees a peak-normalised image
+        alpha = hp["alpha"]
+        y_s = (y / alpha).contiguous()
+    den, y_run = (cnn, y_s) if learned else (haar, y)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    # warm-up (also primes kernel attributes; graph capture happens inside each run)
-    plan.fb_run(den, y, x0=x, gamma=gamma, L=L, max_iter=max(args.warmup, 3), check_every=2,
+    steps = args.steps + (args.steps & 1)  # the graph replays iteration pairs
+    # ---- timed region: the benchmark loop (learned if weights are present, else plain)
+    x = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    plan.fb_run(den, y_run, x0=x, gamma=gamma, L=L, max_iter=max(args.warmup, 3), check_every=2,
                 use_graph=True, inplace=True)
     torch.cuda.synchronize()
     barrier()
-    k0 = pnp.kernel_launches()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    steps = args.steps + (args.steps & 1)  # the graph replays iteration pairs
     with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        _, st = plan.fb_run(den, y, x0=x, gamma=gamma, L=L, max_iter=steps, check_every=steps,
-                            use_graph=True, inplace=True)
-        ev1.record(stream)
-        torch.cuda.synchronize()
+        ms, launches = _timed_loop(plan, den, y_run, x, gamma, L, steps, stream)
     barrier()
-    launches = pnp.kernel_launches() - k0
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = ws * steps / (ms / 1e3)
+    ms, value = replica_aggregate(ms, steps, dist, ws, "cuda")
 
-    # kernel timing: eager replay of the same steps with CUDA events around each stage
+    # ---- the plain loop: timed the same way, and its SNR after SNR_ITERS iterations from zero
+    xp = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    plan.fb_run(haar, y, x0=xp, gamma=gamma, L=L, max_iter=4, check_every=2, use_graph=True, inplace=True)
+    ms_plain, _ = _timed_loop(plan, haar, y, xp, gamma, L, steps, stream)
+    xp.zero_()
+    _, trace_plain = _run_to_snr(plan, haar, y, xp, gamma, L, x_true, 1.0, None, SNR_ITERS)
+    snr_plain = trace_plain[-1][1]
+    plain = {"iter_per_s": ws * steps / (ms_plain / 1e3), "ms_per_iter": ms_plain / steps,
+             "snr_db_after_%d" % SNR_ITERS: snr_plain,
+             "time_to_snr_s": SNR_ITERS * ms_plain / steps / 1e3,
+             "snr_trace": [(i, round(s, 3)) for i, s in trace_plain[4::5]]}
+    comparison = {"plain": plain}
+    if learned:
+        xl = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+        it_l, trace_l = _run_to_snr(plan, cnn, y_s, xl, gamma, L, x_true, alpha, snr_plain, SNR_MAX_ITERS)
+        comparison["learned"] = {
+            "iter_per_s": value, "ms_per_iter": ms / steps, "alpha": alpha, "sigma_trained": wmeta.get("sigma"),
+            "sigma_heuristic": hp["sigma"], "iters_to_plain_snr": it_l,
+            "time_to_snr_s": None if it_l is None else it_l * ms / steps / 1e3,
+            "snr_db_final": trace_l[-1][1], "iters_run": trace_l[-1][0],
+            "snr_trace": [(i, round(s, 3)) for i, s in trace_l[::2]]}
+
+    # ---- kernel timing: eager replay with CUDA events around each operator stage
     plan.set_timing(True)
     kt = min(steps, 10)
-    plan.fb_run(den, y, x0=x, gamma=gamma, L=L, max_iter=kt, check_every=kt, use_graph=False,
-                inplace=True)
+    xk = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    plan.fb_run(haar, y, x0=xk, gamma=gamma, L=L, max_iter=kt, check_every=kt, use_graph=False, inplace=True)
     tim = plan.read_timing()
     plan.set_timing(False)
     g_ms, g_cnt = tim["gridding"]
     g_ms_launch = g_ms / max(g_cnt, 1)
-    wbytes = 8
-    alg_bytes = info["nnz"] * (wbytes + 4) + M * 8 + 2 * K * K * 8
+    alg_bytes = info["nnz"] * (8 + 4) + M * 8 + 2 * K * K * 8
     hbm, peak_kind = measured_peaks()
     achieved = alg_bytes / (g_ms_launch * 1e-3) / 1e9
+    roof_cnn = None
+    if learned:
+        zin = (x_true / alpha).contiguous()
+        zout = torch.empty_like(zin)
+        for _ in range(2):
+            cnn.denoise(zin, zout)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            cnn.denoise(zin, zout)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        d_ms = e0.elapsed_time(e1) / 5
+        px = _facet_pixels(n, prob["facet_rows"], prob["facet_cols"], prob["halo"])
+        flop = px * CNN_FLOP_PER_PX
+        bf16_peak, bf16_kind = measured_bf16_peak()
+        roof_cnn = {"bound": "tensor", "kernel": "faceted CNN denoiser (cnn_first + 6 x conv64_tc + cnn_last)",
+                    "achieved": flop / (d_ms * 1e-3) / 1e12, "peak": bf16_peak, "peak_kind": bf16_kind,
+                    "unit": "TFLOP/s", "frac": flop / (d_ms * 1e-3) / 1e12 / bf16_peak, "traffic": None,
+                    "flop_per_launch": flop, "ms_per_launch": d_ms}
 
-    # end to end through the public API with host buffers
-    y_host = y.cpu().pin_memory()
-    y_dev = torch.empty_like(y)
+    # ---- end to end through the public API with host buffers
+    y_host = y_run.cpu().pin_memory()
+    y_dev = torch.empty_like(y_run)
     torch.cuda.synchronize()
     e2e_steps = max(1, args.e2e_steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -306,13 +430,14 @@ def run_gpu(args):
 
     out = None
     if rank == 0:
+        desc = wl["desc"] + (", learned faceted CNN (4x4 facets, halo 32, BF16)" if learned else "")
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
                "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "impl": "gpu",
-               "config": {"workload": wl["desc"], "parallelism": f"replicas{ws}",
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16" if learned else "f32",
+               "data": "synthetic", "impl": "gpu",
+               "config": {"workload": desc, "parallelism": f"replicas{ws}",
                           "l2": "inputs larger than L2 (G %.1f GB)" % (info["nnz"] * 12 / 1e9),
-                          "nnz": info["nnz"], "denoiser": "haar", "graph": True},
+                          "nnz": info["nnz"], "denoiser": "cnn" if learned else "haar", "graph": True},
                "clocks": clk.summary(),
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": M * 8,
                        "d2h_bytes_per_step": 16},
@@ -322,14 +447,16 @@ def run_gpu(args):
                             "frac": achieved / hbm, "traffic": profiled_traffic("gridding.cu", wl["name"]),
                             "alg_bytes_per_launch": alg_bytes, "ms_per_launch": g_ms_launch,
                             "stage_ms_per_iter": {k: v[0] / max(v[1], 1) for k, v in tim.items()}},
-               "fb": {"L": L, "gamma": gamma, "t": t, "tau": tau, "rel_change": st.rel_change}}
+               "roofline_denoiser": roof_cnn,
+               "comparison": comparison,
+               "fb": {k: (float(v) if isinstance(v, (int, float, np.floating)) else v) for k, v in hp.items()}}
         if ws == 1 and not args.no_cpu_baseline:
             rows, y_rows = cpu_sample_inputs(prob, None, y.cpu().numpy().astype(np.complex128))
-            xs = x.cpu().numpy().astype(np.float64)
+            xs = xp.cpu().numpy().astype(np.float64)
             est, parts = oracle_sample(prob, rows, xs, y_rows, gamma, t)
             out["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                   "sample": f"one FP64 oracle iteration: full-size FFT pair, G "
-                                             f"restricted to {CPU_SAMPLE_ROWS} seeded rows (time "
+                                   "sample": f"one FP64 oracle iteration of the plain loop: full-size FFT "
+                                             f"pair, G restricted to {CPU_SAMPLE_ROWS} seeded rows (time "
                                              f"scaled by M/{CPU_SAMPLE_ROWS}); numpy FFT and scipy "
                                              f"CSR are single-threaded",
                                    "parts_s": parts, "host_cores": os.cpu_count()}
@@ -367,11 +494,11 @@ def run_kernel_case(args):
 
 
 def cnn_case(args):
-    """The faceted CNN denoiser on the 4096^2 workload: 16 uneven facets, 32 px halo."""
+    """The faceted CNN denoiser on the 4096^2 workload (or --cnn-side): 16 uneven facets, 32 px halo."""
     import torch
     import paper_2207_11336_gb300 as pnp
     import synth
-    prob = synth.make_problem("C3", M=16, with_sky=True)
+    prob = synth.make_problem("C3", M=16, n=args.cnn_side, with_sky=True)
     n = prob["n"]
     params = synth.cnn_init(synth.rng_for("train"), 64, 8, 0.1)
     den = pnp.CnnDenoiser(params, n, facet_rows=prob["facet_rows"], facet_cols=prob["facet_cols"], halo=32)
@@ -387,15 +514,9 @@ def cnn_case(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(args.steps, 1)
-    h = 32
-    edges_r = np.concatenate([[0], np.cumsum(prob["facet_rows"])])
-    edges_c = np.concatenate([[0], np.cumsum(prob["facet_cols"])])
-    px = 0
-    for a0, a1 in zip(edges_r[:-1], edges_r[1:]):
-        for b0, b1 in zip(edges_c[:-1], edges_c[1:]):
-            px += (min(n, a1 + h) - max(0, a0 - h)) * (min(n, b1 + h) - max(0, b0 - h))
-    flop = px * (2 * 9 * 64 + 6 * 2 * 9 * 64 * 64 + 2 * 9 * 64)
-    print(json.dumps({"case": "cnn 4096^2, 16 facets, halo 32", "ms": ms, "pixels_with_halo": int(px),
+    px = _facet_pixels(n, prob["facet_rows"], prob["facet_cols"], 32)
+    flop = px * CNN_FLOP_PER_PX
+    print(json.dumps({"case": f"cnn {n}^2, 16 facets, halo 32", "ms": ms, "pixels_with_halo": int(px),
                       "TFLOP_per_call": flop / 1e12, "TFLOPs": flop / ms / 1e9,
                       "status": den.device_status()}))
     return 0

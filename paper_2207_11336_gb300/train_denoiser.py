@@ -11,6 +11,16 @@ n from ``torch.randn`` (passed in as an input) and takes one Adam step on the
 l1 loss through the library's own forward and backward kernels
 (``CnnTrainer``); the step size follows a cosine decay.
 
+Noise units.  The heuristic sigma can sit far below the image peak (a dynamic
+range of ~1e6 for the 4096^2 workload), below what BF16 hidden activations
+resolve next to biases of the size Adam's steps give them.  The network is
+therefore trained on u / s at noise level sigma / s with s = 2^round(log2 sigma),
+i.e. in units of the noise, and s is folded back into the first and last layers
+(W1 / s, s W8, s b8), so the saved network acts on images at their own scale:
+z - s N(z / s).  With s a power of two the folding is exact in binary floating
+point, including the BF16 rounding of the weights, so inference and the oracle
+use the folded weights unchanged.
+
     python -m paper_2207_11336_gb300.train_denoiser --workload C3 \\
         --out paper_2207_11336_gb300/weights/dncnn_C3.npz
 """
@@ -64,9 +74,25 @@ def noisy_problem(name: str, stream=None):
     return prob, plan, x_true, y, tau
 
 
+def noise_unit(sigma: float) -> float:
+    """s = 2^round(log2 sigma): the power of two nearest the training noise level."""
+    return float(2.0 ** np.round(np.log2(sigma)))
+
+
+def fold_scale(params, s: float):
+    """Weights of z -> s N(z / s) for the network N given by params (exact for s a power of two)."""
+    out = [(np.array(W, dtype=np.float64), np.array(b, dtype=np.float64)) for W, b in params]
+    out[0] = (out[0][0] / s, out[0][1])
+    out[-1] = (out[-1][0] * s, out[-1][1] * s)
+    return out
+
+
 def train(pool, sigma: float, steps: int, batch: int = 16, lr: float = 5e-4, lr_min: float = 1e-5,
-          seed: int = 0, params=None, log_every: int = 200, log=print):
-    """Adam on the l1 loss over random dihedral transforms of pool images; returns (params, history)."""
+          seed: int = 0, params=None, log_every: int = 200, log=print, scale: float = 1.0):
+    """Adam on the l1 loss over random dihedral transforms of pool images; returns (params, history).
+
+    With ``scale`` s the images are divided by s and the noise level is sigma / s (noise units); the
+    returned parameters are those of the network in those units (see ``fold_scale``)."""
     import torch
     import synth
     import paper_2207_11336_gb300 as pnp
@@ -77,7 +103,6 @@ def train(pool, sigma: float, steps: int, batch: int = 16, lr: float = 5e-4, lr_
     gen = torch.Generator(device="cuda").manual_seed(seed)
     hist = []
     t0 = time.perf_counter()
-    run = 0.0
     for it in range(steps):
         cur = lr_min + 0.5 * (lr - lr_min) * (1.0 + np.cos(np.pi * it / max(steps - 1, 1)))
         tr.set_lr(cur)
@@ -86,15 +111,18 @@ def train(pool, sigma: float, steps: int, batch: int = 16, lr: float = 5e-4, lr_
         k = int(torch.randint(0, 8, (1,), generator=gen, device="cuda").item())
         if k & 4:
             u = u.transpose(1, 2)
-        u = torch.rot90(u, k & 3, dims=(1, 2)).contiguous()
+        u = torch.rot90(u, k & 3, dims=(1, 2))
+        if scale != 1.0:
+            u = u * (1.0 / scale)
+        u = u.contiguous()
         noise = torch.randn((batch, s, s), device="cuda", generator=gen)
         want = (it + 1) % log_every == 0 or it == steps - 1
-        loss = tr.step(u, noise, sigma, update=True, want_loss=want)
+        loss = tr.step(u, noise, sigma / scale, update=True, want_loss=want)
         if want:
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
-            hist.append((it + 1, loss, el))
-            log(f"step {it + 1:6d}  loss {loss:.4e}  lr {cur:.2e}  {el:7.1f} s")
+            hist.append((it + 1, loss * scale, el))
+            log(f"step {it + 1:6d}  loss {loss * scale:.4e} (image units)  lr {cur:.2e}  {el:7.1f} s")
     out, _ = tr.read()
     tr.close()
     return out, hist
@@ -130,6 +158,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--image-units", action="store_true",
+                    help="train at the images' own scale instead of in noise units")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
                                                   "dncnn_C3.npz"))
     a = ap.parse_args(argv)
@@ -154,9 +184,12 @@ def main(argv=None):
     else:
         sigma = a.sigma
     meta["sigma"] = sigma
+    scale = 1.0 if a.image_units else noise_unit(sigma)
+    meta["noise_unit"] = scale
     pool = torch.from_numpy(pool_np).cuda()
     params, hist = train(pool, sigma, a.steps, a.batch, a.lr, seed=a.seed,
-                         log=lambda s: print(s, flush=True))
+                         log=lambda s: print(s, flush=True), scale=scale)
+    params = fold_scale(params, scale)
     meta["loss_history"] = np.array([h[1] for h in hist])
     meta["train_seconds"] = hist[-1][2] if hist else 0.0
     save(a.out, params, meta)
