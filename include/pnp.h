@@ -88,6 +88,9 @@ typedef struct pnp_plan_info {
   double beta;          /* KB shape parameter                                  */
   double dl;            /* pixel size [rad] used for the w-term (0: none)      */
   int64_t device_bytes; /* device memory held by the plan                      */
+  int region_pitch;     /* row pitch (cells) of the gridding pass's shared-memory
+                           grid regions, chosen at plan time to limit bank
+                           conflicts for the plan's mix of supports J        */
 } pnp_plan_info;
 
 /* ------------------------------------------------------------------ plans */

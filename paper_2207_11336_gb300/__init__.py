@@ -55,7 +55,7 @@ class _Info(C.Structure):
     _fields_ = [("n", C.c_int), ("K", C.c_int), ("J", C.c_int), ("weight_dtype", C.c_int),
                 ("tile", C.c_int), ("nblocks", C.c_int), ("M", C.c_int64), ("nnz", C.c_int64),
                 ("n_units", C.c_int64), ("beta", C.c_double), ("dl", C.c_double),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("region_pitch", C.c_int)]
 
 
 _lib = None

@@ -91,6 +91,7 @@ struct pnp_plan {
   int tile = 48;       // gridding tile side T (cells)
   int ntc = 0;         // tiles per grid side, ceil(K / tile)
   int slots = 8;       // register slots per lane per row (32*slots >= Jmax^2)
+  int pitch = 0;       // row pitch (cells) of the staged gridding regions (0: the region side)
   int rpw = 2;         // rows per warp in flight
   int64_t M = 0, nnz = 0, unit_nnz = 1 << 17;
   double beta = 0, dl = 0;
@@ -149,6 +150,8 @@ int fft_adjoint(pnp_plan* p, int mode, const float* x, float* out,  // d_gridB -
                 float gamma, float t);
 // gridding.cu
 int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out);
+// choose p->pitch from the plan's number of rows per support J (rows_per_J[0..16])
+int gridding_pitch(pnp_plan* p, const int64_t* rows_per_J);
 int permute_y(pnp_plan* p, const float2* y_user);  // d_ysorted = y_user[perm]
 // plan_build.cu
 int build_units(pnp_plan* p);

@@ -28,7 +28,7 @@ namespace {
 constexpr uint32_t WAIT_LIMIT = 1u << 26;  // bounded mbarrier waits (seconds, not forever)
 
 struct GArgs {
-  int K, logK, T, S, ntc;
+  int K, logK, T, S, P, ntc;  // grid side, log2 K, tile side, staged region side, region row pitch, tiles per side
   const Unit* units;
   long long n_units;
   const Chunk* chunks;
@@ -159,10 +159,10 @@ __device__ __forceinline__ void consumers_sync() {
 }
 
 struct RowCtx {
-  float2* sx;     // staged input region (complex)
+  float2* sx;     // staged input region (complex), S rows of pitch P cells
   float* sy_re;   // accumulated output region, real plane
   float* sy_im;   // accumulated output region, imaginary plane
-  int S, r0, c0, logK, Km, lane;
+  int S, P, r0, c0, logK, Km, lane;
 };
 
 // Rows q0, q0 + NCW, ... of one J-uniform chunk, SL register slots of 32 taps per lane.
@@ -178,8 +178,8 @@ __device__ __forceinline__ void process_chunk(const GArgs& A, const Chunk& ch, c
   const int toff = (int)(ch.tap_begin & 3LL);
   const int roff = (int)(ch.row_begin & 1LL);
   const int nn = ch.nn;
-  const int lane = C.lane, S = C.S, logK = C.logK, Km = C.Km;
-  const int dummy = S * S + lane;
+  const int lane = C.lane, S = C.S, P = C.P, logK = C.logK, Km = C.Km;
+  const int dummy = S * P + lane;
   for (int q = q0; q < ch.nrows; q += GPASS_CONSUMERS) {
     const int beg = toff + q * nn;
     float2 wv[SL];
@@ -196,7 +196,7 @@ __device__ __forceinline__ void process_chunk(const GArgs& A, const Chunk& ch, c
       const bool in = lr < (unsigned)S && lc < (unsigned)S;
       if (live && !in) atomicOr(A.status, 1);
       const bool use = live && in;
-      idx[s] = use ? (int)(lr * S + lc) : dummy;
+      idx[s] = use ? (int)(lr * P + lc) : dummy;
       wv[s] = use ? w : make_float2(0.f, 0.f);
     }
     float2 r = make_float2(0.f, 0.f);
@@ -244,13 +244,14 @@ __global__ void __launch_bounds__(GPASS_THREADS) gpass(GArgs A) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ uint64_t full[NSTAGE], empty[NSTAGE];
   __shared__ volatile int s_abort;
-  const int S = A.S, SS = S * S, logK = A.logK, Km = A.K - 1;
-  const int region_bytes = (((SS + 32) * 8 + 127) & ~127);  // + one dummy cell per lane
+  const int S = A.S, P = A.P, SS = S * S, SP = S * P, logK = A.logK, Km = A.K - 1;
+  const int region_bytes = (((SP + 32) * 8 + 127) & ~127);  // + one dummy cell per lane
   // input region: interleaved complex; output region: separate real and imaginary planes
-  // (consecutive cells in consecutive banks, so the scatter atomics do not conflict)
+  // (consecutive cells in consecutive banks); rows of both are P cells apart, P chosen at
+  // plan time to spread the lanes of a J x J tap block over the banks (gridding_pitch)
   float2* sx = reinterpret_cast<float2*>(sm);
   float* sy_re = reinterpret_cast<float*>(MODE == G_FUSED ? sm + region_bytes : sm);
-  float* sy_im = sy_re + (SS + 32);
+  float* sy_im = sy_re + (SP + 32);
   unsigned char* stages = sm + (MODE == G_FUSED ? 2 : 1) * region_bytes;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   constexpr int NCW = GPASS_CONSUMERS;
@@ -314,16 +315,16 @@ __global__ void __launch_bounds__(GPASS_THREADS) gpass(GArgs A) {
     if (MODE != G_GRID)
       for (int c = ctid; c < SS; c += CT) {
         const int i = c / S, jj = c - i * S;
-        sx[c] = A.gridA[((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km)];
+        sx[i * P + jj] = A.gridA[((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km)];
       }
-    if (ctid < 32 && MODE != G_GRID) sx[SS + ctid] = make_float2(0.f, 0.f);
+    if (ctid < 32 && MODE != G_GRID) sx[SP + ctid] = make_float2(0.f, 0.f);
     if (MODE != G_DEGRID)
-      for (int c = ctid; c < SS; c += CT) {
+      for (int c = ctid; c < SP + 32; c += CT) {
         sy_re[c] = 0.f;
         sy_im[c] = 0.f;
       }
     consumers_sync();
-    const RowCtx C{sx, sy_re, sy_im, S, r0, c0, logK, Km, lane};
+    const RowCtx C{sx, sy_re, sy_im, S, P, r0, c0, logK, Km, lane};
 
     for (int ci = 0; ci < U.nchunks; ++ci) {
       bool ok = false;
@@ -360,9 +361,9 @@ __global__ void __launch_bounds__(GPASS_THREADS) gpass(GArgs A) {
     consumers_sync();  // all scatters of this unit are in sy
     if (MODE != G_DEGRID && !s_abort) {
       for (int c = ctid; c < SS; c += CT) {
-        const float2 v = make_float2(sy_re[c], sy_im[c]);
+        const int i = c / S, jj = c - i * S;
+        const float2 v = make_float2(sy_re[i * P + jj], sy_im[i * P + jj]);
         if (v.x != 0.f || v.y != 0.f) {
-          const int i = c / S, jj = c - i * S;
           atomicAdd(&A.gridB[((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km)], v);
         }
       }
@@ -381,7 +382,7 @@ __global__ void permute_kernel(const float2* __restrict__ y, const int32_t* __re
 
 template <int MODE, typename WT>
 int launch_gpass(pnp_plan* p, const GArgs& A) {
-  const int region_bytes = (((A.S * A.S + 32) * 8 + 127) & ~127);
+  const int region_bytes = (((A.S * A.P + 32) * 8 + 127) & ~127);
   const int smem = (MODE == G_FUSED ? 2 : 1) * region_bytes + NSTAGE * StageLayout<WT>::SIZE;
   static int attr = 0;
   static int per_sm = 0;
@@ -405,7 +406,55 @@ int dispatch_wt(pnp_plan* p, const GArgs& A) {
                                   : launch_gpass<MODE, float2>(p, A);
 }
 
+// Modelled shared-memory wavefronts of one row of J x J taps on regions of row pitch P: lane t of
+// register slot s holds tap 32 s + t at cell (t / J) P + t % J; the residual gathers 8-byte cells
+// (two banks each) and the scatter issues one 4-byte atomic per plane.  A wavefront serves each
+// bank once, so a warp access costs the largest number of lanes that meet in one bank.
+int64_t row_wavefronts(int J, int P) {
+  const int nn = J * J;
+  int64_t total = 0;
+  for (int s = 0; s * 32 < nn; ++s) {
+    int g[32] = {}, sc[32] = {};
+    const int lanes = std::min(32, nn - 32 * s);
+    for (int l = 0; l < lanes; ++l) {
+      const int t = 32 * s + l, addr = (t / J) * P + t % J;
+      sc[addr & 31]++;
+      g[(2 * addr) & 31]++;
+      g[(2 * addr + 1) & 31]++;
+    }
+    int mg = 0, ms = 0;
+    for (int b = 0; b < 32; ++b) {
+      mg = std::max(mg, g[b]);
+      ms = std::max(ms, sc[b]);
+    }
+    total += std::max(mg, (2 * lanes + 31) / 32) + 2 * ms;
+  }
+  return total;
+}
+
 }  // namespace
+
+int gridding_pitch(pnp_plan* p, const int64_t* rows_per_J) {
+  const int S = p->tile + p->Jmax - 1;
+  int optin = 0;
+  PNP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+  const int stage = NSTAGE * std::max(StageLayout<float2>::SIZE, StageLayout<__nv_bfloat162>::SIZE);
+  int best = S;
+  int64_t best_cost = -1;
+  for (int P = S; P < S + 32; ++P) {
+    const int region_bytes = (((S * P + 32) * 8 + 127) & ~127);
+    if (2 * region_bytes + stage + 1024 > optin) break;  // fused pass: two regions + the stages
+    int64_t cost = 0;
+    for (int J = 1; J <= 16; ++J)
+      if (rows_per_J[J]) cost += rows_per_J[J] * row_wavefronts(J, P);
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      best = P;
+    }
+  }
+  p->pitch = best;
+  return PNP_OK;
+}
 
 int permute_y(pnp_plan* p, const float2* y_user) {
   if (p->M == 0) return PNP_OK;
@@ -427,6 +476,7 @@ int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out) {
   A.logK = p->logK;
   A.T = p->tile;
   A.S = p->tile + p->Jmax - 1;
+  A.P = p->pitch > 0 ? p->pitch : A.S;
   A.ntc = p->ntc;
   A.units = p->d_units;
   A.n_units = p->n_units;

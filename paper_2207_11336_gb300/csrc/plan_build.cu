@@ -433,6 +433,11 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     cudaFree(d_mu);
     if (e != cudaSuccess) return fail(PNP_ERR_CUDA, std::string("build_rows: ") + cudaGetErrorString(e));
   }
+  {
+    std::vector<int64_t> rows_per_J(17, 0);
+    for (int64_t m = 0; m < M; ++m) rows_per_J[sgeom[m].J]++;  // geom was released above
+    if (int rc = gridding_pitch(p, rows_per_J.data())) return rc;
+  }
   return build_units(p);
 }
 

@@ -236,6 +236,7 @@ int pnp_plan_get_info(const pnp_plan* p, pnp_plan_info* info) {
   info->beta = p->beta;
   info->dl = p->dl;
   info->device_bytes = p->device_bytes;
+  info->region_pitch = p->pitch > 0 ? p->pitch : p->tile + p->Jmax - 1;
   return PNP_OK;
 }
 
