@@ -387,7 +387,7 @@ def run_gpu(args):
     plan.set_timing(False)
     g_ms, g_cnt = tim["gridding"]
     g_ms_launch = g_ms / max(g_cnt, 1)
-    alg_bytes = info["nnz"] * (8 + 4) + M * 8 + 2 * K * K * 8
+    alg_bytes = info["nnz"] * (8 + 2) + M * 8 + 2 * K * K * 8   # weight + 16-bit cell per tap
     hbm, peak_kind = measured_peaks()
     achieved = alg_bytes / (g_ms_launch * 1e-3) / 1e9
     roof_cnn = None
@@ -436,7 +436,7 @@ def run_gpu(args):
                "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16" if learned else "f32",
                "data": "synthetic", "impl": "gpu",
                "config": {"workload": desc, "parallelism": f"replicas{ws}",
-                          "l2": "inputs larger than L2 (G %.1f GB)" % (info["nnz"] * 12 / 1e9),
+                          "l2": "inputs larger than L2 (G %.1f GB)" % (info["nnz"] * 10 / 1e9),
                           "nnz": info["nnz"], "denoiser": "cnn" if learned else "haar", "graph": True},
                "clocks": clk.summary(),
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": M * 8,
@@ -486,7 +486,7 @@ def run_kernel_case(args):
     t = plan.read_timing()
     info = plan.info
     ms = t["gridding"][0] / max(t["gridding"][1], 1)
-    alg = info["nnz"] * 12 + M * 8 + 2 * K * K * 8
+    alg = info["nnz"] * 10 + M * 8 + 2 * K * K * 8
     print(json.dumps({"case": "gridding 1024^2/2048^2 M=2e6", "nnz": info["nnz"], "units": info["n_units"],
                       "gridding_ms": ms, "alg_bytes": alg, "GBps": alg / ms / 1e6,
                       "stage_ms": {k: v[0] / max(v[1], 1) for k, v in t.items()}}))

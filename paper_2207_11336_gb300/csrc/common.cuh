@@ -108,7 +108,7 @@ struct pnp_plan {
   float2* d_gridB = nullptr;   // K*K: G^H r   (layout [k1][k0]); kept zero between uses
   float2* d_tmp = nullptr;     // K*n: half-transformed intermediate
   void* d_w = nullptr;         // nnz weights (float2 or bf16x2)
-  int32_t* d_cols = nullptr;   // nnz internal column indices k1*K + k0
+  uint16_t* d_cells = nullptr; // nnz cell indices lr * pitch + lc in the row's staged tile region
   int64_t* d_rowptr = nullptr; // M+1 (sorted order)
   int32_t* d_perm = nullptr;   // sorted row -> caller row
   float2* d_ysorted = nullptr; // M scratch: y in sorted order

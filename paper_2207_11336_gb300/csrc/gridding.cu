@@ -34,13 +34,13 @@ struct GArgs {
   const Chunk* chunks;
   const int64_t* rowptr;
   const void* w;
-  const int32_t* cols;
+  const uint16_t* cells;  // per tap: cell lr * P + lc of the row's staged region
   const int32_t* perm;
   const float2* y_in;   // sorted order (G_GRID, G_FUSED); NULL in G_FUSED = no data term
   float2* y_out;        // caller order (G_DEGRID)
   const float2* gridA;  // input grid (G_DEGRID, G_FUSED)
   float2* gridB;        // output grid (G_GRID, G_FUSED)
-  int* status;          // bit 0: tap outside the staged region (skipped); bit 1: pipeline wait timed out
+  int* status;          // bit 1: pipeline wait timed out; bit 2: inconsistent work list (chunk skipped)
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -105,14 +105,14 @@ __device__ __forceinline__ float2 w_at(const unsigned char* base, int i) {
   }
 }
 
-// Shared-memory stage: [weights | columns | visibilities], each 128-B aligned.  Every
+// Shared-memory stage: [weights | cells | visibilities], each 128-B aligned.  Every
 // row of a chunk has the same support J (rows are sorted by J within a tile), so
 // row q of a chunk starts at tap q J^2 and the row offsets need not be read.
 template <typename WT>
 struct StageLayout {
   static constexpr int al(int b) { return (b + 127) & ~127; }
-  static constexpr int W_BYTES = (CHUNK_TAPS + 8) * WBytes<WT>::value;
-  static constexpr int C_BYTES = (CHUNK_TAPS + 8) * 4;
+  static constexpr int W_BYTES = (CHUNK_TAPS + 16) * WBytes<WT>::value;
+  static constexpr int C_BYTES = (CHUNK_TAPS + 16) * 2;
   static constexpr int Y_BYTES = (CHUNK_ROWS + 4) * 8;
   static constexpr int W_OFF = 0;
   static constexpr int C_OFF = al(W_BYTES);
@@ -138,15 +138,16 @@ __device__ __forceinline__ void issue_chunk(const GArgs& A, const Chunk& ch, uns
                                             uint64_t* bar) {
   using L = StageLayout<WT>;
   constexpr int WB = WBytes<WT>::value;
-  // 16-byte aligned copy windows around the chunk (the arrays are padded at the end)
-  const long long tb0 = ch.tap_begin & ~3LL, te = (ch.tap_begin + ch.ntaps + 3) & ~3LL;
+  // 16-byte aligned copy windows around the chunk, 8 taps (16 B of cells) granular; the arrays
+  // are padded at the end
+  const long long tb0 = ch.tap_begin & ~7LL, te = (ch.tap_begin + ch.ntaps + 7) & ~7LL;
   const long long rb0 = ch.row_begin & ~1LL, ye = (ch.row_begin + ch.nrows + 1) & ~1LL;
-  const uint32_t wbytes = (uint32_t)((te - tb0) * WB), cbytes = (uint32_t)((te - tb0) * 4);
+  const uint32_t wbytes = (uint32_t)((te - tb0) * WB), cbytes = (uint32_t)((te - tb0) * 2);
   const uint32_t ybytes = (uint32_t)((ye - rb0) * 8);
   const bool need_y = MODE != G_DEGRID && A.y_in != nullptr;
   mbar_expect_tx(bar, wbytes + cbytes + (need_y ? ybytes : 0));
   bulk_g2s(stage + L::W_OFF, reinterpret_cast<const unsigned char*>(A.w) + tb0 * WB, wbytes, bar);
-  bulk_g2s(stage + L::C_OFF, A.cols + tb0, cbytes, bar);
+  bulk_g2s(stage + L::C_OFF, A.cells + tb0, cbytes, bar);
   if (need_y) bulk_g2s(stage + L::Y_OFF, A.y_in + rb0, ybytes, bar);
 }
 
@@ -166,20 +167,21 @@ struct RowCtx {
 };
 
 // Rows q0, q0 + NCW, ... of one J-uniform chunk, SL register slots of 32 taps per lane.
-// Lanes without a tap (and taps that fail the region check) point at their own dummy
-// cell SS + lane of the staged regions with weight 0, so the slot loops are branch-free.
+// Each tap carries its cell in the staged region (computed when G was built); lanes
+// without a tap point at their own dummy cell S P + lane with weight 0, so the slot loops
+// are branch-free, and every cell is clamped into the region.
 template <int MODE, typename WT, int SL>
 __device__ __forceinline__ void process_chunk(const GArgs& A, const Chunk& ch, const unsigned char* stage,
                                               int q0, const RowCtx& C) {
   using L = StageLayout<WT>;
   const unsigned char* sw = stage + L::W_OFF;
-  const int32_t* sc = reinterpret_cast<const int32_t*>(stage + L::C_OFF);
+  const uint16_t* sc = reinterpret_cast<const uint16_t*>(stage + L::C_OFF);
   const float2* syv = reinterpret_cast<const float2*>(stage + L::Y_OFF);
-  const int toff = (int)(ch.tap_begin & 3LL);
+  const int toff = (int)(ch.tap_begin & 7LL);
   const int roff = (int)(ch.row_begin & 1LL);
   const int nn = ch.nn;
-  const int lane = C.lane, S = C.S, P = C.P, logK = C.logK, Km = C.Km;
-  const int dummy = S * P + lane;
+  const int lane = C.lane;
+  const int dummy = C.S * C.P + lane;
   for (int q = q0; q < ch.nrows; q += GPASS_CONSUMERS) {
     const int beg = toff + q * nn;
     float2 wv[SL];
@@ -190,14 +192,8 @@ __device__ __forceinline__ void process_chunk(const GArgs& A, const Chunk& ch, c
       const bool live = t < nn;
       const int tt = live ? beg + t : beg;
       const float2 w = w_at<WT>(sw, tt);
-      const int col = sc[tt];
-      const unsigned lr = (unsigned)(((col >> logK) - C.r0) & Km);
-      const unsigned lc = (unsigned)((col - C.c0) & Km);
-      const bool in = lr < (unsigned)S && lc < (unsigned)S;
-      if (live && !in) atomicOr(A.status, 1);
-      const bool use = live && in;
-      idx[s] = use ? (int)(lr * P + lc) : dummy;
-      wv[s] = use ? w : make_float2(0.f, 0.f);
+      idx[s] = live ? min((int)sc[tt], dummy) : dummy;
+      wv[s] = live ? w : make_float2(0.f, 0.f);
     }
     float2 r = make_float2(0.f, 0.f);
     if (MODE != G_GRID) {
@@ -338,7 +334,7 @@ __global__ void __launch_bounds__(GPASS_THREADS) gpass(GArgs A) {
         const unsigned char* stage = stages + st * L::SIZE;
         // rows are dealt to warps round robin over the whole stream, so no warp idles per chunk
         const int q0 = warp >= rb ? warp - rb : warp - rb + NCW;
-        if (ch.nn * ch.nrows != ch.ntaps || (ch.tap_begin & 3LL) + ch.ntaps > CHUNK_TAPS + 8) {
+        if (ch.nn * ch.nrows != ch.ntaps || (ch.tap_begin & 7LL) + ch.ntaps > CHUNK_TAPS + 16) {
           if (lane == 0) atomicOr(A.status, 4);  // inconsistent work list: skip the chunk
         } else if (ch.nn <= 64) {
           process_chunk<MODE, WT, 2>(A, ch, stage, q0, C);
@@ -483,7 +479,7 @@ int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out) {
   A.chunks = p->d_chunks;
   A.rowptr = p->d_rowptr;
   A.w = p->d_w;
-  A.cols = p->d_cols;
+  A.cells = p->d_cells;
   A.perm = p->d_perm;
   A.y_in = (mode == G_DEGRID || y_user == nullptr) ? nullptr : p->d_ysorted;
   A.y_out = y_out;

@@ -43,7 +43,9 @@ struct BuildArgs {
   const RowGeom* geom;       // sorted order
   const int64_t* rowptr;
   void* w;
-  int32_t* cols;
+  uint16_t* cells;
+  int T, S, P;               // gridding tile side, staged region side and row pitch
+  int* err;                  // set when a tap falls outside its row's staged region
   int bf16;
 };
 
@@ -118,25 +120,31 @@ __global__ void __launch_bounds__(256) build_rows(BuildArgs A) {
     } else {
       reinterpret_cast<float2*>(A.w)[beg + t] = make_float2(wr, wi);
     }
-    A.cols[beg + t] = (((g.s1 + i1) & Km) << A.logK) | ((g.s0 + i0) & Km);
+    // cell of the tap in the staged region of the row's tile (the tile of its first tap)
+    const int r0 = (((g.s1 % A.K) + A.K) % A.K) / A.T * A.T, c0 = (((g.s0 % A.K) + A.K) % A.K) / A.T * A.T;
+    const int lr = (g.s1 + i1 - r0) & Km, lc = (g.s0 + i0 - c0) & Km;
+    if (lr >= A.S || lc >= A.S) atomicOr(A.err, 1);
+    A.cells[beg + t] = (uint16_t)(lr < A.S && lc < A.S ? lr * A.P + lc : 0);
   }
 }
 
-// gather rows for export: canonical column order k0*K + k1, float weights
+// gather rows for export: canonical column order k0*K + k1, float weights.  src_off holds per
+// row (first tap, tap count, tile origin r0, tile origin c0); cells are lr * P + lc from the origin.
 __global__ void export_rows(const int64_t* __restrict__ src_off, const int64_t* __restrict__ dst_off,
-                            int64_t nrows, const void* w, const int32_t* cols, int bf16, int logK,
+                            int64_t nrows, const void* w, const uint16_t* cells, int P, int bf16, int logK,
                             float2* out_w, int32_t* out_c) {
   const int64_t r = blockIdx.x;
   if (r >= nrows) return;
-  const int64_t s = src_off[2 * r], cnt = src_off[2 * r + 1], d = dst_off[r];
+  const int64_t s = src_off[4 * r], cnt = src_off[4 * r + 1], d = dst_off[r];
+  const int r0 = (int)src_off[4 * r + 2], c0 = (int)src_off[4 * r + 3];
   const int Km = (1 << logK) - 1;
   for (int64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
     float2 v;
     if (bf16) v = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(w)[s + t]);
     else v = reinterpret_cast<const float2*>(w)[s + t];
-    const int c = cols[s + t];
+    const int c = cells[s + t], lr = c / P, lc = c - lr * P;
     out_w[d + t] = v;
-    out_c[d + t] = ((c & Km) << logK) | (c >> logK);
+    out_c[d + t] = (((c0 + lc) & Km) << logK) | ((r0 + lr) & Km);
   }
 }
 
@@ -283,6 +291,11 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
   }
   p->Jmax = Jmax;
   p->slots = Jmax * Jmax <= 64 ? 2 : (Jmax * Jmax <= 128 ? 4 : 8);
+  {
+    std::vector<int64_t> rows_per_J(17, 0);
+    for (int64_t m = 0; m < M; ++m) rows_per_J[geom[m].J]++;
+    if (int rc = gridding_pitch(p, rows_per_J.data())) return rc;
+  }
 
   // stable LSD counting sort: first by support J, then by (tile, block) key, so that rows of
   // one tile come out grouped by J (each gridding chunk then holds rows of a single J)
@@ -375,11 +388,11 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     p->device_bytes += (int64_t)((p->nnz + TAP_PAD) * wbytes);
     PNP_CUDA(cudaMemset(w, 0, (p->nnz + TAP_PAD) * wbytes));
   }
-  if (int rc = dev_alloc(p, &p->d_cols, (size_t)p->nnz + TAP_PAD)) return rc;
+  if (int rc = dev_alloc(p, &p->d_cells, (size_t)p->nnz + TAP_PAD)) return rc;
   if (int rc = dev_alloc(p, &p->d_rowptr, (size_t)M + 1 + ROW_PAD)) return rc;
   if (int rc = dev_alloc(p, &p->d_perm, (size_t)M)) return rc;
   if (int rc = dev_alloc(p, &p->d_ysorted, (size_t)M + ROW_PAD)) return rc;
-  PNP_CUDA(cudaMemset(p->d_cols, 0, ((size_t)p->nnz + TAP_PAD) * sizeof(int32_t)));
+  PNP_CUDA(cudaMemset(p->d_cells, 0, ((size_t)p->nnz + TAP_PAD) * sizeof(uint16_t)));
   PNP_CUDA(cudaMemset(p->d_ysorted, 0, ((size_t)M + ROW_PAD) * sizeof(float2)));
   if (int rc = dev_alloc(p, &p->d_acc, 8)) return rc;
   if (int rc = dev_alloc(p, &p->d_status, 4)) return rc;
@@ -407,6 +420,7 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
       cudaFree(d_geom);
       return fail(PNP_ERR_OOM, "plan build scratch allocation failed");
     }
+    PNP_CUDA(cudaMemsetAsync(p->d_status + 3, 0, sizeof(int), p->stream));
     PNP_CUDA(cudaMemcpy(d_geom, sgeom.data(), M * sizeof(RowGeom), cudaMemcpyHostToDevice));
     PNP_CUDA(cudaMemcpy(d_mu, mu.data(), mu.size() * sizeof(double), cudaMemcpyHostToDevice));
     BuildArgs A{};
@@ -423,7 +437,11 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     A.geom = d_geom;
     A.rowptr = p->d_rowptr;
     A.w = p->d_w;
-    A.cols = p->d_cols;
+    A.cells = p->d_cells;
+    A.T = p->tile;
+    A.S = p->tile + p->Jmax - 1;
+    A.P = p->pitch;
+    A.err = p->d_status + 3;
     A.bf16 = p->wdtype == PNP_W_BF16C;
     build_rows<<<(unsigned)((M + 7) / 8), 256, 0, p->stream>>>(A);
     cudaError_t e = cudaGetLastError();
@@ -432,33 +450,35 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     cudaFree(d_geom);
     cudaFree(d_mu);
     if (e != cudaSuccess) return fail(PNP_ERR_CUDA, std::string("build_rows: ") + cudaGetErrorString(e));
-  }
-  {
-    std::vector<int64_t> rows_per_J(17, 0);
-    for (int64_t m = 0; m < M; ++m) rows_per_J[sgeom[m].J]++;  // geom was released above
-    if (int rc = gridding_pitch(p, rows_per_J.data())) return rc;
+    int err = 0;
+    PNP_CUDA(cudaMemcpy(&err, p->d_status + 3, sizeof(int), cudaMemcpyDeviceToHost));
+    PNP_CUDA(cudaMemset(p->d_status + 3, 0, sizeof(int)));
+    if (err) return fail(PNP_ERR_INVALID_ARG, "internal: a tap of G falls outside its row's gridding region");
   }
   return build_units(p);
 }
 
 int export_rows_impl(const pnp_plan* p, const int64_t* rows, int64_t nrows, int64_t* offsets,
                      float* weights, int32_t* cols) {
-  std::vector<int64_t> src(2 * nrows), dst(nrows);
+  std::vector<int64_t> src(4 * nrows), dst(nrows);
   offsets[0] = 0;
   for (int64_t i = 0; i < nrows; ++i) {
     if (rows[i] < 0 || rows[i] >= p->M) return fail(PNP_ERR_INVALID_ARG, "export row index out of range");
     const int64_t s = p->h_inv[rows[i]];
-    src[2 * i] = p->h_rowptr[s];
-    src[2 * i + 1] = p->h_rowptr[s + 1] - p->h_rowptr[s];
+    const int tile = p->h_key[s] / p->nblocks;
+    src[4 * i] = p->h_rowptr[s];
+    src[4 * i + 1] = p->h_rowptr[s + 1] - p->h_rowptr[s];
+    src[4 * i + 2] = (int64_t)(tile / p->ntc) * p->tile;
+    src[4 * i + 3] = (int64_t)(tile % p->ntc) * p->tile;
     dst[i] = offsets[i];
-    offsets[i + 1] = offsets[i] + src[2 * i + 1];
+    offsets[i + 1] = offsets[i] + src[4 * i + 1];
   }
   if (!weights || !cols || nrows == 0) return PNP_OK;
   const int64_t total = offsets[nrows];
   int64_t *d_src = nullptr, *d_dst = nullptr;
   float2* d_w = nullptr;
   int32_t* d_c = nullptr;
-  if (cudaMalloc(&d_src, 2 * nrows * sizeof(int64_t)) || cudaMalloc(&d_dst, nrows * sizeof(int64_t)) ||
+  if (cudaMalloc(&d_src, 4 * nrows * sizeof(int64_t)) || cudaMalloc(&d_dst, nrows * sizeof(int64_t)) ||
       cudaMalloc(&d_w, total * sizeof(float2)) || cudaMalloc(&d_c, total * sizeof(int32_t))) {
     cudaGetLastError();
     cudaFree(d_src);
@@ -467,10 +487,10 @@ int export_rows_impl(const pnp_plan* p, const int64_t* rows, int64_t nrows, int6
     return fail(PNP_ERR_OOM, "export scratch allocation failed");
   }
   int rc = PNP_OK;
-  cudaError_t e = cudaMemcpy(d_src, src.data(), 2 * nrows * sizeof(int64_t), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMemcpy(d_src, src.data(), 4 * nrows * sizeof(int64_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_dst, dst.data(), nrows * sizeof(int64_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
-    export_rows<<<(unsigned)nrows, 128, 0, p->stream>>>(d_src, d_dst, nrows, p->d_w, p->d_cols,
+    export_rows<<<(unsigned)nrows, 128, 0, p->stream>>>(d_src, d_dst, nrows, p->d_w, p->d_cells, p->pitch,
                                                          p->wdtype == PNP_W_BF16C, p->logK, d_w, d_c);
     g_launches.fetch_add(1);
     e = cudaGetLastError();
