@@ -56,8 +56,8 @@ __host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 // first tap in one grid tile (and one data block).
 constexpr int CHUNK_TAPS = 4096;
 constexpr int CHUNK_ROWS = 128;
-constexpr int NSTAGE = 3;          // shared-memory pipeline depth of the gridding pass
-constexpr int GPASS_CONSUMERS = 24; // consumer warps per gridding CTA (plus one producer warp)
+constexpr int NSTAGE = 4;          // shared-memory pipeline depth of the gridding pass
+constexpr int GPASS_CONSUMERS = 16; // consumer warps per gridding CTA (plus one producer warp)
 constexpr int GPASS_THREADS = 32 * (GPASS_CONSUMERS + 1);
 constexpr int TAP_PAD = 16;        // weights/columns are allocated nnz + TAP_PAD long
 constexpr int ROW_PAD = 4;         // row offsets M + 1 + ROW_PAD, sorted y M + ROW_PAD
@@ -65,11 +65,13 @@ constexpr int ROW_PAD = 4;         // row offsets M + 1 + ROW_PAD, sorted y M + 
 struct Chunk {
   long long row_begin;
   long long tap_begin;
+  long long run_begin;  // first entry of the chunk's run list in the plan's run array
   int nrows;
   int ntaps;
-  int nn;   // taps per row (J^2, the same for every row of the chunk)
-  int pad;
+  int nn;     // taps per row (J^2, the same for every row of the chunk)
+  int nruns;  // runs of rows sharing one tap window; the list holds nruns + 1 row offsets
 };
+constexpr int RUN_MAX = 6;         // rows per run at most (keeps the consumer warps balanced)
 
 struct Unit {
   long long chunk_begin;
@@ -109,6 +111,8 @@ struct pnp_plan {
   float2* d_tmp = nullptr;     // K*n: half-transformed intermediate
   void* d_w = nullptr;         // nnz weights (float2 or bf16x2)
   uint16_t* d_cells = nullptr; // nnz cell indices lr * pitch + lc in the row's staged tile region
+  uint8_t* d_runs = nullptr;    // per chunk: row offsets where runs start, then nrows (padded by 16)
+  int64_t n_runs = 0;
   int64_t* d_rowptr = nullptr; // M+1 (sorted order)
   int32_t* d_perm = nullptr;   // sorted row -> caller row
   float2* d_ysorted = nullptr; // M scratch: y in sorted order
@@ -131,6 +135,7 @@ struct pnp_plan {
   std::vector<int32_t> h_perm;     // sorted -> caller
   std::vector<int32_t> h_inv;      // caller -> sorted
   std::vector<int32_t> h_key;      // sorted: tile * nblocks + block
+  std::vector<uint16_t> h_start;   // sorted: first tap's cell in the tile (row * tile + col)
 };
 
 struct pnp_den {

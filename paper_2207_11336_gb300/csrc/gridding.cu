@@ -35,6 +35,7 @@ struct GArgs {
   const int64_t* rowptr;
   const void* w;
   const uint16_t* cells;  // per tap: cell lr * P + lc of the row's staged region
+  const uint8_t* runs;    // per chunk: row offsets where runs of a shared tap window start, then nrows
   const int32_t* perm;
   const float2* y_in;   // sorted order (G_GRID, G_FUSED); NULL in G_FUSED = no data term
   float2* y_out;        // caller order (G_DEGRID)
@@ -104,9 +105,8 @@ __device__ __forceinline__ float2 w_at(const unsigned char* base, int i) {
     return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(base)[i]);
   }
 }
-
-// Shared-memory stage: [weights | cells | visibilities], each 128-B aligned.  Every
-// row of a chunk has the same support J (rows are sorted by J within a tile), so
+// Shared-memory stage: [weights | cells | visibilities | run list], each 128-B aligned.
+// Every row of a chunk has the same support J (rows are sorted by J within a tile), so
 // row q of a chunk starts at tap q J^2 and the row offsets need not be read.
 template <typename WT>
 struct StageLayout {
@@ -114,10 +114,12 @@ struct StageLayout {
   static constexpr int W_BYTES = (CHUNK_TAPS + 16) * WBytes<WT>::value;
   static constexpr int C_BYTES = (CHUNK_TAPS + 16) * 2;
   static constexpr int Y_BYTES = (CHUNK_ROWS + 4) * 8;
+  static constexpr int R_BYTES = CHUNK_ROWS + 32;
   static constexpr int W_OFF = 0;
   static constexpr int C_OFF = al(W_BYTES);
   static constexpr int Y_OFF = C_OFF + al(C_BYTES);
-  static constexpr int SIZE = Y_OFF + al(Y_BYTES);
+  static constexpr int R_OFF = Y_OFF + al(Y_BYTES);
+  static constexpr int SIZE = R_OFF + al(R_BYTES);
 };
 
 // Position in a CTA's stream of chunks: unit u (global index) and chunk c within it.
@@ -144,10 +146,13 @@ __device__ __forceinline__ void issue_chunk(const GArgs& A, const Chunk& ch, uns
   const long long rb0 = ch.row_begin & ~1LL, ye = (ch.row_begin + ch.nrows + 1) & ~1LL;
   const uint32_t wbytes = (uint32_t)((te - tb0) * WB), cbytes = (uint32_t)((te - tb0) * 2);
   const uint32_t ybytes = (uint32_t)((ye - rb0) * 8);
+  const long long rs0 = ch.run_begin & ~15LL, re = (ch.run_begin + ch.nruns + 1 + 15) & ~15LL;
+  const uint32_t rbytes = (uint32_t)(re - rs0);
   const bool need_y = MODE != G_DEGRID && A.y_in != nullptr;
-  mbar_expect_tx(bar, wbytes + cbytes + (need_y ? ybytes : 0));
+  mbar_expect_tx(bar, wbytes + cbytes + rbytes + (need_y ? ybytes : 0));
   bulk_g2s(stage + L::W_OFF, reinterpret_cast<const unsigned char*>(A.w) + tb0 * WB, wbytes, bar);
   bulk_g2s(stage + L::C_OFF, A.cells + tb0, cbytes, bar);
+  bulk_g2s(stage + L::R_OFF, A.runs + rs0, rbytes, bar);
   if (need_y) bulk_g2s(stage + L::Y_OFF, A.y_in + rb0, ybytes, bar);
 }
 
@@ -166,64 +171,79 @@ struct RowCtx {
   int S, P, r0, c0, logK, Km, lane;
 };
 
-// Rows q0, q0 + NCW, ... of one J-uniform chunk, SL register slots of 32 taps per lane.
-// Each tap carries its cell in the staged region (computed when G was built); lanes
-// without a tap point at their own dummy cell S P + lane with weight 0, so the slot loops
-// are branch-free, and every cell is clamped into the region.
+// Runs k0, k0 + NCW, ... of one J-uniform chunk, SL register slots of 32 taps per lane.
+// The rows of a run share their tap window (same first cell, same support): the run's
+// cells and staged grid values are loaded once, each row contributes its own residual
+// r_m = sum_k G_mk X_k - y_m, and the scatter terms conj(G_mk) r_m are summed in registers
+// over the run before one pair of shared atomics per tap.  Lanes without a tap point at
+// their own dummy cell S P + lane with weight 0, so the slot loops are branch-free, and
+// every cell is clamped into the region.
 template <int MODE, typename WT, int SL>
 __device__ __forceinline__ void process_chunk(const GArgs& A, const Chunk& ch, const unsigned char* stage,
-                                              int q0, const RowCtx& C) {
+                                              int k0, const RowCtx& C) {
   using L = StageLayout<WT>;
   const unsigned char* sw = stage + L::W_OFF;
   const uint16_t* sc = reinterpret_cast<const uint16_t*>(stage + L::C_OFF);
   const float2* syv = reinterpret_cast<const float2*>(stage + L::Y_OFF);
+  const uint8_t* sr = stage + L::R_OFF + (int)(ch.run_begin & 15LL);
   const int toff = (int)(ch.tap_begin & 7LL);
   const int roff = (int)(ch.row_begin & 1LL);
   const int nn = ch.nn;
   const int lane = C.lane;
   const int dummy = C.S * C.P + lane;
-  for (int q = q0; q < ch.nrows; q += GPASS_CONSUMERS) {
-    const int beg = toff + q * nn;
-    float2 wv[SL];
+  for (int k = k0; k < ch.nruns; k += GPASS_CONSUMERS) {
+    const int qe = min((int)sr[k + 1], ch.nrows), qb = min((int)sr[k], qe);
     int idx[SL];
+    float2 xv[SL], ar[SL];
 #pragma unroll
     for (int s = 0; s < SL; ++s) {
       const int t = lane + 32 * s;
-      const bool live = t < nn;
-      const int tt = live ? beg + t : beg;
-      const float2 w = w_at<WT>(sw, tt);
-      idx[s] = live ? min((int)sc[tt], dummy) : dummy;
-      wv[s] = live ? w : make_float2(0.f, 0.f);
+      idx[s] = t < nn ? min((int)sc[toff + qb * nn + t], dummy) : dummy;
+      if (MODE != G_GRID) xv[s] = C.sx[idx[s]];
+      ar[s] = make_float2(0.f, 0.f);
     }
-    float2 r = make_float2(0.f, 0.f);
-    if (MODE != G_GRID) {
-      float2 acc = make_float2(0.f, 0.f);
+    for (int q = qb; q < qe; ++q) {
+      const int beg = toff + q * nn;
+      float2 r = make_float2(0.f, 0.f);
+      if (MODE != G_GRID) {
+        float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int s = 0; s < SL; ++s) {
+          const int t = lane + 32 * s;
+          const float2 w = t < nn ? w_at<WT>(sw, beg + t) : make_float2(0.f, 0.f);
+          acc.x = fmaf(w.x, xv[s].x, fmaf(-w.y, xv[s].y, acc.x));
+          acc.y = fmaf(w.x, xv[s].y, fmaf(w.y, xv[s].x, acc.y));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+        }
+        if (MODE == G_DEGRID) {
+          if (lane == 0) A.y_out[A.perm[ch.row_begin + q]] = acc;
+          continue;
+        }
+        r = acc;
+        if (A.y_in) r = csub(r, syv[roff + q]);
+      } else {
+        r = syv[roff + q];
+      }
 #pragma unroll
       for (int s = 0; s < SL; ++s) {
-        const float2 xv = C.sx[idx[s]];
-        acc.x = fmaf(wv[s].x, xv.x, fmaf(-wv[s].y, xv.y, acc.x));
-        acc.y = fmaf(wv[s].x, xv.y, fmaf(wv[s].y, xv.x, acc.y));
+        const int t = lane + 32 * s;
+        const float2 w = t < nn ? w_at<WT>(sw, beg + t) : make_float2(0.f, 0.f);
+        const float2 c = cmulc(w, r);
+        ar[s].x += c.x;
+        ar[s].y += c.y;
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-      }
-      if (MODE == G_DEGRID) {
-        if (lane == 0) A.y_out[A.perm[ch.row_begin + q]] = acc;
-        continue;
-      }
-      r = acc;
-      if (A.y_in) r = csub(r, syv[roff + q]);
-    } else {
-      r = syv[roff + q];
     }
+    if (MODE != G_DEGRID) {
 #pragma unroll
-    for (int s = 0; s < SL; ++s) {
-      if (lane + 32 * s < nn) {  // a predicated pair of atomics, no divergent branch
-        const float2 c = cmulc(wv[s], r);
-        atomicAdd(&C.sy_re[idx[s]], c.x);
-        atomicAdd(&C.sy_im[idx[s]], c.y);
+      for (int s = 0; s < SL; ++s) {
+        if (lane + 32 * s < nn) {  // a predicated pair of atomics, no divergent branch
+          atomicAdd(&C.sy_re[idx[s]], ar[s].x);
+          atomicAdd(&C.sy_im[idx[s]], ar[s].y);
+        }
       }
     }
   }
@@ -332,9 +352,10 @@ __global__ void __launch_bounds__(GPASS_THREADS) gpass(GArgs A) {
       // a warp works on the stage only when all of its lanes saw the copy land
       if (__all_sync(0xffffffffu, ok)) {
         const unsigned char* stage = stages + st * L::SIZE;
-        // rows are dealt to warps round robin over the whole stream, so no warp idles per chunk
+        // runs are dealt to warps round robin over the whole stream, so no warp idles per chunk
         const int q0 = warp >= rb ? warp - rb : warp - rb + NCW;
-        if (ch.nn * ch.nrows != ch.ntaps || (ch.tap_begin & 7LL) + ch.ntaps > CHUNK_TAPS + 16) {
+        if (ch.nn * ch.nrows != ch.ntaps || (ch.tap_begin & 7LL) + ch.ntaps > CHUNK_TAPS + 16 ||
+            ch.nruns < 1 || ch.nruns > ch.nrows || (ch.run_begin & 15LL) + ch.nruns + 1 > CHUNK_ROWS + 32) {
           if (lane == 0) atomicOr(A.status, 4);  // inconsistent work list: skip the chunk
         } else if (ch.nn <= 64) {
           process_chunk<MODE, WT, 2>(A, ch, stage, q0, C);
@@ -346,7 +367,7 @@ __global__ void __launch_bounds__(GPASS_THREADS) gpass(GArgs A) {
           process_chunk<MODE, WT, 8>(A, ch, stage, q0, C);
         }
       }
-      rb = (rb + ch.nrows) % NCW;
+      rb = (rb + (ch.nruns > 0 ? ch.nruns : 0)) % NCW;
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[st]);  // this warp is done with the stage
       if (++st == NSTAGE) {
@@ -435,6 +456,8 @@ int gridding_pitch(pnp_plan* p, const int64_t* rows_per_J) {
   int optin = 0;
   PNP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
   const int stage = NSTAGE * std::max(StageLayout<float2>::SIZE, StageLayout<__nv_bfloat162>::SIZE);
+  if (2 * ((((S * S + 32) * 8 + 127) & ~127)) + stage + 1024 > optin)
+    return fail(PNP_ERR_UNSUPPORTED, "gridding tile and pipeline stages do not fit in shared memory");
   int best = S;
   int64_t best_cost = -1;
   for (int P = S; P < S + 32; ++P) {
@@ -480,6 +503,7 @@ int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out) {
   A.rowptr = p->d_rowptr;
   A.w = p->d_w;
   A.cells = p->d_cells;
+  A.runs = p->d_runs;
   A.perm = p->d_perm;
   A.y_in = (mode == G_DEGRID || y_user == nullptr) ? nullptr : p->d_ysorted;
   A.y_out = y_out;

@@ -192,6 +192,7 @@ int dev_alloc(pnp_plan* p, T** ptr, size_t count) {
 int build_units(pnp_plan* p) {
   std::vector<Unit> units;
   std::vector<Chunk> chunks;
+  std::vector<uint8_t> runs;
   const int64_t M = p->M;
   auto nnz_of = [&](int64_t i) { return p->h_rowptr[i + 1] - p->h_rowptr[i]; };
   int64_t i = 0;
@@ -218,7 +219,17 @@ int build_units(pnp_plan* p) {
       ch.nrows = nr;
       ch.ntaps = (int)nt;
       ch.nn = (int)row_nnz;
-      ch.pad = 0;
+      // runs: consecutive rows whose first tap is the same cell share their whole tap window
+      // (same support), at most RUN_MAX rows each
+      ch.run_begin = (long long)runs.size();
+      int last = 0;
+      for (int q = 0; q < nr; ++q)
+        if (q == 0 || p->h_start[ch.row_begin + q] != p->h_start[ch.row_begin + q - 1] || q - last == RUN_MAX) {
+          runs.push_back((uint8_t)q);
+          last = q;
+        }
+      ch.nruns = (int)((long long)runs.size() - ch.run_begin);
+      runs.push_back((uint8_t)nr);
       chunks.push_back(ch);
       unit_taps += nt;
     }
@@ -235,10 +246,19 @@ int build_units(pnp_plan* p) {
     p->device_bytes -= p->n_chunks * (int64_t)sizeof(Chunk);
     p->d_chunks = nullptr;
   }
+  if (p->d_runs) {
+    cudaFree(p->d_runs);
+    p->device_bytes -= p->n_runs + 32;
+    p->d_runs = nullptr;
+  }
   p->n_units = (int64_t)units.size();
   p->n_chunks = (int64_t)chunks.size();
   if (int rc = dev_alloc(p, &p->d_units, units.size())) return rc;
   if (int rc = dev_alloc(p, &p->d_chunks, chunks.size())) return rc;
+  p->n_runs = (int64_t)runs.size();
+  runs.resize(runs.size() + 32, 0);  // the stage copies 16-byte windows around each list
+  if (int rc = dev_alloc(p, &p->d_runs, runs.size())) return rc;
+  PNP_CUDA(cudaMemcpy(p->d_runs, runs.data(), runs.size(), cudaMemcpyHostToDevice));
   if (!units.empty()) {
     PNP_CUDA(cudaMemcpy(p->d_units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice));
     PNP_CUDA(cudaMemcpy(p->d_chunks, chunks.data(), chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice));
@@ -265,6 +285,7 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
   p->ntc = ntc;
   std::vector<RowGeom> geom(M);
   std::vector<int32_t> key(M);
+  std::vector<uint16_t> startc(M);  // first tap's cell within its tile
   int Jmax = J;
   double amax = 0.0;
   for (int64_t m = 0; m < M; ++m) {
@@ -285,6 +306,7 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     g.s1 = (int)std::floor(g.kap1 - 0.5 * g.J) + 1;
     const int f0 = ((g.s0 % K) + K) % K, f1 = ((g.s1 % K) + K) % K;
     key[m] = ((f1 / p->tile) * ntc + (f0 / p->tile)) * p->nblocks + (block ? block[m] : 0);
+    startc[m] = (uint16_t)((f1 % p->tile) * p->tile + (f0 % p->tile));
     Jmax = std::max(Jmax, g.J);
     amax = std::max(amax, std::fabs(g.a));
     geom[m] = g;
@@ -297,14 +319,25 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     if (int rc = gridding_pitch(p, rows_per_J.data())) return rc;
   }
 
-  // stable LSD counting sort: first by support J, then by (tile, block) key, so that rows of
-  // one tile come out grouped by J (each gridding chunk then holds rows of a single J)
+  // stable LSD counting sort: by the first tap's cell in the tile, then by support J, then by
+  // (tile, block) key, so that rows of one tile come out grouped by J (each gridding chunk then
+  // holds rows of a single J) and, within that, rows with the same tap window are adjacent
+  // (the gridding pass gathers and scatters such a run once)
   std::vector<int32_t> by_j(M);
   {
+    const int nc = p->tile * p->tile;
+    std::vector<int64_t> cc(nc + 1, 0);
+    for (int64_t m = 0; m < M; ++m) cc[startc[m] + 1]++;
+    for (int c = 0; c < nc; ++c) cc[c + 1] += cc[c];
+    std::vector<int32_t> by_c(M);
+    for (int64_t m = 0; m < M; ++m) by_c[cc[startc[m]]++] = (int32_t)m;
     std::vector<int64_t> cj(18, 0);
     for (int64_t m = 0; m < M; ++m) cj[geom[m].J + 1]++;
     for (int j = 0; j < 17; ++j) cj[j + 1] += cj[j];
-    for (int64_t m = 0; m < M; ++m) by_j[cj[geom[m].J]++] = (int32_t)m;
+    for (int64_t i = 0; i < M; ++i) {
+      const int32_t m = by_c[i];
+      by_j[cj[geom[m].J]++] = m;
+    }
   }
   const int64_t nkeys = (int64_t)ntc * ntc * p->nblocks;
   std::vector<int64_t> cnt(nkeys + 1, 0);
@@ -321,11 +354,13 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
   std::vector<int32_t>().swap(by_j);
   std::vector<RowGeom> sgeom(M);
   p->h_key.assign(M, 0);
+  p->h_start.assign(M, 0);
   p->h_rowptr.assign(M + 1, 0);
   for (int64_t i = 0; i < M; ++i) {
     const int64_t m = p->h_perm[i];
     sgeom[i] = geom[m];
     p->h_key[i] = key[m];
+    p->h_start[i] = startc[m];
     p->h_rowptr[i + 1] = p->h_rowptr[i] + (int64_t)geom[m].J * geom[m].J;
   }
   p->nnz = p->h_rowptr[M];

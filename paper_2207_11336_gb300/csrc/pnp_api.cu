@@ -63,6 +63,7 @@ void free_plan(pnp_plan* p) {
   cudaFree(p->d_tmp);
   cudaFree(p->d_w);
   cudaFree(p->d_cells);
+  cudaFree(p->d_runs);
   cudaFree(p->d_rowptr);
   cudaFree(p->d_perm);
   cudaFree(p->d_ysorted);
