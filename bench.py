@@ -318,6 +318,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     plan = pnp.Plan(n, K, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"],
                     block=prob["block"], nblocks=BLOCKS[wl["name"]], stream=stream)
+    tune = plan.autotune(reps=2)   # run cap x unit size of the gridding pass, timed on this GPU
     info = plan.info
     x_true = torch.from_numpy(prob["x_true"].astype(np.float32)).cuda()
     y0 = plan.phi_forward(x_true)
@@ -437,7 +438,8 @@ def run_gpu(args):
                "data": "synthetic", "impl": "gpu",
                "config": {"workload": desc, "parallelism": f"replicas{ws}",
                           "l2": "inputs larger than L2 (G %.1f GB)" % (info["nnz"] * 10 / 1e9),
-                          "nnz": info["nnz"], "denoiser": "cnn" if learned else "haar", "graph": True},
+                          "nnz": info["nnz"], "denoiser": "cnn" if learned else "haar", "graph": True,
+                          "gridding_autotune": tune, "region_pitch": info["region_pitch"]},
                "clocks": clk.summary(),
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": M * 8,
                        "d2h_bytes_per_step": 16},

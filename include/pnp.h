@@ -91,6 +91,8 @@ typedef struct pnp_plan_info {
   int region_pitch;     /* row pitch (cells) of the gridding pass's shared-memory
                            grid regions, chosen at plan time to limit bank
                            conflicts for the plan's mix of supports J        */
+  int run_max;          /* rows at most per run of rows sharing a tap window  */
+  int64_t unit_nnz;     /* taps at most per gridding work unit                */
 } pnp_plan_info;
 
 /* ------------------------------------------------------------------ plans */
@@ -123,6 +125,17 @@ int pnp_plan_get_info(const pnp_plan* plan, pnp_plan_info* info);
 /* Set the rows per work unit of the gridding kernels (autotuner hook; 0 keeps
  * the current choice).  Rebuilds the work list only; G is unchanged. */
 int pnp_plan_set_unit_nnz(pnp_plan* plan, int64_t unit_nnz);
+
+/* Autotuner of the gridding pass's work decomposition (a performance setting
+ * with no counterpart in the paper; results change only in the order of the
+ * floating-point sums).  Times `reps` fused gridding passes on the plan's
+ * stream for every pair of run cap (rows at most per run of rows sharing a tap
+ * window: 3, 4, 6, 8) and unit size (2^16, 2^17, 2^18 taps), keeps the fastest
+ * and rebuilds the work list for it (G is unchanged).  Synchronous; the output
+ * grid is left cleared.  Outputs (each may be NULL): the chosen run cap and
+ * unit size, and the chosen pass's mean time in ms (-1 for an empty operator).
+ * reps must lie in [1, 100]. */
+int pnp_plan_autotune(pnp_plan* plan, int reps, int* run_max_out, int64_t* unit_nnz_out, double* ms_out);
 
 /* Device-side status flags of the plan's kernels (synchronous read).  Bit 0:
  * a gridding tap fell outside its tile's staged shared-memory region and was

@@ -31,7 +31,7 @@ EXPORTED = [
     "pnp_last_error", "pnp_kernel_launch_count", "pnp_plan_set_timing", "pnp_plan_read_timing",
     "pnp_plan_device_status", "pnp_haar_denoise_noalloc", "pnp_den_device_status",
     "pnp_cnn_trainer_create", "pnp_cnn_trainer_destroy", "pnp_cnn_train_step", "pnp_cnn_trainer_read",
-    "pnp_cnn_num_params", "pnp_cnn_trainer_set_lr",
+    "pnp_cnn_num_params", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune",
 ]
 
 
@@ -55,7 +55,8 @@ class _Info(C.Structure):
     _fields_ = [("n", C.c_int), ("K", C.c_int), ("J", C.c_int), ("weight_dtype", C.c_int),
                 ("tile", C.c_int), ("nblocks", C.c_int), ("M", C.c_int64), ("nnz", C.c_int64),
                 ("n_units", C.c_int64), ("beta", C.c_double), ("dl", C.c_double),
-                ("device_bytes", C.c_int64), ("region_pitch", C.c_int)]
+                ("device_bytes", C.c_int64), ("region_pitch", C.c_int), ("run_max", C.c_int),
+                ("unit_nnz", C.c_int64)]
 
 
 _lib = None
@@ -75,6 +76,7 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_plan_destroy.restype = None
     L.pnp_plan_get_info.argtypes = [vp, C.POINTER(_Info)]
     L.pnp_plan_set_unit_nnz.argtypes = [vp, i64]
+    L.pnp_plan_autotune.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(dbl)]
     L.pnp_plan_export_rows.argtypes = [vp, vp, i64, vp, vp, vp]
     L.phi_forward.argtypes = [vp, vp, vp]
     L.phi_adjoint.argtypes = [vp, vp, vp]
@@ -105,7 +107,7 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
                  "pnp_den_create_cnn", "denoise", "pnp_fb_run", "pnp_plan_set_timing",
                  "pnp_plan_read_timing", "pnp_plan_device_status", "pnp_haar_denoise_noalloc",
                  "pnp_den_device_status", "pnp_cnn_trainer_create", "pnp_cnn_train_step",
-                 "pnp_cnn_trainer_read", "pnp_cnn_trainer_set_lr"):
+                 "pnp_cnn_trainer_read", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -197,6 +199,12 @@ class Plan:
 
     def set_unit_nnz(self, unit_nnz: int):
         _check(lib().pnp_plan_set_unit_nnz(self._h, int(unit_nnz)))
+
+    def autotune(self, reps: int = 2) -> dict:
+        """Time the gridding pass's run cap x unit size candidates and keep the fastest."""
+        r, u, ms = C.c_int(), C.c_int64(), C.c_double()
+        _check(lib().pnp_plan_autotune(self._h, int(reps), C.byref(r), C.byref(u), C.byref(ms)))
+        return {"run_max": r.value, "unit_nnz": u.value, "gridding_ms": ms.value}
 
     def device_status(self) -> int:
         """Device status flags (0 when every kernel check passed)."""

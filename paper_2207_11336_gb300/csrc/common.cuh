@@ -71,7 +71,7 @@ struct Chunk {
   int nn;     // taps per row (J^2, the same for every row of the chunk)
   int nruns;  // runs of rows sharing one tap window; the list holds nruns + 1 row offsets
 };
-constexpr int RUN_MAX = 6;         // rows per run at most (keeps the consumer warps balanced)
+constexpr int RUN_MAX = 6;         // default cap on rows per run (keeps the consumer warps balanced)
 
 struct Unit {
   long long chunk_begin;
@@ -94,6 +94,7 @@ struct pnp_plan {
   int ntc = 0;         // tiles per grid side, ceil(K / tile)
   int slots = 8;       // register slots per lane per row (32*slots >= Jmax^2)
   int pitch = 0;       // row pitch (cells) of the staged gridding regions (0: the region side)
+  int run_max = pnp::RUN_MAX;  // rows per run of a shared tap window, at most
   int rpw = 2;         // rows per warp in flight
   int64_t M = 0, nnz = 0, unit_nnz = 1 << 17;
   double beta = 0, dl = 0;

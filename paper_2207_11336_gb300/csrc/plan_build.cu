@@ -220,11 +220,11 @@ int build_units(pnp_plan* p) {
       ch.ntaps = (int)nt;
       ch.nn = (int)row_nnz;
       // runs: consecutive rows whose first tap is the same cell share their whole tap window
-      // (same support), at most RUN_MAX rows each
+      // (same support), at most run_max rows each
       ch.run_begin = (long long)runs.size();
       int last = 0;
       for (int q = 0; q < nr; ++q)
-        if (q == 0 || p->h_start[ch.row_begin + q] != p->h_start[ch.row_begin + q - 1] || q - last == RUN_MAX) {
+        if (q == 0 || p->h_start[ch.row_begin + q] != p->h_start[ch.row_begin + q - 1] || q - last == p->run_max) {
           runs.push_back((uint8_t)q);
           last = q;
         }

@@ -238,6 +238,8 @@ int pnp_plan_get_info(const pnp_plan* p, pnp_plan_info* info) {
   info->dl = p->dl;
   info->device_bytes = p->device_bytes;
   info->region_pitch = p->pitch > 0 ? p->pitch : p->tile + p->Jmax - 1;
+  info->run_max = p->run_max;
+  info->unit_nnz = p->unit_nnz;
   return PNP_OK;
 }
 
@@ -247,6 +249,72 @@ int pnp_plan_set_unit_nnz(pnp_plan* p, int64_t unit_nnz) {
   PNP_CUDA(cudaStreamSynchronize(p->stream));
   p->unit_nnz = unit_nnz;
   return build_units(p);
+}
+
+int pnp_plan_autotune(pnp_plan* p, int reps, int* run_max_out, int64_t* unit_nnz_out, double* ms_out) {
+  if (!p || reps < 1 || reps > 100) return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  PNP_CUDA(cudaStreamSynchronize(p->stream));
+  const int old_run = p->run_max;
+  const int64_t old_unit = p->unit_nnz;
+  int best_run = old_run;
+  int64_t best_unit = old_unit;
+  float best_ms = -1.f;
+  if (p->M > 0 && p->n_units > 0) {
+    const int runs[] = {3, 4, 6, 8};
+    const int64_t units[] = {int64_t(1) << 16, int64_t(1) << 17, int64_t(1) << 18};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PNP_CUDA(cudaEventCreate(&e0));
+    PNP_CUDA(cudaEventCreate(&e1));
+    const bool saved_timing = p->timing;
+    p->timing = false;
+    int rc = PNP_OK;
+    for (int r : runs) {
+      for (int64_t u : units) {
+        p->run_max = r;
+        p->unit_nnz = u;
+        if ((rc = build_units(p))) break;
+        if ((rc = gridding_pass(p, G_FUSED, nullptr, nullptr))) break;  // warm-up
+        if (cudaEventRecord(e0, p->stream) != cudaSuccess) {
+          cudaGetLastError();
+          rc = fail(PNP_ERR_CUDA, "autotune: event record failed");
+          break;
+        }
+        for (int i = 0; i < reps && !rc; ++i) rc = gridding_pass(p, G_FUSED, nullptr, nullptr);
+        if (rc) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          cudaGetLastError();
+          rc = fail(PNP_ERR_CUDA, "autotune: timing failed");
+          break;
+        }
+        ms /= reps;
+        if (best_ms < 0.f || ms < best_ms) {
+          best_ms = ms;
+          best_run = r;
+          best_unit = u;
+        }
+      }
+      if (rc) break;
+    }
+    p->timing = saved_timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the timed passes accumulated into the output grid: start it from zero again
+    if (!rc && cudaMemsetAsync(p->d_gridB, 0, (size_t)p->K * p->K * sizeof(float2), p->stream) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(PNP_ERR_CUDA, "autotune: clearing the grid failed");
+    }
+    p->run_max = rc ? old_run : best_run;
+    p->unit_nnz = rc ? old_unit : best_unit;
+    if (int rc2 = build_units(p)) return rc2;
+    if (rc) return rc;
+    PNP_CUDA(cudaStreamSynchronize(p->stream));
+  }
+  if (run_max_out) *run_max_out = p->run_max;
+  if (unit_nnz_out) *unit_nnz_out = p->unit_nnz;
+  if (ms_out) *ms_out = best_ms;
+  return PNP_OK;
 }
 
 int pnp_plan_device_status(pnp_plan* p, int* flags) {

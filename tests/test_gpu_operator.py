@@ -181,6 +181,27 @@ def test_unit_size_does_not_change_result():
     assert rel_l2(y1, y0) <= 1e-6
 
 
+def test_autotune_keeps_results_and_reports_its_choice():
+    """The tuner only changes the work list: gradient steps agree up to summation order."""
+    n, K, M = 64, 128, 20000
+    pr = _problem(n, K, M, with_w=True, seed=9)
+    gpu, ora = _plans(pr, n, K)
+    yh = ora.forward(pr["x"] * 1.3) + 0.1 * synth.complex_normal(M, pr["rng"])
+    x, y = to_dev_f32(pr["x"]), to_dev_c64(yh)
+    gamma = 1.0 / M
+    g0 = to_host(gpu.grad_step(x, y, gamma))
+    choice = gpu.autotune(reps=1)
+    assert choice["run_max"] in (3, 4, 6, 8) and choice["unit_nnz"] in (1 << 16, 1 << 17, 1 << 18)
+    assert choice["gridding_ms"] > 0
+    info = gpu.info
+    assert (info["run_max"], info["unit_nnz"]) == (choice["run_max"], choice["unit_nnz"])
+    g1 = to_host(gpu.grad_step(x, y, gamma))
+    assert gpu.device_status() == 0
+    assert rel_l2((pr["x"] - g1) / gamma, (pr["x"] - g0) / gamma) <= 1e-6
+    ref = ofb.gradient_step(ora, pr["x"], yh, gamma)
+    assert rel_l2((pr["x"] - g1) / gamma, (pr["x"] - ref) / gamma) <= TOL
+
+
 def test_bf16_weights_error_is_bounded():
     n, K, M = 64, 128, 20000
     pr = _problem(n, K, M, with_w=True, seed=8)
