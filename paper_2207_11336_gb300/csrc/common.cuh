@@ -59,6 +59,9 @@ constexpr int CHUNK_ROWS = 128;
 constexpr int NSTAGE = 4;          // shared-memory pipeline depth of the gridding pass
 constexpr int GPASS_CONSUMERS = 16; // consumer warps per gridding CTA (plus one producer warp)
 constexpr int GPASS_THREADS = 32 * (GPASS_CONSUMERS + 1);
+// twiddles of the radix-16 passes 1 and 2 of the FFT: entry off(p) + r 16^p + k holds
+// exp(-2 pi i r k / 16^(p+1)), off(1) = 0, off(2) = 256 (independent of the transform length)
+constexpr int TWP_ENTRIES = 16 * 16 + 16 * 256;
 constexpr int TAP_PAD = 16;        // weights/columns are allocated nnz + TAP_PAD long
 constexpr int ROW_PAD = 4;         // row offsets M + 1 + ROW_PAD, sorted y M + ROW_PAD
 
@@ -107,6 +110,7 @@ struct pnp_plan {
   // device buffers
   float* d_cinv = nullptr;     // n: 1 / c(a - n/2)
   float2* d_tw = nullptr;      // K: exp(-2 pi i j / K)
+  float2* d_twp = nullptr;     // radix-16 pass twiddles [16 + 256][16]: see fft.cu
   float2* d_gridA = nullptr;   // K*K: F Z x   (layout [k1][k0])
   float2* d_gridB = nullptr;   // K*K: G^H r   (layout [k1][k0]); kept zero between uses
   float2* d_tmp = nullptr;     // K*n: half-transformed intermediate

@@ -136,9 +136,10 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int idx
 // s is this row's padded shared-memory buffer (K + K/16 float2).
 template <int LOGK, int DIR>
 __device__ __forceinline__ void fft_row(float2 (&v)[16], float2* s, int j,
-                                        const float2* __restrict__ tw) {
+                                        const float2* __restrict__ tw, const float2* __restrict__ twp) {
   constexpr int K = 1 << LOGK;
   constexpr int Q = LOGK / 4;
+  static_assert(Q <= 3, "the pass twiddle tables cover radix-16 passes 1 and 2");
   constexpr int REM = LOGK % 4;
   constexpr int K16 = K / 16;
 #pragma unroll
@@ -146,9 +147,11 @@ __device__ __forceinline__ void fft_row(float2 (&v)[16], float2* s, int j,
     const int Ns = 1 << (4 * p);
     const int k = j & (Ns - 1);
     if (p > 0) {
-      const int step = K >> (4 * p + 4);
+      // exp(dir 2 pi i r k / 16^(p+1)) from the pass's [r][k] table: consecutive k of a warp read
+      // consecutive entries (the full-length table would be read with a stride of r k)
+      const float2* tp = twp + (p == 1 ? 0 : 256) + k;
 #pragma unroll
-      for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twiddle<DIR>(tw, r * k * step));
+      for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twiddle<DIR>(tp, r * Ns));
     }
     dft16<DIR>(v);
     if (!(p == Q - 1 && REM == 0)) {
@@ -197,6 +200,7 @@ struct FftArgs {
   const float* x;          // P1 input image / Q2 current iterate
   const float* cinv;       // 1 / c(p)
   const float2* tw;
+  const float2* twp;       // radix-16 pass twiddles (TWP_ENTRIES)
   float2* tmp;             // T (K x n) or U (n x K)
   float2* grid;            // P2 output / Q1 input (re-zeroed)
   float* out;              // Q2 output image
@@ -223,7 +227,7 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_p1(FftArgs A) {
     v[i] = (live && b >= 0) ? make_float2(A.x[(size_t)a * n + b] * ca * A.cinv[b], 0.f)
                             : make_float2(0.f, 0.f);
   }
-  fft_row<LOGK, -1>(v, s, j, A.tw);
+  fft_row<LOGK, -1>(v, s, j, A.tw, A.twp);
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < 16; ++i) s[PADI(j + i * T)] = v[i];
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_p2(FftArgs A) {
     const int a = unpad_index(j + i * T, n, K);
     v[i] = a >= 0 ? row[a] : make_float2(0.f, 0.f);
   }
-  fft_row<LOGK, -1>(v, s, j, A.tw);
+  fft_row<LOGK, -1>(v, s, j, A.tw, A.twp);
   float2* g = A.grid + (size_t)k1 * K;
 #pragma unroll
   for (int i = 0; i < 16; ++i) g[j + i * T] = v[i];
@@ -273,7 +277,7 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_q1(FftArgs A) {
   for (int i = 0; i < 16; ++i) v[i] = g[j + i * T];
 #pragma unroll
   for (int i = 0; i < 16; ++i) g[j + i * T] = make_float2(0.f, 0.f);
-  fft_row<LOGK, +1>(v, s, j, A.tw);
+  fft_row<LOGK, +1>(v, s, j, A.tw, A.twp);
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < 16; ++i) s[PADI(j + i * T)] = v[i];
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(FftArgs A) {
     float2 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = row[j + i * T];
-    fft_row<LOGK, +1>(v, smem, j, A.tw);
+    fft_row<LOGK, +1>(v, smem, j, A.tw, A.twp);
     const float ca = A.cinv[a];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
@@ -436,6 +440,7 @@ int fft_forward(pnp_plan* p, const float* x) {
   A.x = x;
   A.cinv = p->d_cinv;
   A.tw = p->d_tw;
+  A.twp = p->d_twp;
   A.tmp = p->d_tmp;
   A.grid = p->d_gridA;
   cudaEvent_t ev;
@@ -463,6 +468,7 @@ int fft_adjoint(pnp_plan* p, int mode, const float* x, float* out, float gamma, 
   A.x = x;
   A.cinv = p->d_cinv;
   A.tw = p->d_tw;
+  A.twp = p->d_twp;
   A.tmp = p->d_tmp;
   A.grid = p->d_gridB;
   A.out = out;

@@ -408,6 +408,7 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
   const size_t KK = (size_t)K * K;
   if (int rc = dev_alloc(p, &p->d_cinv, n)) return rc;
   if (int rc = dev_alloc(p, &p->d_tw, K)) return rc;
+  if (int rc = dev_alloc(p, &p->d_twp, TWP_ENTRIES)) return rc;
   if (int rc = dev_alloc(p, &p->d_gridA, KK)) return rc;
   if (int rc = dev_alloc(p, &p->d_gridB, KK)) return rc;
   if (int rc = dev_alloc(p, &p->d_tmp, (size_t)K * n)) return rc;
@@ -435,6 +436,18 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     if (int rc = dev_alloc(p, &p->d_img[i], (size_t)n * n)) return rc;
   PNP_CUDA(cudaMemcpy(p->d_cinv, cinv.data(), n * sizeof(float), cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(p->d_tw, tw.data(), K * sizeof(float2), cudaMemcpyHostToDevice));
+  {
+    std::vector<float2> twp(TWP_ENTRIES);
+    for (int q = 1, off = 0; q <= 2; off += 16 * (1 << (4 * q)), ++q) {
+      const int Ns = 1 << (4 * q);
+      for (int r = 0; r < 16; ++r)
+        for (int k = 0; k < Ns; ++k) {
+          const double ang = -2.0 * M_PI * (double)(r * k) / (16.0 * Ns);
+          twp[off + r * Ns + k] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+        }
+    }
+    PNP_CUDA(cudaMemcpy(p->d_twp, twp.data(), TWP_ENTRIES * sizeof(float2), cudaMemcpyHostToDevice));
+  }
   PNP_CUDA(cudaMemset(p->d_gridB, 0, KK * sizeof(float2)));
   PNP_CUDA(cudaMemset(p->d_acc, 0, 8 * sizeof(double)));
   PNP_CUDA(cudaMemset(p->d_status, 0, 4 * sizeof(int)));

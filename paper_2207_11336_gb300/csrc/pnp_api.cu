@@ -58,6 +58,7 @@ void free_plan(pnp_plan* p) {
   clear_timing(p);
   cudaFree(p->d_cinv);
   cudaFree(p->d_tw);
+  cudaFree(p->d_twp);
   cudaFree(p->d_gridA);
   cudaFree(p->d_gridB);
   cudaFree(p->d_tmp);
