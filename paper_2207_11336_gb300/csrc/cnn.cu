@@ -69,6 +69,7 @@ constexpr int EPI_WARPS = 16;                           // 2 row parities x 2 ch
 constexpr int MMA_WARP = EPI_WARPS, TMA_WARP = EPI_WARPS + 1;
 constexpr int CONV_THREADS = (EPI_WARPS + 2) * 32;
 constexpr int LAST_ROWS = 2;                            // cnn_last: output rows per block
+constexpr int FIRST_ROWS = 8;                           // cnn_first: image rows per block
 constexpr int LAST_BYTES = (LAST_ROWS + 2) * ROW_BYTES; // its staged rows (66560)
 constexpr uint32_t CNN_WAIT_LIMIT = 1u << 26;
 
@@ -430,14 +431,16 @@ struct FirstArgs {
 constexpr int SEG_STRIDE = 9;  // uint4 per pixel in shared memory (8 channel blocks + 16 B of padding)
 
 __global__ void __launch_bounds__(128) cnn_first(FirstArgs A) {
-  // grid (x segments of 128, row y, facet f): thread m computes the 64 channels of pixel x0 + m;
-  // the block then writes each 8-channel plane of the segment as one contiguous 2-KB run
+  // grid (x segments of 128, groups of FIRST_ROWS rows, facet f): thread m computes the 64
+  // channels of pixel x0 + m row after row (a rolling 3 x 3 window of z in registers); the
+  // block writes each 8-channel plane of a row segment as one contiguous 2-KB run
   __shared__ __align__(16) uint4 seg[TILE_PX * SEG_STRIDE];
   __shared__ __align__(16) float sw[CH * 9];  // [c / 4][tap][c % 4]: one float4 per (4 channels, tap)
   __shared__ __align__(16) float sb[CH];
-  const int f = blockIdx.z, y = blockIdx.y, x0 = blockIdx.x * TILE_PX;
+  const int f = blockIdx.z, ya = blockIdx.y * FIRST_ROWS, x0 = blockIdx.x * TILE_PX;
   const int4 fc = A.facets[f];  // R0, C0, Hf, Wf
-  if (y >= fc.z || x0 >= fc.w) return;  // outside the facet: the canvas keeps its zeros
+  if (ya >= fc.z || x0 >= fc.w) return;  // outside the facet: the canvas keeps its zeros
+  const int yb = min(ya + FIRST_ROWS, fc.z);
   for (int i = threadIdx.x; i < CH * 9; i += blockDim.x) {
     const int ch = i / 9, t = i % 9;
     sw[((ch >> 2) * 9 + t) * 4 + (ch & 3)] = A.w1[i];
@@ -447,48 +450,57 @@ __global__ void __launch_bounds__(128) cnn_first(FirstArgs A) {
   const float4* sw4 = reinterpret_cast<const float4*>(sw);
   const float4* sb4 = reinterpret_cast<const float4*>(sb);
   const int x = x0 + threadIdx.x;
-  uint4 pk[8];
-  if (x < fc.w) {
-    const float* zf = A.z + (size_t)f * A.zplane;
-    float zin[9];
+  const bool live = x < fc.w;
+  const float* zf = A.z + (size_t)f * A.zplane;
+  auto zat = [&](int yy, int xx) -> float {
+    return (live && yy >= 0 && yy < fc.z && xx >= 0 && xx < fc.w) ? zf[(size_t)(fc.x + yy) * A.n + fc.y + xx] : 0.f;
+  };
+  float zin[9];  // rows y-1, y, y+1 x columns x-1, x, x+1
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
-      zin[t] = (yy >= 0 && yy < fc.z && xx >= 0 && xx < fc.w) ? zf[(size_t)(fc.x + yy) * A.n + fc.y + xx] : 0.f;
-    }
+  for (int t = 0; t < 6; ++t) zin[t + 3] = zat(ya + t / 3 - 1, x + t % 3 - 1);
+  const size_t plane = (size_t)A.Wc * 8;
+  for (int y = ya; y < yb; ++y) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      uint32_t wv[4];
+    for (int t = 0; t < 6; ++t) zin[t] = zin[t + 3];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int g = 2 * q + h;
-        float4 a = sb4[g];
+    for (int t = 0; t < 3; ++t) zin[6 + t] = zat(y + 1, x + t - 1);
+    uint4 pk[8];
+    if (live) {
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-          const float4 w = sw4[g * 9 + t];
-          a.x = fmaf(w.x, zin[t], a.x);
-          a.y = fmaf(w.y, zin[t], a.y);
-          a.z = fmaf(w.z, zin[t], a.z);
-          a.w = fmaf(w.w, zin[t], a.w);
+      for (int q = 0; q < 8; ++q) {
+        uint32_t wv[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int g = 2 * q + h;
+          float4 a = sb4[g];
+#pragma unroll
+          for (int t = 0; t < 9; ++t) {
+            const float4 w = sw4[g * 9 + t];
+            a.x = fmaf(w.x, zin[t], a.x);
+            a.y = fmaf(w.y, zin[t], a.y);
+            a.z = fmaf(w.z, zin[t], a.z);
+            a.w = fmaf(w.w, zin[t], a.w);
+          }
+          __nv_bfloat162 h0 = __floats2bfloat162_rn(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
+          __nv_bfloat162 h1 = __floats2bfloat162_rn(fmaxf(a.z, 0.f), fmaxf(a.w, 0.f));
+          wv[2 * h] = *reinterpret_cast<uint32_t*>(&h0);
+          wv[2 * h + 1] = *reinterpret_cast<uint32_t*>(&h1);
         }
-        __nv_bfloat162 h0 = __floats2bfloat162_rn(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
-        __nv_bfloat162 h1 = __floats2bfloat162_rn(fmaxf(a.z, 0.f), fmaxf(a.w, 0.f));
-        wv[2 * h] = *reinterpret_cast<uint32_t*>(&h0);
-        wv[2 * h + 1] = *reinterpret_cast<uint32_t*>(&h1);
+        pk[q] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
       }
-      pk[q] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) pk[q] = make_uint4(0u, 0u, 0u, 0u);
     }
-  } else {
+    __syncthreads();  // the previous row's segment has been stored
 #pragma unroll
-    for (int q = 0; q < 8; ++q) pk[q] = make_uint4(0u, 0u, 0u, 0u);
-  }
-#pragma unroll
-  for (int q = 0; q < 8; ++q) seg[threadIdx.x * SEG_STRIDE + q] = pk[q];
-  __syncthreads();
-  const size_t base = canvas_index(f, y, x0, 0, A.Hc, A.Wc), plane = (size_t)A.Wc * 8;
-  for (int i = threadIdx.x; i < TILE_PX * 8; i += blockDim.x) {
-    const int q = i / TILE_PX, px = i % TILE_PX;
-    *reinterpret_cast<uint4*>(A.out + base + q * plane + px * 8) = seg[px * SEG_STRIDE + q];
+    for (int q = 0; q < 8; ++q) seg[threadIdx.x * SEG_STRIDE + q] = pk[q];
+    __syncthreads();
+    const size_t base = canvas_index(f, y, x0, 0, A.Hc, A.Wc);
+    for (int i = threadIdx.x; i < TILE_PX * 8; i += blockDim.x) {
+      const int q = i / TILE_PX, px = i % TILE_PX;
+      *reinterpret_cast<uint4*>(A.out + base + q * plane + px * 8) = seg[px * SEG_STRIDE + q];
+    }
   }
 }
 
@@ -509,15 +521,15 @@ struct LastArgs {
 __device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
 
-__global__ void __launch_bounds__(256) cnn_last(LastArgs A, const __grid_constant__ CUtensorMap tmap) {
-  // grid (core column segments of 128, core row pairs, facet): one TMA load stages facet rows
-  // y0-1 .. y0+2, pixels x0-1 .. x0+128 of the layer-7 activations (zero outside the canvas), in
+__global__ void __launch_bounds__(LAST_ROWS * TILE_PX) cnn_last(LastArgs A, const __grid_constant__ CUtensorMap tmap) {
+  // grid (core column segments of 128, groups of LAST_ROWS core rows, facet): one TMA load stages
+  // facet rows y0-1 .. y0+LAST_ROWS, pixels x0-1 .. x0+128 of the layer-7 activations (zero outside the canvas), in
   // the convolution's shared-memory layout; thread (r, m) then computes N(z) for core pixel
   // (y0 + r, x0 + m) and writes max(0, z - N(z)) with its FP64 stopping-test terms
   extern __shared__ __align__(1024) unsigned char st[];  // [LAST_ROWS + 2][8][STAGE_PX][8] BF16
   __shared__ __align__(16) float sw[9 * CH];
   __shared__ uint64_t full;
-  __shared__ double red[2 * 8];
+  __shared__ double red[2 * LAST_ROWS * TILE_PX / 32];
   const int f = blockIdx.z;
   const int4 core = A.cores[f];  // r0, r1, c0, c1
   const int4 fc = A.facets[f];   // R0, C0, Hf, Wf
@@ -544,7 +556,7 @@ __global__ void __launch_bounds__(256) cnn_last(LastArgs A, const __grid_constan
   double s0 = 0.0, s1 = 0.0;
   if (iy < core.y && ix < core.w) {
     const float4* sw4 = reinterpret_cast<const float4*>(sw);
-    float nz = A.b8;
+    float acc[4] = {A.b8, 0.f, 0.f, 0.f};  // four partial sums: shorter dependency chains
 #pragma unroll 1
     for (int t = 0; t < 9; ++t) {
       const unsigned char* src = st + (r + t / 3) * ROW_BYTES + (m + t % 3) * 16;
@@ -552,16 +564,18 @@ __global__ void __launch_bounds__(256) cnn_last(LastArgs A, const __grid_constan
       for (int cb = 0; cb < 8; ++cb) {
         const uint4 v = *reinterpret_cast<const uint4*>(src + cb * KB_BYTES);
         const float4 wa = sw4[(t * CH + cb * 8) / 4], wb = sw4[(t * CH + cb * 8) / 4 + 1];
-        nz = fmaf(wa.x, bf16_lo(v.x), nz);
-        nz = fmaf(wa.y, bf16_hi(v.x), nz);
-        nz = fmaf(wa.z, bf16_lo(v.y), nz);
-        nz = fmaf(wa.w, bf16_hi(v.y), nz);
-        nz = fmaf(wb.x, bf16_lo(v.z), nz);
-        nz = fmaf(wb.y, bf16_hi(v.z), nz);
-        nz = fmaf(wb.z, bf16_lo(v.w), nz);
-        nz = fmaf(wb.w, bf16_hi(v.w), nz);
+        float& a = acc[cb & 3];
+        a = fmaf(wa.x, bf16_lo(v.x), a);
+        a = fmaf(wa.y, bf16_hi(v.x), a);
+        a = fmaf(wa.z, bf16_lo(v.y), a);
+        a = fmaf(wa.w, bf16_hi(v.y), a);
+        a = fmaf(wb.x, bf16_lo(v.z), a);
+        a = fmaf(wb.y, bf16_hi(v.z), a);
+        a = fmaf(wb.z, bf16_lo(v.w), a);
+        a = fmaf(wb.w, bf16_hi(v.w), a);
       }
     }
+    const float nz = (acc[0] + acc[1]) + (acc[2] + acc[3]);
     const size_t p = (size_t)iy * A.n + ix;
     const float zv = A.z[p];
     const float o = fmaxf(0.f, zv - nz);
@@ -587,7 +601,7 @@ __global__ void __launch_bounds__(256) cnn_last(LastArgs A, const __grid_constan
     __syncthreads();
     if (threadIdx.x == 0) {
       double t0 = 0.0, t1 = 0.0;
-      for (int w = 0; w < 8; ++w) {
+      for (int w = 0; w < LAST_ROWS * TILE_PX / 32; ++w) {
         t0 += red[2 * w];
         t1 += red[2 * w + 1];
       }
@@ -776,7 +790,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
   const int sms = sms_of_device();
   {
     FirstArgs F{z, n, 0, S->d_facets, S->F, S->Hc, S->Wc, S->d_w1, S->d_b, S->d_canvas[0]};
-    cnn_first<<<dim3(S->Wc / TILE_PX, S->Hc, S->F), TILE_PX, 0, s>>>(F);
+    cnn_first<<<dim3(S->Wc / TILE_PX, (S->Hc + FIRST_ROWS - 1) / FIRST_ROWS, S->F), TILE_PX, 0, s>>>(F);
     PNP_CHECK_LAUNCH();
   }
   static bool attr = false;
@@ -843,7 +857,7 @@ std::vector<int4> conv_strips(int F, const int* Hf, const int* Wf) {
 int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, const int4* facets, int F, int Hc,
                      int Wc, const float* w1, const float* b1, __nv_bfloat16* out) {
   FirstArgs A{z, n, zplane, facets, F, Hc, Wc, w1, b1, out};
-  cnn_first<<<dim3(Wc / TILE_PX, Hc, F), TILE_PX, 0, s>>>(A);
+  cnn_first<<<dim3(Wc / TILE_PX, (Hc + FIRST_ROWS - 1) / FIRST_ROWS, F), TILE_PX, 0, s>>>(A);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
