@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="C3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-bf16-g", dest="bf16_g", action="store_false",
+                    help="skip timing the plain loop with BF16 weights in G")
     ap.add_argument("--kernel-case", choices=["gridding", "cnn"], default=None,
                     help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
     ap.add_argument("--cnn-side", type=int, default=4096,
@@ -369,6 +371,22 @@ def run_gpu(args):
              "time_to_snr_s": SNR_ITERS * ms_plain / steps / 1e3,
              "snr_trace": [(i, round(s, 3)) for i, s in trace_plain[4::5]]}
     comparison = {"plain": plain}
+    if args.bf16_g:
+        # mixed precision: the same operator with G stored as BF16 complex weights (FP32 accumulation)
+        plan_bf = pnp.Plan(n, K, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"], weight_dtype="bf16",
+                           block=prob["block"], nblocks=BLOCKS[wl["name"]], stream=stream)
+        tune_bf = plan_bf.autotune(reps=2)
+        y_bf = plan_bf.phi_forward(x_true)
+        err = float(torch.linalg.vector_norm((y_bf - y0).to(torch.complex128)) /
+                    torch.linalg.vector_norm(y0.to(torch.complex128)))
+        xb = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+        plan_bf.fb_run(haar, y, x0=xb, gamma=gamma, L=L, max_iter=4, check_every=2, use_graph=True, inplace=True)
+        ms_bf, _ = _timed_loop(plan_bf, haar, y, xb, gamma, L, steps, stream)
+        comparison["plain_bf16_G"] = {"iter_per_s": ws * steps / (ms_bf / 1e3), "ms_per_iter": ms_bf / steps,
+                                      "phi_rel_l2_vs_c64_G": err, "gridding_autotune": tune_bf,
+                                      "G_bytes": plan_bf.info["nnz"] * 6}
+        plan_bf.close()
+        del plan_bf, y_bf, xb
     if learned:
         xl = torch.zeros((n, n), dtype=torch.float32, device="cuda")
         it_l, trace_l = _run_to_snr(plan, cnn, y_s, xl, gamma, L, x_true, alpha, snr_plain, SNR_MAX_ITERS)
