@@ -18,9 +18,10 @@
 //   conv64_tc   canvas -> canvas: one 64 -> 64 layer as an implicit GEMM on the
 //               5th-generation tensor cores (tcgen05.mma, FP32 accumulators in
 //               tensor memory), one 128-pixel row segment per tile;
-//   cnn_last    canvas -> image: layer 8 (64 -> 1) on CUDA cores from the same
-//               TMA-staged tile as the convolution, fused with
-//               D(z) = max(0, z - N(z)) on the facet cores and the FP64 norms.
+//   conv64_tc<16> canvas -> image: layer 8 (64 -> 1) with the same kernel, its
+//               output channel padded to the smallest MMA width (N = 16),
+//               over the facet cores only, fused with D(z) = max(0, z - N(z))
+//               and the FP64 stopping-test norms.
 //
 // conv64_tc layout.  A tile is 2 x 128 output pixels (x0 .. x0+127 of rows y,
 // y+1 of one facet).  Its inputs -- rows y-1..y+2, pixels x0-1 .. x0+128, 64
@@ -61,16 +62,20 @@ constexpr int KB_BYTES = STAGE_PX * 16;                 // one 8-channel block o
 constexpr int ROW_BYTES = 8 * KB_BYTES;                 // one staged input row, 8 channel blocks (16640)
 constexpr int IN_SLOTS = 8;                             // ring of staged input rows
 constexpr int ACC_SLOTS = 8;                            // ring of output-row accumulators in tensor memory
-constexpr int TMEM_COLS = ACC_SLOTS * CH;               // 512: all of the SM's tensor memory
-constexpr int B_GROUP_BYTES = 3 * CH * 16;              // one (dx, kb) group: [dy=2 | dy=1 | dy=0] x 64 co x 8 ci
-constexpr int B_BYTES = 3 * 8 * B_GROUP_BYTES;          // 73728
-constexpr int CONV_SMEM = IN_SLOTS * ROW_BYTES + B_BYTES;  // 206848
+// Geometry of the convolution kernel for NO output channels per pixel: 64 for the hidden layers,
+// 16 for the last layer (its single output channel padded to the smallest MMA width N = 16).
+template <int NO>
+struct ConvGeom {
+  static constexpr int TMEM_COLS = ACC_SLOTS * NO;            // 512 (NO = 64) or 128 (NO = 16) columns
+  static constexpr int B_GROUP_BYTES = 3 * NO * 16;           // one (dx, kb) group: [dy=2 | dy=1 | dy=0] x NO co x 8 ci
+  static constexpr int B_BYTES = 3 * 8 * B_GROUP_BYTES;       // 73728 (NO = 64)
+  static constexpr int SMEM = IN_SLOTS * ROW_BYTES + B_BYTES;  // 206848 (NO = 64)
+};
+constexpr int NO_LAST = 16;
 constexpr int EPI_WARPS = 16;                           // 2 row parities x 2 channel halves x 4 lane quarters
 constexpr int MMA_WARP = EPI_WARPS, TMA_WARP = EPI_WARPS + 1;
 constexpr int CONV_THREADS = (EPI_WARPS + 2) * 32;
-constexpr int LAST_ROWS = 2;                            // cnn_last: output rows per block
 constexpr int FIRST_ROWS = 8;                           // cnn_first: image rows per block
-constexpr int LAST_BYTES = (LAST_ROWS + 2) * ROW_BYTES; // its staged rows (66560)
 constexpr uint32_t CNN_WAIT_LIMIT = 1u << 26;
 
 struct CnnState {
@@ -81,6 +86,9 @@ struct CnnState {
   int4* d_cores = nullptr;               // per facet: (r0, r1, c0, c1)
   int4* d_strips = nullptr;              // conv64_tc work list (conv_strips)
   int n_strips = 0;
+  int4* d_lstrips = nullptr;             // last layer's work list: strips of the facet cores (last_strips)
+  int n_lstrips = 0;
+  __nv_bfloat16* d_wlast = nullptr;      // last layer's B operand (last_wpack_index), output channel 0 of 16
   __nv_bfloat16* d_canvas[2] = {nullptr, nullptr};
   float* d_w1 = nullptr;                 // [64][9]  (BF16-rounded values)
   float* d_b = nullptr;                  // [8][64] biases (layer 8 uses entry 0)
@@ -89,7 +97,6 @@ struct CnnState {
   int* d_status = nullptr;
   float b8 = 0.f;                        // last layer's bias (host copy)
   CUtensorMap map[2];                    // TMA descriptors of the two canvases, one-row boxes (conv64_tc)
-  CUtensorMap map_last[2];               // the same canvases, (LAST_ROWS + 2)-row boxes (cnn_last)
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -113,16 +120,6 @@ __device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
     if (ok) return true;
   }
   return false;
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(dst)), "l"(src),
-               "r"(valid ? 16 : 0)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-// arrive on the mbarrier once all cp.async copies issued so far by this thread have landed
-__device__ __forceinline__ void cp_async_arrive(uint64_t* b) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(b)) : "memory");
 }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -176,6 +173,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
 }
+__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
+  return r;
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: no swizzle, K-major canonical layout.
@@ -203,13 +205,13 @@ struct Piece {
 
 // K steps 1..11 of an input row (dx = dk / 4, K step kk = dk % 4), with compile-time offsets
 // added to the row's A descriptor and the pieces' B descriptors.
-template <int NP>
+template <int NP, int NO>
 __device__ __forceinline__ void mma_steps(uint32_t tmem, uint64_t arow, uint64_t bbase, const Piece (&pc)[2]) {
 #pragma unroll
   for (int dk = 1; dk < 12; ++dk) {
     const int dx = dk >> 2, kk = dk & 3;
     const uint64_t ad = arow + (uint64_t)((2 * kk * KB_BYTES + dx * 16) >> 4);
-    const uint64_t bo = (uint64_t)(((dx * 8 + 2 * kk) * B_GROUP_BYTES) >> 4);
+    const uint64_t bo = (uint64_t)(((dx * 8 + 2 * kk) * ConvGeom<NO>::B_GROUP_BYTES) >> 4);
 #pragma unroll
     for (int i = 0; i < NP; ++i) mma_bf16(tmem + pc[i].tcol, ad, bbase + bo + pc[i].boff, pc[i].idesc, 1u);
   }
@@ -217,27 +219,39 @@ __device__ __forceinline__ void mma_steps(uint32_t tmem, uint64_t arow, uint64_t
 
 // Pieces for output rows a..b of input row s (ring index of row 0 = g0): one, or two where the
 // accumulator ring wraps.
+template <int NO>
 __device__ __forceinline__ int make_pieces(int a, int b, int s, uint32_t g0, Piece (&pc)[2]) {
   const uint32_t k = (g0 + a) % ACC_SLOTS;
   const int n = b - a + 1, cnt = min(n, (int)(ACC_SLOTS - k));
-  pc[0] = Piece{k * CH, (uint32_t)((2 - (s - a)) * (CH * 16 >> 4)), idesc_n(cnt * CH)};
+  pc[0] = Piece{k * NO, (uint32_t)((2 - (s - a)) * (NO * 16 >> 4)), idesc_n(cnt * NO)};
   if (cnt == n) return 1;
-  pc[1] = Piece{0u, (uint32_t)((2 - (s - a - cnt)) * (CH * 16 >> 4)), idesc_n((n - cnt) * CH)};
+  pc[1] = Piece{0u, (uint32_t)((2 - (s - a - cnt)) * (NO * 16 >> 4)), idesc_n((n - cnt) * NO)};
   return 2;
 }
 
 struct ConvArgs {
   __nv_bfloat16* out;
-  const __nv_bfloat16* w;  // B operand, conv_wpack_index layout
+  const __nv_bfloat16* w;  // B operand, conv_wpack_index layout (NO = 64) or last_wpack_index (NO = 16)
   const float* bias;       // [64] (forward mode)
-  const int4* strips;      // conv_strips
+  const int4* strips;      // conv_strips, or last_strips for the last layer
   int n_strips, Hc, Wc;
   int* status;
   int mode;                    // 0: forward, out = ReLU(acc + bias); 1: backward data, out = acc * [mask > 0]
   const __nv_bfloat16* mask;   // backward data: activations whose ReLU mask gates the output (same canvas layout)
+  // last layer (NO = 16): img = max(0, z - (N + b8)) on the facet cores, FP64 stopping-test terms in acc
+  const float* z;
+  const float* x_prev;
+  float* img;
+  int n;
+  const int4* facets;  // per facet: (R0, C0, Hf, Wf)
+  const int4* cores;   // per facet: (r0, r1, c0, c1)
+  float b8;
+  double* acc;
 };
 
+template <int NO>
 __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const __grid_constant__ CUtensorMap tmap) {
+  using Gm = ConvGeom<NO>;
   extern __shared__ __align__(1024) unsigned char sm[];  // [IN_SLOTS][ROW_BYTES] input ring, then B
   unsigned char* sb = sm + IN_SLOTS * ROW_BYTES;
   __shared__ uint64_t in_full[IN_SLOTS], in_empty[IN_SLOTS], t_full[ACC_SLOTS], t_empty[ACC_SLOTS];
@@ -250,7 +264,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
   {
     const uint4* src = reinterpret_cast<const uint4*>(A.w);
     uint4* dst = reinterpret_cast<uint4*>(sb);
-    for (int i = threadIdx.x; i < B_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < Gm::B_BYTES / 16; i += blockDim.x) dst[i] = src[i];
     if (threadIdx.x < CH) s_bias[threadIdx.x] = A.bias ? A.bias[threadIdx.x] : 0.f;  // no bias in backward mode
   }
   if (threadIdx.x == 0) {
@@ -260,13 +274,14 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
     }
     for (int k = 0; k < ACC_SLOTS; ++k) {
       bar_init(&t_full[k], 1);
-      bar_init(&t_empty[k], EPI_WARPS / 2 * 32);  // the warps of one row parity drain a row
+      // a row is drained by the 8 warps of its parity (NO = 64) or the 4 warps of its phase (NO = 16)
+      bar_init(&t_empty[k], (NO == CH ? EPI_WARPS / 2 : EPI_WARPS / 4) * 32);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
   if (warp == MMA_WARP) {
-    tmem_alloc(&s_tmem, TMEM_COLS);  // ACC_SLOTS accumulators of 128 pixels x 64 channels, FP32
+    tmem_alloc(&s_tmem, Gm::TMEM_COLS);  // ACC_SLOTS accumulators of 128 pixels x NO channels, FP32
     tmem_relinquish();
   }
   fence_async_smem();  // the weights written above are read by the tensor cores (async proxy)
@@ -305,7 +320,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
     // accumulate = 0 in its own MMA on the first K step.
     if (lane == 0) {
       const uint64_t adesc0 = smem_desc(su32(sm), KB_BYTES, 128);
-      const uint64_t bdesc0 = smem_desc(su32(sb), B_GROUP_BYTES, 128);
+      const uint64_t bdesc0 = smem_desc(su32(sb), Gm::B_GROUP_BYTES, 128);
       uint32_t L = 0, g0 = 0;  // input rows consumed; ring index of the strip's first output row
       for (int strip = blockIdx.x; strip < A.n_strips && !s_abort; strip += stride) {
         const int4 S = A.strips[strip];
@@ -323,22 +338,22 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
           const int r_lo = max(0, s - 2), r_hi = min(R - 1, s);
           const uint64_t arow = adesc0 + (uint64_t)((slot * ROW_BYTES) >> 4);
           Piece pc[2];
-          const int np = make_pieces(r_lo, r_hi, s, g0, pc);
+          const int np = make_pieces<NO>(r_lo, r_hi, s, g0, pc);
           // first K step (dx = 0, kk = 0): a fresh row starts its accumulator (accumulate = 0)
           if (fresh) {
             if (r_hi > r_lo) {
               Piece p0[2];
-              const int n0 = make_pieces(r_lo, r_hi - 1, s, g0, p0);
+              const int n0 = make_pieces<NO>(r_lo, r_hi - 1, s, g0, p0);
               for (int i = 0; i < n0; ++i) mma_bf16(tmem + p0[i].tcol, arow, bdesc0 + p0[i].boff, p0[i].idesc, 1u);
             }
-            mma_bf16(tmem + ((g0 + r_hi) % ACC_SLOTS) * CH, arow, bdesc0 + 2 * (CH * 16 >> 4), idesc_n(CH), 0u);
+            mma_bf16(tmem + ((g0 + r_hi) % ACC_SLOTS) * NO, arow, bdesc0 + 2 * (NO * 16 >> 4), idesc_n(NO), 0u);
           } else {
             for (int i = 0; i < np; ++i) mma_bf16(tmem + pc[i].tcol, arow, bdesc0 + pc[i].boff, pc[i].idesc, 1u);
           }
           if (np == 1)
-            mma_steps<1>(tmem, arow, bdesc0, pc);
+            mma_steps<1, NO>(tmem, arow, bdesc0, pc);
           else
-            mma_steps<2>(tmem, arow, bdesc0, pc);
+            mma_steps<2, NO>(tmem, arow, bdesc0, pc);
           mma_commit(&in_empty[slot]);                                 // the input slot may be refilled
           if (s >= 2) mma_commit(&t_full[(g0 + s - 2) % ACC_SLOTS]);   // output row s-2 is complete
         }
@@ -349,69 +364,128 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
     }
     __syncwarp();
   } else {
-    // ---------------- epilogue: tensor memory -> bias + ReLU -> BF16 -> canvas.  Warp w drains the
-    // output rows of parity w / 8; it reads TMEM lanes 32 (w % 4) .. + 31 (the lanes a warp may
-    // access), i.e. pixels 32 (w % 4) + lane, channels 32 ((w / 4) % 2) .. + 31.
-    const int lq = warp & 3, par = warp >> 3, half = (warp >> 2) & 1;
-    const int m = lq * 32 + lane;
-    const size_t plane = (size_t)A.Wc * 8;
-    uint32_t g0 = 0;
-    bool stop = false;
-    for (int strip = blockIdx.x; strip < A.n_strips && !stop; strip += stride) {
-      const int4 S = A.strips[strip];
-      const int ya = S.z >> 16, R = S.z & 0xFFFF, Hf = S.w >> 16, Wf = S.w & 0xFFFF;
-      for (int r = (int)((g0 + par) & 1); r < R; r += 2) {  // rows whose ring index has parity par
-        const uint32_t g = g0 + r, k = g % ACC_SLOTS;
-        const bool ok = !s_abort && bar_wait(&t_full[k], (g / ACC_SLOTS) & 1);
-        if (!ok) s_abort = 1;
-        if (!__all_sync(0xffffffffu, ok)) {
-          stop = true;
-          break;
-        }
-        tc_fence_after();
-        uint32_t v[32];
-        tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(k * CH + half * 32), v);
-        tmem_wait_ld();
-        tc_fence_before();
-        bar_arrive(&t_empty[k]);  // this thread's share of the row is in registers
-        const int y = ya + r, x = S.y + m;
-        if (y >= A.Hc || x >= A.Wc) continue;
-        const bool live = x < Wf && y < Hf;  // outside the facet the canvas stays zero
-        const size_t pix = canvas_index(S.x, y, x, 32 * half, A.Hc, A.Wc);  // block q at pix + q * plane
-        uint4 pk[4];
-        uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
-        if (A.mode == 0) {
-#pragma unroll
-          for (int c = 0; c < 32; c += 2) {
-            const float v0 = live ? fmaxf(0.f, __uint_as_float(v[c]) + s_bias[32 * half + c]) : 0.f;
-            const float v1 = live ? fmaxf(0.f, __uint_as_float(v[c + 1]) + s_bias[32 * half + c + 1]) : 0.f;
-            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-            pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+    if constexpr (NO == CH) {
+      // ---------------- epilogue: tensor memory -> bias + ReLU -> BF16 -> canvas.  Warp w drains the
+      // output rows of parity w / 8; it reads TMEM lanes 32 (w % 4) .. + 31 (the lanes a warp may
+      // access), i.e. pixels 32 (w % 4) + lane, channels 32 ((w / 4) % 2) .. + 31.
+      const int lq = warp & 3, par = warp >> 3, half = (warp >> 2) & 1;
+      const int m = lq * 32 + lane;
+      const size_t plane = (size_t)A.Wc * 8;
+      uint32_t g0 = 0;
+      bool stop = false;
+      for (int strip = blockIdx.x; strip < A.n_strips && !stop; strip += stride) {
+        const int4 S = A.strips[strip];
+        const int ya = S.z >> 16, R = S.z & 0xFFFF, Hf = S.w >> 16, Wf = S.w & 0xFFFF;
+        for (int r = (int)((g0 + par) & 1); r < R; r += 2) {  // rows whose ring index has parity par
+          const uint32_t g = g0 + r, k = g % ACC_SLOTS;
+          const bool ok = !s_abort && bar_wait(&t_full[k], (g / ACC_SLOTS) & 1);
+          if (!ok) s_abort = 1;
+          if (!__all_sync(0xffffffffu, ok)) {
+            stop = true;
+            break;
           }
-        } else {
-          uint4 mk[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) mk[q] = *reinterpret_cast<const uint4*>(A.mask + pix + q * plane);
-          const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(mk);
-#pragma unroll
-          for (int c = 0; c < 32; c += 2) {
-            const float v0 = (live && __bfloat162float(mh[c]) > 0.f) ? __uint_as_float(v[c]) : 0.f;
-            const float v1 = (live && __bfloat162float(mh[c + 1]) > 0.f) ? __uint_as_float(v[c + 1]) : 0.f;
-            __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-            pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+          tc_fence_after();
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(k * CH + half * 32), v);
+          tmem_wait_ld();
+          tc_fence_before();
+          bar_arrive(&t_empty[k]);  // this thread's share of the row is in registers
+          const int y = ya + r, x = S.y + m;
+          if (y >= A.Hc || x >= A.Wc) continue;
+          const bool live = x < Wf && y < Hf;  // outside the facet the canvas stays zero
+          const size_t pix = canvas_index(S.x, y, x, 32 * half, A.Hc, A.Wc);  // block q at pix + q * plane
+          uint4 pk[4];
+          uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+          if (A.mode == 0) {
+  #pragma unroll
+            for (int c = 0; c < 32; c += 2) {
+              const float v0 = live ? fmaxf(0.f, __uint_as_float(v[c]) + s_bias[32 * half + c]) : 0.f;
+              const float v1 = live ? fmaxf(0.f, __uint_as_float(v[c + 1]) + s_bias[32 * half + c + 1]) : 0.f;
+              __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+              pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+            }
+          } else {
+            uint4 mk[4];
+  #pragma unroll
+            for (int q = 0; q < 4; ++q) mk[q] = *reinterpret_cast<const uint4*>(A.mask + pix + q * plane);
+            const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(mk);
+  #pragma unroll
+            for (int c = 0; c < 32; c += 2) {
+              const float v0 = (live && __bfloat162float(mh[c]) > 0.f) ? __uint_as_float(v[c]) : 0.f;
+              const float v1 = (live && __bfloat162float(mh[c + 1]) > 0.f) ? __uint_as_float(v[c + 1]) : 0.f;
+              __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+              pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+            }
           }
+  #pragma unroll
+          for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(A.out + pix + q * plane) = pk[q];
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(A.out + pix + q * plane) = pk[q];
+        g0 += R;
       }
-      g0 += R;
+  
+    } else {
+      // ---------------- last layer: warp w drains the output rows of phase w / 4 (ring index mod 4);
+      // it reads column 0 (N(z) before its bias) of TMEM lanes 32 (w % 4) .. + 31, i.e. pixels
+      // 32 (w % 4) + lane, and writes max(0, z - N(z)) on the facet core.  The row's z and x_prev
+      // are loaded before the wait for its accumulator, so their latency overlaps it.
+      const int lq = warp & 3, phase = warp >> 2;
+      const int m = lq * 32 + lane;
+      double s0 = 0.0, s1 = 0.0;
+      uint32_t g0 = 0;
+      bool stop = false;
+      for (int strip = blockIdx.x; strip < A.n_strips && !stop; strip += stride) {
+        const int4 S = A.strips[strip];
+        const int ya = S.z >> 16, R = S.z & 0xFFFF;
+        const int4 fc = A.facets[S.x], core = A.cores[S.x];
+        for (int r = (int)((phase - g0) & 3); r < R; r += 4) {  // rows whose ring index is = phase mod 4
+          const uint32_t g = g0 + r, k = g % ACC_SLOTS;
+          const int iy = fc.x + ya + r, ix = fc.y + S.y + m;
+          const bool in_core = iy >= core.x && iy < core.y && ix >= core.z && ix < core.w;
+          const size_t p = in_core ? (size_t)iy * A.n + ix : 0;
+          const float zv = in_core ? A.z[p] : 0.f;
+          const float xp = (in_core && A.x_prev) ? A.x_prev[p] : 0.f;
+          const bool ok = !s_abort && bar_wait(&t_full[k], (g / ACC_SLOTS) & 1);
+          if (!ok) s_abort = 1;
+          if (!__all_sync(0xffffffffu, ok)) {
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t v = tmem_ld1(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(k * NO));
+          tmem_wait_ld();
+          tc_fence_before();
+          bar_arrive(&t_empty[k]);
+          if (!in_core) continue;
+          const float o = fmaxf(0.f, zv - (__uint_as_float(v) + A.b8));
+          A.img[p] = o;
+          s1 += (double)o * o;
+          // fmaxf(0, NaN) is 0, so positivity would hide a non-finite input: poison the norms
+          if (!isfinite(zv)) s1 = __longlong_as_double(0x7ff8000000000000LL);
+          if (A.x_prev) {
+            const double dd = (double)o - xp;
+            s0 += dd * dd;
+          }
+        }
+        g0 += R;
+      }
+      if (A.acc) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        if (lane == 0) {
+          atomicAdd(&A.acc[0], s0);
+          atomicAdd(&A.acc[1], s1);
+        }
+      }
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == MMA_WARP) {
     tc_fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
+    tmem_dealloc(tmem, Gm::TMEM_COLS);
   }
   if (threadIdx.x == 0 && s_abort) atomicOr(A.status, 2);
 }
@@ -504,114 +578,12 @@ __global__ void __launch_bounds__(128) cnn_first(FirstArgs A) {
   }
 }
 
-// ------------------------------------------------------------ layer 8 (64 -> 1) + residual
-struct LastArgs {
-  const float* z;
-  const float* x_prev;
-  float* out;
-  int n;
-  const int4* facets;
-  const int4* cores;
-  const float* w8;  // [9][64] (BF16-rounded values)
-  float b8;
-  double* acc;
-  int* status;
-};
-
-__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
-__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xFFFF0000u); }
-
-__global__ void __launch_bounds__(LAST_ROWS * TILE_PX) cnn_last(LastArgs A, const __grid_constant__ CUtensorMap tmap) {
-  // grid (core column segments of 128, groups of LAST_ROWS core rows, facet): one TMA load stages
-  // facet rows y0-1 .. y0+LAST_ROWS, pixels x0-1 .. x0+128 of the layer-7 activations (zero outside the canvas), in
-  // the convolution's shared-memory layout; thread (r, m) then computes N(z) for core pixel
-  // (y0 + r, x0 + m) and writes max(0, z - N(z)) with its FP64 stopping-test terms
-  extern __shared__ __align__(1024) unsigned char st[];  // [LAST_ROWS + 2][8][STAGE_PX][8] BF16
-  __shared__ __align__(16) float sw[9 * CH];
-  __shared__ uint64_t full;
-  __shared__ double red[2 * LAST_ROWS * TILE_PX / 32];
-  const int f = blockIdx.z;
-  const int4 core = A.cores[f];  // r0, r1, c0, c1
-  const int4 fc = A.facets[f];   // R0, C0, Hf, Wf
-  const int iy0 = core.x + blockIdx.y * LAST_ROWS, ix0 = core.z + blockIdx.x * TILE_PX;
-  if (iy0 >= core.y || ix0 >= core.w) return;
-  const int y0 = iy0 - fc.x, x0 = ix0 - fc.y;  // facet (= canvas) coordinates
-  if (threadIdx.x == 0) {
-    bar_init(&full, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    bar_expect_tx(&full, LAST_BYTES);
-    tma_load_5d(st, &tmap, 0, x0 - 1, 0, y0 - 1, f, &full);
-  }
-  for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = A.w8[i];
-  __syncthreads();
-  if (!bar_wait(&full, 0)) {
-    if (threadIdx.x == 0) {
-      atomicOr(A.status, 4);
-      bar_wait(&full, 0);  // the copy must land before the block's shared memory is released
-    }
-    return;
-  }
-  const int r = threadIdx.x / TILE_PX, m = threadIdx.x % TILE_PX;
-  const int iy = iy0 + r, ix = ix0 + m;
-  double s0 = 0.0, s1 = 0.0;
-  if (iy < core.y && ix < core.w) {
-    const float4* sw4 = reinterpret_cast<const float4*>(sw);
-    float acc[4] = {A.b8, 0.f, 0.f, 0.f};  // four partial sums: shorter dependency chains
-#pragma unroll 1
-    for (int t = 0; t < 9; ++t) {
-      const unsigned char* src = st + (r + t / 3) * ROW_BYTES + (m + t % 3) * 16;
-#pragma unroll
-      for (int cb = 0; cb < 8; ++cb) {
-        const uint4 v = *reinterpret_cast<const uint4*>(src + cb * KB_BYTES);
-        const float4 wa = sw4[(t * CH + cb * 8) / 4], wb = sw4[(t * CH + cb * 8) / 4 + 1];
-        float& a = acc[cb & 3];
-        a = fmaf(wa.x, bf16_lo(v.x), a);
-        a = fmaf(wa.y, bf16_hi(v.x), a);
-        a = fmaf(wa.z, bf16_lo(v.y), a);
-        a = fmaf(wa.w, bf16_hi(v.y), a);
-        a = fmaf(wb.x, bf16_lo(v.z), a);
-        a = fmaf(wb.y, bf16_hi(v.z), a);
-        a = fmaf(wb.z, bf16_lo(v.w), a);
-        a = fmaf(wb.w, bf16_hi(v.w), a);
-      }
-    }
-    const float nz = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-    const size_t p = (size_t)iy * A.n + ix;
-    const float zv = A.z[p];
-    const float o = fmaxf(0.f, zv - nz);
-    A.out[p] = o;
-    s1 = (double)o * o;
-    if (!isfinite(zv)) s1 = __longlong_as_double(0x7ff8000000000000LL);
-    if (A.x_prev) {
-      const double dd = (double)o - A.x_prev[p];
-      s0 = dd * dd;
-    }
-  }
-  if (A.acc) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    }
-    const int wid = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-      red[2 * wid] = s0;
-      red[2 * wid + 1] = s1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t0 = 0.0, t1 = 0.0;
-      for (int w = 0; w < LAST_ROWS * TILE_PX / 32; ++w) {
-        t0 += red[2 * w];
-        t1 += red[2 * w + 1];
-      }
-      atomicAdd(&A.acc[0], t0);
-      atomicAdd(&A.acc[1], t1);
-    }
-  }
+// ------------------------------------------------------------ host helpers
+// B operand of the last layer: weight W8[0][ci][dy][dx] at [dx][ci / 8][2 - dy][co = 0 of 16][ci % 8]
+size_t last_wpack_index(int dy, int dx, int ci) {
+  return ((((size_t)dx * 8 + (ci >> 3)) * 3 + (2 - dy)) * NO_LAST + 0) * 8 + (ci & 7);
 }
 
-// ------------------------------------------------------------ host helpers
 uint16_t to_bf16_bits(float f) {
   uint32_t u;
   std::memcpy(&u, &f, 4);
@@ -704,6 +676,19 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   }
   const std::vector<int4> strips = conv_strips(S->F, S->Hf.data(), S->Wf.data());
   S->n_strips = (int)strips.size();
+  // the last layer computes the facet cores only: strips of ~STRIP_ROWS core rows x 128 core columns
+  std::vector<int4> lstrips;
+  for (int f = 0; f < S->F; ++f) {
+    const int cr0 = S->fr0[f] - S->R0[f], cr1 = S->fr1[f] - S->R0[f];
+    const int cc0 = S->fc0[f] - S->C0[f], cc1 = S->fc1[f] - S->C0[f];
+    const int k = std::max(1, (cr1 - cr0 + STRIP_ROWS - 1) / STRIP_ROWS);
+    for (int x0 = cc0; x0 < cc1; x0 += TILE_PX)
+      for (int i = 0; i < k; ++i) {
+        const int ya = cr0 + (int)((int64_t)(cr1 - cr0) * i / k), yb = cr0 + (int)((int64_t)(cr1 - cr0) * (i + 1) / k);
+        if (yb > ya) lstrips.push_back(make_int4(f, x0, (ya << 16) | (yb - ya), (S->Hf[f] << 16) | S->Wf[f]));
+      }
+  }
+  S->n_lstrips = (int)lstrips.size();
 
   // weights: layer shapes 64x1, 6 x 64x64, 1x64, each W[co][ci][3][3] then b[co]
   std::vector<float> w1(CH * 9), w8(9 * CH), bias(8 * CH, 0.f);
@@ -725,8 +710,12 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
     for (int co = 0; co < CH; ++co) bias[(l + 1) * CH + co] = W[off + co];
     off += CH;
   }
+  std::vector<uint16_t> wlast(ConvGeom<NO_LAST>::B_BYTES / 2, 0);
   for (int ci = 0; ci < CH; ++ci)
-    for (int t = 0; t < 9; ++t) w8[t * CH + ci] = bf16_round(W[off + ci * 9 + t]);
+    for (int t = 0; t < 9; ++t) {
+      w8[t * CH + ci] = bf16_round(W[off + ci * 9 + t]);
+      wlast[last_wpack_index(t / 3, t % 3, ci)] = to_bf16_bits(W[off + ci * 9 + t]);
+    }
   off += CH * 9;
   bias[7 * CH] = W[off];
   S->b8 = W[off];
@@ -746,6 +735,8 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   if (int rc = al((void**)&S->d_facets, S->F * sizeof(int4))) return rc;
   if (int rc = al((void**)&S->d_cores, S->F * sizeof(int4))) return rc;
   if (int rc = al((void**)&S->d_strips, std::max<size_t>(1, strips.size()) * sizeof(int4))) return rc;
+  if (int rc = al((void**)&S->d_lstrips, std::max<size_t>(1, lstrips.size()) * sizeof(int4))) return rc;
+  if (int rc = al((void**)&S->d_wlast, wlast.size() * 2)) return rc;
   if (int rc = al((void**)&S->d_w1, w1.size() * 4)) return rc;
   if (int rc = al((void**)&S->d_w8, w8.size() * 4)) return rc;
   if (int rc = al((void**)&S->d_b, bias.size() * 4)) return rc;
@@ -755,6 +746,9 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   PNP_CUDA(cudaMemcpy(S->d_cores, cores.data(), S->F * sizeof(int4), cudaMemcpyHostToDevice));
   if (!strips.empty())
     PNP_CUDA(cudaMemcpy(S->d_strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!lstrips.empty())
+    PNP_CUDA(cudaMemcpy(S->d_lstrips, lstrips.data(), lstrips.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  PNP_CUDA(cudaMemcpy(S->d_wlast, wlast.data(), wlast.size() * 2, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_w1, w1.data(), w1.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_w8, w8.data(), w8.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_b, bias.data(), bias.size() * 4, cudaMemcpyHostToDevice));
@@ -762,7 +756,6 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   PNP_CUDA(cudaMemset(S->d_status, 0, 4 * sizeof(int)));
   for (int i = 0; i < 2; ++i) {
     if (int rc = make_canvas_map(&S->map[i], S->d_canvas[i], S->F, S->Hc, S->Wc, 1)) return rc;
-    if (int rc = make_canvas_map(&S->map_last[i], S->d_canvas[i], S->F, S->Hc, S->Wc, LAST_ROWS + 2)) return rc;
   }
   return PNP_OK;
 }
@@ -774,6 +767,8 @@ void cnn_destroy(pnp_den* d) {
   cudaFree(S->d_facets);
   cudaFree(S->d_cores);
   cudaFree(S->d_strips);
+  cudaFree(S->d_lstrips);
+  cudaFree(S->d_wlast);
   cudaFree(S->d_w1);
   cudaFree(S->d_w8);
   cudaFree(S->d_b);
@@ -795,7 +790,9 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
   }
   static bool attr = false;
   if (!attr) {
-    PNP_CUDA(cudaFuncSetAttribute(conv64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM));
+    PNP_CUDA(cudaFuncSetAttribute(conv64_tc<CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, ConvGeom<CH>::SMEM));
+    PNP_CUDA(cudaFuncSetAttribute(conv64_tc<NO_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  ConvGeom<NO_LAST>::SMEM));
     attr = true;
   }
   int cur = 0;
@@ -803,24 +800,16 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
     ConvArgs C{S->d_canvas[1 - cur], S->d_wmid + (size_t)l * 9 * CH * CH, S->d_b + (l + 1) * CH, S->d_strips,
                S->n_strips, S->Hc, S->Wc, S->d_status, 0, nullptr};
     const int grid = std::max(1, std::min(S->n_strips, sms));
-    conv64_tc<<<grid, CONV_THREADS, CONV_SMEM, s>>>(C, S->map[cur]);
+    conv64_tc<CH><<<grid, CONV_THREADS, ConvGeom<CH>::SMEM, s>>>(C, S->map[cur]);
     PNP_CHECK_LAUNCH();
     cur = 1 - cur;
   }
   {
-    LastArgs L{z, x_prev, out, n, S->d_facets, S->d_cores, S->d_w8, S->b8, acc, S->d_status};
-    int maxrows = 1, maxcols = 1;
-    for (int f = 0; f < S->F; ++f) {
-      maxrows = std::max(maxrows, S->fr1[f] - S->fr0[f]);
-      maxcols = std::max(maxcols, S->fc1[f] - S->fc0[f]);
-    }
-    static bool lattr = false;
-    if (!lattr) {
-      PNP_CUDA(cudaFuncSetAttribute(cnn_last, cudaFuncAttributeMaxDynamicSharedMemorySize, LAST_BYTES));
-      lattr = true;
-    }
-    const dim3 lgrid((maxcols + TILE_PX - 1) / TILE_PX, (maxrows + LAST_ROWS - 1) / LAST_ROWS, S->F);
-    cnn_last<<<lgrid, LAST_ROWS * TILE_PX, LAST_BYTES, s>>>(L, S->map_last[cur]);
+    // layer 8 on the tensor cores, fused with D(z) = max(0, z - N(z)) on the facet cores and the norms
+    ConvArgs C{nullptr, S->d_wlast, nullptr, S->d_lstrips, S->n_lstrips, S->Hc, S->Wc, S->d_status, 2, nullptr,
+               z, x_prev, out, n, S->d_facets, S->d_cores, S->b8, acc};
+    const int grid = std::max(1, std::min(S->n_lstrips, sms));
+    conv64_tc<NO_LAST><<<grid, CONV_THREADS, ConvGeom<NO_LAST>::SMEM, s>>>(C, S->map[cur]);
     PNP_CHECK_LAUNCH();
   }
   return PNP_OK;
@@ -831,12 +820,12 @@ int conv64_launch(cudaStream_t s, const void* in_map, __nv_bfloat16* out, const 
                   const __nv_bfloat16* mask, int* status) {
   static bool attr = false;
   if (!attr) {
-    PNP_CUDA(cudaFuncSetAttribute(conv64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM));
+    PNP_CUDA(cudaFuncSetAttribute(conv64_tc<CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, ConvGeom<CH>::SMEM));
     attr = true;
   }
   ConvArgs C{out, w_packed, bias, strips, n_strips, Hc, Wc, status, mode, mask};
   const int grid = std::max(1, std::min(n_strips, sms_of_device()));
-  conv64_tc<<<grid, CONV_THREADS, CONV_SMEM, s>>>(C, *static_cast<const CUtensorMap*>(in_map));
+  conv64_tc<CH><<<grid, CONV_THREADS, ConvGeom<CH>::SMEM, s>>>(C, *static_cast<const CUtensorMap*>(in_map));
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
