@@ -23,25 +23,25 @@
 //               over the facet cores only, fused with D(z) = max(0, z - N(z))
 //               and the FP64 stopping-test norms.
 //
-// conv64_tc layout.  A tile is 2 x 128 output pixels (x0 .. x0+127 of rows y,
-// y+1 of one facet).  Its inputs -- rows y-1..y+2, pixels x0-1 .. x0+128, 64
-// channels -- are staged in shared memory channel-block-major: [row][kb][pixel][8 ch], so
-// for every (kb) the 130 pixels are 16 bytes apart.  That is the canonical
-// no-swizzle K-major operand layout (core matrix = 8 pixels x 8 channels,
-// 128 contiguous bytes), and tap (dy, dx) of the 3x3 stencil is the same
-// matrix with its start address moved by dx pixels (16 B).  Per output row the
-// 9 taps x 4 K-steps (16 channels each) accumulate M=128 x N=64 into tensor
-// memory; the two output rows share the staged rows.
-// Weights of all taps sit in shared memory as [tap][kb][co][8 ci] (K-major B).
-// The staged tile is one TMA transfer: the canvas is described to the TMA unit
-// as a 5-D tensor (8 channels, x, channel block, y, facet), whose box
-// (8, 130, 8, 4, 1) lands in shared memory in exactly that operand layout, with
-// zeros outside the canvas.  Warp roles: warps 0-15 drain tensor memory (bias,
-// ReLU, BF16, store; warp w takes the TMEM lane quarter w % 4, output row w / 8
-// and channel half (w / 4) % 2, so four warps per scheduler hide each other's
-// latency), warp 16 allocates tensor memory and issues the MMAs (one lane),
-// warp 17 issues the TMA loads (one lane).  Two input buffers and two
-// accumulators are pipelined with mbarriers; every wait is bounded.
+// conv64_tc layout.  Work is a strip: one 128-pixel column segment (x0 .. x0+127)
+// of about 32 consecutive output rows of a facet.  The strip's input rows (64
+// channels, pixels x0-1 .. x0+128) stream through a ring of shared-memory row
+// slots, staged channel-block-major: [kb][pixel][8 ch] with the 130 pixels of a
+// block 16 bytes apart (in a 128-byte aligned 2176-byte plane).  That is the
+// canonical no-swizzle K-major operand layout (core matrix = 8 pixels x 8
+// channels, 128 contiguous bytes), and tap (dy, dx) of the 3x3 stencil is the
+// same matrix with its start address moved by dx pixels (16 B).  Input row s
+// serves output rows s-2, s-1, s (taps dy = 2, 1, 0): with the weights of one
+// (dx, kb) stored as [dy=2 | dy=1 | dy=0] x NO output channels, one MMA of
+// M = 128 pixels, K = 16 channels and N = NO x (rows served) per (dx, K step)
+// accumulates all of them into a ring of output-row accumulators in tensor
+// memory.  Each staged row is two TMA transfers per channel block: the canvas is
+// described as 8-byte elements (2 per pixel) so the 128-pixel main box (2 KB)
+// and the 2-pixel halo box (32 B) are runs of whole sectors, with zeros outside
+// the canvas.  Warp roles: warps 0-15 drain tensor memory (bias, ReLU, BF16,
+// store for the hidden layers; the residual and norms for the last one), warp 16
+// allocates tensor memory and issues the MMAs (one lane), warp 17 issues the TMA
+// loads (one lane).  The rings are pipelined with mbarriers; every wait is bounded.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -58,8 +58,10 @@ namespace {
 constexpr int CH = 64;
 constexpr int TILE_PX = 128;                            // output pixels per row segment (the MMA's M)
 constexpr int STAGE_PX = TILE_PX + 2;                   // x0-1 .. x0+128
-constexpr int KB_BYTES = STAGE_PX * 16;                 // one 8-channel block of a staged row (2080)
-constexpr int ROW_BYTES = 8 * KB_BYTES;                 // one staged input row, 8 channel blocks (16640)
+constexpr int KB_BYTES = 136 * 16;                      // one 8-channel block of a staged row: 130 pixels in a
+                                                        // 128-byte aligned plane of 136 (2176 bytes)
+constexpr int ROW_BYTES = 8 * KB_BYTES;                 // one staged input row, 8 channel blocks (17408)
+constexpr int ROW_DATA_BYTES = 8 * STAGE_PX * 16;       // bytes the TMA delivers per staged row (16640)
 constexpr int IN_SLOTS = 8;                             // ring of staged input rows
 constexpr int ACC_SLOTS = 8;                            // ring of output-row accumulators in tensor memory
 // Geometry of the convolution kernel for NO output channels per pixel: 64 for the hidden layers,
@@ -69,7 +71,7 @@ struct ConvGeom {
   static constexpr int TMEM_COLS = ACC_SLOTS * NO;            // 512 (NO = 64) or 128 (NO = 16) columns
   static constexpr int B_GROUP_BYTES = 3 * NO * 16;           // one (dx, kb) group: [dy=2 | dy=1 | dy=0] x NO co x 8 ci
   static constexpr int B_BYTES = 3 * 8 * B_GROUP_BYTES;       // 73728 (NO = 64)
-  static constexpr int SMEM = IN_SLOTS * ROW_BYTES + B_BYTES;  // 206848 (NO = 64)
+  static constexpr int SMEM = IN_SLOTS * ROW_BYTES + B_BYTES;  // 212992 (NO = 64)
 };
 constexpr int NO_LAST = 16;
 constexpr int EPI_WARPS = 16;                           // 2 row parities x 2 channel halves x 4 lane quarters
@@ -96,7 +98,7 @@ struct CnnState {
   float* d_w8 = nullptr;                 // [9][64] (BF16-rounded values)
   int* d_status = nullptr;
   float b8 = 0.f;                        // last layer's bias (host copy)
-  CUtensorMap map[2];                    // TMA descriptors of the two canvases, one-row boxes (conv64_tc)
+  CUtensorMap map[2][2];                 // TMA descriptors of the two canvases (main, halo boxes; conv64_tc)
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -126,13 +128,13 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 __device__ __forceinline__ void bar_expect_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
-// 5-D tiled TMA load into shared memory, completion counted on an mbarrier
-__device__ __forceinline__ void tma_load_5d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+// 4-D tiled TMA load into shared memory, completion counted on an mbarrier
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(
           su32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(su32(bar))
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(su32(bar))
       : "memory");
 }
 
@@ -250,7 +252,8 @@ struct ConvArgs {
 };
 
 template <int NO>
-__global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const __grid_constant__ CUtensorMap tmain,
+                                                           const __grid_constant__ CUtensorMap thalo) {
   using Gm = ConvGeom<NO>;
   extern __shared__ __align__(1024) unsigned char sm[];  // [IN_SLOTS][ROW_BYTES] input ring, then B
   unsigned char* sb = sm + IN_SLOTS * ROW_BYTES;
@@ -302,8 +305,16 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
           const uint32_t slot = L % IN_SLOTS;
           if (L >= IN_SLOTS && !bar_wait(&in_empty[slot], ((L / IN_SLOTS) - 1) & 1)) s_abort = 1;
           if (s_abort) break;
-          bar_expect_tx(&in_full[slot], ROW_BYTES);
-          tma_load_5d(sm + slot * ROW_BYTES, &tmap, 0, S.y - 1, 0, ya - 1 + s, S.x, &in_full[slot]);
+          // per 8-channel block: pixels x0-1 .. x0+126 (2 KB) and x0+127, x0+128 (32 B), each a run of
+          // whole sectors of the block's plane (the canvas seen as 8-byte elements, 2 per pixel)
+          bar_expect_tx(&in_full[slot], ROW_DATA_BYTES);
+          unsigned char* dst = sm + slot * ROW_BYTES;
+          const int y = ya - 1 + s;
+#pragma unroll 1
+          for (int kb = 0; kb < 8; ++kb) {
+            tma_load_4d(dst + kb * KB_BYTES, &tmain, 2 * (S.y - 1), kb, y, S.x, &in_full[slot]);
+            tma_load_4d(dst + kb * KB_BYTES + TILE_PX * 16, &thalo, 2 * (S.y + TILE_PX - 1), kb, y, S.x, &in_full[slot]);
+          }
         }
       }
       // every issued load must land before the CTA ends (bounded)
@@ -597,9 +608,9 @@ float bf16_round(float f) {
   return o;
 }
 
-// A canvas as the 5-D tensor (8 ch, x, kb, y, f); the box (8, 130, 8, rows, 1) lands in shared
-// memory as [row][kb][130 pixels][8 ch], the K-major operand layout of conv64_tc.
-int make_canvas_map(CUtensorMap* map, const __nv_bfloat16* canvas, int F, int Hc, int Wc, int rows) {
+// The two TMA descriptors of a canvas for conv64_tc's row loads (main and halo boxes of one
+// channel block's plane row, the canvas seen as 8-byte elements).
+int make_canvas_maps(CUtensorMap* maps, const __nv_bfloat16* canvas, int F, int Hc, int Wc) {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   if (!enc) {
     void* fn = nullptr;
@@ -608,14 +619,19 @@ int make_canvas_map(CUtensorMap* map, const __nv_bfloat16* canvas, int F, int Hc
     if (q != cudaDriverEntryPointSuccess || !fn) return fail(PNP_ERR_UNSUPPORTED, "cuTensorMapEncodeTiled unavailable");
     enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t dims[5] = {8, (cuuint64_t)Wc, 8, (cuuint64_t)Hc, (cuuint64_t)F};
-  const cuuint64_t strides[4] = {16, (cuuint64_t)Wc * 16, (cuuint64_t)Wc * CH * 2, (cuuint64_t)Hc * Wc * CH * 2};
-  const cuuint32_t box[5] = {8, (cuuint32_t)STAGE_PX, 8, (cuuint32_t)rows, 1};
-  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(canvas), dims, strides,
-                         box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return fail(PNP_ERR_UNSUPPORTED, "tensor map encoding failed (" + std::to_string((int)r) + ")");
+  // the canvas as 8-byte elements: (2 Wc per 8-channel plane row, 8 channel blocks, Hc rows, F facets)
+  const cuuint64_t dims[4] = {2 * (cuuint64_t)Wc, 8, (cuuint64_t)Hc, (cuuint64_t)F};
+  const cuuint64_t strides[3] = {(cuuint64_t)Wc * 16, (cuuint64_t)Wc * CH * 2, (cuuint64_t)Hc * Wc * CH * 2};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const cuuint32_t box_main[4] = {2 * TILE_PX, 1, 1, 1}, box_halo[4] = {2 * (STAGE_PX - TILE_PX), 1, 1, 1};
+  const cuuint32_t* boxes[2] = {box_main, box_halo};
+  for (int i = 0; i < 2; ++i) {
+    const CUresult r = enc(&maps[i], CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, const_cast<__nv_bfloat16*>(canvas), dims,
+                           strides, boxes[i], estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+      return fail(PNP_ERR_UNSUPPORTED, "tensor map encoding failed (" + std::to_string((int)r) + ")");
+  }
   return PNP_OK;
 }
 
@@ -755,7 +771,7 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   PNP_CUDA(cudaMemcpy(S->d_wmid, wmid.data(), wmid.size() * 2, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemset(S->d_status, 0, 4 * sizeof(int)));
   for (int i = 0; i < 2; ++i) {
-    if (int rc = make_canvas_map(&S->map[i], S->d_canvas[i], S->F, S->Hc, S->Wc, 1)) return rc;
+    if (int rc = make_canvas_maps(S->map[i], S->d_canvas[i], S->F, S->Hc, S->Wc)) return rc;
   }
   return PNP_OK;
 }
@@ -800,7 +816,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
     ConvArgs C{S->d_canvas[1 - cur], S->d_wmid + (size_t)l * 9 * CH * CH, S->d_b + (l + 1) * CH, S->d_strips,
                S->n_strips, S->Hc, S->Wc, S->d_status, 0, nullptr};
     const int grid = std::max(1, std::min(S->n_strips, sms));
-    conv64_tc<CH><<<grid, CONV_THREADS, ConvGeom<CH>::SMEM, s>>>(C, S->map[cur]);
+    conv64_tc<CH><<<grid, CONV_THREADS, ConvGeom<CH>::SMEM, s>>>(C, S->map[cur][0], S->map[cur][1]);
     PNP_CHECK_LAUNCH();
     cur = 1 - cur;
   }
@@ -809,7 +825,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
     ConvArgs C{nullptr, S->d_wlast, nullptr, S->d_lstrips, S->n_lstrips, S->Hc, S->Wc, S->d_status, 2, nullptr,
                z, x_prev, out, n, S->d_facets, S->d_cores, S->b8, acc};
     const int grid = std::max(1, std::min(S->n_lstrips, sms));
-    conv64_tc<NO_LAST><<<grid, CONV_THREADS, ConvGeom<NO_LAST>::SMEM, s>>>(C, S->map[cur]);
+    conv64_tc<NO_LAST><<<grid, CONV_THREADS, ConvGeom<NO_LAST>::SMEM, s>>>(C, S->map[cur][0], S->map[cur][1]);
     PNP_CHECK_LAUNCH();
   }
   return PNP_OK;
@@ -825,7 +841,8 @@ int conv64_launch(cudaStream_t s, const void* in_map, __nv_bfloat16* out, const 
   }
   ConvArgs C{out, w_packed, bias, strips, n_strips, Hc, Wc, status, mode, mask};
   const int grid = std::max(1, std::min(n_strips, sms_of_device()));
-  conv64_tc<CH><<<grid, CONV_THREADS, ConvGeom<CH>::SMEM, s>>>(C, *static_cast<const CUtensorMap*>(in_map));
+  const CUtensorMap* maps = static_cast<const CUtensorMap*>(in_map);
+  conv64_tc<CH><<<grid, CONV_THREADS, ConvGeom<CH>::SMEM, s>>>(C, maps[0], maps[1]);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
@@ -852,7 +869,7 @@ int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, cons
 }
 
 int canvas_map_create(void* map_out, const __nv_bfloat16* canvas, int F, int Hc, int Wc) {
-  return make_canvas_map(static_cast<CUtensorMap*>(map_out), canvas, F, Hc, Wc, 1);
+  return make_canvas_maps(static_cast<CUtensorMap*>(map_out), canvas, F, Hc, Wc);
 }
 
 int cnn_status(pnp_den* d, int* flags) {

@@ -285,8 +285,8 @@ struct pnp_cnn_trainer {
   int4 *facets = nullptr, *strips = nullptr;
   double* loss = nullptr;
   int* status = nullptr;
-  alignas(64) unsigned char map_act[8][128];  // TMA descriptors of act[1..7]
-  alignas(64) unsigned char map_dp[2][128];   // and of the two gradient canvases
+  alignas(64) unsigned char map_act[8][256];  // TMA descriptors (main, halo) of act[1..7]
+  alignas(64) unsigned char map_dp[2][256];   // and of the two gradient canvases
 };
 
 using namespace pnp;

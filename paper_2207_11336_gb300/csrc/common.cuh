@@ -197,7 +197,8 @@ int conv64_launch(cudaStream_t s, const void* in_map, __nv_bfloat16* out, const 
 __host__ __device__ __forceinline__ size_t canvas_index(int f, int y, int x, int c, int Hc, int Wc) {
   return ((((size_t)f * Hc + y) * 8 + (c >> 3)) * Wc + x) * 8 + (c & 7);
 }
-// TMA descriptor (a 128-byte CUtensorMap written to map_out) of an activation canvas
+// TMA descriptors of an activation canvas for the convolution's row loads: two 128-byte
+// CUtensorMaps written to map_out (the 128-pixel main box and the 2-pixel halo box)
 int canvas_map_create(void* map_out, const __nv_bfloat16* canvas, int F, int Hc, int Wc);
 int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, const int4* facets, int F, int Hc,
                      int Wc, const float* w1, const float* b1, __nv_bfloat16* out);
