@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-bf16-g", dest="bf16_g", action="store_false",
                     help="skip timing the plain loop with BF16 weights in G")
-    ap.add_argument("--kernel-case", choices=["gridding", "cnn"], default=None,
+    ap.add_argument("--kernel-case", choices=["gridding", "cnn", "fft"], default=None,
                     help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
     ap.add_argument("--cnn-side", type=int, default=4096,
                     help="image side of the cnn kernel case (4x4 facets scaled with it, 32 px halo)")
@@ -513,6 +513,26 @@ def run_kernel_case(args):
     return 0
 
 
+def fft_case(args):
+    """The FFT passes of the 4096^2 / 8192^2 operator with only 1000 visibilities (1.4 GB on the device)."""
+    import torch
+    import paper_2207_11336_gb300 as pnp
+    import synth
+    prob = synth.make_problem("C3", M=1000)
+    plan = pnp.Plan(prob["n"], prob["K"], prob["omega"], prob["w"], prob["dl"], prob["J_per_row"])
+    x = torch.from_numpy(prob["x_true"].astype(np.float32)).cuda()
+    y = torch.from_numpy(prob["noise"].astype(np.complex64)).cuda()
+    out = torch.empty_like(x)
+    for _ in range(max(args.warmup, 1)):
+        plan.grad_step(x, y, 1e-10, out)
+    plan.set_timing(True)
+    for _ in range(max(args.steps, 1)):
+        plan.grad_step(x, y, 1e-10, out)
+    t = plan.read_timing()
+    print(json.dumps({"case": "fft passes 4096^2 / 8192^2", "stage_ms": {k: v[0] / max(v[1], 1) for k, v in t.items()}}))
+    return 0
+
+
 def cnn_case(args):
     """The faceted CNN denoiser on the 4096^2 workload (or --cnn-side): 16 uneven facets, 32 px halo."""
     import torch
@@ -546,6 +566,8 @@ def main():
     args = parse()
     if args.kernel_case == "cnn":
         return cnn_case(args)
+    if args.kernel_case == "fft":
+        return fft_case(args)
     if args.kernel_case:
         return run_kernel_case(args)
     if args.impl == "reference":
