@@ -132,6 +132,8 @@ def test_empty_operator():
     assert np.array_equal(out, np.ones((n, n)))
     xa = to_host(plan.phi_adjoint(y))
     assert np.array_equal(xa, np.zeros((n, n)))
+    choice = plan.autotune(reps=1)       # nothing to time: the defaults stay
+    assert choice["gridding_ms"] == -1.0 and choice["run_max"] == plan.info["run_max"]
 
 
 def test_invalid_arguments_raise():
