@@ -188,8 +188,15 @@ def profiled_traffic(kernel_file: str, workload: str):
 
 
 # ---------------------------------------------------------------- CPU oracle sample
-def oracle_sample(prob, rows, x, y_rows, gamma, t):
-    """Time one oracle PnP-FB iteration on a row sample of G; returns (s/iter estimate, parts)."""
+CNN_TILE = 96   # side of the image tile the FP64 oracle network is timed on
+
+
+def oracle_sample(prob, rows, x, y_rows, gamma, t, cnn=None):
+    """Time one oracle PnP-FB iteration on a row sample of G; returns (s/iter estimate, parts).
+
+    With ``cnn`` = (params, pixels) the denoiser is the FP64 oracle network, timed on a
+    CNN_TILE^2 tile of the iterate and scaled to ``pixels`` (the facets with their halos);
+    otherwise the Haar prox on the whole image."""
     from oracle import fb as ofb
     from oracle import nufft as onu
     n, K, M = prob["n"], prob["K"], prob["M"]
@@ -205,12 +212,19 @@ def oracle_sample(prob, rows, x, y_rows, gamma, t):
         grid = GH @ r
     t2 = time.perf_counter()
     z = x - gamma * onu.zero_pad_adjoint(gs, onu.dft2_adjoint(grid.reshape(K, K))).real
-    ofb.haar_denoise(z, t)
     t3 = time.perf_counter()
+    if cnn is None:
+        ofb.haar_denoise(z, t)
+        den = time.perf_counter() - t3
+    else:
+        from oracle import cnn as ocnn
+        params, pixels = cnn
+        ocnn.denoise(params, z[:CNN_TILE, :CNN_TILE], bf16=False)
+        den = (time.perf_counter() - t3) * pixels / CNN_TILE ** 2
     g_full = (t2 - t1) / reps * (M / rows.size)
-    est = (t1 - t0) + g_full + (t3 - t2)
+    est = (t1 - t0) + g_full + (t3 - t2) + den
     return est, dict(fft_and_pad_s=(t1 - t0) + (t3 - t2), g_pass_scaled_s=g_full,
-                     g_sample_s=(t2 - t1) / reps)
+                     g_sample_s=(t2 - t1) / reps, denoiser_s=den)
 
 
 def cpu_sample_inputs(prob, x_dev_np, y_np):
@@ -220,6 +234,13 @@ def cpu_sample_inputs(prob, x_dev_np, y_np):
 
 
 # ---------------------------------------------------------------- reference arm
+def workload_desc(wl, learned):
+    """The workload's description with the denoiser the timed loop applies."""
+    if not learned:
+        return wl["desc"]
+    return wl["desc"].replace(", Haar prox", "") + ", learned faceted CNN denoiser (4x4 facets, halo 32)"
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -237,22 +258,29 @@ def run_reference(args):
     G = onu.degridding_matrix(gs, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"], rows)
     y_rows = G @ Xt + 1e-3 * prob["noise"][rows]
     gamma, t = 1.0 / M, 1e-6
+    cnn, desc = None, wl["desc"]
+    if os.path.exists(WEIGHTS) and "facet_rows" in prob:   # the same loop as the GPU arm times
+        from paper_2207_11336_gb300.train_denoiser import load as load_weights
+        params, _ = load_weights(WEIGHTS)
+        cnn = (params, _facet_pixels(n, prob["facet_rows"], prob["facet_cols"], prob["halo"]))
+        desc = workload_desc(wl, True)
     times = []
     for i in range(args.warmup + args.steps):
-        est, _ = oracle_sample(prob, rows, x, y_rows, gamma, t)
+        est, _ = oracle_sample(prob, rows, x, y_rows, gamma, t, cnn)
         if i >= args.warmup:
             times.append(est)
     total = sum(times)
     val = len(times) / total
+    sample = (f"per step: one FP64 oracle iteration with the full-size FFT pair, G restricted to {CPU_SAMPLE_ROWS} "
+              f"seeded rows (time scaled by M/{CPU_SAMPLE_ROWS})"
+              + (f" and the FP64 network on a {CNN_TILE}^2 tile (time scaled to the facets' pixels)" if cnn else ""))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": wl["desc"],
-                                            "l2": "inputs larger than L2 (G 31.8 GB)"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"per step: one FP64 oracle iteration with the full-size "
-                                       f"FFT pair and G restricted to {CPU_SAMPLE_ROWS} seeded "
-                                       f"rows, G time scaled by M/{CPU_SAMPLE_ROWS}"},
+            "data": "synthetic", "config": {"workload": desc,
+                                            "l2": "inputs larger than L2 (G %.1f GB)"
+                                                  % ((prob["J_per_row"].astype(np.int64) ** 2).sum() * 10 / 1e9)},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -449,7 +477,7 @@ def run_gpu(args):
 
     out = None
     if rank == 0:
-        desc = wl["desc"] + (", learned faceted CNN (4x4 facets, halo 32, BF16)" if learned else "")
+        desc = workload_desc(wl, learned)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps,
                "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16" if learned else "f32",
@@ -472,13 +500,20 @@ def run_gpu(args):
                "fb": {k: (float(v) if isinstance(v, (int, float, np.floating)) else v) for k, v in hp.items()}}
         if ws == 1 and not args.no_cpu_baseline:
             rows, y_rows = cpu_sample_inputs(prob, None, y.cpu().numpy().astype(np.complex128))
-            xs = xp.cpu().numpy().astype(np.float64)
-            est, parts = oracle_sample(prob, rows, xs, y_rows, gamma, t)
+            if learned:
+                xs = xl.cpu().numpy().astype(np.float64)
+                cnn_arg = (params, _facet_pixels(n, prob["facet_rows"], prob["facet_cols"], prob["halo"]))
+                ys = y_rows / alpha
+            else:
+                xs, cnn_arg, ys = xp.cpu().numpy().astype(np.float64), None, y_rows
+            est, parts = oracle_sample(prob, rows, xs, ys, gamma, t, cnn_arg)
             out["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                   "sample": f"one FP64 oracle iteration of the plain loop: full-size FFT "
-                                             f"pair, G restricted to {CPU_SAMPLE_ROWS} seeded rows (time "
-                                             f"scaled by M/{CPU_SAMPLE_ROWS}); numpy FFT and scipy "
-                                             f"CSR are single-threaded",
+                                   "sample": f"one FP64 oracle iteration of the timed loop: full-size FFT pair, G "
+                                             f"restricted to {CPU_SAMPLE_ROWS} seeded rows (time scaled by "
+                                             f"M/{CPU_SAMPLE_ROWS})"
+                                             + (f", the FP64 network on a {CNN_TILE}^2 tile (time scaled to the "
+                                                f"facets' pixels)" if learned else ", Haar prox")
+                                             + "; numpy FFT and scipy CSR are single-threaded",
                                    "parts_s": parts, "host_cores": os.cpu_count()}
         print(json.dumps(out), flush=True)
     if dist is not None:
