@@ -93,6 +93,7 @@ typedef struct pnp_plan_info {
                            conflicts for the plan's mix of supports J        */
   int run_max;          /* rows at most per run of rows sharing a tap window  */
   int64_t unit_nnz;     /* taps at most per gridding work unit                */
+  int row_batch;        /* rows of a run whose residuals one warp forms together */
 } pnp_plan_info;
 
 /* ------------------------------------------------------------------ plans */
@@ -126,12 +127,21 @@ int pnp_plan_get_info(const pnp_plan* plan, pnp_plan_info* info);
  * the current choice).  Rebuilds the work list only; G is unchanged. */
 int pnp_plan_set_unit_nnz(pnp_plan* plan, int64_t unit_nnz);
 
+/* Set how many rows of a run of rows sharing a tap window one warp of the
+ * gridding pass forms the residuals of together (1, 2 or 4; 0 keeps the
+ * current choice; anything else is PNP_ERR_INVALID_ARG).  Autotuner hook: a
+ * performance setting only, results are unchanged (the warp sums keep their
+ * pairing order).  Synchronises the plan's stream. */
+int pnp_plan_set_row_batch(pnp_plan* plan, int row_batch);
+
 /* Autotuner of the gridding pass's work decomposition (a performance setting
  * with no counterpart in the paper; results change only in the order of the
  * floating-point sums).  Times `reps` fused gridding passes on the plan's
- * stream for every pair of run cap (rows at most per run of rows sharing a tap
- * window: 3, 4, 6, 8) and unit size (2^16, 2^17, 2^18 taps), keeps the fastest
- * and rebuilds the work list for it (G is unchanged).  Synchronous; the output
+ * stream for every triple of run cap (rows at most per run of rows sharing a
+ * tap window: 3, 4, 6, 8), unit size (2^16, 2^17, 2^18 taps) and row batch
+ * (rows of a run whose residuals a warp forms together: 1, 2, 4), keeps the
+ * fastest and rebuilds the work list for it (G is unchanged; the chosen row
+ * batch is reported by pnp_plan_get_info).  Synchronous; the output
  * grid is left cleared.  Outputs (each may be NULL): the chosen run cap and
  * unit size, and the chosen pass's mean time in ms (-1 for an empty operator).
  * reps must lie in [1, 100]. */

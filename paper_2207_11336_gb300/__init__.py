@@ -26,7 +26,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "DIVERGED", -5: "TIMEOUT
 
 EXPORTED = [
     "pnp_plan_create", "pnp_plan_destroy", "pnp_plan_get_info", "pnp_plan_set_unit_nnz",
-    "pnp_plan_export_rows", "phi_forward", "phi_adjoint", "grad_step", "op_norm",
+    "pnp_plan_set_row_batch", "pnp_plan_export_rows", "phi_forward", "phi_adjoint", "grad_step", "op_norm",
     "pnp_den_create_haar", "pnp_den_create_cnn", "pnp_den_destroy", "denoise", "pnp_fb_run",
     "pnp_last_error", "pnp_kernel_launch_count", "pnp_plan_set_timing", "pnp_plan_read_timing",
     "pnp_plan_device_status", "pnp_haar_denoise_noalloc", "pnp_den_device_status",
@@ -56,7 +56,7 @@ class _Info(C.Structure):
                 ("tile", C.c_int), ("nblocks", C.c_int), ("M", C.c_int64), ("nnz", C.c_int64),
                 ("n_units", C.c_int64), ("beta", C.c_double), ("dl", C.c_double),
                 ("device_bytes", C.c_int64), ("region_pitch", C.c_int), ("run_max", C.c_int),
-                ("unit_nnz", C.c_int64)]
+                ("unit_nnz", C.c_int64), ("row_batch", C.c_int)]
 
 
 _lib = None
@@ -76,6 +76,7 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_plan_destroy.restype = None
     L.pnp_plan_get_info.argtypes = [vp, C.POINTER(_Info)]
     L.pnp_plan_set_unit_nnz.argtypes = [vp, i64]
+    L.pnp_plan_set_row_batch.argtypes = [vp, i32]
     L.pnp_plan_autotune.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(dbl)]
     L.pnp_plan_export_rows.argtypes = [vp, vp, i64, vp, vp, vp]
     L.phi_forward.argtypes = [vp, vp, vp]
@@ -102,7 +103,8 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_plan_read_timing.argtypes = [vp, vp, vp]
     L.pnp_last_error.restype = C.c_char_p
     L.pnp_kernel_launch_count.restype = i64
-    for name in ("pnp_plan_create", "pnp_plan_get_info", "pnp_plan_set_unit_nnz", "pnp_plan_export_rows",
+    for name in ("pnp_plan_create", "pnp_plan_get_info", "pnp_plan_set_unit_nnz", "pnp_plan_set_row_batch",
+                 "pnp_plan_export_rows",
                  "phi_forward", "phi_adjoint", "grad_step", "op_norm", "pnp_den_create_haar",
                  "pnp_den_create_cnn", "denoise", "pnp_fb_run", "pnp_plan_set_timing",
                  "pnp_plan_read_timing", "pnp_plan_device_status", "pnp_haar_denoise_noalloc",
@@ -200,11 +202,16 @@ class Plan:
     def set_unit_nnz(self, unit_nnz: int):
         _check(lib().pnp_plan_set_unit_nnz(self._h, int(unit_nnz)))
 
+    def set_row_batch(self, row_batch: int):
+        """Rows of a run whose residuals one warp forms together (1, 2 or 4)."""
+        _check(lib().pnp_plan_set_row_batch(self._h, int(row_batch)))
+
     def autotune(self, reps: int = 2) -> dict:
-        """Time the gridding pass's run cap x unit size candidates and keep the fastest."""
+        """Time the gridding pass's run cap x unit size x row batch candidates and keep the fastest."""
         r, u, ms = C.c_int(), C.c_int64(), C.c_double()
         _check(lib().pnp_plan_autotune(self._h, int(reps), C.byref(r), C.byref(u), C.byref(ms)))
-        return {"run_max": r.value, "unit_nnz": u.value, "gridding_ms": ms.value}
+        return {"run_max": r.value, "unit_nnz": u.value, "row_batch": self.info["row_batch"],
+                "gridding_ms": ms.value}
 
     def device_status(self) -> int:
         """Device status flags (0 when every kernel check passed)."""

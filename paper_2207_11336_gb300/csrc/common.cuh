@@ -98,6 +98,7 @@ struct pnp_plan {
   int slots = 8;       // register slots per lane per row (32*slots >= Jmax^2)
   int pitch = 0;       // row pitch (cells) of the staged gridding regions (0: the region side)
   int run_max = pnp::RUN_MAX;  // rows per run of a shared tap window, at most
+  int row_batch = 2;           // rows of a run whose residuals a warp forms together (1, 2, 4)
   int rpw = 2;         // rows per warp in flight
   int64_t M = 0, nnz = 0, unit_nnz = 1 << 17;
   double beta = 0, dl = 0;

@@ -105,7 +105,10 @@ __device__ __forceinline__ float2 w_at(const unsigned char* base, int i) {
     return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(base)[i]);
   }
 }
-// Shared-memory stage: [weights | cells | visibilities | run list], each 128-B aligned.
+// Shared-memory stage: [weights | cells | visibilities | run list | chunk descriptor], each
+// 128-B aligned.  The producer writes the descriptor with plain stores before its arrive on
+// the stage's full barrier (release), so consumers read it from shared memory after their
+// wait (acquire) instead of each fetching it from global memory.
 // Every row of a chunk has the same support J (rows are sorted by J within a tile), so
 // row q of a chunk starts at tap q J^2 and the row offsets need not be read.
 template <typename WT>
@@ -119,21 +122,9 @@ struct StageLayout {
   static constexpr int C_OFF = al(W_BYTES);
   static constexpr int Y_OFF = C_OFF + al(C_BYTES);
   static constexpr int R_OFF = Y_OFF + al(Y_BYTES);
-  static constexpr int SIZE = R_OFF + al(R_BYTES);
+  static constexpr int H_OFF = R_OFF + al(R_BYTES);
+  static constexpr int SIZE = H_OFF + al((int)sizeof(Chunk));
 };
-
-// Position in a CTA's stream of chunks: unit u (global index) and chunk c within it.
-struct StreamPos {
-  long long u;
-  int c;
-};
-
-__device__ __forceinline__ bool advance(StreamPos& s, const GArgs& A) {
-  if (++s.c < A.units[s.u].nchunks) return true;
-  s.c = 0;
-  s.u += gridDim.x;
-  return s.u < A.n_units;
-}
 
 template <int MODE, typename WT>
 __device__ __forceinline__ void issue_chunk(const GArgs& A, const Chunk& ch, unsigned char* stage,
@@ -149,6 +140,7 @@ __device__ __forceinline__ void issue_chunk(const GArgs& A, const Chunk& ch, uns
   const long long rs0 = ch.run_begin & ~15LL, re = (ch.run_begin + ch.nruns + 1 + 15) & ~15LL;
   const uint32_t rbytes = (uint32_t)(re - rs0);
   const bool need_y = MODE != G_DEGRID && A.y_in != nullptr;
+  *reinterpret_cast<Chunk*>(stage + L::H_OFF) = ch;  // published by the arrive below
   mbar_expect_tx(bar, wbytes + cbytes + rbytes + (need_y ? ybytes : 0));
   bulk_g2s(stage + L::W_OFF, reinterpret_cast<const unsigned char*>(A.w) + tb0 * WB, wbytes, bar);
   bulk_g2s(stage + L::C_OFF, A.cells + tb0, cbytes, bar);
@@ -171,14 +163,41 @@ struct RowCtx {
   int S, P, r0, c0, logK, Km, lane;
 };
 
+// Warp sums of V per-lane values (V a power of two, 2 <= V <= 32).  The first log2 V
+// butterfly stages exchange half of the values still held with the partner lane, so each
+// stage costs V / 2^(stage+1) shuffles instead of V, and the last stages sum one value; the
+// adds follow the same pairing tree as V separate xor butterflies.  On return v[0] of lane l
+// holds the sum of value l >> (5 - log2 V).
+template <int V>
+__device__ __forceinline__ void warp_sum_many(float (&v)[V], int lane) {
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int o = 16 >> st, n = V >> st;
+    if (n > 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int i = 0; i < n / 2; ++i) {
+        const float send = up ? v[i] : v[i + n / 2];
+        const float keep = up ? v[i + n / 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    }
+  }
+}
+
+constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v / 2); }
+
 // Runs k0, k0 + NCW, ... of one J-uniform chunk, SL register slots of 32 taps per lane.
 // The rows of a run share their tap window (same first cell, same support): the run's
 // cells and staged grid values are loaded once, each row contributes its own residual
 // r_m = sum_k G_mk X_k - y_m, and the scatter terms conj(G_mk) r_m are summed in registers
 // over the run before one pair of shared atomics per tap.  Lanes without a tap point at
 // their own dummy cell S P + lane with weight 0, so the slot loops are branch-free, and
-// every cell is clamped into the region.
-template <int MODE, typename WT, int SL>
+// every cell is clamped into the region.  The residuals of RB rows of a run are formed
+// together (independent FMA chains, one multi-value warp sum) before their scatter terms.
+template <int MODE, typename WT, int SL, int RB>
 __device__ __forceinline__ void process_chunk(const GArgs& A, const Chunk& ch, const unsigned char* stage,
                                               int k0, const RowCtx& C) {
   using L = StageLayout<WT>;
@@ -202,39 +221,58 @@ __device__ __forceinline__ void process_chunk(const GArgs& A, const Chunk& ch, c
       if (MODE != G_GRID) xv[s] = C.sx[idx[s]];
       ar[s] = make_float2(0.f, 0.f);
     }
-    for (int q = qb; q < qe; ++q) {
-      const int beg = toff + q * nn;
-      float2 r = make_float2(0.f, 0.f);
-      if (MODE != G_GRID) {
-        float2 acc = make_float2(0.f, 0.f);
+    if (MODE == G_GRID) {
+      for (int q = qb; q < qe; ++q) {
+        const int beg = toff + q * nn;
+        const float2 r = syv[roff + q];
 #pragma unroll
         for (int s = 0; s < SL; ++s) {
           const int t = lane + 32 * s;
           const float2 w = t < nn ? w_at<WT>(sw, beg + t) : make_float2(0.f, 0.f);
-          acc.x = fmaf(w.x, xv[s].x, fmaf(-w.y, xv[s].y, acc.x));
-          acc.y = fmaf(w.x, xv[s].y, fmaf(w.y, xv[s].x, acc.y));
+          ar[s].x = fmaf(w.x, r.x, fmaf(w.y, r.y, ar[s].x));   // += conj(w) r
+          ar[s].y = fmaf(w.x, r.y, fmaf(-w.y, r.x, ar[s].y));
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-          acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-        }
-        if (MODE == G_DEGRID) {
-          if (lane == 0) A.y_out[A.perm[ch.row_begin + q]] = acc;
-          continue;
-        }
-        r = acc;
-        if (A.y_in) r = csub(r, syv[roff + q]);
-      } else {
-        r = syv[roff + q];
       }
+    } else {
+      constexpr int SH = 5 - ilog2c(2 * RB);  // value i of the warp sum sits in lane i << SH
+      for (int q = qb; q < qe; q += RB) {
+        float v[2 * RB];
 #pragma unroll
-      for (int s = 0; s < SL; ++s) {
-        const int t = lane + 32 * s;
-        const float2 w = t < nn ? w_at<WT>(sw, beg + t) : make_float2(0.f, 0.f);
-        const float2 c = cmulc(w, r);
-        ar[s].x += c.x;
-        ar[s].y += c.y;
+        for (int b = 0; b < RB; ++b) {
+          float2 acc = make_float2(0.f, 0.f);
+          if (b == 0 || q + b < qe) {  // warp-uniform
+            const int beg = toff + (q + b) * nn;
+#pragma unroll
+            for (int s = 0; s < SL; ++s) {
+              const int t = lane + 32 * s;
+              const float2 w = t < nn ? w_at<WT>(sw, beg + t) : make_float2(0.f, 0.f);
+              acc.x = fmaf(w.x, xv[s].x, fmaf(-w.y, xv[s].y, acc.x));
+              acc.y = fmaf(w.x, xv[s].y, fmaf(w.y, xv[s].x, acc.y));
+            }
+          }
+          v[2 * b] = acc.x;
+          v[2 * b + 1] = acc.y;
+        }
+        warp_sum_many<2 * RB>(v, lane);
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+          if (b > 0 && q + b >= qe) break;  // warp-uniform
+          float2 r = make_float2(__shfl_sync(0xffffffffu, v[0], (2 * b) << SH),
+                                 __shfl_sync(0xffffffffu, v[0], (2 * b + 1) << SH));
+          if (MODE == G_DEGRID) {
+            if (lane == 0) A.y_out[A.perm[ch.row_begin + q + b]] = r;
+            continue;
+          }
+          if (A.y_in) r = csub(r, syv[roff + q + b]);
+          const int beg = toff + (q + b) * nn;
+#pragma unroll
+          for (int s = 0; s < SL; ++s) {
+            const int t = lane + 32 * s;
+            const float2 w = t < nn ? w_at<WT>(sw, beg + t) : make_float2(0.f, 0.f);
+            ar[s].x = fmaf(w.x, r.x, fmaf(w.y, r.y, ar[s].x));   // += conj(w) r
+            ar[s].y = fmaf(w.x, r.y, fmaf(-w.y, r.x, ar[s].y));
+          }
+        }
       }
     }
     if (MODE != G_DEGRID) {
@@ -254,8 +292,8 @@ __device__ __forceinline__ void process_chunk(const GArgs& A, const Chunk& ch, c
 // warp produces them.  full[s] completes when stage s has landed (TMA
 // transaction count); empty[s] completes when every consumer warp has released
 // stage s.  Consumer warps only meet at unit boundaries (tile restage/flush).
-template <int MODE, typename WT>
-__global__ void __launch_bounds__(GPASS_THREADS) gpass(GArgs A) {
+template <int MODE, typename WT, int RB>
+__global__ void __launch_bounds__(GPASS_THREADS, 1) gpass(GArgs A) {
   using L = StageLayout<WT>;
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ uint64_t full[NSTAGE], empty[NSTAGE];
@@ -287,7 +325,12 @@ __global__ void __launch_bounds__(GPASS_THREADS) gpass(GArgs A) {
   if (warp == NCW) {
     // ---------------- producer warp (lane 0 issues every copy)
     if (lane != 0) return;
-    StreamPos pos{(long long)blockIdx.x, 0};
+    // The descriptors of the next chunk are loaded before the current one is issued, so their
+    // latency overlaps the wait for a free stage instead of adding to every issue.
+    long long u = blockIdx.x;
+    int c = 0;
+    Unit U = A.units[u];
+    Chunk cur = A.chunks[U.chunk_begin];
     int st = 0;
     uint32_t ph = 0;       // parity of the current use of stage st
     long long j = 0;
@@ -298,15 +341,26 @@ __global__ void __launch_bounds__(GPASS_THREADS) gpass(GArgs A) {
         break;
       }
       if (s_abort) break;
+      Chunk nxt = cur;
+      if (++c < U.nchunks) {
+        nxt = A.chunks[U.chunk_begin + c];
+      } else {
+        c = 0;
+        u += gridDim.x;
+        more = u < A.n_units;
+        if (more) {
+          U = A.units[u];
+          nxt = A.chunks[U.chunk_begin];
+        }
+      }
       fence_proxy_async();
-      const Unit U = A.units[pos.u];
-      issue_chunk<MODE, WT>(A, A.chunks[U.chunk_begin + pos.c], stages + st * L::SIZE, &full[st]);
+      issue_chunk<MODE, WT>(A, cur, stages + st * L::SIZE, &full[st]);
       ++j;
       if (++st == NSTAGE) {
         st = 0;
         ph ^= 1u;
       }
-      more = advance(pos, A);
+      cur = nxt;
     }
     // every issued copy must land before the CTA's shared memory can be released
     for (int d = 0; d < NSTAGE && d < j; ++d) {
@@ -348,23 +402,23 @@ __global__ void __launch_bounds__(GPASS_THREADS) gpass(GArgs A) {
         ok = mbar_wait(&full[st], ph);
         if (!ok) s_abort = 1;
       }
-      const Chunk ch = A.chunks[U.chunk_begin + ci];
+      const unsigned char* stage = stages + st * L::SIZE;
+      const Chunk ch = ok ? *reinterpret_cast<const Chunk*>(stage + L::H_OFF) : A.chunks[U.chunk_begin + ci];
       // a warp works on the stage only when all of its lanes saw the copy land
       if (__all_sync(0xffffffffu, ok)) {
-        const unsigned char* stage = stages + st * L::SIZE;
         // runs are dealt to warps round robin over the whole stream, so no warp idles per chunk
         const int q0 = warp >= rb ? warp - rb : warp - rb + NCW;
         if (ch.nn * ch.nrows != ch.ntaps || (ch.tap_begin & 7LL) + ch.ntaps > CHUNK_TAPS + 16 ||
             ch.nruns < 1 || ch.nruns > ch.nrows || (ch.run_begin & 15LL) + ch.nruns + 1 > CHUNK_ROWS + 32) {
           if (lane == 0) atomicOr(A.status, 4);  // inconsistent work list: skip the chunk
         } else if (ch.nn <= 64) {
-          process_chunk<MODE, WT, 2>(A, ch, stage, q0, C);
+          process_chunk<MODE, WT, 2, RB>(A, ch, stage, q0, C);
         } else if (ch.nn <= 96) {
-          process_chunk<MODE, WT, 3>(A, ch, stage, q0, C);
+          process_chunk<MODE, WT, 3, RB>(A, ch, stage, q0, C);
         } else if (ch.nn <= 160) {
-          process_chunk<MODE, WT, 5>(A, ch, stage, q0, C);
+          process_chunk<MODE, WT, 5, RB>(A, ch, stage, q0, C);
         } else {
-          process_chunk<MODE, WT, 8>(A, ch, stage, q0, C);
+          process_chunk<MODE, WT, 8, RB>(A, ch, stage, q0, C);
         }
       }
       rb = (rb + (ch.nruns > 0 ? ch.nruns : 0)) % NCW;
@@ -397,30 +451,44 @@ __global__ void permute_kernel(const float2* __restrict__ y, const int32_t* __re
     out[i] = y[perm[i]];
 }
 
-template <int MODE, typename WT>
+template <int MODE, typename WT, int RB>
 int launch_gpass(pnp_plan* p, const GArgs& A) {
   const int region_bytes = (((A.S * A.P + 32) * 8 + 127) & ~127);
   const int smem = (MODE == G_FUSED ? 2 : 1) * region_bytes + NSTAGE * StageLayout<WT>::SIZE;
   static int attr = 0;
   static int per_sm = 0;
   if (smem > attr) {
-    PNP_CUDA(cudaFuncSetAttribute(gpass<MODE, WT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PNP_CUDA(cudaFuncSetAttribute(gpass<MODE, WT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr = smem;
-    PNP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gpass<MODE, WT>, GPASS_THREADS, smem));
+    PNP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gpass<MODE, WT, RB>, GPASS_THREADS, smem));
   }
   if (per_sm < 1) return fail(PNP_ERR_UNSUPPORTED, "gridding tile does not fit in shared memory");
   long long grid = (long long)per_sm * p->num_sms;
   if (grid > A.n_units) grid = A.n_units;
   if (grid < 1) return PNP_OK;
-  gpass<MODE, WT><<<(unsigned)grid, GPASS_THREADS, smem, p->stream>>>(A);
+  gpass<MODE, WT, RB><<<(unsigned)grid, GPASS_THREADS, smem, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
 
-template <int MODE>
+template <int MODE, int RB>
 int dispatch_wt(pnp_plan* p, const GArgs& A) {
-  return p->wdtype == PNP_W_BF16C ? launch_gpass<MODE, __nv_bfloat162>(p, A)
-                                  : launch_gpass<MODE, float2>(p, A);
+  return p->wdtype == PNP_W_BF16C ? launch_gpass<MODE, __nv_bfloat162, RB>(p, A)
+                                  : launch_gpass<MODE, float2, RB>(p, A);
+}
+
+// rows whose residuals one warp forms together (G_GRID takes its residuals as input)
+template <int MODE>
+int dispatch_rb(pnp_plan* p, const GArgs& A) {
+  if constexpr (MODE == G_GRID) {
+    return dispatch_wt<MODE, 1>(p, A);
+  } else {
+    switch (p->row_batch) {
+      case 1: return dispatch_wt<MODE, 1>(p, A);
+      case 4: return dispatch_wt<MODE, 4>(p, A);
+      default: return dispatch_wt<MODE, 2>(p, A);
+    }
+  }
 }
 
 // Modelled shared-memory wavefronts of one row of J x J taps on regions of row pitch P: lane t of
@@ -514,9 +582,9 @@ int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out) {
   if (int rc = stage_begin(p, 1, &ev)) return rc;
   int rc;
   switch (mode) {
-    case G_DEGRID: rc = dispatch_wt<G_DEGRID>(p, A); break;
-    case G_GRID: rc = dispatch_wt<G_GRID>(p, A); break;
-    default: rc = dispatch_wt<G_FUSED>(p, A); break;
+    case G_DEGRID: rc = dispatch_rb<G_DEGRID>(p, A); break;
+    case G_GRID: rc = dispatch_rb<G_GRID>(p, A); break;
+    default: rc = dispatch_rb<G_FUSED>(p, A); break;
   }
   if (rc) return rc;
   return stage_end(p, 1, ev);

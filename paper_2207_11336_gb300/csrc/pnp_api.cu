@@ -240,6 +240,7 @@ int pnp_plan_get_info(const pnp_plan* p, pnp_plan_info* info) {
   info->device_bytes = p->device_bytes;
   info->region_pitch = p->pitch > 0 ? p->pitch : p->tile + p->Jmax - 1;
   info->run_max = p->run_max;
+  info->row_batch = p->row_batch;
   info->unit_nnz = p->unit_nnz;
   return PNP_OK;
 }
@@ -252,17 +253,27 @@ int pnp_plan_set_unit_nnz(pnp_plan* p, int64_t unit_nnz) {
   return build_units(p);
 }
 
+int pnp_plan_set_row_batch(pnp_plan* p, int row_batch) {
+  if (!p || (row_batch != 0 && row_batch != 1 && row_batch != 2 && row_batch != 4))
+    return fail(PNP_ERR_INVALID_ARG, "row_batch must be 0, 1, 2 or 4");
+  if (row_batch == 0) return PNP_OK;
+  PNP_CUDA(cudaStreamSynchronize(p->stream));
+  p->row_batch = row_batch;
+  return PNP_OK;
+}
+
 int pnp_plan_autotune(pnp_plan* p, int reps, int* run_max_out, int64_t* unit_nnz_out, double* ms_out) {
   if (!p || reps < 1 || reps > 100) return fail(PNP_ERR_INVALID_ARG, "bad argument");
   PNP_CUDA(cudaStreamSynchronize(p->stream));
-  const int old_run = p->run_max;
+  const int old_run = p->run_max, old_rb = p->row_batch;
   const int64_t old_unit = p->unit_nnz;
-  int best_run = old_run;
+  int best_run = old_run, best_rb = old_rb;
   int64_t best_unit = old_unit;
   float best_ms = -1.f;
   if (p->M > 0 && p->n_units > 0) {
     const int runs[] = {3, 4, 6, 8};
     const int64_t units[] = {int64_t(1) << 16, int64_t(1) << 17, int64_t(1) << 18};
+    const int batches[] = {1, 2, 4};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     PNP_CUDA(cudaEventCreate(&e0));
     PNP_CUDA(cudaEventCreate(&e1));
@@ -274,27 +285,32 @@ int pnp_plan_autotune(pnp_plan* p, int reps, int* run_max_out, int64_t* unit_nnz
         p->run_max = r;
         p->unit_nnz = u;
         if ((rc = build_units(p))) break;
-        if ((rc = gridding_pass(p, G_FUSED, nullptr, nullptr))) break;  // warm-up
-        if (cudaEventRecord(e0, p->stream) != cudaSuccess) {
-          cudaGetLastError();
-          rc = fail(PNP_ERR_CUDA, "autotune: event record failed");
-          break;
+        for (int rb : batches) {
+          p->row_batch = rb;
+          if ((rc = gridding_pass(p, G_FUSED, nullptr, nullptr))) break;  // warm-up
+          if (cudaEventRecord(e0, p->stream) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(PNP_ERR_CUDA, "autotune: event record failed");
+            break;
+          }
+          for (int i = 0; i < reps && !rc; ++i) rc = gridding_pass(p, G_FUSED, nullptr, nullptr);
+          if (rc) break;
+          float ms = 0.f;
+          if (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(PNP_ERR_CUDA, "autotune: timing failed");
+            break;
+          }
+          ms /= reps;
+          if (best_ms < 0.f || ms < best_ms) {
+            best_ms = ms;
+            best_run = r;
+            best_unit = u;
+            best_rb = rb;
+          }
         }
-        for (int i = 0; i < reps && !rc; ++i) rc = gridding_pass(p, G_FUSED, nullptr, nullptr);
         if (rc) break;
-        float ms = 0.f;
-        if (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-          cudaGetLastError();
-          rc = fail(PNP_ERR_CUDA, "autotune: timing failed");
-          break;
-        }
-        ms /= reps;
-        if (best_ms < 0.f || ms < best_ms) {
-          best_ms = ms;
-          best_run = r;
-          best_unit = u;
-        }
       }
       if (rc) break;
     }
@@ -307,6 +323,7 @@ int pnp_plan_autotune(pnp_plan* p, int reps, int* run_max_out, int64_t* unit_nnz
       rc = fail(PNP_ERR_CUDA, "autotune: clearing the grid failed");
     }
     p->run_max = rc ? old_run : best_run;
+    p->row_batch = rc ? old_rb : best_rb;
     p->unit_nnz = rc ? old_unit : best_unit;
     if (int rc2 = build_units(p)) return rc2;
     if (rc) return rc;

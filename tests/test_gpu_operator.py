@@ -183,6 +183,35 @@ def test_unit_size_does_not_change_result():
     assert rel_l2(y1, y0) <= 1e-6
 
 
+@pytest.mark.parametrize("row_batch", [1, 2, 4])
+def test_row_batch_matches_oracle(row_batch):
+    """Residuals formed 1, 2 or 4 rows at a time: same pairing of the warp sums, so the
+    de-gridded rows agree bit for bit and the fused gradient matches the oracle."""
+    n, K, M = 128, 256, 60000
+    pr = _problem(n, K, M, with_w=True, seed=11)
+    # rows clustered on 2000 cells with the same fractional offset, so that long runs of
+    # rows sharing a tap window (cut at the run cap) and partial last batches both occur
+    rng = pr["rng"]
+    cells = rng.integers(-K // 3, K // 3, (2000, 2))
+    kap = cells[rng.integers(0, 2000, M)] + rng.uniform(0.6, 0.7, (M, 2))
+    pr["omega"] = 2 * np.pi * kap / K
+    gpu, ora = _plans(pr, n, K)
+    yh = ora.forward(pr["x"] * 0.7) + 0.05 * synth.complex_normal(M, pr["rng"])
+    x, y = to_dev_f32(pr["x"]), to_dev_c64(yh)
+    gpu.set_row_batch(1)
+    y1 = to_host(gpu.phi_forward(x))
+    gpu.set_row_batch(row_batch)
+    assert gpu.info["row_batch"] == row_batch
+    yb = to_host(gpu.phi_forward(x))
+    assert np.array_equal(yb, y1)
+    assert rel_l2(yb, ora.forward(pr["x"])) <= TOL
+    gamma = 1.0 / M
+    g = to_host(gpu.grad_step(x, y, gamma))
+    assert gpu.device_status() == 0
+    ref = ofb.gradient_step(ora, pr["x"], yh, gamma)
+    assert rel_l2((pr["x"] - g) / gamma, (pr["x"] - ref) / gamma) <= TOL
+
+
 def test_autotune_keeps_results_and_reports_its_choice():
     """The tuner only changes the work list: gradient steps agree up to summation order."""
     n, K, M = 64, 128, 20000
@@ -197,6 +226,7 @@ def test_autotune_keeps_results_and_reports_its_choice():
     assert choice["gridding_ms"] > 0
     info = gpu.info
     assert (info["run_max"], info["unit_nnz"]) == (choice["run_max"], choice["unit_nnz"])
+    assert choice["row_batch"] in (1, 2, 4) and info["row_batch"] == choice["row_batch"]
     g1 = to_host(gpu.grad_step(x, y, gamma))
     assert gpu.device_status() == 0
     assert rel_l2((pr["x"] - g1) / gamma, (pr["x"] - g0) / gamma) <= 1e-6
