@@ -27,12 +27,16 @@ CONFIGS = {
 
 
 def make_problem(name: str, M: int | None = None, n: int | None = None, K: int | None = None,
-                 freq_hz: float = 1.399e9, root_seed: int = 0, with_sky: bool = True) -> dict:
+                 freq_hz: float = 1.399e9, root_seed: int = 0, with_sky: bool = True,
+                 n_stacks: int = 1) -> dict:
     """Seeded inputs for one workload (sizes may be overridden for small cases).
 
     Returns a dict with n, K, M, omega (M, 2) rad/px, w (M,) wavelengths, dl,
     J_per_row (int8 or None for a single J=7), x_true (n, n) float64 sky,
-    noise (M,) standard complex normal draws, block (M,) int32, facet widths.
+    noise (M,) standard complex normal draws, block (M,) int32, facet widths,
+    and the w-stack layout: stack (M,) int32 ids and w_centres (n_stacks,).  With
+    n_stacks > 1 (w-stacking hybrid, App. E) the supports follow the residual
+    |w - centre| against the unstacked |w| quartile edges.
     """
     cfg = dict(CONFIGS[name])
     if M is not None:
@@ -48,6 +52,13 @@ def make_problem(name: str, M: int | None = None, n: int | None = None, K: int |
                isnr_db=cfg["isnr_db"], iters=cfg["iters"], halo=cfg["halo"])
     out["J_per_row"] = (mk.j_per_row_by_w_quartile(w, cfg["supports"])
                         if cfg["supports"] is not None else None)
+    if n_stacks > 1:
+        if cfg["supports"] is None or dl == 0.0:
+            raise ValueError(f"{name} has no w-terms to stack")
+        out["stack"], out["w_centres"] = mk.w_stacks(w, n_stacks)
+        out["J_per_row"] = mk.j_per_row_stacked(w, out["stack"], out["w_centres"], w, cfg["supports"])
+    else:
+        out["stack"], out["w_centres"] = np.zeros(m, dtype=np.int32), np.zeros(1)
     if with_sky:
         scale = nn / 256.0
         out["x_true"] = mk.sky_model(nn, mk.rng_for("sky", root_seed),

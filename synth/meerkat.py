@@ -96,6 +96,37 @@ def j_per_row_by_w_quartile(w: np.ndarray, supports=(7, 9, 12, 16)) -> np.ndarra
     return np.asarray(supports, dtype=np.int8)[q]
 
 
+def w_stacks(w: np.ndarray, n_stacks: int) -> tuple[np.ndarray, np.ndarray]:
+    """w-stack id (int32) per row and the stack centres (float64, wavelengths).
+
+    The rows are binned into n_stacks equal-count bins of w (quantile edges);
+    each centre is the midpoint of its bin's w range, which minimises the
+    largest residual |w - centre| left to the row kernels.
+    """
+    w = np.asarray(w, dtype=np.float64)
+    if n_stacks < 1:
+        raise ValueError("n_stacks must be >= 1")
+    edges = np.quantile(w, np.linspace(0.0, 1.0, n_stacks + 1)[1:-1]) if w.size else np.zeros(n_stacks - 1)
+    stack = np.searchsorted(edges, w, side="right").astype(np.int32)
+    centres = np.zeros(n_stacks)
+    for s in range(n_stacks):
+        ws = w[stack == s]
+        if ws.size:
+            centres[s] = 0.5 * (ws.min() + ws.max())
+    return stack, centres
+
+
+def j_per_row_stacked(w: np.ndarray, stack: np.ndarray, centres: np.ndarray, w_ref: np.ndarray,
+                      supports=(7, 9, 12, 16)) -> np.ndarray:
+    """Per-row support J (int8) of a w-stacked operator: the |w| quartile edges of the
+    unstacked rows w_ref, applied to each row's residual |w - centre of its stack|, so a
+    row gets the support an unstacked row with that |w| would get."""
+    edges = np.quantile(np.abs(np.asarray(w_ref, dtype=np.float64)), [0.25, 0.5, 0.75])
+    resid = np.abs(np.asarray(w, dtype=np.float64) - np.asarray(centres)[stack])
+    q = np.searchsorted(edges, resid, side="right")
+    return np.asarray(supports, dtype=np.int8)[q]
+
+
 def _add_blobs(img, rng, n_blobs, sigma_lo, sigma_hi, peak_lo, peak_hi):
     n0, n1 = img.shape
     ya, xa = np.mgrid[0:n0, 0:n1]
