@@ -94,6 +94,7 @@ typedef struct pnp_plan_info {
   int run_max;          /* rows at most per run of rows sharing a tap window  */
   int64_t unit_nnz;     /* taps at most per gridding work unit                */
   int row_batch;        /* rows of a run whose residuals one warp forms together */
+  int nstacks;          /* w-stacks P of the operator (1: w wholly in G)      */
 } pnp_plan_info;
 
 /* ------------------------------------------------------------------ plans */
@@ -118,6 +119,24 @@ typedef struct pnp_plan_info {
 int pnp_plan_create(pnp_plan** plan, int n, int K, int64_t M, const double* uvw_host,
                     double dl, const int8_t* J_per_row_host, int J, int weight_dtype,
                     const int32_t* block_host, int nblocks, void* stream);
+
+/* The w-stacking hybrid of App. E (Eq. phip): Phi = [Phi_1; ...; Phi_P] with
+ * Phi_p = G_p F Z_p.  Arguments as pnp_plan_create, plus
+ *  stack_host     host, M int32 stack ids in [0, nstacks) (NULL only when M == 0
+ *                 or nstacks == 1)
+ *  nstacks        P in [1, 64]
+ *  w_centres_host host, P float64 stack centres w_p [wavelengths] (NULL only when
+ *                 nstacks == 1, meaning w_1 = 0)
+ * Z_p multiplies pixel (a, b) by exp(i pi w_p dl^2 ((a - n/2)^2 + (b - n/2)^2))
+ * before the grid correction; row m of stack p is w-folded with w_m - w_p only,
+ * so J_per_row may be chosen from that residual.  Every operator call runs the
+ * stacks one after the other through the plan's single pair of grids and sums
+ * the adjoints (Eq. phidagphi).  dl must be > 0 when nstacks > 1.  Errors as
+ * pnp_plan_create; stack ids out of range are PNP_ERR_INVALID_ARG. */
+int pnp_plan_create_stacked(pnp_plan** plan, int n, int K, int64_t M, const double* uvw_host,
+                            double dl, const int8_t* J_per_row_host, int J, int weight_dtype,
+                            const int32_t* block_host, int nblocks, const int32_t* stack_host,
+                            int nstacks, const double* w_centres_host, void* stream);
 
 void pnp_plan_destroy(pnp_plan* plan);
 

@@ -25,7 +25,7 @@ PNP_DEN_HAAR, PNP_DEN_CNN = 0, 1
 ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "DIVERGED", -5: "TIMEOUT", -6: "UNSUPPORTED"}
 
 EXPORTED = [
-    "pnp_plan_create", "pnp_plan_destroy", "pnp_plan_get_info", "pnp_plan_set_unit_nnz",
+    "pnp_plan_create", "pnp_plan_create_stacked", "pnp_plan_destroy", "pnp_plan_get_info", "pnp_plan_set_unit_nnz",
     "pnp_plan_set_row_batch", "pnp_plan_export_rows", "phi_forward", "phi_adjoint", "grad_step", "op_norm",
     "pnp_den_create_haar", "pnp_den_create_cnn", "pnp_den_destroy", "denoise", "pnp_fb_run",
     "pnp_last_error", "pnp_kernel_launch_count", "pnp_plan_set_timing", "pnp_plan_read_timing",
@@ -56,7 +56,7 @@ class _Info(C.Structure):
                 ("tile", C.c_int), ("nblocks", C.c_int), ("M", C.c_int64), ("nnz", C.c_int64),
                 ("n_units", C.c_int64), ("beta", C.c_double), ("dl", C.c_double),
                 ("device_bytes", C.c_int64), ("region_pitch", C.c_int), ("run_max", C.c_int),
-                ("unit_nnz", C.c_int64), ("row_batch", C.c_int)]
+                ("unit_nnz", C.c_int64), ("row_batch", C.c_int), ("nstacks", C.c_int)]
 
 
 _lib = None
@@ -72,6 +72,8 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L = C.CDLL(path)
     vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
     L.pnp_plan_create.argtypes = [C.POINTER(vp), i32, i32, i64, vp, dbl, vp, i32, i32, vp, i32, vp]
+    L.pnp_plan_create_stacked.argtypes = [C.POINTER(vp), i32, i32, i64, vp, dbl, vp, i32, i32, vp, i32, vp, i32,
+                                          vp, vp]
     L.pnp_plan_destroy.argtypes = [vp]
     L.pnp_plan_destroy.restype = None
     L.pnp_plan_get_info.argtypes = [vp, C.POINTER(_Info)]
@@ -103,7 +105,7 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_plan_read_timing.argtypes = [vp, vp, vp]
     L.pnp_last_error.restype = C.c_char_p
     L.pnp_kernel_launch_count.restype = i64
-    for name in ("pnp_plan_create", "pnp_plan_get_info", "pnp_plan_set_unit_nnz", "pnp_plan_set_row_batch",
+    for name in ("pnp_plan_create", "pnp_plan_create_stacked", "pnp_plan_get_info", "pnp_plan_set_unit_nnz", "pnp_plan_set_row_batch",
                  "pnp_plan_export_rows",
                  "phi_forward", "phi_adjoint", "grad_step", "op_norm", "pnp_den_create_haar",
                  "pnp_den_create_cnn", "denoise", "pnp_fb_run", "pnp_plan_set_timing",
@@ -167,11 +169,14 @@ class Plan:
 
     ``omega``: (M, 2) float64 rad/pixel (column 0 pairs with image axis 0);
     ``w``: (M,) wavelengths; ``dl``: pixel size [rad] for the w-term (0: none);
-    ``J_per_row``: (M,) int8 supports in [J, 16] or None.
+    ``J_per_row``: (M,) int8 supports in [J, 16] or None;
+    ``stack``, ``w_centres``: the w-stacking hybrid of App. E (Eq. phip): (M,) int32
+    stack ids in [0, P) and the P stack centres [wavelengths]; Z_p then carries the
+    centre chirp and the rows of G only the offset w - w_p.
     """
 
     def __init__(self, n, K, omega, w=None, dl=0.0, J_per_row=None, J=7, weight_dtype="c64",
-                 block=None, nblocks=1, stream=None):
+                 block=None, nblocks=1, stream=None, stack=None, w_centres=None):
         import torch
         L = lib()
         omega = np.asarray(omega, dtype=np.float64)
@@ -186,10 +191,19 @@ class Plan:
         self.stream = torch.cuda.current_stream() if stream is None else stream
         self._h = C.c_void_p()
         wd = PNP_W_BF16C if weight_dtype in ("bf16", PNP_W_BF16C) else PNP_W_C64
-        _check(L.pnp_plan_create(C.byref(self._h), int(n), int(K), int(M), uvw.ctypes.data, float(dl),
-                                 None if jr is None else jr.ctypes.data, int(J), wd,
-                                 None if blk is None else blk.ctypes.data, int(nblocks),
-                                 _stream_handle(self.stream)))
+        if w_centres is None:
+            _check(L.pnp_plan_create(C.byref(self._h), int(n), int(K), int(M), uvw.ctypes.data, float(dl),
+                                     None if jr is None else jr.ctypes.data, int(J), wd,
+                                     None if blk is None else blk.ctypes.data, int(nblocks),
+                                     _stream_handle(self.stream)))
+        else:
+            wc = np.ascontiguousarray(w_centres, dtype=np.float64)
+            stk = np.ascontiguousarray(np.zeros(M) if stack is None else stack, dtype=np.int32)
+            _check(L.pnp_plan_create_stacked(C.byref(self._h), int(n), int(K), int(M), uvw.ctypes.data,
+                                             float(dl), None if jr is None else jr.ctypes.data, int(J), wd,
+                                             None if blk is None else blk.ctypes.data, int(nblocks),
+                                             stk.ctypes.data, int(wc.size), wc.ctypes.data,
+                                             _stream_handle(self.stream)))
         self.n, self.K, self.M = int(n), int(K), int(M)
 
     # ------------------------------------------------------------------ info

@@ -102,6 +102,10 @@ struct pnp_plan {
   int rpw = 2;         // rows per warp in flight
   int64_t M = 0, nnz = 0, unit_nnz = 1 << 17;
   double beta = 0, dl = 0;
+  int nstacks = 1;             // w-stacks P (App. E): rows sorted by stack, then tile and block
+  int64_t nkeys = 0;           // (tile, block) keys per stack
+  std::vector<double> w_centres;       // P stack centres [wavelengths]
+  std::vector<int64_t> h_stack_units;  // P+1: the work units of stack s are [s], [s+1])
   cudaStream_t stream = nullptr;   // caller's stream: every launch goes here
   cudaStream_t cstream = nullptr;  // private non-blocking stream for graph capture/replay
   cudaEvent_t ev_join[2] = {nullptr, nullptr};
@@ -129,6 +133,8 @@ struct pnp_plan {
   double* d_acc = nullptr;     // FP64 accumulators [8]
   int* d_status = nullptr;     // device status flags [4] (bit 0: gridding index out of range)
   float* d_img[3] = {nullptr, nullptr, nullptr};  // n*n work images
+  float2* d_chirp = nullptr;   // P*n (P > 1): per stack and image axis exp(i pi a_p (a - n/2)^2)
+  float* d_gacc = nullptr;     // n*n (P > 1): gradient image accumulated over the stacks
   int64_t device_bytes = 0;
 
   // optional per-stage event timing: (stage, start, stop)
@@ -140,7 +146,7 @@ struct pnp_plan {
   std::vector<int64_t> h_rowptr;   // M+1
   std::vector<int32_t> h_perm;     // sorted -> caller
   std::vector<int32_t> h_inv;      // caller -> sorted
-  std::vector<int32_t> h_key;      // sorted: tile * nblocks + block
+  std::vector<int32_t> h_key;      // sorted: (stack * ntc^2 + tile) * nblocks + block
   std::vector<uint16_t> h_start;   // sorted: first tap's cell in the tile (row * tile + col)
 };
 
@@ -156,16 +162,20 @@ namespace pnp {
 int stage_begin(pnp_plan* p, int stage, cudaEvent_t* a);
 int stage_end(pnp_plan* p, int stage, cudaEvent_t a);
 // fft.cu
-int fft_forward(pnp_plan* p, const float* x);                       // x -> d_gridA
-int fft_adjoint(pnp_plan* p, int mode, const float* x, float* out,  // d_gridB -> out
-                float gamma, float t);
-// gridding.cu
-int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out);
+// Stack s selects the centre chirp of Z_s (none for a plan with one stack); the adjoint of a
+// stack other than the last only accumulates Re{Z_s^H ...} into d_gacc, and the last one adds
+// the accumulated sum before its epilogue `mode`.
+int fft_forward(pnp_plan* p, const float* x, int s);                       // x -> d_gridA
+int fft_adjoint(pnp_plan* p, int mode, const float* x, float* out,         // d_gridB -> out
+                float gamma, float t, int s);
+// gridding.cu: the work units of stack s
+int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out, int s);
 // choose p->pitch from the plan's number of rows per support J (rows_per_J[0..16])
 int gridding_pitch(pnp_plan* p, const int64_t* rows_per_J);
 int permute_y(pnp_plan* p, const float2* y_user);  // d_ysorted = y_user[perm]
 // plan_build.cu
 int build_units(pnp_plan* p);
+int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t* block, const int32_t* stack);
 // update.cu
 int haar_denoise_dev(cudaStream_t s, const float* z, float* out, int n, float t, double* acc,
                      const float* x_prev);

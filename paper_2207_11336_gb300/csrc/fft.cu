@@ -207,10 +207,23 @@ struct FftArgs {
   double* acc;             // Q1 zeroes acc[0..3]; Q2 accumulates
   float gamma, t;
   int epi;
+  const float2* chirp;     // n (w-stack s of several): exp(i pi a_s (a - n/2)^2) per image axis, else NULL
+  float* gacc;             // n x n gradient image summed over the w-stacks
+  int gacc_mode;           // GACC_*: how the Q2 gradient meets gacc
 };
 
+// Q2 and the sum over w-stacks (Eq. phidagphi): the first stack writes its Re{Z_s^H F^H ...}
+// image to gacc, later ones add to it, and the last adds gacc to its own before the epilogue.
+enum GaccMode { GACC_NONE = 0, GACC_WRITE = 1, GACC_ADD = 2, GACC_FINAL = 3 };
+
+__device__ __forceinline__ float2 cmul2(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
 // ---------------------------------------------------------------- P1
-template <int LOGK, int R>
+// CH: the input is modulated by a w-stack's centre chirp (compiled separately so that the
+// plain operator keeps its register allocation)
+template <int LOGK, int R, bool CH>
 __global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_p1(FftArgs A) {
   constexpr int K = 1 << LOGK, T = K / 16, SROW = K + K / 16 + 1;
   extern __shared__ float2 smem[];
@@ -226,6 +239,17 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_p1(FftArgs A) {
     const int b = unpad_index(j + i * T, n, K);
     v[i] = (live && b >= 0) ? make_float2(A.x[(size_t)a * n + b] * ca * A.cinv[b], 0.f)
                             : make_float2(0.f, 0.f);
+  }
+  if (CH && live) {  // Z_s of a w-stack: the centre chirp, separable over the two axes
+    const float2 cha = A.chirp[a];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int b = unpad_index(j + i * T, n, K);
+      if (b >= 0) {
+        const float2 c = cmul2(cha, A.chirp[b]);
+        v[i] = make_float2(v[i].x * c.x, v[i].x * c.y);
+      }
+    }
   }
   fft_row<LOGK, -1>(v, s, j, A.tw, A.twp);
   __syncthreads();
@@ -315,7 +339,7 @@ __device__ __forceinline__ void block_reduce_add(double v0, double v1, double* a
 
 // ---------------------------------------------------------------- Q2
 // Two image rows per CTA, processed one after the other through one FFT buffer.
-template <int LOGK>
+template <int LOGK, bool CH>
 __global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(FftArgs A) {
   constexpr int K = 1 << LOGK, T = K / 16, SROW = K + K / 16 + 1;
   extern __shared__ float2 smem[];
@@ -332,13 +356,36 @@ __global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(FftArgs A) {
     for (int i = 0; i < 16; ++i) v[i] = row[j + i * T];
     fft_row<LOGK, +1>(v, smem, j, A.tw, A.twp);
     const float ca = A.cinv[a];
+    if (CH) {  // Re{conj(chirp) v}: the adjoint of the centre chirp of Z_s
+      const float2 cha = A.chirp[a];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int b = unpad_index(j + i * T, n, K);
-      if (b >= 0) gs[q * n + b] = v[i].x * ca * A.cinv[b];
+      for (int i = 0; i < 16; ++i) {
+        const int b = unpad_index(j + i * T, n, K);
+        if (b >= 0) {
+          const float2 c = cmul2(cha, A.chirp[b]);
+          gs[q * n + b] = (v[i].x * c.x + v[i].y * c.y) * ca * A.cinv[b];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int b = unpad_index(j + i * T, n, K);
+        if (b >= 0) gs[q * n + b] = v[i].x * ca * A.cinv[b];
+      }
     }
   }
   __syncthreads();
+  if (CH && A.gacc_mode != GACC_NONE) {
+    const size_t base = (size_t)a0 * n;
+    for (int i = j; i < 2 * n; i += T) {
+      float g = gs[i];
+      if (A.gacc_mode != GACC_WRITE) g += A.gacc[base + i];
+      if (A.gacc_mode == GACC_FINAL) gs[i] = g;
+      else A.gacc[base + i] = g;
+    }
+    if (A.gacc_mode != GACC_FINAL) return;  // uniform over the CTA
+    __syncthreads();
+  }
   double s0 = 0.0, s1 = 0.0;
   const float gamma = A.gamma;
   const size_t base = (size_t)a0 * n;
@@ -399,11 +446,15 @@ int launch_forward(pnp_plan* p, const FftArgs& A) {
   const int smem = R * SROW * 8;
   static bool attr = false;
   if (!attr) {
-    PNP_CUDA(cudaFuncSetAttribute(fft_p1<LOGK, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PNP_CUDA(cudaFuncSetAttribute(fft_p1<LOGK, R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PNP_CUDA(cudaFuncSetAttribute(fft_p1<LOGK, R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     PNP_CUDA(cudaFuncSetAttribute(fft_p2<LOGK, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr = true;
   }
-  fft_p1<LOGK, R><<<(p->n + R - 1) / R, R * T, smem, p->stream>>>(A);
+  if (A.chirp)
+    fft_p1<LOGK, R, true><<<(p->n + R - 1) / R, R * T, smem, p->stream>>>(A);
+  else
+    fft_p1<LOGK, R, false><<<(p->n + R - 1) / R, R * T, smem, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
   fft_p2<LOGK, R><<<K / R, R * T, smem, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
@@ -422,20 +473,26 @@ int launch_adjoint(pnp_plan* p, const FftArgs& A) {
     attr1 = true;
   }
   if (smem2 > attr2) {
-    PNP_CUDA(cudaFuncSetAttribute(fft_q2<LOGK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+    PNP_CUDA(cudaFuncSetAttribute(fft_q2<LOGK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+    PNP_CUDA(cudaFuncSetAttribute(fft_q2<LOGK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
     attr2 = smem2;
   }
   fft_q1<LOGK, R><<<K / R, R * T, smem1, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
-  fft_q2<LOGK><<<p->n / 2, T, smem2, p->stream>>>(A);
+  if (A.chirp)
+    fft_q2<LOGK, true><<<p->n / 2, T, smem2, p->stream>>>(A);
+  else
+    fft_q2<LOGK, false><<<p->n / 2, T, smem2, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
 
 }  // namespace
 
-int fft_forward(pnp_plan* p, const float* x) {
+int fft_forward(pnp_plan* p, const float* x, int s) {
+  if (s < 0 || s >= p->nstacks) return fail(PNP_ERR_INVALID_ARG, "internal: stack index out of range");
   FftArgs A{};
+  A.chirp = p->nstacks > 1 ? p->d_chirp + (size_t)s * p->n : nullptr;
   A.n = p->n;
   A.x = x;
   A.cinv = p->d_cinv;
@@ -462,8 +519,14 @@ int fft_forward(pnp_plan* p, const float* x) {
   return stage_end(p, 0, ev);
 }
 
-int fft_adjoint(pnp_plan* p, int mode, const float* x, float* out, float gamma, float t) {
+int fft_adjoint(pnp_plan* p, int mode, const float* x, float* out, float gamma, float t, int s) {
+  if (s < 0 || s >= p->nstacks) return fail(PNP_ERR_INVALID_ARG, "internal: stack index out of range");
   FftArgs A{};
+  if (p->nstacks > 1) {
+    A.chirp = p->d_chirp + (size_t)s * p->n;
+    A.gacc = p->d_gacc;
+    A.gacc_mode = s == 0 ? GACC_WRITE : (s == p->nstacks - 1 ? GACC_FINAL : GACC_ADD);
+  }
   A.n = p->n;
   A.x = x;
   A.cinv = p->d_cinv;

@@ -30,7 +30,7 @@ constexpr uint32_t WAIT_LIMIT = 1u << 26;  // bounded mbarrier waits (seconds, n
 struct GArgs {
   int K, logK, T, S, P, ntc;  // grid side, log2 K, tile side, staged region side, region row pitch, tiles per side
   const Unit* units;
-  long long n_units;
+  long long u_begin, n_units;  // this launch walks units [u_begin, n_units) (one w-stack)
   const Chunk* chunks;
   const int64_t* rowptr;
   const void* w;
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(GPASS_THREADS, 1) gpass(GArgs A) {
   constexpr int NCW = GPASS_CONSUMERS;
   constexpr int CT = NCW * 32;
 
-  if (blockIdx.x >= A.n_units) return;
+  if (A.u_begin + blockIdx.x >= A.n_units) return;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(&full[s], 1);
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(GPASS_THREADS, 1) gpass(GArgs A) {
     if (lane != 0) return;
     // The descriptors of the next chunk are loaded before the current one is issued, so their
     // latency overlaps the wait for a free stage instead of adding to every issue.
-    long long u = blockIdx.x;
+    long long u = A.u_begin + blockIdx.x;
     int c = 0;
     Unit U = A.units[u];
     Chunk cur = A.chunks[U.chunk_begin];
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(GPASS_THREADS, 1) gpass(GArgs A) {
   int st = 0;
   uint32_t ph = 0;
   int rb = 0;  // rows of the stream before the current chunk, modulo NCW
-  for (long long u = blockIdx.x; u < A.n_units; u += gridDim.x) {
+  for (long long u = A.u_begin + blockIdx.x; u < A.n_units; u += gridDim.x) {
     const Unit U = A.units[u];
     const int tr = U.tile / A.ntc, tc = U.tile - tr * A.ntc;
     const int r0 = tr * A.T, c0 = tc * A.T;
@@ -464,7 +464,7 @@ int launch_gpass(pnp_plan* p, const GArgs& A) {
   }
   if (per_sm < 1) return fail(PNP_ERR_UNSUPPORTED, "gridding tile does not fit in shared memory");
   long long grid = (long long)per_sm * p->num_sms;
-  if (grid > A.n_units) grid = A.n_units;
+  if (grid > A.n_units - A.u_begin) grid = A.n_units - A.u_begin;
   if (grid < 1) return PNP_OK;
   gpass<MODE, WT, RB><<<(unsigned)grid, GPASS_THREADS, smem, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
@@ -556,8 +556,11 @@ int permute_y(pnp_plan* p, const float2* y_user) {
 // mode G_DEGRID: y_out (caller order) = G gridA.
 // mode G_GRID:   gridB += G^H d_ysorted.
 // mode G_FUSED:  gridB += G^H (G gridA - d_ysorted)  (no data term when y_user == NULL).
-int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out) {
+int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out, int s) {
   if (p->M == 0 || p->n_units == 0) return PNP_OK;
+  if (s < 0 || s >= p->nstacks) return fail(PNP_ERR_INVALID_ARG, "internal: stack index out of range");
+  const long long ub = p->h_stack_units[s], ue = p->h_stack_units[s + 1];
+  if (ub >= ue) return PNP_OK;  // a stack without rows grids nothing
   GArgs A{};
   A.K = p->K;
   A.logK = p->logK;
@@ -566,7 +569,8 @@ int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out) {
   A.P = p->pitch > 0 ? p->pitch : A.S;
   A.ntc = p->ntc;
   A.units = p->d_units;
-  A.n_units = p->n_units;
+  A.u_begin = ub;
+  A.n_units = ue;
   A.chunks = p->d_chunks;
   A.rowptr = p->d_rowptr;
   A.w = p->d_w;

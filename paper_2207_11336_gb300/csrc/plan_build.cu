@@ -195,12 +195,14 @@ int build_units(pnp_plan* p) {
   std::vector<uint8_t> runs;
   const int64_t M = p->M;
   auto nnz_of = [&](int64_t i) { return p->h_rowptr[i + 1] - p->h_rowptr[i]; };
+  std::vector<int64_t> stack_units(p->nstacks + 1, 0);
   int64_t i = 0;
   while (i < M) {
     const int32_t key = p->h_key[i];
     Unit u;
     u.chunk_begin = (long long)chunks.size();
-    u.tile = key / p->nblocks;
+    u.tile = (int)((key % p->nkeys) / p->nblocks);
+    stack_units[key / p->nkeys + 1] = (int64_t)units.size() + 1;  // units of a stack are consecutive
     int64_t unit_taps = 0;
     while (i < M && p->h_key[i] == key && (unit_taps == 0 || unit_taps + nnz_of(i) <= p->unit_nnz)) {
       Chunk ch;
@@ -253,6 +255,9 @@ int build_units(pnp_plan* p) {
   }
   p->n_units = (int64_t)units.size();
   p->n_chunks = (int64_t)chunks.size();
+  for (int s = 0; s < p->nstacks; ++s)  // empty stacks start and end where the previous one ends
+    stack_units[s + 1] = std::max(stack_units[s + 1], stack_units[s]);
+  p->h_stack_units.swap(stack_units);
   if (int rc = dev_alloc(p, &p->d_units, units.size())) return rc;
   if (int rc = dev_alloc(p, &p->d_chunks, chunks.size())) return rc;
   p->n_runs = (int64_t)runs.size();
@@ -266,7 +271,7 @@ int build_units(pnp_plan* p) {
   return PNP_OK;
 }
 
-int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t* block) {
+int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t* block, const int32_t* stack) {
   const int n = p->n, K = p->K, J = p->J;
   const int64_t M = p->M;
   p->beta = kb_beta(J, (double)K / n);
@@ -292,7 +297,11 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     RowGeom g;
     g.kap0 = uvw[3 * m] * (K / (2.0 * M_PI));
     g.kap1 = uvw[3 * m + 1] * (K / (2.0 * M_PI));
-    g.a = p->dl > 0 ? uvw[3 * m + 2] * p->dl * p->dl : 0.0;
+    if (stack && (stack[m] < 0 || stack[m] >= p->nstacks))
+      return fail(PNP_ERR_INVALID_ARG, "stack id out of range at row " + std::to_string(m));
+    // w-stacking (App. E): the row kernel carries only the offset from its stack's centre
+    const double wres = uvw[3 * m + 2] - (stack ? p->w_centres[stack[m]] : 0.0);
+    g.a = p->dl > 0 ? wres * p->dl * p->dl : 0.0;
     g.J = Jrow ? Jrow[m] : J;
     if (!(std::isfinite(g.kap0) && std::isfinite(g.kap1) && std::isfinite(g.a)))
       return fail(PNP_ERR_INVALID_ARG, "non-finite uvw at row " + std::to_string(m));
@@ -340,6 +349,8 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     }
   }
   const int64_t nkeys = (int64_t)ntc * ntc * p->nblocks;
+  if (nkeys * p->nstacks > INT32_MAX) return fail(PNP_ERR_UNSUPPORTED, "too many (stack, tile, block) keys");
+  p->nkeys = nkeys;
   std::vector<int64_t> cnt(nkeys + 1, 0);
   for (int64_t m = 0; m < M; ++m) cnt[key[m] + 1]++;
   for (int64_t k = 0; k < nkeys; ++k) cnt[k + 1] += cnt[k];
@@ -347,10 +358,19 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
   p->h_inv.assign(M, 0);
   for (int64_t i = 0; i < M; ++i) {
     const int32_t m = by_j[i];
-    const int64_t pos = cnt[key[m]]++;
-    p->h_perm[pos] = m;
-    p->h_inv[m] = (int32_t)pos;
+    p->h_perm[cnt[key[m]]++] = m;
   }
+  if (stack && p->nstacks > 1) {  // most significant: the w-stack
+    std::vector<int64_t> cs(p->nstacks + 1, 0);
+    for (int64_t m = 0; m < M; ++m) cs[stack[m] + 1]++;
+    for (int s = 0; s < p->nstacks; ++s) cs[s + 1] += cs[s];
+    for (int64_t i = 0; i < M; ++i) {
+      const int32_t m = p->h_perm[i];
+      by_j[cs[stack[m]]++] = m;
+    }
+    p->h_perm.swap(by_j);
+  }
+  for (int64_t i = 0; i < M; ++i) p->h_inv[p->h_perm[i]] = (int32_t)i;
   std::vector<int32_t>().swap(by_j);
   std::vector<RowGeom> sgeom(M);
   p->h_key.assign(M, 0);
@@ -359,7 +379,7 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
   for (int64_t i = 0; i < M; ++i) {
     const int64_t m = p->h_perm[i];
     sgeom[i] = geom[m];
-    p->h_key[i] = key[m];
+    p->h_key[i] = (int32_t)((stack ? (int64_t)stack[m] : 0) * nkeys + key[m]);
     p->h_start[i] = startc[m];
     p->h_rowptr[i + 1] = p->h_rowptr[i] + (int64_t)geom[m].J * geom[m].J;
   }
@@ -434,6 +454,20 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
   if (int rc = dev_alloc(p, &p->d_status, 4)) return rc;
   for (int i = 0; i < 3; ++i)
     if (int rc = dev_alloc(p, &p->d_img[i], (size_t)n * n)) return rc;
+  if (p->nstacks > 1) {
+    // Z_s of stack s: the paraxial w-modulation of the stack centre, separable per axis
+    std::vector<float2> ch((size_t)p->nstacks * n);
+    for (int s = 0; s < p->nstacks; ++s) {
+      const double as = p->w_centres[s] * p->dl * p->dl;
+      for (int a = 0; a < n; ++a) {
+        const double q = (double)(a - n / 2), ph = M_PI * as * q * q;
+        ch[(size_t)s * n + a] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+      }
+    }
+    if (int rc = dev_alloc(p, &p->d_chirp, ch.size())) return rc;
+    if (int rc = dev_alloc(p, &p->d_gacc, (size_t)n * n)) return rc;
+    PNP_CUDA(cudaMemcpy(p->d_chirp, ch.data(), ch.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  }
   PNP_CUDA(cudaMemcpy(p->d_cinv, cinv.data(), n * sizeof(float), cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(p->d_tw, tw.data(), K * sizeof(float2), cudaMemcpyHostToDevice));
   {
@@ -513,7 +547,7 @@ int export_rows_impl(const pnp_plan* p, const int64_t* rows, int64_t nrows, int6
   for (int64_t i = 0; i < nrows; ++i) {
     if (rows[i] < 0 || rows[i] >= p->M) return fail(PNP_ERR_INVALID_ARG, "export row index out of range");
     const int64_t s = p->h_inv[rows[i]];
-    const int tile = p->h_key[s] / p->nblocks;
+    const int tile = (int)((p->h_key[s] % p->nkeys) / p->nblocks);
     src[4 * i] = p->h_rowptr[s];
     src[4 * i + 1] = p->h_rowptr[s + 1] - p->h_rowptr[s];
     src[4 * i + 2] = (int64_t)(tile / p->ntc) * p->tile;

@@ -16,7 +16,6 @@ int fail(int code, const std::string& msg) {
   return code;
 }
 
-int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t* block);
 int export_rows_impl(const pnp_plan* p, const int64_t* rows, int64_t nrows, int64_t* offsets,
                      float* weights, int32_t* cols);
 int norm2_dev(cudaStream_t s, const float* v, int64_t count, double* acc);
@@ -76,6 +75,8 @@ void free_plan(pnp_plan* p) {
   for (auto& e : p->ev_join)
     if (e) cudaEventDestroy(e);
   for (float* im : p->d_img) cudaFree(im);
+  cudaFree(p->d_chirp);
+  cudaFree(p->d_gacc);
   delete p;
 }
 
@@ -87,12 +88,24 @@ int read_acc(pnp_plan* p, double* h, int count) {
   return PNP_OK;
 }
 
+// Re{Phi^H (Phi xf - y)} (or Re{Phi^H Phi xf} without y) through epilogue `epi`, summed over the
+// plan's w-stacks (Eq. phidagphi): per stack the forward FFT with Z_s, the fused gridding pass
+// over the stack's rows and the adjoint FFT; all stacks share one pair of grids.
+int normal_pass(pnp_plan* p, const float2* y_sorted, const float* xf, int epi, const float* xe, float* out,
+                float gamma, float t) {
+  for (int s = 0; s < p->nstacks; ++s) {
+    if (int rc = fft_forward(p, xf, s)) return rc;
+    if (int rc = gridding_pass(p, G_FUSED, y_sorted, nullptr, s)) return rc;
+    if (int rc = fft_adjoint(p, epi, xe, out, gamma, t, s)) return rc;
+  }
+  return PNP_OK;
+}
+
 // One FB iteration x_next = D(x_cur - gamma grad f(x_cur)); FP64 norms land in acc[0..1].
 int fb_iteration(pnp_plan* p, pnp_den* d, const float* cur, float* nxt, double gamma) {
-  if (int rc = fft_forward(p, cur)) return rc;
-  if (int rc = gridding_pass(p, G_FUSED, reinterpret_cast<const float2*>(p->d_ysorted), nullptr)) return rc;
-  if (d->kind == PNP_DEN_HAAR) return fft_adjoint(p, EPI_HAAR, cur, nxt, (float)gamma, (float)d->t);
-  if (int rc = fft_adjoint(p, EPI_GRAD, cur, p->d_img[1], (float)gamma, 0.f)) return rc;
+  const float2* ys = reinterpret_cast<const float2*>(p->d_ysorted);
+  if (d->kind == PNP_DEN_HAAR) return normal_pass(p, ys, cur, EPI_HAAR, cur, nxt, (float)gamma, (float)d->t);
+  if (int rc = normal_pass(p, ys, cur, EPI_GRAD, cur, p->d_img[1], (float)gamma, 0.f)) return rc;
   return cnn_denoise(d, p->stream, p->d_img[1], nxt, p->n, p->d_acc, cur);
 }
 
@@ -172,6 +185,14 @@ int64_t pnp_kernel_launch_count(void) { return g_launches.load(); }
 int pnp_plan_create(pnp_plan** plan, int n, int K, int64_t M, const double* uvw_host, double dl,
                     const int8_t* J_per_row_host, int J, int weight_dtype, const int32_t* block_host,
                     int nblocks, void* stream) {
+  return pnp_plan_create_stacked(plan, n, K, M, uvw_host, dl, J_per_row_host, J, weight_dtype, block_host,
+                                 nblocks, nullptr, 1, nullptr, stream);
+}
+
+int pnp_plan_create_stacked(pnp_plan** plan, int n, int K, int64_t M, const double* uvw_host, double dl,
+                            const int8_t* J_per_row_host, int J, int weight_dtype, const int32_t* block_host,
+                            int nblocks, const int32_t* stack_host, int nstacks, const double* w_centres_host,
+                            void* stream) {
   if (!plan) return fail(PNP_ERR_INVALID_ARG, "plan pointer is NULL");
   *plan = nullptr;
   if (n < 8 || (n & 1)) return fail(PNP_ERR_INVALID_ARG, "n must be even and >= 8");
@@ -183,7 +204,16 @@ int pnp_plan_create(pnp_plan** plan, int n, int K, int64_t M, const double* uvw_
   if (weight_dtype != PNP_W_C64 && weight_dtype != PNP_W_BF16C) return fail(PNP_ERR_INVALID_ARG, "bad weight_dtype");
   if (nblocks < 1) return fail(PNP_ERR_INVALID_ARG, "nblocks must be >= 1");
   if (!(dl >= 0.0) || !std::isfinite(dl)) return fail(PNP_ERR_INVALID_ARG, "dl must be finite and >= 0");
+  if (nstacks < 1 || nstacks > 64) return fail(PNP_ERR_INVALID_ARG, "nstacks must lie in [1, 64]");
+  if (nstacks > 1 && (!stack_host && M > 0)) return fail(PNP_ERR_INVALID_ARG, "stack ids are NULL");
+  if (nstacks > 1 && !w_centres_host) return fail(PNP_ERR_INVALID_ARG, "w_centres is NULL");
+  if (nstacks > 1 && dl == 0.0) return fail(PNP_ERR_INVALID_ARG, "w-stacking needs dl > 0");
+  for (int s = 0; w_centres_host && s < nstacks; ++s)
+    if (!std::isfinite(w_centres_host[s])) return fail(PNP_ERR_INVALID_ARG, "non-finite w centre");
   pnp_plan* p = new pnp_plan();
+  p->nstacks = nstacks;
+  p->w_centres.assign(nstacks, 0.0);
+  if (w_centres_host) p->w_centres.assign(w_centres_host, w_centres_host + nstacks);
   p->n = n;
   p->K = K;
   p->logK = 0;
@@ -208,7 +238,7 @@ int pnp_plan_create(pnp_plan** plan, int n, int K, int64_t M, const double* uvw_
     free_plan(p);
     return fail(PNP_ERR_CUDA, "stream/event creation failed");
   }
-  int rc = plan_build(p, uvw_host, J_per_row_host, block_host);
+  int rc = plan_build(p, uvw_host, J_per_row_host, block_host, nstacks > 1 ? stack_host : nullptr);
   if (rc != PNP_OK) {
     std::string keep = t_err;
     free_plan(p);
@@ -241,6 +271,7 @@ int pnp_plan_get_info(const pnp_plan* p, pnp_plan_info* info) {
   info->region_pitch = p->pitch > 0 ? p->pitch : p->tile + p->Jmax - 1;
   info->run_max = p->run_max;
   info->row_batch = p->row_batch;
+  info->nstacks = p->nstacks;
   info->unit_nnz = p->unit_nnz;
   return PNP_OK;
 }
@@ -287,13 +318,15 @@ int pnp_plan_autotune(pnp_plan* p, int reps, int* run_max_out, int64_t* unit_nnz
         if ((rc = build_units(p))) break;
         for (int rb : batches) {
           p->row_batch = rb;
-          if ((rc = gridding_pass(p, G_FUSED, nullptr, nullptr))) break;  // warm-up
+          for (int s = 0; s < p->nstacks && !rc; ++s) rc = gridding_pass(p, G_FUSED, nullptr, nullptr, s);  // warm-up
+          if (rc) break;
           if (cudaEventRecord(e0, p->stream) != cudaSuccess) {
             cudaGetLastError();
             rc = fail(PNP_ERR_CUDA, "autotune: event record failed");
             break;
           }
-          for (int i = 0; i < reps && !rc; ++i) rc = gridding_pass(p, G_FUSED, nullptr, nullptr);
+          for (int i = 0; i < reps && !rc; ++i)
+            for (int s = 0; s < p->nstacks && !rc; ++s) rc = gridding_pass(p, G_FUSED, nullptr, nullptr, s);
           if (rc) break;
           float ms = 0.f;
           if (cudaEventRecord(e1, p->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
@@ -379,15 +412,21 @@ int pnp_plan_export_rows(const pnp_plan* p, const int64_t* rows, int64_t nrows, 
 
 int phi_forward(pnp_plan* p, const float* x, float* y) {
   if (!p || !x || (p->M > 0 && !y)) return fail(PNP_ERR_INVALID_ARG, "NULL argument");
-  if (int rc = fft_forward(p, x)) return rc;
-  return gridding_pass(p, G_DEGRID, nullptr, reinterpret_cast<float2*>(y));
+  for (int s = 0; s < p->nstacks; ++s) {
+    if (int rc = fft_forward(p, x, s)) return rc;
+    if (int rc = gridding_pass(p, G_DEGRID, nullptr, reinterpret_cast<float2*>(y), s)) return rc;
+  }
+  return PNP_OK;
 }
 
 int phi_adjoint(pnp_plan* p, const float* y, float* x) {
   if (!p || !x || (p->M > 0 && !y)) return fail(PNP_ERR_INVALID_ARG, "NULL argument");
   if (int rc = permute_y(p, reinterpret_cast<const float2*>(y))) return rc;
-  if (int rc = gridding_pass(p, G_GRID, reinterpret_cast<const float2*>(y), nullptr)) return rc;
-  return fft_adjoint(p, EPI_ADJ, nullptr, x, 0.f, 0.f);
+  for (int s = 0; s < p->nstacks; ++s) {
+    if (int rc = gridding_pass(p, G_GRID, reinterpret_cast<const float2*>(y), nullptr, s)) return rc;
+    if (int rc = fft_adjoint(p, EPI_ADJ, nullptr, x, 0.f, 0.f, s)) return rc;
+  }
+  return PNP_OK;
 }
 
 int grad_step(pnp_plan* p, const float* x, const float* y, double gamma, float* x_out) {
@@ -395,9 +434,7 @@ int grad_step(pnp_plan* p, const float* x, const float* y, double gamma, float* 
   if (x == x_out) return fail(PNP_ERR_INVALID_ARG, "x and x_out must not alias");
   if (!std::isfinite(gamma)) return fail(PNP_ERR_INVALID_ARG, "gamma must be finite");
   if (int rc = permute_y(p, reinterpret_cast<const float2*>(y))) return rc;
-  if (int rc = fft_forward(p, x)) return rc;
-  if (int rc = gridding_pass(p, G_FUSED, reinterpret_cast<const float2*>(y), nullptr)) return rc;
-  return fft_adjoint(p, EPI_GRAD, x, x_out, (float)gamma, 0.f);
+  return normal_pass(p, reinterpret_cast<const float2*>(y), x, EPI_GRAD, x, x_out, (float)gamma, 0.f);
 }
 
 int op_norm(pnp_plan* p, const float* v0, int max_it, double tol, double* L_out, int* iters_out) {
@@ -413,9 +450,7 @@ int op_norm(pnp_plan* p, const float* v0, int max_it, double tol, double* L_out,
   double L = 0.0, h[2];
   int it = 0;
   for (it = 1; it <= max_it; ++it) {
-    if (int rc = fft_forward(p, v)) return rc;
-    if (int rc = gridding_pass(p, G_FUSED, nullptr, nullptr)) return rc;
-    if (int rc = fft_adjoint(p, EPI_NORMAL, nullptr, g, 0.f, 0.f)) return rc;
+    if (int rc = normal_pass(p, nullptr, v, EPI_NORMAL, nullptr, g, 0.f, 0.f)) return rc;
     if (int rc = scale_image(p->stream, g, v, N, p->d_acc, 0)) return rc;
     if (int rc = read_acc(p, h, 1)) return rc;
     const double Ln = std::sqrt(h[0]);
