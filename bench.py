@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-bf16-g", dest="bf16_g", action="store_false",
                     help="skip timing the plain loop with BF16 weights in G")
+    ap.add_argument("--wstacks", type=int, default=8,
+                    help="w-stacks of the stacked-operator comparison line (0 skips it)")
     ap.add_argument("--kernel-case", choices=["gridding", "cnn", "fft"], default=None,
                     help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
     ap.add_argument("--cnn-side", type=int, default=4096,
@@ -415,6 +417,35 @@ def run_gpu(args):
                                       "G_bytes": plan_bf.info["nnz"] * 6}
         plan_bf.close()
         del plan_bf, y_bf, xb
+    if args.wstacks > 1 and prob["dl"] > 0 and prob["J_per_row"] is not None:
+        # the w-stacking hybrid (App. E): P stacks with the centre chirps in Z_p and the residual w in G
+        supports = synth.CONFIGS[wl["name"]]["supports"]
+        stk, cen = synth.w_stacks_min_taps(prob["w"], args.wstacks, supports)
+        jr_s = synth.j_per_row_stacked(prob["w"], stk, cen, prob["w"], supports)
+        t_plan = time.perf_counter()
+        plan_ws = pnp.Plan(n, K, prob["omega"], prob["w"], prob["dl"], jr_s, block=prob["block"],
+                           nblocks=BLOCKS[wl["name"]], stream=stream, stack=stk, w_centres=cen)
+        t_plan = time.perf_counter() - t_plan
+        tune_ws = plan_ws.autotune(reps=2)
+        y_ws = plan_ws.phi_forward(x_true)
+        err = float(torch.linalg.vector_norm((y_ws - y0).to(torch.complex128)) /
+                    torch.linalg.vector_norm(y0.to(torch.complex128)))
+        xw = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+        plan_ws.fb_run(haar, y, x0=xw, gamma=gamma, L=L, max_iter=4, check_every=2, use_graph=True, inplace=True)
+        ms_ws, _ = _timed_loop(plan_ws, haar, y, xw, gamma, L, steps, stream)
+        plan_ws.set_timing(True)
+        plan_ws.fb_run(haar, y, x0=xw, gamma=gamma, L=L, max_iter=5, check_every=5, use_graph=False, inplace=True)
+        tw = plan_ws.read_timing()
+        plan_ws.set_timing(False)
+        comparison["plain_wstacked"] = {
+            "stacks": args.wstacks, "w_centres": [round(float(v), 1) for v in cen],
+            "iter_per_s": ws * steps / (ms_ws / 1e3), "ms_per_iter": ms_ws / steps,
+            "nnz": plan_ws.info["nnz"], "G_bytes": plan_ws.info["nnz"] * 10,
+            "G_bytes_unstacked": info["nnz"] * 10,
+            "gridding_ms_per_iter": tw["gridding"][0] / 5, "fft_ms_per_iter": (tw["fft_forward"][0] + tw["fft_adjoint"][0]) / 5,
+            "phi_rel_l2_vs_unstacked": err, "plan_build_s": t_plan, "gridding_autotune": tune_ws}
+        plan_ws.close()
+        del plan_ws, y_ws, xw
     if learned:
         xl = torch.zeros((n, n), dtype=torch.float32, device="cuda")
         it_l, trace_l = _run_to_snr(plan, cnn, y_s, xl, gamma, L, x_true, alpha, snr_plain, SNR_MAX_ITERS)

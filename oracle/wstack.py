@@ -28,6 +28,28 @@ import numpy as np
 from . import nufft as nu
 
 
+def centre_chirp(n: int, w_centre: float, dl: float) -> np.ndarray:
+    """The image modulation of Z_p: exp(i pi a_p (p0^2 + p1^2)), a_p = w_p dl^2, on the n x n pixels."""
+    p = nu.pixel_offsets(n).astype(np.float64)
+    ch = np.exp(1j * np.pi * w_centre * dl * dl * p * p)
+    return np.outer(ch, ch)
+
+
+def forward_rows(n: int, K: int, omega, w, dl: float, stack, w_centres, J_per_row, x, rows) -> np.ndarray:
+    """Rows ``rows`` of Phi x for the stacked operator, one full-size FFT per stack they touch."""
+    rows = np.asarray(rows)
+    stack = np.asarray(stack)
+    w_res = np.asarray(w, dtype=np.float64) - np.asarray(w_centres, dtype=np.float64)[stack]
+    gs = nu.GridSpec(n, K)
+    out = np.zeros(rows.size, dtype=np.complex128)
+    for s in np.unique(stack[rows]):
+        sel = np.nonzero(stack[rows] == s)[0]
+        Xhat = nu.dft2(nu.zero_pad(gs, x * centre_chirp(n, float(w_centres[s]), dl))).ravel()
+        G = nu.degridding_matrix(gs, omega, w_res, dl, J_per_row, rows[sel])
+        out[sel] = G @ Xhat
+    return out
+
+
 class StackedOperator:
     """Phi = [Phi_1; ...; Phi_P] with Phi_p = G_p F Z_p (FP64); rows keep the caller's order."""
 
@@ -41,14 +63,12 @@ class StackedOperator:
         self.P = self.w_centres.size
         Jr = None if J_per_row is None else np.asarray(J_per_row, dtype=np.int64)
         self.rows, self.ops, self.chirps = [], [], []
-        p = nu.pixel_offsets(n).astype(np.float64)
         for s in range(self.P):
             r = np.nonzero(stack == s)[0]
             self.rows.append(r)
             self.ops.append(nu.Operator(n, K, omega[r], w[r] - self.w_centres[s], dl,
                                         None if Jr is None else Jr[r], J, beta))
-            ch = np.exp(1j * np.pi * self.w_centres[s] * dl * dl * p * p)  # one axis of Z_p's chirp
-            self.chirps.append(np.outer(ch, ch))
+            self.chirps.append(centre_chirp(n, self.w_centres[s], dl))
 
     def forward(self, x) -> np.ndarray:
         """y = Phi x: row block p is G_p F Z_p x (Eq. phip)."""

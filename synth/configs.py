@@ -35,8 +35,9 @@ def make_problem(name: str, M: int | None = None, n: int | None = None, K: int |
     J_per_row (int8 or None for a single J=7), x_true (n, n) float64 sky,
     noise (M,) standard complex normal draws, block (M,) int32, facet widths,
     and the w-stack layout: stack (M,) int32 ids and w_centres (n_stacks,).  With
-    n_stacks > 1 (w-stacking hybrid, App. E) the supports follow the residual
-    |w - centre| against the unstacked |w| quartile edges.
+    n_stacks > 1 (w-stacking hybrid, App. E) the stacks are the minimum-taps
+    partition of w and the supports follow the residual |w - centre| against the
+    unstacked |w| quartile edges.
     """
     cfg = dict(CONFIGS[name])
     if M is not None:
@@ -55,7 +56,7 @@ def make_problem(name: str, M: int | None = None, n: int | None = None, K: int |
     if n_stacks > 1:
         if cfg["supports"] is None or dl == 0.0:
             raise ValueError(f"{name} has no w-terms to stack")
-        out["stack"], out["w_centres"] = mk.w_stacks(w, n_stacks)
+        out["stack"], out["w_centres"] = mk.w_stacks_min_taps(w, n_stacks, cfg["supports"])
         out["J_per_row"] = mk.j_per_row_stacked(w, out["stack"], out["w_centres"], w, cfg["supports"])
     else:
         out["stack"], out["w_centres"] = np.zeros(m, dtype=np.int32), np.zeros(1)

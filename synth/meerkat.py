@@ -116,6 +116,65 @@ def w_stacks(w: np.ndarray, n_stacks: int) -> tuple[np.ndarray, np.ndarray]:
     return stack, centres
 
 
+def w_stacks_min_taps(w: np.ndarray, n_stacks: int, supports=(7, 9, 12, 16), bins: int = 512):
+    """w-stack layout (stack ids int32, centres float64) that minimises the taps of G.
+
+    A planning rule for the w-stacking hybrid (App. E leaves the binning to a cost model of
+    the operator): w is cut into ``bins`` equal-count bins (fine where the rows are dense),
+    and dynamic programming splits them into n_stacks contiguous stacks minimising the sum
+    over rows of J^2 with J given by ``j_per_row_stacked``'s rule (residual |w - centre|
+    against the unstacked |w| quartile edges, taken at the bin's edge farther from the
+    centre).  Each stack takes the best of three centres: the midpoint of its w range, its
+    median, and its point nearest w = 0 (so a stack holding w = 0 can keep the central rows
+    on the unstacked supports).  Rows are then assigned by the chosen w edges.
+    """
+    w = np.asarray(w, dtype=np.float64)
+    if n_stacks < 1:
+        raise ValueError("n_stacks must be >= 1")
+    if w.size == 0 or n_stacks == 1:
+        return np.zeros(w.size, dtype=np.int32), np.array([0.5 * (w.min() + w.max()) if w.size else 0.0])
+    qe = np.quantile(np.abs(w), [0.25, 0.5, 0.75])
+    sq = np.asarray(supports, dtype=np.float64) ** 2
+    edges = np.unique(np.quantile(w, np.linspace(0.0, 1.0, bins + 1)))
+    bins = edges.size - 1
+    if bins < 1:
+        return np.zeros(w.size, dtype=np.int32), np.full(n_stacks, w[0])
+    cnt, _ = np.histogram(w, edges)
+    cost = np.full((bins + 1, bins + 1), np.inf)
+    centre = np.zeros((bins + 1, bins + 1))
+    for i in range(bins):
+        j = np.arange(i + 1, bins + 1)
+        outside = np.arange(i, bins)[None, :] >= j[:, None]
+        best_c, best_t = None, None
+        for c in (0.5 * (edges[i] + edges[j]), edges[(i + j) // 2], np.clip(0.0, edges[i], edges[j])):
+            r = np.maximum(np.abs(edges[None, i:-1] - c[:, None]), np.abs(edges[None, i + 1:] - c[:, None]))
+            taps = sq[np.searchsorted(qe, r, side="right")] * cnt[None, i:]
+            taps[outside] = 0.0
+            t = taps.sum(axis=1)
+            if best_t is None:
+                best_c, best_t = c.copy(), t
+            else:
+                better = t < best_t
+                best_c[better], best_t[better] = c[better], t[better]
+        cost[i, i + 1:] = best_t
+        centre[i, i + 1:] = best_c
+    best = np.full((n_stacks + 1, bins + 1), np.inf)
+    best[0, 0] = 0.0
+    arg = np.zeros((n_stacks + 1, bins + 1), dtype=np.int64)
+    for p in range(1, n_stacks + 1):
+        for j in range(1, bins + 1):
+            v = best[p - 1, :j] + cost[:j, j]
+            k = int(np.argmin(v))
+            best[p, j], arg[p, j] = v[k], k
+    cuts = [bins]
+    for p in range(n_stacks, 0, -1):
+        cuts.append(int(arg[p, cuts[-1]]))
+    cuts = np.asarray(cuts[::-1])
+    we = edges[cuts]
+    stack = np.clip(np.searchsorted(we[1:-1], w, side="right"), 0, n_stacks - 1).astype(np.int32)
+    return stack, centre[cuts[:-1], cuts[1:]].astype(np.float64)
+
+
 def j_per_row_stacked(w: np.ndarray, stack: np.ndarray, centres: np.ndarray, w_ref: np.ndarray,
                       supports=(7, 9, 12, 16)) -> np.ndarray:
     """Per-row support J (int8) of a w-stacked operator: the |w| quartile edges of the

@@ -109,3 +109,36 @@ def test_stacking_lowers_truncation_error_at_fixed_support():
         errs.append(_rel(StackedOperator(n, K, omega, w, dl, stack, cen, J7).forward(x), yd))
     assert all(e1 > e2 for e1, e2 in zip(errs, errs[1:]))
     assert errs[-1] < errs[0] / 4
+
+
+def test_min_taps_partition():
+    # heavy-tailed w (most rows near 0, long tails): the minimum-taps partition never holds more
+    # taps than one stack at 0 and beats equal-count bins
+    rng = _rng(12)
+    w = rng.standard_t(2, 20000) * 300.0
+    qs = synth.j_per_row_by_w_quartile(w).astype(np.int64)
+    for P in (2, 3, 4, 8):
+        stack, cen = synth.w_stacks_min_taps(w, P)
+        assert stack.min() >= 0 and stack.max() < P and cen.size == P
+        assert np.all(np.diff(cen) >= 0)
+        for s in range(P):                                   # contiguous in w
+            if s and (stack == s).any() and (stack == s - 1).any():
+                assert w[stack == s].min() >= w[stack == s - 1].max()
+        J = synth.j_per_row_stacked(w, stack, cen, w).astype(np.int64)
+        assert (J ** 2).sum() <= (qs ** 2).sum()
+        se, ce = synth.w_stacks(w, P)
+        Je = synth.j_per_row_stacked(w, se, ce, w).astype(np.int64)
+        assert (J ** 2).sum() <= (Je ** 2).sum()
+
+
+def test_forward_rows_equals_the_operator_rows():
+    n, K, M = 16, 32, 200
+    omega, w, dl = _problem(n, K, M, seed=13)
+    stack, cen = synth.w_stacks(w, 3)
+    Jr = synth.j_per_row_stacked(w, stack, cen, w)
+    x = _rng(14).random((n, n))
+    rows = np.sort(_rng(15).choice(M, 40, replace=False))
+    from oracle.wstack import forward_rows
+    y_rows = forward_rows(n, K, omega, w, dl, stack, cen, Jr, x, rows)
+    assert np.allclose(y_rows, StackedOperator(n, K, omega, w, dl, stack, cen, Jr).forward(x)[rows],
+                       rtol=0, atol=1e-12 * np.abs(y_rows).max())
