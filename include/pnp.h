@@ -274,6 +274,20 @@ int pnp_cnn_trainer_read(pnp_cnn_trainer* trainer, float* weights_host, float* g
  * moment estimates and the step count are kept. */
 int pnp_cnn_trainer_set_lr(pnp_cnn_trainer* trainer, double lr);
 
+/* Spectral norm of the Jacobian of Q = 2D - I, D(z) = z - N(z), at each image of a batch: the
+ * quantity the firm non-expansiveness constraint of Eq. training_loss (App. C) bounds by 1.
+ * Runs `iters` power iterations on J_Q^T J_Q with J_Q = I - 2 J_N, J_N the network with its
+ * ReLU masks at z frozen (Jacobian-vector products on the tensor cores, BF16 tangents and
+ * gradients as in training), independently per image.
+ *  z          device, batch x size x size float32 inputs (the trainer's batch geometry)
+ *  v0         device, batch x size x size float32 start vectors (normalised per image)
+ *  iters      >= 1
+ *  sigma_host host, batch float64: ||J_Q v|| for the last unit iterate v (the estimate)
+ *  v_out      device, batch x size x size float32 or NULL: the last iterate, normalised
+ * Overwrites the trainer's activations and gradient canvases; synchronous. */
+int pnp_cnn_jacobian_norm(pnp_cnn_trainer* trainer, const float* z, const float* v0, int iters,
+                          double* sigma_host, float* v_out);
+
 /* Number of FP32 parameters of the CNN (weights and biases of the 8 layers). */
 int64_t pnp_cnn_num_params(void);
 

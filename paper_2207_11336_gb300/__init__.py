@@ -31,7 +31,7 @@ EXPORTED = [
     "pnp_last_error", "pnp_kernel_launch_count", "pnp_plan_set_timing", "pnp_plan_read_timing",
     "pnp_plan_device_status", "pnp_haar_denoise_noalloc", "pnp_den_device_status",
     "pnp_cnn_trainer_create", "pnp_cnn_trainer_destroy", "pnp_cnn_train_step", "pnp_cnn_trainer_read",
-    "pnp_cnn_num_params", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune",
+    "pnp_cnn_num_params", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm",
 ]
 
 
@@ -102,6 +102,7 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_cnn_trainer_read.argtypes = [vp, vp, vp, i32]
     L.pnp_cnn_num_params.restype = i64
     L.pnp_cnn_trainer_set_lr.argtypes = [vp, dbl]
+    L.pnp_cnn_jacobian_norm.argtypes = [vp, vp, vp, i32, vp, vp]
     L.pnp_plan_read_timing.argtypes = [vp, vp, vp]
     L.pnp_last_error.restype = C.c_char_p
     L.pnp_kernel_launch_count.restype = i64
@@ -111,7 +112,7 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
                  "pnp_den_create_cnn", "denoise", "pnp_fb_run", "pnp_plan_set_timing",
                  "pnp_plan_read_timing", "pnp_plan_device_status", "pnp_haar_denoise_noalloc",
                  "pnp_den_device_status", "pnp_cnn_trainer_create", "pnp_cnn_train_step",
-                 "pnp_cnn_trainer_read", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune"):
+                 "pnp_cnn_trainer_read", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -409,6 +410,18 @@ class CnnTrainer:
     def set_lr(self, lr: float):
         """Adam step size for the following steps (moments are kept)."""
         _check(lib().pnp_cnn_trainer_set_lr(self._h, float(lr)))
+
+    def jacobian_norm(self, z, v0, iters: int = 20):
+        """(sigma per image, last unit iterate): ||grad (2D - I)(z)||_S by power iteration, the
+        quantity the firm non-expansiveness constraint of Eq. training_loss bounds by 1."""
+        import torch
+        shape = (self.batch, self.size, self.size)
+        _cuda_f32(z, shape, "z")
+        _cuda_f32(v0, shape, "v0")
+        sig = np.zeros(self.batch, dtype=np.float64)
+        v = torch.empty(shape, dtype=torch.float32, device=z.device)
+        _check(lib().pnp_cnn_jacobian_norm(self._h, _ptr(z), _ptr(v0), int(iters), sig.ctypes.data, _ptr(v)))
+        return sig, v
 
     def read(self, weights=True, grads=False, clear_grads=False):
         """(params or None, flat gradients or None) from the device."""

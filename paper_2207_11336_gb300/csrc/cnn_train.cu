@@ -242,6 +242,128 @@ __global__ void __launch_bounds__(256) wgrad64(Dims d, const __nv_bfloat16* __re
   if (t == 4 && threadIdx.x < CH) atomicAdd(&db[threadIdx.x], bsum);
 }
 
+// ---------------------------------------------------------------- Jacobian of Q = 2D - I
+// With D(z) = z - N(z), J_Q = I - 2 J_N, and J_N at z is the network with its ReLU masks at z
+// frozen and no biases.  Layers 2-7 of J_N v run on the tensor cores (conv64 backward-data mode
+// with the forward weights and the masks [act_{k+1} > 0]); J_N^T w is the back-propagation of
+// the training step.  These kernels are the one-channel ends of both chains.
+
+// t1[p][c] = [act1[p][c] > 0] * sum_t W1[c][t] v[p + off_t]
+__global__ void __launch_bounds__(256) tangent_first(Dims d, const float* __restrict__ v,
+                                                     const float* __restrict__ w1r,
+                                                     const __nv_bfloat16* __restrict__ act1,
+                                                     __nv_bfloat16* __restrict__ t1) {
+  __shared__ float sw[9 * CH];
+  for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = w1r[i];
+  __syncthreads();
+  const int64_t total = (int64_t)d.B * d.s * d.s;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(p / ((int64_t)d.s * d.s)), y = (int)((p / d.s) % d.s), x = (int)(p % d.s);
+    float vt[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+      vt[t] = (yy >= 0 && yy < d.s && xx >= 0 && xx < d.s) ? v[((int64_t)b * d.s + yy) * d.s + xx] : 0.f;
+    }
+#pragma unroll 4
+    for (int c = 0; c < CH / 2; ++c) {
+      const size_t at = cidx(d, b, y, x, 2 * c);
+      float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        v0 = fmaf(sw[(2 * c) * 9 + t], vt[t], v0);
+        v1 = fmaf(sw[(2 * c + 1) * 9 + t], vt[t], v1);
+      }
+      const float2 av = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(act1 + at));
+      *reinterpret_cast<__nv_bfloat162*>(t1 + at) = __floats2bfloat162_rn(av.x > 0.f ? v0 : 0.f, av.y > 0.f ? v1 : 0.f);
+    }
+  }
+}
+
+// w[p] = v[p] - 2 sum_{t, c} W8[c][t] t7[p + off_t][c]   (J_Q v from the layer-7 tangent)
+__global__ void __launch_bounds__(256) tangent_last(Dims d, const __nv_bfloat16* __restrict__ t7,
+                                                    const float* __restrict__ w8r, const float* __restrict__ v,
+                                                    float* __restrict__ w) {
+  __shared__ float sw[9 * CH];
+  for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[i] = w8r[i];
+  __syncthreads();
+  const int64_t total = (int64_t)d.B * d.s * d.s;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(p / ((int64_t)d.s * d.s)), y = (int)((p / d.s) % d.s), x = (int)(p % d.s);
+    float jn = 0.f;
+    for (int t = 0; t < 9; ++t) {
+      const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+      if (yy < 0 || yy >= d.s || xx < 0 || xx >= d.s) continue;
+#pragma unroll
+      for (int cb = 0; cb < 8; ++cb) {
+        const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(t7 + cidx(d, b, yy, xx, 8 * cb));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = 4 * cb + k;
+          const float2 tv = __bfloat1622float2(a[k]);
+          jn = fmaf(sw[t * CH + 2 * c], tv.x, fmaf(sw[t * CH + 2 * c + 1], tv.y, jn));
+        }
+      }
+    }
+    w[p] = v[p] - 2.f * jn;
+  }
+}
+
+// u[p] = w[p] - 2 sum_{t, c} W1[c][t] dpre1[p - off_t][c]   (J_Q^T w from the layer-1 gradient)
+__global__ void __launch_bounds__(256) cotangent_first(Dims d, const __nv_bfloat16* __restrict__ dpre1,
+                                                       const float* __restrict__ w1r, const float* __restrict__ w,
+                                                       float* __restrict__ u) {
+  __shared__ float sw[9 * CH];  // [t][c]
+  for (int i = threadIdx.x; i < 9 * CH; i += blockDim.x) sw[(i % 9) * CH + i / 9] = w1r[i];
+  __syncthreads();
+  const int64_t total = (int64_t)d.B * d.s * d.s;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(p / ((int64_t)d.s * d.s)), y = (int)((p / d.s) % d.s), x = (int)(p % d.s);
+    float jt = 0.f;
+    for (int t = 0; t < 9; ++t) {
+      const int yy = y - (t / 3 - 1), xx = x - (t % 3 - 1);
+      if (yy < 0 || yy >= d.s || xx < 0 || xx >= d.s) continue;
+#pragma unroll
+      for (int cb = 0; cb < 8; ++cb) {
+        const __nv_bfloat162* a = reinterpret_cast<const __nv_bfloat162*>(dpre1 + cidx(d, b, yy, xx, 8 * cb));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int c = 4 * cb + k;
+          const float2 gv = __bfloat1622float2(a[k]);
+          jt = fmaf(sw[t * CH + 2 * c], gv.x, fmaf(sw[t * CH + 2 * c + 1], gv.y, jt));
+        }
+      }
+    }
+    u[p] = w[p] - 2.f * jt;
+  }
+}
+
+// n2[b] += sum_p x[b][p]^2 (FP64); grid (blocks per image, B)
+__global__ void __launch_bounds__(256) image_norm2(const float* __restrict__ x, int64_t plane, double* n2) {
+  __shared__ double red[256];
+  const float* xb = x + (int64_t)blockIdx.y * plane;
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < plane; i += (int64_t)gridDim.x * blockDim.x)
+    s += (double)xb[i] * xb[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x >> 1; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(&n2[blockIdx.y], red[0]);
+}
+
+// v[b][p] = u[b][p] / sqrt(n2[b]) (a zero image stays zero)
+__global__ void __launch_bounds__(256) image_unit(const float* __restrict__ u, const double* __restrict__ n2,
+                                                  int64_t plane, int B, float* __restrict__ v) {
+  const int64_t total = plane * B;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const double n = n2[i / plane];
+    v[i] = n > 0.0 ? (float)(u[i] / sqrt(n)) : 0.f;
+  }
+}
+
 // Adam (Kingma & Ba 2015) on the master weights; the gradient is cleared for the next step.
 __global__ void adam_step(float* __restrict__ w, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
                           int64_t count, float lr, float b1, float b2, float eps, float c1, float c2) {
@@ -285,6 +407,8 @@ struct pnp_cnn_trainer {
   int4 *facets = nullptr, *strips = nullptr;
   double* loss = nullptr;
   int* status = nullptr;
+  float *jv = nullptr, *jw = nullptr, *ju = nullptr;  // Jacobian power iteration images (B x s x s)
+  double* jn2 = nullptr;                                // their per-image squared norms [B]
   alignas(64) unsigned char map_act[8][256];  // TMA descriptors (main, halo) of act[1..7]
   alignas(64) unsigned char map_dp[2][256];   // and of the two gradient canvases
 };
@@ -296,7 +420,7 @@ void trainer_free(pnp_cnn_trainer* T) {
   if (!T) return;
   for (void* p : {(void*)T->w, (void*)T->g, (void*)T->m, (void*)T->v, (void*)T->w1r, (void*)T->w8r, (void*)T->bias,
                   (void*)T->wf, (void*)T->wb, (void*)T->z, (void*)T->gout, (void*)T->facets, (void*)T->strips,
-                  (void*)T->loss, (void*)T->status})
+                  (void*)T->loss, (void*)T->status, (void*)T->jv, (void*)T->jw, (void*)T->ju, (void*)T->jn2})
     cudaFree(p);
   for (auto p : T->act) cudaFree(p);
   for (auto p : T->dp) cudaFree(p);
@@ -305,6 +429,18 @@ void trainer_free(pnp_cnn_trainer* T) {
 
 int prep(pnp_cnn_trainer* T) {
   prep_weights<<<nblocks(6 * (int64_t)NWM), 256, 0, T->stream>>>(T->w, T->w1r, T->w8r, T->bias, T->wf, T->wb);
+  PNP_CHECK_LAUNCH();
+  return PNP_OK;
+}
+}  // namespace
+
+namespace {
+// per-image squared norms of x into T->jn2
+int image_norms(pnp_cnn_trainer* T, const float* x) {
+  const int64_t plane = (int64_t)T->d.s * T->d.s;
+  PNP_CUDA(cudaMemsetAsync(T->jn2, 0, T->d.B * sizeof(double), T->stream));
+  const int bx = (int)std::min<int64_t>((plane + 255) / 256, 64);
+  image_norm2<<<dim3(bx, T->d.B), 256, 0, T->stream>>>(x, plane, T->jn2);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
@@ -334,7 +470,8 @@ int pnp_cnn_trainer_create(pnp_cnn_trainer** out, const float* weights_host, int
             al((void**)&T->bias, 8 * CH * 4) && al((void**)&T->wf, 6 * (size_t)NWM * 2) &&
             al((void**)&T->wb, 6 * (size_t)NWM * 2) && al((void**)&T->z, npx * 4) && al((void**)&T->gout, npx * 4) &&
             al((void**)&T->facets, batch * sizeof(int4)) && al((void**)&T->loss, sizeof(double)) &&
-            al((void**)&T->status, 4 * sizeof(int));
+            al((void**)&T->status, 4 * sizeof(int)) && al((void**)&T->jv, npx * 4) && al((void**)&T->jw, npx * 4) &&
+            al((void**)&T->ju, npx * 4) && al((void**)&T->jn2, batch * sizeof(double));
   for (int i = 1; ok && i <= 7; ++i) ok = al((void**)&T->act[i], canvas * 2);
   for (int i = 0; ok && i < 2; ++i) ok = al((void**)&T->dp[i], canvas * 2);
   std::vector<int4> facets(batch, make_int4(0, 0, size, size));
@@ -434,6 +571,61 @@ int pnp_cnn_train_step(pnp_cnn_trainer* T, const float* u, const float* noise, d
     PNP_CUDA(cudaMemcpyAsync(loss_host, T->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
     PNP_CUDA(cudaStreamSynchronize(s));
   }
+  return PNP_OK;
+}
+
+int pnp_cnn_jacobian_norm(pnp_cnn_trainer* T, const float* z, const float* v0, int iters, double* sigma_host,
+                          float* v_out) {
+  if (!T || !z || !v0 || iters < 1 || iters > 100000 || !sigma_host) return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  const Dims d = T->d;
+  const int64_t plane = (int64_t)d.s * d.s, npx = plane * d.B;
+  cudaStream_t s = T->stream;
+  // the primal pass at z fixes the ReLU masks
+  if (int rc = cnn_first_launch(s, z, d.s, plane, T->facets, d.B, d.Hc, d.Wc, T->w1r, T->bias, T->act[1])) return rc;
+  for (int k = 1; k <= 6; ++k)
+    if (int rc = conv64_launch(s, T->map_act[k], T->act[k + 1], T->wf + (size_t)(k - 1) * NWM, T->bias + k * CH,
+                               T->strips, T->n_strips, d.Hc, d.Wc, 0, nullptr, T->status))
+      return rc;
+  if (int rc = image_norms(T, v0)) return rc;
+  image_unit<<<nblocks(npx), 256, 0, s>>>(v0, T->jn2, plane, d.B, T->jv);
+  PNP_CHECK_LAUNCH();
+  for (int it = 0; it < iters; ++it) {
+    // w = J_Q v: tangents through layers 1..7 (masks [act_k > 0]), then layer 8
+    tangent_first<<<nblocks(npx), 256, 0, s>>>(d, T->jv, T->w1r, T->act[1], T->dp[0]);
+    PNP_CHECK_LAUNCH();
+    int cur = 0;
+    for (int k = 1; k <= 6; ++k) {
+      if (int rc = conv64_launch(s, T->map_dp[cur], T->dp[1 - cur], T->wf + (size_t)(k - 1) * NWM, nullptr, T->strips,
+                                 T->n_strips, d.Hc, d.Wc, 1, T->act[k + 1], T->status))
+        return rc;
+      cur = 1 - cur;
+    }
+    tangent_last<<<nblocks(npx), 256, 0, s>>>(d, T->dp[cur], T->w8r, T->jv, T->jw);
+    PNP_CHECK_LAUNCH();
+    // u = J_Q^T w: the training step's back-propagation with cotangent w
+    last_bwd<<<nblocks(npx), 256, 0, s>>>(d, T->act[7], T->w8r, T->jw, T->dp[0]);
+    PNP_CHECK_LAUNCH();
+    cur = 0;
+    for (int k = 6; k >= 1; --k) {
+      if (int rc = conv64_launch(s, T->map_dp[cur], T->dp[1 - cur], T->wb + (size_t)(k - 1) * NWM, nullptr, T->strips,
+                                 T->n_strips, d.Hc, d.Wc, 1, T->act[k], T->status))
+        return rc;
+      cur = 1 - cur;
+    }
+    cotangent_first<<<nblocks(npx), 256, 0, s>>>(d, T->dp[cur], T->w1r, T->jw, T->ju);
+    PNP_CHECK_LAUNCH();
+    if (it == iters - 1) {  // sigma = ||J_Q v|| for the current unit v
+      if (int rc = image_norms(T, T->jw)) return rc;
+      PNP_CUDA(cudaMemcpyAsync(sigma_host, T->jn2, d.B * sizeof(double), cudaMemcpyDeviceToHost, s));
+      PNP_CUDA(cudaStreamSynchronize(s));
+      for (int b = 0; b < d.B; ++b) sigma_host[b] = std::sqrt(sigma_host[b]);
+    }
+    if (int rc = image_norms(T, T->ju)) return rc;
+    image_unit<<<nblocks(npx), 256, 0, s>>>(T->ju, T->jn2, plane, d.B, T->jv);
+    PNP_CHECK_LAUNCH();
+  }
+  if (v_out) PNP_CUDA(cudaMemcpyAsync(v_out, T->jv, npx * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  PNP_CUDA(cudaStreamSynchronize(s));
   return PNP_OK;
 }
 
