@@ -288,6 +288,20 @@ int pnp_cnn_trainer_set_lr(pnp_cnn_trainer* trainer, double lr);
 int pnp_cnn_jacobian_norm(pnp_cnn_trainer* trainer, const float* z, const float* v0, int iters,
                           double* sigma_host, float* v_out);
 
+/* One training step with the soft firm non-expansiveness penalty of Eq. training_loss (App. C,
+ * the constraint relaxed to a penalty as the paper describes): the l1 loss of
+ * pnp_cnn_train_step plus
+ *   P = lambda / batch * sum_b max(||J_Q(z_b) v_b||^2, 1 - eps),   z = u + sigma n,
+ * with v_b the unit vector after `iters` power iterations on J_Q^T J_Q at z_b from v0 (iters = 0:
+ * v0 normalised), held fixed; P's weight gradients come from back-propagating -4 lambda/batch
+ * J_Q v through the frozen-mask network (biases get none).  Arguments as pnp_cnn_train_step, plus
+ *  v0           device, batch x size x size float32 start vectors
+ *  iters        >= 0;  lambda >= 0;  eps in [0, 1]
+ *  penalty_host host float64 or NULL: P (synchronous when given) */
+int pnp_cnn_train_step_fne(pnp_cnn_trainer* trainer, const float* u, const float* noise, double sigma,
+                           const float* v0, int iters, double lambda, double eps, int update,
+                           double* loss_host, double* penalty_host);
+
 /* Number of FP32 parameters of the CNN (weights and biases of the 8 layers). */
 int64_t pnp_cnn_num_params(void);
 

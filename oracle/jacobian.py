@@ -76,3 +76,51 @@ def q_jacobian_norm(params, z, v0, iters: int, bf16: bool = False):
         sigma = float(np.linalg.norm(w))
         v = u / np.linalg.norm(u)
     return sigma, v
+
+
+def fne_penalty_and_grads(params, z, v, lam: float, eps: float, bf16: bool = False):
+    """Soft firm non-expansiveness penalty and its weight gradients (Eq. training_loss relaxed).
+
+    For a batch z (B, H, W) and unit vectors v (B, H, W) from the power iteration, held fixed:
+        P = lam / B * sum_b max(||J_Q(z_b) v_b||^2, 1 - eps),   J_Q = I - 2 J_N.
+    J_N v is the frozen-mask network without biases applied to v, so d||J_Q v||^2 / dW is the
+    back-propagation of the cotangent -4 (J_Q v) through that tangent network (layer inputs: the
+    tangents, layer 1's input: v).  The biases get no gradient (they enter only through the
+    masks, which are locally constant), nor does an image whose ||J_Q v||^2 <= 1 - eps.
+    Returns (P, [(dW, db)] per layer, [||J_Q v_b||^2 per image]).
+    """
+    z = np.asarray(z, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    B = z.shape[0]
+    last = len(params) - 1
+    grads = [(np.zeros_like(W), np.zeros_like(b)) for W, b in params]
+    P, n2s = 0.0, []
+    for bi in range(B):
+        acts = _acts(params, z[bi], bf16)
+        ts = [v[bi][None, None]]
+        for i, (Wt, b) in enumerate(params):
+            Wq = to_bf16(Wt) if bf16 else Wt
+            t = conv_forward(ts[-1], Wq, np.zeros_like(b))
+            if i < last:
+                t = t * (acts[i + 1] > 0)
+                if bf16:
+                    t = to_bf16(t)
+            ts.append(t)
+        w = v[bi] - 2.0 * ts[-1][0, 0]
+        n2 = float(np.sum(w * w))
+        n2s.append(n2)
+        P += lam / B * max(n2, 1.0 - eps)
+        if n2 <= 1.0 - eps:
+            continue
+        g = (-4.0 * lam / B * w)[None, None]
+        for i in range(last, -1, -1):
+            Wt, _ = params[i]
+            if i < last:
+                g = g * (acts[i + 1] > 0)
+                if bf16:
+                    g = to_bf16(g)
+            Wq = to_bf16(Wt) if bf16 else Wt
+            dx, dW, _ = conv_backward(ts[i], Wq, g)
+            grads[i] = (grads[i][0] + dW, grads[i][1])
+            g = dx
+    return P, grads, n2s

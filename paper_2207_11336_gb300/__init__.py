@@ -32,6 +32,7 @@ EXPORTED = [
     "pnp_plan_device_status", "pnp_haar_denoise_noalloc", "pnp_den_device_status",
     "pnp_cnn_trainer_create", "pnp_cnn_trainer_destroy", "pnp_cnn_train_step", "pnp_cnn_trainer_read",
     "pnp_cnn_num_params", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm",
+    "pnp_cnn_train_step_fne",
 ]
 
 
@@ -103,6 +104,7 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_cnn_num_params.restype = i64
     L.pnp_cnn_trainer_set_lr.argtypes = [vp, dbl]
     L.pnp_cnn_jacobian_norm.argtypes = [vp, vp, vp, i32, vp, vp]
+    L.pnp_cnn_train_step_fne.argtypes = [vp, vp, vp, dbl, vp, i32, dbl, dbl, i32, C.POINTER(dbl), C.POINTER(dbl)]
     L.pnp_plan_read_timing.argtypes = [vp, vp, vp]
     L.pnp_last_error.restype = C.c_char_p
     L.pnp_kernel_launch_count.restype = i64
@@ -112,7 +114,8 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
                  "pnp_den_create_cnn", "denoise", "pnp_fb_run", "pnp_plan_set_timing",
                  "pnp_plan_read_timing", "pnp_plan_device_status", "pnp_haar_denoise_noalloc",
                  "pnp_den_device_status", "pnp_cnn_trainer_create", "pnp_cnn_train_step",
-                 "pnp_cnn_trainer_read", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm"):
+                 "pnp_cnn_trainer_read", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm",
+                 "pnp_cnn_train_step_fne"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -410,6 +413,22 @@ class CnnTrainer:
     def set_lr(self, lr: float):
         """Adam step size for the following steps (moments are kept)."""
         _check(lib().pnp_cnn_trainer_set_lr(self._h, float(lr)))
+
+    def step_fne(self, u, noise, sigma: float, v0, iters: int, lam: float, eps: float = 0.0,
+                 update: bool = True, want_values: bool = False):
+        """One training step with the soft firm non-expansiveness penalty (Eq. training_loss):
+        l1 loss + lam/B sum_b max(||J_Q v_b||^2, 1 - eps), v_b from ``iters`` power iterations
+        from v0.  Returns (loss, penalty) when ``want_values``."""
+        shape = (self.batch, self.size, self.size)
+        _cuda_f32(u, shape, "u")
+        _cuda_f32(noise, shape, "noise")
+        _cuda_f32(v0, shape, "v0")
+        loss, pen = C.c_double(0.0), C.c_double(0.0)
+        _check(lib().pnp_cnn_train_step_fne(self._h, _ptr(u), _ptr(noise), float(sigma), _ptr(v0), int(iters),
+                                            float(lam), float(eps), 1 if update else 0,
+                                            C.byref(loss) if want_values else None,
+                                            C.byref(pen) if want_values else None))
+        return (loss.value, pen.value) if want_values else None
 
     def jacobian_norm(self, z, v0, iters: int = 20):
         """(sigma per image, last unit iterate): ||grad (2D - I)(z)||_S by power iteration, the

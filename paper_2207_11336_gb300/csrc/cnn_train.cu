@@ -364,6 +364,16 @@ __global__ void __launch_bounds__(256) image_unit(const float* __restrict__ u, c
   }
 }
 
+// Cotangent of the soft firm non-expansiveness penalty lam/B sum_b max(||w_b||^2, 1 - eps) with
+// w = J_Q v: c[b][p] = -4 lam/B w[b][p] where ||w_b||^2 > 1 - eps, else 0.
+__global__ void __launch_bounds__(256) fne_cotangent(const float* __restrict__ w, const double* __restrict__ n2,
+                                                     int64_t plane, int B, float scale, double floor_,
+                                                     float* __restrict__ c) {
+  const int64_t total = plane * B;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    c[i] = n2[i / plane] > floor_ ? -4.f * scale * w[i] : 0.f;
+}
+
 // Adam (Kingma & Ba 2015) on the master weights; the gradient is cleared for the next step.
 __global__ void adam_step(float* __restrict__ w, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
                           int64_t count, float lr, float b1, float b2, float eps, float c1, float c2) {
@@ -409,6 +419,9 @@ struct pnp_cnn_trainer {
   int* status = nullptr;
   float *jv = nullptr, *jw = nullptr, *ju = nullptr;  // Jacobian power iteration images (B x s x s)
   double* jn2 = nullptr;                                // their per-image squared norms [B]
+  __nv_bfloat16* tan[8] = {};                           // tangents t_1..t_7 of the penalty's J_N v
+  float* junk = nullptr;                                // bias-gradient sink of the tangent network [64]
+  alignas(64) unsigned char map_tan[8][256];            // TMA descriptors of tan[1..6]
   alignas(64) unsigned char map_act[8][256];  // TMA descriptors (main, halo) of act[1..7]
   alignas(64) unsigned char map_dp[2][256];   // and of the two gradient canvases
 };
@@ -424,6 +437,8 @@ void trainer_free(pnp_cnn_trainer* T) {
     cudaFree(p);
   for (auto p : T->act) cudaFree(p);
   for (auto p : T->dp) cudaFree(p);
+  for (auto p : T->tan) cudaFree(p);
+  cudaFree(T->junk);
   delete T;
 }
 
@@ -443,6 +458,79 @@ int image_norms(pnp_cnn_trainer* T, const float* x) {
   image_norm2<<<dim3(bx, T->d.B), 256, 0, T->stream>>>(x, plane, T->jn2);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
+}
+}  // namespace
+
+namespace {
+// the forward pass at z that fixes the ReLU masks (activations act[1..7])
+int primal_forward(pnp_cnn_trainer* T, const float* z) {
+  const Dims d = T->d;
+  cudaStream_t s = T->stream;
+  if (int rc = cnn_first_launch(s, z, d.s, (int64_t)d.s * d.s, T->facets, d.B, d.Hc, d.Wc, T->w1r, T->bias,
+                                T->act[1]))
+    return rc;
+  for (int k = 1; k <= 6; ++k)
+    if (int rc = conv64_launch(s, T->map_act[k], T->act[k + 1], T->wf + (size_t)(k - 1) * NWM, T->bias + k * CH,
+                               T->strips, T->n_strips, d.Hc, d.Wc, 0, nullptr, T->status))
+      return rc;
+  return PNP_OK;
+}
+
+// Power iteration on J_Q^T J_Q at the current activations from v0 (normalised per image):
+// T->jv ends as the last unit iterate; sigma_host (if given) gets ||J_Q v|| of the last step.
+int power_iterate(pnp_cnn_trainer* T, const float* v0, int iters, double* sigma_host) {
+  const Dims d = T->d;
+  const int64_t plane = (int64_t)d.s * d.s, npx = plane * d.B;
+  cudaStream_t s = T->stream;
+  if (int rc = image_norms(T, v0)) return rc;
+  image_unit<<<nblocks(npx), 256, 0, s>>>(v0, T->jn2, plane, d.B, T->jv);
+  PNP_CHECK_LAUNCH();
+  for (int it = 0; it < iters; ++it) {
+    // w = J_Q v: tangents through layers 1..7 (masks [act_k > 0]), then layer 8
+    tangent_first<<<nblocks(npx), 256, 0, s>>>(d, T->jv, T->w1r, T->act[1], T->dp[0]);
+    PNP_CHECK_LAUNCH();
+    int cur = 0;
+    for (int k = 1; k <= 6; ++k) {
+      if (int rc = conv64_launch(s, T->map_dp[cur], T->dp[1 - cur], T->wf + (size_t)(k - 1) * NWM, nullptr, T->strips,
+                                 T->n_strips, d.Hc, d.Wc, 1, T->act[k + 1], T->status))
+        return rc;
+      cur = 1 - cur;
+    }
+    tangent_last<<<nblocks(npx), 256, 0, s>>>(d, T->dp[cur], T->w8r, T->jv, T->jw);
+    PNP_CHECK_LAUNCH();
+    // u = J_Q^T w: the training step's back-propagation with cotangent w
+    last_bwd<<<nblocks(npx), 256, 0, s>>>(d, T->act[7], T->w8r, T->jw, T->dp[0]);
+    PNP_CHECK_LAUNCH();
+    cur = 0;
+    for (int k = 6; k >= 1; --k) {
+      if (int rc = conv64_launch(s, T->map_dp[cur], T->dp[1 - cur], T->wb + (size_t)(k - 1) * NWM, nullptr, T->strips,
+                                 T->n_strips, d.Hc, d.Wc, 1, T->act[k], T->status))
+        return rc;
+      cur = 1 - cur;
+    }
+    cotangent_first<<<nblocks(npx), 256, 0, s>>>(d, T->dp[cur], T->w1r, T->jw, T->ju);
+    PNP_CHECK_LAUNCH();
+    if (sigma_host && it == iters - 1) {  // sigma = ||J_Q v|| for the current unit v
+      if (int rc = image_norms(T, T->jw)) return rc;
+      PNP_CUDA(cudaMemcpyAsync(sigma_host, T->jn2, d.B * sizeof(double), cudaMemcpyDeviceToHost, s));
+      PNP_CUDA(cudaStreamSynchronize(s));
+      for (int b = 0; b < d.B; ++b) sigma_host[b] = std::sqrt(sigma_host[b]);
+    }
+    if (int rc = image_norms(T, T->ju)) return rc;
+    image_unit<<<nblocks(npx), 256, 0, s>>>(T->ju, T->jn2, plane, d.B, T->jv);
+    PNP_CHECK_LAUNCH();
+  }
+  return PNP_OK;
+}
+
+// Adam on the accumulated gradients, then the BF16 operands are re-packed
+int adam_update(pnp_cnn_trainer* T) {
+  T->t += 1;
+  const float c1 = (float)(1.0 - std::pow(T->b1, T->t)), c2 = (float)(1.0 - std::pow(T->b2, T->t));
+  adam_step<<<nblocks(NPARAM), 256, 0, T->stream>>>(T->w, T->g, T->m, T->v, NPARAM, (float)T->lr, (float)T->b1,
+                                                    (float)T->b2, (float)T->eps, c1, c2);
+  PNP_CHECK_LAUNCH();
+  return prep(T);
 }
 }  // namespace
 
@@ -471,9 +559,11 @@ int pnp_cnn_trainer_create(pnp_cnn_trainer** out, const float* weights_host, int
             al((void**)&T->wb, 6 * (size_t)NWM * 2) && al((void**)&T->z, npx * 4) && al((void**)&T->gout, npx * 4) &&
             al((void**)&T->facets, batch * sizeof(int4)) && al((void**)&T->loss, sizeof(double)) &&
             al((void**)&T->status, 4 * sizeof(int)) && al((void**)&T->jv, npx * 4) && al((void**)&T->jw, npx * 4) &&
-            al((void**)&T->ju, npx * 4) && al((void**)&T->jn2, batch * sizeof(double));
+            al((void**)&T->ju, npx * 4) && al((void**)&T->jn2, batch * sizeof(double)) &&
+            al((void**)&T->junk, CH * sizeof(float));
   for (int i = 1; ok && i <= 7; ++i) ok = al((void**)&T->act[i], canvas * 2);
   for (int i = 0; ok && i < 2; ++i) ok = al((void**)&T->dp[i], canvas * 2);
+  for (int i = 1; ok && i <= 7; ++i) ok = al((void**)&T->tan[i], canvas * 2);
   std::vector<int4> facets(batch, make_int4(0, 0, size, size));
   const std::vector<int> sides(batch, size);
   const std::vector<int4> strips = conv_strips(batch, sides.data(), sides.data());
@@ -490,6 +580,7 @@ int pnp_cnn_trainer_create(pnp_cnn_trainer** out, const float* weights_host, int
   if (e == cudaSuccess) e = cudaMemset(T->status, 0, 4 * sizeof(int));
   for (int i = 1; e == cudaSuccess && i <= 7; ++i) e = cudaMemset(T->act[i], 0, canvas * 2);
   for (int i = 0; e == cudaSuccess && i < 2; ++i) e = cudaMemset(T->dp[i], 0, canvas * 2);
+  for (int i = 1; e == cudaSuccess && i <= 7; ++i) e = cudaMemset(T->tan[i], 0, canvas * 2);
   if (e == cudaSuccess) e = cudaMemcpy(T->facets, facets.data(), batch * sizeof(int4), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(T->strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice);
@@ -505,6 +596,11 @@ int pnp_cnn_trainer_create(pnp_cnn_trainer** out, const float* weights_host, int
     }
   for (int i = 0; i < 2; ++i)
     if (int rc = canvas_map_create(T->map_dp[i], T->dp[i], batch, T->d.Hc, T->d.Wc)) {
+      trainer_free(T);
+      return rc;
+    }
+  for (int i = 1; i <= 6; ++i)
+    if (int rc = canvas_map_create(T->map_tan[i], T->tan[i], batch, T->d.Hc, T->d.Wc)) {
       trainer_free(T);
       return rc;
     }
@@ -559,14 +655,8 @@ int pnp_cnn_train_step(pnp_cnn_trainer* T, const float* u, const float* noise, d
   wgrad_onechannel<<<wgb, 576, 0, s>>>(d, 1, T->z, T->dp[cur], T->g + OFF_W1, T->g + OFF_B1);
   PNP_CHECK_LAUNCH();
   // ---------------- update
-  if (update) {
-    T->t += 1;
-    const float c1 = (float)(1.0 - std::pow(T->b1, T->t)), c2 = (float)(1.0 - std::pow(T->b2, T->t));
-    adam_step<<<nblocks(NPARAM), 256, 0, s>>>(T->w, T->g, T->m, T->v, NPARAM, (float)T->lr, (float)T->b1,
-                                              (float)T->b2, (float)T->eps, c1, c2);
-    PNP_CHECK_LAUNCH();
-    if (int rc = prep(T)) return rc;
-  }
+  if (update)
+    if (int rc = adam_update(T)) return rc;
   if (loss_host) {
     PNP_CUDA(cudaMemcpyAsync(loss_host, T->loss, sizeof(double), cudaMemcpyDeviceToHost, s));
     PNP_CUDA(cudaStreamSynchronize(s));
@@ -578,54 +668,71 @@ int pnp_cnn_jacobian_norm(pnp_cnn_trainer* T, const float* z, const float* v0, i
                           float* v_out) {
   if (!T || !z || !v0 || iters < 1 || iters > 100000 || !sigma_host) return fail(PNP_ERR_INVALID_ARG, "bad argument");
   const Dims d = T->d;
+  const int64_t npx = (int64_t)d.s * d.s * d.B;
+  if (int rc = primal_forward(T, z)) return rc;  // fixes the ReLU masks
+  if (int rc = power_iterate(T, v0, iters, sigma_host)) return rc;
+  if (v_out) PNP_CUDA(cudaMemcpyAsync(v_out, T->jv, npx * sizeof(float), cudaMemcpyDeviceToDevice, T->stream));
+  PNP_CUDA(cudaStreamSynchronize(T->stream));
+  return PNP_OK;
+}
+
+int pnp_cnn_train_step_fne(pnp_cnn_trainer* T, const float* u, const float* noise, double sigma, const float* v0,
+                           int iters, double lambda, double eps, int update, double* loss_host,
+                           double* penalty_host) {
+  if (!T || !u || !noise || !v0 || !(sigma >= 0) || iters < 0 || iters > 100000 || !(lambda >= 0) ||
+      !std::isfinite(lambda) || !(eps >= 0) || !(eps <= 1))
+    return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  const Dims d = T->d;
   const int64_t plane = (int64_t)d.s * d.s, npx = plane * d.B;
   cudaStream_t s = T->stream;
-  // the primal pass at z fixes the ReLU masks
-  if (int rc = cnn_first_launch(s, z, d.s, plane, T->facets, d.B, d.Hc, d.Wc, T->w1r, T->bias, T->act[1])) return rc;
-  for (int k = 1; k <= 6; ++k)
-    if (int rc = conv64_launch(s, T->map_act[k], T->act[k + 1], T->wf + (size_t)(k - 1) * NWM, T->bias + k * CH,
-                               T->strips, T->n_strips, d.Hc, d.Wc, 0, nullptr, T->status))
-      return rc;
-  if (int rc = image_norms(T, v0)) return rc;
-  image_unit<<<nblocks(npx), 256, 0, s>>>(v0, T->jn2, plane, d.B, T->jv);
-  PNP_CHECK_LAUNCH();
-  for (int it = 0; it < iters; ++it) {
-    // w = J_Q v: tangents through layers 1..7 (masks [act_k > 0]), then layer 8
-    tangent_first<<<nblocks(npx), 256, 0, s>>>(d, T->jv, T->w1r, T->act[1], T->dp[0]);
-    PNP_CHECK_LAUNCH();
-    int cur = 0;
-    for (int k = 1; k <= 6; ++k) {
-      if (int rc = conv64_launch(s, T->map_dp[cur], T->dp[1 - cur], T->wf + (size_t)(k - 1) * NWM, nullptr, T->strips,
-                                 T->n_strips, d.Hc, d.Wc, 1, T->act[k + 1], T->status))
-        return rc;
-      cur = 1 - cur;
-    }
-    tangent_last<<<nblocks(npx), 256, 0, s>>>(d, T->dp[cur], T->w8r, T->jv, T->jw);
-    PNP_CHECK_LAUNCH();
-    // u = J_Q^T w: the training step's back-propagation with cotangent w
-    last_bwd<<<nblocks(npx), 256, 0, s>>>(d, T->act[7], T->w8r, T->jw, T->dp[0]);
-    PNP_CHECK_LAUNCH();
-    cur = 0;
-    for (int k = 6; k >= 1; --k) {
-      if (int rc = conv64_launch(s, T->map_dp[cur], T->dp[1 - cur], T->wb + (size_t)(k - 1) * NWM, nullptr, T->strips,
-                                 T->n_strips, d.Hc, d.Wc, 1, T->act[k], T->status))
-        return rc;
-      cur = 1 - cur;
-    }
-    cotangent_first<<<nblocks(npx), 256, 0, s>>>(d, T->dp[cur], T->w1r, T->jw, T->ju);
-    PNP_CHECK_LAUNCH();
-    if (it == iters - 1) {  // sigma = ||J_Q v|| for the current unit v
-      if (int rc = image_norms(T, T->jw)) return rc;
-      PNP_CUDA(cudaMemcpyAsync(sigma_host, T->jn2, d.B * sizeof(double), cudaMemcpyDeviceToHost, s));
-      PNP_CUDA(cudaStreamSynchronize(s));
-      for (int b = 0; b < d.B; ++b) sigma_host[b] = std::sqrt(sigma_host[b]);
-    }
-    if (int rc = image_norms(T, T->ju)) return rc;
-    image_unit<<<nblocks(npx), 256, 0, s>>>(T->ju, T->jn2, plane, d.B, T->jv);
+  // the l1 term: forward at z = u + sigma n (activations kept), gradients accumulated, no update
+  if (int rc = pnp_cnn_train_step(T, u, noise, sigma, 0, loss_host)) return rc;
+  // v: the leading right singular vector of J_Q at z, by power iteration (iters = 0: v0 itself)
+  if (iters > 0) {
+    if (int rc = power_iterate(T, v0, iters, nullptr)) return rc;
+  } else {
+    if (int rc = image_norms(T, v0)) return rc;
+    image_unit<<<nblocks(npx), 256, 0, s>>>(v0, T->jn2, plane, d.B, T->jv);
     PNP_CHECK_LAUNCH();
   }
-  if (v_out) PNP_CUDA(cudaMemcpyAsync(v_out, T->jv, npx * sizeof(float), cudaMemcpyDeviceToDevice, s));
-  PNP_CUDA(cudaStreamSynchronize(s));
+  // w = J_Q v with every tangent kept for the weight gradients
+  tangent_first<<<nblocks(npx), 256, 0, s>>>(d, T->jv, T->w1r, T->act[1], T->tan[1]);
+  PNP_CHECK_LAUNCH();
+  for (int k = 1; k <= 6; ++k)
+    if (int rc = conv64_launch(s, T->map_tan[k], T->tan[k + 1], T->wf + (size_t)(k - 1) * NWM, nullptr, T->strips,
+                               T->n_strips, d.Hc, d.Wc, 1, T->act[k + 1], T->status))
+      return rc;
+  tangent_last<<<nblocks(npx), 256, 0, s>>>(d, T->tan[7], T->w8r, T->jv, T->jw);
+  PNP_CHECK_LAUNCH();
+  if (int rc = image_norms(T, T->jw)) return rc;
+  fne_cotangent<<<nblocks(npx), 256, 0, s>>>(T->jw, T->jn2, plane, d.B, (float)(lambda / d.B), 1.0 - eps, T->gout);
+  PNP_CHECK_LAUNCH();
+  // back-propagation of the cotangent through the tangent network (no bias gradients)
+  const int wgb = (int)((npx + WG_CHUNK - 1) / WG_CHUNK);
+  wgrad_onechannel<<<wgb, 576, 0, s>>>(d, 0, T->gout, T->tan[7], T->g + OFF_W8, T->junk);
+  PNP_CHECK_LAUNCH();
+  last_bwd<<<nblocks(npx), 256, 0, s>>>(d, T->act[7], T->w8r, T->gout, T->dp[0]);
+  PNP_CHECK_LAUNCH();
+  int cur = 0;
+  for (int k = 6; k >= 1; --k) {
+    wgrad64<<<dim3(wgb, 9), 256, 0, s>>>(d, T->dp[cur], T->tan[k], T->g + OFF_MID + (k - 1) * MID_STRIDE, T->junk);
+    PNP_CHECK_LAUNCH();
+    if (int rc = conv64_launch(s, T->map_dp[cur], T->dp[1 - cur], T->wb + (size_t)(k - 1) * NWM, nullptr, T->strips,
+                               T->n_strips, d.Hc, d.Wc, 1, T->act[k], T->status))
+      return rc;
+    cur = 1 - cur;
+  }
+  wgrad_onechannel<<<wgb, 576, 0, s>>>(d, 1, T->jv, T->dp[cur], T->g + OFF_W1, T->junk);
+  PNP_CHECK_LAUNCH();
+  if (penalty_host) {
+    std::vector<double> n2(d.B);
+    PNP_CUDA(cudaMemcpyAsync(n2.data(), T->jn2, d.B * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PNP_CUDA(cudaStreamSynchronize(s));
+    double P = 0.0;
+    for (double q : n2) P += lambda / d.B * std::max(q, 1.0 - eps);
+    *penalty_host = P;
+  }
+  if (update) return adam_update(T);
   return PNP_OK;
 }
 

@@ -88,11 +88,16 @@ def fold_scale(params, s: float):
 
 
 def train(pool, sigma: float, steps: int, batch: int = 16, lr: float = 5e-4, lr_min: float = 1e-5,
-          seed: int = 0, params=None, log_every: int = 200, log=print, scale: float = 1.0):
+          seed: int = 0, params=None, log_every: int = 200, log=print, scale: float = 1.0,
+          fne_lambda: float = 0.0, fne_iters: int = 4, fne_eps: float = 0.05):
     """Adam on the l1 loss over random dihedral transforms of pool images; returns (params, history).
 
     With ``scale`` s the images are divided by s and the noise level is sigma / s (noise units); the
-    returned parameters are those of the network in those units (see ``fold_scale``)."""
+    returned parameters are those of the network in those units (see ``fold_scale``).
+    With ``fne_lambda`` > 0 every step adds the soft firm non-expansiveness penalty of
+    Eq. training_loss, fne_lambda / B sum_b max(||grad(2D - I)(z_b) v_b||^2, 1 - fne_eps), v_b from
+    ``fne_iters`` power iterations from Gaussian draws (the Jacobian of D does not change with the
+    noise-unit scaling)."""
     import torch
     import synth
     import paper_2207_11336_gb300 as pnp
@@ -117,12 +122,20 @@ def train(pool, sigma: float, steps: int, batch: int = 16, lr: float = 5e-4, lr_
         u = u.contiguous()
         noise = torch.randn((batch, s, s), device="cuda", generator=gen)
         want = (it + 1) % log_every == 0 or it == steps - 1
-        loss = tr.step(u, noise, sigma / scale, update=True, want_loss=want)
+        pen = None
+        if fne_lambda > 0:
+            v0 = torch.randn((batch, s, s), device="cuda", generator=gen)
+            vals = tr.step_fne(u, noise, sigma / scale, v0, fne_iters, fne_lambda, fne_eps, update=True,
+                               want_values=want)
+            loss, pen = vals if want else (None, None)
+        else:
+            loss = tr.step(u, noise, sigma / scale, update=True, want_loss=want)
         if want:
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
             hist.append((it + 1, loss * scale, el))
-            log(f"step {it + 1:6d}  loss {loss * scale:.4e} (image units)  lr {cur:.2e}  {el:7.1f} s")
+            extra = "" if pen is None else f"  penalty {pen:.4e}"
+            log(f"step {it + 1:6d}  loss {loss * scale:.4e} (image units){extra}  lr {cur:.2e}  {el:7.1f} s")
     out, _ = tr.read()
     tr.close()
     return out, hist
@@ -160,6 +173,11 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--image-units", action="store_true",
                     help="train at the images' own scale instead of in noise units")
+    ap.add_argument("--init", default=None, help="start from these weights (fine-tuning)")
+    ap.add_argument("--fne-lambda", type=float, default=0.0,
+                    help="weight of the soft firm non-expansiveness penalty (0: l1 loss only)")
+    ap.add_argument("--fne-iters", type=int, default=4, help="power iterations per penalised step")
+    ap.add_argument("--fne-eps", type=float, default=0.05, help="penalty floor 1 - eps on ||grad(2D - I)||^2")
     ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
                                                   "dncnn_C3.npz"))
     a = ap.parse_args(argv)
@@ -168,7 +186,7 @@ def main(argv=None):
     print(f"pool: {pool_np.shape} in {time.perf_counter() - t0:.1f} s", flush=True)
     import torch
     meta = dict(workload=a.workload, images=a.images, size=a.size, batch=a.batch, steps=a.steps, lr=a.lr,
-                seed=a.seed)
+                seed=a.seed, fne_lambda=a.fne_lambda, fne_iters=a.fne_iters, fne_eps=a.fne_eps)
     if a.sigma is None:
         from paper_2207_11336_gb300 import heuristics
         import synth
@@ -187,8 +205,13 @@ def main(argv=None):
     scale = 1.0 if a.image_units else noise_unit(sigma)
     meta["noise_unit"] = scale
     pool = torch.from_numpy(pool_np).cuda()
-    params, hist = train(pool, sigma, a.steps, a.batch, a.lr, seed=a.seed,
-                         log=lambda s: print(s, flush=True), scale=scale)
+    init = None
+    if a.init:
+        # fine-tuning: the saved network acts at image scale; train() works in noise units
+        init = fold_scale(load(a.init)[0], 1.0 / scale)
+    params, hist = train(pool, sigma, a.steps, a.batch, a.lr, seed=a.seed, params=init,
+                         log=lambda s: print(s, flush=True), scale=scale, fne_lambda=a.fne_lambda,
+                         fne_iters=a.fne_iters, fne_eps=a.fne_eps)
     params = fold_scale(params, scale)
     meta["loss_history"] = np.array([h[1] for h in hist])
     meta["train_seconds"] = hist[-1][2] if hist else 0.0

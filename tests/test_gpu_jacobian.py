@@ -80,3 +80,53 @@ def test_trained_denoiser_jacobian_norm_is_reported():
     print("||grad(2D - I)||_S of the trained network at sigma = %.3g:" % sigma, sig)
     assert np.all(np.isfinite(sig)) and np.all(sig > 0.5)
     tr.close()
+
+
+def test_penalty_gradients_match_oracle():
+    """The penalty's weight gradients (trainer gradients with the penalty minus without it) against
+    the oracle's back-propagation through the frozen-mask tangent network; iters = 0 fixes v."""
+    B, s, sigma = 2, 24, 0.05
+    params = synth.cnn_init(np.random.default_rng(41), 64, 8, last_scale=0.3)
+    rng = np.random.default_rng(42)
+    u = np.stack([synth.training_image(s, rng) for _ in range(B)]).astype(np.float32)
+    nz = rng.standard_normal((B, s, s)).astype(np.float32)
+    v0 = rng.standard_normal((B, s, s)).astype(np.float32)
+    tr = pnp.CnnTrainer(params, B, s)
+    ud, nd, vd = (torch.from_numpy(a).cuda() for a in (u, nz, v0))
+    tr.step(ud, nd, sigma, update=False)
+    _, g1 = tr.read(weights=False, grads=True, clear_grads=True)
+    loss, pen = tr.step_fne(ud, nd, sigma, vd, 0, lam=1.0, eps=1.0, update=False, want_values=True)
+    _, g2 = tr.read(weights=False, grads=True, clear_grads=True)
+    tr.close()
+    gp = pnp.unpack_cnn_weights(g2.astype(np.float64) - g1.astype(np.float64))
+    z = (u + np.float32(sigma) * nz).astype(np.float64)
+    v = v0.astype(np.float64) / np.linalg.norm(v0.astype(np.float64), axis=(1, 2), keepdims=True)
+    P, grads, _ = oj.fne_penalty_and_grads(params, z, v, 1.0, 1.0, bf16=True)
+    assert pen == pytest.approx(P, rel=2.0 ** -6)
+    for li, ((dW, _), (gW, gb)) in enumerate(zip(grads, gp)):
+        cos = float(np.vdot(gW, dW) / (np.linalg.norm(gW) * np.linalg.norm(dW)))
+        assert cos >= 0.995, (li, cos)
+        # the gradient reaching layer 1 has passed 7 BF16 tangents and 7 BF16 back-propagated
+        # gradients, and its sums cancel: a few percent of its norm, not one BF16 unit
+        assert np.linalg.norm(gW - dW) <= 2.0 ** -4 * np.linalg.norm(dW), li
+        assert np.abs(gb).max() <= 1e-3 * max(np.abs(g1).max(), 1e-30)   # no bias gradient
+
+
+def test_penalised_training_lowers_the_jacobian_norm():
+    B, s = 4, 32
+    params = synth.cnn_init(np.random.default_rng(43), 64, 8, last_scale=1.0)
+    rng = np.random.default_rng(44)
+    u = torch.from_numpy(np.stack([synth.training_image(s, rng) for _ in range(B)]).astype(np.float32)).cuda()
+    gen = torch.Generator(device="cuda").manual_seed(45)
+    tr = pnp.CnnTrainer(params, B, s, lr=2e-4)
+    zt = u + 0.05 * torch.randn(u.shape, device="cuda", generator=gen)
+    v0 = torch.randn(u.shape, device="cuda", generator=gen)
+    before, _ = tr.jacobian_norm(zt.contiguous(), v0, 20)
+    for _ in range(60):
+        nz = torch.randn(u.shape, device="cuda", generator=gen)
+        vv = torch.randn(u.shape, device="cuda", generator=gen)
+        tr.step_fne(u, nz, 0.05, vv, 3, lam=1.0, eps=0.05)
+    after, _ = tr.jacobian_norm(zt.contiguous(), v0, 20)
+    tr.close()
+    print("||grad(2D - I)||_S before / after 60 penalised steps:", before, after)
+    assert after.max() < before.max()

@@ -64,3 +64,34 @@ def test_bf16_mirror_differs_by_rounding_only():
     _, acts = ocnn.network(params, z, bf16=True, keep=True)
     a, b = oj.jvp(params, z, v, bf16=True, acts=acts), oj.jvp(params, z, v, acts=acts)
     assert np.linalg.norm(a - b) <= 2.0 ** -6 * np.linalg.norm(b)
+
+
+def test_penalty_gradient_matches_central_differences():
+    params = _net(17, channels=4, depth=3)
+    z = np.stack([_img(18), _img(19)])
+    v = np.stack([_img(20), _img(21)])
+    v /= np.linalg.norm(v, axis=(1, 2), keepdims=True)
+    lam, eps = 0.7, 0.5
+    P, grads, n2 = oj.fne_penalty_and_grads(params, z, v, lam, eps)
+    assert P == pytest.approx(lam / 2 * sum(max(a, 1 - eps) for a in n2))
+    h = 1e-6
+    for li, idx in [(0, (1, 0, 2, 1)), (1, (2, 3, 0, 0)), (2, (0, 1, 1, 2))]:
+        def pen(delta):
+            p2 = [(W.copy(), b.copy()) for W, b in params]
+            p2[li][0][idx] += delta
+            return oj.fne_penalty_and_grads(p2, z, v, lam, eps)[0]
+        fd = (pen(h) - pen(-h)) / (2 * h)
+        assert grads[li][0][idx] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+    assert all(np.all(db == 0) for _, db in grads)
+
+
+def test_penalty_inactive_below_the_bound():
+    params = _net(22)
+    z, v = _img(23)[None], _img(24)[None]
+    v = v / np.linalg.norm(v)
+    P, grads, n2 = oj.fne_penalty_and_grads(params, z, v, 1.0, 1.0 - 2 * n2_of(params, z, v))
+    assert all(np.all(dW == 0) for dW, _ in grads)
+
+
+def n2_of(params, z, v):
+    return oj.fne_penalty_and_grads(params, z, v, 1.0, 0.0)[2][0]
