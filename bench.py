@@ -290,6 +290,8 @@ def run_reference(args):
 
 # ---------------------------------------------------------------- GPU arm
 WEIGHTS = os.path.join(ROOT, "paper_2207_11336_gb300", "weights", "dncnn_C3.npz")
+# the same network fine-tuned with the soft firm non-expansiveness penalty of Eq. training_loss
+WEIGHTS_FNE = os.path.join(ROOT, "paper_2207_11336_gb300", "weights", "dncnn_C3_fne.npz")
 SNR_ITERS = 200          # the plain loop's SNR after this many iterations is the target
 SNR_CHUNK = 10           # the learned loop's SNR is checked every SNR_CHUNK iterations
 SNR_MAX_ITERS = 600
@@ -455,6 +457,21 @@ def run_gpu(args):
             "time_to_snr_s": None if it_l is None else it_l * ms / steps / 1e3,
             "snr_db_final": trace_l[-1][1], "iters_run": trace_l[-1][0],
             "snr_trace": [(i, round(s, 3)) for i, s in trace_l[::2]]}
+        if os.path.exists(WEIGHTS_FNE):
+            # the learned loop with the penalised network (same architecture and cost per iteration)
+            params_f, meta_f = load_weights(WEIGHTS_FNE)
+            cnn_f = pnp.CnnDenoiser(params_f, n, facet_rows=prob["facet_rows"], facet_cols=prob["facet_cols"],
+                                    halo=prob["halo"], stream=stream)
+            xf = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+            it_f, trace_f = _run_to_snr(plan, cnn_f, y_s, xf, gamma, L, x_true, alpha, snr_plain, SNR_MAX_ITERS)
+            comparison["learned_fne"] = {
+                "weights": "dncnn_C3 fine-tuned %d steps with the penalty, lambda %g" % (
+                    int(meta_f.get("steps", 0)), float(meta_f.get("fne_lambda", 0.0))),
+                "iters_to_plain_snr": it_f, "time_to_snr_s": None if it_f is None else it_f * ms / steps / 1e3,
+                "snr_db_final": trace_f[-1][1], "iters_run": trace_f[-1][0],
+                "snr_trace": [(i, round(s, 3)) for i, s in trace_f[::2]]}
+            cnn_f.close()
+            del xf
 
     # ---- kernel timing: eager replay with CUDA events around each operator stage
     plan.set_timing(True)
