@@ -61,6 +61,8 @@ def parse():
                     help="skip timing the plain loop with BF16 weights in G")
     ap.add_argument("--wstacks", type=int, default=8,
                     help="w-stacks of the stacked-operator comparison line (0 skips it)")
+    ap.add_argument("--holo-rows", type=int, default=20_000_000,
+                    help="rows of the 256^2 / 512^2 holographic comparison line (0 skips it)")
     ap.add_argument("--kernel-case", choices=["gridding", "cnn", "fft"], default=None,
                     help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
     ap.add_argument("--cnn-side", type=int, default=4096,
@@ -448,6 +450,37 @@ def run_gpu(args):
             "phi_rel_l2_vs_unstacked": err, "plan_build_s": t_plan, "gridding_autotune": tune_ws}
         plan_ws.close()
         del plan_ws, y_ws, xw
+    if args.holo_rows > 0:
+        # App. E, Eq. phidagphi: with many rows per grid cell the holographic H = G^H G is far smaller
+        # than G; the 256^2 image / 512^2 grid layout with M rows (KB J = 7), plain loop with G vs with H
+        ph = synth.make_problem("C0", M=args.holo_rows)
+        nh, Kh = ph["n"], ph["K"]
+        plan_h = pnp.Plan(nh, Kh, ph["omega"], stream=stream)
+        xth = torch.from_numpy(ph["x_true"].astype(np.float32)).cuda()
+        y0h = plan_h.phi_forward(xth)
+        tauh = synth.noise_std_for_isnr(float(torch.linalg.vector_norm(y0h.to(torch.complex128)).item()),
+                                        ph["M"], ph["isnr_db"])
+        yh = (y0h + tauh * torch.from_numpy(ph["noise"].astype(np.complex64)).cuda()).contiguous()
+        Lh, _ = plan_h.op_norm(None, 200, 1e-6)
+        haar_h = pnp.HaarDenoiser(tauh / np.sqrt(2.0 * Lh), stream=stream)
+        res_h = {}
+        for mode in ("G", "H"):
+            if mode == "H":
+                t_b = time.perf_counter()
+                plan_h.set_holographic(True)
+                res_h["H_build_s"] = time.perf_counter() - t_b
+            xh = torch.zeros((nh, nh), dtype=torch.float32, device="cuda")
+            plan_h.fb_run(haar_h, yh, x0=xh, L=Lh, max_iter=4, check_every=2, use_graph=True, inplace=True)
+            ms_h, _ = _timed_loop(plan_h, haar_h, yh, xh, 1.98 / Lh, Lh, steps, stream)
+            res_h[mode] = {"iter_per_s": ws * steps / (ms_h / 1e3), "ms_per_iter": ms_h / steps}
+            res_h["x_" + mode] = xh
+        res_h["x_rel_diff_H_vs_G"] = float(torch.linalg.vector_norm((res_h.pop("x_H") - res_h["x_G"]).double()) /
+                                           torch.linalg.vector_norm(res_h.pop("x_G").double()))
+        comparison["plain_holographic"] = dict(
+            workload="256^2 image, 512^2 grid, M=%.0e vis, KB J=7, Haar prox" % args.holo_rows,
+            G_bytes=plan_h.info["nnz"] * 10, H_bytes=plan_h.info["holographic_bytes"], **res_h)
+        plan_h.close()
+        del plan_h, yh, y0h, xth
     if learned:
         xl = torch.zeros((n, n), dtype=torch.float32, device="cuda")
         it_l, trace_l = _run_to_snr(plan, cnn, y_s, xl, gamma, L, x_true, alpha, snr_plain, SNR_MAX_ITERS)

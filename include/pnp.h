@@ -95,6 +95,7 @@ typedef struct pnp_plan_info {
   int64_t unit_nnz;     /* taps at most per gridding work unit                */
   int row_batch;        /* rows of a run whose residuals one warp forms together */
   int nstacks;          /* w-stacks P of the operator (1: w wholly in G)      */
+  int64_t holographic_bytes; /* device bytes of the holographic H (0: not built) */
 } pnp_plan_info;
 
 /* ------------------------------------------------------------------ plans */
@@ -145,6 +146,15 @@ int pnp_plan_get_info(const pnp_plan* plan, pnp_plan_info* info);
 /* Set the rows per work unit of the gridding kernels (autotuner hook; 0 keeps
  * the current choice).  Rebuilds the work list only; G is unchanged. */
 int pnp_plan_set_unit_nnz(pnp_plan* plan, int64_t unit_nnz);
+
+/* Holographic form of the normal operator (App. E, Eq. phidagphi): with enable != 0 the plan
+ * builds (once) H = G^H G, stored per grid cell as a (2 Jmax - 1)^2 stencil (device bytes
+ * (2 Jmax - 1)^2 K^2 8, reported in pnp_plan_info; PNP_ERR_OOM when that does not fit), and
+ * from then on pnp_fb_run forms the dirty grid G^H y once per run and iterates with
+ * Re{Z^H F^H (H F Z x - G^H y)}, and op_norm with H, without reading G.  grad_step, phi_forward
+ * and phi_adjoint keep using G.  enable == 0 switches back (H is kept).  Plans with several
+ * w-stacks: PNP_ERR_UNSUPPORTED.  Synchronous. */
+int pnp_plan_set_holographic(pnp_plan* plan, int enable);
 
 /* Set how many rows of a run of rows sharing a tap window one warp of the
  * gridding pass forms the residuals of together (1, 2 or 4; 0 keeps the

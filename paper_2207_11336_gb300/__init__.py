@@ -26,7 +26,7 @@ ERRORS = {-1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "DIVERGED", -5: "TIMEOUT
 
 EXPORTED = [
     "pnp_plan_create", "pnp_plan_create_stacked", "pnp_plan_destroy", "pnp_plan_get_info", "pnp_plan_set_unit_nnz",
-    "pnp_plan_set_row_batch", "pnp_plan_export_rows", "phi_forward", "phi_adjoint", "grad_step", "op_norm",
+    "pnp_plan_set_row_batch", "pnp_plan_set_holographic", "pnp_plan_export_rows", "phi_forward", "phi_adjoint", "grad_step", "op_norm",
     "pnp_den_create_haar", "pnp_den_create_cnn", "pnp_den_destroy", "denoise", "pnp_fb_run",
     "pnp_last_error", "pnp_kernel_launch_count", "pnp_plan_set_timing", "pnp_plan_read_timing",
     "pnp_plan_device_status", "pnp_haar_denoise_noalloc", "pnp_den_device_status",
@@ -57,7 +57,8 @@ class _Info(C.Structure):
                 ("tile", C.c_int), ("nblocks", C.c_int), ("M", C.c_int64), ("nnz", C.c_int64),
                 ("n_units", C.c_int64), ("beta", C.c_double), ("dl", C.c_double),
                 ("device_bytes", C.c_int64), ("region_pitch", C.c_int), ("run_max", C.c_int),
-                ("unit_nnz", C.c_int64), ("row_batch", C.c_int), ("nstacks", C.c_int)]
+                ("unit_nnz", C.c_int64), ("row_batch", C.c_int), ("nstacks", C.c_int),
+                ("holographic_bytes", C.c_int64)]
 
 
 _lib = None
@@ -80,6 +81,7 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_plan_get_info.argtypes = [vp, C.POINTER(_Info)]
     L.pnp_plan_set_unit_nnz.argtypes = [vp, i64]
     L.pnp_plan_set_row_batch.argtypes = [vp, i32]
+    L.pnp_plan_set_holographic.argtypes = [vp, i32]
     L.pnp_plan_autotune.argtypes = [vp, i32, C.POINTER(i32), C.POINTER(i64), C.POINTER(dbl)]
     L.pnp_plan_export_rows.argtypes = [vp, vp, i64, vp, vp, vp]
     L.phi_forward.argtypes = [vp, vp, vp]
@@ -108,7 +110,8 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_plan_read_timing.argtypes = [vp, vp, vp]
     L.pnp_last_error.restype = C.c_char_p
     L.pnp_kernel_launch_count.restype = i64
-    for name in ("pnp_plan_create", "pnp_plan_create_stacked", "pnp_plan_get_info", "pnp_plan_set_unit_nnz", "pnp_plan_set_row_batch",
+    for name in ("pnp_plan_create", "pnp_plan_create_stacked", "pnp_plan_get_info", "pnp_plan_set_unit_nnz",
+                 "pnp_plan_set_row_batch", "pnp_plan_set_holographic",
                  "pnp_plan_export_rows",
                  "phi_forward", "phi_adjoint", "grad_step", "op_norm", "pnp_den_create_haar",
                  "pnp_den_create_cnn", "denoise", "pnp_fb_run", "pnp_plan_set_timing",
@@ -219,6 +222,10 @@ class Plan:
 
     def set_unit_nnz(self, unit_nnz: int):
         _check(lib().pnp_plan_set_unit_nnz(self._h, int(unit_nnz)))
+
+    def set_holographic(self, enable: bool = True):
+        """Use the holographic H = G^H G in the FB loop and op_norm (App. E, Eq. phidagphi)."""
+        _check(lib().pnp_plan_set_holographic(self._h, 1 if enable else 0))
 
     def set_row_batch(self, row_batch: int):
         """Rows of a run whose residuals one warp forms together (1, 2 or 4)."""

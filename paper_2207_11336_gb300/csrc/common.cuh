@@ -135,6 +135,10 @@ struct pnp_plan {
   float* d_img[3] = {nullptr, nullptr, nullptr};  // n*n work images
   float2* d_chirp = nullptr;   // P*n (P > 1): per stack and image axis exp(i pi a_p (a - n/2)^2)
   float* d_gacc = nullptr;     // n*n (P > 1): gradient image accumulated over the stacks
+  float2* d_H = nullptr;       // holographic H = G^H G: [S*S offsets][K*K cells], S = 2 Jmax - 1
+  float2* d_dirty = nullptr;   // K*K: G^H y of the current FB run (holographic mode)
+  int holo_S = 0;
+  bool holo = false;           // FB loop and op_norm apply H instead of streaming G
   int64_t device_bytes = 0;
 
   // optional per-stage event timing: (stage, start, stop)
@@ -176,6 +180,10 @@ int permute_y(pnp_plan* p, const float2* y_user);  // d_ysorted = y_user[perm]
 // plan_build.cu
 int build_units(pnp_plan* p);
 int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t* block, const int32_t* stack);
+// holographic.cu: build H (once), the dirty grid of the sorted data, one application of H
+int holo_build_plan(pnp_plan* p);
+int holo_dirty_grid(pnp_plan* p);
+int holo_apply_pass(pnp_plan* p, bool data_term);  // d_gridB = H d_gridA (- d_dirty)
 // update.cu
 int haar_denoise_dev(cudaStream_t s, const float* z, float* out, int n, float t, double* acc,
                      const float* x_prev);

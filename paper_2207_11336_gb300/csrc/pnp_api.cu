@@ -77,6 +77,8 @@ void free_plan(pnp_plan* p) {
   for (float* im : p->d_img) cudaFree(im);
   cudaFree(p->d_chirp);
   cudaFree(p->d_gacc);
+  cudaFree(p->d_H);
+  cudaFree(p->d_dirty);
   delete p;
 }
 
@@ -92,7 +94,12 @@ int read_acc(pnp_plan* p, double* h, int count) {
 // plan's w-stacks (Eq. phidagphi): per stack the forward FFT with Z_s, the fused gridding pass
 // over the stack's rows and the adjoint FFT; all stacks share one pair of grids.
 int normal_pass(pnp_plan* p, const float2* y_sorted, const float* xf, int epi, const float* xe, float* out,
-                float gamma, float t) {
+                float gamma, float t, bool holo_ok) {
+  if (holo_ok && p->holo) {  // App. E, Eq. phidagphi: H F Z x - G^H y without reading G
+    if (int rc = fft_forward(p, xf, 0)) return rc;
+    if (int rc = holo_apply_pass(p, y_sorted != nullptr)) return rc;
+    return fft_adjoint(p, epi, xe, out, gamma, t, 0);
+  }
   for (int s = 0; s < p->nstacks; ++s) {
     if (int rc = fft_forward(p, xf, s)) return rc;
     if (int rc = gridding_pass(p, G_FUSED, y_sorted, nullptr, s)) return rc;
@@ -104,8 +111,8 @@ int normal_pass(pnp_plan* p, const float2* y_sorted, const float* xf, int epi, c
 // One FB iteration x_next = D(x_cur - gamma grad f(x_cur)); FP64 norms land in acc[0..1].
 int fb_iteration(pnp_plan* p, pnp_den* d, const float* cur, float* nxt, double gamma) {
   const float2* ys = reinterpret_cast<const float2*>(p->d_ysorted);
-  if (d->kind == PNP_DEN_HAAR) return normal_pass(p, ys, cur, EPI_HAAR, cur, nxt, (float)gamma, (float)d->t);
-  if (int rc = normal_pass(p, ys, cur, EPI_GRAD, cur, p->d_img[1], (float)gamma, 0.f)) return rc;
+  if (d->kind == PNP_DEN_HAAR) return normal_pass(p, ys, cur, EPI_HAAR, cur, nxt, (float)gamma, (float)d->t, true);
+  if (int rc = normal_pass(p, ys, cur, EPI_GRAD, cur, p->d_img[1], (float)gamma, 0.f, true)) return rc;
   return cnn_denoise(d, p->stream, p->d_img[1], nxt, p->n, p->d_acc, cur);
 }
 
@@ -272,6 +279,7 @@ int pnp_plan_get_info(const pnp_plan* p, pnp_plan_info* info) {
   info->run_max = p->run_max;
   info->row_batch = p->row_batch;
   info->nstacks = p->nstacks;
+  info->holographic_bytes = p->d_H ? (int64_t)p->holo_S * p->holo_S * p->K * p->K * 8 : 0;
   info->unit_nnz = p->unit_nnz;
   return PNP_OK;
 }
@@ -282,6 +290,16 @@ int pnp_plan_set_unit_nnz(pnp_plan* p, int64_t unit_nnz) {
   PNP_CUDA(cudaStreamSynchronize(p->stream));
   p->unit_nnz = unit_nnz;
   return build_units(p);
+}
+
+int pnp_plan_set_holographic(pnp_plan* p, int enable) {
+  if (!p) return fail(PNP_ERR_INVALID_ARG, "NULL plan");
+  if (enable) {
+    PNP_CUDA(cudaStreamSynchronize(p->stream));
+    if (int rc = holo_build_plan(p)) return rc;
+  }
+  p->holo = enable != 0;
+  return PNP_OK;
 }
 
 int pnp_plan_set_row_batch(pnp_plan* p, int row_batch) {
@@ -434,7 +452,7 @@ int grad_step(pnp_plan* p, const float* x, const float* y, double gamma, float* 
   if (x == x_out) return fail(PNP_ERR_INVALID_ARG, "x and x_out must not alias");
   if (!std::isfinite(gamma)) return fail(PNP_ERR_INVALID_ARG, "gamma must be finite");
   if (int rc = permute_y(p, reinterpret_cast<const float2*>(y))) return rc;
-  return normal_pass(p, reinterpret_cast<const float2*>(y), x, EPI_GRAD, x, x_out, (float)gamma, 0.f);
+  return normal_pass(p, reinterpret_cast<const float2*>(y), x, EPI_GRAD, x, x_out, (float)gamma, 0.f, false);
 }
 
 int op_norm(pnp_plan* p, const float* v0, int max_it, double tol, double* L_out, int* iters_out) {
@@ -450,7 +468,7 @@ int op_norm(pnp_plan* p, const float* v0, int max_it, double tol, double* L_out,
   double L = 0.0, h[2];
   int it = 0;
   for (it = 1; it <= max_it; ++it) {
-    if (int rc = normal_pass(p, nullptr, v, EPI_NORMAL, nullptr, g, 0.f, 0.f)) return rc;
+    if (int rc = normal_pass(p, nullptr, v, EPI_NORMAL, nullptr, g, 0.f, 0.f, true)) return rc;
     if (int rc = scale_image(p->stream, g, v, N, p->d_acc, 0)) return rc;
     if (int rc = read_acc(p, h, 1)) return rc;
     const double Ln = std::sqrt(h[0]);
@@ -527,6 +545,8 @@ int pnp_fb_run(pnp_plan* p, pnp_den* d, const float* y, const pnp_params* prm, f
   const bool graph = prm->use_graph != 0;
   const int bit = 1 << d->kind;
   if (int rc = permute_y(p, reinterpret_cast<const float2*>(y))) return rc;
+  if (p->holo)
+    if (int rc = holo_dirty_grid(p)) return rc;  // G^H y once per run (App. E, Eq. phidagphi)
   float* buf[2] = {x, p->d_img[0]};
   int c = 0, k = 0, rc = PNP_OK;
   double h[2] = {0, 0}, rel = 0, xn = 0, xn_min = -1;

@@ -28,3 +28,7 @@ def to_host(t):
 
 def rel_l2(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def PnPError_type():
+    return pnp.PnPError
