@@ -176,9 +176,16 @@ int pnp_plan_set_row_batch(pnp_plan* plan, int row_batch);
  * reps must lie in [1, 100]. */
 int pnp_plan_autotune(pnp_plan* plan, int reps, int* run_max_out, int64_t* unit_nnz_out, double* ms_out);
 
-/* Device-side status flags of the plan's kernels (synchronous read).  Bit 0:
- * a gridding tap fell outside its tile's staged shared-memory region and was
- * skipped (an internal consistency check; never set by a correct plan). */
+/* Device-side status flags of the plan's kernels (synchronous read; the flags
+ * stay set for the plan's lifetime).  Each is an internal consistency check
+ * that a correct plan never sets:
+ *  bit 1 (2)   a wait of the gridding pass's copy pipeline ran out (bounded
+ *              wait): the pass stopped early and its output is incomplete;
+ *  bit 2 (4)   a chunk of the gridding work list was inconsistent and skipped;
+ *  bit 4 (16)  a tap pair outside the holographic stencil was skipped while
+ *              building H.
+ * Taps outside their staged region are caught when the plan is built
+ * (pnp_plan_create fails with PNP_ERR_INVALID_ARG). */
 int pnp_plan_device_status(pnp_plan* plan, int* flags_host);
 
 /* Per-stage CUDA-event timing (profiling aid).  While enabled, every
