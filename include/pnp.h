@@ -55,7 +55,7 @@ enum {
 enum { PNP_W_C64 = 0, PNP_W_BF16C = 1 };
 
 /* Denoiser kinds. */
-enum { PNP_DEN_HAAR = 0, PNP_DEN_CNN = 1 };
+enum { PNP_DEN_HAAR = 0, PNP_DEN_CNN = 1, PNP_DEN_SARA = 2 };
 
 typedef struct pnp_plan pnp_plan;
 typedef struct pnp_den pnp_den;
@@ -248,6 +248,26 @@ int pnp_den_create_haar(pnp_den** den, double t, void* stream);
 int pnp_den_create_cnn(pnp_den** den, const float* weights_host,
                        const int32_t* facet_rows_host, int nfr,
                        const int32_t* facet_cols_host, int nfc, int halo, int n, void* stream);
+
+/* uSARA's denoiser (App. B): the prox of gamma_lambda ||W Psi^T x||_1 + iota_+(x) for the SARA
+ * dictionary Psi (the Dirac basis and the 2-D Daubechies db1..db8 bases, each a `levels`-level
+ * separable DWT with periodic extension, divided by 3 so that Psi Psi^T = I), computed by
+ * `prox_iters` dual forward-backward iterations x = max(0, z - Psi u), u <- clip(u + Psi^T x,
+ * -gamma_lambda w, gamma_lambda w) warm-started from the previous call's u.  The weights w start
+ * at 1; pnp_den_sara_reweight sets w = rho / (rho + |Psi^T x|), the majoriser of the log-sum prior
+ * at x (Eq. lambda: gamma_lambda = tau / sqrt(2L), rho = gamma_lambda).
+ *  n          image side, a multiple of 2^levels with n / 2^levels >= 1;  levels in [1, 8]
+ *  prox_iters >= 1
+ * Device memory: 2 x 9 n^2 + 5 n^2 floats.  Used by denoise() and pnp_fb_run like the others. */
+int pnp_den_create_sara(pnp_den** den, int n, int levels, double gamma_lambda, double rho, int prox_iters,
+                        void* stream);
+/* w = rho / (rho + |Psi^T x|) for the device n x n image x (the reweighting step of uSARA). */
+int pnp_den_sara_reweight(pnp_den* den, const float* x);
+/* The SARA dictionary of a SARA denoiser: direction 1 writes Psi^T in (device, 9 x n x n, basis
+ * order Dirac, db1, ..., db8; each DWT's coefficients in one n x n array, the level's approximation
+ * in the top-left corner and its details beside and below it); direction -1 writes Psi in
+ * (in: 9 x n x n, out: n x n). */
+int pnp_sara_transform(pnp_den* den, const float* in, float* out, int direction);
 
 void pnp_den_destroy(pnp_den* den);
 

@@ -170,7 +170,7 @@ def prox_weighted_l1_pos(psi: Sara, z: np.ndarray, t: np.ndarray, max_iter: int 
 
 
 def usara(op, y, gamma: float, gamma_lambda: float, rho: float, n_reweights: int, fb_iters: int,
-          prox_iters: int = 100, psi: Sara | None = None, x0=None):
+          prox_iters: int = 100, psi: Sara | None = None, x0=None, prox_tol: float = 1e-6):
     """Reweighted PnP-FB with the SARA prior: n_reweights + 1 convex surrogates of fb_iters FB
     iterations each (the dual variable of the prox is warm-started from one call to the next)."""
     psi = Sara() if psi is None else psi
@@ -181,6 +181,6 @@ def usara(op, y, gamma: float, gamma_lambda: float, rho: float, n_reweights: int
     for _ in range(n_reweights + 1):
         for _ in range(fb_iters):
             z = x - gamma * op.adjoint(op.forward(x) - y)
-            x, u, _ = prox_weighted_l1_pos(psi, z, gamma_lambda * w, prox_iters, 1e-6, u0=u)
+            x, u, _ = prox_weighted_l1_pos(psi, z, gamma_lambda * w, prox_iters, prox_tol, u0=u)
         w = reweighting_weights(psi.analysis(x), rho)
     return x

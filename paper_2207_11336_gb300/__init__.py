@@ -32,7 +32,7 @@ EXPORTED = [
     "pnp_plan_device_status", "pnp_haar_denoise_noalloc", "pnp_den_device_status",
     "pnp_cnn_trainer_create", "pnp_cnn_trainer_destroy", "pnp_cnn_train_step", "pnp_cnn_trainer_read",
     "pnp_cnn_num_params", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm",
-    "pnp_cnn_train_step_fne",
+    "pnp_cnn_train_step_fne", "pnp_den_create_sara", "pnp_den_sara_reweight", "pnp_sara_transform",
 ]
 
 
@@ -91,6 +91,9 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_den_create_haar.argtypes = [C.POINTER(vp), dbl, vp]
     L.pnp_den_create_cnn.argtypes = [C.POINTER(vp), vp, vp, i32, vp, i32, i32, i32, vp]
     L.pnp_den_destroy.argtypes = [vp]
+    L.pnp_den_create_sara.argtypes = [C.POINTER(vp), i32, i32, dbl, dbl, i32, vp]
+    L.pnp_den_sara_reweight.argtypes = [vp, vp]
+    L.pnp_sara_transform.argtypes = [vp, vp, vp, i32]
     L.pnp_den_destroy.restype = None
     L.denoise.argtypes = [vp, vp, vp, i32]
     L.pnp_fb_run.argtypes = [vp, vp, vp, C.POINTER(_Params), vp, C.POINTER(_Stats)]
@@ -118,7 +121,8 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
                  "pnp_plan_read_timing", "pnp_plan_device_status", "pnp_haar_denoise_noalloc",
                  "pnp_den_device_status", "pnp_cnn_trainer_create", "pnp_cnn_train_step",
                  "pnp_cnn_trainer_read", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm",
-                 "pnp_cnn_train_step_fne"):
+                 "pnp_cnn_train_step_fne", "pnp_den_create_sara", "pnp_den_sara_reweight",
+                 "pnp_sara_transform"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -373,6 +377,40 @@ class HaarDenoiser(_Denoiser):
         self._h = C.c_void_p()
         _check(lib().pnp_den_create_haar(C.byref(self._h), float(t), _stream_handle(stream)))
         self.t = float(t)
+
+
+class SaraDenoiser(_Denoiser):
+    """uSARA's denoiser (App. B): the prox of gamma_lambda ||W Psi^T x||_1 + positivity for the SARA
+    dictionary by ``prox_iters`` dual forward-backward iterations (warm-started); ``reweight(x)``
+    sets W from the log-sum prior at x."""
+
+    def __init__(self, n: int, gamma_lambda: float, rho: float, prox_iters: int = 20, levels: int = 4,
+                 stream=None):
+        lib()
+        self.n = int(n)
+        self._h = C.c_void_p()
+        _check(lib().pnp_den_create_sara(C.byref(self._h), self.n, int(levels), float(gamma_lambda), float(rho),
+                                         int(prox_iters), _stream_handle(stream)))
+
+    def reweight(self, x):
+        _cuda_f32(x, (self.n, self.n), "x")
+        _check(lib().pnp_den_sara_reweight(self._h, _ptr(x)))
+
+    def analysis(self, x):
+        """Psi^T x: (9, n, n)."""
+        import torch
+        _cuda_f32(x, (self.n, self.n), "x")
+        out = torch.empty((9, self.n, self.n), dtype=torch.float32, device=x.device)
+        _check(lib().pnp_sara_transform(self._h, _ptr(x), _ptr(out), 1))
+        return out
+
+    def synthesis(self, c):
+        """Psi c for c of shape (9, n, n)."""
+        import torch
+        _cuda_f32(c, (9, self.n, self.n), "c")
+        out = torch.empty((self.n, self.n), dtype=torch.float32, device=c.device)
+        _check(lib().pnp_sara_transform(self._h, _ptr(c), _ptr(out), -1))
+        return out
 
 
 def pack_cnn_weights(params) -> np.ndarray:

@@ -223,4 +223,10 @@ int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, cons
                      int Wc, const float* w1, const float* b1, __nv_bfloat16* out);
 int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc,
                 const float* x_prev);
+// sara.cu: uSARA's denoiser (App. B)
+int sara_create(pnp_den* d, int n, int levels, double gamma_lambda, double rho, int iters);
+void sara_destroy(pnp_den* d);
+int sara_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc, const float* x_prev);
+int sara_reweight(pnp_den* d, const float* x);
+int sara_transform(pnp_den* d, const float* in, float* out, int direction);
 }  // namespace pnp

@@ -113,6 +113,7 @@ int fb_iteration(pnp_plan* p, pnp_den* d, const float* cur, float* nxt, double g
   const float2* ys = reinterpret_cast<const float2*>(p->d_ysorted);
   if (d->kind == PNP_DEN_HAAR) return normal_pass(p, ys, cur, EPI_HAAR, cur, nxt, (float)gamma, (float)d->t, true);
   if (int rc = normal_pass(p, ys, cur, EPI_GRAD, cur, p->d_img[1], (float)gamma, 0.f, true)) return rc;
+  if (d->kind == PNP_DEN_SARA) return sara_denoise(d, p->stream, p->d_img[1], nxt, p->n, p->d_acc, cur);
   return cnn_denoise(d, p->stream, p->d_img[1], nxt, p->n, p->d_acc, cur);
 }
 
@@ -511,10 +512,45 @@ int pnp_den_create_cnn(pnp_den** den, const float* weights_host, const int32_t* 
   return PNP_OK;
 }
 
+int pnp_den_create_sara(pnp_den** den, int n, int levels, double gamma_lambda, double rho, int prox_iters,
+                        void* stream) {
+  if (!den) return fail(PNP_ERR_INVALID_ARG, "NULL denoiser pointer");
+  *den = nullptr;
+  if (levels < 1 || levels > 8 || n < 2 || n % (1 << levels) != 0)
+    return fail(PNP_ERR_INVALID_ARG, "n must be a multiple of 2^levels, levels in [1, 8]");
+  if (!(gamma_lambda >= 0) || !std::isfinite(gamma_lambda) || !(rho > 0) || !std::isfinite(rho) || prox_iters < 1)
+    return fail(PNP_ERR_INVALID_ARG, "bad SARA parameters");
+  pnp_den* d = new pnp_den();
+  d->kind = PNP_DEN_SARA;
+  d->t = gamma_lambda;
+  d->stream = reinterpret_cast<cudaStream_t>(stream);
+  if (int rc = sara_create(d, n, levels, gamma_lambda, rho, prox_iters)) {
+    std::string keep = t_err;
+    sara_destroy(d);
+    delete d;
+    t_err = keep;
+    return rc;
+  }
+  *den = d;
+  return PNP_OK;
+}
+
+int pnp_den_sara_reweight(pnp_den* den, const float* x) {
+  if (!den || !x || den->kind != PNP_DEN_SARA) return fail(PNP_ERR_INVALID_ARG, "not a SARA denoiser");
+  return sara_reweight(den, x);
+}
+
+int pnp_sara_transform(pnp_den* den, const float* in, float* out, int direction) {
+  if (!den || !in || !out || den->kind != PNP_DEN_SARA || (direction != 1 && direction != -1))
+    return fail(PNP_ERR_INVALID_ARG, "bad argument");
+  return sara_transform(den, in, out, direction);
+}
+
 void pnp_den_destroy(pnp_den* den) {
   if (!den) return;
   cudaStreamSynchronize(den->stream);
   if (den->kind == PNP_DEN_CNN) cnn_destroy(den);
+  if (den->kind == PNP_DEN_SARA) sara_destroy(den);
   delete den;
 }
 
@@ -530,6 +566,7 @@ int denoise(pnp_den* d, const float* x_in, float* x_out, int n) {
   if (!d || !x_in || !x_out || n < 2 || (n & 1)) return fail(PNP_ERR_INVALID_ARG, "bad argument");
   if (x_in == x_out) return fail(PNP_ERR_INVALID_ARG, "x_in and x_out must not alias");
   if (d->kind == PNP_DEN_HAAR) return haar_denoise_dev(d->stream, x_in, x_out, n, (float)d->t, nullptr, nullptr);
+  if (d->kind == PNP_DEN_SARA) return sara_denoise(d, d->stream, x_in, x_out, n, nullptr, nullptr);
   return cnn_denoise(d, d->stream, x_in, x_out, n, nullptr, nullptr);
 }
 

@@ -1,0 +1,388 @@
+// uSARA's handcrafted denoiser (App. B): the prox of gamma lambda ||W Psi^T x||_1 + iota_+(x) for
+// the SARA dictionary Psi (the Dirac basis and the 2-D Daubechies bases db1..db8, each a multi-level
+// separable DWT with periodic extension, divided by 3 so that Psi Psi^T = I), by dual
+// forward-backward sub-iterations:
+//   x = max(0, z - Psi u),   u <- clip(u + Psi^T x, -t, t),   t = gamma lambda w,
+// warm-started from the previous call's u, and the reweighting w = rho / (rho + |Psi^T x|) that
+// majorises the log-sum prior at the current image.
+//
+// Each DWT level is one pass along each axis over the level's m x m block: analysis
+// a[j] = sum_k f[k] x[(2 j + k) mod m] (low half, then high half), synthesis as the gather
+// x[p] = sum_{k : p - k even} lo[k] a[((p - k) mod m) / 2] + hi[k] d[((p - k) mod m) / 2].
+// The Daubechies filters are computed on the host by spectral factorisation (minimum-phase roots
+// of z^(N-1) P_N((2 - z - 1/z) / 4), Durand-Kerner iteration with Newton polish).
+#include <complex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pnp {
+namespace {
+
+constexpr int SARA_FILTERS = 8, SARA_BASES = 9, MAXTAP = 16;
+
+struct SaraState {
+  int n = 0, levels = 0, iters = 0;
+  double gl = 0, rho = 0;   // gamma lambda (threshold scale), log-sum floor
+  float* filt = nullptr;    // [8][2][16]: low-pass, high-pass (zero padded)
+  int len[SARA_FILTERS] = {};
+  float *u = nullptr, *w = nullptr;            // 9 n^2: dual variable, weights
+  float *A = nullptr, *T = nullptr, *S = nullptr, *X = nullptr;  // n^2 work images
+};
+
+using cd = std::complex<double>;
+
+std::vector<double> polymul(const std::vector<double>& a, const std::vector<double>& b) {
+  std::vector<double> r(a.size() + b.size() - 1, 0.0);
+  for (size_t i = 0; i < a.size(); ++i)
+    for (size_t j = 0; j < b.size(); ++j) r[i + j] += a[i] * b[j];
+  return r;
+}
+
+cd polyval(const std::vector<double>& c, cd z) {  // highest power first
+  cd v = 0.0;
+  for (double a : c) v = v * z + a;
+  return v;
+}
+
+// low-pass filter of the orthonormal Daubechies wavelet with N vanishing moments (length 2N)
+std::vector<double> daubechies(int N) {
+  if (N == 1) return {1.0 / std::sqrt(2.0), 1.0 / std::sqrt(2.0)};
+  const std::vector<double> yz = {-0.25, 0.5, -0.25};  // y z with y = (2 - z - 1/z) / 4
+  std::vector<double> Q(2 * N - 1, 0.0);
+  for (int k = 0; k < N; ++k) {
+    std::vector<double> term = {1.0};
+    for (int i = 0; i < k; ++i) term = polymul(term, yz);
+    term.resize(term.size() + (N - 1 - k), 0.0);  // times z^(N-1-k)
+    double binom = 1.0;                          // C(N-1+k, k)
+    for (int i = 1; i <= k; ++i) binom = binom * (N - 1 + i) / i;
+    const size_t off = Q.size() - term.size();
+    for (size_t i = 0; i < term.size(); ++i) Q[off + i] += binom * term[i];
+  }
+  const int d = (int)Q.size() - 1;
+  std::vector<double> a(Q);
+  for (double& v : a) v /= Q[0];
+  std::vector<cd> r(d);
+  for (int i = 0; i < d; ++i) r[i] = std::pow(cd(0.4, 0.9), i);
+  for (int it = 0; it < 2000; ++it) {  // Durand-Kerner
+    double step = 0.0;
+    for (int i = 0; i < d; ++i) {
+      cd den = 1.0;
+      for (int j = 0; j < d; ++j)
+        if (j != i) den *= r[i] - r[j];
+      const cd dz = polyval(a, r[i]) / den;
+      r[i] -= dz;
+      step = std::max(step, std::abs(dz));
+    }
+    if (step < 1e-15) break;
+  }
+  std::vector<double> da(d);  // derivative, for the Newton polish
+  for (int i = 0; i < d; ++i) da[i] = a[i] * (d - i);
+  for (int it = 0; it < 3; ++it)
+    for (cd& z : r) z -= polyval(a, z) / polyval(da, z);
+  std::vector<cd> L = {1.0};
+  for (const cd& z : r)
+    if (std::abs(z) < 1.0) {
+      std::vector<cd> nl(L.size() + 1, 0.0);
+      for (size_t i = 0; i < L.size(); ++i) {
+        nl[i] += L[i];
+        nl[i + 1] -= L[i] * z;
+      }
+      L.swap(nl);
+    }
+  std::vector<double> h(L.size());
+  for (size_t i = 0; i < L.size(); ++i) h[i] = L[i].real();
+  for (int i = 0; i < N; ++i) h = polymul(h, {1.0, 1.0});
+  double s = 0.0;
+  for (double v : h) s += v;
+  for (double& v : h) v *= std::sqrt(2.0) / s;
+  return h;
+}
+
+// analysis along axis 0 of the m x m block (row stride n): out[j][c] low, out[m/2 + j][c] high
+__global__ void dwt_axis0(const float* __restrict__ in, float* __restrict__ out, int n, int m,
+                          const float* __restrict__ f, int L) {
+  const int half = m / 2;
+  const int64_t total = (int64_t)half * m;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / m), c = (int)(idx % m);
+    float sl = 0.f, sh = 0.f;
+    for (int k = 0; k < L; ++k) {
+      const float v = in[(int64_t)((2 * j + k) % m) * n + c];
+      sl = fmaf(f[k], v, sl);
+      sh = fmaf(f[MAXTAP + k], v, sh);
+    }
+    out[(int64_t)j * n + c] = sl;
+    out[(int64_t)(half + j) * n + c] = sh;
+  }
+}
+
+// analysis along axis 1: out[i][j] low, out[i][m/2 + j] high
+__global__ void dwt_axis1(const float* __restrict__ in, float* __restrict__ out, int n, int m,
+                          const float* __restrict__ f, int L) {
+  const int half = m / 2;
+  const int64_t total = (int64_t)m * half;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / half), j = (int)(idx % half);
+    const float* row = in + (int64_t)i * n;
+    float sl = 0.f, sh = 0.f;
+    for (int k = 0; k < L; ++k) {
+      const float v = row[(2 * j + k) % m];
+      sl = fmaf(f[k], v, sl);
+      sh = fmaf(f[MAXTAP + k], v, sh);
+    }
+    out[(int64_t)i * n + j] = sl;
+    out[(int64_t)i * n + half + j] = sh;
+  }
+}
+
+// synthesis along axis 1: out[i][p] = sum_{k: p - k even} lo[k] in[i][j] + hi[k] in[i][m/2 + j]
+__global__ void idwt_axis1(const float* __restrict__ in, float* __restrict__ out, int n, int m,
+                           const float* __restrict__ f, int L) {
+  const int half = m / 2;
+  const int64_t total = (int64_t)m * m;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / m), p = (int)(idx % m);
+    const float* row = in + (int64_t)i * n;
+    float acc = 0.f;
+    for (int k = (p & 1); k < L; k += 2) {
+      const int j = ((((p - k) % m) + m) % m) / 2;
+      acc = fmaf(f[k], row[j], fmaf(f[MAXTAP + k], row[half + j], acc));
+    }
+    out[(int64_t)i * n + p] = acc;
+  }
+}
+
+// synthesis along axis 0: out[p][c] = sum_{k: p - k even} lo[k] in[j][c] + hi[k] in[m/2 + j][c]
+__global__ void idwt_axis0(const float* __restrict__ in, float* __restrict__ out, int n, int m,
+                           const float* __restrict__ f, int L) {
+  const int half = m / 2;
+  const int64_t total = (int64_t)m * m;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(idx / m), c = (int)(idx % m);
+    float acc = 0.f;
+    for (int k = (p & 1); k < L; k += 2) {
+      const int j = ((((p - k) % m) + m) % m) / 2;
+      acc = fmaf(f[k], in[(int64_t)j * n + c], fmaf(f[MAXTAP + k], in[(int64_t)(half + j) * n + c], acc));
+    }
+    out[(int64_t)p * n + c] = acc;
+  }
+}
+
+// mode 0: s = v / 3;  mode 1: s += v / 3;  mode 2: x = max(0, z - (s + v / 3))
+__global__ void sara_accum(const float* __restrict__ v, float* __restrict__ s, const float* __restrict__ z,
+                           float* __restrict__ x, int64_t count, int mode) {
+  const float third = 1.f / 3.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const float a = v[i] * third;
+    if (mode == 0) s[i] = a;
+    else if (mode == 1) s[i] += a;
+    else x[i] = fmaxf(0.f, z[i] - (s[i] + a));
+  }
+}
+
+__global__ void sara_third(float* __restrict__ c, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    c[i] *= 1.f / 3.f;
+}
+
+// u = clip(u + c / 3, -gl w, gl w)  (the dual step; c = B_b x)
+__global__ void sara_dual(float* __restrict__ u, const float* __restrict__ c, const float* __restrict__ w, float gl,
+                          int64_t count) {
+  const float third = 1.f / 3.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const float t = gl * w[i];
+    u[i] = fminf(t, fmaxf(-t, u[i] + c[i] * third));
+  }
+}
+
+// w = rho / (rho + |c / 3|)
+__global__ void sara_weights(const float* __restrict__ c, float* __restrict__ w, float rho, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    w[i] = rho / (rho + fabsf(c[i] * (1.f / 3.f)));
+}
+
+__global__ void __launch_bounds__(256) sara_norms(const float* __restrict__ x, const float* __restrict__ prev,
+                                                  int64_t count, double* acc) {
+  __shared__ double r0[256], r1[256];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i], d = v - (prev ? prev[i] : 0.f);
+    a += d * d;
+    b += v * v;
+  }
+  r0[threadIdx.x] = a;
+  r1[threadIdx.x] = b;
+  __syncthreads();
+  for (int k = blockDim.x >> 1; k > 0; k >>= 1) {
+    if (threadIdx.x < k) {
+      r0[threadIdx.x] += r0[threadIdx.x + k];
+      r1[threadIdx.x] += r1[threadIdx.x + k];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&acc[0], r0[0]);
+    atomicAdd(&acc[1], r1[0]);
+  }
+}
+
+int grid1(int64_t count) { return (int)std::min<int64_t>((count + 255) / 256, 4096); }
+
+// c = B_b x for basis b (1..8) of the n x n image x (c may not alias x)
+int basis_analysis(SaraState* S, cudaStream_t s, int b, const float* x, float* c) {
+  const int n = S->n;
+  const float* f = S->filt + (size_t)(b - 1) * 2 * MAXTAP;
+  const int L = S->len[b - 1];
+  PNP_CUDA(cudaMemcpyAsync(c, x, (size_t)n * n * 4, cudaMemcpyDeviceToDevice, s));
+  for (int l = 0; l < S->levels; ++l) {
+    const int m = n >> l;
+    dwt_axis0<<<grid1((int64_t)m * m / 2), 256, 0, s>>>(c, S->T, n, m, f, L);
+    PNP_CHECK_LAUNCH();
+    dwt_axis1<<<grid1((int64_t)m * m / 2), 256, 0, s>>>(S->T, c, n, m, f, L);
+    PNP_CHECK_LAUNCH();
+  }
+  return PNP_OK;
+}
+
+// x = B_b^T c (x may not alias c; S->T is scratch)
+int basis_synthesis(SaraState* S, cudaStream_t s, int b, const float* c, float* x) {
+  const int n = S->n;
+  const float* f = S->filt + (size_t)(b - 1) * 2 * MAXTAP;
+  const int L = S->len[b - 1];
+  PNP_CUDA(cudaMemcpyAsync(x, c, (size_t)n * n * 4, cudaMemcpyDeviceToDevice, s));
+  for (int l = S->levels - 1; l >= 0; --l) {
+    const int m = n >> l;
+    idwt_axis1<<<grid1((int64_t)m * m), 256, 0, s>>>(x, S->T, n, m, f, L);
+    PNP_CHECK_LAUNCH();
+    idwt_axis0<<<grid1((int64_t)m * m), 256, 0, s>>>(S->T, x, n, m, f, L);
+    PNP_CHECK_LAUNCH();
+  }
+  return PNP_OK;
+}
+
+// x = max(0, z - Psi u)
+int primal(SaraState* S, cudaStream_t s, const float* z, float* x) {
+  const int64_t N = (int64_t)S->n * S->n;
+  sara_accum<<<grid1(N), 256, 0, s>>>(S->u, S->S, nullptr, nullptr, N, 0);
+  PNP_CHECK_LAUNCH();
+  for (int b = 1; b < SARA_BASES; ++b) {
+    if (int rc = basis_synthesis(S, s, b, S->u + (size_t)b * N, S->A)) return rc;
+    sara_accum<<<grid1(N), 256, 0, s>>>(S->A, S->S, z, x, N, b == SARA_BASES - 1 ? 2 : 1);
+    PNP_CHECK_LAUNCH();
+  }
+  return PNP_OK;
+}
+
+}  // namespace
+
+int sara_create(pnp_den* d, int n, int levels, double gl, double rho, int iters) {
+  SaraState* S = new SaraState();
+  S->n = n;
+  S->levels = levels;
+  S->iters = iters;
+  S->gl = gl;
+  S->rho = rho;
+  std::vector<float> filt((size_t)SARA_FILTERS * 2 * MAXTAP, 0.f);
+  for (int N = 1; N <= SARA_FILTERS; ++N) {
+    const std::vector<double> h = daubechies(N);
+    const int L = (int)h.size();
+    if (L != 2 * N) {  // the factorisation must keep exactly N - 1 roots inside the unit circle
+      d->impl = S;
+      return fail(PNP_ERR_UNSUPPORTED, "internal: Daubechies factorisation failed for N = " + std::to_string(N));
+    }
+    S->len[N - 1] = L;
+    for (int k = 0; k < L; ++k) {
+      filt[(size_t)(N - 1) * 2 * MAXTAP + k] = (float)h[k];
+      filt[(size_t)(N - 1) * 2 * MAXTAP + MAXTAP + k] = (float)((k & 1 ? -1.0 : 1.0) * h[L - 1 - k]);
+    }
+  }
+  const size_t N2 = (size_t)n * n;
+  bool ok = cudaMalloc(&S->filt, filt.size() * 4) == cudaSuccess &&
+            cudaMalloc(&S->u, SARA_BASES * N2 * 4) == cudaSuccess &&
+            cudaMalloc(&S->w, SARA_BASES * N2 * 4) == cudaSuccess && cudaMalloc(&S->A, N2 * 4) == cudaSuccess &&
+            cudaMalloc(&S->T, N2 * 4) == cudaSuccess && cudaMalloc(&S->S, N2 * 4) == cudaSuccess &&
+            cudaMalloc(&S->X, N2 * 4) == cudaSuccess;
+  d->impl = S;
+  if (!ok) {
+    cudaGetLastError();
+    return fail(PNP_ERR_OOM, "SARA denoiser allocation failed");
+  }
+  PNP_CUDA(cudaMemcpy(S->filt, filt.data(), filt.size() * 4, cudaMemcpyHostToDevice));
+  PNP_CUDA(cudaMemset(S->u, 0, SARA_BASES * N2 * 4));
+  std::vector<float> ones(SARA_BASES * N2, 1.f);
+  PNP_CUDA(cudaMemcpy(S->w, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice));
+  return PNP_OK;
+}
+
+void sara_destroy(pnp_den* d) {
+  SaraState* S = static_cast<SaraState*>(d->impl);
+  if (!S) return;
+  for (float* p : {S->filt, S->u, S->w, S->A, S->T, S->S, S->X}) cudaFree(p);
+  delete S;
+  d->impl = nullptr;
+}
+
+// the prox by S->iters dual-FB iterations from the kept u; out = x; FP64 norms into acc[0..1]
+int sara_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc, const float* x_prev) {
+  SaraState* S = static_cast<SaraState*>(d->impl);
+  if (!S || n != S->n) return fail(PNP_ERR_INVALID_ARG, "image side differs from the SARA denoiser's");
+  const int64_t N = (int64_t)n * n;
+  if (int rc = primal(S, s, z, out)) return rc;
+  for (int it = 0; it < S->iters; ++it) {
+    sara_dual<<<grid1(N), 256, 0, s>>>(S->u, out, S->w, (float)S->gl, N);  // the Dirac basis
+    PNP_CHECK_LAUNCH();
+    for (int b = 1; b < SARA_BASES; ++b) {
+      if (int rc = basis_analysis(S, s, b, out, S->A)) return rc;
+      sara_dual<<<grid1(N), 256, 0, s>>>(S->u + (size_t)b * N, S->A, S->w + (size_t)b * N, (float)S->gl, N);
+      PNP_CHECK_LAUNCH();
+    }
+    if (int rc = primal(S, s, z, out)) return rc;
+  }
+  if (acc) {
+    sara_norms<<<grid1(N), 256, 0, s>>>(out, x_prev, N, acc);
+    PNP_CHECK_LAUNCH();
+  }
+  return PNP_OK;
+}
+
+int sara_reweight(pnp_den* d, const float* x) {
+  SaraState* S = static_cast<SaraState*>(d->impl);
+  const int64_t N = (int64_t)S->n * S->n;
+  cudaStream_t s = d->stream;
+  sara_weights<<<grid1(N), 256, 0, s>>>(x, S->w, (float)S->rho, N);
+  PNP_CHECK_LAUNCH();
+  for (int b = 1; b < SARA_BASES; ++b) {
+    if (int rc = basis_analysis(S, s, b, x, S->A)) return rc;
+    sara_weights<<<grid1(N), 256, 0, s>>>(S->A, S->w + (size_t)b * N, (float)S->rho, N);
+    PNP_CHECK_LAUNCH();
+  }
+  return PNP_OK;
+}
+
+// direction 1: out (9 n^2) = Psi^T in;  direction -1: out (n^2) = Psi in
+int sara_transform(pnp_den* d, const float* in, float* out, int direction) {
+  SaraState* S = static_cast<SaraState*>(d->impl);
+  const int64_t N = (int64_t)S->n * S->n;
+  cudaStream_t s = d->stream;
+  if (direction > 0) {
+    for (int b = 0; b < SARA_BASES; ++b) {
+      float* c = out + (size_t)b * N;
+      if (b == 0) PNP_CUDA(cudaMemcpyAsync(c, in, N * 4, cudaMemcpyDeviceToDevice, s));
+      else if (int rc = basis_analysis(S, s, b, in, c)) return rc;
+      sara_third<<<grid1(N), 256, 0, s>>>(c, N);
+      PNP_CHECK_LAUNCH();
+    }
+  } else {
+    sara_accum<<<grid1(N), 256, 0, s>>>(in, out, nullptr, nullptr, N, 0);
+    PNP_CHECK_LAUNCH();
+    for (int b = 1; b < SARA_BASES; ++b) {
+      if (int rc = basis_synthesis(S, s, b, in + (size_t)b * N, S->A)) return rc;
+      sara_accum<<<grid1(N), 256, 0, s>>>(S->A, out, nullptr, nullptr, N, 1);
+      PNP_CHECK_LAUNCH();
+    }
+  }
+  return PNP_OK;
+}
+
+}  // namespace pnp

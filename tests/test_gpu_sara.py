@@ -1,0 +1,65 @@
+"""GPU uSARA denoiser (App. B) against the SARA oracle: dictionary, prox, reweighting, FB loop."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fb as ofb
+from oracle import nufft as onu
+from oracle import sara as osa
+
+from gpu_common import pnp, rel_l2, require_gpu, to_dev_c64, to_dev_f32, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def test_sara_dictionary_matches_oracle():
+    n = 64
+    x = np.random.default_rng(1).standard_normal((n, n))
+    den = pnp.SaraDenoiser(n, 0.1, 0.1, 1, levels=4)
+    c = to_host(den.analysis(to_dev_f32(x)))
+    psi = osa.Sara(levels=4)
+    ref = psi.analysis(x)
+    assert rel_l2(c, ref) <= 1e-6
+    back = to_host(den.synthesis(to_dev_f32(ref.astype(np.float32))))
+    assert rel_l2(back, psi.synthesis(ref.astype(np.float32).astype(np.float64))) <= 1e-6
+
+
+@pytest.mark.parametrize("reweight", [False, True])
+def test_sara_prox_matches_oracle(reweight):
+    n, gl, iters = 64, 0.05, 25
+    rng = np.random.default_rng(2)
+    z = rng.standard_normal((n, n)) + 0.3
+    den = pnp.SaraDenoiser(n, gl, gl, iters, levels=4)
+    psi = osa.Sara(levels=4)
+    w = np.ones((9, n, n))
+    if reweight:
+        xw = np.maximum(rng.standard_normal((n, n)), 0).astype(np.float32)
+        den.reweight(to_dev_f32(xw))
+        w = osa.reweighting_weights(psi.analysis(xw.astype(np.float64)), gl)
+    x = to_host(den.denoise(to_dev_f32(z)))
+    ref, _, _ = osa.prox_weighted_l1_pos(psi, z.astype(np.float32).astype(np.float64), gl * w, iters, 0.0)
+    assert rel_l2(x, ref) <= 1e-5
+
+
+def test_usara_fb_loop_matches_oracle():
+    n, K, M, iters, prox_iters = 64, 128, 20000, 8, 10
+    prob = synth.make_problem("C0", M=M, n=n, K=K)
+    ora = onu.Operator(n, K, prob["omega"])
+    y0 = ora.forward(prob["x_true"])
+    tau = synth.noise_std_for_isnr(np.linalg.norm(y0), M, prob["isnr_db"])
+    y = y0 + tau * prob["noise"]
+    L, _, _ = ofb.power_iteration(ora, synth.rng_for("power").standard_normal((n, n)), 1000, 1e-10)
+    gamma = ofb.step_size(L)
+    gl = ofb.soft_threshold_from_noise(tau, L)
+    x_ref = osa.usara(ora, y, gamma, gl, gl, 0, iters, prox_iters=prox_iters, psi=osa.Sara(levels=4),
+                      prox_tol=0.0)
+    plan = pnp.Plan(n, K, prob["omega"])
+    den = pnp.SaraDenoiser(n, gl, gl, prox_iters, levels=4)
+    x, st = plan.fb_run(den, to_dev_c64(y), gamma=gamma, L=L, max_iter=iters, check_every=4)
+    assert st.iters == iters
+    assert rel_l2(to_host(x), x_ref) <= 1e-4
