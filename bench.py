@@ -63,6 +63,8 @@ def parse():
                     help="w-stacks of the stacked-operator comparison line (0 skips it)")
     ap.add_argument("--holo-rows", type=int, default=20_000_000,
                     help="rows of the 256^2 / 512^2 holographic comparison line (0 skips it)")
+    ap.add_argument("--usara-prox-iters", type=int, default=10,
+                    help="dual-FB iterations per uSARA denoise in its comparison line (0 skips it)")
     ap.add_argument("--kernel-case", choices=["gridding", "cnn", "fft"], default=None,
                     help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
     ap.add_argument("--cnn-side", type=int, default=4096,
@@ -450,6 +452,26 @@ def run_gpu(args):
             "phi_rel_l2_vs_unstacked": err, "plan_build_s": t_plan, "gridding_autotune": tune_ws}
         plan_ws.close()
         del plan_ws, y_ws, xw
+    if args.usara_prox_iters > 0:
+        # uSARA (App. B) on the same operator: the SARA prox by dual FB, gamma lambda = rho = tau / sqrt(2L)
+        try:
+            sara = pnp.SaraDenoiser(n, t, t, args.usara_prox_iters, levels=4, stream=stream)
+            xu = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+            plan.fb_run(sara, y, x0=xu, gamma=gamma, L=L, max_iter=4, check_every=2, use_graph=True, inplace=True)
+            ms_u, _ = _timed_loop(plan, sara, y, xu, gamma, L, steps, stream)
+            sara.close()
+            sara = pnp.SaraDenoiser(n, t, t, args.usara_prox_iters, levels=4, stream=stream)
+            xu.zero_()
+            _, trace_u = _run_to_snr(plan, sara, y, xu, gamma, L, x_true, 1.0, None, SNR_ITERS)
+            comparison["usara"] = {
+                "prox_iters": args.usara_prox_iters, "reweighting": "none in the timed loop (weights 1)",
+                "iter_per_s": ws * steps / (ms_u / 1e3), "ms_per_iter": ms_u / steps,
+                "snr_db_after_%d" % SNR_ITERS: trace_u[-1][1],
+                "snr_trace": [(i, round(s, 3)) for i, s in trace_u[4::5]]}
+            sara.close()
+            del xu
+        except Exception as e:  # a comparison line; the headline above stands without it
+            comparison["usara"] = {"error": f"{type(e).__name__}: {e}"}
     if args.holo_rows > 0:
         # App. E, Eq. phidagphi: with many rows per grid cell the holographic H = G^H G is far smaller
         # than G; the 256^2 image / 512^2 grid layout with M rows (KB J = 7), plain loop with G vs with H
