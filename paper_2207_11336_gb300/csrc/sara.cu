@@ -11,10 +11,10 @@
 // x[p] = sum_{k : p - k even} lo[k] a[((p - k) mod m) / 2] + hi[k] d[((p - k) mod m) / 2].
 // The Daubechies filters are computed on the host by spectral factorisation (minimum-phase roots
 // of z^(N-1) P_N((2 - z - 1/z) / 4), Durand-Kerner iteration with Newton polish).
-#include <complex>
 #include <vector>
 
 #include "common.cuh"
+#include "daubechies.h"
 
 namespace pnp {
 namespace {
@@ -29,75 +29,6 @@ struct SaraState {
   float *u = nullptr, *w = nullptr;            // 9 n^2: dual variable, weights
   float *A = nullptr, *T = nullptr, *S = nullptr, *X = nullptr;  // n^2 work images
 };
-
-using cd = std::complex<double>;
-
-std::vector<double> polymul(const std::vector<double>& a, const std::vector<double>& b) {
-  std::vector<double> r(a.size() + b.size() - 1, 0.0);
-  for (size_t i = 0; i < a.size(); ++i)
-    for (size_t j = 0; j < b.size(); ++j) r[i + j] += a[i] * b[j];
-  return r;
-}
-
-cd polyval(const std::vector<double>& c, cd z) {  // highest power first
-  cd v = 0.0;
-  for (double a : c) v = v * z + a;
-  return v;
-}
-
-// low-pass filter of the orthonormal Daubechies wavelet with N vanishing moments (length 2N)
-std::vector<double> daubechies(int N) {
-  if (N == 1) return {1.0 / std::sqrt(2.0), 1.0 / std::sqrt(2.0)};
-  const std::vector<double> yz = {-0.25, 0.5, -0.25};  // y z with y = (2 - z - 1/z) / 4
-  std::vector<double> Q(2 * N - 1, 0.0);
-  for (int k = 0; k < N; ++k) {
-    std::vector<double> term = {1.0};
-    for (int i = 0; i < k; ++i) term = polymul(term, yz);
-    term.resize(term.size() + (N - 1 - k), 0.0);  // times z^(N-1-k)
-    double binom = 1.0;                          // C(N-1+k, k)
-    for (int i = 1; i <= k; ++i) binom = binom * (N - 1 + i) / i;
-    const size_t off = Q.size() - term.size();
-    for (size_t i = 0; i < term.size(); ++i) Q[off + i] += binom * term[i];
-  }
-  const int d = (int)Q.size() - 1;
-  std::vector<double> a(Q);
-  for (double& v : a) v /= Q[0];
-  std::vector<cd> r(d);
-  for (int i = 0; i < d; ++i) r[i] = std::pow(cd(0.4, 0.9), i);
-  for (int it = 0; it < 2000; ++it) {  // Durand-Kerner
-    double step = 0.0;
-    for (int i = 0; i < d; ++i) {
-      cd den = 1.0;
-      for (int j = 0; j < d; ++j)
-        if (j != i) den *= r[i] - r[j];
-      const cd dz = polyval(a, r[i]) / den;
-      r[i] -= dz;
-      step = std::max(step, std::abs(dz));
-    }
-    if (step < 1e-15) break;
-  }
-  std::vector<double> da(d);  // derivative, for the Newton polish
-  for (int i = 0; i < d; ++i) da[i] = a[i] * (d - i);
-  for (int it = 0; it < 3; ++it)
-    for (cd& z : r) z -= polyval(a, z) / polyval(da, z);
-  std::vector<cd> L = {1.0};
-  for (const cd& z : r)
-    if (std::abs(z) < 1.0) {
-      std::vector<cd> nl(L.size() + 1, 0.0);
-      for (size_t i = 0; i < L.size(); ++i) {
-        nl[i] += L[i];
-        nl[i + 1] -= L[i] * z;
-      }
-      L.swap(nl);
-    }
-  std::vector<double> h(L.size());
-  for (size_t i = 0; i < L.size(); ++i) h[i] = L[i].real();
-  for (int i = 0; i < N; ++i) h = polymul(h, {1.0, 1.0});
-  double s = 0.0;
-  for (double v : h) s += v;
-  for (double& v : h) v *= std::sqrt(2.0) / s;
-  return h;
-}
 
 // analysis along axis 0 of the m x m block (row stride n): out[j][c] low, out[m/2 + j][c] high
 __global__ void dwt_axis0(const float* __restrict__ in, float* __restrict__ out, int n, int m,
@@ -179,6 +110,11 @@ __global__ void sara_accum(const float* __restrict__ v, float* __restrict__ s, c
     else if (mode == 1) s[i] += a;
     else x[i] = fmaxf(0.f, z[i] - (s[i] + a));
   }
+}
+
+__global__ void sara_fill(float* __restrict__ p, int64_t count, float v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = v;
 }
 
 __global__ void sara_third(float* __restrict__ c, int64_t count) {
@@ -285,7 +221,7 @@ int sara_create(pnp_den* d, int n, int levels, double gl, double rho, int iters)
   S->rho = rho;
   std::vector<float> filt((size_t)SARA_FILTERS * 2 * MAXTAP, 0.f);
   for (int N = 1; N <= SARA_FILTERS; ++N) {
-    const std::vector<double> h = daubechies(N);
+    const std::vector<double> h = daub::daubechies(N);
     const int L = (int)h.size();
     if (L != 2 * N) {  // the factorisation must keep exactly N - 1 roots inside the unit circle
       d->impl = S;
@@ -310,8 +246,9 @@ int sara_create(pnp_den* d, int n, int levels, double gl, double rho, int iters)
   }
   PNP_CUDA(cudaMemcpy(S->filt, filt.data(), filt.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemset(S->u, 0, SARA_BASES * N2 * 4));
-  std::vector<float> ones(SARA_BASES * N2, 1.f);
-  PNP_CUDA(cudaMemcpy(S->w, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice));
+  sara_fill<<<grid1((int64_t)(SARA_BASES * N2)), 256>>>(S->w, (int64_t)(SARA_BASES * N2), 1.f);  // w = 1
+  PNP_CHECK_LAUNCH();
+  PNP_CUDA(cudaDeviceSynchronize());
   return PNP_OK;
 }
 
