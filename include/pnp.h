@@ -258,7 +258,7 @@ int pnp_den_create_cnn(pnp_den** den, const float* weights_host,
  * at x (Eq. lambda: gamma_lambda = tau / sqrt(2L), rho = gamma_lambda).
  *  n          image side, a multiple of 2^levels with n / 2^levels >= 1;  levels in [1, 8]
  *  prox_iters >= 1
- * Device memory: 2 x 9 n^2 + 5 n^2 floats.  Used by denoise() and pnp_fb_run like the others. */
+ * Device memory: 2 x 9 n^2 + 4 n^2 floats.  Used by denoise() and pnp_fb_run like the others. */
 int pnp_den_create_sara(pnp_den** den, int n, int levels, double gamma_lambda, double rho, int prox_iters,
                         void* stream);
 /* w = rho / (rho + |Psi^T x|) for the device n x n image x (the reweighting step of uSARA). */
