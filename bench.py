@@ -38,11 +38,9 @@ sys.path.insert(0, ROOT)
 METRIC = "PnP-FB iter/s (4096² img, 2e7 vis), learned vs plain at equal SNR (dB)"
 UNIT = "iter/s"
 WORKLOADS = {
-    "C3": dict(name="C3", desc="4096^2 image, 8192^2 grid, M=2e7 vis in 64 radial blocks, "
-                               "w-folded G J{7,9,12,16} c64+int32, Haar prox"),
-    "C1": dict(name="C1", desc="2048^2 image, 4096^2 grid, M=2e7 vis, w-folded G J{7,9,12,16} "
-                               "c64+int32, Haar prox"),
-    "C0": dict(name="C0", desc="256^2 image, 512^2 grid, M=2e5 vis, KB J=7, Haar prox"),
+    "C3": dict(name="C3", desc="4096^2 img, 8192^2 grid, 2e7 vis in 64 blocks, Briggs r0, w-folded G J7-16 c64"),
+    "C1": dict(name="C1", desc="2048^2 img, 4096^2 grid, 2e7 vis, w-folded G J7-16 c64"),
+    "C0": dict(name="C0", desc="256^2 img, 512^2 grid, 2e5 vis, KB J7"),
 }
 BLOCKS = {"C3": 64, "C1": 1, "C0": 1}
 CPU_SAMPLE_ROWS = 4000
@@ -65,6 +63,13 @@ def parse():
                     help="rows of the 256^2 / 512^2 holographic comparison line (0 skips it)")
     ap.add_argument("--usara-prox-iters", type=int, default=10,
                     help="dual-FB iterations per uSARA denoise in its comparison line (0 skips it)")
+    ap.add_argument("--usara-iters", type=int, default=300, help="uSARA iterations for its SNR trace")
+    ap.add_argument("--usara-reweight-every", type=int, default=100,
+                    help="FB iterations per weighted-l1 surrogate of uSARA (log-sum reweighting)")
+    ap.add_argument("--converge-iters", type=int, default=2000,
+                    help="iterations of the plain loop whose final SNR (minus 0.5 dB) is the time-to-SNR target")
+    ap.add_argument("--no-fne", dest="fne", action="store_false",
+                    help="skip the learned loop with the penalised network")
     ap.add_argument("--kernel-case", choices=["gridding", "cnn", "fft"], default=None,
                     help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
     ap.add_argument("--cnn-side", type=int, default=4096,
@@ -197,7 +202,7 @@ def profiled_traffic(kernel_file: str, workload: str):
 CNN_TILE = 96   # side of the image tile the FP64 oracle network is timed on
 
 
-def oracle_sample(prob, rows, x, y_rows, gamma, t, cnn=None):
+def oracle_sample(prob, rows, x, y_rows, gamma, t, cnn=None, row_scale=None):
     """Time one oracle PnP-FB iteration on a row sample of G; returns (s/iter estimate, parts).
 
     With ``cnn`` = (params, pixels) the denoiser is the FP64 oracle network, timed on a
@@ -207,7 +212,7 @@ def oracle_sample(prob, rows, x, y_rows, gamma, t, cnn=None):
     from oracle import nufft as onu
     n, K, M = prob["n"], prob["K"], prob["M"]
     gs = onu.GridSpec(n, K)
-    G = onu.degridding_matrix(gs, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"], rows)
+    G = onu.degridding_matrix(gs, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"], rows, row_scale)
     GH = G.conj().T.tocsr()
     t0 = time.perf_counter()
     Xh = onu.dft2(onu.zero_pad(gs, x)).ravel()
@@ -241,10 +246,8 @@ def cpu_sample_inputs(prob, x_dev_np, y_np):
 
 # ---------------------------------------------------------------- reference arm
 def workload_desc(wl, learned):
-    """The workload's description with the denoiser the timed loop applies."""
-    if not learned:
-        return wl["desc"]
-    return wl["desc"].replace(", Haar prox", "") + ", learned faceted CNN denoiser (4x4 facets, halo 32)"
+    """The workload's description with the denoiser the timed loop applies (one string for both arms)."""
+    return wl["desc"] + (", CNN 4x4 facets" if learned else ", Haar")
 
 
 def run_reference(args):
@@ -260,11 +263,13 @@ def run_reference(args):
     # the oracle's y on the sampled rows (noise-free sky model + scaled noise)
     rows, _ = cpu_sample_inputs(prob, None, np.zeros(M, complex))
     gs = onu.GridSpec(n, K)
+    wimg = prob.get("imaging_weight")
+    d = None if wimg is None else np.sqrt(wimg)
     Xt = onu.dft2(onu.zero_pad(gs, prob["x_true"])).ravel()
-    G = onu.degridding_matrix(gs, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"], rows)
+    G = onu.degridding_matrix(gs, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"], rows, d)
     y_rows = G @ Xt + 1e-3 * prob["noise"][rows]
     gamma, t = 1.0 / M, 1e-6
-    cnn, desc = None, wl["desc"]
+    cnn, desc = None, workload_desc(wl, False)
     if os.path.exists(WEIGHTS) and "facet_rows" in prob:   # the same loop as the GPU arm times
         from paper_2207_11336_gb300.train_denoiser import load as load_weights
         params, _ = load_weights(WEIGHTS)
@@ -272,13 +277,14 @@ def run_reference(args):
         desc = workload_desc(wl, True)
     times = []
     for i in range(args.warmup + args.steps):
-        est, _ = oracle_sample(prob, rows, x, y_rows, gamma, t, cnn)
+        est, _ = oracle_sample(prob, rows, x, y_rows, gamma, t, cnn, d)
         if i >= args.warmup:
             times.append(est)
     total = sum(times)
     val = len(times) / total
-    sample = (f"per step: one FP64 oracle iteration with the full-size FFT pair, G restricted to {CPU_SAMPLE_ROWS} "
-              f"seeded rows (time scaled by M/{CPU_SAMPLE_ROWS})"
+    sample = (f"per step: one FP64 oracle iteration with the full-size FFT pair (scipy.fft on {os.cpu_count()} "
+              f"threads), G restricted to {CPU_SAMPLE_ROWS} seeded rows (scipy CSR, one thread; time scaled by "
+              f"M/{CPU_SAMPLE_ROWS})"
               + (f" and the FP64 network on a {CNN_TILE}^2 tile (time scaled to the facets' pixels)" if cnn else ""))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
@@ -286,7 +292,7 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": desc,
                                             "l2": "inputs larger than L2 (G %.1f GB)"
                                                   % ((prob["J_per_row"].astype(np.int64) ** 2).sum() * 10 / 1e9)},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -296,9 +302,8 @@ def run_reference(args):
 WEIGHTS = os.path.join(ROOT, "paper_2207_11336_gb300", "weights", "dncnn_C3.npz")
 # the same network fine-tuned with the soft firm non-expansiveness penalty of Eq. training_loss
 WEIGHTS_FNE = os.path.join(ROOT, "paper_2207_11336_gb300", "weights", "dncnn_C3_fne.npz")
-SNR_ITERS = 200          # the plain loop's SNR after this many iterations is the target
-SNR_CHUNK = 10           # the learned loop's SNR is checked every SNR_CHUNK iterations
-SNR_MAX_ITERS = 600
+SNR_CHUNK = 10           # loops are run in chunks of this many iterations between SNR readings
+TARGET_MARGIN_DB = 0.5   # time-to-SNR target: the plain loop's converged SNR minus this margin
 
 
 def _snr_db(x_true, x):
@@ -307,7 +312,7 @@ def _snr_db(x_true, x):
     return float(20.0 * torch.log10(torch.linalg.vector_norm(xt) / torch.linalg.vector_norm(xt - x.double())))
 
 
-def _timed_loop(plan, den, y, x, gamma, L, steps, stream, clocks=None):
+def _timed_loop(plan, den, y, x, gamma, L, steps, stream, alpha=1.0):
     """ms for ``steps`` graph-replayed iterations (x updated in place), kernel launches inside."""
     import torch
     import paper_2207_11336_gb300 as pnp
@@ -316,25 +321,39 @@ def _timed_loop(plan, den, y, x, gamma, L, steps, stream, clocks=None):
     torch.cuda.synchronize()
     ev0.record(stream)
     plan.fb_run(den, y, x0=x, gamma=gamma, L=L, max_iter=steps, check_every=steps, use_graph=True,
-                inplace=True)
+                inplace=True, alpha=alpha)
     ev1.record(stream)
     torch.cuda.synchronize()
     return ev0.elapsed_time(ev1), pnp.kernel_launches() - k0
 
 
-def _run_to_snr(plan, den, y, x, gamma, L, x_true, scale, target, max_iters):
-    """Iterations (multiples of SNR_CHUNK) until SNR(scale * x) >= target; (iters or None, SNR trace)."""
-    trace = []
-    it = 0
+def _run_to_snr(plan, den, y, gamma, L, x_true, alpha, target, max_iters):
+    """Run the loop from x = 0 in chunks of SNR_CHUNK iterations until SNR >= target (or max_iters);
+    returns (iterations to the target or None, [(iterations, SNR dB)], final iterate)."""
+    import torch
+    n = x_true.shape[0]
+    x = torch.zeros((n, n), dtype=torch.float32, device="cuda")
+    trace, it = [], 0
     while it < max_iters:
         plan.fb_run(den, y, x0=x, gamma=gamma, L=L, max_iter=SNR_CHUNK, check_every=SNR_CHUNK,
-                    use_graph=True, inplace=True)
+                    use_graph=True, inplace=True, alpha=alpha)
         it += SNR_CHUNK
-        snr = _snr_db(x_true, scale * x)
+        snr = _snr_db(x_true, x)
         trace.append((it, snr))
         if target is not None and snr >= target:
-            return it, trace
-    return None, trace
+            return it, trace, x
+    return None, trace, x
+
+
+def _first_at(trace, target):
+    for it, snr in trace:
+        if snr >= target:
+            return it
+    return None
+
+
+def _thin(trace, every):
+    return [(i, round(s, 3)) for i, s in trace if i % every == 0 or i == trace[-1][0]]
 
 
 def run_gpu(args):
@@ -354,30 +373,36 @@ def run_gpu(args):
     prob = synth.make_problem(wl["name"])
     n, K, M = prob["n"], prob["K"], prob["M"]
     stream = torch.cuda.current_stream()
+    wimg = prob.get("imaging_weight")
+    d = None if wimg is None else np.sqrt(wimg)   # Sec. 3: Briggs-weighted data, rows of G scaled by sqrt(w)
     plan = pnp.Plan(n, K, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"],
-                    block=prob["block"], nblocks=BLOCKS[wl["name"]], stream=stream)
+                    block=prob["block"], nblocks=BLOCKS[wl["name"]], stream=stream, row_scale=d)
     tune = plan.autotune(reps=2)   # run cap x unit size of the gridding pass, timed on this GPU
     info = plan.info
     x_true = torch.from_numpy(prob["x_true"].astype(np.float32)).cuda()
-    y0 = plan.phi_forward(x_true)
-    norm_y0 = float(torch.linalg.vector_norm(y0.to(torch.complex128)).item())
-    tau = synth.noise_std_for_isnr(norm_y0, M, prob["isnr_db"])
-    noise = torch.from_numpy(prob["noise"].astype(np.complex64)).cuda()
+    y0 = plan.phi_forward(x_true)                       # weighted model data D Phi x
+    y0_raw = y0 if d is None else y0 / torch.from_numpy(d.astype(np.float32)).cuda()
+    norm_y0 = float(torch.linalg.vector_norm(y0_raw.to(torch.complex128)).item())
+    tau = synth.noise_std_for_isnr(norm_y0, M, prob["isnr_db"])   # 40 dB input SNR of the raw data
+    noise = plan.scale_data(torch.from_numpy(prob["noise"].astype(np.complex64)).cuda())
     y = (y0 + tau * noise).contiguous()
+    tau_w = tau * (1.0 if wimg is None else float(np.sqrt(np.mean(wimg))))   # RMS of the weighted noise
     v0 = torch.from_numpy(synth.rng_for("power").standard_normal((n, n)).astype(np.float32)).cuda()
-    hp = heuristics.imaging_parameters(plan, y, tau, v0)
+    hp = heuristics.imaging_parameters(plan, y, tau_w, v0)
     L, gamma, t = hp["L"], hp["gamma"], hp["noise_level"]
     haar = pnp.HaarDenoiser(t, stream=stream)
 
     learned = os.path.exists(WEIGHTS) and "facet_rows" in prob
+    alpha = 1.0
     if learned:
         params, wmeta = load_weights(WEIGHTS)
         cnn = pnp.CnnDenoiser(params, n, facet_rows=prob["facet_rows"], facet_cols=prob["facet_cols"],
                               halo=prob["halo"], stream=stream)
-        # App. C: the problem is divided by alpha so the denoiser sees a peak-normalised image
-        alpha = hp["alpha"]
-        y_s = (y / alpha).contiguous()
-    den, y_run = (cnn, y_s) if learned else (haar, y)
+        # App. C, F: rescale by an upper bound on the peak that also matches the data's noise level to
+        # the one the network was trained at (Eq. sigma); the library applies it (Eq. invpb2)
+        alpha_match = heuristics.alpha_for_denoiser(tau_w, L, float(wmeta["sigma"]))
+        alpha = max(hp["alpha"], alpha_match)
+    den = cnn if learned else haar
 
     def barrier():
         if dist is not None:
@@ -386,31 +411,35 @@ def run_gpu(args):
     steps = args.steps + (args.steps & 1)  # the graph replays iteration pairs
     # ---- timed region: the benchmark loop (learned if weights are present, else plain)
     x = torch.zeros((n, n), dtype=torch.float32, device="cuda")
-    plan.fb_run(den, y_run, x0=x, gamma=gamma, L=L, max_iter=max(args.warmup, 3), check_every=2,
-                use_graph=True, inplace=True)
+    plan.fb_run(den, y, x0=x, gamma=gamma, L=L, max_iter=max(args.warmup, 3), check_every=2,
+                use_graph=True, inplace=True, alpha=alpha)
     torch.cuda.synchronize()
     barrier()
     with ClockSampler(local) as clk:
-        ms, launches = _timed_loop(plan, den, y_run, x, gamma, L, steps, stream)
+        ms, launches = _timed_loop(plan, den, y, x, gamma, L, steps, stream, alpha)
     barrier()
     ms, value = replica_aggregate(ms, steps, dist, ws, "cuda")
 
-    # ---- the plain loop: timed the same way, and its SNR after SNR_ITERS iterations from zero
+    # ---- the plain loop: timed the same way, then run to convergence (a fixed budget) for the SNR target
     xp = torch.zeros((n, n), dtype=torch.float32, device="cuda")
     plan.fb_run(haar, y, x0=xp, gamma=gamma, L=L, max_iter=4, check_every=2, use_graph=True, inplace=True)
     ms_plain, _ = _timed_loop(plan, haar, y, xp, gamma, L, steps, stream)
-    xp.zero_()
-    _, trace_plain = _run_to_snr(plan, haar, y, xp, gamma, L, x_true, 1.0, None, SNR_ITERS)
-    snr_plain = trace_plain[-1][1]
+    _, trace_plain, xp = _run_to_snr(plan, haar, y, gamma, L, x_true, 1.0, None, args.converge_iters)
+    snr_conv = trace_plain[-1][1]
+    target = snr_conv - TARGET_MARGIN_DB
+    it_plain = _first_at(trace_plain, target)
     plain = {"iter_per_s": ws * steps / (ms_plain / 1e3), "ms_per_iter": ms_plain / steps,
-             "snr_db_after_%d" % SNR_ITERS: snr_plain,
-             "time_to_snr_s": SNR_ITERS * ms_plain / steps / 1e3,
-             "snr_trace": [(i, round(s, 3)) for i, s in trace_plain[4::5]]}
-    comparison = {"plain": plain}
+             "snr_db_converged": snr_conv, "converge_iters": args.converge_iters,
+             "iters_to_target": it_plain, "time_to_target_s": it_plain * ms_plain / steps / 1e3,
+             "snr_trace": _thin(trace_plain, 100)}
+    comparison = {"snr_target_db": target,
+                  "snr_target": "the plain loop's SNR after %d iterations minus %.1f dB"
+                                % (args.converge_iters, TARGET_MARGIN_DB),
+                  "plain": plain}
     if args.bf16_g:
         # mixed precision: the same operator with G stored as BF16 complex weights (FP32 accumulation)
         plan_bf = pnp.Plan(n, K, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"], weight_dtype="bf16",
-                           block=prob["block"], nblocks=BLOCKS[wl["name"]], stream=stream)
+                           block=prob["block"], nblocks=BLOCKS[wl["name"]], stream=stream, row_scale=d)
         tune_bf = plan_bf.autotune(reps=2)
         y_bf = plan_bf.phi_forward(x_true)
         err = float(torch.linalg.vector_norm((y_bf - y0).to(torch.complex128)) /
@@ -430,7 +459,7 @@ def run_gpu(args):
         jr_s = synth.j_per_row_stacked(prob["w"], stk, cen, prob["w"], supports)
         t_plan = time.perf_counter()
         plan_ws = pnp.Plan(n, K, prob["omega"], prob["w"], prob["dl"], jr_s, block=prob["block"],
-                           nblocks=BLOCKS[wl["name"]], stream=stream, stack=stk, w_centres=cen)
+                           nblocks=BLOCKS[wl["name"]], stream=stream, stack=stk, w_centres=cen, row_scale=d)
         t_plan = time.perf_counter() - t_plan
         tune_ws = plan_ws.autotune(reps=2)
         y_ws = plan_ws.phi_forward(x_true)
@@ -453,7 +482,8 @@ def run_gpu(args):
         plan_ws.close()
         del plan_ws, y_ws, xw
     if args.usara_prox_iters > 0:
-        # uSARA (App. B) on the same operator: the SARA prox by dual FB, gamma lambda = rho = tau / sqrt(2L)
+        # uSARA (App. B) on the same operator: the SARA prox by dual FB, gamma lambda = rho = tau / sqrt(2L),
+        # reweighted every usara_reweight_every iterations (the log-sum majoriser)
         try:
             sara = pnp.SaraDenoiser(n, t, t, args.usara_prox_iters, levels=4, stream=stream)
             xu = torch.zeros((n, n), dtype=torch.float32, device="cuda")
@@ -462,12 +492,20 @@ def run_gpu(args):
             sara.close()
             sara = pnp.SaraDenoiser(n, t, t, args.usara_prox_iters, levels=4, stream=stream)
             xu.zero_()
-            _, trace_u = _run_to_snr(plan, sara, y, xu, gamma, L, x_true, 1.0, None, SNR_ITERS)
+            trace_u, it, rw = [], 0, args.usara_reweight_every
+            while it < args.usara_iters:
+                k = min(rw, args.usara_iters - it)
+                plan.fb_run(sara, y, x0=xu, gamma=gamma, L=L, max_iter=k, check_every=k, use_graph=True,
+                            inplace=True)
+                it += k
+                trace_u.append((it, _snr_db(x_true, xu)))
+                if it < args.usara_iters:
+                    sara.reweight(xu)
             comparison["usara"] = {
-                "prox_iters": args.usara_prox_iters, "reweighting": "none in the timed loop (weights 1)",
+                "prox_iters": args.usara_prox_iters, "reweight_every": rw,
                 "iter_per_s": ws * steps / (ms_u / 1e3), "ms_per_iter": ms_u / steps,
-                "snr_db_after_%d" % SNR_ITERS: trace_u[-1][1],
-                "snr_trace": [(i, round(s, 3)) for i, s in trace_u[4::5]]}
+                "iters_run": it, "snr_db_final": trace_u[-1][1], "iters_to_target": _first_at(trace_u, target),
+                "snr_trace": _thin(trace_u, 100)}
             sara.close()
             del xu
         except Exception as e:  # a comparison line; the headline above stands without it
@@ -503,30 +541,30 @@ def run_gpu(args):
             G_bytes=plan_h.info["nnz"] * 10, H_bytes=plan_h.info["holographic_bytes"], **res_h)
         plan_h.close()
         del plan_h, yh, y0h, xth
+    xl = None
     if learned:
-        xl = torch.zeros((n, n), dtype=torch.float32, device="cuda")
-        it_l, trace_l = _run_to_snr(plan, cnn, y_s, xl, gamma, L, x_true, alpha, snr_plain, SNR_MAX_ITERS)
+        it_l, trace_l, xl = _run_to_snr(plan, cnn, y, gamma, L, x_true, alpha, target, args.converge_iters)
         comparison["learned"] = {
-            "iter_per_s": value, "ms_per_iter": ms / steps, "alpha": alpha, "sigma_trained": wmeta.get("sigma"),
-            "sigma_heuristic": hp["sigma"], "iters_to_plain_snr": it_l,
-            "time_to_snr_s": None if it_l is None else it_l * ms / steps / 1e3,
+            "iter_per_s": value, "ms_per_iter": ms / steps, "alpha": alpha, "alpha_dirty_peak": hp["alpha"],
+            "alpha_matched_to_sigma": alpha_match, "sigma_trained": float(wmeta["sigma"]),
+            "sigma_heuristic_at_dirty_peak": hp["sigma"], "iters_to_target": it_l,
+            "time_to_target_s": None if it_l is None else it_l * ms / steps / 1e3,
             "snr_db_final": trace_l[-1][1], "iters_run": trace_l[-1][0],
-            "snr_trace": [(i, round(s, 3)) for i, s in trace_l[::2]]}
-        if os.path.exists(WEIGHTS_FNE):
+            "snr_trace": _thin(trace_l, 100)}
+        if os.path.exists(WEIGHTS_FNE) and args.fne:
             # the learned loop with the penalised network (same architecture and cost per iteration)
             params_f, meta_f = load_weights(WEIGHTS_FNE)
             cnn_f = pnp.CnnDenoiser(params_f, n, facet_rows=prob["facet_rows"], facet_cols=prob["facet_cols"],
                                     halo=prob["halo"], stream=stream)
-            xf = torch.zeros((n, n), dtype=torch.float32, device="cuda")
-            it_f, trace_f = _run_to_snr(plan, cnn_f, y_s, xf, gamma, L, x_true, alpha, snr_plain, SNR_MAX_ITERS)
+            alpha_f = max(hp["alpha"], heuristics.alpha_for_denoiser(tau_w, L, float(meta_f["sigma"])))
+            it_f, trace_f, _ = _run_to_snr(plan, cnn_f, y, gamma, L, x_true, alpha_f, target, args.converge_iters)
             comparison["learned_fne"] = {
                 "weights": "dncnn_C3 fine-tuned %d steps with the penalty, lambda %g" % (
-                    int(meta_f.get("steps", 0)), float(meta_f.get("fne_lambda", 0.0))),
-                "iters_to_plain_snr": it_f, "time_to_snr_s": None if it_f is None else it_f * ms / steps / 1e3,
+                    int(meta_f.get("steps", 0)), float(meta_f.get("fne_lambda", 0.0))), "alpha": alpha_f,
+                "iters_to_target": it_f, "time_to_target_s": None if it_f is None else it_f * ms / steps / 1e3,
                 "snr_db_final": trace_f[-1][1], "iters_run": trace_f[-1][0],
-                "snr_trace": [(i, round(s, 3)) for i, s in trace_f[::2]]}
+                "snr_trace": _thin(trace_f, 100)}
             cnn_f.close()
-            del xf
 
     # ---- kernel timing: eager replay with CUDA events around each operator stage
     plan.set_timing(True)
@@ -537,7 +575,10 @@ def run_gpu(args):
     plan.set_timing(False)
     g_ms, g_cnt = tim["gridding"]
     g_ms_launch = g_ms / max(g_cnt, 1)
-    alg_bytes = info["nnz"] * (8 + 2) + M * 8 + 2 * K * K * 8   # weight + 16-bit cell per tap
+    # algorithmic bytes of one fused pass: G read once as complex64 weight + int32 column per tap, the
+    # data y, and the grid read and written (12 B per tap, 8 B per row, 16 B per cell)
+    alg_bytes = info["nnz"] * 12 + M * 8 + 2 * K * K * 8
+    moved_bytes = info["nnz"] * (8 + 2) + M * 8 + 2 * K * K * 8   # what the pass stores: 16-bit cells
     hbm, peak_kind = measured_peaks()
     achieved = alg_bytes / (g_ms_launch * 1e-3) / 1e9
     roof_cnn = None
@@ -561,9 +602,10 @@ def run_gpu(args):
                     "unit": "TFLOP/s", "frac": flop / (d_ms * 1e-3) / 1e12 / bf16_peak, "traffic": None,
                     "flop_per_launch": flop, "ms_per_launch": d_ms}
 
-    # ---- end to end through the public API with host buffers
-    y_host = y_run.cpu().pin_memory()
-    y_dev = torch.empty_like(y_run)
+    # ---- end to end through the public API with host buffers: y in, the image out, every step
+    y_host = y.cpu().pin_memory()
+    x_host = torch.empty((n, n), dtype=torch.float32).pin_memory()
+    y_dev = torch.empty_like(y)
     torch.cuda.synchronize()
     e2e_steps = max(1, args.e2e_steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -571,8 +613,9 @@ def run_gpu(args):
     e0.record(stream)
     for _ in range(e2e_steps):
         y_dev.copy_(y_host, non_blocking=True)
-        plan.fb_run(den, y_dev, x0=x, gamma=gamma, L=L, max_iter=1, check_every=1,
-                    use_graph=False, inplace=True)   # ends with the D2H read of the FP64 norms
+        plan.fb_run(den, y_dev, x0=x, gamma=gamma, L=L, max_iter=1, check_every=1, use_graph=False,
+                    inplace=True, alpha=alpha)   # reads the FP64 norms back
+        x_host.copy_(x, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t_start)
@@ -591,32 +634,35 @@ def run_gpu(args):
                           "gridding_autotune": tune, "region_pitch": info["region_pitch"]},
                "clocks": clk.summary(),
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": M * 8,
-                       "d2h_bytes_per_step": 16},
+                       "d2h_bytes_per_step": n * n * 4 + 16},
                "gpu_launches": launches,
                "roofline": {"bound": "hbm", "kernel": "gpass<G_FUSED> (degrid+residual+grid)",
                             "achieved": achieved, "peak": hbm, "peak_kind": peak_kind, "unit": "GB/s",
                             "frac": achieved / hbm, "traffic": profiled_traffic("gridding.cu", wl["name"]),
                             "alg_bytes_per_launch": alg_bytes, "ms_per_launch": g_ms_launch,
+                            "moved_bytes_per_launch": moved_bytes,
+                            "frac_of_moved_bytes": moved_bytes / (g_ms_launch * 1e-3) / 1e9 / hbm,
                             "stage_ms_per_iter": {k: v[0] / max(v[1], 1) for k, v in tim.items()}},
                "roofline_denoiser": roof_cnn,
                "comparison": comparison,
                "fb": {k: (float(v) if isinstance(v, (int, float, np.floating)) else v) for k, v in hp.items()}}
+        out["fb"]["tau_raw"] = tau
         if ws == 1 and not args.no_cpu_baseline:
             rows, y_rows = cpu_sample_inputs(prob, None, y.cpu().numpy().astype(np.complex128))
             if learned:
-                xs = xl.cpu().numpy().astype(np.float64)
+                xs = xl.cpu().numpy().astype(np.float64) / alpha
                 cnn_arg = (params, _facet_pixels(n, prob["facet_rows"], prob["facet_cols"], prob["halo"]))
                 ys = y_rows / alpha
             else:
                 xs, cnn_arg, ys = xp.cpu().numpy().astype(np.float64), None, y_rows
-            est, parts = oracle_sample(prob, rows, xs, ys, gamma, t, cnn_arg)
-            out["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                   "sample": f"one FP64 oracle iteration of the timed loop: full-size FFT pair, G "
-                                             f"restricted to {CPU_SAMPLE_ROWS} seeded rows (time scaled by "
+            est, parts = oracle_sample(prob, rows, xs, ys, gamma, t, cnn_arg, d)
+            out["cpu_baseline"] = {"value": 1.0 / est, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                   "sample": f"one FP64 oracle iteration of the timed loop: full-size FFT pair "
+                                             f"(scipy.fft on {os.cpu_count()} threads), G restricted to "
+                                             f"{CPU_SAMPLE_ROWS} seeded rows (scipy CSR, one thread; time scaled by "
                                              f"M/{CPU_SAMPLE_ROWS})"
                                              + (f", the FP64 network on a {CNN_TILE}^2 tile (time scaled to the "
-                                                f"facets' pixels)" if learned else ", Haar prox")
-                                             + "; numpy FFT and scipy CSR are single-threaded",
+                                                f"facets' pixels)" if learned else ", Haar prox"),
                                    "parts_s": parts, "host_cores": os.cpu_count()}
         print(json.dumps(out), flush=True)
     if dist is not None:

@@ -70,7 +70,25 @@ typedef struct pnp_params {
   int use_graph;     /* 1: replay iterations as one captured CUDA graph          */
   double diverge_factor; /* > 0: fail with PNP_ERR_DIVERGED if ||x+|| grows past
                             this factor times its smallest checked value        */
+  double alpha;      /* rescaling of App. C (Eq. invpb2): the loop solves
+                        y / alpha = Phi (x / alpha) + n / alpha, i.e. it starts
+                        from x_inout / alpha, iterates on y / alpha and writes
+                        alpha x back, so the denoiser (and a Haar threshold)
+                        acts on the peak-normalised image; <= 0 means 1       */
+  int positivity;    /* PNP_POSITIVITY_ON (0, the default) ends every denoiser
+                        with the projection max(0, .) (App. B, C);
+                        PNP_POSITIVITY_OFF leaves it out                      */
+  int fallback;      /* 1: when the loop with a learned (CNN) denoiser diverges
+                        (non-finite iterate or diverge_factor exceeded), restart
+                        from the last checked finite iterate with the plain Haar
+                        denoiser at threshold fallback_t for the remaining
+                        iterations instead of failing (App. C: the plain loop is
+                        the learned loop's fallback); 0: fail                 */
+  double fallback_t; /* Haar threshold of the fallback, in the rescaled units
+                        of alpha (>= 0)                                       */
 } pnp_params;
+
+enum { PNP_POSITIVITY_ON = 0, PNP_POSITIVITY_OFF = 1 };
 
 /* Outputs of pnp_fb_run. */
 typedef struct pnp_stats {
@@ -78,7 +96,9 @@ typedef struct pnp_stats {
   double L;           /* Lipschitz constant used                                 */
   double gamma;       /* step size used                                          */
   double rel_change;  /* ||x^k - x^{k-1}|| / ||x^k|| at the last check (FP64)    */
-  double x_norm;      /* ||x^k|| at the last check (FP64)                        */
+  double x_norm;      /* ||x^k|| at the last check (FP64), rescaled units        */
+  int fallback_iter;  /* iteration from which the plain Haar fallback ran (the
+                         last checked finite iterate), or -1 when it did not  */
 } pnp_stats;
 
 /* Read-only facts about a plan. */
@@ -138,6 +158,41 @@ int pnp_plan_create_stacked(pnp_plan** plan, int n, int K, int64_t M, const doub
                             double dl, const int8_t* J_per_row_host, int J, int weight_dtype,
                             const int32_t* block_host, int nblocks, const int32_t* stack_host,
                             int nstacks, const double* w_centres_host, void* stream);
+
+/* Every option of plan creation in one descriptor (zero-initialise it, then set what is
+ * needed; a zero stack count or block count means 1).  The fields are those of
+ * pnp_plan_create_stacked plus
+ *  row_scale_host  host, M float64 data weights d_m > 0 multiplying the rows of G, or NULL
+ *                  for none: Phi = D G F Z with D = diag(d).  Sec. 3 images data weighted by
+ *                  the Briggs scheme (robust 0); with imaging weights w_m the data fidelity
+ *                  1/2 ||D (G F Z x - y)||^2 uses d_m = sqrt(w_m), so that Re{Phi^H Phi} delta
+ *                  is the weighted dirty beam and Re{Phi^H y} the weighted dirty image.
+ *                  Every call of the plan then takes and returns visibilities of the weighted
+ *                  model, y_m = d_m y_raw_m (pnp_plan_scale_data forms them).  Non-finite or
+ *                  non-positive entries are PNP_ERR_INVALID_ARG. */
+typedef struct pnp_plan_desc {
+  int n, K;
+  int64_t M;
+  const double* uvw_host;
+  double dl;
+  const int8_t* J_per_row_host;
+  int J;
+  int weight_dtype;
+  const int32_t* block_host;
+  int nblocks;
+  const int32_t* stack_host;
+  int nstacks;
+  const double* w_centres_host;
+  const double* row_scale_host;
+  void* stream;
+} pnp_plan_desc;
+
+int pnp_plan_create_desc(pnp_plan** plan, const pnp_plan_desc* desc);
+
+/* y_out = D y_in for the plan's data weights D (the weighted data of the model
+ * D y = D G F Z x + D n); a copy when the plan has none.  y_in, y_out: dev M
+ * complex64 in the caller's order (may alias). */
+int pnp_plan_scale_data(pnp_plan* plan, const float* y_in, float* y_out);
 
 void pnp_plan_destroy(pnp_plan* plan);
 
@@ -363,11 +418,15 @@ int pnp_fb_run(pnp_plan* plan, pnp_den* den, const float* y, const pnp_params* p
  * no allocating library routine: its scratch (two doubles per pair of image
  * rows) is a static device array of 128 KiB that every GPU loading the library
  * holds until exit.  Limit: n even, 2 <= n <= 16384; larger n is rejected with
- * PNP_ERR_INVALID_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call shares the array: calls that
- * overlap on the GPU race and must be serialised by the caller.  Asynchronous
- * on stream (NULL: legacy default stream). */
+ * PNP_ERR_INVALID_ARG, and so are z or x_prev overlapping x_out.  Every call
+ * looks up the array's device address (cudaGetSymbolAddress, which allocates
+ * nothing) with the caller's device current, so the address stays right after
+ * the device's context is recreated; the first lookup on a device may load the
+ * library's device code, so make the first call on each device before any
+ * stream capture.  Every call shares the array: calls that overlap on the GPU
+ * race and must be serialised by the caller.  A non-finite z makes
+ * norms[1] NaN (the signal the stopping test reads).  Asynchronous on stream
+ * (NULL: legacy default stream). */
 int pnp_haar_denoise_noalloc(const float* z, const float* x_prev, float* x_out, int n, double t,
                              double* norms, void* stream);
 

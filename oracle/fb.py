@@ -142,14 +142,19 @@ def haar_denoise(z: np.ndarray, t: float, positivity: bool = True) -> np.ndarray
 
 # ---------------------------------------------------------------- FB loop
 def pnp_fb(op, y, gamma: float, denoiser, iters: int, x0=None, tol: float = 0.0,
-           x_true=None):
+           x_true=None, alpha: float = 1.0):
     """x^{k+1} = D(x^k - gamma grad f(x^k)) (Eq. fb with a plug-in denoiser D).
 
+    With ``alpha`` the loop solves the rescaled problem of App. C (Eq. invpb2),
+    y / alpha = Phi (x / alpha) + n / alpha: it starts from x0 / alpha, iterates
+    on y / alpha, and the returned image is alpha times its result (the SNR in
+    the history is that of alpha x).
     Returns (x, history) where history holds per iteration the relative change
     ||x^{k+1} - x^k|| / ||x^{k+1}||, f(x^{k+1}) and, if x_true is given, the SNR.
     """
     n = op.n
-    x = np.zeros((n, n)) if x0 is None else np.array(x0, dtype=np.float64)
+    x = np.zeros((n, n)) if x0 is None else np.array(x0, dtype=np.float64) / alpha
+    y = np.asarray(y) / alpha
     hist = {"rel_change": [], "f": [], "snr": []}
     for _ in range(iters):
         x_new = denoiser(gradient_step(op, x, y, gamma))
@@ -159,10 +164,10 @@ def pnp_fb(op, y, gamma: float, denoiser, iters: int, x0=None, tol: float = 0.0,
         hist["rel_change"].append(rc)
         hist["f"].append(data_fidelity(op, x, y))
         if x_true is not None:
-            hist["snr"].append(snr_db(x_true, x))
+            hist["snr"].append(snr_db(x_true, alpha * x))
         if tol > 0 and rc < tol:
             break
-    return x, hist
+    return alpha * x, hist
 
 
 def snr_db(x_true, x) -> float:

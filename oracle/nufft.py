@@ -12,7 +12,7 @@ Conventions (readings where the paper is silent):
 * Z zero-pads onto a K x K grid (pixel offset p at grid index p mod K) and
   divides by the separable grid correction c(p_0) c(p_1), the continuous
   Fourier transform of the interpolation kernel (Eq. 1, Fessler 2003).
-* F is the unnormalised forward 2-D DFT (numpy's fft2), F^H its exact adjoint
+* F is the unnormalised forward 2-D DFT (scipy's fft2), F^H its exact adjoint
   (K^2 * ifft2).
 * G row m holds the Kaiser-Bessel (KB) kernel taps around
   kappa = omega K / (2 pi): per axis the J integers k with |kappa - k| < J/2
@@ -36,9 +36,14 @@ W ~ exp(i pi a (p_0^2 + p_1^2)), a = w dl^2, which is separable per axis:
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
+import scipy.fft as sfft
 import scipy.sparse as sps
 import scipy.special as spec
+
+FFT_WORKERS = os.cpu_count() or 1   # threads of the FFT (the sparse products are single-threaded)
 
 
 # ---------------------------------------------------------------- KB kernel
@@ -108,13 +113,13 @@ def zero_pad_adjoint(gs: GridSpec, grid: np.ndarray) -> np.ndarray:
 
 
 def dft2(grid: np.ndarray) -> np.ndarray:
-    """F: unnormalised forward 2-D DFT."""
-    return np.fft.fft2(grid)
+    """F: unnormalised forward 2-D DFT (scipy's FFT on all host cores)."""
+    return sfft.fft2(grid, workers=FFT_WORKERS)
 
 
 def dft2_adjoint(grid: np.ndarray) -> np.ndarray:
     """F^H: exact adjoint of the unnormalised DFT, K^2 ifft2."""
-    return np.fft.ifft2(grid) * (grid.shape[0] * grid.shape[1])
+    return sfft.ifft2(grid, workers=FFT_WORKERS) * (grid.shape[0] * grid.shape[1])
 
 
 # ---------------------------------------------------------------- w-kernel
@@ -174,11 +179,14 @@ def row_axis_weights(kappa, a, Jm: int, gs: GridSpec, w_hat_cache=None):
 
 
 def degridding_matrix(gs: GridSpec, omega: np.ndarray, w=None, dl: float = 0.0,
-                      J_per_row=None, rows=None) -> sps.csr_matrix:
+                      J_per_row=None, rows=None, row_scale=None) -> sps.csr_matrix:
     """G as a scipy CSR matrix (len(rows) x K^2, complex128), rows in the given order.
 
     Row m: outer product of the two per-axis weight vectors of
-    ``row_axis_weights`` (KB row, or the w-folded row when w and dl are set).
+    ``row_axis_weights`` (KB row, or the w-folded row when w and dl are set),
+    times the data weight d_m when ``row_scale`` is given (Sec. 3: weighted
+    data; the fidelity 1/2 ||D (G F Z x - y)||^2 with d_m = sqrt of the imaging
+    weight makes Re{Phi^H Phi} delta the weighted dirty beam).
     """
     K = gs.K
     omega = np.asarray(omega, dtype=np.float64)
@@ -206,6 +214,8 @@ def degridding_matrix(gs: GridSpec, omega: np.ndarray, w=None, dl: float = 0.0,
             pos = indptr[ss][:, None] + np.arange(Jm * Jm)[None, :]
             data[pos] = wv
             cols[pos] = cv
+    if row_scale is not None:
+        data *= np.repeat(np.asarray(row_scale, dtype=np.float64)[rows], nnz_row)
     return sps.csr_matrix((data, cols, indptr), shape=(R, K * K))
 
 
@@ -214,10 +224,10 @@ class Operator:
     """Phi = G F Z and its adjoints for one problem (FP64)."""
 
     def __init__(self, n: int, K: int, omega, w=None, dl: float = 0.0, J_per_row=None,
-                 J: int = 7, beta: float | None = None, rows=None):
+                 J: int = 7, beta: float | None = None, rows=None, row_scale=None):
         self.gs = GridSpec(n, K, J, beta)
         self.n, self.K = n, K
-        self.G = degridding_matrix(self.gs, omega, w, dl, J_per_row, rows)
+        self.G = degridding_matrix(self.gs, omega, w, dl, J_per_row, rows, row_scale)
         self.GH = self.G.conj().T.tocsr()
         self.M = self.G.shape[0]
 

@@ -33,7 +33,9 @@ EXPORTED = [
     "pnp_cnn_trainer_create", "pnp_cnn_trainer_destroy", "pnp_cnn_train_step", "pnp_cnn_trainer_read",
     "pnp_cnn_num_params", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm",
     "pnp_cnn_train_step_fne", "pnp_den_create_sara", "pnp_den_sara_reweight", "pnp_sara_transform",
+    "pnp_plan_create_desc", "pnp_plan_scale_data",
 ]
+PNP_POSITIVITY_ON, PNP_POSITIVITY_OFF = 0, 1
 
 
 class PnPError(RuntimeError):
@@ -44,12 +46,22 @@ class PnPError(RuntimeError):
 
 class _Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("L", C.c_double), ("max_iter", C.c_int), ("tol", C.c_double),
-                ("check_every", C.c_int), ("use_graph", C.c_int), ("diverge_factor", C.c_double)]
+                ("check_every", C.c_int), ("use_graph", C.c_int), ("diverge_factor", C.c_double),
+                ("alpha", C.c_double), ("positivity", C.c_int), ("fallback", C.c_int),
+                ("fallback_t", C.c_double)]
 
 
 class _Stats(C.Structure):
     _fields_ = [("iters", C.c_int), ("L", C.c_double), ("gamma", C.c_double),
-                ("rel_change", C.c_double), ("x_norm", C.c_double)]
+                ("rel_change", C.c_double), ("x_norm", C.c_double), ("fallback_iter", C.c_int)]
+
+
+class _PlanDesc(C.Structure):
+    _fields_ = [("n", C.c_int), ("K", C.c_int), ("M", C.c_int64), ("uvw_host", C.c_void_p), ("dl", C.c_double),
+                ("J_per_row_host", C.c_void_p), ("J", C.c_int), ("weight_dtype", C.c_int),
+                ("block_host", C.c_void_p), ("nblocks", C.c_int), ("stack_host", C.c_void_p),
+                ("nstacks", C.c_int), ("w_centres_host", C.c_void_p), ("row_scale_host", C.c_void_p),
+                ("stream", C.c_void_p)]
 
 
 class _Info(C.Structure):
@@ -76,6 +88,8 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_plan_create.argtypes = [C.POINTER(vp), i32, i32, i64, vp, dbl, vp, i32, i32, vp, i32, vp]
     L.pnp_plan_create_stacked.argtypes = [C.POINTER(vp), i32, i32, i64, vp, dbl, vp, i32, i32, vp, i32, vp, i32,
                                           vp, vp]
+    L.pnp_plan_create_desc.argtypes = [C.POINTER(vp), C.POINTER(_PlanDesc)]
+    L.pnp_plan_scale_data.argtypes = [vp, vp, vp]
     L.pnp_plan_destroy.argtypes = [vp]
     L.pnp_plan_destroy.restype = None
     L.pnp_plan_get_info.argtypes = [vp, C.POINTER(_Info)]
@@ -122,7 +136,7 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
                  "pnp_den_device_status", "pnp_cnn_trainer_create", "pnp_cnn_train_step",
                  "pnp_cnn_trainer_read", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm",
                  "pnp_cnn_train_step_fne", "pnp_den_create_sara", "pnp_den_sara_reweight",
-                 "pnp_sara_transform"):
+                 "pnp_sara_transform", "pnp_plan_create_desc", "pnp_plan_scale_data"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -173,6 +187,7 @@ class FBStats:
     gamma: float
     rel_change: float
     x_norm: float
+    fallback_iter: int = -1
 
 
 class Plan:
@@ -187,7 +202,7 @@ class Plan:
     """
 
     def __init__(self, n, K, omega, w=None, dl=0.0, J_per_row=None, J=7, weight_dtype="c64",
-                 block=None, nblocks=1, stream=None, stack=None, w_centres=None):
+                 block=None, nblocks=1, stream=None, stack=None, w_centres=None, row_scale=None):
         import torch
         L = lib()
         omega = np.asarray(omega, dtype=np.float64)
@@ -199,22 +214,20 @@ class Plan:
         uvw = np.ascontiguousarray(uvw)
         jr = None if J_per_row is None else np.ascontiguousarray(J_per_row, dtype=np.int8)
         blk = None if block is None else np.ascontiguousarray(block, dtype=np.int32)
+        wc = None if w_centres is None else np.ascontiguousarray(w_centres, dtype=np.float64)
+        stk = None if wc is None else np.ascontiguousarray(np.zeros(M) if stack is None else stack, dtype=np.int32)
+        rs = None if row_scale is None else np.ascontiguousarray(row_scale, dtype=np.float64)
+        if rs is not None and rs.shape != (M,):
+            raise ValueError(f"row_scale has shape {rs.shape}, expected ({M},)")
         self.stream = torch.cuda.current_stream() if stream is None else stream
         self._h = C.c_void_p()
         wd = PNP_W_BF16C if weight_dtype in ("bf16", PNP_W_BF16C) else PNP_W_C64
-        if w_centres is None:
-            _check(L.pnp_plan_create(C.byref(self._h), int(n), int(K), int(M), uvw.ctypes.data, float(dl),
-                                     None if jr is None else jr.ctypes.data, int(J), wd,
-                                     None if blk is None else blk.ctypes.data, int(nblocks),
-                                     _stream_handle(self.stream)))
-        else:
-            wc = np.ascontiguousarray(w_centres, dtype=np.float64)
-            stk = np.ascontiguousarray(np.zeros(M) if stack is None else stack, dtype=np.int32)
-            _check(L.pnp_plan_create_stacked(C.byref(self._h), int(n), int(K), int(M), uvw.ctypes.data,
-                                             float(dl), None if jr is None else jr.ctypes.data, int(J), wd,
-                                             None if blk is None else blk.ctypes.data, int(nblocks),
-                                             stk.ctypes.data, int(wc.size), wc.ctypes.data,
-                                             _stream_handle(self.stream)))
+        ptr = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+        desc = _PlanDesc(int(n), int(K), int(M), uvw.ctypes.data, float(dl), ptr(jr), int(J), wd, ptr(blk),
+                         int(nblocks), ptr(stk), 1 if wc is None else int(wc.size), ptr(wc), ptr(rs),
+                         _stream_handle(self.stream).value)
+        _check(L.pnp_plan_create_desc(C.byref(self._h), C.byref(desc)))
+        self.weighted = rs is not None
         self.n, self.K, self.M = int(n), int(K), int(M)
 
     # ------------------------------------------------------------------ info
@@ -271,6 +284,15 @@ class Plan:
         return off, wts, cols
 
     # ------------------------------------------------------------------ operator
+    def scale_data(self, y, out=None):
+        """D y for the plan's data weights D (a copy without weights): the weighted data."""
+        import torch
+        _cuda_c64(y, self.M, "y")
+        o = torch.empty_like(y) if out is None else out
+        _cuda_c64(o, self.M, "out")
+        _check(lib().pnp_plan_scale_data(self._h, _ptr(y), _ptr(o)))
+        return o
+
     def phi_forward(self, x, out=None):
         """y = Phi x (Eq. 1)."""
         import torch
@@ -310,9 +332,14 @@ class Plan:
         return Lv.value, it.value
 
     def fb_run(self, den, y, x0=None, gamma=0.0, L=0.0, max_iter=200, tol=0.0, check_every=10,
-               use_graph=True, diverge_factor=0.0, inplace=False):
+               use_graph=True, diverge_factor=0.0, inplace=False, alpha=1.0, positivity=True,
+               fallback_t=None):
         """Run Eq. fb with denoiser ``den`` from x0 (zeros if None); returns (x, FBStats).
 
+        ``alpha`` rescales the problem as in App. C (Eq. invpb2): the loop iterates on y / alpha
+        from x0 / alpha and returns alpha x.  ``positivity`` keeps the final max(0, .) of the
+        denoiser.  ``fallback_t`` (learned denoiser only): on divergence, continue from the last
+        checked finite iterate with the Haar denoiser at this threshold (rescaled units).
         With ``inplace`` the iterate is updated in x0 itself."""
         import torch
         _cuda_c64(y, self.M, "y")
@@ -322,10 +349,12 @@ class Plan:
             x = x0 if inplace else x0.clone()
         _cuda_f32(x, (self.n, self.n), "x0")
         prm = _Params(float(gamma), float(L), int(max_iter), float(tol), int(check_every),
-                      1 if use_graph else 0, float(diverge_factor))
+                      1 if use_graph else 0, float(diverge_factor), float(alpha),
+                      PNP_POSITIVITY_ON if positivity else PNP_POSITIVITY_OFF,
+                      0 if fallback_t is None else 1, 0.0 if fallback_t is None else float(fallback_t))
         st = _Stats()
         _check(lib().pnp_fb_run(self._h, den._h, _ptr(y), C.byref(prm), _ptr(x), C.byref(st)))
-        return x, FBStats(st.iters, st.L, st.gamma, st.rel_change, st.x_norm)
+        return x, FBStats(st.iters, st.L, st.gamma, st.rel_change, st.x_norm, st.fallback_iter)
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -249,6 +249,7 @@ struct ConvArgs {
   const int4* cores;   // per facet: (r0, r1, c0, c1)
   float b8;
   double* acc;
+  int pos;             // last layer: 1 applies the positivity projection max(0, .)
 };
 
 template <int NO>
@@ -467,7 +468,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
           tc_fence_before();
           bar_arrive(&t_empty[k]);
           if (!in_core) continue;
-          const float o = fmaxf(0.f, zv - (__uint_as_float(v) + A.b8));
+          const float res = zv - (__uint_as_float(v) + A.b8);
+          const float o = A.pos ? fmaxf(0.f, res) : res;
           A.img[p] = o;
           s1 += (double)o * o;
           // fmaxf(0, NaN) is 0, so positivity would hide a non-finite input: poison the norms
@@ -794,7 +796,8 @@ void cnn_destroy(pnp_den* d) {
   d->impl = nullptr;
 }
 
-int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc, const float* x_prev) {
+int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc, const float* x_prev,
+                bool positivity) {
   CnnState* S = static_cast<CnnState*>(d->impl);
   if (!S) return fail(PNP_ERR_INVALID_ARG, "CNN denoiser not initialised");
   if (n != S->n) return fail(PNP_ERR_INVALID_ARG, "image side differs from the one the CNN denoiser was built for");
@@ -823,7 +826,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
   {
     // layer 8 on the tensor cores, fused with D(z) = max(0, z - N(z)) on the facet cores and the norms
     ConvArgs C{nullptr, S->d_wlast, nullptr, S->d_lstrips, S->n_lstrips, S->Hc, S->Wc, S->d_status, 2, nullptr,
-               z, x_prev, out, n, S->d_facets, S->d_cores, S->b8, acc};
+               z, x_prev, out, n, S->d_facets, S->d_cores, S->b8, acc, positivity ? 1 : 0};
     const int grid = std::max(1, std::min(S->n_lstrips, sms));
     conv64_tc<NO_LAST><<<grid, CONV_THREADS, ConvGeom<NO_LAST>::SMEM, s>>>(C, S->map[cur][0], S->map[cur][1]);
     PNP_CHECK_LAUNCH();

@@ -83,7 +83,8 @@ struct Unit {
 };
 
 // Q2 epilogue modes of the last inverse-FFT pass (see fft.cu).
-enum EpiMode { EPI_ADJ = 0, EPI_GRAD = 1, EPI_HAAR = 2, EPI_Z = 3, EPI_NORMAL = 4 };
+// EPI_HAAR_NOPOS: the Haar prox without the final positivity projection.
+enum EpiMode { EPI_ADJ = 0, EPI_GRAD = 1, EPI_HAAR = 2, EPI_Z = 3, EPI_NORMAL = 4, EPI_HAAR_NOPOS = 5 };
 
 // Gridding pass modes (see gridding.cu).
 enum GMode { G_DEGRID = 0, G_GRID = 1, G_FUSED = 2 };
@@ -111,6 +112,17 @@ struct pnp_plan {
   cudaEvent_t ev_join[2] = {nullptr, nullptr};
   int device = 0, num_sms = 0;
   int primed = 0;  // bit k: an eager FB iteration with denoiser kind k has configured every kernel
+  uint64_t epoch = 0;  // bumped whenever the gridding work decomposition changes (captured graphs go stale)
+  // CUDA graph of two FB iterations kept across pnp_fb_run calls, valid while its key matches
+  struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+    uint64_t den_serial = 0, epoch = 0;
+    const float* x = nullptr;
+    double gamma = 0;
+    int epi = 0;
+    bool holo = false;
+  } graph;
 
   // device buffers
   float* d_cinv = nullptr;     // n: 1 / c(a - n/2)
@@ -137,6 +149,7 @@ struct pnp_plan {
   float* d_gacc = nullptr;     // n*n (P > 1): gradient image accumulated over the stacks
   float2* d_H = nullptr;       // holographic H = G^H G: [S*S offsets][K*K cells], S = 2 Jmax - 1
   float2* d_dirty = nullptr;   // K*K: G^H y of the current FB run (holographic mode)
+  float* d_rowscale = nullptr; // M (caller order): data weights d_m folded into the rows of G, or NULL
   int holo_S = 0;
   bool holo = false;           // FB loop and op_norm apply H instead of streaming G
   int64_t device_bytes = 0;
@@ -156,6 +169,7 @@ struct pnp_plan {
 
 struct pnp_den {
   int kind = PNP_DEN_HAAR;
+  uint64_t serial = 0;    // unique per denoiser created in this process (keys the plan's graph cache)
   double t = 0;
   cudaStream_t stream = nullptr;
   void* impl = nullptr;   // CNN state (cnn.cu)
@@ -176,10 +190,11 @@ int fft_adjoint(pnp_plan* p, int mode, const float* x, float* out,         // d_
 int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out, int s);
 // choose p->pitch from the plan's number of rows per support J (rows_per_J[0..16])
 int gridding_pitch(pnp_plan* p, const int64_t* rows_per_J);
-int permute_y(pnp_plan* p, const float2* y_user);  // d_ysorted = y_user[perm]
+int permute_y(pnp_plan* p, const float2* y_user, float scale = 1.f);  // d_ysorted = scale y_user[perm]
 // plan_build.cu
 int build_units(pnp_plan* p);
-int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t* block, const int32_t* stack);
+int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t* block, const int32_t* stack,
+               const double* row_scale);
 // holographic.cu: build H (once), the dirty grid of the sorted data, one application of H
 int holo_build_plan(pnp_plan* p);
 int holo_dirty_grid(pnp_plan* p);
@@ -190,6 +205,8 @@ int haar_denoise_dev(cudaStream_t s, const float* z, float* out, int n, float t,
 int scale_image(cudaStream_t s, const float* in, float* out, int64_t count, const double* acc,
                 int acc_index);
 int zero_acc(cudaStream_t s, double* acc, int count);
+int mul_image(cudaStream_t s, const float* in, float* out, int64_t count, float f);  // out = f in
+int row_scale_c64(cudaStream_t s, const float2* y_in, const float* d, float2* y_out, int64_t count);
 // cnn.cu
 int cnn_create(pnp_den* d, const float* weights_host, const int32_t* fr, int nfr,
                const int32_t* fc, int nfc, int halo, int n);
@@ -222,11 +239,12 @@ int canvas_map_create(void* map_out, const __nv_bfloat16* canvas, int F, int Hc,
 int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, const int4* facets, int F, int Hc,
                      int Wc, const float* w1, const float* b1, __nv_bfloat16* out);
 int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc,
-                const float* x_prev);
+                const float* x_prev, bool positivity = true);
 // sara.cu: uSARA's denoiser (App. B)
 int sara_create(pnp_den* d, int n, int levels, double gamma_lambda, double rho, int iters);
 void sara_destroy(pnp_den* d);
-int sara_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc, const float* x_prev);
+int sara_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc, const float* x_prev,
+                 bool positivity = true);
 int sara_reweight(pnp_den* d, const float* x);
 int sara_transform(pnp_den* d, const float* in, float* out, int direction);
 }  // namespace pnp

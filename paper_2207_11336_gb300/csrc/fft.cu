@@ -397,8 +397,10 @@ __global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(FftArgs A) {
     }
   } else if (A.epi == EPI_GRAD) {
     for (int i = j; i < 2 * n; i += T) A.out[base + i] = A.x[base + i] - gamma * gs[i];
-  } else {  // EPI_HAAR: z = x - gamma g on 2x2 blocks, Haar soft-threshold, positivity
+  } else {  // EPI_HAAR(_NOPOS): z = x - gamma g on 2x2 blocks, Haar soft-threshold, positivity (or not)
     const float t = A.t;
+    const bool pos = A.epi == EPI_HAAR;
+    auto proj = [pos](float v) { return pos ? fmaxf(0.f, v) : v; };
     for (int bb = j; bb < n / 2; bb += T) {
       const int b = 2 * bb;
       const float x00 = A.x[base + b], x01 = A.x[base + b + 1];
@@ -409,10 +411,10 @@ __global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(FftArgs A) {
       const float hh = soft(0.5f * (z00 - z01 + z10 - z11), t);
       const float hv = soft(0.5f * (z00 + z01 - z10 - z11), t);
       const float hd = soft(0.5f * (z00 - z01 - z10 + z11), t);
-      const float o00 = fmaxf(0.f, 0.5f * (ha + hh + hv + hd));
-      const float o01 = fmaxf(0.f, 0.5f * (ha - hh + hv - hd));
-      const float o10 = fmaxf(0.f, 0.5f * (ha + hh - hv - hd));
-      const float o11 = fmaxf(0.f, 0.5f * (ha - hh - hv + hd));
+      const float o00 = proj(0.5f * (ha + hh + hv + hd));
+      const float o01 = proj(0.5f * (ha - hh + hv - hd));
+      const float o10 = proj(0.5f * (ha + hh - hv - hd));
+      const float o11 = proj(0.5f * (ha - hh - hv + hd));
       A.out[base + b] = o00;
       A.out[base + b + 1] = o01;
       A.out[base + n + b] = o10;
@@ -425,7 +427,7 @@ __global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(FftArgs A) {
       if (!(isfinite(z00) && isfinite(z01) && isfinite(z10) && isfinite(z11))) s1 = __longlong_as_double(0x7ff8000000000000LL);
     }
   }
-  if (A.acc && (A.epi == EPI_HAAR || A.epi == EPI_NORMAL))
+  if (A.acc && (A.epi == EPI_HAAR || A.epi == EPI_HAAR_NOPOS || A.epi == EPI_NORMAL))
     block_reduce_add(s0, s1, A.acc, reinterpret_cast<double*>(smem));
 }
 

@@ -445,10 +445,12 @@ __global__ void __launch_bounds__(GPASS_THREADS, 1) gpass(GArgs A) {
 }
 
 __global__ void permute_kernel(const float2* __restrict__ y, const int32_t* __restrict__ perm,
-                               float2* __restrict__ out, int64_t M) {
+                               float2* __restrict__ out, int64_t M, float scale) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
-       i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = y[perm[i]];
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = y[perm[i]];
+    out[i] = make_float2(v.x * scale, v.y * scale);
+  }
 }
 
 template <int MODE, typename WT, int RB>
@@ -543,12 +545,12 @@ int gridding_pitch(pnp_plan* p, const int64_t* rows_per_J) {
   return PNP_OK;
 }
 
-int permute_y(pnp_plan* p, const float2* y_user) {
+int permute_y(pnp_plan* p, const float2* y_user, float scale) {
   if (p->M == 0) return PNP_OK;
   const int threads = 256;
   long long blocks = (p->M + threads - 1) / threads;
   if (blocks > 8L * p->num_sms * 8) blocks = 8L * p->num_sms * 8;
-  permute_kernel<<<(unsigned)blocks, threads, 0, p->stream>>>(y_user, p->d_perm, p->d_ysorted, p->M);
+  permute_kernel<<<(unsigned)blocks, threads, 0, p->stream>>>(y_user, p->d_perm, p->d_ysorted, p->M, scale);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }

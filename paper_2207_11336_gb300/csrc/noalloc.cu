@@ -14,7 +14,6 @@
 // be cleared first.  Calls that overlap on the GPU (two streams, or two host
 // threads) race on the array and must be serialised by the caller.
 #include <cmath>
-#include <mutex>
 
 #include "common.cuh"
 
@@ -23,28 +22,25 @@ namespace {
 
 constexpr int NOALLOC_MAX_N = 16384;          // largest image side accepted
 constexpr int NOALLOC_ROWS = NOALLOC_MAX_N / 2;
-constexpr int NOALLOC_MAX_DEVICES = 64;
 
 // per pair of image rows: ||x_out - x_prev||^2 and ||x_out||^2 partial sums (128 KiB)
 static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_ROWS];
 
-std::mutex g_addr_mu;
-double* g_addr[NOALLOC_MAX_DEVICES] = {};
-
-// Device address of the scratch array for the current device, looked up once
-// per device with that device current (the host-side symbol is only a stand-in).
+// Device address of the scratch array for the current device (the host-side symbol is only a
+// stand-in).  Looked up on every call with the caller's device current: the lookup allocates
+// nothing, and a cached address would go stale if the caller recreated the device's primary
+// context (cudaDeviceReset), after which the module can load at another address.
 int scratch_address(double** out) {
-  int dev = 0;
-  PNP_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(PNP_ERR_UNSUPPORTED, "device index too large");
-  std::lock_guard<std::mutex> lk(g_addr_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    PNP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_addr[dev];
+  void* p = nullptr;
+  PNP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  *out = static_cast<double*>(p);
   return PNP_OK;
+}
+
+// true when the byte ranges [a, a + bytes) and [b, b + bytes) overlap
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + bytes && y < x + bytes;
 }
 
 __device__ __forceinline__ float soft_na(float c, float t) {
@@ -138,7 +134,10 @@ extern "C" int pnp_haar_denoise_noalloc(const float* z, const float* x_prev, flo
     return fail(PNP_ERR_INVALID_ARG, "n = " + std::to_string(n) + " exceeds the allocation-free limit of " +
                                          std::to_string(NOALLOC_MAX_N) + " pixels per side");
   if (!(t >= 0) || !std::isfinite(t)) return fail(PNP_ERR_INVALID_ARG, "t must be finite and >= 0");
-  if (z == x_out) return fail(PNP_ERR_INVALID_ARG, "z and x_out must not alias");
+  const size_t bytes = (size_t)n * n * sizeof(float);
+  if (overlaps(z, x_out, bytes)) return fail(PNP_ERR_INVALID_ARG, "z and x_out must not overlap");
+  if (x_prev && overlaps(x_prev, x_out, bytes))
+    return fail(PNP_ERR_INVALID_ARG, "x_prev and x_out must not overlap");
   double* scratch = nullptr;
   if (int rc = scratch_address(&scratch)) return rc;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

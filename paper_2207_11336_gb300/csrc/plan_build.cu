@@ -30,6 +30,7 @@ constexpr int MAX_D = 15;  // |d| <= MAX_D, so 2 MAX_D + 1 <= 32 lanes
 
 struct RowGeom {
   double kap0, kap1, a;  // kappa per axis, chirp rate a = w dl^2
+  double d;              // data weight d_m multiplying the row (1 without weighting)
   int s0, s1;            // first tap (unwrapped) per axis
   int J;                 // row support J_m
 };
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(256) build_rows(BuildArgs A) {
   for (int t = lane; t < nn; t += 32) {
     const int i1 = t / Jm, i0 = t - i1 * Jm;  // k1-major, k0-minor
     const double2 a = s_g[wl][0][i0], b = s_g[wl][1][i1];
-    const float wr = (float)(a.x * b.x - a.y * b.y), wi = (float)(a.x * b.y + a.y * b.x);
+    const float wr = (float)(g.d * (a.x * b.x - a.y * b.y)), wi = (float)(g.d * (a.x * b.y + a.y * b.x));
     if (A.bf16) {
       __nv_bfloat162 h = __floats2bfloat162_rn(wr, wi);
       reinterpret_cast<__nv_bfloat162*>(A.w)[beg + t] = h;
@@ -190,6 +191,7 @@ int dev_alloc(pnp_plan* p, T** ptr, size_t count) {
 }  // namespace
 
 int build_units(pnp_plan* p) {
+  ++p->epoch;  // a captured FB graph launches the old work list: it must be captured again
   std::vector<Unit> units;
   std::vector<Chunk> chunks;
   std::vector<uint8_t> runs;
@@ -271,7 +273,8 @@ int build_units(pnp_plan* p) {
   return PNP_OK;
 }
 
-int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t* block, const int32_t* stack) {
+int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t* block, const int32_t* stack,
+               const double* row_scale) {
   const int n = p->n, K = p->K, J = p->J;
   const int64_t M = p->M;
   p->beta = kb_beta(J, (double)K / n);
@@ -303,6 +306,9 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     const double wres = uvw[3 * m + 2] - (stack ? p->w_centres[stack[m]] : 0.0);
     g.a = p->dl > 0 ? wres * p->dl * p->dl : 0.0;
     g.J = Jrow ? Jrow[m] : J;
+    g.d = row_scale ? row_scale[m] : 1.0;
+    if (!(g.d > 0.0) || !std::isfinite(g.d))
+      return fail(PNP_ERR_INVALID_ARG, "row scale must be finite and > 0 at row " + std::to_string(m));
     if (!(std::isfinite(g.kap0) && std::isfinite(g.kap1) && std::isfinite(g.a)))
       return fail(PNP_ERR_INVALID_ARG, "non-finite uvw at row " + std::to_string(m));
     if (std::fabs(uvw[3 * m]) > 4 * M_PI || std::fabs(uvw[3 * m + 1]) > 4 * M_PI)
@@ -491,6 +497,12 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     PNP_CUDA(cudaMemcpy(p->d_rowptr, rp.data(), rp.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
   }
   if (M) PNP_CUDA(cudaMemcpy(p->d_perm, p->h_perm.data(), M * sizeof(int32_t), cudaMemcpyHostToDevice));
+  if (M && row_scale) {  // the data weights in the caller's row order, for pnp_plan_scale_data
+    std::vector<float> d(M);
+    for (int64_t m = 0; m < M; ++m) d[m] = (float)row_scale[m];
+    if (int rc = dev_alloc(p, &p->d_rowscale, (size_t)M)) return rc;
+    PNP_CUDA(cudaMemcpy(p->d_rowscale, d.data(), M * sizeof(float), cudaMemcpyHostToDevice));
+  }
 
   // build G rows on the GPU
   if (M) {

@@ -9,6 +9,7 @@ namespace pnp {
 
 static thread_local std::string t_err;
 std::atomic<int64_t> g_launches{0};
+static std::atomic<uint64_t> g_den_serial{0};
 
 void set_error(const std::string& msg) { t_err = msg; }
 int fail(int code, const std::string& msg) {
@@ -79,6 +80,8 @@ void free_plan(pnp_plan* p) {
   cudaFree(p->d_gacc);
   cudaFree(p->d_H);
   cudaFree(p->d_dirty);
+  cudaFree(p->d_rowscale);
+  if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
   delete p;
 }
 
@@ -109,40 +112,50 @@ int normal_pass(pnp_plan* p, const float2* y_sorted, const float* xf, int epi, c
 }
 
 // One FB iteration x_next = D(x_cur - gamma grad f(x_cur)); FP64 norms land in acc[0..1].
-int fb_iteration(pnp_plan* p, pnp_den* d, const float* cur, float* nxt, double gamma) {
+// pos: the denoiser ends with the positivity projection.
+int fb_iteration(pnp_plan* p, pnp_den* d, const float* cur, float* nxt, double gamma, bool pos) {
   const float2* ys = reinterpret_cast<const float2*>(p->d_ysorted);
-  if (d->kind == PNP_DEN_HAAR) return normal_pass(p, ys, cur, EPI_HAAR, cur, nxt, (float)gamma, (float)d->t, true);
+  if (d->kind == PNP_DEN_HAAR)
+    return normal_pass(p, ys, cur, pos ? EPI_HAAR : EPI_HAAR_NOPOS, cur, nxt, (float)gamma, (float)d->t, true);
   if (int rc = normal_pass(p, ys, cur, EPI_GRAD, cur, p->d_img[1], (float)gamma, 0.f, true)) return rc;
-  if (d->kind == PNP_DEN_SARA) return sara_denoise(d, p->stream, p->d_img[1], nxt, p->n, p->d_acc, cur);
-  return cnn_denoise(d, p->stream, p->d_img[1], nxt, p->n, p->d_acc, cur);
+  if (d->kind == PNP_DEN_SARA) return sara_denoise(d, p->stream, p->d_img[1], nxt, p->n, p->d_acc, cur, pos);
+  return cnn_denoise(d, p->stream, p->d_img[1], nxt, p->n, p->d_acc, cur, pos);
 }
 
-// Captures two FB iterations (x -> work -> x) once and replays them on the
-// plan's private stream, joined to the caller's stream with events.
+// Replays two FB iterations (x -> work -> x) as one CUDA graph on the plan's private stream,
+// joined to the caller's stream with events.  The instantiated graph is kept in the plan and
+// reused by later pnp_fb_run calls while the denoiser, the iterate buffer, gamma, the
+// positivity choice, the holographic switch and the gridding work list are unchanged.
 struct GraphRunner {
   pnp_plan* p;
   pnp_den* d;
   float** buf;
   double gamma;
-  cudaGraphExec_t exec = nullptr;
-  int64_t kernels = 0;
-  GraphRunner(pnp_plan* p_, pnp_den* d_, float** b, double g) : p(p_), d(d_), buf(b), gamma(g) {}
-  ~GraphRunner() {
-    if (exec) cudaGraphExecDestroy(exec);
+  bool pos;
+  GraphRunner(pnp_plan* p_, pnp_den* d_, float** b, double g, bool ps) : p(p_), d(d_), buf(b), gamma(g), pos(ps) {}
+  bool cached() const {
+    const auto& c = p->graph;
+    return c.exec && c.den_serial == d->serial && c.x == buf[0] && c.gamma == gamma && c.epi == (pos ? 1 : 0) &&
+           c.holo == p->holo && c.epoch == p->epoch;
   }
   int capture() {
+    if (p->graph.exec) {
+      cudaGraphExecDestroy(p->graph.exec);
+      p->graph.exec = nullptr;
+    }
     cudaGraph_t g = nullptr;
     const int64_t before = g_launches.load();
     PNP_CUDA(cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = fb_iteration(p, d, buf[0], buf[1], gamma);
-    if (!rc) rc = fb_iteration(p, d, buf[1], buf[0], gamma);
+    int rc = fb_iteration(p, d, buf[0], buf[1], gamma, pos);
+    if (!rc) rc = fb_iteration(p, d, buf[1], buf[0], gamma, pos);
     cudaError_t e = cudaStreamEndCapture(p->stream, &g);
-    kernels = g_launches.load() - before;
+    const int64_t kernels = g_launches.load() - before;
     g_launches.fetch_sub(kernels);
     if (!rc && e != cudaSuccess) {
       cudaGetLastError();
       rc = fail(PNP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     }
+    cudaGraphExec_t exec = nullptr;
     if (!rc) {
       e = cudaGraphInstantiate(&exec, g, 0);
       if (e != cudaSuccess) {
@@ -152,6 +165,17 @@ struct GraphRunner {
       }
     }
     if (g) cudaGraphDestroy(g);
+    if (!rc) {
+      auto& c = p->graph;
+      c.exec = exec;
+      c.kernels = kernels;
+      c.den_serial = d->serial;
+      c.x = buf[0];
+      c.gamma = gamma;
+      c.epi = pos ? 1 : 0;
+      c.holo = p->holo;
+      c.epoch = p->epoch;
+    }
     return rc;
   }
   int run_pairs(int pairs) {
@@ -159,14 +183,14 @@ struct GraphRunner {
     PNP_CUDA(cudaEventRecord(p->ev_join[0], user));
     PNP_CUDA(cudaStreamWaitEvent(p->cstream, p->ev_join[0], 0));
     p->stream = p->cstream;
-    int rc = exec ? PNP_OK : capture();
+    int rc = cached() ? PNP_OK : capture();
     for (int i = 0; i < pairs && rc == PNP_OK; ++i) {
-      cudaError_t e = cudaGraphLaunch(exec, p->stream);
+      cudaError_t e = cudaGraphLaunch(p->graph.exec, p->stream);
       if (e != cudaSuccess) {
         cudaGetLastError();
         rc = fail(PNP_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
       } else {
-        g_launches.fetch_add(kernels);
+        g_launches.fetch_add(p->graph.kernels);
       }
     }
     p->stream = user;
@@ -201,8 +225,38 @@ int pnp_plan_create_stacked(pnp_plan** plan, int n, int K, int64_t M, const doub
                             const int8_t* J_per_row_host, int J, int weight_dtype, const int32_t* block_host,
                             int nblocks, const int32_t* stack_host, int nstacks, const double* w_centres_host,
                             void* stream) {
+  pnp_plan_desc d{};
+  d.n = n;
+  d.K = K;
+  d.M = M;
+  d.uvw_host = uvw_host;
+  d.dl = dl;
+  d.J_per_row_host = J_per_row_host;
+  d.J = J;
+  d.weight_dtype = weight_dtype;
+  d.block_host = block_host;
+  d.nblocks = nblocks;
+  d.stack_host = stack_host;
+  d.nstacks = nstacks;
+  d.w_centres_host = w_centres_host;
+  d.stream = stream;
+  if (nblocks < 1) return fail(PNP_ERR_INVALID_ARG, "nblocks must be >= 1");
+  if (nstacks < 1 || nstacks > 64) return fail(PNP_ERR_INVALID_ARG, "nstacks must lie in [1, 64]");
+  return pnp_plan_create_desc(plan, &d);
+}
+
+int pnp_plan_create_desc(pnp_plan** plan, const pnp_plan_desc* desc) {
   if (!plan) return fail(PNP_ERR_INVALID_ARG, "plan pointer is NULL");
   *plan = nullptr;
+  if (!desc) return fail(PNP_ERR_INVALID_ARG, "plan descriptor is NULL");
+  const int n = desc->n, K = desc->K, J = desc->J, weight_dtype = desc->weight_dtype;
+  const int64_t M = desc->M;
+  const double dl = desc->dl;
+  const double* uvw_host = desc->uvw_host;
+  const int nblocks = desc->nblocks > 0 ? desc->nblocks : 1;
+  const int nstacks = desc->nstacks > 0 ? desc->nstacks : 1;
+  const int32_t* stack_host = desc->stack_host;
+  const double* w_centres_host = desc->w_centres_host;
   if (n < 8 || (n & 1)) return fail(PNP_ERR_INVALID_ARG, "n must be even and >= 8");
   if (!is_pow2(K) || K < 64 || K > 16384) return fail(PNP_ERR_INVALID_ARG, "K must be a power of two in [64, 16384]");
   if (n > K / 2) return fail(PNP_ERR_INVALID_ARG, "n must be <= K/2 (at least 2x oversampling)");
@@ -210,9 +264,8 @@ int pnp_plan_create_stacked(pnp_plan** plan, int n, int K, int64_t M, const doub
   if (M < 0 || M > INT32_MAX) return fail(PNP_ERR_INVALID_ARG, "M must lie in [0, 2^31)");
   if (M > 0 && !uvw_host) return fail(PNP_ERR_INVALID_ARG, "uvw is NULL");
   if (weight_dtype != PNP_W_C64 && weight_dtype != PNP_W_BF16C) return fail(PNP_ERR_INVALID_ARG, "bad weight_dtype");
-  if (nblocks < 1) return fail(PNP_ERR_INVALID_ARG, "nblocks must be >= 1");
   if (!(dl >= 0.0) || !std::isfinite(dl)) return fail(PNP_ERR_INVALID_ARG, "dl must be finite and >= 0");
-  if (nstacks < 1 || nstacks > 64) return fail(PNP_ERR_INVALID_ARG, "nstacks must lie in [1, 64]");
+  if (nstacks > 64) return fail(PNP_ERR_INVALID_ARG, "nstacks must lie in [1, 64]");
   if (nstacks > 1 && (!stack_host && M > 0)) return fail(PNP_ERR_INVALID_ARG, "stack ids are NULL");
   if (nstacks > 1 && !w_centres_host) return fail(PNP_ERR_INVALID_ARG, "w_centres is NULL");
   if (nstacks > 1 && dl == 0.0) return fail(PNP_ERR_INVALID_ARG, "w-stacking needs dl > 0");
@@ -231,7 +284,7 @@ int pnp_plan_create_stacked(pnp_plan** plan, int n, int K, int64_t M, const doub
   p->dl = dl;
   p->wdtype = weight_dtype;
   p->nblocks = nblocks;
-  p->stream = reinterpret_cast<cudaStream_t>(stream);
+  p->stream = reinterpret_cast<cudaStream_t>(desc->stream);
   p->tile = K >= 128 ? 32 : 16;
   if (cudaGetDevice(&p->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
@@ -246,7 +299,8 @@ int pnp_plan_create_stacked(pnp_plan** plan, int n, int K, int64_t M, const doub
     free_plan(p);
     return fail(PNP_ERR_CUDA, "stream/event creation failed");
   }
-  int rc = plan_build(p, uvw_host, J_per_row_host, block_host, nstacks > 1 ? stack_host : nullptr);
+  int rc = plan_build(p, uvw_host, desc->J_per_row_host, desc->block_host, nstacks > 1 ? stack_host : nullptr,
+                      desc->row_scale_host);
   if (rc != PNP_OK) {
     std::string keep = t_err;
     free_plan(p);
@@ -255,6 +309,18 @@ int pnp_plan_create_stacked(pnp_plan** plan, int n, int K, int64_t M, const doub
   }
   *plan = p;
   return PNP_OK;
+}
+
+int pnp_plan_scale_data(pnp_plan* p, const float* y_in, float* y_out) {
+  if (!p || (p->M > 0 && (!y_in || !y_out))) return fail(PNP_ERR_INVALID_ARG, "NULL argument");
+  if (p->M == 0) return PNP_OK;
+  if (!p->d_rowscale) {
+    if (y_in != y_out)
+      PNP_CUDA(cudaMemcpyAsync(y_out, y_in, (size_t)p->M * sizeof(float2), cudaMemcpyDeviceToDevice, p->stream));
+    return PNP_OK;
+  }
+  return row_scale_c64(p->stream, reinterpret_cast<const float2*>(y_in), p->d_rowscale,
+                       reinterpret_cast<float2*>(y_out), p->M);
 }
 
 void pnp_plan_destroy(pnp_plan* plan) {
@@ -308,6 +374,7 @@ int pnp_plan_set_row_batch(pnp_plan* p, int row_batch) {
     return fail(PNP_ERR_INVALID_ARG, "row_batch must be 0, 1, 2 or 4");
   if (row_batch == 0) return PNP_OK;
   PNP_CUDA(cudaStreamSynchronize(p->stream));
+  if (row_batch != p->row_batch) ++p->epoch;
   p->row_batch = row_batch;
   return PNP_OK;
 }
@@ -488,6 +555,7 @@ int pnp_den_create_haar(pnp_den** den, double t, void* stream) {
   pnp_den* d = new pnp_den();
   d->kind = PNP_DEN_HAAR;
   d->t = t;
+  d->serial = ++g_den_serial;
   d->stream = reinterpret_cast<cudaStream_t>(stream);
   *den = d;
   return PNP_OK;
@@ -499,6 +567,7 @@ int pnp_den_create_cnn(pnp_den** den, const float* weights_host, const int32_t* 
   *den = nullptr;
   pnp_den* d = new pnp_den();
   d->kind = PNP_DEN_CNN;
+  d->serial = ++g_den_serial;
   d->stream = reinterpret_cast<cudaStream_t>(stream);
   int rc = cnn_create(d, weights_host, facet_rows_host, nfr, facet_cols_host, nfc, halo, n);
   if (rc != PNP_OK) {
@@ -522,6 +591,7 @@ int pnp_den_create_sara(pnp_den** den, int n, int levels, double gamma_lambda, d
     return fail(PNP_ERR_INVALID_ARG, "bad SARA parameters");
   pnp_den* d = new pnp_den();
   d->kind = PNP_DEN_SARA;
+  d->serial = ++g_den_serial;
   d->t = gamma_lambda;
   d->stream = reinterpret_cast<cudaStream_t>(stream);
   if (int rc = sara_create(d, n, levels, gamma_lambda, rho, prox_iters)) {
@@ -573,6 +643,16 @@ int denoise(pnp_den* d, const float* x_in, float* x_out, int n) {
 int pnp_fb_run(pnp_plan* p, pnp_den* d, const float* y, const pnp_params* prm, float* x, pnp_stats* st) {
   if (!p || !d || !prm || !x || (p->M > 0 && !y)) return fail(PNP_ERR_INVALID_ARG, "NULL argument");
   if (prm->max_iter < 0) return fail(PNP_ERR_INVALID_ARG, "max_iter must be >= 0");
+  if (!std::isfinite(prm->alpha)) return fail(PNP_ERR_INVALID_ARG, "alpha must be finite");
+  if (prm->positivity != PNP_POSITIVITY_ON && prm->positivity != PNP_POSITIVITY_OFF)
+    return fail(PNP_ERR_INVALID_ARG, "positivity must be PNP_POSITIVITY_ON or PNP_POSITIVITY_OFF");
+  if (prm->fallback != 0 && prm->fallback != 1) return fail(PNP_ERR_INVALID_ARG, "fallback must be 0 or 1");
+  if (prm->fallback && (!(prm->fallback_t >= 0) || !std::isfinite(prm->fallback_t)))
+    return fail(PNP_ERR_INVALID_ARG, "fallback_t must be finite and >= 0");
+  const double alpha = prm->alpha > 0 ? prm->alpha : 1.0;
+  const bool pos = prm->positivity == PNP_POSITIVITY_ON;
+  const bool fallback = prm->fallback == 1 && d->kind == PNP_DEN_CNN;
+  const int64_t N = (int64_t)p->n * p->n;
   double L = prm->L;
   if (!(L > 0)) {
     if (int rc = op_norm(p, nullptr, 500, 1e-6, &L, nullptr)) return rc;
@@ -580,15 +660,32 @@ int pnp_fb_run(pnp_plan* p, pnp_den* d, const float* y, const pnp_params* prm, f
   const double gamma = prm->gamma > 0 ? prm->gamma : 1.98 / L;
   const int check = prm->check_every > 0 ? prm->check_every : 10;
   const bool graph = prm->use_graph != 0;
-  const int bit = 1 << d->kind;
-  if (int rc = permute_y(p, reinterpret_cast<const float2*>(y))) return rc;
+  // App. C, Eq. invpb2: iterate on y / alpha from x / alpha
+  if (int rc = permute_y(p, reinterpret_cast<const float2*>(y), (float)(1.0 / alpha))) return rc;
   if (p->holo)
     if (int rc = holo_dirty_grid(p)) return rc;  // G^H y once per run (App. E, Eq. phidagphi)
+  if (alpha != 1.0)
+    if (int rc = mul_image(p->stream, x, x, N, (float)(1.0 / alpha))) return rc;
   float* buf[2] = {x, p->d_img[0]};
-  int c = 0, k = 0, rc = PNP_OK;
+  float* keep = p->d_img[2];  // fallback: the last checked finite iterate
+  pnp_den plain;              // the fallback's Haar denoiser (no device state)
+  plain.kind = PNP_DEN_HAAR;
+  plain.t = prm->fallback_t;
+  plain.stream = p->stream;
+  plain.serial = 0;
+  pnp_den* den = d;
+  int c = 0, k = 0, rc = PNP_OK, fell = -1, k_keep = 0;
   double h[2] = {0, 0}, rel = 0, xn = 0, xn_min = -1;
-  GraphRunner gr(p, d, buf, gamma);
+  if (fallback) {
+    plain.serial = ++g_den_serial;
+    if (cudaMemcpyAsync(keep, x, N * sizeof(float), cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(PNP_ERR_CUDA, "saving the start iterate failed");
+    }
+  }
   while (k < prm->max_iter && rc == PNP_OK) {
+    const int bit = 1 << den->kind;
+    GraphRunner gr(p, den, buf, gamma, pos);
     const int chunk = std::min(check, prm->max_iter - k);
     for (int done = 0; done < chunk && rc == PNP_OK;) {
       const int left = chunk - done;
@@ -596,7 +693,7 @@ int pnp_fb_run(pnp_plan* p, pnp_den* d, const float* y, const pnp_params* prm, f
         rc = gr.run_pairs(left / 2);
         done += 2 * (left / 2);
       } else {
-        rc = fb_iteration(p, d, buf[c], buf[1 - c], gamma);
+        rc = fb_iteration(p, den, buf[c], buf[1 - c], gamma, pos);
         if (rc == PNP_OK) p->primed |= bit;
         c = 1 - c;
         ++done;
@@ -607,23 +704,48 @@ int pnp_fb_run(pnp_plan* p, pnp_den* d, const float* y, const pnp_params* prm, f
     if ((rc = read_acc(p, h, 2))) break;
     xn = std::sqrt(h[1]);
     rel = xn > 0 ? std::sqrt(h[0]) / xn : 0.0;
-    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) {
-      rc = fail(PNP_ERR_DIVERGED, "iterate became non-finite at iteration " + std::to_string(k));
-      break;
-    }
-    if (prm->diverge_factor > 0 && xn_min > 0 && xn > prm->diverge_factor * xn_min) {
-      rc = fail(PNP_ERR_DIVERGED, "iterate norm grew past the divergence factor at iteration " + std::to_string(k));
+    std::string why;
+    if (!std::isfinite(h[0]) || !std::isfinite(h[1])) why = "iterate became non-finite at iteration " + std::to_string(k);
+    else if (prm->diverge_factor > 0 && xn_min > 0 && xn > prm->diverge_factor * xn_min)
+      why = "iterate norm grew past the divergence factor at iteration " + std::to_string(k);
+    if (!why.empty()) {
+      if (fallback && den == d) {
+        // App. C: the learned loop falls back to the plain one from the last checked finite iterate
+        if (cudaMemcpyAsync(buf[c], keep, N * sizeof(float), cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess) {
+          cudaGetLastError();
+          rc = fail(PNP_ERR_CUDA, "restoring the last finite iterate failed");
+          break;
+        }
+        den = &plain;
+        fell = k_keep;
+        k = k_keep;
+        xn_min = -1;
+        continue;
+      }
+      rc = fail(PNP_ERR_DIVERGED, why);
       break;
     }
     if (xn > 0 && (xn_min < 0 || xn < xn_min)) xn_min = xn;
+    if (fallback && den == d) {
+      if (cudaMemcpyAsync(keep, buf[c], N * sizeof(float), cudaMemcpyDeviceToDevice, p->stream) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(PNP_ERR_CUDA, "saving the checked iterate failed");
+        break;
+      }
+      k_keep = k;
+    }
     if (prm->tol > 0 && rel < prm->tol) break;
   }
   if (c == 1) {
-    cudaError_t e = cudaMemcpyAsync(x, buf[1], (size_t)p->n * p->n * sizeof(float), cudaMemcpyDeviceToDevice, p->stream);
+    cudaError_t e = cudaMemcpyAsync(x, buf[1], (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice, p->stream);
     if (e != cudaSuccess && rc == PNP_OK) {
       cudaGetLastError();
       rc = fail(PNP_ERR_CUDA, cudaGetErrorString(e));
     }
+  }
+  if (alpha != 1.0) {  // the solution of the rescaled problem times alpha
+    const int rc2 = mul_image(p->stream, x, x, N, (float)alpha);
+    if (rc == PNP_OK) rc = rc2;
   }
   if (st) {
     st->iters = k;
@@ -631,6 +753,7 @@ int pnp_fb_run(pnp_plan* p, pnp_den* d, const float* y, const pnp_params* prm, f
     st->gamma = gamma;
     st->rel_change = rel;
     st->x_norm = xn;
+    st->fallback_iter = fell;
   }
   return rc;
 }

@@ -100,7 +100,7 @@ __global__ void idwt_axis0(const float* __restrict__ in, float* __restrict__ out
   }
 }
 
-// mode 0: s = v / 3;  mode 1: s += v / 3;  mode 2: x = max(0, z - (s + v / 3))
+// mode 0: s = v / 3;  mode 1: s += v / 3;  mode 2: x = max(0, z - (s + v / 3));  mode 3: x = z - (s + v / 3)
 __global__ void sara_accum(const float* __restrict__ v, float* __restrict__ s, const float* __restrict__ z,
                            float* __restrict__ x, int64_t count, int mode) {
   const float third = 1.f / 3.f;
@@ -108,7 +108,8 @@ __global__ void sara_accum(const float* __restrict__ v, float* __restrict__ s, c
     const float a = v[i] * third;
     if (mode == 0) s[i] = a;
     else if (mode == 1) s[i] += a;
-    else x[i] = fmaxf(0.f, z[i] - (s[i] + a));
+    else if (mode == 2) x[i] = fmaxf(0.f, z[i] - (s[i] + a));
+    else x[i] = z[i] - (s[i] + a);
   }
 }
 
@@ -198,13 +199,13 @@ int basis_synthesis(SaraState* S, cudaStream_t s, int b, const float* c, float* 
 }
 
 // x = max(0, z - Psi u)
-int primal(SaraState* S, cudaStream_t s, const float* z, float* x) {
+int primal(SaraState* S, cudaStream_t s, const float* z, float* x, bool positivity) {
   const int64_t N = (int64_t)S->n * S->n;
   sara_accum<<<grid1(N), 256, 0, s>>>(S->u, S->S, nullptr, nullptr, N, 0);
   PNP_CHECK_LAUNCH();
   for (int b = 1; b < SARA_BASES; ++b) {
     if (int rc = basis_synthesis(S, s, b, S->u + (size_t)b * N, S->A)) return rc;
-    sara_accum<<<grid1(N), 256, 0, s>>>(S->A, S->S, z, x, N, b == SARA_BASES - 1 ? 2 : 1);
+    sara_accum<<<grid1(N), 256, 0, s>>>(S->A, S->S, z, x, N, b == SARA_BASES - 1 ? (positivity ? 2 : 3) : 1);
     PNP_CHECK_LAUNCH();
   }
   return PNP_OK;
@@ -261,11 +262,12 @@ void sara_destroy(pnp_den* d) {
 }
 
 // the prox by S->iters dual-FB iterations from the kept u; out = x; FP64 norms into acc[0..1]
-int sara_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc, const float* x_prev) {
+int sara_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, double* acc, const float* x_prev,
+                 bool positivity) {
   SaraState* S = static_cast<SaraState*>(d->impl);
   if (!S || n != S->n) return fail(PNP_ERR_INVALID_ARG, "image side differs from the SARA denoiser's");
   const int64_t N = (int64_t)n * n;
-  if (int rc = primal(S, s, z, out)) return rc;
+  if (int rc = primal(S, s, z, out, positivity)) return rc;
   for (int it = 0; it < S->iters; ++it) {
     sara_dual<<<grid1(N), 256, 0, s>>>(S->u, out, S->w, (float)S->gl, N);  // the Dirac basis
     PNP_CHECK_LAUNCH();
@@ -274,7 +276,7 @@ int sara_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, 
       sara_dual<<<grid1(N), 256, 0, s>>>(S->u + (size_t)b * N, S->A, S->w + (size_t)b * N, (float)S->gl, N);
       PNP_CHECK_LAUNCH();
     }
-    if (int rc = primal(S, s, z, out)) return rc;
+    if (int rc = primal(S, s, z, out, positivity)) return rc;
   }
   if (acc) {
     sara_norms<<<grid1(N), 256, 0, s>>>(out, x_prev, N, acc);

@@ -88,6 +88,20 @@ __global__ void fill_kernel(float* out, int64_t count, float v) {
     out[i] = v;
 }
 
+__global__ void mul_kernel(const float* __restrict__ in, float* __restrict__ out, int64_t count, float f) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i] * f;
+}
+
+// y_out[m] = d[m] y_in[m] (complex by real, per row)
+__global__ void rowscale_kernel(const float2* y_in, const float* __restrict__ d, float2* y_out, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = y_in[i];
+    const float s = d[i];
+    y_out[i] = make_float2(v.x * s, v.y * s);
+  }
+}
+
 __global__ void zero_kernel(double* acc, int count) {
   if (threadIdx.x < count) acc[threadIdx.x] = 0.0;
 }
@@ -124,6 +138,19 @@ int scale_image(cudaStream_t s, const float* in, float* out, int64_t count, cons
 
 int fill_image(cudaStream_t s, float* out, int64_t count, float v) {
   fill_kernel<<<grid_for(count), 256, 0, s>>>(out, count, v);
+  PNP_CHECK_LAUNCH();
+  return PNP_OK;
+}
+
+int mul_image(cudaStream_t s, const float* in, float* out, int64_t count, float f) {
+  mul_kernel<<<grid_for(count), 256, 0, s>>>(in, out, count, f);
+  PNP_CHECK_LAUNCH();
+  return PNP_OK;
+}
+
+int row_scale_c64(cudaStream_t s, const float2* y_in, const float* d, float2* y_out, int64_t count) {
+  if (count == 0) return PNP_OK;
+  rowscale_kernel<<<grid_for(count), 256, 0, s>>>(y_in, d, y_out, count);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }

@@ -9,7 +9,9 @@
   upper bound on the sky's peak by which the problem is rescaled before a
   learned denoiser trained on peak-normalised images is applied (App. C, F);
 * sigma = tau / (alpha sqrt(2L)), the noise level a denoiser must be trained
-  for to act on the rescaled problem (Eq. sigma).
+  for to act on the rescaled problem (Eq. sigma), and conversely the alpha that
+  matches a problem to a denoiser trained at a given sigma (App. F: one
+  denoiser for several data sets, each rescaled by its own alpha).
 
 Every operator application runs in the library's kernels; only scalars are
 combined here.
@@ -42,3 +44,11 @@ def imaging_parameters(plan, y, tau: float, v0=None, max_it: int = 1000, tol: fl
     noise = tau / np.sqrt(2.0 * L)
     return dict(L=L, power_iters=it, gamma=1.98 / L, tau=tau, noise_level=noise, beta=beta, alpha=alpha,
                 sigma=noise / alpha)
+
+
+def alpha_for_denoiser(tau: float, L: float, sigma_train: float) -> float:
+    """alpha with tau / (alpha sqrt(2L)) = sigma_train: Eq. sigma solved for alpha (App. F).
+
+    A valid rescaling needs alpha >= the peak of the sought image; callers take the larger of this
+    and the dirty-peak bound."""
+    return tau / (sigma_train * np.sqrt(2.0 * L))

@@ -14,7 +14,7 @@ from .meerkat import (  # noqa: F401
     SEED_STREAMS, rng_for, antenna_layout, uvw_track, imaging_geometry,
     j_per_row_by_w_quartile, sky_model, training_image, complex_normal,
     noise_std_for_isnr, radial_blocks, facet_layout, w_stacks, w_stacks_min_taps,
-    j_per_row_stacked,
+    j_per_row_stacked, briggs_weights,
 )
 from .configs import CONFIGS, make_problem  # noqa: F401
 from .weights import cnn_init  # noqa: F401,E402

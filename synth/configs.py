@@ -20,9 +20,11 @@ CONFIGS = {
     "C1": dict(n=2048, K=4096, M=20_000_000, hours=12.0, supports=(7, 9, 12, 16),
                w_spread=4.0, isnr_db=40.0, n_blocks=1, facets=(4, 512, 512), halo=32, iters=200),
     "C3": dict(n=4096, K=8192, M=20_000_000, hours=12.0, supports=(7, 9, 12, 16),
-               w_spread=4.0, isnr_db=40.0, n_blocks=64, facets=(4, 768, 1280), halo=32, iters=200),
+               w_spread=4.0, isnr_db=40.0, n_blocks=64, facets=(4, 768, 1280), halo=32, iters=200,
+               robust=0.0),
     "C4": dict(n=8192, K=16384, M=25_000_000, hours=12.0, supports=(7, 8, 8, 9),
-               w_spread=2.0, isnr_db=40.0, n_blocks=1, facets=(8, 1024, 1024), halo=32, iters=500),
+               w_spread=2.0, isnr_db=40.0, n_blocks=1, facets=(8, 1024, 1024), halo=32, iters=500,
+               robust=0.0),
 }
 
 
@@ -33,6 +35,8 @@ def make_problem(name: str, M: int | None = None, n: int | None = None, K: int |
 
     Returns a dict with n, K, M, omega (M, 2) rad/px, w (M,) wavelengths, dl,
     J_per_row (int8 or None for a single J=7), x_true (n, n) float64 sky,
+    imaging_weight (M,) Briggs weights (robust 0, Sec. 3) for the wide-field workloads
+    (None for the others: natural weighting),
     noise (M,) standard complex normal draws, block (M,) int32, facet widths,
     and the w-stack layout: stack (M,) int32 ids and w_centres (n_stacks,).  With
     n_stacks > 1 (w-stacking hybrid, App. E) the stacks are the minimum-taps
@@ -65,6 +69,8 @@ def make_problem(name: str, M: int | None = None, n: int | None = None, K: int |
         out["x_true"] = mk.sky_model(nn, mk.rng_for("sky", root_seed),
                                      n_points=int(round(200 * scale)), n_blobs=5)
     out["noise"] = mk.complex_normal(m, mk.rng_for("noise", root_seed))
+    robust = cfg.get("robust")
+    out["imaging_weight"] = None if robust is None else mk.briggs_weights(omega, nn, robust)
     out["block"] = (mk.radial_blocks(omega, cfg["n_blocks"], mk.rng_for("blocks", root_seed))
                     if cfg["n_blocks"] > 1 else np.zeros(m, dtype=np.int32))
     if cfg["facets"] is not None:

@@ -88,6 +88,31 @@ def imaging_geometry(uvw_lambda: np.ndarray, n: int, K: int, nyquist_frac: float
     return omega, w, dl
 
 
+def briggs_weights(omega: np.ndarray, n: int, robust: float) -> np.ndarray:
+    """Briggs (robust) imaging weights of the visibilities (Briggs 1995), float64 (M,).
+
+    Sec. 3 images data weighted by this scheme with robust parameter 0; the weights are a
+    property of the data set, fixed before imaging, and reach the imaging problem as an
+    input like the uv coverage.  Each row (natural weight 1) falls in a cell of the n x n uv
+    grid whose spacing is the inverse field of view (cell = 2 pi / n rad/px in omega); W_k
+    counts the rows in cell k together with the rows whose conjugate (-u, -v) lands there
+    (each baseline samples both).  With f^2 = (5 * 10^-robust)^2 / (sum_m W_k(m) / M), the
+    mean cell occupancy seen by a visibility, a row in cell k gets 1 / (1 + W_k f^2):
+    robust -> +inf gives natural weighting (all 1), robust -> -inf uniform weighting (1 / W_k
+    up to a constant).
+    """
+    omega = np.asarray(omega, dtype=np.float64)
+    k = np.rint(omega * (n / (2.0 * np.pi))).astype(np.int64) % n
+    cell = k[:, 0] * n + k[:, 1]
+    conj = ((-k[:, 0]) % n) * n + ((-k[:, 1]) % n)
+    W = (np.bincount(cell, minlength=n * n) + np.bincount(conj, minlength=n * n)).astype(np.float64)
+    Wm = W[cell]
+    if Wm.size == 0:
+        return np.zeros(0)
+    f2 = (5.0 * 10.0 ** (-robust)) ** 2 / (Wm.sum() / Wm.size)
+    return 1.0 / (1.0 + Wm * f2)
+
+
 def j_per_row_by_w_quartile(w: np.ndarray, supports=(7, 9, 12, 16)) -> np.ndarray:
     """Per-row kernel support J (int8): the q-th |w| quartile gets supports[q]."""
     aw = np.abs(w)

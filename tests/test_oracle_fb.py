@@ -155,3 +155,38 @@ def test_pnp_fb_fixed_point_and_history():
     x, h = fb.pnp_fb(op, y, gamma, den, 3000, tol=1e-12, x_true=x_true)
     assert np.allclose(den(fb.gradient_step(op, x, y, gamma)), x, atol=1e-8 * abs(x).max())
     assert len(h["rel_change"]) == len(h["f"]) == len(h["snr"])
+
+
+def test_weighted_operator_dirty_beam_and_adjoint():
+    """Data weights d_m on the rows (Sec. 3, Briggs): the weighted dirty beam at the phase centre is
+    sum_m d_m^2 (y_m = 1 exactly for a delta at the centre, so only the NUFFT error remains), which
+    fails if the weights were applied once or not squared; the adjoint identity holds to 1e-12."""
+    rng = np.random.default_rng(21)
+    n, K, M = 16, 32, 500
+    omega = rng.uniform(-0.8 * np.pi, 0.8 * np.pi, (M, 2))
+    d = np.sqrt(synth.briggs_weights(omega, n, 0.0))
+    op = nu.Operator(n, K, omega, J=7, row_scale=d)
+    delta = np.zeros((n, n))
+    delta[n // 2, n // 2] = 1.0
+    assert fb.psf_peak(op) == pytest.approx(np.sum(d ** 2), rel=2e-6)
+    assert np.allclose(op.forward(delta), d, rtol=0, atol=2e-6)
+    x = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    r = synth.complex_normal(M, rng)
+    lhs = np.vdot(op.forward(x), r)
+    rhs = np.vdot(x, op.adjoint_complex(r))
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(op.forward(x)) * np.linalg.norm(r)
+
+
+def test_alpha_rescaling_is_exact_for_the_haar_loop():
+    """App. C, Eq. invpb2: soft thresholding and positivity are positively homogeneous, so the loop on
+    y / alpha with threshold t / alpha, multiplied by alpha, is the loop on y with threshold t."""
+    op, rng = _small_problem(n=16, K=32, M=800, seed=3)
+    x_true = np.maximum(rng.standard_normal((16, 16)), 0)
+    y = op.forward(x_true) + 0.05 * synth.complex_normal(op.M, rng)
+    L, _, _ = fb.power_iteration(op, rng.standard_normal((16, 16)), 2000, 1e-12)
+    gamma, t, alpha = fb.step_size(L), 0.02, 7.5
+    x1, _ = fb.pnp_fb(op, y, gamma, lambda z: fb.haar_denoise(z, t), 40)
+    x2, _ = fb.pnp_fb(op, y, gamma, lambda z: fb.haar_denoise(z, t / alpha), 40, alpha=alpha)
+    assert np.allclose(x1, x2, rtol=1e-12, atol=1e-12 * abs(x1).max())
+    x3, _ = fb.pnp_fb(op, y, gamma, lambda z: fb.haar_denoise(z, t), 40, alpha=alpha)
+    assert not np.allclose(x1, x3, rtol=1e-6)   # the threshold does not scale by itself
