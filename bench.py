@@ -70,6 +70,8 @@ def parse():
                     help="iterations of the plain loop whose final SNR (minus 0.5 dB) is the time-to-SNR target")
     ap.add_argument("--no-fne", dest="fne", action="store_false",
                     help="skip the learned loop with the penalised network")
+    ap.add_argument("--weights", default=None, help="network of the learned loop (default: the committed one)")
+    ap.add_argument("--weights-fne", default=None, help="penalised network of the learned_fne line")
     ap.add_argument("--kernel-case", choices=["gridding", "cnn", "fft"], default=None,
                     help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
     ap.add_argument("--cnn-side", type=int, default=4096,
@@ -357,6 +359,9 @@ def _thin(trace, every):
 
 
 def run_gpu(args):
+    global WEIGHTS, WEIGHTS_FNE
+    WEIGHTS = args.weights or WEIGHTS
+    WEIGHTS_FNE = args.weights_fne or WEIGHTS_FNE
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)

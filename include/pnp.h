@@ -116,6 +116,7 @@ typedef struct pnp_plan_info {
   int row_batch;        /* rows of a run whose residuals one warp forms together */
   int nstacks;          /* w-stacks P of the operator (1: w wholly in G)      */
   int64_t holographic_bytes; /* device bytes of the holographic H (0: not built) */
+  int compensated;      /* 1: gridding sums are compensated (pnp_plan_set_compensated) */
 } pnp_plan_info;
 
 /* ------------------------------------------------------------------ plans */
@@ -210,6 +211,15 @@ int pnp_plan_set_unit_nnz(pnp_plan* plan, int64_t unit_nnz);
  * and phi_adjoint keep using G.  enable == 0 switches back (H is kept).  Plans with several
  * w-stacks: PNP_ERR_UNSUPPORTED.  Synchronous. */
 int pnp_plan_set_holographic(pnp_plan* plan, int enable);
+
+/* Compensated summation of the gridding pass's scatter-add (G^H r, App. A; Eq. phidagphi sums
+ * many rows into each grid cell).  With enable = 1 (the default) every atomic addition of a work
+ * unit's partial sums into the output grid is followed by the addition of its exact rounding
+ * error (TwoSum, from the value the atomic returns) into a second grid, and the adjoint FFT
+ * reads the sum of the two; in dense uv cells, where thousands of rows meet, this removes the
+ * error of the FP32 sums over work units.  enable = 0 uses plain FP32 atomics.  The plan holds
+ * the second grid (K^2 complex64) either way.  Synchronises the plan's stream. */
+int pnp_plan_set_compensated(pnp_plan* plan, int enable);
 
 /* Set how many rows of a run of rows sharing a tap window one warp of the
  * gridding pass forms the residuals of together (1, 2 or 4; 0 keeps the
@@ -361,6 +371,10 @@ int pnp_cnn_train_step(pnp_cnn_trainer* trainer, const float* u, const float* no
  * NULL skips one); clear_grads != 0 zeroes the gradients afterwards.  Returns
  * PNP_ERR_TIMEOUT if a bounded device wait gave up during training. */
 int pnp_cnn_trainer_read(pnp_cnn_trainer* trainer, float* weights_host, float* grads_host, int clear_grads);
+
+/* One Adam step (the update of pnp_cnn_train_step with update != 0) on the gradients accumulated
+ * so far, e.g. by steps with update = 0 whose gradients the caller has read; clears them. */
+int pnp_cnn_trainer_apply_update(pnp_cnn_trainer* trainer);
 
 /* Set the Adam step size used by later pnp_cnn_train_step calls (lr > 0); the
  * moment estimates and the step count are kept. */

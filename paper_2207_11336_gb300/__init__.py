@@ -33,7 +33,7 @@ EXPORTED = [
     "pnp_cnn_trainer_create", "pnp_cnn_trainer_destroy", "pnp_cnn_train_step", "pnp_cnn_trainer_read",
     "pnp_cnn_num_params", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm",
     "pnp_cnn_train_step_fne", "pnp_den_create_sara", "pnp_den_sara_reweight", "pnp_sara_transform",
-    "pnp_plan_create_desc", "pnp_plan_scale_data",
+    "pnp_plan_create_desc", "pnp_plan_scale_data", "pnp_plan_set_compensated", "pnp_cnn_trainer_apply_update",
 ]
 PNP_POSITIVITY_ON, PNP_POSITIVITY_OFF = 0, 1
 
@@ -70,7 +70,7 @@ class _Info(C.Structure):
                 ("n_units", C.c_int64), ("beta", C.c_double), ("dl", C.c_double),
                 ("device_bytes", C.c_int64), ("region_pitch", C.c_int), ("run_max", C.c_int),
                 ("unit_nnz", C.c_int64), ("row_batch", C.c_int), ("nstacks", C.c_int),
-                ("holographic_bytes", C.c_int64)]
+                ("holographic_bytes", C.c_int64), ("compensated", C.c_int)]
 
 
 _lib = None
@@ -90,6 +90,8 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
                                           vp, vp]
     L.pnp_plan_create_desc.argtypes = [C.POINTER(vp), C.POINTER(_PlanDesc)]
     L.pnp_plan_scale_data.argtypes = [vp, vp, vp]
+    L.pnp_plan_set_compensated.argtypes = [vp, i32]
+    L.pnp_cnn_trainer_apply_update.argtypes = [vp]
     L.pnp_plan_destroy.argtypes = [vp]
     L.pnp_plan_destroy.restype = None
     L.pnp_plan_get_info.argtypes = [vp, C.POINTER(_Info)]
@@ -136,7 +138,8 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
                  "pnp_den_device_status", "pnp_cnn_trainer_create", "pnp_cnn_train_step",
                  "pnp_cnn_trainer_read", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm",
                  "pnp_cnn_train_step_fne", "pnp_den_create_sara", "pnp_den_sara_reweight",
-                 "pnp_sara_transform", "pnp_plan_create_desc", "pnp_plan_scale_data"):
+                 "pnp_sara_transform", "pnp_plan_create_desc", "pnp_plan_scale_data",
+                 "pnp_plan_set_compensated", "pnp_cnn_trainer_apply_update"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -243,6 +246,10 @@ class Plan:
     def set_holographic(self, enable: bool = True):
         """Use the holographic H = G^H G in the FB loop and op_norm (App. E, Eq. phidagphi)."""
         _check(lib().pnp_plan_set_holographic(self._h, 1 if enable else 0))
+
+    def set_compensated(self, enable: bool = True):
+        """Compensated (TwoSum) summation of the gridding pass's flushes into the output grid."""
+        _check(lib().pnp_plan_set_compensated(self._h, 1 if enable else 0))
 
     def set_row_batch(self, row_batch: int):
         """Rows of a run whose residuals one warp forms together (1, 2 or 4)."""
@@ -483,6 +490,10 @@ class CnnTrainer:
         _check(lib().pnp_cnn_train_step(self._h, _ptr(u), _ptr(noise), float(sigma), 1 if update else 0,
                                         C.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
+
+    def apply_update(self):
+        """One Adam step on the gradients accumulated by steps with update=False (clears them)."""
+        _check(lib().pnp_cnn_trainer_apply_update(self._h))
 
     def set_lr(self, lr: float):
         """Adam step size for the following steps (moments are kept)."""

@@ -751,6 +751,11 @@ int pnp_cnn_trainer_read(pnp_cnn_trainer* T, float* weights_host, float* grads_h
   return PNP_OK;
 }
 
+int pnp_cnn_trainer_apply_update(pnp_cnn_trainer* T) {
+  if (!T) return fail(PNP_ERR_INVALID_ARG, "NULL trainer");
+  return adam_update(T);
+}
+
 int pnp_cnn_trainer_set_lr(pnp_cnn_trainer* T, double lr) {
   if (!T || !(lr > 0)) return fail(PNP_ERR_INVALID_ARG, "bad argument");
   T->lr = lr;

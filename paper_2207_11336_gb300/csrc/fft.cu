@@ -203,6 +203,7 @@ struct FftArgs {
   const float2* twp;       // radix-16 pass twiddles (TWP_ENTRIES)
   float2* tmp;             // T (K x n) or U (n x K)
   float2* grid;            // P2 output / Q1 input (re-zeroed)
+  float2* grid_lo;         // Q1: compensation terms added to the input (re-zeroed), or NULL
   float* out;              // Q2 output image
   double* acc;             // Q1 zeroes acc[0..3]; Q2 accumulates
   float gamma, t;
@@ -299,6 +300,13 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_q1(FftArgs A) {
   float2 v[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = g[j + i * T];
+  if (A.grid_lo) {  // the compensated sums: high part + rounding errors
+    float2* gl = A.grid_lo + (size_t)k1 * K;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = cadd(v[i], gl[j + i * T]);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) gl[j + i * T] = make_float2(0.f, 0.f);
+  }
 #pragma unroll
   for (int i = 0; i < 16; ++i) g[j + i * T] = make_float2(0.f, 0.f);
   fft_row<LOGK, +1>(v, s, j, A.tw, A.twp);
@@ -536,6 +544,7 @@ int fft_adjoint(pnp_plan* p, int mode, const float* x, float* out, float gamma, 
   A.twp = p->d_twp;
   A.tmp = p->d_tmp;
   A.grid = p->d_gridB;
+  A.grid_lo = p->compensated ? p->d_gridB_lo : nullptr;
   A.out = out;
   A.acc = p->d_acc;
   A.gamma = gamma;

@@ -41,8 +41,16 @@ struct GArgs {
   float2* y_out;        // caller order (G_DEGRID)
   const float2* gridA;  // input grid (G_DEGRID, G_FUSED)
   float2* gridB;        // output grid (G_GRID, G_FUSED)
+  float2* gridB_lo;     // compensation grid: the rounding error of every flush into gridB, or NULL
   int* status;          // bit 1: pipeline wait timed out; bit 2: inconsistent work list (chunk skipped)
 };
+
+// Rounding error of the float sum s = a + b (Knuth's TwoSum): a + b = s + err exactly.  The
+// intrinsics keep the compiler from contracting or reassociating the sequence.
+__device__ __forceinline__ float two_sum_err(float a, float b, float s) {
+  const float bb = __fsub_rn(s, a);
+  return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
 
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -435,7 +443,17 @@ __global__ void __launch_bounds__(GPASS_THREADS, 1) gpass(GArgs A) {
         const int i = c / S, jj = c - i * S;
         const float2 v = make_float2(sy_re[i * P + jj], sy_im[i * P + jj]);
         if (v.x != 0.f || v.y != 0.f) {
-          atomicAdd(&A.gridB[((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km)], v);
+          const size_t g = ((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km);
+          if (A.gridB_lo) {
+            // compensated summation: the atomic returns the value it added to, so the exact rounding
+            // error of its (round-to-nearest) sum goes to the compensation grid
+            const float2 old = atomicAdd(&A.gridB[g], v);
+            const float ex = two_sum_err(old.x, v.x, __fadd_rn(old.x, v.x));
+            const float ey = two_sum_err(old.y, v.y, __fadd_rn(old.y, v.y));
+            if (ex != 0.f || ey != 0.f) atomicAdd(&A.gridB_lo[g], make_float2(ex, ey));
+          } else {
+            atomicAdd(&A.gridB[g], v);
+          }
         }
       }
     }
@@ -583,6 +601,7 @@ int gridding_pass(pnp_plan* p, int mode, const float2* y_user, float2* y_out, in
   A.y_out = y_out;
   A.gridA = p->d_gridA;
   A.gridB = p->d_gridB;
+  A.gridB_lo = p->compensated ? p->d_gridB_lo : nullptr;
   A.status = p->d_status;
   cudaEvent_t ev;
   if (int rc = stage_begin(p, 1, &ev)) return rc;

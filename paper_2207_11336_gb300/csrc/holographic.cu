@@ -159,12 +159,30 @@ int holo_build_plan(pnp_plan* p) {
   return PNP_OK;
 }
 
+namespace {
+// out = hi + lo (lo may be NULL); hi and lo are left zero
+__global__ void take_grid(float2* __restrict__ hi, float2* __restrict__ lo, float2* __restrict__ out, int64_t count) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 v = hi[i];
+    hi[i] = make_float2(0.f, 0.f);
+    if (lo) {
+      const float2 e = lo[i];
+      v = make_float2(v.x + e.x, v.y + e.y);
+      lo[i] = make_float2(0.f, 0.f);
+    }
+    out[i] = v;
+  }
+}
+}  // namespace
+
 int holo_dirty_grid(pnp_plan* p) {
-  // G^H y from the sorted data: the gridding pass accumulates into the (zero) output grid
+  // G^H y from the sorted data: the gridding pass accumulates into the (zero) output grid and,
+  // compensated, its rounding errors into the compensation grid; dirty = their sum, both re-zeroed
   if (int rc = gridding_pass(p, G_GRID, p->d_ysorted, nullptr, 0)) return rc;
-  const size_t KK = (size_t)p->K * p->K;
-  PNP_CUDA(cudaMemcpyAsync(p->d_dirty, p->d_gridB, KK * sizeof(float2), cudaMemcpyDeviceToDevice, p->stream));
-  PNP_CUDA(cudaMemsetAsync(p->d_gridB, 0, KK * sizeof(float2), p->stream));
+  const int64_t KK = (int64_t)p->K * p->K;
+  const unsigned grid = (unsigned)std::min<int64_t>((KK + 255) / 256, (int64_t)p->num_sms * 16);
+  take_grid<<<grid, 256, 0, p->stream>>>(p->d_gridB, p->compensated ? p->d_gridB_lo : nullptr, p->d_dirty, KK);
+  PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
 

@@ -437,6 +437,7 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
   if (int rc = dev_alloc(p, &p->d_twp, TWP_ENTRIES)) return rc;
   if (int rc = dev_alloc(p, &p->d_gridA, KK)) return rc;
   if (int rc = dev_alloc(p, &p->d_gridB, KK)) return rc;
+  if (int rc = dev_alloc(p, &p->d_gridB_lo, KK)) return rc;
   if (int rc = dev_alloc(p, &p->d_tmp, (size_t)K * n)) return rc;
   const size_t wbytes = p->wdtype == PNP_W_BF16C ? 4 : 8;
   {
@@ -489,6 +490,7 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     PNP_CUDA(cudaMemcpy(p->d_twp, twp.data(), TWP_ENTRIES * sizeof(float2), cudaMemcpyHostToDevice));
   }
   PNP_CUDA(cudaMemset(p->d_gridB, 0, KK * sizeof(float2)));
+  PNP_CUDA(cudaMemset(p->d_gridB_lo, 0, KK * sizeof(float2)));
   PNP_CUDA(cudaMemset(p->d_acc, 0, 8 * sizeof(double)));
   PNP_CUDA(cudaMemset(p->d_status, 0, 4 * sizeof(int)));
   {

@@ -61,6 +61,7 @@ void free_plan(pnp_plan* p) {
   cudaFree(p->d_twp);
   cudaFree(p->d_gridA);
   cudaFree(p->d_gridB);
+  cudaFree(p->d_gridB_lo);
   cudaFree(p->d_tmp);
   cudaFree(p->d_w);
   cudaFree(p->d_cells);
@@ -348,6 +349,7 @@ int pnp_plan_get_info(const pnp_plan* p, pnp_plan_info* info) {
   info->nstacks = p->nstacks;
   info->holographic_bytes = p->d_H ? (int64_t)p->holo_S * p->holo_S * p->K * p->K * 8 : 0;
   info->unit_nnz = p->unit_nnz;
+  info->compensated = p->compensated ? 1 : 0;
   return PNP_OK;
 }
 
@@ -366,6 +368,14 @@ int pnp_plan_set_holographic(pnp_plan* p, int enable) {
     if (int rc = holo_build_plan(p)) return rc;
   }
   p->holo = enable != 0;
+  return PNP_OK;
+}
+
+int pnp_plan_set_compensated(pnp_plan* p, int enable) {
+  if (!p || (enable != 0 && enable != 1)) return fail(PNP_ERR_INVALID_ARG, "enable must be 0 or 1");
+  PNP_CUDA(cudaStreamSynchronize(p->stream));
+  if ((enable == 1) != p->compensated) ++p->epoch;
+  p->compensated = enable == 1;
   return PNP_OK;
 }
 
@@ -437,7 +447,8 @@ int pnp_plan_autotune(pnp_plan* p, int reps, int* run_max_out, int64_t* unit_nnz
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     // the timed passes accumulated into the output grid: start it from zero again
-    if (!rc && cudaMemsetAsync(p->d_gridB, 0, (size_t)p->K * p->K * sizeof(float2), p->stream) != cudaSuccess) {
+    if (!rc && (cudaMemsetAsync(p->d_gridB, 0, (size_t)p->K * p->K * sizeof(float2), p->stream) != cudaSuccess ||
+                cudaMemsetAsync(p->d_gridB_lo, 0, (size_t)p->K * p->K * sizeof(float2), p->stream) != cudaSuccess)) {
       cudaGetLastError();
       rc = fail(PNP_ERR_CUDA, "autotune: clearing the grid failed");
     }

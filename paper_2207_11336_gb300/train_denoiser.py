@@ -58,20 +58,26 @@ def image_pool(count: int, size: int, seed: int = 0, workers: int | None = None)
 
 
 def noisy_problem(name: str, stream=None):
-    """(problem dict, plan, x_true, y, tau) for a benchmark workload: y = Phi x_true + tau n."""
+    """(problem dict, plan, x_true, y, tau) for a benchmark workload: y = D (Phi x_true + tau_raw n) with
+    the workload's data weights D (Sec. 3: Briggs; none for natural weighting), the raw noise level set
+    by the input SNR, and tau the RMS of the weighted noise D tau_raw n."""
     import torch
     import synth
     import paper_2207_11336_gb300 as pnp
     prob = synth.make_problem(name)
     nblocks = int(prob["block"].max()) + 1
+    wimg = prob.get("imaging_weight")
+    d = None if wimg is None else np.sqrt(wimg)
     plan = pnp.Plan(prob["n"], prob["K"], prob["omega"], prob["w"], prob["dl"], prob["J_per_row"],
-                    block=prob["block"], nblocks=nblocks, stream=stream)
+                    block=prob["block"], nblocks=nblocks, stream=stream, row_scale=d)
     x_true = torch.from_numpy(prob["x_true"].astype(np.float32)).cuda()
     y0 = plan.phi_forward(x_true)
-    norm_y0 = float(torch.linalg.vector_norm(y0.to(torch.complex128)).item())
+    y0_raw = y0 if d is None else y0 / torch.from_numpy(d.astype(np.float32)).cuda()
+    norm_y0 = float(torch.linalg.vector_norm(y0_raw.to(torch.complex128)).item())
     tau = synth.noise_std_for_isnr(norm_y0, prob["M"], prob["isnr_db"])
-    y = (y0 + tau * torch.from_numpy(prob["noise"].astype(np.complex64)).cuda()).contiguous()
-    return prob, plan, x_true, y, tau
+    y = (y0 + tau * plan.scale_data(torch.from_numpy(prob["noise"].astype(np.complex64)).cuda())).contiguous()
+    tau_w = tau * (1.0 if wimg is None else float(np.sqrt(np.mean(wimg))))
+    return prob, plan, x_true, y, tau_w
 
 
 def noise_unit(sigma: float) -> float:

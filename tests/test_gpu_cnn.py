@@ -90,3 +90,36 @@ def test_pnp_fb_with_cnn_matches_oracle():
     x, st = plan.fb_run(den, yd, L=L, max_iter=iters, check_every=2)
     assert st.iters == iters
     assert rel_l2(to_host(x), x_ref) <= 5e-3
+
+
+def test_cnn_error_against_the_unrounded_fp64_network():
+    """The BF16 tensor-core network against the FP64 network without any rounding (the oracle's
+    exact definition), the error stated per result: N(z) and D(z).  Each of the 8 layers rounds
+    its weights and its input activations to BF16 (unit roundoff u = 2^-9); independent rounding
+    errors of relative size u on both factors of every product give about sqrt(2) u per layer,
+    and 8 layers in sequence about 4 u = 2^-7 on N(z), which is the bound asserted (with a factor
+    two of margin for correlated errors).  D(z) = z - N(z) carries the same absolute error, so
+    relative to D it scales by ||N|| / ||D||."""
+    import os
+    from paper_2207_11336_gb300.train_denoiser import load
+    wpath = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                         "paper_2207_11336_gb300", "weights", "dncnn_C3.npz")
+    cases = [("random init", _params(9), _sky(96, 10))]
+    if os.path.exists(wpath):
+        params, meta = load(wpath)
+        sig = float(meta["sigma"])
+        u = synth.training_image(96, np.random.default_rng(12))
+        cases.append(("trained, sky + sigma noise", params,
+                      u + sig * np.random.default_rng(13).standard_normal((96, 96))))
+    for name, params, z in cases:
+        zf = z.astype(np.float32).astype(np.float64)
+        den = pnp.CnnDenoiser(params, 96, halo=0)
+        d_gpu = to_host(den.denoise(to_dev_f32(zf)))
+        n_ref = ocnn.network(params, zf, bf16=False)
+        d_ref = np.maximum(zf - n_ref, 0)
+        live = d_ref > 0
+        e_n = rel_l2((zf - d_gpu)[live], n_ref[live])
+        e_d = rel_l2(d_gpu, d_ref)
+        print(f"{name}: BF16 network vs unrounded FP64 network: N(z) rel L2 {e_n:.2e}, D(z) rel L2 {e_d:.2e}")
+        assert e_n <= 2 * 2.0 ** -7, name
+        assert e_d <= 2 * 2.0 ** -7 * np.linalg.norm(n_ref[live]) / np.linalg.norm(d_ref) + 1e-6, name

@@ -71,3 +71,26 @@ def test_training_reduces_loss():
     assert np.mean(losses[-10:]) < 0.8 * np.mean(losses[:5])
     w, _ = tr.read()
     assert all(np.isfinite(W).all() and np.isfinite(b).all() for W, b in w)
+
+
+def test_gpu_adam_matches_oracle_over_three_updates():
+    """The GPU Adam kernel against the oracle's adam_step on the same gradients: each step the
+    gradients the GPU accumulated are read back and the oracle applies its update to the weights it
+    read before; the moments carry over three updates (bias correction at t = 1, 2, 3).  FP32 on
+    the GPU against FP64: the weights agree to 1e-6 of the step size."""
+    B, s, sigma, lr = 2, 32, 0.1, 1e-3
+    params = synth.cnn_init(np.random.default_rng(21), 64, 8, last_scale=0.05)
+    tr = pnp.CnnTrainer(params, B, s, lr=lr)
+    st = ocnn.adam_init(params)
+    w_prev, _ = tr.read()
+    for step in range(3):
+        u, nz = _batch(B, s, 30 + step)
+        tr.step(torch.from_numpy(u).cuda(), torch.from_numpy(nz).cuda(), sigma, update=False)
+        _, g = tr.read(weights=False, grads=True)
+        tr.apply_update()
+        w_gpu, _ = tr.read()
+        ref = ocnn.adam_step(w_prev, pnp.unpack_cnn_weights(g), st, lr=lr)
+        for (Wg, bg), (Wr, br) in zip(w_gpu, ref):
+            assert np.abs(Wg - Wr).max() <= 1e-6 * lr + 1e-7 * np.abs(Wr).max(), step
+            assert np.abs(bg - br).max() <= 1e-6 * lr + 1e-7 * np.abs(br).max(), step
+        w_prev = w_gpu

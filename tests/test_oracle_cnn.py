@@ -98,3 +98,24 @@ def test_residual_form_and_positivity():
     d = cnn.denoise(params, z, positivity=False)
     assert np.allclose(d, z - cnn.network(params, z))
     assert np.array_equal(cnn.denoise(params, z), np.maximum(d, 0))
+
+
+def test_adam_matches_torch_over_several_steps():
+    """The oracle's Adam beyond the first step (momentum and bias correction) against torch.optim.Adam
+    fed the same gradients, an independent implementation of Kingma & Ba's update."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(8)
+    params = _tiny_net(rng)
+    st = cnn.adam_init(params)
+    tp = [torch.tensor(a, dtype=torch.float64, requires_grad=True) for W, b in params for a in (W, b)]
+    opt = torch.optim.Adam(tp, lr=2e-3, betas=(0.9, 0.999), eps=1e-8)
+    cur = params
+    for step in range(5):
+        grads = [(rng.standard_normal(W.shape), rng.standard_normal(b.shape)) for W, b in params]
+        cur = cnn.adam_step(cur, grads, st, lr=2e-3)
+        for t, g in zip(tp, [a for gW, gb in grads for a in (gW, gb)]):
+            t.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        mine = [a for W, b in cur for a in (W, b)]
+        for a, t in zip(mine, tp):
+            assert np.allclose(a, t.detach().numpy(), rtol=1e-12, atol=1e-14), step
