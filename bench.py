@@ -41,8 +41,9 @@ WORKLOADS = {
     "C3": dict(name="C3", desc="4096^2 img, 8192^2 grid, 2e7 vis in 64 blocks, Briggs r0, w-folded G J7-16 c64"),
     "C1": dict(name="C1", desc="2048^2 img, 4096^2 grid, 2e7 vis, w-folded G J7-16 c64"),
     "C0": dict(name="C0", desc="256^2 img, 512^2 grid, 2e5 vis, KB J7"),
+    "C4": dict(name="C4", desc="8192^2 img, 16384^2 grid, 2.5e7 vis (one band), Briggs r0, w-folded G J7-9 bf16"),
 }
-BLOCKS = {"C3": 64, "C1": 1, "C0": 1}
+BLOCKS = {"C3": 64, "C1": 1, "C0": 1, "C4": 1}
 CPU_SAMPLE_ROWS = 4000
 
 
@@ -71,6 +72,8 @@ def parse():
     ap.add_argument("--no-fne", dest="fne", action="store_false",
                     help="skip the learned loop with the penalised network")
     ap.add_argument("--weights", default=None, help="network of the learned loop (default: the committed one)")
+    ap.add_argument("--band-mhz", type=float, default=1053.0,
+                    help="frequency band of the 8192^2 workload (C4): 1053 or 1399")
     ap.add_argument("--weights-fne", default=None, help="penalised network of the learned_fne line")
     ap.add_argument("--kernel-case", choices=["gridding", "cnn", "fft"], default=None,
                     help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
@@ -257,8 +260,12 @@ def run_reference(args):
     if rank != 0:
         return 0
     import synth
-    wl = WORKLOADS[args.workload]
-    prob = synth.make_problem(wl["name"])
+    wl = dict(WORKLOADS[args.workload])
+    if wl["name"] == "C4":
+        prob = synth.make_problem("C4", freq_hz=args.band_mhz * 1e6)
+        wl["desc"] = wl["desc"].replace("(one band)", "at %.0f MHz" % args.band_mhz)
+    else:
+        prob = synth.make_problem(wl["name"])
     from oracle import nufft as onu
     n, K, M = prob["n"], prob["K"], prob["M"]
     x = np.zeros((n, n))
@@ -374,13 +381,20 @@ def run_gpu(args):
     from paper_2207_11336_gb300.train_denoiser import load as load_weights
     import synth
 
-    wl = WORKLOADS[args.workload]
-    prob = synth.make_problem(wl["name"])
+    wl = dict(WORKLOADS[args.workload])
+    wide = wl["name"] == "C4"   # the wide-field scale: one band of two, BF16 G, 8 x 8 facets
+    if wide:
+        prob = synth.make_problem("C4", freq_hz=args.band_mhz * 1e6)
+        wl["desc"] = wl["desc"].replace("(one band)", "at %.0f MHz" % args.band_mhz)
+        for k in ("bf16_g", "wstacks", "holo_rows", "usara_prox_iters"):   # comparison lines of the 4096^2 case
+            setattr(args, k, 0)
+    else:
+        prob = synth.make_problem(wl["name"])
     n, K, M = prob["n"], prob["K"], prob["M"]
     stream = torch.cuda.current_stream()
     wimg = prob.get("imaging_weight")
     d = None if wimg is None else np.sqrt(wimg)   # Sec. 3: Briggs-weighted data, rows of G scaled by sqrt(w)
-    plan = pnp.Plan(n, K, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"],
+    plan = pnp.Plan(n, K, prob["omega"], prob["w"], prob["dl"], prob["J_per_row"], weight_dtype="bf16" if wide else "c64",
                     block=prob["block"], nblocks=BLOCKS[wl["name"]], stream=stream, row_scale=d)
     tune = plan.autotune(reps=2)   # run cap x unit size of the gridding pass, timed on this GPU
     info = plan.info
@@ -582,8 +596,9 @@ def run_gpu(args):
     g_ms_launch = g_ms / max(g_cnt, 1)
     # algorithmic bytes of one fused pass: G read once as complex64 weight + int32 column per tap, the
     # data y, and the grid read and written (12 B per tap, 8 B per row, 16 B per cell)
-    alg_bytes = info["nnz"] * 12 + M * 8 + 2 * K * K * 8
-    moved_bytes = info["nnz"] * (8 + 2) + M * 8 + 2 * K * K * 8   # what the pass stores: 16-bit cells
+    wbytes = 4 if wide else 8   # BF16 or complex64 weight per tap
+    alg_bytes = info["nnz"] * (wbytes + 4) + M * 8 + 2 * K * K * 8
+    moved_bytes = info["nnz"] * (wbytes + 2) + M * 8 + 2 * K * K * 8   # what the pass stores: 16-bit cells
     hbm, peak_kind = measured_peaks()
     achieved = alg_bytes / (g_ms_launch * 1e-3) / 1e9
     roof_cnn = None
@@ -634,7 +649,7 @@ def run_gpu(args):
                "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16" if learned else "f32",
                "data": "synthetic", "impl": "gpu",
                "config": {"workload": desc, "parallelism": f"replicas{ws}",
-                          "l2": "inputs larger than L2 (G %.1f GB)" % (info["nnz"] * 10 / 1e9),
+                          "l2": "inputs larger than L2 (G %.1f GB)" % (info["nnz"] * (wbytes + 2) / 1e9),
                           "nnz": info["nnz"], "denoiser": "cnn" if learned else "haar", "graph": True,
                           "gridding_autotune": tune, "region_pitch": info["region_pitch"]},
                "clocks": clk.summary(),

@@ -91,6 +91,7 @@ struct CnnState {
   int4* d_lstrips = nullptr;             // last layer's work list: strips of the facet cores (last_strips)
   int n_lstrips = 0;
   __nv_bfloat16* d_wlast = nullptr;      // last layer's B operand (last_wpack_index), output channel 0 of 16
+  uint32_t* d_wfrag = nullptr;           // last layer's weights as mma.sync B fragments [4 k][2 n][32 lanes][2]
   __nv_bfloat16* d_canvas[2] = {nullptr, nullptr};
   float* d_w1 = nullptr;                 // [64][9]  (BF16-rounded values)
   float* d_b = nullptr;                  // [8][64] biases (layer 8 uses entry 0)
@@ -98,6 +99,7 @@ struct CnnState {
   float* d_w8 = nullptr;                 // [9][64] (BF16-rounded values)
   int* d_status = nullptr;
   float b8 = 0.f;                        // last layer's bias (host copy)
+  bool last_tc = false;                  // layer 8 on the tcgen05 convolution instead of cnn_last
   CUtensorMap map[2][2];                 // TMA descriptors of the two canvases (main, halo boxes; conv64_tc)
 };
 
@@ -591,6 +593,152 @@ __global__ void __launch_bounds__(128) cnn_first(FirstArgs A) {
   }
 }
 
+// ------------------------------------------------------------ last layer (64 -> 1)
+// The last layer has one output channel, so as a 3 x 3 convolution it is 1/64 of a hidden layer's
+// work; run as the tensor-core convolution above it pays a hidden layer's MMA-issue cost (one
+// 4 KB A tile per (dx, K step)).  Here it is split instead into a per-pixel projection onto the
+// nine taps, P[y][x][t] = sum_c W8[c][t] h[y][x][c] (a GEMM with M = pixels, K = 64 channels,
+// N = 9 taps padded to 16, on the tensor cores with mma.sync: each activation is read once), and
+// a 3 x 3 gather N[y][x] = b8 + sum_t P[y + dy - 1][x + dx - 1][t] (t = 3 dy + dx) from a ring of
+// three projected rows in shared memory, fused with D(z) = max(0, z - N(z)) and the FP64
+// stopping-test sums.  A CTA walks one strip of the last layer's work list (128 core columns x
+// about 32 core rows of a facet) row by row; P covers the 144 pixels x0 - 1 .. x0 + 142 of each
+// activation row (9 M tiles of 16), so the gather never leaves the CTA.
+constexpr int LAST_PX = 144;   // projected pixels per row: x0 - 1 .. x0 + 142
+constexpr int LAST_TS = 9;     // taps kept per pixel in shared memory (row stride: conflict-free gathers)
+constexpr int LAST_THREADS = 128;
+
+struct LastArgs {
+  const __nv_bfloat16* canvas;  // layer-7 activations (canvas layout)
+  const int4* strips;           // last_strips: (f, x0, ya << 16 | rows, Hf << 16 | Wf), facet-local
+  int n_strips, Hc, Wc, n;
+  const int4* facets;           // (R0, C0, Hf, Wf)
+  const int4* cores;            // (r0, r1, c0, c1) in image coordinates
+  const uint32_t* wfrag;        // [4 k steps][2 n tiles][32 lanes][2] packed BF16 pairs
+  float b8;
+  const float* z;
+  const float* x_prev;
+  float* img;
+  double* acc;
+  int pos;
+};
+
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(LAST_THREADS) cnn_last(LastArgs A) {
+  __shared__ float sP[3][LAST_PX * LAST_TS];
+  __shared__ double red[2][LAST_THREADS / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, t4 = lane & 3;
+  uint32_t bw[4][2][2];  // this lane's B fragments, the whole kernel
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const uint2 v = reinterpret_cast<const uint2*>(A.wfrag)[(ks * 2 + nt) * 32 + lane];
+      bw[ks][nt][0] = v.x;
+      bw[ks][nt][1] = v.y;
+    }
+  double s0 = 0.0, s1 = 0.0;
+  const size_t plane = (size_t)A.Wc * 8;
+  for (int si = blockIdx.x; si < A.n_strips; si += gridDim.x) {
+    const int4 S = A.strips[si];
+    const int f = S.x, x0 = S.y, ya = S.z >> 16, R = S.z & 0xFFFF, Hf = S.w >> 16, Wf = S.w & 0xFFFF;
+    const int4 fc = A.facets[f], core = A.cores[f];
+    for (int r = ya - 1; r <= ya + R; ++r) {
+      // ---- project activation row r onto the taps: warp w takes M tiles w, w + 4, w + 8
+      float* P = sP[(r - ya + 1) % 3];
+      const bool row_ok = r >= 0 && r < Hf;
+      const size_t rbase = ((size_t)f * A.Hc + (row_ok ? r : 0)) * 8 * plane;
+      for (int mt = warp; mt < LAST_PX / 16; mt += LAST_THREADS / 32) {
+        const int p_lo = x0 - 1 + mt * 16 + g, p_hi = p_lo + 8;  // pixels of fragment rows g and g + 8
+        const bool ok_lo = row_ok && p_lo >= 0 && p_lo < Wf, ok_hi = row_ok && p_hi >= 0 && p_hi < Wf;
+        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          // channels 16 ks + 2 t4 (+1) sit in channel block 2 ks, 16 ks + 8 + 2 t4 (+1) in block 2 ks + 1
+          const uint32_t* b0 = reinterpret_cast<const uint32_t*>(A.canvas + rbase + (size_t)(2 * ks) * plane);
+          const uint32_t* b1 = reinterpret_cast<const uint32_t*>(A.canvas + rbase + (size_t)(2 * ks + 1) * plane);
+          uint32_t a[4];
+          a[0] = ok_lo ? __ldg(b0 + (size_t)p_lo * 4 + t4) : 0u;
+          a[1] = ok_hi ? __ldg(b0 + (size_t)p_hi * 4 + t4) : 0u;
+          a[2] = ok_lo ? __ldg(b1 + (size_t)p_lo * 4 + t4) : 0u;
+          a[3] = ok_hi ? __ldg(b1 + (size_t)p_hi * 4 + t4) : 0u;
+          mma_bf16_16816(d0, a, bw[ks][0][0], bw[ks][0][1]);
+          mma_bf16_16816(d1, a, bw[ks][1][0], bw[ks][1][1]);
+        }
+        // D fragment: (row g, cols 2 t4, 2 t4 + 1) and (row g + 8, same cols); taps 0..7 in tile 0, 8 in tile 1
+        const int pl = mt * 16 + g, ph = pl + 8;
+        P[pl * LAST_TS + 2 * t4] = d0[0];
+        P[pl * LAST_TS + 2 * t4 + 1] = d0[1];
+        P[ph * LAST_TS + 2 * t4] = d0[2];
+        P[ph * LAST_TS + 2 * t4 + 1] = d0[3];
+        if (t4 == 0) {
+          P[pl * LAST_TS + 8] = d1[0];
+          P[ph * LAST_TS + 8] = d1[2];
+        }
+      }
+      __syncthreads();
+      // ---- output row r - 1: its three projected rows are in the ring
+      const int yo = r - 1;
+      if (yo >= ya) {
+        const float* Pm = sP[(yo - ya) % 3];      // row yo - 1
+        const float* P0 = sP[(yo - ya + 1) % 3];  // row yo
+        const float* Pp = sP[(yo - ya + 2) % 3];  // row yo + 1
+        float nv = A.b8;
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const int q = (tid + dx) * LAST_TS;
+          nv += Pm[q + dx] + P0[q + 3 + dx] + Pp[q + 6 + dx];
+        }
+        const int iy = fc.x + yo, ix = fc.y + x0 + tid;
+        if (iy >= core.x && iy < core.y && ix >= core.z && ix < core.w) {
+          const size_t pix = (size_t)iy * A.n + ix;
+          const float zv = A.z[pix];
+          const float res = zv - nv;
+          const float o = A.pos ? fmaxf(0.f, res) : res;
+          A.img[pix] = o;
+          s1 += (double)o * o;
+          // fmaxf(0, NaN) is 0, so positivity would hide a non-finite input: poison the norms
+          if (!isfinite(zv)) s1 = __longlong_as_double(0x7ff8000000000000LL);
+          if (A.x_prev) {
+            const double dd = (double)o - A.x_prev[pix];
+            s0 += dd * dd;
+          }
+        }
+      }
+      __syncthreads();  // the slot of row r - 2 is overwritten next
+    }
+  }
+  if (A.acc) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (lane == 0) {
+      red[0][warp] = s0;
+      red[1][warp] = s1;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a0 = 0.0, a1 = 0.0;
+      for (int w = 0; w < LAST_THREADS / 32; ++w) {
+        a0 += red[0][w];
+        a1 += red[1][w];
+      }
+      atomicAdd(&A.acc[0], a0);
+      atomicAdd(&A.acc[1], a1);
+    }
+  }
+}
+
 // ------------------------------------------------------------ host helpers
 // B operand of the last layer: weight W8[0][ci][dy][dx] at [dx][ci / 8][2 - dy][co = 0 of 16][ci % 8]
 size_t last_wpack_index(int dy, int dx, int ci) {
@@ -734,6 +882,21 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
       w8[t * CH + ci] = bf16_round(W[off + ci * 9 + t]);
       wlast[last_wpack_index(t / 3, t % 3, ci)] = to_bf16_bits(W[off + ci * 9 + t]);
     }
+  // mma.sync B fragments of the tap projection: element (k, n) of K step ks / N tile nt is
+  // W8[c = 16 ks + k][tap = 8 nt + n] (zero for taps >= 9); lane l holds k = 2 (l % 4) (+1) in its
+  // first register and k + 8 (+9) in its second, n = l / 4, the lower k in the low half
+  std::vector<uint32_t> wfrag(4 * 2 * 32 * 2, 0u);
+  auto w8bits = [&](int c, int tap) -> uint32_t {
+    return tap < 9 ? (uint32_t)to_bf16_bits(W[off + c * 9 + tap]) : 0u;
+  };
+  for (int ks = 0; ks < 4; ++ks)
+    for (int nt = 0; nt < 2; ++nt)
+      for (int l = 0; l < 32; ++l) {
+        const int tap = 8 * nt + l / 4, k = 16 * ks + 2 * (l % 4);
+        uint32_t* o = &wfrag[((ks * 2 + nt) * 32 + l) * 2];
+        o[0] = w8bits(k, tap) | (w8bits(k + 1, tap) << 16);
+        o[1] = w8bits(k + 8, tap) | (w8bits(k + 9, tap) << 16);
+      }
   off += CH * 9;
   bias[7 * CH] = W[off];
   S->b8 = W[off];
@@ -755,6 +918,7 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   if (int rc = al((void**)&S->d_strips, std::max<size_t>(1, strips.size()) * sizeof(int4))) return rc;
   if (int rc = al((void**)&S->d_lstrips, std::max<size_t>(1, lstrips.size()) * sizeof(int4))) return rc;
   if (int rc = al((void**)&S->d_wlast, wlast.size() * 2)) return rc;
+  if (int rc = al((void**)&S->d_wfrag, wfrag.size() * 4)) return rc;
   if (int rc = al((void**)&S->d_w1, w1.size() * 4)) return rc;
   if (int rc = al((void**)&S->d_w8, w8.size() * 4)) return rc;
   if (int rc = al((void**)&S->d_b, bias.size() * 4)) return rc;
@@ -767,6 +931,7 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   if (!lstrips.empty())
     PNP_CUDA(cudaMemcpy(S->d_lstrips, lstrips.data(), lstrips.size() * sizeof(int4), cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_wlast, wlast.data(), wlast.size() * 2, cudaMemcpyHostToDevice));
+  PNP_CUDA(cudaMemcpy(S->d_wfrag, wfrag.data(), wfrag.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_w1, w1.data(), w1.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_w8, w8.data(), w8.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_b, bias.data(), bias.size() * 4, cudaMemcpyHostToDevice));
@@ -787,6 +952,7 @@ void cnn_destroy(pnp_den* d) {
   cudaFree(S->d_strips);
   cudaFree(S->d_lstrips);
   cudaFree(S->d_wlast);
+  cudaFree(S->d_wfrag);
   cudaFree(S->d_w1);
   cudaFree(S->d_w8);
   cudaFree(S->d_b);
@@ -823,12 +989,18 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
     PNP_CHECK_LAUNCH();
     cur = 1 - cur;
   }
-  {
-    // layer 8 on the tensor cores, fused with D(z) = max(0, z - N(z)) on the facet cores and the norms
+  if (S->last_tc) {
+    // layer 8 as the tensor-core convolution, fused with D(z) = max(0, z - N(z)) on the facet cores
     ConvArgs C{nullptr, S->d_wlast, nullptr, S->d_lstrips, S->n_lstrips, S->Hc, S->Wc, S->d_status, 2, nullptr,
                z, x_prev, out, n, S->d_facets, S->d_cores, S->b8, acc, positivity ? 1 : 0};
     const int grid = std::max(1, std::min(S->n_lstrips, sms));
     conv64_tc<NO_LAST><<<grid, CONV_THREADS, ConvGeom<NO_LAST>::SMEM, s>>>(C, S->map[cur][0], S->map[cur][1]);
+    PNP_CHECK_LAUNCH();
+  } else {
+    // layer 8 as a tap projection + 3 x 3 gather, fused with D(z) = max(0, z - N(z)) and the norms
+    LastArgs L{S->d_canvas[cur], S->d_lstrips, S->n_lstrips, S->Hc, S->Wc, n, S->d_facets, S->d_cores,
+               S->d_wfrag, S->b8, z, x_prev, out, acc, positivity ? 1 : 0};
+    cnn_last<<<std::max(1, S->n_lstrips), LAST_THREADS, 0, s>>>(L);
     PNP_CHECK_LAUNCH();
   }
   return PNP_OK;

@@ -225,7 +225,7 @@ __device__ __forceinline__ float2 cmul2(float2 a, float2 b) {
 // CH: the input is modulated by a w-stack's centre chirp (compiled separately so that the
 // plain operator keeps its register allocation)
 template <int LOGK, int R, bool CH>
-__global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_p1(FftArgs A) {
+__global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_p1(const __grid_constant__ FftArgs A) {
   constexpr int K = 1 << LOGK, T = K / 16, SROW = K + K / 16 + 1;
   extern __shared__ float2 smem[];
   const int rr = threadIdx.x / T, j = threadIdx.x % T;
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_p1(FftArgs A) {
 
 // ---------------------------------------------------------------- P2
 template <int LOGK, int R>
-__global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_p2(FftArgs A) {
+__global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_p2(const __grid_constant__ FftArgs A) {
   constexpr int K = 1 << LOGK, T = K / 16, SROW = K + K / 16 + 1;
   extern __shared__ float2 smem[];
   const int rr = threadIdx.x / T, j = threadIdx.x % T;
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_p2(FftArgs A) {
 
 // ---------------------------------------------------------------- Q1
 template <int LOGK, int R>
-__global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_q1(FftArgs A) {
+__global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_q1(const __grid_constant__ FftArgs A) {
   constexpr int K = 1 << LOGK, T = K / 16, SROW = K + K / 16 + 1;
   extern __shared__ float2 smem[];
   const int rr = threadIdx.x / T, j = threadIdx.x % T;
@@ -326,29 +326,41 @@ __device__ __forceinline__ float soft(float c, float t) {
   return m > 0.f ? copysignf(m, c) : 0.f;
 }
 
+// acc[0] += sum of v0, acc[1] += sum of v1 over the block: warp shuffles, then one pair of
+// partial sums per warp in shared memory (red: 2 doubles per warp) summed by thread 0
 __device__ __forceinline__ void block_reduce_add(double v0, double v1, double* acc, double* red) {
-  // red holds 2 doubles per thread; blocks narrower than a warp use the shared-memory path only
-  __syncthreads();
-  red[2 * threadIdx.x] = v0;
-  red[2 * threadIdx.x + 1] = v1;
-  __syncthreads();
-  for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      red[2 * threadIdx.x] += red[2 * (threadIdx.x + s)];
-      red[2 * threadIdx.x + 1] += red[2 * (threadIdx.x + s) + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (blockDim.x >= 32) {  // whole warps (blocks narrower than a warp keep one value per thread)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, o);
     }
-    __syncthreads();
   }
+  __syncthreads();  // red aliases the FFT buffer
+  if (blockDim.x < 32) {
+    red[2 * threadIdx.x] = v0;
+    red[2 * threadIdx.x + 1] = v1;
+  } else if (lane == 0) {
+    red[2 * warp] = v0;
+    red[2 * warp + 1] = v1;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    atomicAdd(&acc[0], red[0]);
-    atomicAdd(&acc[1], red[1]);
+    double s0 = 0.0, s1 = 0.0;
+    for (int w = 0; w < (blockDim.x < 32 ? (int)blockDim.x : (int)(blockDim.x >> 5)); ++w) {
+      s0 += red[2 * w];
+      s1 += red[2 * w + 1];
+    }
+    atomicAdd(&acc[0], s0);
+    atomicAdd(&acc[1], s1);
   }
 }
 
 // ---------------------------------------------------------------- Q2
 // Two image rows per CTA, processed one after the other through one FFT buffer.
 template <int LOGK, bool CH>
-__global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(FftArgs A) {
+__global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(const __grid_constant__ FftArgs A) {
   constexpr int K = 1 << LOGK, T = K / 16, SROW = K + K / 16 + 1;
   extern __shared__ float2 smem[];
   float* gs = reinterpret_cast<float*>(smem + SROW);  // 2 x n gradient values
