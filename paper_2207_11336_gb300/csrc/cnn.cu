@@ -77,7 +77,7 @@ constexpr int NO_LAST = 16;
 constexpr int EPI_WARPS = 16;                           // 2 row parities x 2 channel halves x 4 lane quarters
 constexpr int MMA_WARP = EPI_WARPS, TMA_WARP = EPI_WARPS + 1;
 constexpr int CONV_THREADS = (EPI_WARPS + 2) * 32;
-constexpr int FIRST_ROWS = 8;                           // cnn_first: image rows per block
+constexpr int FIRST_ROWS = 16;                          // cnn_first: image rows per block
 constexpr uint32_t CNN_WAIT_LIMIT = 1u << 26;
 
 struct CnnState {
@@ -517,79 +517,56 @@ struct FirstArgs {
   __nv_bfloat16* out;
 };
 
-constexpr int SEG_STRIDE = 9;  // uint4 per pixel in shared memory (8 channel blocks + 16 B of padding)
+// Layer 1 (1 -> 64).  A block covers a 32-pixel column segment of FIRST_ROWS rows of a facet;
+// warp w computes the 8 channels of channel block w for the segment's 32 pixels, row after row,
+// with that block's 72 weights and 8 biases in registers (each weight is loaded once per block,
+// not once per pixel).  The block stages the (FIRST_ROWS + 2) x 34 input window of z (zero
+// outside the extended facet: 'same' padding) in shared memory; a warp's store of one row is the
+// 32 pixels' 16-byte channel-block vectors, one contiguous 512-byte run of the block's plane.
+constexpr int FIRST_PX = 32;
 
-__global__ void __launch_bounds__(128) cnn_first(FirstArgs A) {
-  // grid (x segments of 128, groups of FIRST_ROWS rows, facet f): thread m computes the 64
-  // channels of pixel x0 + m row after row (a rolling 3 x 3 window of z in registers); the
-  // block writes each 8-channel plane of a row segment as one contiguous 2-KB run
-  __shared__ __align__(16) uint4 seg[TILE_PX * SEG_STRIDE];
-  __shared__ __align__(16) float sw[CH * 9];  // [c / 4][tap][c % 4]: one float4 per (4 channels, tap)
-  __shared__ __align__(16) float sb[CH];
-  const int f = blockIdx.z, ya = blockIdx.y * FIRST_ROWS, x0 = blockIdx.x * TILE_PX;
+__global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
+  __shared__ float zt[FIRST_ROWS + 2][FIRST_PX + 2];
+  const int f = blockIdx.z, ya = blockIdx.y * FIRST_ROWS, x0 = blockIdx.x * FIRST_PX;
   const int4 fc = A.facets[f];  // R0, C0, Hf, Wf
-  if (ya >= fc.z || x0 >= fc.w) return;  // outside the facet: the canvas keeps its zeros
-  const int yb = min(ya + FIRST_ROWS, fc.z);
-  for (int i = threadIdx.x; i < CH * 9; i += blockDim.x) {
-    const int ch = i / 9, t = i % 9;
-    sw[((ch >> 2) * 9 + t) * 4 + (ch & 3)] = A.w1[i];
-  }
-  if (threadIdx.x < CH) sb[threadIdx.x] = A.b1[threadIdx.x];
-  __syncthreads();
-  const float4* sw4 = reinterpret_cast<const float4*>(sw);
-  const float4* sb4 = reinterpret_cast<const float4*>(sb);
-  const int x = x0 + threadIdx.x;
-  const bool live = x < fc.w;
+  if (ya >= fc.z || x0 >= A.Wc) return;
   const float* zf = A.z + (size_t)f * A.zplane;
-  auto zat = [&](int yy, int xx) -> float {
-    return (live && yy >= 0 && yy < fc.z && xx >= 0 && xx < fc.w) ? zf[(size_t)(fc.x + yy) * A.n + fc.y + xx] : 0.f;
-  };
-  float zin[9];  // rows y-1, y, y+1 x columns x-1, x, x+1
+  for (int i = threadIdx.x; i < (FIRST_ROWS + 2) * (FIRST_PX + 2); i += blockDim.x) {
+    const int r = i / (FIRST_PX + 2), c = i % (FIRST_PX + 2);
+    const int yy = ya + r - 1, xx = x0 + c - 1;
+    zt[r][c] = (yy >= 0 && yy < fc.z && xx >= 0 && xx < fc.w) ? zf[(size_t)(fc.x + yy) * A.n + fc.y + xx] : 0.f;
+  }
+  const int cb = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float w[8][9], b[8];
 #pragma unroll
-  for (int t = 0; t < 6; ++t) zin[t + 3] = zat(ya + t / 3 - 1, x + t % 3 - 1);
-  const size_t plane = (size_t)A.Wc * 8;
+  for (int c = 0; c < 8; ++c) {
+    b[c] = A.b1[cb * 8 + c];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) w[c][t] = A.w1[(cb * 8 + c) * 9 + t];
+  }
+  __syncthreads();
+  const int x = x0 + lane;
+  if (x >= A.Wc) return;
+  const bool live = x < fc.w;
+  const int yb = min(ya + FIRST_ROWS, fc.z);
   for (int y = ya; y < yb; ++y) {
+    const int r = y - ya;
+    float zin[9];
 #pragma unroll
-    for (int t = 0; t < 6; ++t) zin[t] = zin[t + 3];
+    for (int t = 0; t < 9; ++t) zin[t] = zt[r + t / 3][lane + t % 3];
+    uint32_t pk[4];
 #pragma unroll
-    for (int t = 0; t < 3; ++t) zin[6 + t] = zat(y + 1, x + t - 1);
-    uint4 pk[8];
-    if (live) {
+    for (int c = 0; c < 8; c += 2) {
+      float a0 = b[c], a1 = b[c + 1];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        uint32_t wv[4];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int g = 2 * q + h;
-          float4 a = sb4[g];
-#pragma unroll
-          for (int t = 0; t < 9; ++t) {
-            const float4 w = sw4[g * 9 + t];
-            a.x = fmaf(w.x, zin[t], a.x);
-            a.y = fmaf(w.y, zin[t], a.y);
-            a.z = fmaf(w.z, zin[t], a.z);
-            a.w = fmaf(w.w, zin[t], a.w);
-          }
-          __nv_bfloat162 h0 = __floats2bfloat162_rn(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
-          __nv_bfloat162 h1 = __floats2bfloat162_rn(fmaxf(a.z, 0.f), fmaxf(a.w, 0.f));
-          wv[2 * h] = *reinterpret_cast<uint32_t*>(&h0);
-          wv[2 * h + 1] = *reinterpret_cast<uint32_t*>(&h1);
-        }
-        pk[q] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      for (int t = 0; t < 9; ++t) {
+        a0 = fmaf(w[c][t], zin[t], a0);
+        a1 = fmaf(w[c + 1][t], zin[t], a1);
       }
-    } else {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) pk[q] = make_uint4(0u, 0u, 0u, 0u);
+      __nv_bfloat162 h = __floats2bfloat162_rn(live ? fmaxf(a0, 0.f) : 0.f, live ? fmaxf(a1, 0.f) : 0.f);
+      pk[c / 2] = *reinterpret_cast<uint32_t*>(&h);
     }
-    __syncthreads();  // the previous row's segment has been stored
-#pragma unroll
-    for (int q = 0; q < 8; ++q) seg[threadIdx.x * SEG_STRIDE + q] = pk[q];
-    __syncthreads();
-    const size_t base = canvas_index(f, y, x0, 0, A.Hc, A.Wc);
-    for (int i = threadIdx.x; i < TILE_PX * 8; i += blockDim.x) {
-      const int q = i / TILE_PX, px = i % TILE_PX;
-      *reinterpret_cast<uint4*>(A.out + base + q * plane + px * 8) = seg[px * SEG_STRIDE + q];
-    }
+    *reinterpret_cast<uint4*>(A.out + canvas_index(f, y, x, cb * 8, A.Hc, A.Wc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
 }
 
@@ -970,7 +947,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
   const int sms = sms_of_device();
   {
     FirstArgs F{z, n, 0, S->d_facets, S->F, S->Hc, S->Wc, S->d_w1, S->d_b, S->d_canvas[0]};
-    cnn_first<<<dim3(S->Wc / TILE_PX, (S->Hc + FIRST_ROWS - 1) / FIRST_ROWS, S->F), TILE_PX, 0, s>>>(F);
+    cnn_first<<<dim3(S->Wc / FIRST_PX, (S->Hc + FIRST_ROWS - 1) / FIRST_ROWS, S->F), 256, 0, s>>>(F);
     PNP_CHECK_LAUNCH();
   }
   static bool attr = false;
@@ -1038,7 +1015,7 @@ std::vector<int4> conv_strips(int F, const int* Hf, const int* Wf) {
 int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, const int4* facets, int F, int Hc,
                      int Wc, const float* w1, const float* b1, __nv_bfloat16* out) {
   FirstArgs A{z, n, zplane, facets, F, Hc, Wc, w1, b1, out};
-  cnn_first<<<dim3(Wc / TILE_PX, (Hc + FIRST_ROWS - 1) / FIRST_ROWS, F), TILE_PX, 0, s>>>(A);
+  cnn_first<<<dim3(Wc / FIRST_PX, (Hc + FIRST_ROWS - 1) / FIRST_ROWS, F), 256, 0, s>>>(A);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }

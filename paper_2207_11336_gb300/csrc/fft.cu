@@ -134,7 +134,9 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int idx
 // Length-K FFT of one row.  On entry v[i] holds element j + i*K/16 of the
 // row; on exit v[i] holds output element j + i*K/16 (natural order).
 // s is this row's padded shared-memory buffer (K + K/16 float2).
-template <int LOGK, int DIR>
+// TWS: stride of the twiddle table tw for the radix-2/4/8 tail pass (the table holds exp(-2 pi i t / L)
+// for a length L = TWS 2^LOGK: the plan's length-K table serves the length-K/2 transforms with TWS = 2).
+template <int LOGK, int DIR, int TWS = 1>
 __device__ __forceinline__ void fft_row(float2 (&v)[16], float2* s, int j,
                                         const float2* __restrict__ tw, const float2* __restrict__ twp) {
   constexpr int K = 1 << LOGK;
@@ -174,7 +176,7 @@ __device__ __forceinline__ void fft_row(float2 (&v)[16], float2* s, int j,
 #pragma unroll
       for (int r = 0; r < RS; ++r) {
         u[r] = v[t + r * G];
-        if (r) u[r] = cmul(u[r], twiddle<DIR>(tw, r * jj));
+        if (r) u[r] = cmul(u[r], twiddle<DIR>(tw, r * jj * TWS));
       }
       if constexpr (RS == 2) dft2<DIR>(u[0], u[1]);
       if constexpr (RS == 4) dft4<DIR>(u[0], u[1], u[2], u[3]);
@@ -358,43 +360,13 @@ __device__ __forceinline__ void block_reduce_add(double v0, double v1, double* a
 }
 
 // ---------------------------------------------------------------- Q2
-// Two image rows per CTA, processed one after the other through one FFT buffer.
-template <int LOGK, bool CH>
-__global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(const __grid_constant__ FftArgs A) {
-  constexpr int K = 1 << LOGK, T = K / 16, SROW = K + K / 16 + 1;
+// Epilogue of the last inverse pass on two image rows a0, a0 + 1 whose gradient values
+// Re{Z^H F^H ...} sit in gs (2 x n, shared memory): the w-stack sum, then the adjoint / gradient
+// step / gradient step + Haar prox (+ positivity) / power-iteration norm, and the FP64 sums.
+template <bool CH>
+__device__ __forceinline__ void q2_epilogue(const FftArgs& A, float* gs, int a0, int j, int T) {
   extern __shared__ float2 smem[];
-  float* gs = reinterpret_cast<float*>(smem + SROW);  // 2 x n gradient values
-  const int j = threadIdx.x;
   const int n = A.n;
-  const int a0 = 2 * blockIdx.x;
-#pragma unroll 1
-  for (int q = 0; q < 2; ++q) {
-    const int a = a0 + q;
-    const float2* row = A.tmp + (size_t)a * K;
-    float2 v[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = row[j + i * T];
-    fft_row<LOGK, +1>(v, smem, j, A.tw, A.twp);
-    const float ca = A.cinv[a];
-    if (CH) {  // Re{conj(chirp) v}: the adjoint of the centre chirp of Z_s
-      const float2 cha = A.chirp[a];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int b = unpad_index(j + i * T, n, K);
-        if (b >= 0) {
-          const float2 c = cmul2(cha, A.chirp[b]);
-          gs[q * n + b] = (v[i].x * c.x + v[i].y * c.y) * ca * A.cinv[b];
-        }
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int b = unpad_index(j + i * T, n, K);
-        if (b >= 0) gs[q * n + b] = v[i].x * ca * A.cinv[b];
-      }
-    }
-  }
-  __syncthreads();
   if (CH && A.gacc_mode != GACC_NONE) {
     const size_t base = (size_t)a0 * n;
     for (int i = j; i < 2 * n; i += T) {
@@ -451,6 +423,219 @@ __global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(const __grid_constant
     block_reduce_add(s0, s1, A.acc, reinterpret_cast<double*>(smem));
 }
 
+// Two image rows per CTA, processed one after the other through one FFT buffer.
+template <int LOGK, bool CH>
+__global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(const __grid_constant__ FftArgs A) {
+  constexpr int K = 1 << LOGK, T = K / 16, SROW = K + K / 16 + 1;
+  extern __shared__ float2 smem[];
+  float* gs = reinterpret_cast<float*>(smem + SROW);  // 2 x n gradient values
+  const int j = threadIdx.x;
+  const int n = A.n;
+  const int a0 = 2 * blockIdx.x;
+#pragma unroll 1
+  for (int q = 0; q < 2; ++q) {
+    const int a = a0 + q;
+    const float2* row = A.tmp + (size_t)a * K;
+    float2 v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = row[j + i * T];
+    fft_row<LOGK, +1>(v, smem, j, A.tw, A.twp);
+    const float ca = A.cinv[a];
+    if (CH) {  // Re{conj(chirp) v}: the adjoint of the centre chirp of Z_s
+      const float2 cha = A.chirp[a];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int b = unpad_index(j + i * T, n, K);
+        if (b >= 0) {
+          const float2 c = cmul2(cha, A.chirp[b]);
+          gs[q * n + b] = (v[i].x * c.x + v[i].y * c.y) * ca * A.cinv[b];
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int b = unpad_index(j + i * T, n, K);
+        if (b >= 0) gs[q * n + b] = v[i].x * ca * A.cinv[b];
+      }
+    }
+  }
+  __syncthreads();
+  q2_epilogue<CH>(A, gs, a0, j, T);
+}
+
+// ---------------------------------------------------------------- split passes (K = 2n)
+// With twofold oversampling (K = 2n) each length-K transform of the operator halves into two
+// length-n transforms.  Forward, n non-zero inputs at the centred positions p mod K:
+//   V[2m] = DFT_n(u)[m],  V[2m + 1] = DFT_n(s w u)[m],
+// with u[e] the input at centred offset e (e < n/2) or e - n (e >= n/2), s[e] = +1 (e < n/2) or -1,
+// w[e] = exp(-2 pi i e / K).  Inverse, keeping the n centred outputs j in [-n/2, n/2):
+//   X[j] = IDFT_n(G[0::2])[j mod n] + exp(+2 pi i j / K) IDFT_n(G[1::2])[j mod n].
+// No transform runs over zero padding, and a length-n transform needs one shared-memory exchange
+// fewer than a length-2n one.  Layouts and epilogues are those of the general passes above.
+
+// P1 (split): image row a, output parity par (blockIdx.y): the even or odd half of its length-K
+// transform along axis 1, written transposed into T[k1 = 2m + par][a].
+template <int LOGK, int R, bool CH>
+__global__ void __launch_bounds__(R * (1 << LOGK) / 32) fft_p1s(const __grid_constant__ FftArgs A) {
+  constexpr int LN = LOGK - 1, N = 1 << LN, T = N / 16, SROW = N + N / 16 + 1, H = N / 2;
+  extern __shared__ float2 smem[];
+  const int rr = threadIdx.x / T, j = threadIdx.x % T, par = blockIdx.y;
+  const int a = blockIdx.x * R + rr;
+  const bool live = a < N;
+  float2* s = smem + rr * SROW;
+  const float ca = live ? A.cinv[a] : 0.f;
+  float2 v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int e = j + i * T, b = e < H ? e + H : e - H;
+    float2 val = make_float2(live ? A.x[(size_t)a * N + b] * ca * A.cinv[b] : 0.f, 0.f);
+    if (CH && live) {  // Z_s of a w-stack: the centre chirp, separable over the two axes
+      const float2 c = cmul(A.chirp[a], A.chirp[b]);
+      val = make_float2(val.x * c.x, val.x * c.y);
+    }
+    if (par) {
+      const float2 w = A.tw[e];
+      val = cmul(val, e < H ? w : make_float2(-w.x, -w.y));
+    }
+    v[i] = val;
+  }
+  fft_row<LN, -1, 2>(v, s, j, A.tw, A.twp);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 16; ++i) s[PADI(j + i * T)] = v[i];
+  __syncthreads();
+  const int a0 = blockIdx.x * R;
+  for (int idx = threadIdx.x; idx < R * N; idx += R * T) {
+    const int r = idx % R, m = idx / R;
+    if (a0 + r < N) A.tmp[(size_t)(2 * m + par) * N + a0 + r] = smem[r * SROW + PADI(m)];
+  }
+}
+
+// P2 (split): row k1 of T (the n centred inputs along axis 0); both halves, written interleaved
+// (one 16-byte store per output pair V[2m], V[2m + 1]).
+template <int LOGK, int R>
+__global__ void __launch_bounds__(R * (1 << LOGK) / 32) fft_p2s(const __grid_constant__ FftArgs A) {
+  constexpr int LN = LOGK - 1, N = 1 << LN, K = 2 * N, T = N / 16, SROW = N + N / 16 + 1, H = N / 2;
+  extern __shared__ float2 smem[];
+  const int rr = threadIdx.x / T, j = threadIdx.x % T;
+  const int k1 = blockIdx.x * R + rr;
+  float2* s = smem + rr * SROW;
+  const float2* row = A.tmp + (size_t)k1 * N;
+  float2 u[16], w[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int e = j + i * T;
+    u[i] = row[e < H ? e + H : e - H];
+    const float2 t = A.tw[e];
+    w[i] = cmul(u[i], e < H ? t : make_float2(-t.x, -t.y));
+  }
+  fft_row<LN, -1, 2>(u, s, j, A.tw, A.twp);
+  __syncthreads();
+  fft_row<LN, -1, 2>(w, s, j, A.tw, A.twp);
+  float4* g = reinterpret_cast<float4*>(A.grid + (size_t)k1 * K);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) g[j + i * T] = make_float4(u[i].x, u[i].y, w[i].x, w[i].y);
+}
+
+// exp(+2 pi i jo / K) X_o + X_e for the centred output offset jo of transform index q
+__device__ __forceinline__ float2 split_combine(float2 xe, float2 xo, int q, int N, const float2* __restrict__ tw) {
+  const int jo = q < N / 2 ? q : q - N;
+  const float2 t = tw[jo < 0 ? jo + 2 * N : jo];  // exp(-2 pi i jo / K)
+  return make_float2(xe.x + xo.x * t.x + xo.y * t.y, xe.y + xo.y * t.x - xo.x * t.y);
+}
+
+// Q1 (split): row k1 of the gridded data (even and odd samples: one 16-byte load per pair, plus the
+// compensation grid), inverse transforms, the n centred outputs written transposed into U[a][k1];
+// the grid (and compensation grid) row is re-zeroed.
+template <int LOGK, int R>
+__global__ void __launch_bounds__(R * (1 << LOGK) / 32) fft_q1s(const __grid_constant__ FftArgs A) {
+  constexpr int LN = LOGK - 1, N = 1 << LN, K = 2 * N, T = N / 16, SROW = N + N / 16 + 1, H = N / 2;
+  extern __shared__ float2 smem[];
+  const int rr = threadIdx.x / T, j = threadIdx.x % T;
+  const int k1 = blockIdx.x * R + rr;
+  if (blockIdx.x == 0 && threadIdx.x < 4 && A.acc) A.acc[threadIdx.x] = 0.0;
+  float2* s = smem + rr * SROW;
+  float4* g = reinterpret_cast<float4*>(A.grid + (size_t)k1 * K);
+  float2 ge[16], go[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const float4 q = g[j + i * T];
+    ge[i] = make_float2(q.x, q.y);
+    go[i] = make_float2(q.z, q.w);
+  }
+  if (A.grid_lo) {  // the compensated sums: high part + rounding errors
+    float4* gl = reinterpret_cast<float4*>(A.grid_lo + (size_t)k1 * K);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float4 q = gl[j + i * T];
+      ge[i] = cadd(ge[i], make_float2(q.x, q.y));
+      go[i] = cadd(go[i], make_float2(q.z, q.w));
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) gl[j + i * T] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) g[j + i * T] = make_float4(0.f, 0.f, 0.f, 0.f);
+  fft_row<LN, +1, 2>(ge, s, j, A.tw, A.twp);
+  __syncthreads();
+  fft_row<LN, +1, 2>(go, s, j, A.tw, A.twp);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const int q = j + i * T, a = q < H ? q + H : q - H;  // image row of centred offset jo
+    s[PADI(a)] = split_combine(ge[i], go[i], q, N, A.tw);
+  }
+  __syncthreads();
+  const int k10 = blockIdx.x * R;
+  for (int idx = threadIdx.x; idx < R * N; idx += R * T) {
+    const int r = idx % R, a = idx / R;
+    A.tmp[(size_t)a * K + k10 + r] = smem[r * SROW + PADI(a)];
+  }
+}
+
+// Q2 (split): rows a of U (even and odd samples), inverse transforms and the centred outputs, then
+// the epilogue of fft_q2 (two image rows per CTA).
+template <int LOGK, bool CH>
+__global__ void __launch_bounds__((1 << LOGK) / 32, (1 << LOGK) / 32 <= 256 ? 2 : 1) fft_q2s(
+    const __grid_constant__ FftArgs A) {
+  constexpr int LN = LOGK - 1, N = 1 << LN, K = 2 * N, T = N / 16, SROW = N + N / 16 + 1, H = N / 2;
+  extern __shared__ float2 smem[];
+  float* gs = reinterpret_cast<float*>(smem + SROW);  // 2 x n gradient values
+  const int j = threadIdx.x;
+  const int a0 = 2 * blockIdx.x;
+#pragma unroll 1
+  for (int q2 = 0; q2 < 2; ++q2) {
+    const int a = a0 + q2;
+    const float4* row = reinterpret_cast<const float4*>(A.tmp + (size_t)a * K);
+    float2 ge[16], go[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const float4 q = row[j + i * T];
+      ge[i] = make_float2(q.x, q.y);
+      go[i] = make_float2(q.z, q.w);
+    }
+    if (q2) __syncthreads();  // the previous row's transforms are done with the buffer
+    fft_row<LN, +1, 2>(ge, smem, j, A.tw, A.twp);
+    __syncthreads();
+    fft_row<LN, +1, 2>(go, smem, j, A.tw, A.twp);
+    const float ca = A.cinv[a];
+    const float2 cha = CH ? A.chirp[a] : make_float2(1.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int q = j + i * T, b = q < H ? q + H : q - H;
+      const float2 x = split_combine(ge[i], go[i], q, N, A.tw);
+      if (CH) {  // Re{conj(chirp) x}: the adjoint of the centre chirp of Z_s
+        const float2 c = cmul(cha, A.chirp[b]);
+        gs[q2 * N + b] = (x.x * c.x + x.y * c.y) * ca * A.cinv[b];
+      } else {
+        gs[q2 * N + b] = x.x * ca * A.cinv[b];
+      }
+    }
+  }
+  __syncthreads();
+  q2_epilogue<CH>(A, gs, a0, j, T);
+}
+
 // ---------------------------------------------------------------- launchers
 constexpr int SMEM_BUDGET = 140 * 1024;
 
@@ -462,8 +647,65 @@ constexpr int rows_per_cta() {
   return r;
 }
 
+// rows per CTA of the split passes: T = K / 32 threads per row, at most `max_threads` threads and
+// `max_rows` rows, the rows' buffers within the shared-memory budget
+template <int LOGK>
+constexpr int split_rows(int max_threads, int max_rows) {
+  constexpr int N = 1 << (LOGK - 1), T = N / 16;
+  int r = max_rows;
+  while (r > 1 && (r * T > max_threads || r * (N + N / 16 + 1) * 8 > SMEM_BUDGET)) r >>= 1;
+  return r;
+}
+
+// the split passes when K = 2n (every launch configuration of the general passes otherwise)
+template <int LOGK>
+int launch_forward_split(pnp_plan* p, const FftArgs& A) {
+  constexpr int N = 1 << (LOGK - 1), T = N / 16, SROW = N + N / 16 + 1;
+  constexpr int R1 = split_rows<LOGK>(1024, 16), R2 = split_rows<LOGK>(512, 16);
+  const int smem1 = R1 * SROW * 8, smem2 = R2 * SROW * 8;
+  static bool attr = false;
+  if (!attr) {
+    PNP_CUDA(cudaFuncSetAttribute(fft_p1s<LOGK, R1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
+    PNP_CUDA(cudaFuncSetAttribute(fft_p1s<LOGK, R1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
+    PNP_CUDA(cudaFuncSetAttribute(fft_p2s<LOGK, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+    attr = true;
+  }
+  const dim3 g1((N + R1 - 1) / R1, 2);
+  if (A.chirp)
+    fft_p1s<LOGK, R1, true><<<g1, R1 * T, smem1, p->stream>>>(A);
+  else
+    fft_p1s<LOGK, R1, false><<<g1, R1 * T, smem1, p->stream>>>(A);
+  PNP_CHECK_LAUNCH();
+  fft_p2s<LOGK, R2><<<2 * N / R2, R2 * T, smem2, p->stream>>>(A);
+  PNP_CHECK_LAUNCH();
+  return PNP_OK;
+}
+
+template <int LOGK>
+int launch_adjoint_split(pnp_plan* p, const FftArgs& A) {
+  constexpr int N = 1 << (LOGK - 1), T = N / 16, SROW = N + N / 16 + 1;
+  constexpr int R2 = split_rows<LOGK>(512, 16);
+  const int smem1 = R2 * SROW * 8, smem2 = SROW * 8 + 2 * N * 4;
+  static bool attr = false;
+  if (!attr) {
+    PNP_CUDA(cudaFuncSetAttribute(fft_q1s<LOGK, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
+    PNP_CUDA(cudaFuncSetAttribute(fft_q2s<LOGK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+    PNP_CUDA(cudaFuncSetAttribute(fft_q2s<LOGK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+    attr = true;
+  }
+  fft_q1s<LOGK, R2><<<2 * N / R2, R2 * T, smem1, p->stream>>>(A);
+  PNP_CHECK_LAUNCH();
+  if (A.chirp)
+    fft_q2s<LOGK, true><<<N / 2, T, smem2, p->stream>>>(A);
+  else
+    fft_q2s<LOGK, false><<<N / 2, T, smem2, p->stream>>>(A);
+  PNP_CHECK_LAUNCH();
+  return PNP_OK;
+}
+
 template <int LOGK>
 int launch_forward(pnp_plan* p, const FftArgs& A) {
+  if (2 * p->n == (1 << LOGK)) return launch_forward_split<LOGK>(p, A);
   constexpr int K = 1 << LOGK, T = K / 16, R = rows_per_cta<LOGK>(), SROW = K + K / 16 + 1;
   const int smem = R * SROW * 8;
   static bool attr = false;
@@ -485,6 +727,7 @@ int launch_forward(pnp_plan* p, const FftArgs& A) {
 
 template <int LOGK>
 int launch_adjoint(pnp_plan* p, const FftArgs& A) {
+  if (2 * p->n == (1 << LOGK)) return launch_adjoint_split<LOGK>(p, A);
   constexpr int K = 1 << LOGK, T = K / 16, R = rows_per_cta<LOGK>(), SROW = K + K / 16 + 1;
   const int smem1 = R * SROW * 8;
   const int smem2 = SROW * 8 + 2 * p->n * 4;

@@ -111,6 +111,21 @@ def test_every_fft_size_against_direct_nudft(K):
     assert rel_l2(xa, onu.nudft_adjoint(omega, r, n).real) <= TOL
 
 
+@pytest.mark.parametrize("K", [64, 128, 256, 512, 1024, 2048, 4096, 8192])
+def test_twofold_oversampled_sizes_against_oracle(K):
+    """n = K/2, the oversampling of every workload: the FFT passes split each length-K transform into
+    two length-n ones (no transform over zero padding); forward and adjoint against the FP64 oracle."""
+    n, M = K // 2, 3000
+    rng = np.random.default_rng(K + 1)
+    omega = rng.uniform(-np.pi, np.pi, (M, 2))
+    x = rng.random((n, n))
+    plan = pnp.Plan(n, K, omega)
+    ora = onu.Operator(n, K, omega)
+    assert rel_l2(to_host(plan.phi_forward(to_dev_f32(x))), ora.forward(x)) <= TOL
+    r = synth.complex_normal(M, rng)
+    assert rel_l2(to_host(plan.phi_adjoint(to_dev_c64(r))), ora.adjoint(r)) <= TOL
+
+
 def test_op_norm_parity():
     n, K, M = 64, 128, 20000
     pr = _problem(n, K, M, seed=4)
