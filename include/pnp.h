@@ -217,8 +217,10 @@ int pnp_plan_set_holographic(pnp_plan* plan, int enable);
  * unit's partial sums into the output grid is followed by the addition of its exact rounding
  * error (TwoSum, from the value the atomic returns) into a second grid, and the adjoint FFT
  * reads the sum of the two; in dense uv cells, where thousands of rows meet, this removes the
- * error of the FP32 sums over work units.  enable = 0 uses plain FP32 atomics.  The plan holds
- * the second grid (K^2 complex64) either way.  Synchronises the plan's stream. */
+ * error of the FP32 sums over work units.  The errors are ~2^-24 of the sums, so the second grid
+ * holds them as BF16 pairs (4 bytes per cell).  enable = 0 uses plain FP32 atomics (faster: no
+ * atomic waits for its result and the adjoint FFT reads one grid).  The plan holds the second
+ * grid either way.  Synchronises the plan's stream. */
 int pnp_plan_set_compensated(pnp_plan* plan, int enable);
 
 /* Set how many rows of a run of rows sharing a tap window one warp of the

@@ -375,12 +375,15 @@ __global__ void __launch_bounds__(256) fne_cotangent(const float* __restrict__ w
 }
 
 // Adam (Kingma & Ba 2015) on the master weights; the gradient is cleared for the next step.
+// omb1 = 1 - b1 and omb2 = 1 - b2 come from the host in double precision: formed in FP32 from
+// b2 = 0.999f, 1 - b2 would be off by 1.3e-5 relative, and the step m^/sqrt(v^) by half that.
 __global__ void adam_step(float* __restrict__ w, float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                          int64_t count, float lr, float b1, float b2, float eps, float c1, float c2) {
+                          int64_t count, float lr, float b1, float b2, float omb1, float omb2, float eps, float c1,
+                          float c2) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    const float mi = b1 * m[i] + omb1 * gi;
+    const float vi = b2 * v[i] + omb2 * gi * gi;
     m[i] = mi;
     v[i] = vi;
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
@@ -528,7 +531,8 @@ int adam_update(pnp_cnn_trainer* T) {
   T->t += 1;
   const float c1 = (float)(1.0 - std::pow(T->b1, T->t)), c2 = (float)(1.0 - std::pow(T->b2, T->t));
   adam_step<<<nblocks(NPARAM), 256, 0, T->stream>>>(T->w, T->g, T->m, T->v, NPARAM, (float)T->lr, (float)T->b1,
-                                                    (float)T->b2, (float)T->eps, c1, c2);
+                                                    (float)T->b2, (float)(1.0 - T->b1), (float)(1.0 - T->b2),
+                                                    (float)T->eps, c1, c2);
   PNP_CHECK_LAUNCH();
   return prep(T);
 }

@@ -205,7 +205,7 @@ struct FftArgs {
   const float2* twp;       // radix-16 pass twiddles (TWP_ENTRIES)
   float2* tmp;             // T (K x n) or U (n x K)
   float2* grid;            // P2 output / Q1 input (re-zeroed)
-  float2* grid_lo;         // Q1: compensation terms added to the input (re-zeroed), or NULL
+  __nv_bfloat162* grid_lo; // Q1: compensation terms added to the input (re-zeroed), or NULL
   float* out;              // Q2 output image
   double* acc;             // Q1 zeroes acc[0..3]; Q2 accumulates
   float gamma, t;
@@ -303,11 +303,11 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_q1(const __grid_cons
 #pragma unroll
   for (int i = 0; i < 16; ++i) v[i] = g[j + i * T];
   if (A.grid_lo) {  // the compensated sums: high part + rounding errors
-    float2* gl = A.grid_lo + (size_t)k1 * K;
+    __nv_bfloat162* gl = A.grid_lo + (size_t)k1 * K;
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = cadd(v[i], gl[j + i * T]);
+    for (int i = 0; i < 16; ++i) v[i] = cadd(v[i], __bfloat1622float2(gl[j + i * T]));
 #pragma unroll
-    for (int i = 0; i < 16; ++i) gl[j + i * T] = make_float2(0.f, 0.f);
+    for (int i = 0; i < 16; ++i) gl[j + i * T] = __floats2bfloat162_rn(0.f, 0.f);
   }
 #pragma unroll
   for (int i = 0; i < 16; ++i) g[j + i * T] = make_float2(0.f, 0.f);
@@ -563,16 +563,16 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 32) fft_q1s(const __grid_con
     ge[i] = make_float2(q.x, q.y);
     go[i] = make_float2(q.z, q.w);
   }
-  if (A.grid_lo) {  // the compensated sums: high part + rounding errors
-    float4* gl = reinterpret_cast<float4*>(A.grid_lo + (size_t)k1 * K);
+  if (A.grid_lo) {  // the compensated sums: high part + rounding errors (BF16 pairs, 8 bytes per 2 cells)
+    uint2* gl = reinterpret_cast<uint2*>(A.grid_lo + (size_t)k1 * K);
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      const float4 q = gl[j + i * T];
-      ge[i] = cadd(ge[i], make_float2(q.x, q.y));
-      go[i] = cadd(go[i], make_float2(q.z, q.w));
+      const uint2 q = gl[j + i * T];
+      ge[i] = cadd(ge[i], __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x)));
+      go[i] = cadd(go[i], __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y)));
     }
 #pragma unroll
-    for (int i = 0; i < 16; ++i) gl[j + i * T] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < 16; ++i) gl[j + i * T] = make_uint2(0u, 0u);
   }
 #pragma unroll
   for (int i = 0; i < 16; ++i) g[j + i * T] = make_float4(0.f, 0.f, 0.f, 0.f);

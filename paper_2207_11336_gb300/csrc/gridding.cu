@@ -41,7 +41,7 @@ struct GArgs {
   float2* y_out;        // caller order (G_DEGRID)
   const float2* gridA;  // input grid (G_DEGRID, G_FUSED)
   float2* gridB;        // output grid (G_GRID, G_FUSED)
-  float2* gridB_lo;     // compensation grid: the rounding error of every flush into gridB, or NULL
+  __nv_bfloat162* gridB_lo;  // compensation grid: the rounding errors of the flushes into gridB, or NULL
   int* status;          // bit 1: pipeline wait timed out; bit 2: inconsistent work list (chunk skipped)
 };
 
@@ -439,21 +439,43 @@ __global__ void __launch_bounds__(GPASS_THREADS, 1) gpass(GArgs A) {
     }
     consumers_sync();  // all scatters of this unit are in sy
     if (MODE != G_DEGRID && !s_abort) {
-      for (int c = ctid; c < SS; c += CT) {
-        const int i = c / S, jj = c - i * S;
-        const float2 v = make_float2(sy_re[i * P + jj], sy_im[i * P + jj]);
-        if (v.x != 0.f || v.y != 0.f) {
-          const size_t g = ((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km);
-          if (A.gridB_lo) {
-            // compensated summation: the atomic returns the value it added to, so the exact rounding
-            // error of its (round-to-nearest) sum goes to the compensation grid
-            const float2 old = atomicAdd(&A.gridB[g], v);
-            const float ex = two_sum_err(old.x, v.x, __fadd_rn(old.x, v.x));
-            const float ey = two_sum_err(old.y, v.y, __fadd_rn(old.y, v.y));
-            if (ex != 0.f || ey != 0.f) atomicAdd(&A.gridB_lo[g], make_float2(ex, ey));
-          } else {
-            atomicAdd(&A.gridB[g], v);
+      if (A.gridB_lo) {
+        // compensated summation: each atomic returns the value it added to, so the exact rounding
+        // error of its (round-to-nearest) sum goes to the compensation grid.  A thread issues the
+        // atomics of FB cells before it waits for their results.
+        constexpr int FB = 4;
+        for (int c0f = ctid; c0f < SS; c0f += FB * CT) {
+          float2 v[FB], old[FB];
+          size_t g[FB];
+#pragma unroll
+          for (int f = 0; f < FB; ++f) {
+            const int c = c0f + f * CT;
+            v[f] = make_float2(0.f, 0.f);
+            g[f] = 0;
+            if (c < SS) {
+              const int i = c / S, jj = c - i * S;
+              v[f] = make_float2(sy_re[i * P + jj], sy_im[i * P + jj]);
+              g[f] = ((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km);
+            }
           }
+#pragma unroll
+          for (int f = 0; f < FB; ++f)
+            if (v[f].x != 0.f || v[f].y != 0.f) old[f] = atomicAdd(&A.gridB[g[f]], v[f]);
+#pragma unroll
+          for (int f = 0; f < FB; ++f) {
+            if (v[f].x != 0.f || v[f].y != 0.f) {
+              const float ex = two_sum_err(old[f].x, v[f].x, __fadd_rn(old[f].x, v[f].x));
+              const float ey = two_sum_err(old[f].y, v[f].y, __fadd_rn(old[f].y, v[f].y));
+              if (ex != 0.f || ey != 0.f) atomicAdd(&A.gridB_lo[g[f]], __floats2bfloat162_rn(ex, ey));
+            }
+          }
+        }
+      } else {
+        for (int c = ctid; c < SS; c += CT) {
+          const int i = c / S, jj = c - i * S;
+          const float2 v = make_float2(sy_re[i * P + jj], sy_im[i * P + jj]);
+          if (v.x != 0.f || v.y != 0.f)
+            atomicAdd(&A.gridB[((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km)], v);
         }
       }
     }

@@ -161,14 +161,15 @@ int holo_build_plan(pnp_plan* p) {
 
 namespace {
 // out = hi + lo (lo may be NULL); hi and lo are left zero
-__global__ void take_grid(float2* __restrict__ hi, float2* __restrict__ lo, float2* __restrict__ out, int64_t count) {
+__global__ void take_grid(float2* __restrict__ hi, __nv_bfloat162* __restrict__ lo, float2* __restrict__ out,
+                          int64_t count) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
     float2 v = hi[i];
     hi[i] = make_float2(0.f, 0.f);
     if (lo) {
-      const float2 e = lo[i];
+      const float2 e = __bfloat1622float2(lo[i]);
       v = make_float2(v.x + e.x, v.y + e.y);
-      lo[i] = make_float2(0.f, 0.f);
+      lo[i] = __floats2bfloat162_rn(0.f, 0.f);
     }
     out[i] = v;
   }

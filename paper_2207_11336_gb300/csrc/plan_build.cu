@@ -490,7 +490,7 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     PNP_CUDA(cudaMemcpy(p->d_twp, twp.data(), TWP_ENTRIES * sizeof(float2), cudaMemcpyHostToDevice));
   }
   PNP_CUDA(cudaMemset(p->d_gridB, 0, KK * sizeof(float2)));
-  PNP_CUDA(cudaMemset(p->d_gridB_lo, 0, KK * sizeof(float2)));
+  PNP_CUDA(cudaMemset(p->d_gridB_lo, 0, KK * sizeof(__nv_bfloat162)));
   PNP_CUDA(cudaMemset(p->d_acc, 0, 8 * sizeof(double)));
   PNP_CUDA(cudaMemset(p->d_status, 0, 4 * sizeof(int)));
   {

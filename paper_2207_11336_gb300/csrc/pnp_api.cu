@@ -448,7 +448,7 @@ int pnp_plan_autotune(pnp_plan* p, int reps, int* run_max_out, int64_t* unit_nnz
     cudaEventDestroy(e1);
     // the timed passes accumulated into the output grid: start it from zero again
     if (!rc && (cudaMemsetAsync(p->d_gridB, 0, (size_t)p->K * p->K * sizeof(float2), p->stream) != cudaSuccess ||
-                cudaMemsetAsync(p->d_gridB_lo, 0, (size_t)p->K * p->K * sizeof(float2), p->stream) != cudaSuccess)) {
+                cudaMemsetAsync(p->d_gridB_lo, 0, (size_t)p->K * p->K * sizeof(__nv_bfloat162), p->stream) != cudaSuccess)) {
       cudaGetLastError();
       rc = fail(PNP_ERR_CUDA, "autotune: clearing the grid failed");
     }
