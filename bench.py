@@ -69,12 +69,12 @@ def parse():
                     help="FB iterations per weighted-l1 surrogate of uSARA (log-sum reweighting)")
     ap.add_argument("--converge-iters", type=int, default=2000,
                     help="iterations of the plain loop whose final SNR (minus 0.5 dB) is the time-to-SNR target")
-    ap.add_argument("--no-fne", dest="fne", action="store_false",
-                    help="skip the learned loop with the penalised network")
+    ap.add_argument("--no-l1", dest="l1", action="store_false",
+                    help="skip the learned loop with the network trained without the penalty")
     ap.add_argument("--weights", default=None, help="network of the learned loop (default: the committed one)")
     ap.add_argument("--band-mhz", type=float, default=1053.0,
                     help="frequency band of the 8192^2 workload (C4): 1053 or 1399")
-    ap.add_argument("--weights-fne", default=None, help="penalised network of the learned_fne line")
+    ap.add_argument("--weights-l1", default=None, help="network of the learned_l1 comparison line")
     ap.add_argument("--kernel-case", choices=["gridding", "cnn", "fft"], default=None,
                     help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
     ap.add_argument("--cnn-side", type=int, default=4096,
@@ -308,9 +308,11 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
-WEIGHTS = os.path.join(ROOT, "paper_2207_11336_gb300", "weights", "dncnn_C3.npz")
-# the same network fine-tuned with the soft firm non-expansiveness penalty of Eq. training_loss
-WEIGHTS_FNE = os.path.join(ROOT, "paper_2207_11336_gb300", "weights", "dncnn_C3_fne.npz")
+# the learned loop's network: trained on the l1 loss, then fine-tuned with the soft firm
+# non-expansiveness penalty of Eq. training_loss (the convergence safeguard of App. C)
+WEIGHTS = os.path.join(ROOT, "paper_2207_11336_gb300", "weights", "dncnn_C3_fne.npz")
+# the same network before the penalised fine-tuning (l1 loss only), a comparison line
+WEIGHTS_L1 = os.path.join(ROOT, "paper_2207_11336_gb300", "weights", "dncnn_C3.npz")
 SNR_CHUNK = 10           # loops are run in chunks of this many iterations between SNR readings
 TARGET_MARGIN_DB = 0.5   # time-to-SNR target: the plain loop's converged SNR minus this margin
 
@@ -366,9 +368,9 @@ def _thin(trace, every):
 
 
 def run_gpu(args):
-    global WEIGHTS, WEIGHTS_FNE
+    global WEIGHTS, WEIGHTS_L1
     WEIGHTS = args.weights or WEIGHTS
-    WEIGHTS_FNE = args.weights_fne or WEIGHTS_FNE
+    WEIGHTS_L1 = args.weights_l1 or WEIGHTS_L1
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -564,22 +566,23 @@ def run_gpu(args):
     if learned:
         it_l, trace_l, xl = _run_to_snr(plan, cnn, y, gamma, L, x_true, alpha, target, args.converge_iters)
         comparison["learned"] = {
+            "weights": "l1 loss, then fine-tuned with the firm non-expansiveness penalty (lambda %g, %d steps)" % (
+                float(wmeta.get("fne_lambda", 0.0)), int(wmeta.get("steps", 0))),
             "iter_per_s": value, "ms_per_iter": ms / steps, "alpha": alpha, "alpha_dirty_peak": hp["alpha"],
             "alpha_matched_to_sigma": alpha_match, "sigma_trained": float(wmeta["sigma"]),
             "sigma_heuristic_at_dirty_peak": hp["sigma"], "iters_to_target": it_l,
             "time_to_target_s": None if it_l is None else it_l * ms / steps / 1e3,
             "snr_db_final": trace_l[-1][1], "iters_run": trace_l[-1][0],
             "snr_trace": _thin(trace_l, 100)}
-        if os.path.exists(WEIGHTS_FNE) and args.fne:
-            # the learned loop with the penalised network (same architecture and cost per iteration)
-            params_f, meta_f = load_weights(WEIGHTS_FNE)
+        if os.path.exists(WEIGHTS_L1) and args.l1:
+            # the learned loop with the network trained without the penalty (same cost per iteration)
+            params_f, meta_f = load_weights(WEIGHTS_L1)
             cnn_f = pnp.CnnDenoiser(params_f, n, facet_rows=prob["facet_rows"], facet_cols=prob["facet_cols"],
                                     halo=prob["halo"], stream=stream)
             alpha_f = max(hp["alpha"], heuristics.alpha_for_denoiser(tau_w, L, float(meta_f["sigma"])))
             it_f, trace_f, _ = _run_to_snr(plan, cnn_f, y, gamma, L, x_true, alpha_f, target, args.converge_iters)
-            comparison["learned_fne"] = {
-                "weights": "dncnn_C3 fine-tuned %d steps with the penalty, lambda %g" % (
-                    int(meta_f.get("steps", 0)), float(meta_f.get("fne_lambda", 0.0))), "alpha": alpha_f,
+            comparison["learned_l1"] = {
+                "weights": "l1 loss only, %d steps" % int(meta_f.get("steps", 0)), "alpha": alpha_f,
                 "iters_to_target": it_f, "time_to_target_s": None if it_f is None else it_f * ms / steps / 1e3,
                 "snr_db_final": trace_f[-1][1], "iters_run": trace_f[-1][0],
                 "snr_trace": _thin(trace_f, 100)}
