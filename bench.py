@@ -594,6 +594,12 @@ def run_gpu(args):
     xk = torch.zeros((n, n), dtype=torch.float32, device="cuda")
     plan.fb_run(haar, y, x0=xk, gamma=gamma, L=L, max_iter=kt, check_every=kt, use_graph=False, inplace=True)
     tim = plan.read_timing()
+    # the same stages with the gridding flush's compensated summation switched off (the fast option)
+    comp = bool(info["compensated"])
+    plan.set_compensated(not comp)
+    plan.fb_run(haar, y, x0=xk, gamma=gamma, L=L, max_iter=kt, check_every=kt, use_graph=False, inplace=True)
+    tim_other = plan.read_timing()
+    plan.set_compensated(comp)
     plan.set_timing(False)
     g_ms, g_cnt = tim["gridding"]
     g_ms_launch = g_ms / max(g_cnt, 1)
@@ -665,7 +671,10 @@ def run_gpu(args):
                             "alg_bytes_per_launch": alg_bytes, "ms_per_launch": g_ms_launch,
                             "moved_bytes_per_launch": moved_bytes,
                             "frac_of_moved_bytes": moved_bytes / (g_ms_launch * 1e-3) / 1e9 / hbm,
-                            "stage_ms_per_iter": {k: v[0] / max(v[1], 1) for k, v in tim.items()}},
+                            "stage_ms_per_iter": {k: v[0] / max(v[1], 1) for k, v in tim.items()},
+                            "compensated_gridding": comp,
+                            ("stage_ms_per_iter_uncompensated" if comp else "stage_ms_per_iter_compensated"):
+                                {k: v[0] / max(v[1], 1) for k, v in tim_other.items()}},
                "roofline_denoiser": roof_cnn,
                "comparison": comparison,
                "fb": {k: (float(v) if isinstance(v, (int, float, np.floating)) else v) for k, v in hp.items()}}

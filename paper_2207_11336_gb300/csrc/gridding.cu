@@ -296,11 +296,49 @@ __device__ __forceinline__ void process_chunk(const GArgs& A, const Chunk& ch, c
 }
 
 
+// Compensated flush of a unit's shared-memory partial sums into the output grid: each atomic returns
+// the value it added to, so the thread forms the exact rounding error of the (round-to-nearest) sum
+// (TwoSum) and adds it to the compensation grid.  A thread issues the atomics of two cells before it
+// waits for their results.  Kept out of line so that the registers it needs do not count against the
+// main loop of the gridding pass.
+__device__ __noinline__ void flush_compensated(const float* sy_re, const float* sy_im, float2* gridB,
+                                               __nv_bfloat162* gridB_lo, int S, int P, int r0, int c0,
+                                               int logK, int Km, int ctid) {
+  constexpr int FB = 2, CT = GPASS_CONSUMERS * 32;
+  const int SS = S * S;
+  for (int c0f = ctid; c0f < SS; c0f += FB * CT) {
+    float2 v[FB], old[FB];
+    size_t g[FB];
+#pragma unroll
+    for (int f = 0; f < FB; ++f) {
+      const int c = c0f + f * CT;
+      v[f] = make_float2(0.f, 0.f);
+      g[f] = 0;
+      if (c < SS) {
+        const int i = c / S, jj = c - i * S;
+        v[f] = make_float2(sy_re[i * P + jj], sy_im[i * P + jj]);
+        g[f] = ((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km);
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < FB; ++f)
+      if (v[f].x != 0.f || v[f].y != 0.f) old[f] = atomicAdd(&gridB[g[f]], v[f]);
+#pragma unroll
+    for (int f = 0; f < FB; ++f) {
+      if (v[f].x != 0.f || v[f].y != 0.f) {
+        const float ex = two_sum_err(old[f].x, v[f].x, __fadd_rn(old[f].x, v[f].x));
+        const float ey = two_sum_err(old[f].y, v[f].y, __fadd_rn(old[f].y, v[f].y));
+        if (ex != 0.f || ey != 0.f) atomicAdd(&gridB_lo[g[f]], __floats2bfloat162_rn(ex, ey));
+      }
+    }
+  }
+}
+
 // Warp-specialised CTA: warps 0..GPASS_CONSUMERS-1 consume chunks, the last
 // warp produces them.  full[s] completes when stage s has landed (TMA
 // transaction count); empty[s] completes when every consumer warp has released
 // stage s.  Consumer warps only meet at unit boundaries (tile restage/flush).
-template <int MODE, typename WT, int RB>
+template <int MODE, typename WT, int RB, bool COMP>
 __global__ void __launch_bounds__(GPASS_THREADS, 1) gpass(GArgs A) {
   using L = StageLayout<WT>;
   extern __shared__ __align__(128) unsigned char sm[];
@@ -439,43 +477,15 @@ __global__ void __launch_bounds__(GPASS_THREADS, 1) gpass(GArgs A) {
     }
     consumers_sync();  // all scatters of this unit are in sy
     if (MODE != G_DEGRID && !s_abort) {
-      if (A.gridB_lo) {
-        // compensated summation: each atomic returns the value it added to, so the exact rounding
-        // error of its (round-to-nearest) sum goes to the compensation grid.  A thread issues the
-        // atomics of FB cells before it waits for their results.
-        constexpr int FB = 4;
-        for (int c0f = ctid; c0f < SS; c0f += FB * CT) {
-          float2 v[FB], old[FB];
-          size_t g[FB];
-#pragma unroll
-          for (int f = 0; f < FB; ++f) {
-            const int c = c0f + f * CT;
-            v[f] = make_float2(0.f, 0.f);
-            g[f] = 0;
-            if (c < SS) {
-              const int i = c / S, jj = c - i * S;
-              v[f] = make_float2(sy_re[i * P + jj], sy_im[i * P + jj]);
-              g[f] = ((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km);
-            }
-          }
-#pragma unroll
-          for (int f = 0; f < FB; ++f)
-            if (v[f].x != 0.f || v[f].y != 0.f) old[f] = atomicAdd(&A.gridB[g[f]], v[f]);
-#pragma unroll
-          for (int f = 0; f < FB; ++f) {
-            if (v[f].x != 0.f || v[f].y != 0.f) {
-              const float ex = two_sum_err(old[f].x, v[f].x, __fadd_rn(old[f].x, v[f].x));
-              const float ey = two_sum_err(old[f].y, v[f].y, __fadd_rn(old[f].y, v[f].y));
-              if (ex != 0.f || ey != 0.f) atomicAdd(&A.gridB_lo[g[f]], __floats2bfloat162_rn(ex, ey));
-            }
-          }
-        }
+      if (COMP) {
+        flush_compensated(sy_re, sy_im, A.gridB, A.gridB_lo, S, P, r0, c0, logK, Km, ctid);
       } else {
         for (int c = ctid; c < SS; c += CT) {
           const int i = c / S, jj = c - i * S;
           const float2 v = make_float2(sy_re[i * P + jj], sy_im[i * P + jj]);
-          if (v.x != 0.f || v.y != 0.f)
+          if (v.x != 0.f || v.y != 0.f) {
             atomicAdd(&A.gridB[((size_t)((r0 + i) & Km) << logK) + ((c0 + jj) & Km)], v);
+          }
         }
       }
     }
@@ -493,30 +503,38 @@ __global__ void permute_kernel(const float2* __restrict__ y, const int32_t* __re
   }
 }
 
-template <int MODE, typename WT, int RB>
+template <int MODE, typename WT, int RB, bool COMP>
 int launch_gpass(pnp_plan* p, const GArgs& A) {
   const int region_bytes = (((A.S * A.P + 32) * 8 + 127) & ~127);
   const int smem = (MODE == G_FUSED ? 2 : 1) * region_bytes + NSTAGE * StageLayout<WT>::SIZE;
   static int attr = 0;
   static int per_sm = 0;
   if (smem > attr) {
-    PNP_CUDA(cudaFuncSetAttribute(gpass<MODE, WT, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PNP_CUDA(cudaFuncSetAttribute(gpass<MODE, WT, RB, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr = smem;
-    PNP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gpass<MODE, WT, RB>, GPASS_THREADS, smem));
+    PNP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gpass<MODE, WT, RB, COMP>, GPASS_THREADS, smem));
   }
   if (per_sm < 1) return fail(PNP_ERR_UNSUPPORTED, "gridding tile does not fit in shared memory");
   long long grid = (long long)per_sm * p->num_sms;
   if (grid > A.n_units - A.u_begin) grid = A.n_units - A.u_begin;
   if (grid < 1) return PNP_OK;
-  gpass<MODE, WT, RB><<<(unsigned)grid, GPASS_THREADS, smem, p->stream>>>(A);
+  gpass<MODE, WT, RB, COMP><<<(unsigned)grid, GPASS_THREADS, smem, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
 
 template <int MODE, int RB>
 int dispatch_wt(pnp_plan* p, const GArgs& A) {
-  return p->wdtype == PNP_W_BF16C ? launch_gpass<MODE, __nv_bfloat162, RB>(p, A)
-                                  : launch_gpass<MODE, float2, RB>(p, A);
+  if constexpr (MODE == G_DEGRID) {  // no gridding, nothing to compensate
+    return p->wdtype == PNP_W_BF16C ? launch_gpass<MODE, __nv_bfloat162, RB, false>(p, A)
+                                    : launch_gpass<MODE, float2, RB, false>(p, A);
+  } else if (A.gridB_lo) {
+    return p->wdtype == PNP_W_BF16C ? launch_gpass<MODE, __nv_bfloat162, RB, true>(p, A)
+                                    : launch_gpass<MODE, float2, RB, true>(p, A);
+  } else {
+    return p->wdtype == PNP_W_BF16C ? launch_gpass<MODE, __nv_bfloat162, RB, false>(p, A)
+                                    : launch_gpass<MODE, float2, RB, false>(p, A);
+  }
 }
 
 // rows whose residuals one warp forms together (G_GRID takes its residuals as input)
