@@ -525,6 +525,16 @@ struct FirstArgs {
 // 32 pixels' 16-byte channel-block vectors, one contiguous 512-byte run of the block's plane.
 constexpr int FIRST_PX = 32;
 
+// d = a * b + c on two FP32 lanes at once (packed FMA, one instruction for a channel pair)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)),
+        "l"(*reinterpret_cast<unsigned long long*>(&c)));
+  return *reinterpret_cast<float2*>(&d);
+}
+
 __global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
   __shared__ float zt[FIRST_ROWS + 2][FIRST_PX + 2];
   const int f = blockIdx.z, ya = blockIdx.y * FIRST_ROWS, x0 = blockIdx.x * FIRST_PX;
@@ -537,12 +547,12 @@ __global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
     zt[r][c] = (yy >= 0 && yy < fc.z && xx >= 0 && xx < fc.w) ? zf[(size_t)(fc.x + yy) * A.n + fc.y + xx] : 0.f;
   }
   const int cb = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float w[8][9], b[8];
+  float2 w[4][9], b[4];  // channel pairs (2 q, 2 q + 1) of the block
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    b[c] = A.b1[cb * 8 + c];
+  for (int q = 0; q < 4; ++q) {
+    b[q] = make_float2(A.b1[cb * 8 + 2 * q], A.b1[cb * 8 + 2 * q + 1]);
 #pragma unroll
-    for (int t = 0; t < 9; ++t) w[c][t] = A.w1[(cb * 8 + c) * 9 + t];
+    for (int t = 0; t < 9; ++t) w[q][t] = make_float2(A.w1[(cb * 8 + 2 * q) * 9 + t], A.w1[(cb * 8 + 2 * q + 1) * 9 + t]);
   }
   __syncthreads();
   const int x = x0 + lane;
@@ -556,15 +566,12 @@ __global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
     for (int t = 0; t < 9; ++t) zin[t] = zt[r + t / 3][lane + t % 3];
     uint32_t pk[4];
 #pragma unroll
-    for (int c = 0; c < 8; c += 2) {
-      float a0 = b[c], a1 = b[c + 1];
+    for (int q = 0; q < 4; ++q) {
+      float2 a = b[q];
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        a0 = fmaf(w[c][t], zin[t], a0);
-        a1 = fmaf(w[c + 1][t], zin[t], a1);
-      }
-      __nv_bfloat162 h = __floats2bfloat162_rn(live ? fmaxf(a0, 0.f) : 0.f, live ? fmaxf(a1, 0.f) : 0.f);
-      pk[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+      for (int t = 0; t < 9; ++t) a = ffma2(w[q][t], make_float2(zin[t], zin[t]), a);
+      __nv_bfloat162 h = __floats2bfloat162_rn(live ? fmaxf(a.x, 0.f) : 0.f, live ? fmaxf(a.y, 0.f) : 0.f);
+      pk[q] = *reinterpret_cast<uint32_t*>(&h);
     }
     *reinterpret_cast<uint4*>(A.out + canvas_index(f, y, x, cb * 8, A.Hc, A.Wc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   }
@@ -629,26 +636,40 @@ __global__ void __launch_bounds__(LAST_THREADS) cnn_last(LastArgs A) {
     const int f = S.x, x0 = S.y, ya = S.z >> 16, R = S.z & 0xFFFF, Hf = S.w >> 16, Wf = S.w & 0xFFFF;
     const int4 fc = A.facets[f], core = A.cores[f];
     for (int r = ya - 1; r <= ya + R; ++r) {
-      // ---- project activation row r onto the taps: warp w takes M tiles w, w + 4, w + 8
+      // ---- project activation row r onto the taps: warp w takes M tiles w, w + 4, w + 8.  All of a
+      // warp's A fragments of the row are loaded before its first MMA, so their loads are in flight
+      // together.
       float* P = sP[(r - ya + 1) % 3];
       const bool row_ok = r >= 0 && r < Hf;
       const size_t rbase = ((size_t)f * A.Hc + (row_ok ? r : 0)) * 8 * plane;
-      for (int mt = warp; mt < LAST_PX / 16; mt += LAST_THREADS / 32) {
+      constexpr int TPW = (LAST_PX / 16 + LAST_THREADS / 32 - 1) / (LAST_THREADS / 32);  // tiles per warp
+      uint32_t a[TPW][4][4];
+#pragma unroll
+      for (int ti = 0; ti < TPW; ++ti) {
+        const int mt = warp + ti * (LAST_THREADS / 32);
         const int p_lo = x0 - 1 + mt * 16 + g, p_hi = p_lo + 8;  // pixels of fragment rows g and g + 8
-        const bool ok_lo = row_ok && p_lo >= 0 && p_lo < Wf, ok_hi = row_ok && p_hi >= 0 && p_hi < Wf;
-        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+        const bool tile = mt < LAST_PX / 16;
+        const bool ok_lo = tile && row_ok && p_lo >= 0 && p_lo < Wf, ok_hi = tile && row_ok && p_hi >= 0 && p_hi < Wf;
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
           // channels 16 ks + 2 t4 (+1) sit in channel block 2 ks, 16 ks + 8 + 2 t4 (+1) in block 2 ks + 1
           const uint32_t* b0 = reinterpret_cast<const uint32_t*>(A.canvas + rbase + (size_t)(2 * ks) * plane);
           const uint32_t* b1 = reinterpret_cast<const uint32_t*>(A.canvas + rbase + (size_t)(2 * ks + 1) * plane);
-          uint32_t a[4];
-          a[0] = ok_lo ? __ldg(b0 + (size_t)p_lo * 4 + t4) : 0u;
-          a[1] = ok_hi ? __ldg(b0 + (size_t)p_hi * 4 + t4) : 0u;
-          a[2] = ok_lo ? __ldg(b1 + (size_t)p_lo * 4 + t4) : 0u;
-          a[3] = ok_hi ? __ldg(b1 + (size_t)p_hi * 4 + t4) : 0u;
-          mma_bf16_16816(d0, a, bw[ks][0][0], bw[ks][0][1]);
-          mma_bf16_16816(d1, a, bw[ks][1][0], bw[ks][1][1]);
+          a[ti][ks][0] = ok_lo ? __ldg(b0 + (size_t)p_lo * 4 + t4) : 0u;
+          a[ti][ks][1] = ok_hi ? __ldg(b0 + (size_t)p_hi * 4 + t4) : 0u;
+          a[ti][ks][2] = ok_lo ? __ldg(b1 + (size_t)p_lo * 4 + t4) : 0u;
+          a[ti][ks][3] = ok_hi ? __ldg(b1 + (size_t)p_hi * 4 + t4) : 0u;
+        }
+      }
+#pragma unroll
+      for (int ti = 0; ti < TPW; ++ti) {
+        const int mt = warp + ti * (LAST_THREADS / 32);
+        if (mt >= LAST_PX / 16) break;  // warp-uniform
+        float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          mma_bf16_16816(d0, a[ti][ks], bw[ks][0][0], bw[ks][0][1]);
+          mma_bf16_16816(d1, a[ti][ks], bw[ks][1][0], bw[ks][1][1]);
         }
         // D fragment: (row g, cols 2 t4, 2 t4 + 1) and (row g + 8, same cols); taps 0..7 in tile 0, 8 in tile 1
         const int pl = mt * 16 + g, ph = pl + 8;

@@ -132,7 +132,7 @@ struct pnp_plan {
   float2* d_gridB = nullptr;   // K*K: G^H r   (layout [k1][k0]); kept zero between uses
   __nv_bfloat162* d_gridB_lo = nullptr; // K*K: compensation terms of d_gridB's atomic sums (BF16 pairs:
                                          // they are ~2^-24 of the sums); kept zero between uses
-  bool compensated = true;     // gridding flushes add their rounding errors to d_gridB_lo (TwoSum)
+  bool compensated = false;    // gridding flushes add their rounding errors to d_gridB_lo (TwoSum)
   float2* d_tmp = nullptr;     // K*n: half-transformed intermediate
   void* d_w = nullptr;         // nnz weights (float2 or bf16x2)
   uint16_t* d_cells = nullptr; // nnz cell indices lr * pitch + lc in the row's staged tile region

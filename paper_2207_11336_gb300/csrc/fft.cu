@@ -511,30 +511,50 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 32) fft_p1s(const __grid_con
   }
 }
 
+// The two length-n transforms of a row run side by side: the CTA's first n/16 threads transform the
+// even half in shared-memory buffer A, the next n/16 the odd half in buffer B (both groups pass the
+// same barriers), so a thread holds one transform's 16 values (64 registers) and two CTAs share an
+// SM, one CTA's loads overlapping the other's transforms.
+template <int LN>
+struct SplitGeom {
+  static constexpr int N = 1 << LN, T = N / 16, SROW = N + N / 16 + 1, H = N / 2;
+};
+
 // P2 (split): row k1 of T (the n centred inputs along axis 0); both halves, written interleaved
 // (one 16-byte store per output pair V[2m], V[2m + 1]).
-template <int LOGK, int R>
-__global__ void __launch_bounds__(R * (1 << LOGK) / 32) fft_p2s(const __grid_constant__ FftArgs A) {
-  constexpr int LN = LOGK - 1, N = 1 << LN, K = 2 * N, T = N / 16, SROW = N + N / 16 + 1, H = N / 2;
+template <int LOGK>
+__global__ void __launch_bounds__((1 << LOGK) / 16, (1 << LOGK) / 16 <= 512 ? 2 : 1) fft_p2s(
+    const __grid_constant__ FftArgs A) {
+  using Sg = SplitGeom<LOGK - 1>;
+  constexpr int N = Sg::N, K = 2 * N, T = Sg::T, H = Sg::H;
   extern __shared__ float2 smem[];
-  const int rr = threadIdx.x / T, j = threadIdx.x % T;
-  const int k1 = blockIdx.x * R + rr;
-  float2* s = smem + rr * SROW;
+  const int grp = threadIdx.x / T, j = threadIdx.x % T, k1 = blockIdx.x;
+  float2* buf = smem + grp * Sg::SROW;
   const float2* row = A.tmp + (size_t)k1 * N;
-  float2 u[16], w[16];
+  float2 v[16];
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
     const int e = j + i * T;
-    u[i] = row[e < H ? e + H : e - H];
-    const float2 t = A.tw[e];
-    w[i] = cmul(u[i], e < H ? t : make_float2(-t.x, -t.y));
+    const float2 u = row[e < H ? e + H : e - H];
+    if (grp) {
+      const float2 t = A.tw[e];
+      v[i] = cmul(u, e < H ? t : make_float2(-t.x, -t.y));
+    } else {
+      v[i] = u;
+    }
   }
-  fft_row<LN, -1, 2>(u, s, j, A.tw, A.twp);
+  fft_row<LOGK - 1, -1, 2>(v, buf, j, A.tw, A.twp);
   __syncthreads();
-  fft_row<LN, -1, 2>(w, s, j, A.tw, A.twp);
-  float4* g = reinterpret_cast<float4*>(A.grid + (size_t)k1 * K);
 #pragma unroll
-  for (int i = 0; i < 16; ++i) g[j + i * T] = make_float4(u[i].x, u[i].y, w[i].x, w[i].y);
+  for (int i = 0; i < 16; ++i) buf[PADI(j + i * T)] = v[i];
+  __syncthreads();
+  float4* g = reinterpret_cast<float4*>(A.grid + (size_t)k1 * K);
+  const float2* be = smem;
+  const float2* bo = smem + Sg::SROW;
+  for (int m = threadIdx.x; m < N; m += 2 * T) {
+    const float2 e = be[PADI(m)], o = bo[PADI(m)];
+    g[m] = make_float4(e.x, e.y, o.x, o.y);
+  }
 }
 
 // exp(+2 pi i jo / K) X_o + X_e for the centred output offset jo of transform index q
@@ -544,86 +564,88 @@ __device__ __forceinline__ float2 split_combine(float2 xe, float2 xo, int q, int
   return make_float2(xe.x + xo.x * t.x + xo.y * t.y, xe.y + xo.y * t.x - xo.x * t.y);
 }
 
-// Q1 (split): row k1 of the gridded data (even and odd samples: one 16-byte load per pair, plus the
-// compensation grid), inverse transforms, the n centred outputs written transposed into U[a][k1];
-// the grid (and compensation grid) row is re-zeroed.
-template <int LOGK, int R>
-__global__ void __launch_bounds__(R * (1 << LOGK) / 32) fft_q1s(const __grid_constant__ FftArgs A) {
-  constexpr int LN = LOGK - 1, N = 1 << LN, K = 2 * N, T = N / 16, SROW = N + N / 16 + 1, H = N / 2;
-  extern __shared__ float2 smem[];
-  const int rr = threadIdx.x / T, j = threadIdx.x % T;
-  const int k1 = blockIdx.x * R + rr;
-  if (blockIdx.x == 0 && threadIdx.x < 4 && A.acc) A.acc[threadIdx.x] = 0.0;
-  float2* s = smem + rr * SROW;
-  float4* g = reinterpret_cast<float4*>(A.grid + (size_t)k1 * K);
-  float2 ge[16], go[16];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const float4 q = g[j + i * T];
-    ge[i] = make_float2(q.x, q.y);
-    go[i] = make_float2(q.z, q.w);
-  }
-  if (A.grid_lo) {  // the compensated sums: high part + rounding errors (BF16 pairs, 8 bytes per 2 cells)
-    uint2* gl = reinterpret_cast<uint2*>(A.grid_lo + (size_t)k1 * K);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const uint2 q = gl[j + i * T];
-      ge[i] = cadd(ge[i], __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x)));
-      go[i] = cadd(go[i], __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y)));
-    }
-#pragma unroll
-    for (int i = 0; i < 16; ++i) gl[j + i * T] = make_uint2(0u, 0u);
-  }
-#pragma unroll
-  for (int i = 0; i < 16; ++i) g[j + i * T] = make_float4(0.f, 0.f, 0.f, 0.f);
-  fft_row<LN, +1, 2>(ge, s, j, A.tw, A.twp);
-  __syncthreads();
-  fft_row<LN, +1, 2>(go, s, j, A.tw, A.twp);
+// Both inverse transforms of a row whose even (grp 0) or odd (grp 1) samples this thread holds in v:
+// on return buffer A holds IDFT_n(G[0::2]) and buffer B IDFT_n(G[1::2]) (natural order, padded).
+template <int LN>
+__device__ __forceinline__ void split_inverse(float2 (&v)[16], float2* buf, int j,
+                                              const float2* __restrict__ tw, const float2* __restrict__ twp) {
+  constexpr int T = SplitGeom<LN>::T;
+  fft_row<LN, +1, 2>(v, buf, j, tw, twp);
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const int q = j + i * T, a = q < H ? q + H : q - H;  // image row of centred offset jo
-    s[PADI(a)] = split_combine(ge[i], go[i], q, N, A.tw);
-  }
+  for (int i = 0; i < 16; ++i) buf[PADI(j + i * T)] = v[i];
   __syncthreads();
-  const int k10 = blockIdx.x * R;
-  for (int idx = threadIdx.x; idx < R * N; idx += R * T) {
-    const int r = idx % R, a = idx / R;
-    A.tmp[(size_t)a * K + k10 + r] = smem[r * SROW + PADI(a)];
-  }
 }
 
-// Q2 (split): rows a of U (even and odd samples), inverse transforms and the centred outputs, then
-// the epilogue of fft_q2 (two image rows per CTA).
-template <int LOGK, bool CH>
-__global__ void __launch_bounds__((1 << LOGK) / 32, (1 << LOGK) / 32 <= 256 ? 2 : 1) fft_q2s(
+// Q1 (split): row k1 of the gridded data (the even samples to one thread group, the odd to the
+// other, plus the compensation grid), inverse transforms, the n centred outputs written transposed
+// into U[a][k1]; the grid (and compensation grid) row is re-zeroed.
+template <int LOGK>
+__global__ void __launch_bounds__((1 << LOGK) / 16, (1 << LOGK) / 16 <= 512 ? 2 : 1) fft_q1s(
     const __grid_constant__ FftArgs A) {
-  constexpr int LN = LOGK - 1, N = 1 << LN, K = 2 * N, T = N / 16, SROW = N + N / 16 + 1, H = N / 2;
+  using Sg = SplitGeom<LOGK - 1>;
+  constexpr int N = Sg::N, K = 2 * N, T = Sg::T, H = Sg::H;
   extern __shared__ float2 smem[];
-  float* gs = reinterpret_cast<float*>(smem + SROW);  // 2 x n gradient values
-  const int j = threadIdx.x;
+  const int grp = threadIdx.x / T, j = threadIdx.x % T, k1 = blockIdx.x;
+  float2* buf = smem + grp * Sg::SROW;
+  if (blockIdx.x == 0 && threadIdx.x < 4 && A.acc) A.acc[threadIdx.x] = 0.0;
+  float2* g = A.grid + (size_t)k1 * K + grp;  // sample 2 m + grp at g[2 m]
+  float2 v[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = g[2 * (j + i * T)];
+  if (A.grid_lo) {  // the compensated sums: high part + rounding errors (BF16 pairs)
+    __nv_bfloat162* gl = A.grid_lo + (size_t)k1 * K + grp;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      v[i] = cadd(v[i], __bfloat1622float2(gl[2 * (j + i * T)]));
+      gl[2 * (j + i * T)] = __floats2bfloat162_rn(0.f, 0.f);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) g[2 * (j + i * T)] = make_float2(0.f, 0.f);
+  split_inverse<LOGK - 1>(v, buf, j, A.tw, A.twp);
+  // transform index q holds image row a = q + n/2 (q < n/2) or q - n/2; combined into buffer B's
+  // free copy: each thread takes pairs (q, q + n/2), both read before either is written
+  const float2* be = smem;
+  float2* bo = smem + Sg::SROW;
+  for (int q = threadIdx.x; q < H; q += 2 * T) {
+    const float2 lo = split_combine(be[PADI(q)], bo[PADI(q)], q, N, A.tw);
+    const float2 hi = split_combine(be[PADI(q + H)], bo[PADI(q + H)], q + H, N, A.tw);
+    bo[PADI(q + H)] = lo;
+    bo[PADI(q)] = hi;
+  }
+  __syncthreads();
+  for (int a = threadIdx.x; a < N; a += 2 * T) A.tmp[(size_t)a * K + k1] = bo[PADI(a)];
+}
+
+// Q2 (split): rows a of U (even samples to one thread group, odd to the other), inverse transforms
+// and the centred outputs, then the epilogue of fft_q2 (two image rows per CTA).
+template <int LOGK, bool CH>
+__global__ void __launch_bounds__((1 << LOGK) / 16, (1 << LOGK) / 16 <= 512 ? 2 : 1) fft_q2s(
+    const __grid_constant__ FftArgs A) {
+  using Sg = SplitGeom<LOGK - 1>;
+  constexpr int N = Sg::N, K = 2 * N, T = Sg::T, H = Sg::H;
+  extern __shared__ float2 smem[];
+  const int grp = threadIdx.x / T, j = threadIdx.x % T;
+  float2* buf = smem + grp * Sg::SROW;
+  float* gs = reinterpret_cast<float*>(smem + 2 * Sg::SROW);  // 2 x n gradient values
   const int a0 = 2 * blockIdx.x;
 #pragma unroll 1
   for (int q2 = 0; q2 < 2; ++q2) {
     const int a = a0 + q2;
-    const float4* row = reinterpret_cast<const float4*>(A.tmp + (size_t)a * K);
-    float2 ge[16], go[16];
+    const float2* row = A.tmp + (size_t)a * K + grp;
+    if (q2) __syncthreads();  // the previous row is done with both buffers
+    float2 v[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const float4 q = row[j + i * T];
-      ge[i] = make_float2(q.x, q.y);
-      go[i] = make_float2(q.z, q.w);
-    }
-    if (q2) __syncthreads();  // the previous row's transforms are done with the buffer
-    fft_row<LN, +1, 2>(ge, smem, j, A.tw, A.twp);
-    __syncthreads();
-    fft_row<LN, +1, 2>(go, smem, j, A.tw, A.twp);
+    for (int i = 0; i < 16; ++i) v[i] = row[2 * (j + i * T)];
+    split_inverse<LOGK - 1>(v, buf, j, A.tw, A.twp);
     const float ca = A.cinv[a];
     const float2 cha = CH ? A.chirp[a] : make_float2(1.f, 0.f);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int q = j + i * T, b = q < H ? q + H : q - H;
-      const float2 x = split_combine(ge[i], go[i], q, N, A.tw);
+    const float2* be = smem;
+    const float2* bo = smem + Sg::SROW;
+    for (int q = threadIdx.x; q < N; q += 2 * T) {
+      const int b = q < H ? q + H : q - H;
+      const float2 x = split_combine(be[PADI(q)], bo[PADI(q)], q, N, A.tw);
       if (CH) {  // Re{conj(chirp) x}: the adjoint of the centre chirp of Z_s
         const float2 c = cmul(cha, A.chirp[b]);
         gs[q2 * N + b] = (x.x * c.x + x.y * c.y) * ca * A.cinv[b];
@@ -633,7 +655,7 @@ __global__ void __launch_bounds__((1 << LOGK) / 32, (1 << LOGK) / 32 <= 256 ? 2 
     }
   }
   __syncthreads();
-  q2_epilogue<CH>(A, gs, a0, j, T);
+  q2_epilogue<CH>(A, gs, a0, threadIdx.x, 2 * T);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -660,14 +682,15 @@ constexpr int split_rows(int max_threads, int max_rows) {
 // the split passes when K = 2n (every launch configuration of the general passes otherwise)
 template <int LOGK>
 int launch_forward_split(pnp_plan* p, const FftArgs& A) {
-  constexpr int N = 1 << (LOGK - 1), T = N / 16, SROW = N + N / 16 + 1;
-  constexpr int R1 = split_rows<LOGK>(1024, 16), R2 = split_rows<LOGK>(512, 16);
-  const int smem1 = R1 * SROW * 8, smem2 = R2 * SROW * 8;
+  using Sg = SplitGeom<LOGK - 1>;
+  constexpr int N = Sg::N, T = Sg::T;
+  constexpr int R1 = split_rows<LOGK>(1024, 16);
+  const int smem1 = R1 * Sg::SROW * 8, smem2 = 2 * Sg::SROW * 8;
   static bool attr = false;
   if (!attr) {
     PNP_CUDA(cudaFuncSetAttribute(fft_p1s<LOGK, R1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
     PNP_CUDA(cudaFuncSetAttribute(fft_p1s<LOGK, R1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
-    PNP_CUDA(cudaFuncSetAttribute(fft_p2s<LOGK, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
+    PNP_CUDA(cudaFuncSetAttribute(fft_p2s<LOGK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
     attr = true;
   }
   const dim3 g1((N + R1 - 1) / R1, 2);
@@ -676,29 +699,29 @@ int launch_forward_split(pnp_plan* p, const FftArgs& A) {
   else
     fft_p1s<LOGK, R1, false><<<g1, R1 * T, smem1, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
-  fft_p2s<LOGK, R2><<<2 * N / R2, R2 * T, smem2, p->stream>>>(A);
+  fft_p2s<LOGK><<<2 * N, 2 * T, smem2, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
 
 template <int LOGK>
 int launch_adjoint_split(pnp_plan* p, const FftArgs& A) {
-  constexpr int N = 1 << (LOGK - 1), T = N / 16, SROW = N + N / 16 + 1;
-  constexpr int R2 = split_rows<LOGK>(512, 16);
-  const int smem1 = R2 * SROW * 8, smem2 = SROW * 8 + 2 * N * 4;
+  using Sg = SplitGeom<LOGK - 1>;
+  constexpr int N = Sg::N, T = Sg::T;
+  const int smem1 = 2 * Sg::SROW * 8, smem2 = 2 * Sg::SROW * 8 + 2 * N * 4;
   static bool attr = false;
   if (!attr) {
-    PNP_CUDA(cudaFuncSetAttribute(fft_q1s<LOGK, R2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
+    PNP_CUDA(cudaFuncSetAttribute(fft_q1s<LOGK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
     PNP_CUDA(cudaFuncSetAttribute(fft_q2s<LOGK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
     PNP_CUDA(cudaFuncSetAttribute(fft_q2s<LOGK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
     attr = true;
   }
-  fft_q1s<LOGK, R2><<<2 * N / R2, R2 * T, smem1, p->stream>>>(A);
+  fft_q1s<LOGK><<<2 * N, 2 * T, smem1, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
   if (A.chirp)
-    fft_q2s<LOGK, true><<<N / 2, T, smem2, p->stream>>>(A);
+    fft_q2s<LOGK, true><<<N / 2, 2 * T, smem2, p->stream>>>(A);
   else
-    fft_q2s<LOGK, false><<<N / 2, T, smem2, p->stream>>>(A);
+    fft_q2s<LOGK, false><<<N / 2, 2 * T, smem2, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
