@@ -577,17 +577,18 @@ __device__ __forceinline__ void split_inverse(float2 (&v)[16], float2* buf, int 
   __syncthreads();
 }
 
-// Q1 (split): row k1 of the gridded data (the even samples to one thread group, the odd to the
-// other, plus the compensation grid), inverse transforms, the n centred outputs written transposed
-// into U[a][k1]; the grid (and compensation grid) row is re-zeroed.
-template <int LOGK>
-__global__ void __launch_bounds__((1 << LOGK) / 16, (1 << LOGK) / 16 <= 512 ? 2 : 1) fft_q1s(
-    const __grid_constant__ FftArgs A) {
+// Q1 (split): rows k1, k1 + 1 of the gridded data (for each, the even samples to one thread group,
+// the odd to another, plus the compensation grid), inverse transforms, and the n centred outputs of
+// both rows written transposed into U[a][k1 .. k1 + 1] (one 16-byte store per image row a); the grid
+// (and compensation grid) rows are re-zeroed.
+template <int LOGK, int R>
+__global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_q1s(const __grid_constant__ FftArgs A) {
   using Sg = SplitGeom<LOGK - 1>;
   constexpr int N = Sg::N, K = 2 * N, T = Sg::T, H = Sg::H;
   extern __shared__ float2 smem[];
-  const int grp = threadIdx.x / T, j = threadIdx.x % T, k1 = blockIdx.x;
-  float2* buf = smem + grp * Sg::SROW;
+  const int r = threadIdx.x / (2 * T), grp = (threadIdx.x / T) & 1, j = threadIdx.x % T;
+  const int k10 = R * blockIdx.x, k1 = k10 + r;
+  float2* buf = smem + (2 * r + grp) * Sg::SROW;
   if (blockIdx.x == 0 && threadIdx.x < 4 && A.acc) A.acc[threadIdx.x] = 0.0;
   float2* g = A.grid + (size_t)k1 * K + grp;  // sample 2 m + grp at g[2 m]
   float2 v[16];
@@ -604,18 +605,27 @@ __global__ void __launch_bounds__((1 << LOGK) / 16, (1 << LOGK) / 16 <= 512 ? 2 
 #pragma unroll
   for (int i = 0; i < 16; ++i) g[2 * (j + i * T)] = make_float2(0.f, 0.f);
   split_inverse<LOGK - 1>(v, buf, j, A.tw, A.twp);
-  // transform index q holds image row a = q + n/2 (q < n/2) or q - n/2; combined into buffer B's
-  // free copy: each thread takes pairs (q, q + n/2), both read before either is written
-  const float2* be = smem;
-  float2* bo = smem + Sg::SROW;
-  for (int q = threadIdx.x; q < H; q += 2 * T) {
+  // transform index q holds image row a = q + n/2 (q < n/2) or q - n/2; combined into the odd
+  // buffer: each thread of the row takes pairs (q, q + n/2), both read before either is written
+  const float2* be = smem + 2 * r * Sg::SROW;
+  float2* bo = smem + (2 * r + 1) * Sg::SROW;
+  for (int q = threadIdx.x % (2 * T); q < H; q += 2 * T) {
     const float2 lo = split_combine(be[PADI(q)], bo[PADI(q)], q, N, A.tw);
     const float2 hi = split_combine(be[PADI(q + H)], bo[PADI(q + H)], q + H, N, A.tw);
     bo[PADI(q + H)] = lo;
     bo[PADI(q)] = hi;
   }
   __syncthreads();
-  for (int a = threadIdx.x; a < N; a += 2 * T) A.tmp[(size_t)a * K + k1] = bo[PADI(a)];
+  const float2* x0 = smem + Sg::SROW;
+  if constexpr (R == 2) {
+    const float2* x1 = smem + 3 * Sg::SROW;
+    for (int a = threadIdx.x; a < N; a += 4 * T) {
+      const float2 u0 = x0[PADI(a)], u1 = x1[PADI(a)];
+      *reinterpret_cast<float4*>(A.tmp + (size_t)a * K + k10) = make_float4(u0.x, u0.y, u1.x, u1.y);
+    }
+  } else {
+    for (int a = threadIdx.x; a < N; a += 2 * T) A.tmp[(size_t)a * K + k10] = x0[PADI(a)];
+  }
 }
 
 // Q2 (split): rows a of U (even samples to one thread group, odd to the other), inverse transforms
@@ -708,15 +718,16 @@ template <int LOGK>
 int launch_adjoint_split(pnp_plan* p, const FftArgs& A) {
   using Sg = SplitGeom<LOGK - 1>;
   constexpr int N = Sg::N, T = Sg::T;
-  const int smem1 = 2 * Sg::SROW * 8, smem2 = 2 * Sg::SROW * 8 + 2 * N * 4;
+  constexpr int RQ = 4 * T <= 1024 ? 2 : 1;  // grid rows per Q1 CTA (two thread groups each)
+  const int smem1 = 2 * RQ * Sg::SROW * 8, smem2 = 2 * Sg::SROW * 8 + 2 * N * 4;
   static bool attr = false;
   if (!attr) {
-    PNP_CUDA(cudaFuncSetAttribute(fft_q1s<LOGK>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
+    PNP_CUDA(cudaFuncSetAttribute(fft_q1s<LOGK, RQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
     PNP_CUDA(cudaFuncSetAttribute(fft_q2s<LOGK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
     PNP_CUDA(cudaFuncSetAttribute(fft_q2s<LOGK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem2));
     attr = true;
   }
-  fft_q1s<LOGK><<<2 * N, 2 * T, smem1, p->stream>>>(A);
+  fft_q1s<LOGK, RQ><<<2 * N / RQ, RQ * 2 * T, smem1, p->stream>>>(A);
   PNP_CHECK_LAUNCH();
   if (A.chirp)
     fft_q2s<LOGK, true><<<N / 2, 2 * T, smem2, p->stream>>>(A);
