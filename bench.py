@@ -41,7 +41,8 @@ WORKLOADS = {
     "C3": dict(name="C3", desc="4096^2 img, 8192^2 grid, 2e7 vis in 64 blocks, Briggs r0, w-folded G J7-16 c64"),
     "C1": dict(name="C1", desc="2048^2 img, 4096^2 grid, 2e7 vis, w-folded G J7-16 c64"),
     "C0": dict(name="C0", desc="256^2 img, 512^2 grid, 2e5 vis, KB J7"),
-    "C4": dict(name="C4", desc="8192^2 img, 16384^2 grid, 2.5e7 vis (one band), Briggs r0, w-folded G J7-9 bf16"),
+    "C4": dict(name="C4", desc="8192^2 img, 16384^2 grid, 2.5e7 vis (one band), Briggs r0, w-folded G J7-9 bf16",
+               facets="8x8"),
 }
 BLOCKS = {"C3": 64, "C1": 1, "C0": 1, "C4": 1}
 CPU_SAMPLE_ROWS = 4000
@@ -252,7 +253,7 @@ def cpu_sample_inputs(prob, x_dev_np, y_np):
 # ---------------------------------------------------------------- reference arm
 def workload_desc(wl, learned):
     """The workload's description with the denoiser the timed loop applies (one string for both arms)."""
-    return wl["desc"] + (", CNN 4x4 facets" if learned else ", Haar")
+    return wl["desc"] + ((", CNN %s facets" % wl.get("facets", "4x4")) if learned else ", Haar")
 
 
 def run_reference(args):

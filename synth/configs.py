@@ -24,7 +24,7 @@ CONFIGS = {
                robust=0.0),
     "C4": dict(n=8192, K=16384, M=25_000_000, hours=12.0, supports=(7, 8, 8, 9),
                w_spread=2.0, isnr_db=40.0, n_blocks=1, facets=(8, 1024, 1024), halo=32, iters=500,
-               robust=0.0),
+               robust=0.0, ref_freq_hz=1.399e9),
 }
 
 
@@ -51,8 +51,13 @@ def make_problem(name: str, M: int | None = None, n: int | None = None, K: int |
         cfg["K"] = int(K if K is not None else 2 * n)
     m, nn, kk = cfg["M"], cfg["n"], cfg["K"]
     enu = mk.antenna_layout(mk.rng_for("uv", root_seed))
-    uvw = mk.uvw_track(enu, m, cfg["hours"], freq_hz=freq_hz)
+    # the pixel size is fixed by a reference band (both bands of the 8192^2 workload share one image
+    # grid, as in Sec. 3): its longest baseline sits at 0.8 of Nyquist, another band's (u, v, w) in
+    # wavelengths scale with its frequency
+    ref = cfg.get("ref_freq_hz", freq_hz)
+    uvw = mk.uvw_track(enu, m, cfg["hours"], freq_hz=ref)
     omega, w, dl = mk.imaging_geometry(uvw, nn, kk, 0.8, cfg["w_spread"])
+    omega, w = omega * (freq_hz / ref), w * (freq_hz / ref)
     out = dict(name=name, n=nn, K=kk, M=m, omega=omega, w=w, dl=dl,
                isnr_db=cfg["isnr_db"], iters=cfg["iters"], halo=cfg["halo"])
     out["J_per_row"] = (mk.j_per_row_by_w_quartile(w, cfg["supports"])
