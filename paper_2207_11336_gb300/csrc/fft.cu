@@ -72,13 +72,30 @@ __device__ __forceinline__ void dft2(float2& a, float2& b) {
   b = csub(t, b);
 }
 
+// complex add and subtract as one packed FP32x2 instruction each (lane-wise IEEE add, the same
+// rounding as two scalar adds)
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+  return *reinterpret_cast<float2*>(&d);
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+  return *reinterpret_cast<float2*>(&d);
+}
+
 template <int DIR>
 __device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
-  float2 s02 = cadd(x0, x2), d02 = csub(x0, x2);
-  float2 s13 = cadd(x1, x3), d13 = rotq<DIR>(csub(x1, x3));
-  x0 = cadd(s02, s13);
-  x2 = csub(s02, s13);
-  x1 = cadd(d02, d13);
+  float2 s02 = padd(x0, x2), d02 = psub(x0, x2);
+  float2 s13 = padd(x1, x3), d13 = rotq<DIR>(psub(x1, x3));
+  x0 = padd(s02, s13);
+  x2 = psub(s02, s13);
+  x1 = cadd(d02, d13);   // the quarter-turn swaps lanes: scalar adds take it as operand order
   x3 = csub(d02, d13);
 }
 
@@ -131,14 +148,26 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int idx
   return w;
 }
 
+// Barrier of the threads of one transform: named barrier `id` over `nthr` threads (whole warps), or
+// the CTA-wide barrier when id is 0.  Transforms that share a CTA but not data then pass their
+// exchanges independently.
+__device__ __forceinline__ void group_sync(int id, int nthr) {
+  if (id == 0)
+    __syncthreads();
+  else
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthr) : "memory");
+}
+
 // Length-K FFT of one row.  On entry v[i] holds element j + i*K/16 of the
 // row; on exit v[i] holds output element j + i*K/16 (natural order).
 // s is this row's padded shared-memory buffer (K + K/16 float2).
 // TWS: stride of the twiddle table tw for the radix-2/4/8 tail pass (the table holds exp(-2 pi i t / L)
 // for a length L = TWS 2^LOGK: the plan's length-K table serves the length-K/2 transforms with TWS = 2).
+// bid: the barrier of the row's threads (group_sync; 0 = the CTA's).
 template <int LOGK, int DIR, int TWS = 1>
 __device__ __forceinline__ void fft_row(float2 (&v)[16], float2* s, int j,
-                                        const float2* __restrict__ tw, const float2* __restrict__ twp) {
+                                        const float2* __restrict__ tw, const float2* __restrict__ twp,
+                                        int bid = 0) {
   constexpr int K = 1 << LOGK;
   constexpr int Q = LOGK / 4;
   static_assert(Q <= 3, "the pass twiddle tables cover radix-16 passes 1 and 2");
@@ -158,10 +187,10 @@ __device__ __forceinline__ void fft_row(float2 (&v)[16], float2* s, int j,
     dft16<DIR>(v);
     if (!(p == Q - 1 && REM == 0)) {
       const int idxD = ((j >> (4 * p)) << (4 * p + 4)) + k;
-      __syncthreads();
+      group_sync(bid, K16);
 #pragma unroll
       for (int r = 0; r < 16; ++r) s[PADI(idxD + r * Ns)] = v[r];
-      __syncthreads();
+      group_sync(bid, K16);
 #pragma unroll
       for (int r = 0; r < 16; ++r) v[r] = s[PADI(j + r * K16)];
     }
@@ -499,8 +528,9 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 32) fft_p1s(const __grid_con
     }
     v[i] = val;
   }
-  fft_row<LN, -1, 2>(v, s, j, A.tw, A.twp);
-  __syncthreads();
+  const int bid = T % 32 == 0 && R < 15 ? 1 + rr : 0;  // the row's named barrier (group_sync)
+  fft_row<LN, -1, 2>(v, s, j, A.tw, A.twp, bid);
+  group_sync(bid, T);
 #pragma unroll
   for (int i = 0; i < 16; ++i) s[PADI(j + i * T)] = v[i];
   __syncthreads();
@@ -512,12 +542,14 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 32) fft_p1s(const __grid_con
 }
 
 // The two length-n transforms of a row run side by side: the CTA's first n/16 threads transform the
-// even half in shared-memory buffer A, the next n/16 the odd half in buffer B (both groups pass the
-// same barriers), so a thread holds one transform's 16 values (64 registers) and two CTAs share an
-// SM, one CTA's loads overlapping the other's transforms.
+// even half in shared-memory buffer A, the next n/16 the odd half in buffer B (each group passes its
+// own named barrier until the halves meet), so a thread holds one transform's 16 values (64
+// registers) and two CTAs share an SM, one CTA's loads overlapping the other's transforms.
 template <int LN>
 struct SplitGeom {
   static constexpr int N = 1 << LN, T = N / 16, SROW = N + N / 16 + 1, H = N / 2;
+  // named barrier of transform g of the CTA (group_sync), when its threads are whole warps
+  static __device__ __forceinline__ int bar(int g) { return T % 32 == 0 && g < 15 ? 1 + g : 0; }
 };
 
 // P2 (split): row k1 of T (the n centred inputs along axis 0); both halves, written interleaved
@@ -543,8 +575,8 @@ __global__ void __launch_bounds__((1 << LOGK) / 16, (1 << LOGK) / 16 <= 512 ? 2 
       v[i] = u;
     }
   }
-  fft_row<LOGK - 1, -1, 2>(v, buf, j, A.tw, A.twp);
-  __syncthreads();
+  fft_row<LOGK - 1, -1, 2>(v, buf, j, A.tw, A.twp, Sg::bar(grp));
+  group_sync(Sg::bar(grp), T);
 #pragma unroll
   for (int i = 0; i < 16; ++i) buf[PADI(j + i * T)] = v[i];
   __syncthreads();
@@ -566,12 +598,15 @@ __device__ __forceinline__ float2 split_combine(float2 xe, float2 xo, int q, int
 
 // Both inverse transforms of a row whose even (grp 0) or odd (grp 1) samples this thread holds in v:
 // on return buffer A holds IDFT_n(G[0::2]) and buffer B IDFT_n(G[1::2]) (natural order, padded).
+// g: the transform's index in the CTA (its named barrier); the last barrier is the CTA's, since the
+// combination reads both buffers.
 template <int LN>
 __device__ __forceinline__ void split_inverse(float2 (&v)[16], float2* buf, int j,
-                                              const float2* __restrict__ tw, const float2* __restrict__ twp) {
-  constexpr int T = SplitGeom<LN>::T;
-  fft_row<LN, +1, 2>(v, buf, j, tw, twp);
-  __syncthreads();
+                                              const float2* __restrict__ tw, const float2* __restrict__ twp, int g) {
+  using Sg = SplitGeom<LN>;
+  constexpr int T = Sg::T;
+  fft_row<LN, +1, 2>(v, buf, j, tw, twp, Sg::bar(g));
+  group_sync(Sg::bar(g), T);
 #pragma unroll
   for (int i = 0; i < 16; ++i) buf[PADI(j + i * T)] = v[i];
   __syncthreads();
@@ -604,7 +639,7 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_q1s(const __grid_con
   }
 #pragma unroll
   for (int i = 0; i < 16; ++i) g[2 * (j + i * T)] = make_float2(0.f, 0.f);
-  split_inverse<LOGK - 1>(v, buf, j, A.tw, A.twp);
+  split_inverse<LOGK - 1>(v, buf, j, A.tw, A.twp, 2 * r + grp);
   // transform index q holds image row a = q + n/2 (q < n/2) or q - n/2; combined into the odd
   // buffer: each thread of the row takes pairs (q, q + n/2), both read before either is written
   const float2* be = smem + 2 * r * Sg::SROW;
@@ -648,7 +683,7 @@ __global__ void __launch_bounds__((1 << LOGK) / 16, (1 << LOGK) / 16 <= 512 ? 2 
     float2 v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = row[2 * (j + i * T)];
-    split_inverse<LOGK - 1>(v, buf, j, A.tw, A.twp);
+    split_inverse<LOGK - 1>(v, buf, j, A.tw, A.twp, grp);
     const float ca = A.cinv[a];
     const float2 cha = CH ? A.chirp[a] : make_float2(1.f, 0.f);
     const float2* be = smem;
@@ -719,7 +754,8 @@ int launch_adjoint_split(pnp_plan* p, const FftArgs& A) {
   using Sg = SplitGeom<LOGK - 1>;
   constexpr int N = Sg::N, T = Sg::T;
   constexpr int RQ = 4 * T <= 1024 ? 2 : 1;  // grid rows per Q1 CTA (two thread groups each)
-  const int smem1 = 2 * RQ * Sg::SROW * 8, smem2 = 2 * Sg::SROW * 8 + 2 * N * 4;
+  const int smem1 = 2 * RQ * Sg::SROW * 8;
+  const int smem2 = 2 * Sg::SROW * 8 + 2 * N * 4;
   static bool attr = false;
   if (!attr) {
     PNP_CUDA(cudaFuncSetAttribute(fft_q1s<LOGK, RQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
