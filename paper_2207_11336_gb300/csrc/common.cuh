@@ -153,6 +153,12 @@ struct pnp_plan {
   float2* d_H = nullptr;       // holographic H = G^H G: [S*S offsets][K*K cells], S = 2 Jmax - 1
   float2* d_dirty = nullptr;   // K*K: G^H y of the current FB run (holographic mode)
   float* d_rowscale = nullptr; // M (caller order): data weights d_m folded into the rows of G, or NULL
+  // uv support of G (the grid cells that hold taps, over every row and w-stack): per grid row k1,
+  // the largest centred |k0| of a tap in the row (-1: no tap), and the centred half-width of the
+  // band of rows k1 that hold taps (-1: none).  The split FFT passes transform and move only what
+  // lies in it (the pruned F of Eq. 1: G reads no other cell and writes no other cell).
+  int* d_rowh = nullptr;       // K
+  int band = -1;
   int holo_S = 0;
   bool holo = false;           // FB loop and op_norm apply H instead of streaming G
   int64_t device_bytes = 0;

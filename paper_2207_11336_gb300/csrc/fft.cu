@@ -242,6 +242,8 @@ struct FftArgs {
   const float2* chirp;     // n (w-stack s of several): exp(i pi a_s (a - n/2)^2) per image axis, else NULL
   float* gacc;             // n x n gradient image summed over the w-stacks
   int gacc_mode;           // GACC_*: how the Q2 gradient meets gacc
+  const int* rowh;         // K: uv support per grid row k1 (largest centred |k0| of a tap, -1: none)
+  int band;                // centred half-width of the band of grid rows k1 that hold taps (-1: none)
 };
 
 // Q2 and the sum over w-stacks (Eq. phidagphi): the first stack writes its Re{Z_s^H F^H ...}
@@ -492,6 +494,9 @@ __global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(const __grid_constant
   q2_epilogue<CH>(A, gs, a0, j, T);
 }
 
+// |centred index| of FFT index k: k for k < K/2, K - k above
+__device__ __forceinline__ int centred_abs(int k, int K) { return k < K / 2 ? k : K - k; }
+
 // ---------------------------------------------------------------- split passes (K = 2n)
 // With twofold oversampling (K = 2n) each length-K transform of the operator halves into two
 // length-n transforms.  Forward, n non-zero inputs at the centred positions p mod K:
@@ -501,6 +506,12 @@ __global__ void __launch_bounds__((1 << LOGK) / 16) fft_q2(const __grid_constant
 //   X[j] = IDFT_n(G[0::2])[j mod n] + exp(+2 pi i j / K) IDFT_n(G[1::2])[j mod n].
 // No transform runs over zero padding, and a length-n transform needs one shared-memory exchange
 // fewer than a length-2n one.  Layouts and epilogues are those of the general passes above.
+//
+// The split passes are also pruned to the uv support of G (FftArgs rowh, band): the forward pair
+// forms only the rows k1 of the band and writes only the cells of each row that hold taps (the
+// degridding reads no other cell; the rest of the forward grid stays zero from the plan's start);
+// the adjoint pair reads and re-zeroes only those cells of the gridded data (the gridding writes no
+// other), transforms only the band's rows, and Q2 reads U only at the band's columns k1.
 
 // P1 (split): image row a, output parity par (blockIdx.y): the even or odd half of its length-K
 // transform along axis 1, written transposed into T[k1 = 2m + par][a].
@@ -537,7 +548,8 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 32) fft_p1s(const __grid_con
   const int a0 = blockIdx.x * R;
   for (int idx = threadIdx.x; idx < R * N; idx += R * T) {
     const int r = idx % R, m = idx / R;
-    if (a0 + r < N) A.tmp[(size_t)(2 * m + par) * N + a0 + r] = smem[r * SROW + PADI(m)];
+    if (a0 + r < N && centred_abs(2 * m + par, 2 * N) <= A.band)  // rows k1 outside the band: never read
+      A.tmp[(size_t)(2 * m + par) * N + a0 + r] = smem[r * SROW + PADI(m)];
   }
 }
 
@@ -561,6 +573,8 @@ __global__ void __launch_bounds__((1 << LOGK) / 16, (1 << LOGK) / 16 <= 512 ? 2 
   constexpr int N = Sg::N, K = 2 * N, T = Sg::T, H = Sg::H;
   extern __shared__ float2 smem[];
   const int grp = threadIdx.x / T, j = threadIdx.x % T, k1 = blockIdx.x;
+  const int h = centred_abs(k1, K) <= A.band ? A.rowh[k1] : -1;  // the row's taps: centred |k0| <= h
+  if (h < 0) return;  // a row without taps (uniform over the CTA)
   float2* buf = smem + grp * Sg::SROW;
   const float2* row = A.tmp + (size_t)k1 * N;
   float2 v[16];
@@ -584,6 +598,7 @@ __global__ void __launch_bounds__((1 << LOGK) / 16, (1 << LOGK) / 16 <= 512 ? 2 
   const float2* be = smem;
   const float2* bo = smem + Sg::SROW;
   for (int m = threadIdx.x; m < N; m += 2 * T) {
+    if (min(centred_abs(2 * m, K), centred_abs(2 * m + 1, K)) > h) continue;  // no tap in the pair
     const float2 e = be[PADI(m)], o = bo[PADI(m)];
     g[m] = make_float4(e.x, e.y, o.x, o.y);
   }
@@ -625,20 +640,30 @@ __global__ void __launch_bounds__(R * (1 << LOGK) / 16) fft_q1s(const __grid_con
   const int k10 = R * blockIdx.x, k1 = k10 + r;
   float2* buf = smem + (2 * r + grp) * Sg::SROW;
   if (blockIdx.x == 0 && threadIdx.x < 4 && A.acc) A.acc[threadIdx.x] = 0.0;
+  bool any = false;  // a row of the CTA in the band (else Q2 never reads its columns of U)
+#pragma unroll
+  for (int q = 0; q < R; ++q) any |= centred_abs(k10 + q, K) <= A.band;
+  if (!any) return;
+  const int h = centred_abs(k1, K) <= A.band ? A.rowh[k1] : -1;  // cells with centred |k0| <= h
   float2* g = A.grid + (size_t)k1 * K + grp;  // sample 2 m + grp at g[2 m]
   float2 v[16];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = g[2 * (j + i * T)];
+  for (int i = 0; i < 16; ++i) {
+    const bool in = centred_abs(2 * (j + i * T) + grp, K) <= h;
+    v[i] = in ? g[2 * (j + i * T)] : make_float2(0.f, 0.f);
+  }
   if (A.grid_lo) {  // the compensated sums: high part + rounding errors (BF16 pairs)
     __nv_bfloat162* gl = A.grid_lo + (size_t)k1 * K + grp;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
+      if (centred_abs(2 * (j + i * T) + grp, K) > h) continue;
       v[i] = cadd(v[i], __bfloat1622float2(gl[2 * (j + i * T)]));
       gl[2 * (j + i * T)] = __floats2bfloat162_rn(0.f, 0.f);
     }
   }
 #pragma unroll
-  for (int i = 0; i < 16; ++i) g[2 * (j + i * T)] = make_float2(0.f, 0.f);
+  for (int i = 0; i < 16; ++i)
+    if (centred_abs(2 * (j + i * T) + grp, K) <= h) g[2 * (j + i * T)] = make_float2(0.f, 0.f);
   split_inverse<LOGK - 1>(v, buf, j, A.tw, A.twp, 2 * r + grp);
   // transform index q holds image row a = q + n/2 (q < n/2) or q - n/2; combined into the odd
   // buffer: each thread of the row takes pairs (q, q + n/2), both read before either is written
@@ -682,7 +707,8 @@ __global__ void __launch_bounds__((1 << LOGK) / 16, (1 << LOGK) / 16 <= 512 ? 2 
     if (q2) __syncthreads();  // the previous row is done with both buffers
     float2 v[16];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = row[2 * (j + i * T)];
+    for (int i = 0; i < 16; ++i)  // columns k1 = 2 m + grp outside the band are zero (Q1 skips them)
+      v[i] = centred_abs(2 * (j + i * T) + grp, K) <= A.band ? row[2 * (j + i * T)] : make_float2(0.f, 0.f);
     split_inverse<LOGK - 1>(v, buf, j, A.tw, A.twp, grp);
     const float ca = A.cinv[a];
     const float2 cha = CH ? A.chirp[a] : make_float2(1.f, 0.f);
@@ -835,6 +861,8 @@ int fft_forward(pnp_plan* p, const float* x, int s) {
   A.twp = p->d_twp;
   A.tmp = p->d_tmp;
   A.grid = p->d_gridA;
+  A.rowh = p->d_rowh;
+  A.band = p->band;
   cudaEvent_t ev;
   if (int rc = stage_begin(p, 0, &ev)) return rc;
   int rc = PNP_OK;
@@ -870,6 +898,8 @@ int fft_adjoint(pnp_plan* p, int mode, const float* x, float* out, float gamma, 
   A.tmp = p->d_tmp;
   A.grid = p->d_gridB;
   A.grid_lo = p->compensated ? p->d_gridB_lo : nullptr;
+  A.rowh = p->d_rowh;
+  A.band = p->band;
   A.out = out;
   A.acc = p->d_acc;
   A.gamma = gamma;

@@ -390,6 +390,26 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     p->h_rowptr[i + 1] = p->h_rowptr[i] + (int64_t)geom[m].J * geom[m].J;
   }
   p->nnz = p->h_rowptr[M];
+  // uv support of G: per grid row k1 the largest centred |k0| of its taps, and the band of rows
+  std::vector<int> rowh(K, -1);
+  {
+    auto centred = [K](int k) {
+      k = ((k % K) + K) % K;
+      return k < K / 2 ? k : k - K;
+    };
+    for (int64_t m = 0; m < M; ++m) {
+      const RowGeom& g = geom[m];
+      const int c0 = centred(g.s0), c0e = c0 + g.J - 1;  // the row's k0 taps, centred (may wrap)
+      const int hm = c0e >= K / 2 ? K / 2 : std::max(std::abs(c0), std::abs(c0e));
+      for (int t = 0; t < g.J; ++t) {
+        int& h = rowh[((g.s1 + t) % K + K) % K];
+        h = std::max(h, hm);
+      }
+    }
+    p->band = -1;
+    for (int k = 0; k < K; ++k)
+      if (rowh[k] >= 0) p->band = std::max(p->band, std::abs(centred(k)));
+  }
   std::vector<RowGeom>().swap(geom);
 
   // w-kernel series: b = bscale * a, qn in [0, qmax], centred at c0 = qmax / 2
@@ -439,6 +459,7 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
   if (int rc = dev_alloc(p, &p->d_gridB, KK)) return rc;
   if (int rc = dev_alloc(p, &p->d_gridB_lo, KK)) return rc;
   if (int rc = dev_alloc(p, &p->d_tmp, (size_t)K * n)) return rc;
+  if (int rc = dev_alloc(p, &p->d_rowh, (size_t)K)) return rc;
   const size_t wbytes = p->wdtype == PNP_W_BF16C ? 4 : 8;
   {
     void* w = nullptr;
@@ -489,8 +510,11 @@ int plan_build(pnp_plan* p, const double* uvw, const int8_t* Jrow, const int32_t
     }
     PNP_CUDA(cudaMemcpy(p->d_twp, twp.data(), TWP_ENTRIES * sizeof(float2), cudaMemcpyHostToDevice));
   }
+  // the forward grid outside G's support is never written (the split passes prune it) and reads as 0
+  PNP_CUDA(cudaMemset(p->d_gridA, 0, KK * sizeof(float2)));
   PNP_CUDA(cudaMemset(p->d_gridB, 0, KK * sizeof(float2)));
   PNP_CUDA(cudaMemset(p->d_gridB_lo, 0, KK * sizeof(__nv_bfloat162)));
+  PNP_CUDA(cudaMemcpy(p->d_rowh, rowh.data(), K * sizeof(int), cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemset(p->d_acc, 0, 8 * sizeof(double)));
   PNP_CUDA(cudaMemset(p->d_status, 0, 4 * sizeof(int)));
   {

@@ -82,6 +82,7 @@ void free_plan(pnp_plan* p) {
   cudaFree(p->d_H);
   cudaFree(p->d_dirty);
   cudaFree(p->d_rowscale);
+  cudaFree(p->d_rowh);
   if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
   delete p;
 }

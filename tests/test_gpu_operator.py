@@ -257,3 +257,35 @@ def test_bf16_weights_error_is_bounded():
     y = to_host(gpu.phi_forward(to_dev_f32(pr["x"])))
     err = rel_l2(y, ora.forward(pr["x"]))
     assert err <= 2.0 ** -8          # one BF16 rounding per weight, averaged over the row
+
+
+@pytest.mark.parametrize("case", ["narrow_band", "single_edge_row", "two_rows"])
+def test_fft_pruned_to_the_uv_support(case):
+    """The split FFT passes transform and move only G's uv support (the band of grid rows k1 that hold
+    taps and, per row, the cells up to the largest centred |k0| of a tap): an asymmetric narrow band,
+    one row whose taps wrap around both grid edges, and two rows far apart.  Forward, adjoint and the
+    fused gradient against the oracle, each twice with different inputs, so that a cell left stale
+    outside the support by one call would show in the next."""
+    n, K = 128, 256
+    rng = np.random.default_rng(41)
+    if case == "narrow_band":
+        M = 4000
+        omega = np.stack([rng.uniform(-np.pi, np.pi, M), rng.uniform(-0.15 * np.pi, 0.1 * np.pi, M)], axis=1)
+    elif case == "single_edge_row":
+        M = 1
+        omega = np.array([[0.995 * np.pi, -0.995 * np.pi]])
+    else:
+        M = 2
+        omega = np.array([[0.1, 0.7 * np.pi], [-0.6 * np.pi, -0.2]])
+    gpu = pnp.Plan(n, K, omega)
+    ora = onu.Operator(n, K, omega)
+    for rep in range(2):
+        x = rng.random((n, n)) + rep
+        assert rel_l2(to_host(gpu.phi_forward(to_dev_f32(x))), ora.forward(x)) <= TOL
+        r = synth.complex_normal(M, rng)
+        assert rel_l2(to_host(gpu.phi_adjoint(to_dev_c64(r))), ora.adjoint(r)) <= TOL
+        y = -ora.forward(x) + synth.complex_normal(M, rng)   # a residual without cancellation (M may be 1)
+        out = to_host(gpu.grad_step(to_dev_f32(x), to_dev_c64(y), 0.5))
+        ref = ofb.gradient_step(ora, x, y, 0.5)
+        assert rel_l2(x - out, x - ref) <= TOL
+    assert gpu.device_status() == 0
