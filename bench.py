@@ -731,11 +731,13 @@ def run_kernel_case(args):
 
 
 def fft_case(args):
-    """The FFT passes of the 4096^2 / 8192^2 operator with only 1000 visibilities (1.4 GB on the device)."""
+    """The FFT passes of the 4096^2 / 8192^2 operator with 2e5 visibilities of the benchmark's uv
+    distribution (1.7 GB on the device): enough rows that the uv support the passes are pruned to is
+    the benchmark's (the disc of the longest baselines)."""
     import torch
     import paper_2207_11336_gb300 as pnp
     import synth
-    prob = synth.make_problem("C3", M=1000)
+    prob = synth.make_problem("C3", M=200_000)
     plan = pnp.Plan(prob["n"], prob["K"], prob["omega"], prob["w"], prob["dl"], prob["J_per_row"])
     x = torch.from_numpy(prob["x_true"].astype(np.float32)).cuda()
     y = torch.from_numpy(prob["noise"].astype(np.complex64)).cuda()
