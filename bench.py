@@ -416,10 +416,12 @@ def run_gpu(args):
 
     learned = os.path.exists(WEIGHTS) and "facet_rows" in prob
     alpha = 1.0
+    cnn_tune = None
     if learned:
         params, wmeta = load_weights(WEIGHTS)
         cnn = pnp.CnnDenoiser(params, n, facet_rows=prob["facet_rows"], facet_cols=prob["facet_cols"],
                               halo=prob["halo"], stream=stream)
+        cnn_tune = cnn.autotune(x_true, reps=2)   # strip height of the convolution work lists, timed here
         # App. C, F: rescale by an upper bound on the peak that also matches the data's noise level to
         # the one the network was trained at (Eq. sigma); the library applies it (Eq. invpb2)
         alpha_match = heuristics.alpha_for_denoiser(tau_w, L, float(wmeta["sigma"]))
@@ -580,6 +582,7 @@ def run_gpu(args):
             params_f, meta_f = load_weights(WEIGHTS_L1)
             cnn_f = pnp.CnnDenoiser(params_f, n, facet_rows=prob["facet_rows"], facet_cols=prob["facet_cols"],
                                     halo=prob["halo"], stream=stream)
+            cnn_f.set_strip_rows(cnn_tune["strip_rows"])
             alpha_f = max(hp["alpha"], heuristics.alpha_for_denoiser(tau_w, L, float(meta_f["sigma"])))
             it_f, trace_f, _ = _run_to_snr(plan, cnn_f, y, gamma, L, x_true, alpha_f, target, args.converge_iters)
             comparison["learned_l1"] = {
@@ -661,7 +664,8 @@ def run_gpu(args):
                "config": {"workload": desc, "parallelism": f"replicas{ws}",
                           "l2": "inputs larger than L2 (G %.1f GB)" % (info["nnz"] * (wbytes + 2) / 1e9),
                           "nnz": info["nnz"], "denoiser": "cnn" if learned else "haar", "graph": True,
-                          "gridding_autotune": tune, "region_pitch": info["region_pitch"]},
+                          "gridding_autotune": tune, "region_pitch": info["region_pitch"],
+                          "cnn_autotune": cnn_tune},
                "clocks": clk.summary(),
                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": M * 8,
                        "d2h_bytes_per_step": n * n * 4 + 16},
@@ -766,17 +770,27 @@ def cnn_case(args):
     for _ in range(max(args.warmup, 1)):
         den.denoise(z, out)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(max(args.steps, 1)):
+
+    def timed():
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(max(args.steps, 1)):
+            den.denoise(z, out)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / max(args.steps, 1)
+
+    ms = timed()
+    by_rows = {}
+    for rows in (16, 24, 32, 48, 64, 96):   # the strip heights the autotuner chooses among
+        den.set_strip_rows(rows)
         den.denoise(z, out)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / max(args.steps, 1)
+        by_rows[rows] = timed()
+    den.set_strip_rows(32)
     px = _facet_pixels(n, prob["facet_rows"], prob["facet_cols"], 32)
     flop = px * CNN_FLOP_PER_PX
     print(json.dumps({"case": f"cnn {n}^2, 16 facets, halo 32", "ms": ms, "pixels_with_halo": int(px),
-                      "TFLOP_per_call": flop / 1e12, "TFLOPs": flop / ms / 1e9,
+                      "TFLOP_per_call": flop / 1e12, "TFLOPs": flop / ms / 1e9, "ms_by_strip_rows": by_rows,
                       "status": den.device_status()}))
     return 0
 

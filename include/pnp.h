@@ -318,6 +318,19 @@ int pnp_den_create_cnn(pnp_den** den, const float* weights_host,
                        const int32_t* facet_rows_host, int nfr,
                        const int32_t* facet_cols_host, int nfc, int halo, int n, void* stream);
 
+/* Work decomposition of a CNN denoiser (a performance setting: the results do not depend on it, bit
+ * for bit).  Each convolution layer walks strips of one 128-pixel column segment by about `rows`
+ * output rows of a facet (the last layer: of a facet core); a strip stages rows + 2 input rows, so
+ * taller strips re-read fewer halo rows and shorter ones balance the SMs better.  Default 32.
+ *  rows   in [4, 1024]; PNP_ERR_INVALID_ARG otherwise or for a denoiser that is not a CNN.
+ * Synchronises the device (work lists in use by launches in flight are not overwritten). */
+int pnp_den_cnn_set_strip_rows(pnp_den* den, int rows);
+/* Autotuner of the strip height above: times `reps` denoises (after one warm-up) of the device
+ * n x n image z for each of 16, 24, 32, 48, 64 and 96 rows on the denoiser's stream (CUDA events),
+ * keeps the fastest and returns it with its time per denoise (rows_out, ms_out may be NULL).
+ * Allocates and frees one n x n scratch image.  reps in [1, 100]. */
+int pnp_den_cnn_autotune(pnp_den* den, const float* z, int n, int reps, int* rows_out, double* ms_out);
+
 /* uSARA's denoiser (App. B): the prox of gamma_lambda ||W Psi^T x||_1 + iota_+(x) for the SARA
  * dictionary Psi (the Dirac basis and the 2-D Daubechies db1..db8 bases, each a `levels`-level
  * separable DWT with periodic extension, divided by 3 so that Psi Psi^T = I), computed by

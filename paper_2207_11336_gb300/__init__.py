@@ -34,6 +34,7 @@ EXPORTED = [
     "pnp_cnn_num_params", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm",
     "pnp_cnn_train_step_fne", "pnp_den_create_sara", "pnp_den_sara_reweight", "pnp_sara_transform",
     "pnp_plan_create_desc", "pnp_plan_scale_data", "pnp_plan_set_compensated", "pnp_cnn_trainer_apply_update",
+    "pnp_den_cnn_set_strip_rows", "pnp_den_cnn_autotune",
 ]
 PNP_POSITIVITY_ON, PNP_POSITIVITY_OFF = 0, 1
 
@@ -92,6 +93,8 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
     L.pnp_plan_scale_data.argtypes = [vp, vp, vp]
     L.pnp_plan_set_compensated.argtypes = [vp, i32]
     L.pnp_cnn_trainer_apply_update.argtypes = [vp]
+    L.pnp_den_cnn_set_strip_rows.argtypes = [vp, i32]
+    L.pnp_den_cnn_autotune.argtypes = [vp, vp, i32, i32, C.POINTER(i32), C.POINTER(dbl)]
     L.pnp_plan_destroy.argtypes = [vp]
     L.pnp_plan_destroy.restype = None
     L.pnp_plan_get_info.argtypes = [vp, C.POINTER(_Info)]
@@ -139,7 +142,8 @@ def lib(path: str = LIB_PATH) -> C.CDLL:
                  "pnp_cnn_trainer_read", "pnp_cnn_trainer_set_lr", "pnp_plan_autotune", "pnp_cnn_jacobian_norm",
                  "pnp_cnn_train_step_fne", "pnp_den_create_sara", "pnp_den_sara_reweight",
                  "pnp_sara_transform", "pnp_plan_create_desc", "pnp_plan_scale_data",
-                 "pnp_plan_set_compensated", "pnp_cnn_trainer_apply_update"):
+                 "pnp_plan_set_compensated", "pnp_cnn_trainer_apply_update", "pnp_den_cnn_set_strip_rows",
+                 "pnp_den_cnn_autotune"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -561,6 +565,18 @@ class CnnDenoiser(_Denoiser):
                                         None if fr is None else fr.ctypes.data, 0 if fr is None else fr.size,
                                         None if fc is None else fc.ctypes.data, 0 if fc is None else fc.size,
                                         int(halo), int(n), _stream_handle(stream)))
+        self.n = int(n)
+
+    def set_strip_rows(self, rows: int):
+        """Output rows per convolution work strip (a performance setting; results are unchanged)."""
+        _check(lib().pnp_den_cnn_set_strip_rows(self._h, int(rows)))
+
+    def autotune(self, z, reps: int = 3) -> dict:
+        """Time the denoise of the device image z for each strip height and keep the fastest."""
+        _cuda_f32(z, (self.n, self.n), "z")
+        rows, ms = C.c_int(), C.c_double()
+        _check(lib().pnp_den_cnn_autotune(self._h, _ptr(z), self.n, int(reps), C.byref(rows), C.byref(ms)))
+        return {"strip_rows": rows.value, "denoise_ms": ms.value}
 
 
 def haar_denoise_noalloc(z, t: float, x_prev=None, out=None, norms=None, stream=None):

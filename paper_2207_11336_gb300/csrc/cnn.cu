@@ -90,6 +90,8 @@ struct CnnState {
   int n_strips = 0;
   int4* d_lstrips = nullptr;             // last layer's work list: strips of the facet cores (last_strips)
   int n_lstrips = 0;
+  int strip_rows = STRIP_ROWS;           // target output rows per strip of both work lists (autotuned)
+  size_t cap_strips = 0, cap_lstrips = 0;  // allocated entries of d_strips, d_lstrips
   __nv_bfloat16* d_wlast = nullptr;      // last layer's B operand (last_wpack_index), output channel 0 of 16
   uint32_t* d_wfrag = nullptr;           // last layer's weights as mma.sync B fragments [4 k][2 n][32 lanes][2]
   __nv_bfloat16* d_canvas[2] = {nullptr, nullptr};
@@ -792,6 +794,47 @@ int sms_of_device() {
 
 }  // namespace
 
+// The two convolution work lists for strips of about `rows` output rows: the hidden layers' strips of
+// the extended facets, and the last layer's strips of the facet cores.  Device arrays grow as needed.
+static int build_strips(CnnState* S, int rows) {
+  const std::vector<int4> strips = conv_strips(S->F, S->Hf.data(), S->Wf.data(), rows);
+  std::vector<int4> lstrips;
+  for (int f = 0; f < S->F; ++f) {
+    const int cr0 = S->fr0[f] - S->R0[f], cr1 = S->fr1[f] - S->R0[f];
+    const int cc0 = S->fc0[f] - S->C0[f], cc1 = S->fc1[f] - S->C0[f];
+    const int k = std::max(1, (cr1 - cr0 + rows - 1) / rows);
+    for (int x0 = cc0; x0 < cc1; x0 += TILE_PX)
+      for (int i = 0; i < k; ++i) {
+        const int ya = cr0 + (int)((int64_t)(cr1 - cr0) * i / k), yb = cr0 + (int)((int64_t)(cr1 - cr0) * (i + 1) / k);
+        if (yb > ya) lstrips.push_back(make_int4(f, x0, (ya << 16) | (yb - ya), (S->Hf[f] << 16) | S->Wf[f]));
+      }
+  }
+  auto fit = [](int4** p, size_t* cap, size_t need) -> int {
+    need = std::max<size_t>(1, need);
+    if (*p && *cap >= need) return PNP_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    if (cudaMalloc(reinterpret_cast<void**>(p), need * sizeof(int4)) != cudaSuccess) {
+      cudaGetLastError();
+      *p = nullptr;
+      return fail(PNP_ERR_OOM, "CNN work list allocation failed");
+    }
+    *cap = need;
+    return PNP_OK;
+  };
+  if (int rc = fit(&S->d_strips, &S->cap_strips, strips.size())) return rc;
+  if (int rc = fit(&S->d_lstrips, &S->cap_lstrips, lstrips.size())) return rc;
+  if (!strips.empty())
+    PNP_CUDA(cudaMemcpy(S->d_strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!lstrips.empty())
+    PNP_CUDA(cudaMemcpy(S->d_lstrips, lstrips.data(), lstrips.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  S->n_strips = (int)strips.size();
+  S->n_lstrips = (int)lstrips.size();
+  S->strip_rows = rows;
+  return PNP_OK;
+}
+
 int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int32_t* fc, int nfc, int halo,
                int n) {
   CnnState* S = new CnnState();
@@ -838,22 +881,6 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
     facets[f] = make_int4(S->R0[f], S->C0[f], S->Hf[f], S->Wf[f]);
     cores[f] = make_int4(S->fr0[f], S->fr1[f], S->fc0[f], S->fc1[f]);
   }
-  const std::vector<int4> strips = conv_strips(S->F, S->Hf.data(), S->Wf.data());
-  S->n_strips = (int)strips.size();
-  // the last layer computes the facet cores only: strips of ~STRIP_ROWS core rows x 128 core columns
-  std::vector<int4> lstrips;
-  for (int f = 0; f < S->F; ++f) {
-    const int cr0 = S->fr0[f] - S->R0[f], cr1 = S->fr1[f] - S->R0[f];
-    const int cc0 = S->fc0[f] - S->C0[f], cc1 = S->fc1[f] - S->C0[f];
-    const int k = std::max(1, (cr1 - cr0 + STRIP_ROWS - 1) / STRIP_ROWS);
-    for (int x0 = cc0; x0 < cc1; x0 += TILE_PX)
-      for (int i = 0; i < k; ++i) {
-        const int ya = cr0 + (int)((int64_t)(cr1 - cr0) * i / k), yb = cr0 + (int)((int64_t)(cr1 - cr0) * (i + 1) / k);
-        if (yb > ya) lstrips.push_back(make_int4(f, x0, (ya << 16) | (yb - ya), (S->Hf[f] << 16) | S->Wf[f]));
-      }
-  }
-  S->n_lstrips = (int)lstrips.size();
-
   // weights: layer shapes 64x1, 6 x 64x64, 1x64, each W[co][ci][3][3] then b[co]
   std::vector<float> w1(CH * 9), w8(9 * CH), bias(8 * CH, 0.f);
   std::vector<uint16_t> wmid((size_t)6 * 9 * CH * CH);
@@ -913,8 +940,6 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   }
   if (int rc = al((void**)&S->d_facets, S->F * sizeof(int4))) return rc;
   if (int rc = al((void**)&S->d_cores, S->F * sizeof(int4))) return rc;
-  if (int rc = al((void**)&S->d_strips, std::max<size_t>(1, strips.size()) * sizeof(int4))) return rc;
-  if (int rc = al((void**)&S->d_lstrips, std::max<size_t>(1, lstrips.size()) * sizeof(int4))) return rc;
   if (int rc = al((void**)&S->d_wlast, wlast.size() * 2)) return rc;
   if (int rc = al((void**)&S->d_wfrag, wfrag.size() * 4)) return rc;
   if (int rc = al((void**)&S->d_w1, w1.size() * 4)) return rc;
@@ -924,10 +949,7 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   if (int rc = al((void**)&S->d_status, 4 * sizeof(int))) return rc;
   PNP_CUDA(cudaMemcpy(S->d_facets, facets.data(), S->F * sizeof(int4), cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_cores, cores.data(), S->F * sizeof(int4), cudaMemcpyHostToDevice));
-  if (!strips.empty())
-    PNP_CUDA(cudaMemcpy(S->d_strips, strips.data(), strips.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  if (!lstrips.empty())
-    PNP_CUDA(cudaMemcpy(S->d_lstrips, lstrips.data(), lstrips.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  if (int rc = build_strips(S, S->strip_rows)) return rc;
   PNP_CUDA(cudaMemcpy(S->d_wlast, wlast.data(), wlast.size() * 2, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_wfrag, wfrag.data(), wfrag.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_w1, w1.data(), w1.size() * 4, cudaMemcpyHostToDevice));
@@ -1020,10 +1042,10 @@ int conv64_launch(cudaStream_t s, const void* in_map, __nv_bfloat16* out, const 
   return PNP_OK;
 }
 
-std::vector<int4> conv_strips(int F, const int* Hf, const int* Wf) {
+std::vector<int4> conv_strips(int F, const int* Hf, const int* Wf, int rows) {
   std::vector<int4> out;
   for (int f = 0; f < F; ++f) {
-    const int k = std::max(1, (Hf[f] + STRIP_ROWS - 1) / STRIP_ROWS);  // strips per column segment
+    const int k = std::max(1, (Hf[f] + rows - 1) / rows);  // strips per column segment
     for (int x0 = 0; x0 < Wf[f]; x0 += TILE_PX)
       for (int i = 0; i < k; ++i) {
         const int ya = (int)((int64_t)Hf[f] * i / k), yb = (int)((int64_t)Hf[f] * (i + 1) / k);
@@ -1043,6 +1065,19 @@ int cnn_first_launch(cudaStream_t s, const float* z, int n, int64_t zplane, cons
 
 int canvas_map_create(void* map_out, const __nv_bfloat16* canvas, int F, int Hc, int Wc) {
   return make_canvas_maps(static_cast<CUtensorMap*>(map_out), canvas, F, Hc, Wc);
+}
+
+int cnn_set_strip_rows(pnp_den* d, int rows) {
+  CnnState* S = static_cast<CnnState*>(d->impl);
+  if (!S) return fail(PNP_ERR_INVALID_ARG, "CNN denoiser not initialised");
+  if (rows < 4 || rows > 1024) return fail(PNP_ERR_INVALID_ARG, "strip rows must lie in [4, 1024]");
+  PNP_CUDA(cudaDeviceSynchronize());  // launches in flight (on any stream) read the current lists
+  return build_strips(S, rows);
+}
+
+int cnn_strip_rows(pnp_den* d) {
+  const CnnState* S = static_cast<const CnnState*>(d->impl);
+  return S ? S->strip_rows : 0;
 }
 
 int cnn_status(pnp_den* d, int* flags) {

@@ -231,7 +231,10 @@ __host__ __device__ __forceinline__ size_t conv_wpack_index(int dy, int dx, int 
 constexpr int STRIP_ROWS = 32;  // target output rows per convolution work unit
 // Work list of conv64_tc: per facet, 128-column segments split into strips of about STRIP_ROWS
 // output rows; each entry is (facet, x0, ya << 16 | rows, Hf << 16 | Wf).
-std::vector<int4> conv_strips(int F, const int* Hf, const int* Wf);
+std::vector<int4> conv_strips(int F, const int* Hf, const int* Wf, int rows = STRIP_ROWS);
+// the denoiser's convolution work lists rebuilt for strips of about `rows` output rows (4..1024)
+int cnn_set_strip_rows(pnp_den* d, int rows);
+int cnn_strip_rows(pnp_den* d);
 // the convolution reads its input through the TMA descriptor in_map (canvas_map_create)
 int conv64_launch(cudaStream_t s, const void* in_map, __nv_bfloat16* out, const __nv_bfloat16* w_packed,
                   const float* bias, const int4* strips, int n_strips, int Hc, int Wc, int mode,

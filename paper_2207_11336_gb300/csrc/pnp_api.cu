@@ -593,6 +593,59 @@ int pnp_den_create_cnn(pnp_den** den, const float* weights_host, const int32_t* 
   return PNP_OK;
 }
 
+int pnp_den_cnn_set_strip_rows(pnp_den* den, int rows) {
+  if (!den || den->kind != PNP_DEN_CNN) return fail(PNP_ERR_INVALID_ARG, "not a CNN denoiser");
+  if (int rc = cnn_set_strip_rows(den, rows)) return rc;
+  den->serial = ++g_den_serial;  // graphs captured with this denoiser hold the old launch sizes
+  return PNP_OK;
+}
+
+int pnp_den_cnn_autotune(pnp_den* den, const float* z, int n, int reps, int* rows_out, double* ms_out) {
+  if (!den || den->kind != PNP_DEN_CNN || !z) return fail(PNP_ERR_INVALID_ARG, "not a CNN denoiser, or NULL input");
+  if (reps < 1 || reps > 100) return fail(PNP_ERR_INVALID_ARG, "reps must lie in [1, 100]");
+  static const int kRows[] = {16, 24, 32, 48, 64, 96};
+  float* out = nullptr;
+  if (cudaMalloc(&out, (size_t)n * n * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(PNP_ERR_OOM, "autotune scratch image");
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = PNP_OK, best = cnn_strip_rows(den);
+  double best_ms = -1.0;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    rc = fail(PNP_ERR_CUDA, "event creation failed");
+  }
+  for (int rows : kRows) {
+    if (rc) break;
+    if ((rc = cnn_set_strip_rows(den, rows))) break;
+    if ((rc = cnn_denoise(den, den->stream, z, out, n, nullptr, nullptr))) break;  // warm
+    if (cudaEventRecord(e0, den->stream) != cudaSuccess) { rc = fail(PNP_ERR_CUDA, "event record"); break; }
+    for (int r = 0; r < reps && !rc; ++r) rc = cnn_denoise(den, den->stream, z, out, n, nullptr, nullptr);
+    if (rc) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, den->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = fail(PNP_ERR_CUDA, "event timing failed");
+      break;
+    }
+    const double per = ms / reps;
+    if (best_ms < 0 || per < best_ms) {
+      best_ms = per;
+      best = rows;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  if (!rc) rc = cnn_set_strip_rows(den, best);
+  den->serial = ++g_den_serial;
+  if (rc) return rc;
+  if (rows_out) *rows_out = best;
+  if (ms_out) *ms_out = best_ms;
+  return PNP_OK;
+}
+
 int pnp_den_create_sara(pnp_den** den, int n, int levels, double gamma_lambda, double rho, int prox_iters,
                         void* stream) {
   if (!den) return fail(PNP_ERR_INVALID_ARG, "NULL denoiser pointer");

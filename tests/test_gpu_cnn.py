@@ -136,3 +136,30 @@ def test_cnn_error_against_the_unrounded_fp64_network():
           f"N(z) rel L2 {e_n:.2e}")
     assert e_d <= 1e-5
     assert e_n <= 0.5
+
+
+def test_strip_height_and_its_autotuner_leave_the_result_unchanged():
+    """The convolution work lists' strip height is a performance setting: every output pixel's MMA
+    chain is the same for any strip height, so the denoised image is identical bit for bit, and the
+    autotuner keeps one of its candidates and the faceted parity."""
+    n = 200
+    params = _params(7)
+    z = _sky(n, 8)
+    fr, fc = [60, 75, 65], [90, 110]
+    den = pnp.CnnDenoiser(params, n, facet_rows=fr, facet_cols=fc, halo=32)
+    zd = to_dev_f32(z)
+    base = to_host(den.denoise(zd))
+    for rows in (4, 16, 48, 1024):
+        den.set_strip_rows(rows)
+        assert np.array_equal(to_host(den.denoise(zd)), base), rows
+    tune = den.autotune(zd, reps=1)
+    assert tune["strip_rows"] in (16, 24, 32, 48, 64, 96) and tune["denoise_ms"] > 0
+    assert np.array_equal(to_host(den.denoise(zd)), base)
+    assert den.device_status() == 0
+    zf = z.astype(np.float32).astype(np.float64)
+    assert rel_l2(base, ocnn.denoise_faceted(params, zf, fr, fc, 32, bf16=True)) <= BF16_U
+    with pytest.raises(pnp.PnPError):
+        den.set_strip_rows(3)
+    h = pnp.HaarDenoiser(0.1)   # a Haar denoiser has no work lists
+    with pytest.raises(pnp.PnPError):
+        pnp._check(pnp.lib().pnp_den_cnn_set_strip_rows(h._h, 32))
