@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="C3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-bf16-g", dest="bf16_g", action="store_false",
                     help="skip timing the plain loop with BF16 weights in G")
     ap.add_argument("--wstacks", type=int, default=8,
@@ -635,20 +635,45 @@ def run_gpu(args):
                     "unit": "TFLOP/s", "frac": flop / (d_ms * 1e-3) / 1e12 / bf16_peak, "traffic": None,
                     "flop_per_launch": flop, "ms_per_launch": d_ms}
 
-    # ---- end to end through the public API with host buffers: y in, the image out, every step
+    # ---- end to end through the public API with host buffers: every step copies its y in from pinned
+    # host memory and its image out to pinned host memory.  The copies run on a second stream, double
+    # buffered: step i + 1's y is uploaded while step i computes, and step i's image (a device snapshot
+    # taken at the end of the step) is read back while step i + 1 computes; the timed region ends when
+    # the last image has reached the host.
     y_host = y.cpu().pin_memory()
     x_host = torch.empty((n, n), dtype=torch.float32).pin_memory()
-    y_dev = torch.empty_like(y)
+    y_dev = [torch.empty_like(y), torch.empty_like(y)]
+    x_snap = torch.empty_like(x)
+    copy_stream = torch.cuda.Stream()
+    up = [torch.cuda.Event(), torch.cuda.Event()]
+    snap_ready, snap_free = torch.cuda.Event(), torch.cuda.Event()
     torch.cuda.synchronize()
     e2e_steps = max(1, args.e2e_steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_start = time.perf_counter()
     e0.record(stream)
-    for _ in range(e2e_steps):
-        y_dev.copy_(y_host, non_blocking=True)
-        plan.fb_run(den, y_dev, x0=x, gamma=gamma, L=L, max_iter=1, check_every=1, use_graph=False,
+    copy_stream.wait_event(e0)
+    with torch.cuda.stream(copy_stream):
+        y_dev[0].copy_(y_host, non_blocking=True)
+        up[0].record(copy_stream)
+        snap_free.record(copy_stream)
+    for i in range(e2e_steps):
+        if i + 1 < e2e_steps:
+            copy_stream.wait_stream(stream)   # step i - 1, the last reader of this buffer, is complete
+            with torch.cuda.stream(copy_stream):
+                y_dev[(i + 1) % 2].copy_(y_host, non_blocking=True)
+                up[(i + 1) % 2].record(copy_stream)
+        stream.wait_event(up[i % 2])
+        plan.fb_run(den, y_dev[i % 2], x0=x, gamma=gamma, L=L, max_iter=1, check_every=1, use_graph=False,
                     inplace=True, alpha=alpha)   # reads the FP64 norms back
-        x_host.copy_(x, non_blocking=True)
+        stream.wait_event(snap_free)             # the previous image has left x_snap
+        x_snap.copy_(x, non_blocking=True)
+        snap_ready.record(stream)
+        copy_stream.wait_event(snap_ready)
+        with torch.cuda.stream(copy_stream):
+            x_host.copy_(x_snap, non_blocking=True)
+            snap_free.record(copy_stream)
+    stream.wait_stream(copy_stream)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_s = max(e0.elapsed_time(e1) / 1e3, time.perf_counter() - t_start)

@@ -541,7 +541,9 @@ __global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
   __shared__ float zt[FIRST_ROWS + 2][FIRST_PX + 2];
   const int f = blockIdx.z, ya = blockIdx.y * FIRST_ROWS, x0 = blockIdx.x * FIRST_PX;
   const int4 fc = A.facets[f];  // R0, C0, Hf, Wf
-  if (ya >= fc.z || x0 >= A.Wc) return;
+  // canvas cells outside the facet are zero from the canvas's allocation and every layer writes zeros
+  // there, so only the facet's own cells are written here
+  if (ya >= fc.z || x0 >= fc.w) return;
   const float* zf = A.z + (size_t)f * A.zplane;
   for (int i = threadIdx.x; i < (FIRST_ROWS + 2) * (FIRST_PX + 2); i += blockDim.x) {
     const int r = i / (FIRST_PX + 2), c = i % (FIRST_PX + 2);
@@ -558,8 +560,7 @@ __global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
   }
   __syncthreads();
   const int x = x0 + lane;
-  if (x >= A.Wc) return;
-  const bool live = x < fc.w;
+  if (x >= fc.w) return;
   const int yb = min(ya + FIRST_ROWS, fc.z);
   for (int y = ya; y < yb; ++y) {
     const int r = y - ya;
@@ -572,7 +573,7 @@ __global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
       float2 a = b[q];
 #pragma unroll
       for (int t = 0; t < 9; ++t) a = ffma2(w[q][t], make_float2(zin[t], zin[t]), a);
-      __nv_bfloat162 h = __floats2bfloat162_rn(live ? fmaxf(a.x, 0.f) : 0.f, live ? fmaxf(a.y, 0.f) : 0.f);
+      __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(a.x, 0.f), fmaxf(a.y, 0.f));
       pk[q] = *reinterpret_cast<uint32_t*>(&h);
     }
     *reinterpret_cast<uint4*>(A.out + canvas_index(f, y, x, cb * 8, A.Hc, A.Wc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
