@@ -519,12 +519,11 @@ def run_gpu(args):
             trace_u, it, rw = [], 0, args.usara_reweight_every
             while it < args.usara_iters:
                 k = min(rw, args.usara_iters - it)
+                # the library re-forms the weights after every rw iterations (Eq. B1's surrogates)
                 plan.fb_run(sara, y, x0=xu, gamma=gamma, L=L, max_iter=k, check_every=k, use_graph=True,
-                            inplace=True)
+                            inplace=True, reweight_every=rw)
                 it += k
                 trace_u.append((it, _snr_db(x_true, xu)))
-                if it < args.usara_iters:
-                    sara.reweight(xu)
             comparison["usara"] = {
                 "prox_iters": args.usara_prox_iters, "reweight_every": rw,
                 "iter_per_s": ws * steps / (ms_u / 1e3), "ms_per_iter": ms_u / steps,

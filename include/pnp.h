@@ -86,6 +86,14 @@ typedef struct pnp_params {
                         the learned loop's fallback); 0: fail                 */
   double fallback_t; /* Haar threshold of the fallback, in the rescaled units
                         of alpha (>= 0)                                       */
+  int reweight_every; /* uSARA (SARA denoiser only, App. B Eq. B1): > 0 re-forms
+                        the weights w = rho / (rho + |Psi^T x|) from the current
+                        iterate (the loop's units) after every this many
+                        iterations of the run, its last one included (so calls
+                        of a multiple of it continue one schedule): the run is
+                        a sequence of weighted-l1 surrogates of the log-sum
+                        prior; 0 keeps the weights.  Other denoisers: must be
+                        0 (PNP_ERR_INVALID_ARG)                               */
 } pnp_params;
 
 enum { PNP_POSITIVITY_ON = 0, PNP_POSITIVITY_OFF = 1 };

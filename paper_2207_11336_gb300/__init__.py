@@ -49,7 +49,7 @@ class _Params(C.Structure):
     _fields_ = [("gamma", C.c_double), ("L", C.c_double), ("max_iter", C.c_int), ("tol", C.c_double),
                 ("check_every", C.c_int), ("use_graph", C.c_int), ("diverge_factor", C.c_double),
                 ("alpha", C.c_double), ("positivity", C.c_int), ("fallback", C.c_int),
-                ("fallback_t", C.c_double)]
+                ("fallback_t", C.c_double), ("reweight_every", C.c_int)]
 
 
 class _Stats(C.Structure):
@@ -344,14 +344,15 @@ class Plan:
 
     def fb_run(self, den, y, x0=None, gamma=0.0, L=0.0, max_iter=200, tol=0.0, check_every=10,
                use_graph=True, diverge_factor=0.0, inplace=False, alpha=1.0, positivity=True,
-               fallback_t=None):
+               fallback_t=None, reweight_every=0):
         """Run Eq. fb with denoiser ``den`` from x0 (zeros if None); returns (x, FBStats).
 
         ``alpha`` rescales the problem as in App. C (Eq. invpb2): the loop iterates on y / alpha
         from x0 / alpha and returns alpha x.  ``positivity`` keeps the final max(0, .) of the
         denoiser.  ``fallback_t`` (learned denoiser only): on divergence, continue from the last
         checked finite iterate with the Haar denoiser at this threshold (rescaled units).
-        With ``inplace`` the iterate is updated in x0 itself."""
+        ``reweight_every`` (SARA denoiser only): re-form the uSARA weights from the iterate every this
+        many iterations.  With ``inplace`` the iterate is updated in x0 itself."""
         import torch
         _cuda_c64(y, self.M, "y")
         if x0 is None:
@@ -362,7 +363,8 @@ class Plan:
         prm = _Params(float(gamma), float(L), int(max_iter), float(tol), int(check_every),
                       1 if use_graph else 0, float(diverge_factor), float(alpha),
                       PNP_POSITIVITY_ON if positivity else PNP_POSITIVITY_OFF,
-                      0 if fallback_t is None else 1, 0.0 if fallback_t is None else float(fallback_t))
+                      0 if fallback_t is None else 1, 0.0 if fallback_t is None else float(fallback_t),
+                      int(reweight_every))
         st = _Stats()
         _check(lib().pnp_fb_run(self._h, den._h, _ptr(y), C.byref(prm), _ptr(x), C.byref(st)))
         return x, FBStats(st.iters, st.L, st.gamma, st.rel_change, st.x_norm, st.fallback_iter)

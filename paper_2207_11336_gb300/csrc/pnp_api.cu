@@ -714,6 +714,9 @@ int pnp_fb_run(pnp_plan* p, pnp_den* d, const float* y, const pnp_params* prm, f
   if (prm->fallback != 0 && prm->fallback != 1) return fail(PNP_ERR_INVALID_ARG, "fallback must be 0 or 1");
   if (prm->fallback && (!(prm->fallback_t >= 0) || !std::isfinite(prm->fallback_t)))
     return fail(PNP_ERR_INVALID_ARG, "fallback_t must be finite and >= 0");
+  if (prm->reweight_every < 0 || (prm->reweight_every > 0 && d->kind != PNP_DEN_SARA))
+    return fail(PNP_ERR_INVALID_ARG, "reweight_every must be 0, or > 0 with a SARA denoiser");
+  const int rw = prm->reweight_every;
   const double alpha = prm->alpha > 0 ? prm->alpha : 1.0;
   const bool pos = prm->positivity == PNP_POSITIVITY_ON;
   const bool fallback = prm->fallback == 1 && d->kind == PNP_DEN_CNN;
@@ -751,7 +754,8 @@ int pnp_fb_run(pnp_plan* p, pnp_den* d, const float* y, const pnp_params* prm, f
   while (k < prm->max_iter && rc == PNP_OK) {
     const int bit = 1 << den->kind;
     GraphRunner gr(p, den, buf, gamma, pos);
-    const int chunk = std::min(check, prm->max_iter - k);
+    int chunk = std::min(check, prm->max_iter - k);
+    if (rw > 0) chunk = std::min(chunk, rw - k % rw);  // a chunk ends at every reweighting
     for (int done = 0; done < chunk && rc == PNP_OK;) {
       const int left = chunk - done;
       if (graph && c == 0 && left >= 2 && (p->primed & bit)) {
@@ -800,6 +804,15 @@ int pnp_fb_run(pnp_plan* p, pnp_den* d, const float* y, const pnp_params* prm, f
       k_keep = k;
     }
     if (prm->tol > 0 && rel < prm->tol) break;
+    // uSARA (App. B): the next weighted-l1 surrogate, majorising the log-sum prior at the current iterate
+    if (rw > 0 && k % rw == 0) {  // also at the end of the run, so that consecutive calls continue it
+      if ((rc = sara_reweight(d, buf[c]))) break;  // on the denoiser's stream: the iterate is ready (read_acc)
+      if (d->stream != p->stream && cudaStreamSynchronize(d->stream) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(PNP_ERR_CUDA, "reweighting failed");
+        break;
+      }
+    }
   }
   if (c == 1) {
     cudaError_t e = cudaMemcpyAsync(x, buf[1], (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice, p->stream);

@@ -63,3 +63,31 @@ def test_usara_fb_loop_matches_oracle():
     x, st = plan.fb_run(den, to_dev_c64(y), gamma=gamma, L=L, max_iter=iters, check_every=4)
     assert st.iters == iters
     assert rel_l2(to_host(x), x_ref) <= 1e-4
+
+
+def test_reweighted_usara_inside_pnp_fb_run_matches_oracle():
+    """uSARA as App. B runs it: three weighted-l1 surrogates of 4 FB iterations each, the weights
+    re-formed from the iterate by pnp_fb_run itself (reweight_every), against the oracle's loop."""
+    n, K, M, fb_iters, prox_iters = 64, 128, 20000, 4, 10
+    prob = synth.make_problem("C0", M=M, n=n, K=K)
+    ora = onu.Operator(n, K, prob["omega"])
+    y0 = ora.forward(prob["x_true"])
+    tau = synth.noise_std_for_isnr(np.linalg.norm(y0), M, prob["isnr_db"])
+    y = y0 + tau * prob["noise"]
+    L, _, _ = ofb.power_iteration(ora, synth.rng_for("power").standard_normal((n, n)), 1000, 1e-10)
+    gamma = ofb.step_size(L)
+    gl = ofb.soft_threshold_from_noise(tau, L)
+    x_ref = osa.usara(ora, y, gamma, gl, gl, 2, fb_iters, prox_iters=prox_iters, psi=osa.Sara(levels=4),
+                      prox_tol=0.0)
+    plan = pnp.Plan(n, K, prob["omega"])
+    den = pnp.SaraDenoiser(n, gl, gl, prox_iters, levels=4)
+    x, st = plan.fb_run(den, to_dev_c64(y), gamma=gamma, L=L, max_iter=3 * fb_iters, check_every=10,
+                        reweight_every=fb_iters)
+    assert st.iters == 3 * fb_iters
+    assert rel_l2(to_host(x), x_ref) <= 1e-4
+    # the same run without reweighting differs (the weights matter), and a Haar denoiser refuses it
+    den2 = pnp.SaraDenoiser(n, gl, gl, prox_iters, levels=4)
+    x_plain, _ = plan.fb_run(den2, to_dev_c64(y), gamma=gamma, L=L, max_iter=3 * fb_iters, check_every=10)
+    assert rel_l2(to_host(x_plain), x_ref) > 1e-4
+    with pytest.raises(pnp.PnPError):
+        plan.fb_run(pnp.HaarDenoiser(0.1), to_dev_c64(y), L=L, max_iter=2, reweight_every=1)
