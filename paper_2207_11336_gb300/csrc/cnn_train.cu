@@ -13,9 +13,11 @@
 //             tensor cores (conv64 forward mode) -> act2..act7; layer 8 and the
 //             l1 loss and its gradient g = dL/dN (CUDA cores);
 //   backward  dpre7 = (W8^T g) * [act7 > 0];  for k = 6..1: dW_{k+1} from
-//             (dpre_{k+1}, act_k) and dpre_k = conv(dpre_{k+1}, flipped W_{k+1}^T)
+//             (dpre_{k+1}, act_k) on the tensor cores (mma.sync, the pixels as the
+//             contraction) and dpre_k = conv(dpre_{k+1}, flipped W_{k+1}^T)
 //             * [act_k > 0] on the tensor cores (conv64 backward-data mode);
-//             dW1 from (dpre_1, z); bias gradients are pixel sums of dpre;
+//             dW1 from (dpre_1, z) and dW8 on CUDA cores (one channel); bias
+//             gradients are pixel sums of dpre;
 //   update    Adam on the FP32 master weights, then re-pack the BF16 operands.
 #include <algorithm>
 #include <cmath>
@@ -190,56 +192,150 @@ __global__ void __launch_bounds__(576) wgrad_onechannel(Dims d, int mode, const 
 }
 
 // dW[co][ci][t] += sum_p dpre[p][co] act[p + off_t][ci]; db[co] += sum_p dpre[p][co] (t == 4 blocks)
-// block: one tap, WG_CHUNK pixels; thread owns a 4 (co) x 4 (ci) tile of the 64 x 64 gradient.
-__global__ void __launch_bounds__(256) wgrad64(Dims d, const __nv_bfloat16* __restrict__ dpre,
-                                               const __nv_bfloat16* __restrict__ act, float* __restrict__ dW,
-                                               float* __restrict__ db) {
-  constexpr int PB = 32;  // pixels staged per round
-  __shared__ float sd[PB][CH], sa[PB][CH];
-  const int t = blockIdx.y, dy = t / 3 - 1, dx = t % 3 - 1;
-  const int co0 = (threadIdx.x / 16) * 4, ci0 = (threadIdx.x % 16) * 4;
-  const int64_t total = (int64_t)d.B * d.s * d.s;
-  const int64_t p0 = (int64_t)blockIdx.x * WG_CHUNK, p1 = min(total, p0 + WG_CHUNK);
-  float acc[4][4] = {};
-  float bsum = 0.f;
-  for (int64_t pb = p0; pb < p1; pb += PB) {
-    // stage PB pixels: dpre at p, act at p + off_t (zero outside the image)
-    for (int e = threadIdx.x; e < PB * CH / 2; e += blockDim.x) {
-      const int q = e / (CH / 2), c2 = e % (CH / 2);
-      const int64_t p = pb + q;
-      float2 dv = make_float2(0.f, 0.f), av = make_float2(0.f, 0.f);
-      if (p < p1) {
-        const int b = (int)(p / ((int64_t)d.s * d.s)), y = (int)((p / d.s) % d.s), x = (int)(p % d.s);
-        dv = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(dpre + cidx(d, b, y, x, 2 * c2)));
-        const int yy = y + dy, xx = x + dx;
-        if (yy >= 0 && yy < d.s && xx >= 0 && xx < d.s)
-          av = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(act + cidx(d, b, yy, xx, 2 * c2)));
-      }
-      sd[q][2 * c2] = dv.x;
-      sd[q][2 * c2 + 1] = dv.y;
-      sa[q][2 * c2] = av.x;
-      sa[q][2 * c2 + 1] = av.y;
+// Weight and bias gradients of a 64 -> 64 layer on the tensor cores (mma.sync m16n8k16, BF16 in, FP32
+// accumulate): dW[co][ci][t] = sum_p dpre[p][co] act[p + off_t][ci] is, per tap t, a 64 x 64 GEMM whose
+// contraction runs over the pixels.  A CTA walks image rows (b, y) in 64-pixel segments; per segment it
+// copies dpre (64 px x 64 ch) and the three activation rows y - 1, y, y + 1 (66 px with the dx halo,
+// zero outside the image) into shared memory as [pixel][channel] rows padded to 72 channels (conflict-free
+// ldmatrix) with cp.async, double buffered: the next segment's copies are in flight while the current one
+// is contracted.  Warp w owns tap w / 2 and output channels 32 (w % 2) .. + 31: 2 x 8 tiles of 16 x 8
+// accumulators.  Both operands are stored pixel-major, so the fragments load with ldmatrix.trans.  Bias
+// gradients (sums of dpre over the pixels) come from the staged dpre.  One atomic per gradient entry per
+// CTA at the end.
+constexpr int WGT_PX = 64;                    // pixels per segment (4 K steps of 16)
+constexpr int WGT_LD = 72;                    // staged row length (channels + 8 of padding)
+constexpr int WGT_WARPS = 18;                 // 9 taps x 2 output-channel halves
+constexpr int WGT_THREADS = WGT_WARPS * 32;
+constexpr int WGT_CHUNKS = 8 * (WGT_PX + 3 * (WGT_PX + 2));  // 16-byte chunks per segment: 2096
+constexpr int WGT_BUF = (WGT_PX + 3 * (WGT_PX + 2)) * WGT_LD;  // staged elements per segment
+constexpr int WGT_SMEM = 2 * WGT_BUF * 2;                       // bytes, two buffers
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t (&r)[4], const void* p) {
+  const uint32_t a = static_cast<uint32_t>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+// 16-byte asynchronous copy global -> shared; nbytes = 0 fills the destination with zeros
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int nbytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(static_cast<uint32_t>(
+                   __cvta_generic_to_shared(dst))),
+               "l"(src), "r"(nbytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// copies of segment sg (image row b * s + y, pixels x0 ..) into the staging buffer buf: chunk e is 16
+// bytes of dpre (e < 512, into [px][WGT_LD]) or of activation row y + r - 1 (into [3][66 px][WGT_LD])
+__device__ __forceinline__ void wgt_issue(const Dims& d, const __nv_bfloat16* __restrict__ dpre,
+                                          const __nv_bfloat16* __restrict__ act, int64_t sg, int segs_per_row,
+                                          __nv_bfloat16* buf) {
+  const int row = (int)(sg / segs_per_row), x0 = (int)(sg % segs_per_row) * WGT_PX;
+  const int b = row / d.s, y = row % d.s;
+  for (int e = threadIdx.x; e < WGT_CHUNKS; e += WGT_THREADS) {
+    int yy = y, x, kb, slot;
+    const __nv_bfloat16* src = dpre;
+    if (e < 8 * WGT_PX) {
+      x = x0 + (e >> 3);
+      kb = e & 7;
+      slot = (e >> 3) * WGT_LD + 8 * kb;
+    } else {
+      const int f = e - 8 * WGT_PX, r = f / (8 * (WGT_PX + 2)), q = f % (8 * (WGT_PX + 2));
+      yy = y + r - 1;
+      x = x0 - 1 + (q >> 3);
+      kb = q & 7;
+      slot = WGT_PX * WGT_LD + (r * (WGT_PX + 2) + (q >> 3)) * WGT_LD + 8 * kb;
+      src = act;
     }
-    __syncthreads();
-#pragma unroll 4
-    for (int q = 0; q < PB; ++q) {
-      const float4 dv = *reinterpret_cast<const float4*>(&sd[q][co0]);
-      const float4 av = *reinterpret_cast<const float4*>(&sa[q][ci0]);
-      const float dd[4] = {dv.x, dv.y, dv.z, dv.w}, aa[4] = {av.x, av.y, av.z, av.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(dd[i], aa[j], acc[i][j]);
-    }
-    if (t == 4 && threadIdx.x < CH)
-      for (int q = 0; q < PB; ++q) bsum += sd[q][threadIdx.x];
-    __syncthreads();
+    const bool in = yy >= 0 && yy < d.s && x >= 0 && x < d.s;
+    cp_async16(buf + slot, in ? src + cidx(d, b, yy, x, 8 * kb) : src, in ? 16 : 0);
   }
+}
+
+__global__ void __launch_bounds__(WGT_THREADS, 1) wgrad64_tc(Dims d, const __nv_bfloat16* __restrict__ dpre,
+                                                             const __nv_bfloat16* __restrict__ act,
+                                                             float* __restrict__ dW, float* __restrict__ db) {
+  extern __shared__ __align__(16) __nv_bfloat16 wsm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = warp >> 1, dy = t / 3, dx = t % 3, co0 = 32 * (warp & 1);
+  const int segs_per_row = (d.s + WGT_PX - 1) / WGT_PX;
+  const int64_t nseg = (int64_t)d.B * d.s * segs_per_row;
+  float acc[2][8][4] = {};
+  float bsum = 0.f;
+  int cur = 0;
+  if ((int64_t)blockIdx.x < nseg) wgt_issue(d, dpre, act, blockIdx.x, segs_per_row, wsm);
+  cp_async_commit();
+  const int i = lane >> 3, r = lane & 7;
+  for (int64_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+    if (sg + gridDim.x < nseg) wgt_issue(d, dpre, act, sg + gridDim.x, segs_per_row, wsm + (1 - cur) * WGT_BUF);
+    cp_async_commit();
+    cp_async_wait1();  // this thread's copies of the current segment have landed
+    __syncthreads();   // and everyone's
+    const __nv_bfloat16* sA = wsm + cur * WGT_BUF;
+    const __nv_bfloat16* sB = sA + WGT_PX * WGT_LD;
+    if (threadIdx.x < CH) {
+      float sacc = 0.f;
+      for (int p = 0; p < WGT_PX; ++p) sacc += __bfloat162float(sA[p * WGT_LD + threadIdx.x]);
+      bsum += sacc;
+    }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+    for (int kk = 0; kk < WGT_PX / 16; ++kk) {
+      uint32_t a[2][4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) atomicAdd(&dW[((size_t)(co0 + i) * CH + (ci0 + j)) * 9 + t], acc[i][j]);
-  if (t == 4 && threadIdx.x < CH) atomicAdd(&db[threadIdx.x], bsum);
+      for (int mt = 0; mt < 2; ++mt)
+        ldsm_x4_trans(a[mt], sA + (16 * kk + r + 8 * (i >> 1)) * WGT_LD + co0 + 16 * mt + 8 * (i & 1));
+#pragma unroll
+      for (int np = 0; np < 4; ++np) {
+        uint32_t bq[4];
+        ldsm_x4_trans(bq, sB + (dy * (WGT_PX + 2) + 16 * kk + r + 8 * (i & 1) + dx) * WGT_LD + 16 * np + 8 * (i >> 1));
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          mma16816(acc[mt][2 * np], a[mt], bq[0], bq[1]);
+          mma16816(acc[mt][2 * np + 1], a[mt], bq[2], bq[3]);
+        }
+      }
+    }
+    __syncthreads();  // the buffer is refilled by the next iteration's copies
+    cur = 1 - cur;
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  const int g = lane >> 2, tq = lane & 3;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int co = co0 + 16 * mt + g + 8 * h, ci = 8 * nt + 2 * tq;
+        atomicAdd(&dW[((size_t)co * CH + ci) * 9 + t], acc[mt][nt][2 * h]);
+        atomicAdd(&dW[((size_t)co * CH + ci + 1) * 9 + t], acc[mt][nt][2 * h + 1]);
+      }
+  if (threadIdx.x < CH && db) atomicAdd(&db[threadIdx.x], bsum);
+}
+
+int wgrad64_launch(cudaStream_t s, const Dims& d, const __nv_bfloat16* dpre, const __nv_bfloat16* act, float* dW,
+                   float* db) {
+  static bool attr = false;
+  if (!attr) {
+    PNP_CUDA(cudaFuncSetAttribute(wgrad64_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, WGT_SMEM));
+    attr = true;
+  }
+  const int64_t nseg = (int64_t)d.B * d.s * ((d.s + WGT_PX - 1) / WGT_PX);
+  int dev = 0, sms = 0;
+  PNP_CUDA(cudaGetDevice(&dev));
+  PNP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nseg, sms));
+  wgrad64_tc<<<grid, WGT_THREADS, WGT_SMEM, s>>>(d, dpre, act, dW, db);
+  PNP_CHECK_LAUNCH();
+  return PNP_OK;
 }
 
 // ---------------------------------------------------------------- Jacobian of Q = 2D - I
@@ -649,8 +745,7 @@ int pnp_cnn_train_step(pnp_cnn_trainer* T, const float* u, const float* noise, d
   int cur = 0;
   for (int k = 6; k >= 1; --k) {
     float* gW = T->g + OFF_MID + (k - 1) * MID_STRIDE;
-    wgrad64<<<dim3(wgb, 9), 256, 0, s>>>(d, T->dp[cur], T->act[k], gW, gW + NWM);
-    PNP_CHECK_LAUNCH();
+    if (int rc = wgrad64_launch(s, d, T->dp[cur], T->act[k], gW, gW + NWM)) return rc;
     if (int rc = conv64_launch(s, T->map_dp[cur], T->dp[1 - cur], T->wb + (size_t)(k - 1) * NWM, nullptr,
                                T->strips, T->n_strips, d.Hc, d.Wc, 1, T->act[k], T->status))
       return rc;
@@ -719,8 +814,8 @@ int pnp_cnn_train_step_fne(pnp_cnn_trainer* T, const float* u, const float* nois
   PNP_CHECK_LAUNCH();
   int cur = 0;
   for (int k = 6; k >= 1; --k) {
-    wgrad64<<<dim3(wgb, 9), 256, 0, s>>>(d, T->dp[cur], T->tan[k], T->g + OFF_MID + (k - 1) * MID_STRIDE, T->junk);
-    PNP_CHECK_LAUNCH();
+    if (int rc = wgrad64_launch(s, d, T->dp[cur], T->tan[k], T->g + OFF_MID + (k - 1) * MID_STRIDE, T->junk))
+      return rc;
     if (int rc = conv64_launch(s, T->map_dp[cur], T->dp[1 - cur], T->wb + (size_t)(k - 1) * NWM, nullptr, T->strips,
                                T->n_strips, d.Hc, d.Wc, 1, T->act[k], T->status))
       return rc;
