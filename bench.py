@@ -568,8 +568,9 @@ def run_gpu(args):
     if learned:
         it_l, trace_l, xl = _run_to_snr(plan, cnn, y, gamma, L, x_true, alpha, target, args.converge_iters)
         comparison["learned"] = {
-            "weights": "l1 loss, then fine-tuned with the firm non-expansiveness penalty (lambda %g, %d steps)" % (
-                float(wmeta.get("fne_lambda", 0.0)), int(wmeta.get("steps", 0))),
+            "weights": "l1 loss, then fine-tuned with the firm non-expansiveness penalty (last stage: lambda %g, "
+                       "%d power iterations per step, %d steps)" % (
+                float(wmeta.get("fne_lambda", 0.0)), int(wmeta.get("fne_iters", 0)), int(wmeta.get("steps", 0))),
             "iter_per_s": value, "ms_per_iter": ms / steps, "alpha": alpha, "alpha_dirty_peak": hp["alpha"],
             "alpha_matched_to_sigma": alpha_match, "sigma_trained": float(wmeta["sigma"]),
             "sigma_heuristic_at_dirty_peak": hp["sigma"], "iters_to_target": it_l,
