@@ -30,6 +30,17 @@ struct SaraState {
   float *A = nullptr, *T = nullptr, *S = nullptr, *X = nullptr;  // n^2 work images
 };
 
+// r mod m for 0 <= r < m + L (r - L < m), and for -L < r < m: subtraction or addition of m instead of
+// an integer division; a loop, since the coarsest levels' blocks can be shorter than a filter
+__device__ __forceinline__ int wrap_up(int r, int m) {
+  while (r >= m) r -= m;
+  return r;
+}
+__device__ __forceinline__ int wrap_down(int r, int m) {
+  while (r < 0) r += m;
+  return r;
+}
+
 // analysis along axis 0 of the m x m block (row stride n): out[j][c] low, out[m/2 + j][c] high
 __global__ void dwt_axis0(const float* __restrict__ in, float* __restrict__ out, int n, int m,
                           const float* __restrict__ f, int L) {
@@ -39,7 +50,7 @@ __global__ void dwt_axis0(const float* __restrict__ in, float* __restrict__ out,
     const int j = (int)(idx / m), c = (int)(idx % m);
     float sl = 0.f, sh = 0.f;
     for (int k = 0; k < L; ++k) {
-      const float v = in[(int64_t)((2 * j + k) % m) * n + c];
+      const float v = in[(int64_t)wrap_up(2 * j + k, m) * n + c];
       sl = fmaf(f[k], v, sl);
       sh = fmaf(f[MAXTAP + k], v, sh);
     }
@@ -58,7 +69,7 @@ __global__ void dwt_axis1(const float* __restrict__ in, float* __restrict__ out,
     const float* row = in + (int64_t)i * n;
     float sl = 0.f, sh = 0.f;
     for (int k = 0; k < L; ++k) {
-      const float v = row[(2 * j + k) % m];
+      const float v = row[wrap_up(2 * j + k, m)];
       sl = fmaf(f[k], v, sl);
       sh = fmaf(f[MAXTAP + k], v, sh);
     }
@@ -77,7 +88,7 @@ __global__ void idwt_axis1(const float* __restrict__ in, float* __restrict__ out
     const float* row = in + (int64_t)i * n;
     float acc = 0.f;
     for (int k = (p & 1); k < L; k += 2) {
-      const int j = ((((p - k) % m) + m) % m) / 2;
+      const int j = wrap_down(p - k, m) / 2;
       acc = fmaf(f[k], row[j], fmaf(f[MAXTAP + k], row[half + j], acc));
     }
     out[(int64_t)i * n + p] = acc;
@@ -93,7 +104,7 @@ __global__ void idwt_axis0(const float* __restrict__ in, float* __restrict__ out
     const int p = (int)(idx / m), c = (int)(idx % m);
     float acc = 0.f;
     for (int k = (p & 1); k < L; k += 2) {
-      const int j = ((((p - k) % m) + m) % m) / 2;
+      const int j = wrap_down(p - k, m) / 2;
       acc = fmaf(f[k], in[(int64_t)j * n + c], fmaf(f[MAXTAP + k], in[(int64_t)(half + j) * n + c], acc));
     }
     out[(int64_t)p * n + c] = acc;
