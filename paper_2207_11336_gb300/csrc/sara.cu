@@ -30,27 +30,45 @@ struct SaraState {
   float *A = nullptr, *T = nullptr, *S = nullptr, *X = nullptr;  // n^2 work images
 };
 
-// r mod m for 0 <= r < m + L (r - L < m), and for -L < r < m: subtraction or addition of m instead of
-// an integer division; a loop, since the coarsest levels' blocks can be shorter than a filter
+// r mod m for 0 <= r < m + L (r - L < m) by subtraction instead of an integer division; a loop, since
+// the coarsest levels' blocks can be shorter than a filter
 __device__ __forceinline__ int wrap_up(int r, int m) {
   while (r >= m) r -= m;
   return r;
 }
-__device__ __forceinline__ int wrap_down(int r, int m) {
+
+// ---- the four passes of a level (analysis and synthesis along each axis of the m x m block, row stride
+// n), each shared-memory tiled: a CTA stages the input rows or row segments its outputs need once, so
+// each input element is read from memory about once per pass instead of once per tap.
+constexpr int DW_TC = 32;          // columns per tile of the axis-0 passes
+constexpr int DW_TJ = 32;          // output rows per tile of the axis-0 analysis
+constexpr int DW_TP = 64;          // output rows per tile of the axis-0 synthesis
+constexpr int DW_TR = 256;         // outputs per CTA of the axis-1 passes
+__device__ __forceinline__ int floor_half(int v) { return v >= 0 ? v / 2 : -((1 - v) / 2); }
+__device__ __forceinline__ int wrap_any(int r, int m) {
+  while (r >= m) r -= m;
   while (r < 0) r += m;
   return r;
 }
 
-// analysis along axis 0 of the m x m block (row stride n): out[j][c] low, out[m/2 + j][c] high
-__global__ void dwt_axis0(const float* __restrict__ in, float* __restrict__ out, int n, int m,
-                          const float* __restrict__ f, int L) {
-  const int half = m / 2;
-  const int64_t total = (int64_t)half * m;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(idx / m), c = (int)(idx % m);
+// analysis along axis 0: grid (ceil(m / DW_TC), ceil(half / DW_TJ)), 256 threads
+__global__ void __launch_bounds__(256) dwt0_tiled(const float* __restrict__ in, float* __restrict__ out, int n, int m,
+                                                  const float* __restrict__ f, int L) {
+  __shared__ float t[2 * DW_TJ + MAXTAP][DW_TC + 1];
+  const int half = m / 2, c0 = blockIdx.x * DW_TC, j0 = blockIdx.y * DW_TJ;
+  const int rows = 2 * DW_TJ + L - 1;
+  for (int e = threadIdx.x; e < rows * DW_TC; e += blockDim.x) {
+    const int rr = e / DW_TC, cc = e % DW_TC, c = c0 + cc;
+    t[rr][cc] = c < m ? in[(int64_t)wrap_up(2 * j0 + rr, m) * n + c] : 0.f;
+  }
+  __syncthreads();
+  const int cc = threadIdx.x % DW_TC, c = c0 + cc;
+  for (int jj = threadIdx.x / DW_TC; jj < DW_TJ; jj += blockDim.x / DW_TC) {
+    const int j = j0 + jj;
+    if (j >= half || c >= m) continue;
     float sl = 0.f, sh = 0.f;
     for (int k = 0; k < L; ++k) {
-      const float v = in[(int64_t)wrap_up(2 * j + k, m) * n + c];
+      const float v = t[2 * jj + k][cc];
       sl = fmaf(f[k], v, sl);
       sh = fmaf(f[MAXTAP + k], v, sh);
     }
@@ -59,53 +77,75 @@ __global__ void dwt_axis0(const float* __restrict__ in, float* __restrict__ out,
   }
 }
 
-// analysis along axis 1: out[i][j] low, out[i][m/2 + j] high
-__global__ void dwt_axis1(const float* __restrict__ in, float* __restrict__ out, int n, int m,
-                          const float* __restrict__ f, int L) {
-  const int half = m / 2;
-  const int64_t total = (int64_t)m * half;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / half), j = (int)(idx % half);
-    const float* row = in + (int64_t)i * n;
-    float sl = 0.f, sh = 0.f;
-    for (int k = 0; k < L; ++k) {
-      const float v = row[wrap_up(2 * j + k, m)];
-      sl = fmaf(f[k], v, sl);
-      sh = fmaf(f[MAXTAP + k], v, sh);
-    }
-    out[(int64_t)i * n + j] = sl;
-    out[(int64_t)i * n + half + j] = sh;
+// analysis along axis 1: grid (ceil(half / DW_TR), m), DW_TR threads
+__global__ void __launch_bounds__(DW_TR) dwt1_tiled(const float* __restrict__ in, float* __restrict__ out, int n, int m,
+                                                    const float* __restrict__ f, int L) {
+  __shared__ float t[2 * DW_TR + MAXTAP];
+  const int half = m / 2, j0 = blockIdx.x * DW_TR, i = blockIdx.y;
+  const float* row = in + (int64_t)i * n;
+  const int cnt = 2 * DW_TR + L - 1;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) t[e] = row[wrap_up(2 * j0 + e, m)];
+  __syncthreads();
+  const int j = j0 + threadIdx.x;
+  if (j >= half) return;
+  float sl = 0.f, sh = 0.f;
+  for (int k = 0; k < L; ++k) {
+    const float v = t[2 * threadIdx.x + k];
+    sl = fmaf(f[k], v, sl);
+    sh = fmaf(f[MAXTAP + k], v, sh);
   }
+  out[(int64_t)i * n + j] = sl;
+  out[(int64_t)i * n + half + j] = sh;
 }
 
-// synthesis along axis 1: out[i][p] = sum_{k: p - k even} lo[k] in[i][j] + hi[k] in[i][m/2 + j]
-__global__ void idwt_axis1(const float* __restrict__ in, float* __restrict__ out, int n, int m,
-                           const float* __restrict__ f, int L) {
-  const int half = m / 2;
-  const int64_t total = (int64_t)m * m;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / m), p = (int)(idx % m);
-    const float* row = in + (int64_t)i * n;
-    float acc = 0.f;
-    for (int k = (p & 1); k < L; k += 2) {
-      const int j = wrap_down(p - k, m) / 2;
-      acc = fmaf(f[k], row[j], fmaf(f[MAXTAP + k], row[half + j], acc));
-    }
-    out[(int64_t)i * n + p] = acc;
+// synthesis along axis 1: grid (ceil(m / DW_TR), m), DW_TR threads.  Output p takes the taps k = p mod 2,
+// p mod 2 + 2, ... at j = ((p - k) mod m) / 2; the CTA stages j = jb .. of the low and high halves, jb the
+// smallest (p - k) / 2 of its outputs (unwrapped), each staged entry wrapped into [0, half).
+__global__ void __launch_bounds__(DW_TR) idwt1_tiled(const float* __restrict__ in, float* __restrict__ out, int n,
+                                                     int m, const float* __restrict__ f, int L) {
+  __shared__ float lo[DW_TR / 2 + MAXTAP / 2 + 2], hi[DW_TR / 2 + MAXTAP / 2 + 2];
+  const int half = m / 2, p0 = blockIdx.x * DW_TR, i = blockIdx.y;
+  const float* row = in + (int64_t)i * n;
+  const int jb = floor_half(p0 - L + 1);
+  const int cnt = floor_half(p0 + DW_TR - 1) - jb + 1;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const int j = wrap_any(jb + e, half);
+    lo[e] = row[j];
+    hi[e] = row[half + j];
   }
+  __syncthreads();
+  const int p = p0 + threadIdx.x;
+  if (p >= m) return;
+  float acc = 0.f;
+  for (int k = (p & 1); k < L; k += 2) {
+    const int e = (p - k) / 2 - jb;  // p - k is even
+    acc = fmaf(f[k], lo[e], fmaf(f[MAXTAP + k], hi[e], acc));
+  }
+  out[(int64_t)i * n + p] = acc;
 }
 
-// synthesis along axis 0: out[p][c] = sum_{k: p - k even} lo[k] in[j][c] + hi[k] in[m/2 + j][c]
-__global__ void idwt_axis0(const float* __restrict__ in, float* __restrict__ out, int n, int m,
-                           const float* __restrict__ f, int L) {
-  const int half = m / 2;
-  const int64_t total = (int64_t)m * m;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int p = (int)(idx / m), c = (int)(idx % m);
+// synthesis along axis 0: grid (ceil(m / DW_TC), ceil(m / DW_TP)), 256 threads
+__global__ void __launch_bounds__(256) idwt0_tiled(const float* __restrict__ in, float* __restrict__ out, int n,
+                                                   int m, const float* __restrict__ f, int L) {
+  __shared__ float lo[DW_TP / 2 + MAXTAP / 2 + 2][DW_TC + 1], hi[DW_TP / 2 + MAXTAP / 2 + 2][DW_TC + 1];
+  const int half = m / 2, c0 = blockIdx.x * DW_TC, p0 = blockIdx.y * DW_TP;
+  const int jb = floor_half(p0 - L + 1);
+  const int cnt = floor_half(p0 + DW_TP - 1) - jb + 1;
+  for (int e = threadIdx.x; e < cnt * DW_TC; e += blockDim.x) {
+    const int rr = e / DW_TC, cc = e % DW_TC, c = c0 + cc;
+    const int j = wrap_any(jb + rr, half);
+    lo[rr][cc] = c < m ? in[(int64_t)j * n + c] : 0.f;
+    hi[rr][cc] = c < m ? in[(int64_t)(half + j) * n + c] : 0.f;
+  }
+  __syncthreads();
+  const int cc = threadIdx.x % DW_TC, c = c0 + cc;
+  for (int pp = threadIdx.x / DW_TC; pp < DW_TP; pp += blockDim.x / DW_TC) {
+    const int p = p0 + pp;
+    if (p >= m || c >= m) continue;
     float acc = 0.f;
     for (int k = (p & 1); k < L; k += 2) {
-      const int j = wrap_down(p - k, m) / 2;
-      acc = fmaf(f[k], in[(int64_t)j * n + c], fmaf(f[MAXTAP + k], in[(int64_t)(half + j) * n + c], acc));
+      const int e = (p - k) / 2 - jb;
+      acc = fmaf(f[k], lo[e][cc], fmaf(f[MAXTAP + k], hi[e][cc], acc));
     }
     out[(int64_t)p * n + c] = acc;
   }
@@ -185,9 +225,10 @@ int basis_analysis(SaraState* S, cudaStream_t s, int b, const float* x, float* c
   PNP_CUDA(cudaMemcpyAsync(c, x, (size_t)n * n * 4, cudaMemcpyDeviceToDevice, s));
   for (int l = 0; l < S->levels; ++l) {
     const int m = n >> l;
-    dwt_axis0<<<grid1((int64_t)m * m / 2), 256, 0, s>>>(c, S->T, n, m, f, L);
+    const int half = m / 2;
+    dwt0_tiled<<<dim3((m + DW_TC - 1) / DW_TC, (half + DW_TJ - 1) / DW_TJ), 256, 0, s>>>(c, S->T, n, m, f, L);
     PNP_CHECK_LAUNCH();
-    dwt_axis1<<<grid1((int64_t)m * m / 2), 256, 0, s>>>(S->T, c, n, m, f, L);
+    dwt1_tiled<<<dim3((half + DW_TR - 1) / DW_TR, m), DW_TR, 0, s>>>(S->T, c, n, m, f, L);
     PNP_CHECK_LAUNCH();
   }
   return PNP_OK;
@@ -201,9 +242,9 @@ int basis_synthesis(SaraState* S, cudaStream_t s, int b, const float* c, float* 
   PNP_CUDA(cudaMemcpyAsync(x, c, (size_t)n * n * 4, cudaMemcpyDeviceToDevice, s));
   for (int l = S->levels - 1; l >= 0; --l) {
     const int m = n >> l;
-    idwt_axis1<<<grid1((int64_t)m * m), 256, 0, s>>>(x, S->T, n, m, f, L);
+    idwt1_tiled<<<dim3((m + DW_TR - 1) / DW_TR, m), DW_TR, 0, s>>>(x, S->T, n, m, f, L);
     PNP_CHECK_LAUNCH();
-    idwt_axis0<<<grid1((int64_t)m * m), 256, 0, s>>>(S->T, x, n, m, f, L);
+    idwt0_tiled<<<dim3((m + DW_TC - 1) / DW_TC, (m + DW_TP - 1) / DW_TP), 256, 0, s>>>(S->T, x, n, m, f, L);
     PNP_CHECK_LAUNCH();
   }
   return PNP_OK;

@@ -17,12 +17,14 @@ def _gpu():
     require_gpu()
 
 
-def test_sara_dictionary_matches_oracle():
-    n = 64
+@pytest.mark.parametrize("n,levels", [(64, 4), (96, 4), (48, 4), (1024, 4), (512, 6)])
+def test_sara_dictionary_matches_oracle(n, levels):
+    """Psi^T and Psi against the oracle: coarse levels shorter than the db8 filter (48 / 8 = 6 < 16),
+    a side that is not a power of two, and sides that span several tiles of the DWT passes."""
     x = np.random.default_rng(1).standard_normal((n, n))
-    den = pnp.SaraDenoiser(n, 0.1, 0.1, 1, levels=4)
+    den = pnp.SaraDenoiser(n, 0.1, 0.1, 1, levels=levels)
     c = to_host(den.analysis(to_dev_f32(x)))
-    psi = osa.Sara(levels=4)
+    psi = osa.Sara(levels=levels)
     ref = psi.analysis(x)
     assert rel_l2(c, ref) <= 1e-6
     back = to_host(den.synthesis(to_dev_f32(ref.astype(np.float32))))
