@@ -222,11 +222,11 @@ int basis_analysis(SaraState* S, cudaStream_t s, int b, const float* x, float* c
   const int n = S->n;
   const float* f = S->filt + (size_t)(b - 1) * 2 * MAXTAP;
   const int L = S->len[b - 1];
-  PNP_CUDA(cudaMemcpyAsync(c, x, (size_t)n * n * 4, cudaMemcpyDeviceToDevice, s));
-  for (int l = 0; l < S->levels; ++l) {
+  for (int l = 0; l < S->levels; ++l) {  // level 0 reads x; its second pass writes all of c
     const int m = n >> l;
     const int half = m / 2;
-    dwt0_tiled<<<dim3((m + DW_TC - 1) / DW_TC, (half + DW_TJ - 1) / DW_TJ), 256, 0, s>>>(c, S->T, n, m, f, L);
+    dwt0_tiled<<<dim3((m + DW_TC - 1) / DW_TC, (half + DW_TJ - 1) / DW_TJ), 256, 0, s>>>(l == 0 ? x : c, S->T, n, m,
+                                                                                         f, L);
     PNP_CHECK_LAUNCH();
     dwt1_tiled<<<dim3((half + DW_TR - 1) / DW_TR, m), DW_TR, 0, s>>>(S->T, c, n, m, f, L);
     PNP_CHECK_LAUNCH();
