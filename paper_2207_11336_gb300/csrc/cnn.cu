@@ -507,6 +507,204 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
   if (threadIdx.x == 0 && s_abort) atomicOr(A.status, 2);
 }
 
+// ------------------------------------------------------------ hidden layers, per-input-row accumulators
+// The 64 -> 64 convolution with one fresh accumulator per staged input row: the 12 MMAs of input row s
+// (3 dx x 4 K steps of 16 channels, M = 128 pixels, N = 192 = the weights of dy = 2, 1, 0 stacked) write
+// D_s = its contributions to output rows s - 2, s - 1, s, in one of two 192-column TMEM buffers, and the
+// epilogue sums the three parts of each output row in registers: out(s - 2) = (D_{s-2}[dy 0] +
+// D_{s-1}[dy 1]) + D_s[dy 2].  Every MMA has the full N = 192 (no accumulator ring to wrap, no fresh-row
+// split), so an input row costs exactly 12 MMAs.  Staging, TMA ring and warp roles as in conv64_tc;
+// epilogue warp w reads TMEM lanes 32 (w % 4) .. + 31 and channels 16 (w / 4) .. + 15 of each part.
+constexpr int ROW_N = 3 * CH;                 // 192 accumulator columns per staged input row
+constexpr int ROW_DBUF = 2;                   // TMEM buffers (2 x 192 of the 512 columns)
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__global__ void __launch_bounds__(CONV_THREADS, 1) conv64_rows(ConvArgs A, const __grid_constant__ CUtensorMap tmain,
+                                                               const __grid_constant__ CUtensorMap thalo) {
+  using Gm = ConvGeom<CH>;
+  extern __shared__ __align__(1024) unsigned char sm[];  // [IN_SLOTS][ROW_BYTES] input ring, then B
+  unsigned char* sb = sm + IN_SLOTS * ROW_BYTES;
+  __shared__ uint64_t in_full[IN_SLOTS], in_empty[IN_SLOTS], d_full[ROW_DBUF], d_empty[ROW_DBUF];
+  __shared__ uint32_t s_tmem;
+  __shared__ float s_bias[CH];
+  __shared__ volatile int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(A.w);
+    uint4* dst = reinterpret_cast<uint4*>(sb);
+    for (int i = threadIdx.x; i < Gm::B_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x < CH) s_bias[threadIdx.x] = A.bias ? A.bias[threadIdx.x] : 0.f;
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < IN_SLOTS; ++i) {
+      bar_init(&in_full[i], 1);
+      bar_init(&in_empty[i], 1);
+    }
+    for (int k = 0; k < ROW_DBUF; ++k) {
+      bar_init(&d_full[k], 1);
+      bar_init(&d_empty[k], EPI_WARPS * 32);  // every epilogue thread reads every buffer
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == MMA_WARP) {
+    tmem_alloc(&s_tmem, 512);
+    tmem_relinquish();
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const int stride = gridDim.x;
+
+  if (warp == TMA_WARP) {
+    // ---------------- TMA producer (as conv64_tc): input rows ya-1 .. ya+R, pixels x0-1 .. x0+128
+    if (lane == 0) {
+      uint32_t L = 0;
+      for (int strip = blockIdx.x; strip < A.n_strips && !s_abort; strip += stride) {
+        const int4 S = A.strips[strip];
+        const int ya = S.z >> 16, R = S.z & 0xFFFF;
+        for (int s = 0; s < R + 2; ++s, ++L) {
+          const uint32_t slot = L % IN_SLOTS;
+          if (L >= IN_SLOTS && !bar_wait(&in_empty[slot], ((L / IN_SLOTS) - 1) & 1)) s_abort = 1;
+          if (s_abort) break;
+          bar_expect_tx(&in_full[slot], ROW_DATA_BYTES);
+          unsigned char* dst = sm + slot * ROW_BYTES;
+          const int y = ya - 1 + s;
+#pragma unroll 1
+          for (int kb = 0; kb < 8; ++kb) {
+            tma_load_4d(dst + kb * KB_BYTES, &tmain, 2 * (S.y - 1), kb, y, S.x, &in_full[slot]);
+            tma_load_4d(dst + kb * KB_BYTES + TILE_PX * 16, &thalo, 2 * (S.y + TILE_PX - 1), kb, y, S.x, &in_full[slot]);
+          }
+        }
+      }
+      for (uint32_t k = (L > IN_SLOTS ? L - IN_SLOTS : 0); k < L; ++k)
+        bar_wait(&in_full[k % IN_SLOTS], (k / IN_SLOTS) & 1);
+    }
+    __syncwarp();
+  } else if (warp == MMA_WARP) {
+    // ---------------- MMA issuer: 12 MMAs of N = 192 per staged input row into buffer L % 2
+    if (lane == 0) {
+      const uint64_t adesc0 = smem_desc(su32(sm), KB_BYTES, 128);
+      const uint64_t bdesc0 = smem_desc(su32(sb), Gm::B_GROUP_BYTES, 128);
+      const uint32_t idesc = idesc_n(ROW_N);
+      uint32_t L = 0;
+      for (int strip = blockIdx.x; strip < A.n_strips && !s_abort; strip += stride) {
+        const int R = A.strips[strip].z & 0xFFFF;
+        for (int s = 0; s < R + 2; ++s, ++L) {
+          const uint32_t slot = L % IN_SLOTS, buf = L % ROW_DBUF;
+          if (!bar_wait(&in_full[slot], (L / IN_SLOTS) & 1)) s_abort = 1;
+          if (L >= ROW_DBUF && !bar_wait(&d_empty[buf], ((L / ROW_DBUF) - 1) & 1)) s_abort = 1;
+          if (s_abort) break;
+          tc_fence_after();
+          const uint64_t arow = adesc0 + (uint64_t)((slot * ROW_BYTES) >> 4);
+          const uint32_t d = tmem + buf * ROW_N;
+#pragma unroll
+          for (int dk = 0; dk < 12; ++dk) {
+            const int dx = dk >> 2, kk = dk & 3;
+            const uint64_t ad = arow + (uint64_t)((2 * kk * KB_BYTES + dx * 16) >> 4);
+            const uint64_t bd = bdesc0 + (uint64_t)(((dx * 8 + 2 * kk) * Gm::B_GROUP_BYTES) >> 4);
+            mma_bf16(d, ad, bd, idesc, dk > 0 ? 1u : 0u);
+          }
+          mma_commit(&in_empty[slot]);  // the input slot may be refilled
+          mma_commit(&d_full[buf]);     // D_s is complete
+        }
+      }
+      // the tensor memory is freed below only after the last MMAs have completed
+      if (L > 0) bar_wait(&in_empty[(L - 1) % IN_SLOTS], ((L - 1) / IN_SLOTS) & 1);
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue: q1 = partial sums of output row s - 1 (its dy = 0 part), q2 = those of
+    // row s - 2 (dy = 0 and 1); staged row s completes row s - 2 with its dy = 2 part
+    const int lq = warp & 3, cq = warp >> 2;
+    const int m = lq * 32 + lane;
+    const size_t plane = (size_t)A.Wc * 8;
+    uint32_t L = 0;
+    bool stop = false;
+    for (int strip = blockIdx.x; strip < A.n_strips && !stop; strip += stride) {
+      const int4 S = A.strips[strip];
+      const int ya = S.z >> 16, R = S.z & 0xFFFF, Hf = S.w >> 16, Wf = S.w & 0xFFFF;
+      float q1[16] = {}, q2[16] = {};
+      for (int s = 0; s < R + 2; ++s, ++L) {
+        const uint32_t buf = L % ROW_DBUF;
+        const bool ok = !s_abort && bar_wait(&d_full[buf], (L / ROW_DBUF) & 1);
+        if (!ok) s_abort = 1;
+        if (!__all_sync(0xffffffffu, ok)) {
+          stop = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + buf * ROW_N + cq * 16;
+        uint32_t v2[16];
+        tmem_ld16(base, v2);  // dy = 2: output row s - 2 (the other two parts are read after it is stored)
+        tmem_wait_ld();
+        const int r = s - 2;  // the output row completed by this input row
+        if (r >= 0) {
+          const int y = ya + r, x = S.y + m;
+          if (y < A.Hc && x < A.Wc) {
+            const bool live = x < Wf && y < Hf;  // outside the facet the canvas stays zero
+            const size_t pix = canvas_index(S.x, y, x, 16 * cq, A.Hc, A.Wc);  // block q at pix + q * plane
+            uint4 pk[2];
+            uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
+            if (A.mode == 0) {
+#pragma unroll
+              for (int c = 0; c < 16; c += 2) {
+                const float a0 = q2[c] + __uint_as_float(v2[c]), a1 = q2[c + 1] + __uint_as_float(v2[c + 1]);
+                const float o0 = live ? fmaxf(0.f, a0 + s_bias[16 * cq + c]) : 0.f;
+                const float o1 = live ? fmaxf(0.f, a1 + s_bias[16 * cq + c + 1]) : 0.f;
+                __nv_bfloat162 h = __floats2bfloat162_rn(o0, o1);
+                pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+              }
+            } else {
+              uint4 mk[2];
+#pragma unroll
+              for (int q = 0; q < 2; ++q) mk[q] = *reinterpret_cast<const uint4*>(A.mask + pix + q * plane);
+              const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(mk);
+#pragma unroll
+              for (int c = 0; c < 16; c += 2) {
+                const float a0 = q2[c] + __uint_as_float(v2[c]), a1 = q2[c + 1] + __uint_as_float(v2[c + 1]);
+                const float o0 = (live && __bfloat162float(mh[c]) > 0.f) ? a0 : 0.f;
+                const float o1 = (live && __bfloat162float(mh[c + 1]) > 0.f) ? a1 : 0.f;
+                __nv_bfloat162 h = __floats2bfloat162_rn(o0, o1);
+                pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) *reinterpret_cast<uint4*>(A.out + pix + q * plane) = pk[q];
+          }
+        }
+        uint32_t v1[16], v0[16];
+        tmem_ld16(base + CH, v1);      // dy = 1: output row s - 1
+        tmem_ld16(base + 2 * CH, v0);  // dy = 0: output row s
+        tmem_wait_ld();
+        tc_fence_before();
+        bar_arrive(&d_empty[buf]);  // this thread's parts of D_s are in registers
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          q2[c] = q1[c] + __uint_as_float(v1[c]);  // row s - 1: dy = 0 + dy = 1 (not used at s = 0)
+          q1[c] = __uint_as_float(v0[c]);          // row s: dy = 0
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+  if (threadIdx.x == 0 && s_abort) atomicOr(A.status, 2);
+}
+
 // ------------------------------------------------------------ layer 1 (1 -> 64)
 struct FirstArgs {
   const float* z;
@@ -996,7 +1194,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
   }
   static bool attr = false;
   if (!attr) {
-    PNP_CUDA(cudaFuncSetAttribute(conv64_tc<CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, ConvGeom<CH>::SMEM));
+    PNP_CUDA(cudaFuncSetAttribute(conv64_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, ConvGeom<CH>::SMEM));
     PNP_CUDA(cudaFuncSetAttribute(conv64_tc<NO_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   ConvGeom<NO_LAST>::SMEM));
     attr = true;
@@ -1006,7 +1204,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
     ConvArgs C{S->d_canvas[1 - cur], S->d_wmid + (size_t)l * 9 * CH * CH, S->d_b + (l + 1) * CH, S->d_strips,
                S->n_strips, S->Hc, S->Wc, S->d_status, 0, nullptr};
     const int grid = std::max(1, std::min(S->n_strips, sms));
-    conv64_tc<CH><<<grid, CONV_THREADS, ConvGeom<CH>::SMEM, s>>>(C, S->map[cur][0], S->map[cur][1]);
+    conv64_rows<<<grid, CONV_THREADS, ConvGeom<CH>::SMEM, s>>>(C, S->map[cur][0], S->map[cur][1]);
     PNP_CHECK_LAUNCH();
     cur = 1 - cur;
   }
@@ -1032,13 +1230,13 @@ int conv64_launch(cudaStream_t s, const void* in_map, __nv_bfloat16* out, const 
                   const __nv_bfloat16* mask, int* status) {
   static bool attr = false;
   if (!attr) {
-    PNP_CUDA(cudaFuncSetAttribute(conv64_tc<CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, ConvGeom<CH>::SMEM));
+    PNP_CUDA(cudaFuncSetAttribute(conv64_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, ConvGeom<CH>::SMEM));
     attr = true;
   }
   ConvArgs C{out, w_packed, bias, strips, n_strips, Hc, Wc, status, mode, mask};
   const int grid = std::max(1, std::min(n_strips, sms_of_device()));
   const CUtensorMap* maps = static_cast<const CUtensorMap*>(in_map);
-  conv64_tc<CH><<<grid, CONV_THREADS, ConvGeom<CH>::SMEM, s>>>(C, maps[0], maps[1]);
+  conv64_rows<<<grid, CONV_THREADS, ConvGeom<CH>::SMEM, s>>>(C, maps[0], maps[1]);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }
