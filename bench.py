@@ -630,7 +630,7 @@ def run_gpu(args):
         px = _facet_pixels(n, prob["facet_rows"], prob["facet_cols"], prob["halo"])
         flop = px * CNN_FLOP_PER_PX
         bf16_peak, bf16_kind = measured_bf16_peak()
-        roof_cnn = {"bound": "tensor", "kernel": "faceted CNN denoiser (cnn_first + 6 x conv64_tc + cnn_last)",
+        roof_cnn = {"bound": "tensor", "kernel": "faceted CNN denoiser (cnn_first + 6 x conv64_rows + cnn_last)",
                     "achieved": flop / (d_ms * 1e-3) / 1e12, "peak": bf16_peak, "peak_kind": bf16_kind,
                     "unit": "TFLOP/s", "frac": flop / (d_ms * 1e-3) / 1e12 / bf16_peak, "traffic": None,
                     "flop_per_launch": flop, "ms_per_launch": d_ms}

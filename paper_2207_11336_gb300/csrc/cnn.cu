@@ -14,34 +14,31 @@
 // so they act as padding.
 //
 // Kernels per application:
-//   cnn_first   z (FP32 image) -> canvas: layer 1 (1 -> 64) on CUDA cores;
-//   conv64_tc   canvas -> canvas: one 64 -> 64 layer as an implicit GEMM on the
-//               5th-generation tensor cores (tcgen05.mma, FP32 accumulators in
-//               tensor memory), one 128-pixel row segment per tile;
-//   conv64_tc<16> canvas -> image: layer 8 (64 -> 1) with the same kernel, its
-//               output channel padded to the smallest MMA width (N = 16),
-//               over the facet cores only, fused with D(z) = max(0, z - N(z))
-//               and the FP64 stopping-test norms.
+//   cnn_first    z (FP32 image) -> canvas: layer 1 (1 -> 64) on CUDA cores;
+//   conv64_rows  canvas -> canvas: one 64 -> 64 layer as an implicit GEMM on the
+//                5th-generation tensor cores (tcgen05.mma, FP32 accumulators in
+//                tensor memory), one 128-pixel row segment per tile;
+//   cnn_last     canvas -> image: layer 8 (64 -> 1) as a tap projection on
+//                mma.sync plus a 3 x 3 gather over the facet cores, fused with
+//                D(z) = max(0, z - N(z)) and the FP64 stopping-test norms.
 //
-// conv64_tc layout.  Work is a strip: one 128-pixel column segment (x0 .. x0+127)
-// of about 32 consecutive output rows of a facet.  The strip's input rows (64
-// channels, pixels x0-1 .. x0+128) stream through a ring of shared-memory row
-// slots, staged channel-block-major: [kb][pixel][8 ch] with the 130 pixels of a
-// block 16 bytes apart (in a 128-byte aligned 2176-byte plane).  That is the
-// canonical no-swizzle K-major operand layout (core matrix = 8 pixels x 8
-// channels, 128 contiguous bytes), and tap (dy, dx) of the 3x3 stencil is the
-// same matrix with its start address moved by dx pixels (16 B).  Input row s
-// serves output rows s-2, s-1, s (taps dy = 2, 1, 0): with the weights of one
-// (dx, kb) stored as [dy=2 | dy=1 | dy=0] x NO output channels, one MMA of
-// M = 128 pixels, K = 16 channels and N = NO x (rows served) per (dx, K step)
-// accumulates all of them into a ring of output-row accumulators in tensor
-// memory.  Each staged row is two TMA transfers per channel block: the canvas is
-// described as 8-byte elements (2 per pixel) so the 128-pixel main box (2 KB)
-// and the 2-pixel halo box (32 B) are runs of whole sectors, with zeros outside
-// the canvas.  Warp roles: warps 0-15 drain tensor memory (bias, ReLU, BF16,
-// store for the hidden layers; the residual and norms for the last one), warp 16
-// allocates tensor memory and issues the MMAs (one lane), warp 17 issues the TMA
-// loads (one lane).  The rings are pipelined with mbarriers; every wait is bounded.
+// conv64_rows layout.  Work is a strip: one 128-pixel column segment (x0 .. x0+127)
+// of a run of consecutive output rows of a facet (the strip height is autotuned).
+// The strip's input rows (64 channels, pixels x0-1 .. x0+128) stream through a
+// ring of shared-memory row slots, staged channel-block-major: [kb][pixel][8 ch]
+// with the 130 pixels of a block 16 bytes apart (in a 128-byte aligned 2176-byte
+// plane).  That is the canonical no-swizzle K-major operand layout (core matrix
+// = 8 pixels x 8 channels, 128 contiguous bytes), and tap (dy, dx) of the 3x3
+// stencil is the same matrix with its start address moved by dx pixels (16 B).
+// Input row s serves output rows s-2, s-1, s (taps dy = 2, 1, 0): with the
+// weights of one (dx, kb) stored as [dy=2 | dy=1 | dy=0] x 64 output channels,
+// one MMA of M = 128 pixels, K = 16 channels and N = 192 per (dx, K step) forms
+// all three contributions in a fresh accumulator of the row; the epilogue adds
+// the three contributions of each output row.  Each staged row is two TMA
+// transfers per channel block: the canvas is described as 8-byte elements (2 per
+// pixel) so the 128-pixel main box (2 KB) and the 2-pixel halo box (32 B) are
+// runs of whole sectors, with zeros outside the canvas.  The rings are pipelined
+// with mbarriers; every wait is bounded.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -63,18 +60,11 @@ constexpr int KB_BYTES = 136 * 16;                      // one 8-channel block o
 constexpr int ROW_BYTES = 8 * KB_BYTES;                 // one staged input row, 8 channel blocks (17408)
 constexpr int ROW_DATA_BYTES = 8 * STAGE_PX * 16;       // bytes the TMA delivers per staged row (16640)
 constexpr int IN_SLOTS = 8;                             // ring of staged input rows
-constexpr int ACC_SLOTS = 8;                            // ring of output-row accumulators in tensor memory
-// Geometry of the convolution kernel for NO output channels per pixel: 64 for the hidden layers,
-// 16 for the last layer (its single output channel padded to the smallest MMA width N = 16).
-template <int NO>
-struct ConvGeom {
-  static constexpr int TMEM_COLS = ACC_SLOTS * NO;            // 512 (NO = 64) or 128 (NO = 16) columns
-  static constexpr int B_GROUP_BYTES = 3 * NO * 16;           // one (dx, kb) group: [dy=2 | dy=1 | dy=0] x NO co x 8 ci
-  static constexpr int B_BYTES = 3 * 8 * B_GROUP_BYTES;       // 73728 (NO = 64)
-  static constexpr int SMEM = IN_SLOTS * ROW_BYTES + B_BYTES;  // 212992 (NO = 64)
-};
-constexpr int NO_LAST = 16;
-constexpr int EPI_WARPS = 16;                           // 2 row parities x 2 channel halves x 4 lane quarters
+// shared memory of the hidden-layer convolution: the input ring and the layer's weights
+constexpr int B_GROUP_BYTES = 3 * CH * 16;              // one (dx, kb) group: [dy=2 | dy=1 | dy=0] x 64 co x 8 ci
+constexpr int B_BYTES = 3 * 8 * B_GROUP_BYTES;          // 73728
+constexpr int CONV_SMEM = IN_SLOTS * ROW_BYTES + B_BYTES;  // 212992
+constexpr int EPI_WARPS = 16;                           // 4 lane quarters x 4 channel quarters
 constexpr int MMA_WARP = EPI_WARPS, TMA_WARP = EPI_WARPS + 1;
 constexpr int CONV_THREADS = (EPI_WARPS + 2) * 32;
 constexpr int FIRST_ROWS = 16;                          // cnn_first: image rows per block
@@ -86,13 +76,12 @@ struct CnnState {
   std::vector<int> R0, C0, Hf, Wf;       // extended facets
   int4* d_facets = nullptr;              // per facet: (R0, C0, Hf, Wf)
   int4* d_cores = nullptr;               // per facet: (r0, r1, c0, c1)
-  int4* d_strips = nullptr;              // conv64_tc work list (conv_strips)
+  int4* d_strips = nullptr;              // conv64_rows work list (conv_strips)
   int n_strips = 0;
   int4* d_lstrips = nullptr;             // last layer's work list: strips of the facet cores (last_strips)
   int n_lstrips = 0;
   int strip_rows = STRIP_ROWS;           // target output rows per strip of both work lists (autotuned)
   size_t cap_strips = 0, cap_lstrips = 0;  // allocated entries of d_strips, d_lstrips
-  __nv_bfloat16* d_wlast = nullptr;      // last layer's B operand (last_wpack_index), output channel 0 of 16
   uint32_t* d_wfrag = nullptr;           // last layer's weights as mma.sync B fragments [4 k][2 n][32 lanes][2]
   __nv_bfloat16* d_canvas[2] = {nullptr, nullptr};
   float* d_w1 = nullptr;                 // [64][9]  (BF16-rounded values)
@@ -101,8 +90,7 @@ struct CnnState {
   float* d_w8 = nullptr;                 // [9][64] (BF16-rounded values)
   int* d_status = nullptr;
   float b8 = 0.f;                        // last layer's bias (host copy)
-  bool last_tc = false;                  // layer 8 on the tcgen05 convolution instead of cnn_last
-  CUtensorMap map[2][2];                 // TMA descriptors of the two canvases (main, halo boxes; conv64_tc)
+  CUtensorMap map[2][2];                 // TMA descriptors of the two canvases (main, halo boxes; conv64_rows)
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -169,21 +157,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-}
-__device__ __forceinline__ uint32_t tmem_ld1(uint32_t taddr) {
-  uint32_t r;
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr));
-  return r;
-}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor: no swizzle, K-major canonical layout.
@@ -203,309 +176,16 @@ __device__ __forceinline__ uint32_t idesc_n(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TILE_PX >> 4) << 24);
 }
 
-// One MMA target of an input row: consecutive accumulator slots (TMEM column), the weight rows
-// (B descriptor start offset, 16-byte units) and the instruction descriptor (N = 64 x rows).
-struct Piece {
-  uint32_t tcol, boff, idesc;
-};
-
-// K steps 1..11 of an input row (dx = dk / 4, K step kk = dk % 4), with compile-time offsets
-// added to the row's A descriptor and the pieces' B descriptors.
-template <int NP, int NO>
-__device__ __forceinline__ void mma_steps(uint32_t tmem, uint64_t arow, uint64_t bbase, const Piece (&pc)[2]) {
-#pragma unroll
-  for (int dk = 1; dk < 12; ++dk) {
-    const int dx = dk >> 2, kk = dk & 3;
-    const uint64_t ad = arow + (uint64_t)((2 * kk * KB_BYTES + dx * 16) >> 4);
-    const uint64_t bo = (uint64_t)(((dx * 8 + 2 * kk) * ConvGeom<NO>::B_GROUP_BYTES) >> 4);
-#pragma unroll
-    for (int i = 0; i < NP; ++i) mma_bf16(tmem + pc[i].tcol, ad, bbase + bo + pc[i].boff, pc[i].idesc, 1u);
-  }
-}
-
-// Pieces for output rows a..b of input row s (ring index of row 0 = g0): one, or two where the
-// accumulator ring wraps.
-template <int NO>
-__device__ __forceinline__ int make_pieces(int a, int b, int s, uint32_t g0, Piece (&pc)[2]) {
-  const uint32_t k = (g0 + a) % ACC_SLOTS;
-  const int n = b - a + 1, cnt = min(n, (int)(ACC_SLOTS - k));
-  pc[0] = Piece{k * NO, (uint32_t)((2 - (s - a)) * (NO * 16 >> 4)), idesc_n(cnt * NO)};
-  if (cnt == n) return 1;
-  pc[1] = Piece{0u, (uint32_t)((2 - (s - a - cnt)) * (NO * 16 >> 4)), idesc_n((n - cnt) * NO)};
-  return 2;
-}
-
 struct ConvArgs {
   __nv_bfloat16* out;
-  const __nv_bfloat16* w;  // B operand, conv_wpack_index layout (NO = 64) or last_wpack_index (NO = 16)
+  const __nv_bfloat16* w;  // B operand, conv_wpack_index layout
   const float* bias;       // [64] (forward mode)
-  const int4* strips;      // conv_strips, or last_strips for the last layer
+  const int4* strips;      // conv_strips
   int n_strips, Hc, Wc;
   int* status;
   int mode;                    // 0: forward, out = ReLU(acc + bias); 1: backward data, out = acc * [mask > 0]
   const __nv_bfloat16* mask;   // backward data: activations whose ReLU mask gates the output (same canvas layout)
-  // last layer (NO = 16): img = max(0, z - (N + b8)) on the facet cores, FP64 stopping-test terms in acc
-  const float* z;
-  const float* x_prev;
-  float* img;
-  int n;
-  const int4* facets;  // per facet: (R0, C0, Hf, Wf)
-  const int4* cores;   // per facet: (r0, r1, c0, c1)
-  float b8;
-  double* acc;
-  int pos;             // last layer: 1 applies the positivity projection max(0, .)
 };
-
-template <int NO>
-__global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const __grid_constant__ CUtensorMap tmain,
-                                                           const __grid_constant__ CUtensorMap thalo) {
-  using Gm = ConvGeom<NO>;
-  extern __shared__ __align__(1024) unsigned char sm[];  // [IN_SLOTS][ROW_BYTES] input ring, then B
-  unsigned char* sb = sm + IN_SLOTS * ROW_BYTES;
-  __shared__ uint64_t in_full[IN_SLOTS], in_empty[IN_SLOTS], t_full[ACC_SLOTS], t_empty[ACC_SLOTS];
-  __shared__ uint32_t s_tmem;
-  __shared__ float s_bias[CH];
-  __shared__ volatile int s_abort;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  // weights (already in the operand layout) and biases into shared memory
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(A.w);
-    uint4* dst = reinterpret_cast<uint4*>(sb);
-    for (int i = threadIdx.x; i < Gm::B_BYTES / 16; i += blockDim.x) dst[i] = src[i];
-    if (threadIdx.x < CH) s_bias[threadIdx.x] = A.bias ? A.bias[threadIdx.x] : 0.f;  // no bias in backward mode
-  }
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < IN_SLOTS; ++i) {
-      bar_init(&in_full[i], 1);
-      bar_init(&in_empty[i], 1);
-    }
-    for (int k = 0; k < ACC_SLOTS; ++k) {
-      bar_init(&t_full[k], 1);
-      // a row is drained by the 8 warps of its parity (NO = 64) or the 4 warps of its phase (NO = 16)
-      bar_init(&t_empty[k], (NO == CH ? EPI_WARPS / 2 : EPI_WARPS / 4) * 32);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_abort = 0;
-  }
-  if (warp == MMA_WARP) {
-    tmem_alloc(&s_tmem, Gm::TMEM_COLS);  // ACC_SLOTS accumulators of 128 pixels x NO channels, FP32
-    tmem_relinquish();
-  }
-  fence_async_smem();  // the weights written above are read by the tensor cores (async proxy)
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = s_tmem;
-  const int stride = gridDim.x;
-
-  if (warp == TMA_WARP) {
-    // ---------------- TMA producer: input rows ya-1 .. ya+R of each strip, pixels x0-1 .. x0+128
-    if (lane == 0) {
-      uint32_t L = 0;  // rows loaded so far (ring position)
-      for (int strip = blockIdx.x; strip < A.n_strips && !s_abort; strip += stride) {
-        const int4 S = A.strips[strip];
-        const int ya = S.z >> 16, R = S.z & 0xFFFF;
-        for (int s = 0; s < R + 2; ++s, ++L) {
-          const uint32_t slot = L % IN_SLOTS;
-          if (L >= IN_SLOTS && !bar_wait(&in_empty[slot], ((L / IN_SLOTS) - 1) & 1)) s_abort = 1;
-          if (s_abort) break;
-          // per 8-channel block: pixels x0-1 .. x0+126 (2 KB) and x0+127, x0+128 (32 B), each a run of
-          // whole sectors of the block's plane (the canvas seen as 8-byte elements, 2 per pixel)
-          bar_expect_tx(&in_full[slot], ROW_DATA_BYTES);
-          unsigned char* dst = sm + slot * ROW_BYTES;
-          const int y = ya - 1 + s;
-#pragma unroll 1
-          for (int kb = 0; kb < 8; ++kb) {
-            tma_load_4d(dst + kb * KB_BYTES, &tmain, 2 * (S.y - 1), kb, y, S.x, &in_full[slot]);
-            tma_load_4d(dst + kb * KB_BYTES + TILE_PX * 16, &thalo, 2 * (S.y + TILE_PX - 1), kb, y, S.x, &in_full[slot]);
-          }
-        }
-      }
-      // every issued load must land before the CTA ends (bounded)
-      for (uint32_t k = (L > IN_SLOTS ? L - IN_SLOTS : 0); k < L; ++k)
-        bar_wait(&in_full[k % IN_SLOTS], (k / IN_SLOTS) & 1);
-    }
-    __syncwarp();
-  } else if (warp == MMA_WARP) {
-    // ---------------- MMA issuer.  Input row s of a strip (staged row s = facet row ya-1+s) feeds
-    // output rows s-2, s-1, s with taps dy = 2, 1, 0.  With the weights of one (dx, kb) stored as
-    // [dy=2 | dy=1 | dy=0], the output rows r_lo..r_hi take the contiguous weight rows from block
-    // 2-(s-r_lo) on, and their accumulators are consecutive ring slots: one MMA of N = 64 x rows
-    // (split where the ring wraps) per (dx, K step).  A fresh output row (r = s) starts with
-    // accumulate = 0 in its own MMA on the first K step.
-    if (lane == 0) {
-      const uint64_t adesc0 = smem_desc(su32(sm), KB_BYTES, 128);
-      const uint64_t bdesc0 = smem_desc(su32(sb), Gm::B_GROUP_BYTES, 128);
-      uint32_t L = 0, g0 = 0;  // input rows consumed; ring index of the strip's first output row
-      for (int strip = blockIdx.x; strip < A.n_strips && !s_abort; strip += stride) {
-        const int4 S = A.strips[strip];
-        const int R = S.z & 0xFFFF;
-        for (int s = 0; s < R + 2; ++s, ++L) {
-          const uint32_t slot = L % IN_SLOTS;
-          if (!bar_wait(&in_full[slot], (L / IN_SLOTS) & 1)) s_abort = 1;
-          const bool fresh = s < R;
-          if (fresh) {
-            const uint32_t g = g0 + s;
-            if (g >= ACC_SLOTS && !bar_wait(&t_empty[g % ACC_SLOTS], ((g / ACC_SLOTS) - 1) & 1)) s_abort = 1;
-          }
-          if (s_abort) break;
-          tc_fence_after();
-          const int r_lo = max(0, s - 2), r_hi = min(R - 1, s);
-          const uint64_t arow = adesc0 + (uint64_t)((slot * ROW_BYTES) >> 4);
-          Piece pc[2];
-          const int np = make_pieces<NO>(r_lo, r_hi, s, g0, pc);
-          // first K step (dx = 0, kk = 0): a fresh row starts its accumulator (accumulate = 0)
-          if (fresh) {
-            if (r_hi > r_lo) {
-              Piece p0[2];
-              const int n0 = make_pieces<NO>(r_lo, r_hi - 1, s, g0, p0);
-              for (int i = 0; i < n0; ++i) mma_bf16(tmem + p0[i].tcol, arow, bdesc0 + p0[i].boff, p0[i].idesc, 1u);
-            }
-            mma_bf16(tmem + ((g0 + r_hi) % ACC_SLOTS) * NO, arow, bdesc0 + 2 * (NO * 16 >> 4), idesc_n(NO), 0u);
-          } else {
-            for (int i = 0; i < np; ++i) mma_bf16(tmem + pc[i].tcol, arow, bdesc0 + pc[i].boff, pc[i].idesc, 1u);
-          }
-          if (np == 1)
-            mma_steps<1, NO>(tmem, arow, bdesc0, pc);
-          else
-            mma_steps<2, NO>(tmem, arow, bdesc0, pc);
-          mma_commit(&in_empty[slot]);                                 // the input slot may be refilled
-          if (s >= 2) mma_commit(&t_full[(g0 + s - 2) % ACC_SLOTS]);   // output row s-2 is complete
-        }
-        g0 += R;
-      }
-      // the tensor memory is freed below only after the last MMAs have completed
-      if (L > 0) bar_wait(&in_empty[(L - 1) % IN_SLOTS], ((L - 1) / IN_SLOTS) & 1);
-    }
-    __syncwarp();
-  } else {
-    if constexpr (NO == CH) {
-      // ---------------- epilogue: tensor memory -> bias + ReLU -> BF16 -> canvas.  Warp w drains the
-      // output rows of parity w / 8; it reads TMEM lanes 32 (w % 4) .. + 31 (the lanes a warp may
-      // access), i.e. pixels 32 (w % 4) + lane, channels 32 ((w / 4) % 2) .. + 31.
-      const int lq = warp & 3, par = warp >> 3, half = (warp >> 2) & 1;
-      const int m = lq * 32 + lane;
-      const size_t plane = (size_t)A.Wc * 8;
-      uint32_t g0 = 0;
-      bool stop = false;
-      for (int strip = blockIdx.x; strip < A.n_strips && !stop; strip += stride) {
-        const int4 S = A.strips[strip];
-        const int ya = S.z >> 16, R = S.z & 0xFFFF, Hf = S.w >> 16, Wf = S.w & 0xFFFF;
-        for (int r = (int)((g0 + par) & 1); r < R; r += 2) {  // rows whose ring index has parity par
-          const uint32_t g = g0 + r, k = g % ACC_SLOTS;
-          const bool ok = !s_abort && bar_wait(&t_full[k], (g / ACC_SLOTS) & 1);
-          if (!ok) s_abort = 1;
-          if (!__all_sync(0xffffffffu, ok)) {
-            stop = true;
-            break;
-          }
-          tc_fence_after();
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(k * CH + half * 32), v);
-          tmem_wait_ld();
-          tc_fence_before();
-          bar_arrive(&t_empty[k]);  // this thread's share of the row is in registers
-          const int y = ya + r, x = S.y + m;
-          if (y >= A.Hc || x >= A.Wc) continue;
-          const bool live = x < Wf && y < Hf;  // outside the facet the canvas stays zero
-          const size_t pix = canvas_index(S.x, y, x, 32 * half, A.Hc, A.Wc);  // block q at pix + q * plane
-          uint4 pk[4];
-          uint32_t* pw = reinterpret_cast<uint32_t*>(pk);
-          if (A.mode == 0) {
-  #pragma unroll
-            for (int c = 0; c < 32; c += 2) {
-              const float v0 = live ? fmaxf(0.f, __uint_as_float(v[c]) + s_bias[32 * half + c]) : 0.f;
-              const float v1 = live ? fmaxf(0.f, __uint_as_float(v[c + 1]) + s_bias[32 * half + c + 1]) : 0.f;
-              __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-              pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
-            }
-          } else {
-            uint4 mk[4];
-  #pragma unroll
-            for (int q = 0; q < 4; ++q) mk[q] = *reinterpret_cast<const uint4*>(A.mask + pix + q * plane);
-            const __nv_bfloat16* mh = reinterpret_cast<const __nv_bfloat16*>(mk);
-  #pragma unroll
-            for (int c = 0; c < 32; c += 2) {
-              const float v0 = (live && __bfloat162float(mh[c]) > 0.f) ? __uint_as_float(v[c]) : 0.f;
-              const float v1 = (live && __bfloat162float(mh[c + 1]) > 0.f) ? __uint_as_float(v[c + 1]) : 0.f;
-              __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
-              pw[c / 2] = *reinterpret_cast<uint32_t*>(&h);
-            }
-          }
-  #pragma unroll
-          for (int q = 0; q < 4; ++q) *reinterpret_cast<uint4*>(A.out + pix + q * plane) = pk[q];
-        }
-        g0 += R;
-      }
-  
-    } else {
-      // ---------------- last layer: warp w drains the output rows of phase w / 4 (ring index mod 4);
-      // it reads column 0 (N(z) before its bias) of TMEM lanes 32 (w % 4) .. + 31, i.e. pixels
-      // 32 (w % 4) + lane, and writes max(0, z - N(z)) on the facet core.  The row's z and x_prev
-      // are loaded before the wait for its accumulator, so their latency overlaps it.
-      const int lq = warp & 3, phase = warp >> 2;
-      const int m = lq * 32 + lane;
-      double s0 = 0.0, s1 = 0.0;
-      uint32_t g0 = 0;
-      bool stop = false;
-      for (int strip = blockIdx.x; strip < A.n_strips && !stop; strip += stride) {
-        const int4 S = A.strips[strip];
-        const int ya = S.z >> 16, R = S.z & 0xFFFF;
-        const int4 fc = A.facets[S.x], core = A.cores[S.x];
-        for (int r = (int)((phase - g0) & 3); r < R; r += 4) {  // rows whose ring index is = phase mod 4
-          const uint32_t g = g0 + r, k = g % ACC_SLOTS;
-          const int iy = fc.x + ya + r, ix = fc.y + S.y + m;
-          const bool in_core = iy >= core.x && iy < core.y && ix >= core.z && ix < core.w;
-          const size_t p = in_core ? (size_t)iy * A.n + ix : 0;
-          const float zv = in_core ? A.z[p] : 0.f;
-          const float xp = (in_core && A.x_prev) ? A.x_prev[p] : 0.f;
-          const bool ok = !s_abort && bar_wait(&t_full[k], (g / ACC_SLOTS) & 1);
-          if (!ok) s_abort = 1;
-          if (!__all_sync(0xffffffffu, ok)) {
-            stop = true;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t v = tmem_ld1(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(k * NO));
-          tmem_wait_ld();
-          tc_fence_before();
-          bar_arrive(&t_empty[k]);
-          if (!in_core) continue;
-          const float res = zv - (__uint_as_float(v) + A.b8);
-          const float o = A.pos ? fmaxf(0.f, res) : res;
-          A.img[p] = o;
-          s1 += (double)o * o;
-          // fmaxf(0, NaN) is 0, so positivity would hide a non-finite input: poison the norms
-          if (!isfinite(zv)) s1 = __longlong_as_double(0x7ff8000000000000LL);
-          if (A.x_prev) {
-            const double dd = (double)o - xp;
-            s0 += dd * dd;
-          }
-        }
-        g0 += R;
-      }
-      if (A.acc) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        }
-        if (lane == 0) {
-          atomicAdd(&A.acc[0], s0);
-          atomicAdd(&A.acc[1], s1);
-        }
-      }
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == MMA_WARP) {
-    tc_fence_after();
-    tmem_dealloc(tmem, Gm::TMEM_COLS);
-  }
-  if (threadIdx.x == 0 && s_abort) atomicOr(A.status, 2);
-}
 
 // ------------------------------------------------------------ hidden layers, per-input-row accumulators
 // The 64 -> 64 convolution with one fresh accumulator per staged input row: the 12 MMAs of input row s
@@ -513,8 +193,8 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_tc(ConvArgs A, const _
 // D_s = its contributions to output rows s - 2, s - 1, s, in one of two 192-column TMEM buffers, and the
 // epilogue sums the three parts of each output row in registers: out(s - 2) = (D_{s-2}[dy 0] +
 // D_{s-1}[dy 1]) + D_s[dy 2].  Every MMA has the full N = 192 (no accumulator ring to wrap, no fresh-row
-// split), so an input row costs exactly 12 MMAs.  Staging, TMA ring and warp roles as in conv64_tc;
-// epilogue warp w reads TMEM lanes 32 (w % 4) .. + 31 and channels 16 (w / 4) .. + 15 of each part.
+// split), so an input row costs exactly 12 MMAs.  Warp roles: warps 0-15 the epilogue, warp 16 the MMAs
+// (one lane), warp 17 the TMA loads (one lane); epilogue warp w reads TMEM lanes 32 (w % 4) .. + 31 and channels 16 (w / 4) .. + 15 of each part.
 constexpr int ROW_N = 3 * CH;                 // 192 accumulator columns per staged input row
 constexpr int ROW_DBUF = 2;                   // TMEM buffers (2 x 192 of the 512 columns)
 
@@ -528,7 +208,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_rows(ConvArgs A, const __grid_constant__ CUtensorMap tmain,
                                                                const __grid_constant__ CUtensorMap thalo) {
-  using Gm = ConvGeom<CH>;
   extern __shared__ __align__(1024) unsigned char sm[];  // [IN_SLOTS][ROW_BYTES] input ring, then B
   unsigned char* sb = sm + IN_SLOTS * ROW_BYTES;
   __shared__ uint64_t in_full[IN_SLOTS], in_empty[IN_SLOTS], d_full[ROW_DBUF], d_empty[ROW_DBUF];
@@ -539,7 +218,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_rows(ConvArgs A, const
   {
     const uint4* src = reinterpret_cast<const uint4*>(A.w);
     uint4* dst = reinterpret_cast<uint4*>(sb);
-    for (int i = threadIdx.x; i < Gm::B_BYTES / 16; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < B_BYTES / 16; i += blockDim.x) dst[i] = src[i];
     if (threadIdx.x < CH) s_bias[threadIdx.x] = A.bias ? A.bias[threadIdx.x] : 0.f;
   }
   if (threadIdx.x == 0) {
@@ -566,7 +245,9 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_rows(ConvArgs A, const
   const int stride = gridDim.x;
 
   if (warp == TMA_WARP) {
-    // ---------------- TMA producer (as conv64_tc): input rows ya-1 .. ya+R, pixels x0-1 .. x0+128
+    // ---------------- TMA producer: input rows ya-1 .. ya+R of each strip, pixels x0-1 .. x0+128; per
+    // 8-channel block pixels x0-1 .. x0+126 (2 KB) and x0+127, x0+128 (32 B), each a run of whole sectors
+    // of the block's plane (the canvas seen as 8-byte elements, 2 per pixel)
     if (lane == 0) {
       uint32_t L = 0;
       for (int strip = blockIdx.x; strip < A.n_strips && !s_abort; strip += stride) {
@@ -594,7 +275,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_rows(ConvArgs A, const
     // ---------------- MMA issuer: 12 MMAs of N = 192 per staged input row into buffer L % 2
     if (lane == 0) {
       const uint64_t adesc0 = smem_desc(su32(sm), KB_BYTES, 128);
-      const uint64_t bdesc0 = smem_desc(su32(sb), Gm::B_GROUP_BYTES, 128);
+      const uint64_t bdesc0 = smem_desc(su32(sb), B_GROUP_BYTES, 128);
       const uint32_t idesc = idesc_n(ROW_N);
       uint32_t L = 0;
       for (int strip = blockIdx.x; strip < A.n_strips && !s_abort; strip += stride) {
@@ -611,7 +292,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 1) conv64_rows(ConvArgs A, const
           for (int dk = 0; dk < 12; ++dk) {
             const int dx = dk >> 2, kk = dk & 3;
             const uint64_t ad = arow + (uint64_t)((2 * kk * KB_BYTES + dx * 16) >> 4);
-            const uint64_t bd = bdesc0 + (uint64_t)(((dx * 8 + 2 * kk) * Gm::B_GROUP_BYTES) >> 4);
+            const uint64_t bd = bdesc0 + (uint64_t)(((dx * 8 + 2 * kk) * B_GROUP_BYTES) >> 4);
             mma_bf16(d, ad, bd, idesc, dk > 0 ? 1u : 0u);
           }
           mma_commit(&in_empty[slot]);  // the input slot may be refilled
@@ -939,11 +620,6 @@ __global__ void __launch_bounds__(LAST_THREADS) cnn_last(LastArgs A) {
 }
 
 // ------------------------------------------------------------ host helpers
-// B operand of the last layer: weight W8[0][ci][dy][dx] at [dx][ci / 8][2 - dy][co = 0 of 16][ci % 8]
-size_t last_wpack_index(int dy, int dx, int ci) {
-  return ((((size_t)dx * 8 + (ci >> 3)) * 3 + (2 - dy)) * NO_LAST + 0) * 8 + (ci & 7);
-}
-
 uint16_t to_bf16_bits(float f) {
   uint32_t u;
   std::memcpy(&u, &f, 4);
@@ -957,7 +633,7 @@ float bf16_round(float f) {
   return o;
 }
 
-// The two TMA descriptors of a canvas for conv64_tc's row loads (main and halo boxes of one
+// The two TMA descriptors of a canvas for conv64_rows's row loads (main and halo boxes of one
 // channel block's plane row, the canvas seen as 8-byte elements).
 int make_canvas_maps(CUtensorMap* maps, const __nv_bfloat16* canvas, int F, int Hc, int Wc) {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
@@ -1100,12 +776,8 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
     for (int co = 0; co < CH; ++co) bias[(l + 1) * CH + co] = W[off + co];
     off += CH;
   }
-  std::vector<uint16_t> wlast(ConvGeom<NO_LAST>::B_BYTES / 2, 0);
   for (int ci = 0; ci < CH; ++ci)
-    for (int t = 0; t < 9; ++t) {
-      w8[t * CH + ci] = bf16_round(W[off + ci * 9 + t]);
-      wlast[last_wpack_index(t / 3, t % 3, ci)] = to_bf16_bits(W[off + ci * 9 + t]);
-    }
+    for (int t = 0; t < 9; ++t) w8[t * CH + ci] = bf16_round(W[off + ci * 9 + t]);
   // mma.sync B fragments of the tap projection: element (k, n) of K step ks / N tile nt is
   // W8[c = 16 ks + k][tap = 8 nt + n] (zero for taps >= 9); lane l holds k = 2 (l % 4) (+1) in its
   // first register and k + 8 (+9) in its second, n = l / 4, the lower k in the low half
@@ -1139,7 +811,6 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   }
   if (int rc = al((void**)&S->d_facets, S->F * sizeof(int4))) return rc;
   if (int rc = al((void**)&S->d_cores, S->F * sizeof(int4))) return rc;
-  if (int rc = al((void**)&S->d_wlast, wlast.size() * 2)) return rc;
   if (int rc = al((void**)&S->d_wfrag, wfrag.size() * 4)) return rc;
   if (int rc = al((void**)&S->d_w1, w1.size() * 4)) return rc;
   if (int rc = al((void**)&S->d_w8, w8.size() * 4)) return rc;
@@ -1149,7 +820,6 @@ int cnn_create(pnp_den* d, const float* W, const int32_t* fr, int nfr, const int
   PNP_CUDA(cudaMemcpy(S->d_facets, facets.data(), S->F * sizeof(int4), cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_cores, cores.data(), S->F * sizeof(int4), cudaMemcpyHostToDevice));
   if (int rc = build_strips(S, S->strip_rows)) return rc;
-  PNP_CUDA(cudaMemcpy(S->d_wlast, wlast.data(), wlast.size() * 2, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_wfrag, wfrag.data(), wfrag.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_w1, w1.data(), w1.size() * 4, cudaMemcpyHostToDevice));
   PNP_CUDA(cudaMemcpy(S->d_w8, w8.data(), w8.size() * 4, cudaMemcpyHostToDevice));
@@ -1170,7 +840,6 @@ void cnn_destroy(pnp_den* d) {
   cudaFree(S->d_cores);
   cudaFree(S->d_strips);
   cudaFree(S->d_lstrips);
-  cudaFree(S->d_wlast);
   cudaFree(S->d_wfrag);
   cudaFree(S->d_w1);
   cudaFree(S->d_w8);
@@ -1194,9 +863,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
   }
   static bool attr = false;
   if (!attr) {
-    PNP_CUDA(cudaFuncSetAttribute(conv64_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, ConvGeom<CH>::SMEM));
-    PNP_CUDA(cudaFuncSetAttribute(conv64_tc<NO_LAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  ConvGeom<NO_LAST>::SMEM));
+    PNP_CUDA(cudaFuncSetAttribute(conv64_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM));
     attr = true;
   }
   int cur = 0;
@@ -1204,18 +871,11 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
     ConvArgs C{S->d_canvas[1 - cur], S->d_wmid + (size_t)l * 9 * CH * CH, S->d_b + (l + 1) * CH, S->d_strips,
                S->n_strips, S->Hc, S->Wc, S->d_status, 0, nullptr};
     const int grid = std::max(1, std::min(S->n_strips, sms));
-    conv64_rows<<<grid, CONV_THREADS, ConvGeom<CH>::SMEM, s>>>(C, S->map[cur][0], S->map[cur][1]);
+    conv64_rows<<<grid, CONV_THREADS, CONV_SMEM, s>>>(C, S->map[cur][0], S->map[cur][1]);
     PNP_CHECK_LAUNCH();
     cur = 1 - cur;
   }
-  if (S->last_tc) {
-    // layer 8 as the tensor-core convolution, fused with D(z) = max(0, z - N(z)) on the facet cores
-    ConvArgs C{nullptr, S->d_wlast, nullptr, S->d_lstrips, S->n_lstrips, S->Hc, S->Wc, S->d_status, 2, nullptr,
-               z, x_prev, out, n, S->d_facets, S->d_cores, S->b8, acc, positivity ? 1 : 0};
-    const int grid = std::max(1, std::min(S->n_lstrips, sms));
-    conv64_tc<NO_LAST><<<grid, CONV_THREADS, ConvGeom<NO_LAST>::SMEM, s>>>(C, S->map[cur][0], S->map[cur][1]);
-    PNP_CHECK_LAUNCH();
-  } else {
+  {
     // layer 8 as a tap projection + 3 x 3 gather, fused with D(z) = max(0, z - N(z)) and the norms
     LastArgs L{S->d_canvas[cur], S->d_lstrips, S->n_lstrips, S->Hc, S->Wc, n, S->d_facets, S->d_cores,
                S->d_wfrag, S->b8, z, x_prev, out, acc, positivity ? 1 : 0};
@@ -1230,13 +890,13 @@ int conv64_launch(cudaStream_t s, const void* in_map, __nv_bfloat16* out, const 
                   const __nv_bfloat16* mask, int* status) {
   static bool attr = false;
   if (!attr) {
-    PNP_CUDA(cudaFuncSetAttribute(conv64_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, ConvGeom<CH>::SMEM));
+    PNP_CUDA(cudaFuncSetAttribute(conv64_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM));
     attr = true;
   }
   ConvArgs C{out, w_packed, bias, strips, n_strips, Hc, Wc, status, mode, mask};
   const int grid = std::max(1, std::min(n_strips, sms_of_device()));
   const CUtensorMap* maps = static_cast<const CUtensorMap*>(in_map);
-  conv64_rows<<<grid, CONV_THREADS, ConvGeom<CH>::SMEM, s>>>(C, maps[0], maps[1]);
+  conv64_rows<<<grid, CONV_THREADS, CONV_SMEM, s>>>(C, maps[0], maps[1]);
   PNP_CHECK_LAUNCH();
   return PNP_OK;
 }

@@ -229,7 +229,7 @@ __host__ __device__ __forceinline__ size_t conv_wpack_index(int dy, int dx, int 
   return ((((size_t)dx * 8 + (ci >> 3)) * 3 + (2 - dy)) * 64 + co) * 8 + (ci & 7);
 }
 constexpr int STRIP_ROWS = 32;  // target output rows per convolution work unit
-// Work list of conv64_tc: per facet, 128-column segments split into strips of about STRIP_ROWS
+// Work list of the hidden-layer convolution (conv64_rows): per facet, 128-column segments split into strips of about STRIP_ROWS
 // output rows; each entry is (facet, x0, ya << 16 | rows, Hf << 16 | Wf).
 std::vector<int4> conv_strips(int F, const int* Hf, const int* Wf, int rows = STRIP_ROWS);
 // the denoiser's convolution work lists rebuilt for strips of about `rows` output rows (4..1024)
