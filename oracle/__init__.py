@@ -21,7 +21,9 @@ cnn     residual CNN denoiser (App. C): forward, backward, l1 training loss,
 
 Parity status: every function is pinned by a ``-m "not gpu"`` test against
 something other than itself (a library routine, a closed form, an invariant
-or brute force) except ``fb.snr_db`` and ``fb.pnp_fb``'s reconstruction
-quality, for which the paper prints no value on synthetic data: parity
-unpinned (comparative only).
+or brute force): ``fb.snr_db`` by closed-form cases of its definition and
+``fb.pnp_fb`` by its limits with the identity and positivity denoisers
+(numpy's least squares and scipy's NNLS on the dense system).  The paper
+prints no reconstruction SNR for synthetic data, so the SNR values the loops
+reach on the synthetic skies are comparative, not pinned to the paper.
 """

@@ -190,3 +190,56 @@ def test_alpha_rescaling_is_exact_for_the_haar_loop():
     assert np.allclose(x1, x2, rtol=1e-12, atol=1e-12 * abs(x1).max())
     x3, _ = fb.pnp_fb(op, y, gamma, lambda z: fb.haar_denoise(z, t), 40, alpha=alpha)
     assert not np.allclose(x1, x3, rtol=1e-6)   # the threshold does not scale by itself
+
+
+def test_snr_db_closed_forms():
+    """SNR = 20 log10(||x|| / ||x - x_hat||) on cases with a closed form: x_hat = (1 - e) x gives
+    -20 log10(e) (20 dB at e = 0.1; an SNR taken against x_hat instead of x would give 19.08), a
+    perturbation orthogonal to x of relative norm 10^(-k/20) gives k dB, x_hat = 0 gives 0 dB, and
+    the value is invariant to a common scale (a swapped ratio would give negative values)."""
+    rng = np.random.default_rng(31)
+    x = rng.standard_normal((12, 12))
+    for e in (0.1, 0.01, 0.5):
+        assert fb.snr_db(x, (1.0 - e) * x) == pytest.approx(-20.0 * np.log10(e), rel=1e-12)
+    p = rng.standard_normal(x.shape)
+    p -= np.vdot(x, p) / np.vdot(x, x) * x                     # orthogonal to x
+    for k in (3.0, 17.5, 40.0):
+        xh = x + p * (np.linalg.norm(x) / np.linalg.norm(p)) * 10.0 ** (-k / 20.0)
+        assert fb.snr_db(x, xh) == pytest.approx(k, abs=1e-10)
+        assert fb.snr_db(3.7 * x, 3.7 * xh) == pytest.approx(k, abs=1e-10)
+    assert fb.snr_db(x, np.zeros_like(x)) == pytest.approx(0.0, abs=1e-12)
+
+
+def _dense_real_system(op, y):
+    """Phi as a dense complex matrix (columns Phi e_i), stacked as the real least-squares system
+    [Re Phi; Im Phi] x = [Re y; Im y] of 1/2 ||Phi x - y||^2 over real images x."""
+    n = op.n
+    cols = []
+    for i in range(n * n):
+        e = np.zeros(n * n)
+        e[i] = 1.0
+        cols.append(op.forward(e.reshape(n, n)))
+    P = np.stack(cols, axis=1)
+    return np.vstack([P.real, P.imag]), np.concatenate([y.real, y.imag])
+
+
+@pytest.mark.parametrize("den", ["identity", "positivity"])
+def test_pnp_fb_converges_to_the_library_least_squares_solution(den):
+    """Eq. fb with D = identity is gradient descent on 1/2 ||Phi x - y||^2 and with D = positivity
+    projected gradient descent: run to convergence, the oracle's loop must reach the minimiser that
+    numpy's lstsq, respectively scipy's NNLS, computes from the dense system (a wrong sign, a dropped
+    y term or a conjugated operand in the gradient converges elsewhere or diverges)."""
+    from scipy.optimize import nnls
+    op, rng = _small_problem(n=6, K=12, M=200, seed=41)
+    x_true = rng.standard_normal((6, 6))
+    y = op.forward(x_true) + 0.3 * synth.complex_normal(op.M, rng)
+    A, b = _dense_real_system(op, y)
+    if den == "identity":
+        ref = np.linalg.lstsq(A, b, rcond=None)[0].reshape(6, 6)
+        D = lambda z: z                      # noqa: E731
+    else:
+        ref = nnls(A, b, maxiter=10000)[0].reshape(6, 6)
+        D = lambda z: np.maximum(z, 0.0)     # noqa: E731
+    L = np.linalg.norm(A, 2) ** 2
+    x, _ = fb.pnp_fb(op, y, fb.step_size(L), D, 20000, tol=1e-15)
+    assert np.linalg.norm(x - ref) <= 1e-8 * np.linalg.norm(ref)
