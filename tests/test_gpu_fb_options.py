@@ -121,4 +121,11 @@ def test_learned_loop_falls_back_to_the_plain_loop_on_divergence():
     xa, _ = plan.fb_run(cnn, yw, L=L, max_iter=st.fallback_iter, check_every=5, use_graph=False)
     xb, _ = plan.fb_run(pnp.HaarDenoiser(t), yw, x0=xa, L=L, max_iter=60 - st.fallback_iter, check_every=5,
                         use_graph=False)
-    assert rel_l2(xg, to_host(xb)) <= 1e-4
+    # The two runs are the same kernels on the same inputs, but the gridding pass sums with FP32 atomics
+    # in no fixed order, and in the learned stage a last-bit difference can move a hidden activation
+    # across a BF16 rounding boundary (a 2^-9 relative step for that pixel).  Measured on a GB300:
+    # five learned iterations repeated on identical inputs differ in ~900 of 4096 pixels (1.2e-7 rel.
+    # L2), and repeated identical fallback runs differ from one another by up to 6e-5 (1.2e-4 seen
+    # once against the two-stage run).  One BF16 step still separates this from every wrong restart
+    # (the iterate doubles per learned iteration, so restarting one check late is 32x off).
+    assert rel_l2(xg, to_host(xb)) <= 2.0 ** -8
