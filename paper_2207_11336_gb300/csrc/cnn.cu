@@ -67,7 +67,7 @@ constexpr int CONV_SMEM = IN_SLOTS * ROW_BYTES + B_BYTES;  // 212992
 constexpr int EPI_WARPS = 16;                           // 4 lane quarters x 4 channel quarters
 constexpr int MMA_WARP = EPI_WARPS, TMA_WARP = EPI_WARPS + 1;
 constexpr int CONV_THREADS = (EPI_WARPS + 2) * 32;
-constexpr int FIRST_ROWS = 16;                          // cnn_first: image rows per block
+constexpr int FIRST_ROWS = 64;                          // cnn_first: image rows per block
 constexpr uint32_t CNN_WAIT_LIMIT = 1u << 26;
 
 struct CnnState {
