@@ -469,10 +469,15 @@ __global__ void __launch_bounds__(256) cnn_first(FirstArgs A) {
 // three projected rows in shared memory, fused with D(z) = max(0, z - N(z)) and the FP64
 // stopping-test sums.  A CTA walks one strip of the last layer's work list (128 core columns x
 // about 32 core rows of a facet) row by row; P covers the 144 pixels x0 - 1 .. x0 + 142 of each
-// activation row (9 M tiles of 16), so the gather never leaves the CTA.
+// activation row (9 M tiles of 16), so the gather never leaves the CTA.  Each activation row is
+// copied into shared memory with cp.async (16-byte pieces, whole runs of each channel block's
+// plane, zero-filled outside the facet) one row ahead of its projection, double buffered, and the
+// A fragments are read from there with ldmatrix.
 constexpr int LAST_PX = 144;   // projected pixels per row: x0 - 1 .. x0 + 142
 constexpr int LAST_TS = 9;     // taps kept per pixel in shared memory (row stride: conflict-free gathers)
 constexpr int LAST_THREADS = 128;
+constexpr int LAST_ROW_BYTES = 8 * LAST_PX * 16;                                  // one staged row: [block][px][8 ch]
+constexpr int LAST_SMEM = 2 * LAST_ROW_BYTES + 3 * LAST_PX * LAST_TS * 4;        // two staged rows + the P ring
 
 struct LastArgs {
   const __nv_bfloat16* canvas;  // layer-7 activations (canvas layout)
@@ -496,9 +501,35 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
+__device__ __forceinline__ void ldmatrix_x4(uint32_t (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(su32(p)));
+}
+// 16-byte global -> shared copy; nbytes = 0 fills the 16 bytes with zeros (src is not read)
+__device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, int nbytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(su32(dst)), "l"(src), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// activation row r of facet f, pixels x0 - 1 .. x0 + 142, into a staged row [block][px][8 ch] (zero outside
+// rows [0, Hf) and columns [0, Wf): the 'same' padding at the facet's edges)
+__device__ __forceinline__ void last_stage_row(unsigned char* dst, const LastArgs& A, int f, int r, int x0, int Hf,
+                                               int Wf) {
+  const bool row_ok = r >= 0 && r < Hf;
+  for (int c = threadIdx.x; c < 8 * LAST_PX; c += LAST_THREADS) {
+    const int b = c / LAST_PX, p = c - b * LAST_PX, x = x0 - 1 + p;
+    const bool in = row_ok && x >= 0 && x < Wf;
+    const __nv_bfloat16* src = in ? A.canvas + canvas_index(f, r, x, 8 * b, A.Hc, A.Wc) : A.canvas;
+    cp_async16_zfill(dst + (size_t)c * 16, src, in ? 16 : 0);
+  }
+}
 
 __global__ void __launch_bounds__(LAST_THREADS) cnn_last(LastArgs A) {
-  __shared__ float sP[3][LAST_PX * LAST_TS];
+  extern __shared__ __align__(128) unsigned char lsm[];  // [2][LAST_ROW_BYTES] staged rows, then sP
+  float(*sP)[LAST_PX * LAST_TS] = reinterpret_cast<float(*)[LAST_PX * LAST_TS]>(lsm + 2 * LAST_ROW_BYTES);
   __shared__ double red[2][LAST_THREADS / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, t4 = lane & 3;
@@ -511,47 +542,40 @@ __global__ void __launch_bounds__(LAST_THREADS) cnn_last(LastArgs A) {
       bw[ks][nt][0] = v.x;
       bw[ks][nt][1] = v.y;
     }
+  // ldmatrix row addresses: lane l points at pixel (l % 8) + 8 ((l / 8) % 2) of the tile in channel block
+  // 2 ks + l / 16, so the four matrices are the m16n8k16 A fragments a0..a3
+  const int lrow = (lane & 7) + 8 * ((lane >> 3) & 1), lblk = lane >> 4;
   double s0 = 0.0, s1 = 0.0;
-  const size_t plane = (size_t)A.Wc * 8;
   for (int si = blockIdx.x; si < A.n_strips; si += gridDim.x) {
     const int4 S = A.strips[si];
     const int f = S.x, x0 = S.y, ya = S.z >> 16, R = S.z & 0xFFFF, Hf = S.w >> 16, Wf = S.w & 0xFFFF;
     const int4 fc = A.facets[f], core = A.cores[f];
-    for (int r = ya - 1; r <= ya + R; ++r) {
-      // ---- project activation row r onto the taps: warp w takes M tiles w, w + 4, w + 8.  All of a
-      // warp's A fragments of the row are loaded before its first MMA, so their loads are in flight
-      // together.
-      float* P = sP[(r - ya + 1) % 3];
-      const bool row_ok = r >= 0 && r < Hf;
-      const size_t rbase = ((size_t)f * A.Hc + (row_ok ? r : 0)) * 8 * plane;
-      constexpr int TPW = (LAST_PX / 16 + LAST_THREADS / 32 - 1) / (LAST_THREADS / 32);  // tiles per warp
-      uint32_t a[TPW][4][4];
-#pragma unroll
-      for (int ti = 0; ti < TPW; ++ti) {
-        const int mt = warp + ti * (LAST_THREADS / 32);
-        const int p_lo = x0 - 1 + mt * 16 + g, p_hi = p_lo + 8;  // pixels of fragment rows g and g + 8
-        const bool tile = mt < LAST_PX / 16;
-        const bool ok_lo = tile && row_ok && p_lo >= 0 && p_lo < Wf, ok_hi = tile && row_ok && p_hi >= 0 && p_hi < Wf;
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          // channels 16 ks + 2 t4 (+1) sit in channel block 2 ks, 16 ks + 8 + 2 t4 (+1) in block 2 ks + 1
-          const uint32_t* b0 = reinterpret_cast<const uint32_t*>(A.canvas + rbase + (size_t)(2 * ks) * plane);
-          const uint32_t* b1 = reinterpret_cast<const uint32_t*>(A.canvas + rbase + (size_t)(2 * ks + 1) * plane);
-          a[ti][ks][0] = ok_lo ? __ldg(b0 + (size_t)p_lo * 4 + t4) : 0u;
-          a[ti][ks][1] = ok_hi ? __ldg(b0 + (size_t)p_hi * 4 + t4) : 0u;
-          a[ti][ks][2] = ok_lo ? __ldg(b1 + (size_t)p_lo * 4 + t4) : 0u;
-          a[ti][ks][3] = ok_hi ? __ldg(b1 + (size_t)p_hi * 4 + t4) : 0u;
-        }
+    last_stage_row(lsm, A, f, ya - 1, x0, Hf, Wf);
+    cp_async_commit_group();
+    for (int i = 0; i < R + 2; ++i) {
+      const int r = ya - 1 + i;
+      if (i + 1 < R + 2) {  // the next row's copies fly while this row is projected
+        last_stage_row(lsm + ((i + 1) & 1) * LAST_ROW_BYTES, A, f, r + 1, x0, Hf, Wf);
+        cp_async_commit_group();
+        cp_async_wait_group<1>();
+      } else {
+        cp_async_wait_group<0>();
       }
+      __syncthreads();  // row r staged by every thread; the gather of the previous row is done with its slot
+      // ---- project activation row r onto the taps: warp w takes M tiles w, w + 4, w + 8
+      const unsigned char* st = lsm + (i & 1) * LAST_ROW_BYTES;
+      float* P = sP[(r - ya + 1) % 3];
 #pragma unroll
-      for (int ti = 0; ti < TPW; ++ti) {
+      for (int ti = 0; ti < 3; ++ti) {
         const int mt = warp + ti * (LAST_THREADS / 32);
         if (mt >= LAST_PX / 16) break;  // warp-uniform
         float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
-          mma_bf16_16816(d0, a[ti][ks], bw[ks][0][0], bw[ks][0][1]);
-          mma_bf16_16816(d1, a[ti][ks], bw[ks][1][0], bw[ks][1][1]);
+          uint32_t a[4];
+          ldmatrix_x4(a, st + ((size_t)(2 * ks + lblk) * LAST_PX + mt * 16 + lrow) * 16);
+          mma_bf16_16816(d0, a, bw[ks][0][0], bw[ks][0][1]);
+          mma_bf16_16816(d1, a, bw[ks][1][0], bw[ks][1][1]);
         }
         // D fragment: (row g, cols 2 t4, 2 t4 + 1) and (row g + 8, same cols); taps 0..7 in tile 0, 8 in tile 1
         const int pl = mt * 16 + g, ph = pl + 8;
@@ -593,8 +617,10 @@ __global__ void __launch_bounds__(LAST_THREADS) cnn_last(LastArgs A) {
           }
         }
       }
-      __syncthreads();  // the slot of row r - 2 is overwritten next
+      // the next iteration's __syncthreads orders this gather before the ring slot of row r - 2 (and the
+      // staged row just projected) are overwritten
     }
+    __syncthreads();  // the next strip's first copies go to buffer 0 and the ring restarts
   }
   if (A.acc) {
 #pragma unroll
@@ -864,6 +890,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
   static bool attr = false;
   if (!attr) {
     PNP_CUDA(cudaFuncSetAttribute(conv64_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, CONV_SMEM));
+    PNP_CUDA(cudaFuncSetAttribute(cnn_last, cudaFuncAttributeMaxDynamicSharedMemorySize, LAST_SMEM));
     attr = true;
   }
   int cur = 0;
@@ -879,7 +906,7 @@ int cnn_denoise(pnp_den* d, cudaStream_t s, const float* z, float* out, int n, d
     // layer 8 as a tap projection + 3 x 3 gather, fused with D(z) = max(0, z - N(z)) and the norms
     LastArgs L{S->d_canvas[cur], S->d_lstrips, S->n_lstrips, S->Hc, S->Wc, n, S->d_facets, S->d_cores,
                S->d_wfrag, S->b8, z, x_prev, out, acc, positivity ? 1 : 0};
-    cnn_last<<<std::max(1, S->n_lstrips), LAST_THREADS, 0, s>>>(L);
+    cnn_last<<<std::max(1, S->n_lstrips), LAST_THREADS, LAST_SMEM, s>>>(L);
     PNP_CHECK_LAUNCH();
   }
   return PNP_OK;
