@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--band-mhz", type=float, default=1053.0,
                     help="frequency band of the 8192^2 workload (C4): 1053 or 1399")
     ap.add_argument("--weights-l1", default=None, help="network of the learned_l1 comparison line")
+    ap.add_argument("--train-batch", type=int, default=16,
+                    help="batch of 256^2 images of the timed denoiser training steps (0 skips them)")
     ap.add_argument("--kernel-case", choices=["gridding", "cnn", "fft"], default=None,
                     help="run a small profiling case of one kernel (for ncu) instead of the benchmark")
     ap.add_argument("--cnn-side", type=int, default=4096,
@@ -339,6 +341,43 @@ def _timed_loop(plan, den, y, x, gamma, L, steps, stream, alpha=1.0):
     return ev0.elapsed_time(ev1), pnp.kernel_launches() - k0
 
 
+def _time_training(params, batch, stream, size=256, reps=10, fne_reps=3):
+    """Milliseconds per denoiser training step on the GPU (App. C): the l1 step (forward, back-propagation,
+    weight gradients, Adam) and the step with the soft firm non-expansiveness penalty of Eq. training_loss
+    (20 power iterations on J_Q^T J_Q, lambda 10, the last fine-tuning stage's settings), on a batch of
+    ``batch`` synthetic size^2 training images; CUDA events on the trainer's stream.  A separate trainer
+    starting from the benchmark's network: its updates are discarded."""
+    import torch
+    import paper_2207_11336_gb300 as pnp
+    import synth
+    rng = np.random.default_rng(17)
+    u = torch.from_numpy(np.stack([synth.training_image(size, rng) for _ in range(batch)]).astype(np.float32)).cuda()
+    nz = torch.from_numpy(rng.standard_normal((batch, size, size)).astype(np.float32)).cuda()
+    v0 = torch.from_numpy(rng.standard_normal((batch, size, size)).astype(np.float32)).cuda()
+    sigma = 0.05
+    tr = pnp.CnnTrainer(params, batch, size, lr=1e-6, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, k):
+        fn()
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    ms_l1 = timed(lambda: tr.step(u, nz, sigma), reps)
+    ms_fne = timed(lambda: tr.step_fne(u, nz, sigma, v0, 20, 10.0, 0.05), fne_reps)
+    tr.close()
+    flop = 3 * batch * size * size * CNN_FLOP_PER_PX   # forward, data gradients, weight gradients
+    return {"batch": f"{batch} x {size}^2 synthetic training images", "l1_ms_per_step": ms_l1,
+            "l1_images_per_s": batch / ms_l1 * 1e3, "l1_TFLOPs": flop / (ms_l1 * 1e-3) / 1e12,
+            "fne_ms_per_step": ms_fne, "fne_power_iterations": 20}
+
+
 def _run_to_snr(plan, den, y, gamma, L, x_true, alpha, target, max_iters):
     """Run the loop from x = 0 in chunks of SNR_CHUNK iterations until SNR >= target (or max_iters);
     returns (iterations to the target or None, [(iterations, SNR dB)], final iterate)."""
@@ -591,6 +630,8 @@ def run_gpu(args):
                 "snr_db_final": trace_f[-1][1], "iters_run": trace_f[-1][0],
                 "snr_trace": _thin(trace_f, 100)}
             cnn_f.close()
+        if args.train_batch > 0:
+            comparison["training"] = _time_training(params, args.train_batch, stream)
 
     # ---- kernel timing: eager replay with CUDA events around each operator stage
     plan.set_timing(True)
